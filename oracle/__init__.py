@@ -1,0 +1,258 @@
+"""FP64 CPU oracle for one 3DGS^2-TR iteration (test infrastructure only).
+
+Only the tests, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline leg
+import this package; the product path never does.  The arithmetic lives in
+``gs_oracle.cpp`` (plain C++, FP64); this module only marshals numpy arrays.
+
+Parameter matrices are float64 [rows, n] (no padding), rows as in the
+package's synthetic-scene layout: 0..2 mean, 3..5 log-scale, 6..9 quaternion
+(x, y, z, w), 10 opacity logit, 11 + 3k + c SH coefficient k of channel c.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "gs_oracle.cpp")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+CXXFLAGS = ["-O2", "-std=c++17", "-ffp-contract=off", "-fPIC", "-shared"]
+
+
+def build(force: bool = False) -> str:
+    """Compile gs_oracle.cpp into liboracle.so (g++, a few seconds)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.run(["g++", *CXXFLAGS, "-o", tmp, _SRC], check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = C.CDLL(_LIB)
+            d, i64, u64, i32 = C.c_double, C.c_long, C.c_uint64, C.c_int
+            P = C.c_void_p
+            L.or_splitmix64.restype = u64
+            L.or_splitmix64.argtypes = [u64]
+            L.or_rademacher.restype = d
+            L.or_rademacher.argtypes = [u64, C.c_int64, i32, u64]
+            L.or_sh_basis.argtypes = [i32, P, P]
+            L.or_sh_absmax.argtypes = [i32, P]
+            L.or_quat_to_rotmat.argtypes = [P, P]
+            L.or_project.argtypes = [P, i64, i64, i32, P, P]
+            L.or_bin_sort.restype = i64
+            L.or_bin_sort.argtypes = [i32, i64, P, P, P, P, i32, i32, i32, i32, P, P, i64, P]
+            L.or_render.restype = i64
+            L.or_render.argtypes = [P, i64, i64, i32, P, i32, i32, i32, P, P, P, P]
+            L.or_jvp.argtypes = [P, i64, i64, i32, P, i32, i32, i32, P, P]
+            L.or_jacobian.argtypes = [P, i64, i64, i32, P, i32, i32, i32, P]
+            L.or_backward.restype = d
+            L.or_backward.argtypes = [P, i64, i64, i32, P, i32, i32, i32, P, i32, d, u64, C.c_int64, i32,
+                                      P, P, P, P]
+            L.or_shd_radius.argtypes = [P, i64, i64, i32, d, P, P]
+            L.or_tr_update.argtypes = [P, P, P, P, P, i64, i64, i32, P, C.c_int64, d, P]
+            L.or_signature.argtypes = [P, i64, i64, i32, P, i32, i32, i32, P]
+            L.or_hellinger.restype = d
+            L.or_hellinger.argtypes = [P, P, d, P, P, d]
+            L.or_rotation_beta.argtypes = [P, P, P]
+            _lib = L
+    return _lib
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def camera_array(cams) -> np.ndarray:
+    """24 doubles per camera: viewmat (16, row-major), fx, fy, cx, cy, near, width, height, 0."""
+    out = np.zeros((len(cams), 24))
+    for k, c in enumerate(cams):
+        out[k, :16] = np.asarray(c.viewmat, np.float64).reshape(16)
+        out[k, 16:23] = [c.fx, c.fy, c.cx, c.cy, c.near, c.width, c.height]
+    return out
+
+
+def params64(scene_or_params, n: int | None = None) -> np.ndarray:
+    """float64 [rows, n] copy of a scene's parameters with the padding dropped."""
+    if hasattr(scene_or_params, "params"):
+        return _f64(scene_or_params.params[:, : scene_or_params.n])
+    a = np.asarray(scene_or_params)
+    return _f64(a if n is None else a[:, :n])
+
+
+# ---------------------------------------------------------------- primitives
+def splitmix64(x: int) -> int:
+    return int(lib().or_splitmix64(x & 0xFFFFFFFFFFFFFFFF))
+
+
+def rademacher(seed: int, t: int, k: int, j: int) -> float:
+    return float(lib().or_rademacher(seed, t, k, j))
+
+
+def sh_basis(deg: int, direction) -> np.ndarray:
+    d = _f64(direction)
+    Y = np.zeros(16)
+    lib().or_sh_basis(deg, _p(d), _p(Y))
+    return Y[: (deg + 1) ** 2]
+
+
+def sh_absmax(deg: int) -> np.ndarray:
+    Y = np.zeros(16)
+    lib().or_sh_absmax(deg, _p(Y))
+    return Y[: (deg + 1) ** 2]
+
+
+def quat_to_rotmat(q) -> np.ndarray:
+    q = _f64(q)
+    R = np.zeros(9)
+    lib().or_quat_to_rotmat(_p(q), _p(R))
+    return R.reshape(3, 3)
+
+
+def hellinger(mu1, S1, Z1, mu2, S2, Z2) -> float:
+    return float(lib().or_hellinger(_p(_f64(mu1)), _p(_f64(S1)), Z1, _p(_f64(mu2)), _p(_f64(S2)), Z2))
+
+
+def rotation_beta(q, s) -> np.ndarray:
+    b = np.zeros(4)
+    lib().or_rotation_beta(_p(_f64(q)), _p(_f64(s)), _p(b))
+    return b
+
+
+# --------------------------------------------------------------- pipeline
+SPLAT_FIELDS = ("mx", "my", "A", "B", "C", "o", "r", "g", "b", "depth", "radius_raw", "radius", "valid")
+
+
+def project(P: np.ndarray, deg: int, cam) -> dict:
+    P = _f64(P)
+    rows, n = P.shape
+    out = np.zeros((n, 13))
+    ca = camera_array([cam])
+    lib().or_project(_p(P), n, n, deg, _p(ca), _p(out))
+    return {f: out[:, k] for k, f in enumerate(SPLAT_FIELDS)}
+
+
+def bin_sort(mx, my, radius, depth, width: int, height: int, tw: int = 16, th: int = 16):
+    """Pairs and tile ranges from FP32 splat records; arrays are [V, n] (or [n])."""
+    mx = np.ascontiguousarray(np.atleast_2d(mx), np.float32)
+    my = np.ascontiguousarray(np.atleast_2d(my), np.float32)
+    rad = np.ascontiguousarray(np.atleast_2d(radius), np.int32)
+    dp = np.ascontiguousarray(np.atleast_2d(depth), np.float32)
+    V, n = mx.shape
+    T = ((width + tw - 1) // tw) * ((height + th - 1) // th)
+    ranges = np.zeros((V * T, 2), np.uint32)
+    L = lib()
+    P = L.or_bin_sort(V, n, _p(mx), _p(my), _p(rad), _p(dp), width, height, tw, th, None, None, 0, _p(ranges))
+    keys = np.zeros(max(P, 1), np.uint64)
+    vals = np.zeros(max(P, 1), np.uint32)
+    L.or_bin_sort(V, n, _p(mx), _p(my), _p(rad), _p(dp), width, height, tw, th, _p(keys), _p(vals), P, _p(ranges))
+    return keys[:P], vals[:P], ranges
+
+
+def render(P: np.ndarray, deg: int, cams, tw: int = 16, th: int = 16, with_margin: bool = True):
+    P = _f64(P)
+    rows, n = P.shape
+    ca = camera_array(cams)
+    V = len(cams)
+    H, W = cams[0].height, cams[0].width
+    img = np.zeros((V, 3, H, W))
+    T = np.zeros((V, H, W))
+    nc = np.zeros((V, H, W), np.int32)
+    mg = np.zeros((V, H, W)) if with_margin else None
+    pairs = lib().or_render(_p(P), n, n, deg, _p(ca), V, tw, th, _p(img), _p(T), _p(nc), _p(mg))
+    return dict(image=img, final_T=T, n_contrib=nc, margin=mg, n_pairs=int(pairs))
+
+
+def jvp(P: np.ndarray, deg: int, cams, direction: np.ndarray, tw: int = 16, th: int = 16) -> np.ndarray:
+    P = _f64(P)
+    rows, n = P.shape
+    d = _f64(direction)
+    ca = camera_array(cams)
+    V = len(cams)
+    H, W = cams[0].height, cams[0].width
+    out = np.zeros((V, 3, H, W))
+    lib().or_jvp(_p(P), n, n, deg, _p(ca), V, tw, th, _p(d), _p(out))
+    return out
+
+
+def signature(P: np.ndarray, deg: int, cams, tw: int = 16, th: int = 16) -> np.ndarray:
+    """Per-pixel hash of the blend's discrete decisions (contributors, caps, clamps)."""
+    P = _f64(P)
+    rows, n = P.shape
+    ca = camera_array(cams)
+    V = len(cams)
+    H, W = cams[0].height, cams[0].width
+    out = np.zeros((V, H, W), np.uint64)
+    lib().or_signature(_p(P), n, n, deg, _p(ca), V, tw, th, _p(out))
+    return out
+
+
+def jacobian(P: np.ndarray, deg: int, cams, tw: int = 16, th: int = 16) -> np.ndarray:
+    """dC/dx: rows = V*3*H*W image entries, columns = rows_p * n parameters (index r*n + i)."""
+    P = _f64(P)
+    rows, n = P.shape
+    ca = camera_array(cams)
+    V = len(cams)
+    H, W = cams[0].height, cams[0].width
+    J = np.zeros((V * 3 * H * W, rows * n))
+    lib().or_jacobian(_p(P), n, n, deg, _p(ca), V, tw, th, _p(J))
+    return J
+
+
+def backward(P: np.ndarray, deg: int, cams, target: np.ndarray, *, loss_kind: int = 0,
+             gn_floor: float = 1e-3, seed: int = 42, t: int = 1, nu: int = 0,
+             tw: int = 16, th: int = 16, want_tangents: bool = False):
+    """Objective, gradient (rows x n) and, if nu > 0, the Hutchinson diagonal (rows x n)."""
+    P = _f64(P)
+    rows, n = P.shape
+    ca = camera_array(cams)
+    V = len(cams)
+    H, W = cams[0].height, cams[0].width
+    tg = _f64(target)
+    grad = np.zeros((rows, n))
+    hz = np.zeros((rows, n)) if nu > 0 else None
+    it = np.zeros((nu, V, 3, H, W)) if (want_tangents and nu > 0) else None
+    rm = np.zeros((V, H, W))
+    f = lib().or_backward(_p(P), n, n, deg, _p(ca), V, tw, th, _p(tg), loss_kind, gn_floor, seed, t, nu,
+                          _p(grad), _p(hz), _p(it), _p(rm))
+    return dict(loss=float(f), grad=grad, hz=hz, image_tangent=it, res_margin=rm)
+
+
+def tr_config(theta1=0.9, theta2=0.999, d_floor=1e-12, color_floor=1e-2, l=10, mean_exact=0) -> np.ndarray:
+    return np.array([theta1, theta2, d_floor, color_floor, l, mean_exact], np.float64)
+
+
+def shd_radius(P: np.ndarray, deg: int, eps: float, cfg=None) -> np.ndarray:
+    P = _f64(P)
+    rows, n = P.shape
+    cfg = tr_config() if cfg is None else _f64(cfg)
+    eta = np.zeros((rows, n))
+    lib().or_shd_radius(_p(P), n, n, deg, eps, _p(cfg), _p(eta))
+    return eta
+
+
+def tr_update(x, g_ema, d_ema, grad, hz, deg: int, t: int, eps: float, cfg=None):
+    """Algorithm 1 update for step t; returns new (x, g_ema, d_ema, eta) as float64 copies."""
+    x, g, d = _f64(x).copy(), _f64(g_ema).copy(), _f64(d_ema).copy()
+    gr = _f64(grad)
+    h = None if hz is None else _f64(hz)
+    rows, n = x.shape
+    cfg = tr_config() if cfg is None else _f64(cfg)
+    eta = np.zeros_like(x)
+    lib().or_tr_update(_p(x), _p(g), _p(d), _p(gr), _p(h), n, n, deg, _p(cfg), t, eps, _p(eta))
+    return x, g, d, eta

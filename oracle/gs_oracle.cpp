@@ -1,0 +1,1040 @@
+// Plain, slow FP64 CPU oracle for one 3DGS^2-TR iteration.
+//
+// TEST INFRASTRUCTURE ONLY.  Nothing in the product path links or calls this
+// file; only the tests, the package's smoke check and the benchmark's CPU
+// baseline leg do.  It shares no code, header, table or constant with the CUDA
+// library: every formula below is written out again from the paper and from the
+// 3DGS conventions it defers to.
+//
+// What it computes, and where each piece comes from:
+//   * Gaussian primitive and its parameters: Sec. 3.1, Eq. (gaussian-primitive).
+//   * EWA projection, SH colour, tile binning and depth order: Sec. 3.1 (the
+//     tile-based rasteriser the paper defers to 3DGS).
+//   * Alpha blending C = sum_i c_i a_i T_i, T_i = prod_{j<i}(1 - a_j): Sec. 3.1.
+//   * Least-squares objective f = 1/(2m) ||F||^2 with F = sqrt(|residual|):
+//     Sec. 3.2, Eq. (objective); gradient g = (1/m) J^T F: Sec. 4.1.
+//   * Hutchinson diagonal D = (1/m)(1/nu) sum_k z_k . (J^T J z_k): Sec. 4.1.
+//   * Algorithm 1 (EMA of g and D, Newton step, clip, update).
+//   * Squared Hellinger distance and the per-parameter radii: Sec. 4.2 and
+//     Appendix B (mean, scale, opacity, colour, rotation bounds).
+//
+// Precision: FP64 everywhere, except the tile rectangle of a splat, whose
+// integer result is decided in FP32 exactly as the GPU decides it (the inputs of
+// that decision are FP32 values).  Forward-mode derivatives use a one-tangent
+// dual number; the reverse pass of the blend is written out by hand.
+//
+// Build: g++ -O2 -std=c++17 -ffp-contract=off -fPIC -shared.
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <limits>
+#include <vector>
+
+namespace {
+
+// ---------------------------------------------------------------- dual numbers
+struct Dual {
+  double v, d;
+  Dual(double v_ = 0.0, double d_ = 0.0) : v(v_), d(d_) {}
+};
+inline Dual operator+(Dual a, Dual b) { return Dual(a.v + b.v, a.d + b.d); }
+inline Dual operator-(Dual a, Dual b) { return Dual(a.v - b.v, a.d - b.d); }
+inline Dual operator-(Dual a) { return Dual(-a.v, -a.d); }
+inline Dual operator*(Dual a, Dual b) { return Dual(a.v * b.v, a.d * b.v + a.v * b.d); }
+inline Dual operator/(Dual a, Dual b) {
+  return Dual(a.v / b.v, (a.d * b.v - a.v * b.d) / (b.v * b.v));
+}
+inline Dual exp(Dual a) {
+  double e = std::exp(a.v);
+  return Dual(e, e * a.d);
+}
+inline Dual sqrt(Dual a) {
+  double s = std::sqrt(a.v);
+  return Dual(s, a.d / (2.0 * s));
+}
+inline double exp(double a) { return std::exp(a); }
+inline double sqrt(double a) { return std::sqrt(a); }
+inline double val(double x) { return x; }
+inline double val(const Dual& x) { return x.v; }
+
+const double kPi = 3.14159265358979323846;
+
+// ------------------------------------------------------------------- cameras
+struct Cam {
+  double R[3][3], t[3];
+  double fx, fy, cx, cy, znear;
+  int W, H;
+  double pos[3];  // camera centre in world coordinates, -R^T t
+};
+
+// 24 doubles per camera: viewmat[16] (row-major world->camera), fx, fy, cx, cy,
+// near, width, height, unused.
+Cam make_cam(const double* c) {
+  Cam k;
+  for (int r = 0; r < 3; ++r) {
+    for (int q = 0; q < 3; ++q) k.R[r][q] = c[4 * r + q];
+    k.t[r] = c[4 * r + 3];
+  }
+  k.fx = c[16]; k.fy = c[17]; k.cx = c[18]; k.cy = c[19]; k.znear = c[20];
+  k.W = (int)c[21]; k.H = (int)c[22];
+  for (int q = 0; q < 3; ++q)
+    k.pos[q] = -(k.R[0][q] * k.t[0] + k.R[1][q] * k.t[1] + k.R[2][q] * k.t[2]);
+  return k;
+}
+
+// ------------------------------------------------------------- parameters
+// Row layout of the parameter matrix (rows x pitch):
+//   0..2 mean, 3..5 log-scale, 6..9 quaternion (x,y,z,w), 10 opacity logit,
+//   11 + 3k + c: SH coefficient k of colour channel c.
+const int kRowSH = 11;
+inline int n_coeffs(int deg) { return (deg + 1) * (deg + 1); }
+inline int n_rows(int deg) { return kRowSH + 3 * n_coeffs(deg); }
+
+template <class S>
+struct G3 {
+  S mu[3], ls[3], q[4], ol;
+  S sh[16][3];
+  int K;
+};
+
+// Parameters of Gaussian i; if `tan` is given, row r carries tangent tan[r].
+template <class S>
+G3<S> load_gaussian(const double* P, long pitch, long i, int deg, const double* tan) {
+  G3<S> g;
+  g.K = n_coeffs(deg);
+  auto get = [&](int r) -> S {
+    double v = P[(long)r * pitch + i];
+    if constexpr (std::is_same<S, Dual>::value) return Dual(v, tan ? tan[r] : 0.0);
+    else return v;
+  };
+  for (int a = 0; a < 3; ++a) { g.mu[a] = get(a); g.ls[a] = get(3 + a); }
+  for (int a = 0; a < 4; ++a) g.q[a] = get(6 + a);
+  g.ol = get(10);
+  for (int k = 0; k < g.K; ++k)
+    for (int c = 0; c < 3; ++c) g.sh[k][c] = get(kRowSH + 3 * k + c);
+  return g;
+}
+
+// --------------------------------------------------------------- SH basis
+// Real spherical harmonics up to degree 3 in the 3DGS sign convention, written
+// from their normalisation constants sqrt((2l+1)/(4 pi) (l-m)!/(l+m)!) times the
+// Cartesian polynomials.
+template <class S>
+void sh_basis(int deg, S x, S y, S z, S* Y) {
+  const double c0 = 0.5 * std::sqrt(1.0 / kPi);
+  const double c1 = std::sqrt(3.0 / (4.0 * kPi));
+  const double c2a = 0.5 * std::sqrt(15.0 / kPi);
+  const double c2b = 0.25 * std::sqrt(5.0 / kPi);
+  const double c2c = 0.25 * std::sqrt(15.0 / kPi);
+  const double c3a = 0.25 * std::sqrt(35.0 / (2.0 * kPi));
+  const double c3b = 0.5 * std::sqrt(105.0 / kPi);
+  const double c3c = 0.25 * std::sqrt(21.0 / (2.0 * kPi));
+  const double c3d = 0.25 * std::sqrt(7.0 / kPi);
+  const double c3e = 0.25 * std::sqrt(105.0 / kPi);
+  Y[0] = S(c0);
+  if (deg < 1) return;
+  Y[1] = -c1 * y;
+  Y[2] = c1 * z;
+  Y[3] = -c1 * x;
+  if (deg < 2) return;
+  S xx = x * x, yy = y * y, zz = z * z;
+  Y[4] = c2a * (x * y);
+  Y[5] = -c2a * (y * z);
+  Y[6] = c2b * (2.0 * zz - xx - yy);
+  Y[7] = -c2a * (x * z);
+  Y[8] = c2c * (xx - yy);
+  if (deg < 3) return;
+  Y[9] = -c3a * y * (3.0 * xx - yy);
+  Y[10] = c3b * (x * y * z);
+  Y[11] = -c3c * y * (4.0 * zz - xx - yy);
+  Y[12] = c3d * z * (2.0 * zz - 3.0 * xx - 3.0 * yy);
+  Y[13] = -c3c * x * (4.0 * zz - xx - yy);
+  Y[14] = c3e * z * (xx - yy);
+  Y[15] = -c3a * x * (xx - 3.0 * yy);
+}
+
+// ---------------------------------------------------------- rotation matrix
+// Rotation of the normalised quaternion (x, y, z, w), Appendix B.
+template <class S>
+void rotmat(const S q[4], S R[3][3]) {
+  S r = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+  S x = q[0] / r, y = q[1] / r, z = q[2] / r, w = q[3] / r;
+  R[0][0] = 1.0 - 2.0 * (y * y + z * z);
+  R[0][1] = 2.0 * (x * y - w * z);
+  R[0][2] = 2.0 * (x * z + w * y);
+  R[1][0] = 2.0 * (x * y + w * z);
+  R[1][1] = 1.0 - 2.0 * (z * z + x * x);
+  R[1][2] = 2.0 * (y * z - w * x);
+  R[2][0] = 2.0 * (x * z - w * y);
+  R[2][1] = 2.0 * (y * z + w * x);
+  R[2][2] = 1.0 - 2.0 * (x * x + y * y);
+}
+
+// ------------------------------------------------------------- projection
+template <class S>
+struct Splat {
+  bool valid = false;  // in front of the near plane with a positive-definite 2-D covariance
+  S mx, my, A, B, C, o, rgb[3], depth;
+  double radius_raw = 0.0;  // 3 sqrt(lambda_max), before rounding up
+  int radius = 0;
+  int flags = 0;  // bits 0..2: colour channel clamped at 0; bit 3/4: x/y slope clamped
+};
+
+// EWA projection of one Gaussian (3DGS conventions, to which Sec. 3.1 defers):
+//   Sigma = R diag(s^2) R^T, t = W mu + t_w, J the perspective Jacobian with the
+//   image-plane slope clamped at 1.3 x the half field of view,
+//   Sigma' = J R_w Sigma R_w^T J^T + 0.3 I, conic = Sigma'^{-1},
+//   radius = ceil(3 sqrt(lambda_max(Sigma'))), colour = SH(view dir) + 0.5 >= 0,
+//   opacity = sigmoid(logit).
+template <class S>
+Splat<S> project(const G3<S>& g, const Cam& cam) {
+  Splat<S> p;
+  S t[3];
+  for (int r = 0; r < 3; ++r)
+    t[r] = cam.R[r][0] * g.mu[0] + cam.R[r][1] * g.mu[1] + cam.R[r][2] * g.mu[2] + S(cam.t[r]);
+  if (val(t[2]) <= cam.znear) return p;
+
+  S R[3][3];
+  rotmat(g.q, R);
+  S s2[3];
+  for (int a = 0; a < 3; ++a) { S s = exp(g.ls[a]); s2[a] = s * s; }
+  S Sig[3][3];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b)
+      Sig[a][b] = R[a][0] * s2[0] * R[b][0] + R[a][1] * s2[1] * R[b][1] + R[a][2] * s2[2] * R[b][2];
+  // camera-frame covariance R_w Sigma R_w^T
+  S Sc[3][3];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      S acc = 0.0;
+      for (int u = 0; u < 3; ++u)
+        for (int v = 0; v < 3; ++v) acc = acc + cam.R[a][u] * Sig[u][v] * cam.R[b][v];
+      Sc[a][b] = acc;
+    }
+  const double limx = 1.3 * 0.5 * cam.W / cam.fx;
+  const double limy = 1.3 * 0.5 * cam.H / cam.fy;
+  S u = t[0] / t[2], v = t[1] / t[2];
+  S uc = u, vc = v;
+  if (val(u) < -limx) uc = S(-limx);
+  if (val(u) > limx) uc = S(limx);
+  if (val(v) < -limy) vc = S(-limy);
+  if (val(v) > limy) vc = S(limy);
+  if (std::fabs(val(u)) > limx) p.flags |= 8;
+  if (std::fabs(val(v)) > limy) p.flags |= 16;
+  S J[2][3];
+  J[0][0] = cam.fx / t[2]; J[0][1] = S(0.0); J[0][2] = -cam.fx * uc / t[2];
+  J[1][0] = S(0.0); J[1][1] = cam.fy / t[2]; J[1][2] = -cam.fy * vc / t[2];
+  S cov[2][2];
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2; ++b) {
+      S acc = 0.0;
+      for (int x = 0; x < 3; ++x)
+        for (int y = 0; y < 3; ++y) acc = acc + J[a][x] * Sc[x][y] * J[b][y];
+      cov[a][b] = acc;
+    }
+  S a = cov[0][0] + 0.3, b = cov[0][1], c = cov[1][1] + 0.3;
+  S det = a * c - b * b;
+  if (!(val(det) > 0.0)) return p;
+  p.A = c / det;
+  p.B = -b / det;
+  p.C = a / det;
+  double mid = 0.5 * (val(a) + val(c));
+  double lam = mid + std::sqrt(std::max(0.1, mid * mid - val(det)));
+  p.radius_raw = 3.0 * std::sqrt(lam);
+  p.radius = (int)std::ceil(p.radius_raw);
+  p.mx = cam.fx * u + cam.cx;
+  p.my = cam.fy * v + cam.cy;
+  p.depth = t[2];
+
+  S d[3];
+  for (int q = 0; q < 3; ++q) d[q] = g.mu[q] - S(cam.pos[q]);
+  S dn = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+  S Y[16];
+  int deg = (int)std::lround(std::sqrt((double)g.K)) - 1;
+  sh_basis(deg, d[0] / dn, d[1] / dn, d[2] / dn, Y);
+  for (int ch = 0; ch < 3; ++ch) {
+    S acc = 0.5;
+    for (int k = 0; k < g.K; ++k) acc = acc + Y[k] * g.sh[k][ch];
+    p.rgb[ch] = (val(acc) < 0.0) ? S(0.0) : acc;
+    if (val(acc) < 0.0) p.flags |= 1 << ch;
+  }
+  p.o = 1.0 / (1.0 + exp(-g.ol));
+  p.valid = true;
+  return p;
+}
+
+// ---------------------------------------------------------------- binning
+// Tile rectangle [x0, x1) x [y0, y1) of a splat, decided in FP32 from FP32 inputs:
+//   x0 = clamp(floor((mx - r) / tw), 0, Tx),  x1 = clamp(floor((mx + (r + tw - 1)) / tw), 0, Tx)
+// (and the same for y).  Each FP32 operation below rounds once.
+void rect_f32(float mx, float my, int r, int tw, int th, int Tx, int Ty, int& x0, int& x1,
+              int& y0, int& y1) {
+  volatile float lo_x = mx - (float)r;
+  volatile float hi_x = mx + (float)(r + tw - 1);
+  volatile float lo_y = my - (float)r;
+  volatile float hi_y = my + (float)(r + th - 1);
+  float qx0 = lo_x / (float)tw, qx1 = hi_x / (float)tw;
+  float qy0 = lo_y / (float)th, qy1 = hi_y / (float)th;
+  auto cl = [](float q, int hi) {
+    float f = std::floor(q);
+    if (!(f > 0.0f)) return 0;  // also maps NaN to 0
+    if (f > (float)hi) return hi;
+    return (int)f;
+  };
+  x0 = cl(qx0, Tx); x1 = cl(qx1, Tx);
+  y0 = cl(qy0, Ty); y1 = cl(qy1, Ty);
+}
+
+uint32_t f32_bits(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  return u;
+}
+
+struct Pair {
+  uint64_t key;
+  uint32_t val;
+};
+
+// All (tile, splat) pairs of all views, sorted by (key, splat index); key =
+// (view * tiles_per_view + tile) << 32 | bits(depth).
+std::vector<Pair> bin_and_sort(int n_views, long n, const float* mx, const float* my, const int* rad,
+                               const float* depth, int W, int H, int tw, int th) {
+  int Tx = (W + tw - 1) / tw, Ty = (H + th - 1) / th;
+  long T = (long)Tx * Ty;
+  std::vector<Pair> pairs;
+  for (int v = 0; v < n_views; ++v)
+    for (long i = 0; i < n; ++i) {
+      long gi = (long)v * n + i;
+      if (rad[gi] <= 0) continue;
+      int x0, x1, y0, y1;
+      rect_f32(mx[gi], my[gi], rad[gi], tw, th, Tx, Ty, x0, x1, y0, y1);
+      for (int ty = y0; ty < y1; ++ty)
+        for (int tx = x0; tx < x1; ++tx) {
+          uint64_t tile = (uint64_t)v * T + (uint64_t)ty * Tx + tx;
+          pairs.push_back({(tile << 32) | f32_bits(depth[gi]), (uint32_t)i});
+        }
+    }
+  std::sort(pairs.begin(), pairs.end(), [](const Pair& a, const Pair& b) {
+    return a.key < b.key || (a.key == b.key && a.val < b.val);
+  });
+  return pairs;
+}
+
+// --------------------------------------------------------- per-view scene
+struct View {
+  Cam cam;
+  int tw, th, Tx, Ty;
+  std::vector<Splat<double>> sp;
+  std::vector<std::vector<int>> lists;  // per tile, splat indices front to back
+  // per splat, the tile rectangle when its FP32 inputs are moved to the edges of
+  // their rounding uncertainty (lo shrinks, hi grows): x0, x1, y0, y1
+  std::vector<int> lo, hi;
+};
+
+const double kAmbRel = 1e-5;
+
+View build_view(const double* P, long pitch, long n, int deg, const double* cam24, int tw, int th) {
+  View V;
+  V.cam = make_cam(cam24);
+  V.tw = tw; V.th = th;
+  V.Tx = (V.cam.W + tw - 1) / tw;
+  V.Ty = (V.cam.H + th - 1) / th;
+  V.sp.resize(n);
+  std::vector<float> mx(n), my(n), dp(n);
+  std::vector<int> rad(n);
+  V.lo.assign(4 * n, 0);
+  V.hi.assign(4 * n, 0);
+  for (long i = 0; i < n; ++i) {
+    G3<double> g = load_gaussian<double>(P, pitch, i, deg, nullptr);
+    V.sp[i] = project(g, V.cam);
+    const Splat<double>& s = V.sp[i];
+    mx[i] = (float)s.mx; my[i] = (float)s.my; dp[i] = (float)s.depth;
+    rad[i] = s.valid ? s.radius : 0;
+    if (!s.valid) continue;
+    double rr = s.radius_raw;
+    int r_lo = (int)std::ceil(rr * (1.0 - kAmbRel) - 1e-6);
+    int r_hi = (int)std::ceil(rr * (1.0 + kAmbRel) + 1e-6);
+    double ex = kAmbRel * (std::fabs(s.mx) + rr + tw) + 1e-4;
+    double ey = kAmbRel * (std::fabs(s.my) + rr + th) + 1e-4;
+    int a0, a1, b0, b1, c0, c1, d0, d1;
+    // shrunk rectangle: lower edges from the centre moved up, upper edges from it moved down
+    rect_f32((float)(s.mx + ex), (float)(s.my + ey), r_lo, tw, th, V.Tx, V.Ty, a0, a1, b0, b1);
+    rect_f32((float)(s.mx - ex), (float)(s.my - ey), r_lo, tw, th, V.Tx, V.Ty, c0, c1, d0, d1);
+    V.lo[4 * i + 0] = a0; V.lo[4 * i + 1] = c1; V.lo[4 * i + 2] = b0; V.lo[4 * i + 3] = d1;
+    rect_f32((float)(s.mx - ex), (float)(s.my - ey), r_hi, tw, th, V.Tx, V.Ty, a0, a1, b0, b1);
+    rect_f32((float)(s.mx + ex), (float)(s.my + ey), r_hi, tw, th, V.Tx, V.Ty, c0, c1, d0, d1);
+    V.hi[4 * i + 0] = a0; V.hi[4 * i + 1] = c1; V.hi[4 * i + 2] = b0; V.hi[4 * i + 3] = d1;
+  }
+  std::vector<Pair> pairs =
+      bin_and_sort(1, n, mx.data(), my.data(), rad.data(), dp.data(), V.cam.W, V.cam.H, tw, th);
+  V.lists.assign((size_t)V.Tx * V.Ty, {});
+  for (const Pair& p : pairs) V.lists[p.key >> 32].push_back((int)p.val);
+  return V;
+}
+
+// A splat may enter or leave tile (tx, ty) under rounding if the tile lies in its
+// grown rectangle but not in its shrunk one.
+bool tile_ambiguous(const View& V, long i, int tx, int ty) {
+  const int* l = &V.lo[4 * i];
+  const int* h = &V.hi[4 * i];
+  bool in_hi = tx >= h[0] && tx < h[1] && ty >= h[2] && ty < h[3];
+  bool in_lo = tx >= l[0] && tx < l[1] && ty >= l[2] && ty < l[3];
+  return in_hi && !in_lo;
+}
+
+// --------------------------------------------------------------- blending
+struct Contrib {
+  int i;          // splat index
+  double alpha;   // min(0.99, o G)
+  double G;       // exp(power)
+  bool capped;    // o G > 0.99
+  double T;       // transmittance in front of this splat
+  double dx, dy;  // mean - pixel centre
+};
+
+const double kAlphaMin = 1.0 / 255.0;
+const double kAlphaMax = 0.99;
+const double kTMin = 1e-4;
+
+// Front-to-back blend of one pixel (Sec. 3.1): skip a splat whose power is
+// positive or whose alpha is below 1/255, stop before the splat that would bring
+// T below 1e-4, black background.  n_contrib = 1 + list position of the last
+// splat blended.  `margin` receives the smallest relative distance of any
+// decision taken to its threshold.
+template <class S>
+void blend(const std::vector<int>& list, const std::vector<Splat<S>>& sp, double pcx, double pcy,
+           S C[3], S& T, int& n_contrib, double* margin, std::vector<Contrib>* trace) {
+  T = S(1.0);
+  C[0] = C[1] = C[2] = S(0.0);
+  n_contrib = 0;
+  double mg = std::numeric_limits<double>::infinity();
+  for (size_t k = 0; k < list.size(); ++k) {
+    const Splat<S>& g = sp[list[k]];
+    S dx = g.mx - S(pcx), dy = g.my - S(pcy);
+    S power = -0.5 * (g.A * dx * dx + g.C * dy * dy) - g.B * dx * dy;
+    mg = std::min(mg, std::fabs(val(power)) * 1e6);
+    if (val(power) > 0.0) continue;
+    S G = exp(power);
+    S oG = g.o * G;
+    bool capped = val(oG) > kAlphaMax;
+    mg = std::min(mg, std::fabs(val(oG) - kAlphaMax) / kAlphaMax);
+    S alpha = capped ? S(kAlphaMax) : oG;
+    mg = std::min(mg, std::fabs(val(alpha) - kAlphaMin) / kAlphaMin);
+    if (val(alpha) < kAlphaMin) continue;
+    S Tn = T * (1.0 - alpha);
+    mg = std::min(mg, std::fabs(val(Tn) - kTMin) / kTMin);
+    if (val(Tn) < kTMin) break;
+    if (trace) trace->push_back({list[k], val(alpha), val(G), capped, val(T), val(dx), val(dy)});
+    for (int ch = 0; ch < 3; ++ch) C[ch] = C[ch] + g.rgb[ch] * alpha * T;
+    T = Tn;
+    n_contrib = (int)k + 1;
+  }
+  if (margin) *margin = mg;
+}
+
+// 0 for pixels whose value may legitimately differ between an FP32 and an FP64
+// evaluation because a splat's tile set, or the depth order of two splats, lies
+// within rounding of a boundary; +inf otherwise.
+double binning_margin(const View& V, int tx, int ty, double pcx, double pcy) {
+  const std::vector<int>& list = V.lists[(size_t)ty * V.Tx + tx];
+  auto visible_at = [&](long i) {
+    const Splat<double>& g = V.sp[i];
+    double dx = g.mx - pcx, dy = g.my - pcy;
+    double power = -0.5 * (g.A * dx * dx + g.C * dy * dy) - g.B * dx * dy;
+    return g.o * std::exp(power) >= 0.5 * kAlphaMin;
+  };
+  for (long i = 0; i < (long)V.sp.size(); ++i)
+    if (V.sp[i].valid && tile_ambiguous(V, i, tx, ty) && visible_at(i)) return 0.0;
+  for (size_t k = 1; k < list.size(); ++k) {
+    double d0 = V.sp[list[k - 1]].depth, d1 = V.sp[list[k]].depth;
+    if (std::fabs(d1 - d0) <= 1e-6 * std::fabs(d1) && visible_at(list[k - 1]) && visible_at(list[k]))
+      return 0.0;
+  }
+  return std::numeric_limits<double>::infinity();
+}
+
+// Calls f(tx, ty, x, y) for every pixel of the view, tile by tile.
+template <class F>
+void for_each_pixel(const View& V, F f) {
+  for (int ty = 0; ty < V.Ty; ++ty)
+    for (int tx = 0; tx < V.Tx; ++tx)
+      for (int y = ty * V.th; y < std::min((ty + 1) * V.th, V.cam.H); ++y)
+        for (int x = tx * V.tw; x < std::min((tx + 1) * V.tw, V.cam.W); ++x) f(tx, ty, x, y);
+}
+
+// ------------------------------------------------------------ Rademacher
+const uint64_t kGolden = 0x9E3779B97F4A7C15ULL;
+
+// SplitMix64 output for state x (Steele, Lea & Flood 2014): one Weyl increment,
+// then the finaliser with shifts 30, 27, 31.
+uint64_t splitmix64(uint64_t x) {
+  uint64_t z = x + kGolden;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+// Entry j of Rademacher probe k at step t: +1 or -1 from bit 63 of the hash.
+double rademacher(uint64_t seed, int64_t t, int k, uint64_t j) {
+  uint64_t h = splitmix64(seed ^ ((uint64_t)t * kGolden) ^ ((uint64_t)k << 56) ^ j);
+  return (h >> 63) ? -1.0 : 1.0;
+}
+
+// ----------------------------------------------------------- reverse pass
+// Cotangents of the 2-D splat quantities, 9 per splat: (mx, my, A, B, C, o, r, g, b).
+enum { Q_MX, Q_MY, Q_A, Q_B, Q_C, Q_O, Q_R, Q_G, Q_BL, NQ };
+
+// Reverse pass of one pixel's blend, written out from
+//   dC/dc_i = a_i T_i,
+//   dC/da_i = c_i T_i - (sum_{j>i} c_j a_j T_j) / (1 - a_i),
+//   a = o exp(power) (no derivative where a is capped at 0.99),
+//   power = -1/2 (A dx^2 + C dy^2) - B dx dy with dx = mx - px, dy = my - py.
+// `w` is dL/dC at the pixel; the result is added to cot[i * NQ + q].
+void blend_reverse(const std::vector<Contrib>& tr, const std::vector<Splat<double>>& sp,
+                   const double w[3], double* cot) {
+  // suffix[k] = sum over later splats j of c_j a_j T_j
+  std::vector<double> suffix(3 * (tr.size() + 1), 0.0);
+  for (long k = (long)tr.size() - 1; k >= 0; --k)
+    for (int ch = 0; ch < 3; ++ch)
+      suffix[3 * k + ch] = suffix[3 * (k + 1) + ch] + sp[tr[k].i].rgb[ch] * tr[k].alpha * tr[k].T;
+  for (size_t k = 0; k < tr.size(); ++k) {
+    const Contrib& e = tr[k];
+    const Splat<double>& g = sp[e.i];
+    double ga = 0.0;
+    for (int ch = 0; ch < 3; ++ch)
+      ga += w[ch] * (g.rgb[ch] * e.T - suffix[3 * (k + 1) + ch] / (1.0 - e.alpha));
+    double* c = cot + (long)e.i * NQ;
+    c[Q_R] += w[0] * e.alpha * e.T;
+    c[Q_G] += w[1] * e.alpha * e.T;
+    c[Q_BL] += w[2] * e.alpha * e.T;
+    if (e.capped) continue;
+    double gpow = ga * e.alpha;
+    c[Q_O] += ga * e.G;
+    c[Q_A] += -0.5 * e.dx * e.dx * gpow;
+    c[Q_B] += -e.dx * e.dy * gpow;
+    c[Q_C] += -0.5 * e.dy * e.dy * gpow;
+    c[Q_MX] += -(g.A * e.dx + g.B * e.dy) * gpow;
+    c[Q_MY] += -(g.C * e.dy + g.B * e.dx) * gpow;
+  }
+}
+
+// Parameter cotangent of splat i: sum_q cot_q d(splat_q)/d(param_r), with the
+// projection Jacobian taken column by column in forward mode.
+void project_reverse(const double* P, long pitch, long i, int deg, const Cam& cam, const double* cot,
+                     std::vector<double>& gout /* rows values, added */) {
+  int rows = n_rows(deg);
+  std::vector<double> tan(rows, 0.0);
+  for (int r = 0; r < rows; ++r) {
+    std::fill(tan.begin(), tan.end(), 0.0);
+    tan[r] = 1.0;
+    G3<Dual> g = load_gaussian<Dual>(P, pitch, i, deg, tan.data());
+    Splat<Dual> s = project(g, cam);
+    if (!s.valid) continue;
+    const double col[NQ] = {s.mx.d, s.my.d, s.A.d, s.B.d, s.C.d, s.o.d, s.rgb[0].d, s.rgb[1].d, s.rgb[2].d};
+    double acc = 0.0;
+    for (int q = 0; q < NQ; ++q) acc += cot[q] * col[q];
+    gout[r] += acc;
+  }
+}
+
+// Splats of one view in forward mode along the parameter direction `dir`
+// (rows x pitch).
+std::vector<Splat<Dual>> project_tangent(const View& V, const double* P, long pitch, long n, int deg,
+                                         const double* dir) {
+  int rows = n_rows(deg);
+  std::vector<Splat<Dual>> sd(n);
+  std::vector<double> tan(rows);
+  for (long i = 0; i < n; ++i) {
+    for (int r = 0; r < rows; ++r) tan[r] = dir[(long)r * pitch + i];
+    G3<Dual> g = load_gaussian<Dual>(P, pitch, i, deg, tan.data());
+    sd[i] = project(g, V.cam);
+  }
+  return sd;
+}
+
+// Image tangent (3 x H x W) of one view for the given tangent splats.
+void render_tangent(const View& V, const std::vector<Splat<Dual>>& sd, double* out) {
+  long HW = (long)V.cam.W * V.cam.H;
+  for_each_pixel(V, [&](int tx, int ty, int x, int y) {
+    Dual C[3], T;
+    int nc;
+    blend(V.lists[(size_t)ty * V.Tx + tx], sd, x + 0.5, y + 0.5, C, T, nc, nullptr, nullptr);
+    for (int ch = 0; ch < 3; ++ch) out[ch * HW + (long)y * V.cam.W + x] = C[ch].d;
+  });
+}
+
+// ----------------------------------------------------------- trust region
+// The squared Hellinger distance of Sec. 4.2, read as
+//   H^2 = 1/2 (Z + Z') - sqrt(Z Z') det(S)^1/4 det(S')^1/4 / det(Sbar)^1/2
+//         * exp(-1/8 dmu^T Sbar^{-1} dmu),   Sbar = (S + S') / 2,
+// which equals 1/2 * integral (sqrt(G) - sqrt(G'))^2 for G = Z N(mu, S).
+double det3(const double M[3][3]) {
+  return M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1]) -
+         M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0]) +
+         M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0]);
+}
+void inv3(const double M[3][3], double I[3][3]) {
+  double d = det3(M);
+  I[0][0] = (M[1][1] * M[2][2] - M[1][2] * M[2][1]) / d;
+  I[0][1] = (M[0][2] * M[2][1] - M[0][1] * M[2][2]) / d;
+  I[0][2] = (M[0][1] * M[1][2] - M[0][2] * M[1][1]) / d;
+  I[1][0] = (M[1][2] * M[2][0] - M[1][0] * M[2][2]) / d;
+  I[1][1] = (M[0][0] * M[2][2] - M[0][2] * M[2][0]) / d;
+  I[1][2] = (M[0][2] * M[1][0] - M[0][0] * M[1][2]) / d;
+  I[2][0] = (M[1][0] * M[2][1] - M[1][1] * M[2][0]) / d;
+  I[2][1] = (M[0][1] * M[2][0] - M[0][0] * M[2][1]) / d;
+  I[2][2] = (M[0][0] * M[1][1] - M[0][1] * M[1][0]) / d;
+}
+
+double hellinger(const double* mu1, const double* S1, double Z1, const double* mu2, const double* S2,
+                 double Z2) {
+  double A[3][3], B[3][3], M[3][3], Mi[3][3];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      A[a][b] = S1[3 * a + b];
+      B[a][b] = S2[3 * a + b];
+      M[a][b] = 0.5 * (A[a][b] + B[a][b]);
+    }
+  inv3(M, Mi);
+  double d[3] = {mu1[0] - mu2[0], mu1[1] - mu2[1], mu1[2] - mu2[2]};
+  double q = 0.0;
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) q += d[a] * Mi[a][b] * d[b];
+  double bc = std::pow(det3(A), 0.25) * std::pow(det3(B), 0.25) / std::sqrt(det3(M)) * std::exp(-q / 8.0);
+  return 0.5 * (Z1 + Z2) - std::sqrt(Z1 * Z2) * bc;
+}
+
+// Unnormalised rotation matrix R~(q) of Appendix B (entries quadratic in q).
+void rot_unnorm(const double q[4], double R[3][3]) {
+  double x = q[0], y = q[1], z = q[2], w = q[3];
+  double r2 = x * x + y * y + z * z + w * w;
+  R[0][0] = r2 - 2 * (y * y + z * z); R[0][1] = 2 * x * y - 2 * w * z; R[0][2] = 2 * x * z + 2 * w * y;
+  R[1][0] = 2 * x * y + 2 * w * z; R[1][1] = r2 - 2 * (z * z + x * x); R[1][2] = 2 * y * z - 2 * w * x;
+  R[2][0] = 2 * x * z - 2 * w * y; R[2][1] = 2 * y * z + 2 * w * x; R[2][2] = r2 - 2 * (x * x + y * y);
+}
+
+// beta_c of the rotation bound (Appendix B): the second derivative at a = 0 of
+// T(a) = tr(S^-2 dR S^2 dR^T), dR = R(q)^T R(q + a e_c), for Sigma = R S^2 R^T:
+//   beta_c = 2 || S^-1 E' S ||_F^2 + 2 tr(E''),  E' = R^T dR/dq_c,  E'' = R^T d2R/dq_c^2,
+// with R = R~ / r^2, so
+//   dR  = R~'/r^2 - 2 q_c R~/r^4,
+//   d2R = R~''/r^2 - 4 q_c R~'/r^4 - 2 R~/r^4 + 8 q_c^2 R~/r^6.
+// R~ is quadratic in q, so its first and second partial derivatives are given
+// exactly by the symmetric differences (R~(q+e) - R~(q-e))/2 and R~(q+e) - 2R~(q) + R~(q-e).
+void rotation_beta(const double q[4], const double s[3], double beta[4]) {
+  double r2 = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
+  double Rt[3][3], R[3][3];
+  rot_unnorm(q, Rt);
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) R[a][b] = Rt[a][b] / r2;
+  for (int c = 0; c < 4; ++c) {
+    double qp[4], qm[4];
+    for (int a = 0; a < 4; ++a) { qp[a] = q[a]; qm[a] = q[a]; }
+    qp[c] += 1.0; qm[c] -= 1.0;
+    double Rp[3][3], Rm[3][3], d1[3][3], d2[3][3], dR[3][3], ddR[3][3];
+    rot_unnorm(qp, Rp);
+    rot_unnorm(qm, Rm);
+    double qc = q[c];
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) {
+        d1[a][b] = 0.5 * (Rp[a][b] - Rm[a][b]);
+        d2[a][b] = Rp[a][b] - 2.0 * Rt[a][b] + Rm[a][b];
+        dR[a][b] = d1[a][b] / r2 - 2.0 * qc * Rt[a][b] / (r2 * r2);
+        ddR[a][b] = d2[a][b] / r2 - 4.0 * qc * d1[a][b] / (r2 * r2) - 2.0 * Rt[a][b] / (r2 * r2) +
+                    8.0 * qc * qc * Rt[a][b] / (r2 * r2 * r2);
+      }
+    double E1[3][3], E2[3][3];
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) {
+        E1[a][b] = E2[a][b] = 0.0;
+        for (int u = 0; u < 3; ++u) {
+          E1[a][b] += R[u][a] * dR[u][b];
+          E2[a][b] += R[u][a] * ddR[u][b];
+        }
+      }
+    double fro = 0.0;
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) {
+        double m = E1[a][b] * s[b] / s[a];  // (S^-1 E' S)_ab
+        fro += m * m;
+      }
+    beta[c] = 2.0 * fro + 2.0 * (E2[0][0] + E2[1][1] + E2[2][2]);
+  }
+}
+
+// max over the unit sphere of |Y_k|, by a dense grid search refined by a local
+// pattern search.
+void sh_absmax(int deg, double* ymax) {
+  int K = n_coeffs(deg);
+  auto f = [&](int k, double th, double ph) {
+    double Y[16];
+    sh_basis<double>(deg, std::sin(th) * std::cos(ph), std::sin(th) * std::sin(ph), std::cos(th), Y);
+    return std::fabs(Y[k]);
+  };
+  const int NT = 400, NP = 800;
+  for (int k = 0; k < K; ++k) {
+    double best = -1.0, bt = 0.0, bp = 0.0;
+    for (int a = 0; a <= NT; ++a)
+      for (int b = 0; b < NP; ++b) {
+        double th = kPi * a / NT, ph = 2.0 * kPi * b / NP;
+        double v = f(k, th, ph);
+        if (v > best) { best = v; bt = th; bp = ph; }
+      }
+    double step = kPi / NT;
+    while (step > 1e-10) {
+      bool moved = false;
+      for (int dt = -1; dt <= 1; ++dt)
+        for (int dp = -1; dp <= 1; ++dp) {
+          double v = f(k, bt + dt * step, bp + dp * step);
+          if (v > best) { best = v; bt += dt * step; bp += dp * step; moved = true; }
+        }
+      if (!moved) step *= 0.5;
+    }
+    ymax[k] = best;
+  }
+}
+
+struct TRConfig {
+  double theta1, theta2, d_floor, color_floor;
+  int l, mean_exact;
+};
+
+TRConfig read_cfg(const double* c) {
+  TRConfig k;
+  k.theta1 = c[0]; k.theta2 = c[1]; k.d_floor = c[2]; k.color_floor = c[3];
+  k.l = (int)c[4]; k.mean_exact = (int)c[5];
+  return k;
+}
+
+const double kInf = std::numeric_limits<double>::infinity();
+
+// Per-parameter radius eta = SHD(x, eps) of every parameter of splat i (Sec. 4.2,
+// Appendix B), mapped to this parameterisation by the first-order chain rule:
+//   mean        sqrt(-8 Sigma_cc ln(1 - eps/alpha))      (inf when alpha <= eps)
+//   log-scale   sqrt(2 eps / alpha)                       (|dS_c| < sqrt(2 S_c^2 eps/alpha), dS = S dlogS)
+//   quaternion  sqrt(-(8/beta_c) ln(1 - eps/alpha))       (inf when beta_c = 0 or alpha <= eps)
+//   logit       sqrt(4 alpha eps) / (alpha (1 - alpha))   (d alpha = alpha (1 - alpha) d logit)
+//   SH (k, c)   sqrt(4 C_c eps / alpha) / max|Y_k|        (C_c = DC colour, floored)
+void shd_radius(const double* P, long pitch, long i, int deg, double eps, const TRConfig& cfg,
+                const double* ymax, double* eta) {
+  int K = n_coeffs(deg);
+  G3<double> g = load_gaussian<double>(P, pitch, i, deg, nullptr);
+  double alpha = 1.0 / (1.0 + std::exp(-g.ol));
+  double s[3], R[3][3], Sig[3][3];
+  for (int a = 0; a < 3; ++a) s[a] = std::exp(g.ls[a]);
+  rotmat<double>(g.q, R);
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b)
+      Sig[a][b] = R[a][0] * s[0] * s[0] * R[b][0] + R[a][1] * s[1] * s[1] * R[b][1] +
+                  R[a][2] * s[2] * s[2] * R[b][2];
+  double Si[3][3];
+  inv3(Sig, Si);
+  bool logok = alpha > eps;
+  double L = logok ? std::log1p(-eps / alpha) : 0.0;
+  for (int c = 0; c < 3; ++c) {
+    double var = cfg.mean_exact ? 1.0 / Si[c][c] : Sig[c][c];
+    eta[c] = logok ? std::sqrt(-8.0 * var * L) : kInf;
+    eta[3 + c] = std::sqrt(2.0 * eps / alpha);
+  }
+  double beta[4];
+  rotation_beta(g.q, s, beta);
+  for (int c = 0; c < 4; ++c) eta[6 + c] = (logok && beta[c] > 0.0) ? std::sqrt(-8.0 / beta[c] * L) : kInf;
+  eta[10] = std::sqrt(4.0 * alpha * eps) / (alpha * (1.0 - alpha));
+  const double c0 = 0.5 * std::sqrt(1.0 / kPi);
+  for (int ch = 0; ch < 3; ++ch) {
+    double Cc = std::max(c0 * g.sh[0][ch] + 0.5, cfg.color_floor);
+    for (int k = 0; k < K; ++k) eta[kRowSH + 3 * k + ch] = std::sqrt(4.0 * Cc * eps / alpha) / ymax[k];
+  }
+}
+
+struct Scene {
+  const double* P;
+  long pitch, n;
+  int deg;
+};
+
+}  // namespace
+
+// ======================================================================= C ABI
+extern "C" {
+
+uint64_t or_splitmix64(uint64_t x) { return splitmix64(x); }
+
+double or_rademacher(uint64_t seed, int64_t t, int k, uint64_t j) { return rademacher(seed, t, k, j); }
+
+void or_sh_basis(int deg, const double* dir, double* Y) {
+  double n = std::sqrt(dir[0] * dir[0] + dir[1] * dir[1] + dir[2] * dir[2]);
+  sh_basis<double>(deg, dir[0] / n, dir[1] / n, dir[2] / n, Y);
+}
+
+void or_sh_absmax(int deg, double* ymax) { sh_absmax(deg, ymax); }
+
+void or_quat_to_rotmat(const double* q, double* R9) {
+  double R[3][3];
+  rotmat<double>(q, R);
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) R9[3 * a + b] = R[a][b];
+}
+
+// Projection of every splat for one camera.  out: n x 13 doubles
+//   mx, my, A, B, C, o, r, g, b, depth, radius_raw, radius, valid
+void or_project(const double* P, long pitch, long n, int deg, const double* cam24, double* out) {
+  Cam cam = make_cam(cam24);
+  for (long i = 0; i < n; ++i) {
+    Splat<double> s = project(load_gaussian<double>(P, pitch, i, deg, nullptr), cam);
+    double* o = out + 13 * i;
+    double v[13] = {s.mx, s.my, s.A, s.B, s.C, s.o, s.rgb[0], s.rgb[1], s.rgb[2], s.depth,
+                    s.radius_raw, (double)(s.valid ? s.radius : 0), s.valid ? 1.0 : 0.0};
+    if (!s.valid) for (int q = 0; q < 10; ++q) v[q] = 0.0;
+    std::memcpy(o, v, sizeof(v));
+  }
+}
+
+// Binning and depth sort from FP32 splat records of n_views views (arrays are
+// n_views x n).  Writes up to `cap` pairs and the [start, end) range of every
+// tile (2 x n_views x tiles); returns the number of pairs.
+long or_bin_sort(int n_views, long n, const float* mx, const float* my, const int* rad, const float* depth,
+                 int W, int H, int tw, int th, uint64_t* keys, uint32_t* vals, long cap, uint32_t* ranges) {
+  std::vector<Pair> pairs = bin_and_sort(n_views, n, mx, my, rad, depth, W, H, tw, th);
+  long T = (long)((W + tw - 1) / tw) * ((H + th - 1) / th);
+  for (long k = 0; k < 2 * T * n_views; ++k) ranges[k] = 0;
+  for (long p = 0; p < (long)pairs.size(); ++p) {
+    if (p < cap) { keys[p] = pairs[p].key; vals[p] = pairs[p].val; }
+    uint64_t tile = pairs[p].key >> 32;
+    if (p == 0 || (pairs[p - 1].key >> 32) != tile) ranges[2 * tile] = (uint32_t)p;
+    ranges[2 * tile + 1] = (uint32_t)(p + 1);
+  }
+  return (long)pairs.size();
+}
+
+// Render every view.  image: V x 3 x H x W, final_T and margin: V x H x W,
+// n_contrib: V x H x W.  margin is the smallest relative distance of a threshold
+// decision at the pixel, or 0 where binning is within rounding of a boundary.
+// Returns the total number of (tile, splat) pairs.
+long or_render(const double* P, long pitch, long n, int deg, const double* cams, int n_views, int tw, int th,
+               double* image, double* final_T, int32_t* n_contrib, double* margin) {
+  long pairs = 0;
+  for (int v = 0; v < n_views; ++v) {
+    View V = build_view(P, pitch, n, deg, cams + 24 * v, tw, th);
+    long HW = (long)V.cam.W * V.cam.H;
+    for (const auto& l : V.lists) pairs += (long)l.size();
+    double* img = image + v * 3 * HW;
+    for_each_pixel(V, [&](int tx, int ty, int x, int y) {
+      double C[3], T, mg;
+      int nc;
+      blend(V.lists[(size_t)ty * V.Tx + tx], V.sp, x + 0.5, y + 0.5, C, T, nc, &mg, nullptr);
+      long px = (long)y * V.cam.W + x;
+      for (int ch = 0; ch < 3; ++ch) img[ch * HW + px] = C[ch];
+      final_T[v * HW + px] = T;
+      n_contrib[v * HW + px] = nc;
+      if (margin) margin[v * HW + px] = std::min(mg, binning_margin(V, tx, ty, x + 0.5, y + 0.5));
+    });
+  }
+  return pairs;
+}
+
+// Image tangent (V x 3 x H x W) along the parameter direction `dir` (rows x pitch).
+void or_jvp(const double* P, long pitch, long n, int deg, const double* cams, int n_views, int tw, int th,
+            const double* dir, double* img_tan) {
+  long off = 0;
+  for (int v = 0; v < n_views; ++v) {
+    View V = build_view(P, pitch, n, deg, cams + 24 * v, tw, th);
+    std::vector<Splat<Dual>> sd = project_tangent(V, P, pitch, n, deg, dir);
+    render_tangent(V, sd, img_tan + off);
+    off += 3L * V.cam.W * V.cam.H;
+  }
+}
+
+// Full image Jacobian dC/dx for tiny scenes: J has (sum_v 3 H W) rows and
+// (rows * n) columns, column index r * n + i, row-major.
+void or_jacobian(const double* P, long pitch, long n, int deg, const double* cams, int n_views, int tw,
+                 int th, double* J) {
+  int rows = n_rows(deg);
+  long ncol = (long)rows * n;
+  std::vector<double> dir((size_t)rows * pitch, 0.0);
+  long total = 0;
+  for (int v = 0; v < n_views; ++v) {
+    Cam c = make_cam(cams + 24 * v);
+    total += 3L * c.W * c.H;
+  }
+  std::vector<double> col(total);
+  for (int r = 0; r < rows; ++r)
+    for (long i = 0; i < n; ++i) {
+      dir[(size_t)r * pitch + i] = 1.0;
+      or_jvp(P, pitch, n, deg, cams, n_views, tw, th, dir.data(), col.data());
+      dir[(size_t)r * pitch + i] = 0.0;
+      long cidx = (long)r * n + i;
+      for (long k = 0; k < total; ++k) J[k * ncol + cidx] = col[k];
+    }
+}
+
+// One backward + Hutchinson pass over `n_views` views with targets (V x 3 x H x W).
+//   loss_kind 0: F = sqrt(|r|) (L1), dL/dC = sign(r)/(2m), GN weight 1/(4 max(|r|, gn_floor));
+//   loss_kind 1: F = r (L2),          dL/dC = r/m,          GN weight 1.
+// m = sum over views of 3 H W.  grad (rows x n, row pitch n) receives g = (1/m) J^T F.
+// If nu > 0, hz (rows x n) receives (1/nu) sum_k z_k . ((1/m) J^T diag(w) J z_k) with the
+// Rademacher probes of (seed, t, k), and img_tan (nu x V x 3 x H x W, may be null) the
+// tangents J z_k.  res_margin (V x H x W, may be null) receives min over channels of |r|.
+// Returns the objective f = (1/2m) sum F^2.
+double or_backward(const double* P, long pitch, long n, int deg, const double* cams, int n_views, int tw,
+                   int th, const double* target, int loss_kind, double gn_floor, uint64_t seed, int64_t t,
+                   int nu, double* grad, double* hz, double* img_tan, double* res_margin) {
+  int rows = n_rows(deg);
+  double m = 0.0;
+  std::vector<View> views;
+  for (int v = 0; v < n_views; ++v) {
+    views.push_back(build_view(P, pitch, n, deg, cams + 24 * v, tw, th));
+    m += 3.0 * views.back().cam.W * views.back().cam.H;
+  }
+  for (long k = 0; k < (long)rows * n; ++k) grad[k] = 0.0;
+  if (hz) for (long k = 0; k < (long)rows * n; ++k) hz[k] = 0.0;
+
+  // probe directions z_k over the parameter vector (index r * n + i)
+  std::vector<std::vector<double>> z(nu, std::vector<double>((size_t)rows * pitch, 0.0));
+  for (int k = 0; k < nu; ++k)
+    for (int r = 0; r < rows; ++r)
+      for (long i = 0; i < n; ++i) z[k][(size_t)r * pitch + i] = rademacher(seed, t, k, (uint64_t)r * n + i);
+
+  long total = (long)(m + 0.5);  // sum over views of 3 H W
+  double f = 0.0;
+  long img_off = 0;
+  std::vector<double> g_acc(rows);
+  for (int v = 0; v < n_views; ++v) {
+    const View& V = views[v];
+    long HW = (long)V.cam.W * V.cam.H;
+    const double* tg = target + img_off;
+    // streams: 0 = gradient, 1..nu = Gauss-Newton products
+    std::vector<std::vector<double>> cot(1 + nu, std::vector<double>((size_t)n * NQ, 0.0));
+    std::vector<std::vector<double>> jz(nu, std::vector<double>(3 * HW, 0.0));
+    for (int k = 0; k < nu; ++k) {
+      std::vector<Splat<Dual>> sd = project_tangent(V, P, pitch, n, deg, z[k].data());
+      render_tangent(V, sd, jz[k].data());
+      if (img_tan) std::memcpy(img_tan + (long)k * total + img_off, jz[k].data(), 3 * HW * sizeof(double));
+    }
+    for_each_pixel(V, [&](int tx, int ty, int x, int y) {
+      double C[3], T;
+      int nc;
+      std::vector<Contrib> tr;
+      blend(V.lists[(size_t)ty * V.Tx + tx], V.sp, x + 0.5, y + 0.5, C, T, nc, nullptr, &tr);
+      long px = (long)y * V.cam.W + x;
+      double w[3], wgn[3], rmin = kInf;
+      for (int ch = 0; ch < 3; ++ch) {
+        double r = C[ch] - tg[ch * HW + px];
+        rmin = std::min(rmin, std::fabs(r));
+        if (loss_kind == 0) {
+          f += std::fabs(r) / (2.0 * m);
+          w[ch] = (r > 0 ? 1.0 : (r < 0 ? -1.0 : 0.0)) / (2.0 * m);
+          wgn[ch] = 1.0 / (4.0 * std::max(std::fabs(r), gn_floor)) / m;
+        } else {
+          f += r * r / (2.0 * m);
+          w[ch] = r / m;
+          wgn[ch] = 1.0 / m;
+        }
+      }
+      if (res_margin) res_margin[v * HW + px] = rmin;
+      blend_reverse(tr, V.sp, w, cot[0].data());
+      for (int k = 0; k < nu; ++k) {
+        double wk[3];
+        for (int ch = 0; ch < 3; ++ch) wk[ch] = wgn[ch] * jz[k][ch * HW + px];
+        blend_reverse(tr, V.sp, wk, cot[1 + k].data());
+      }
+    });
+    for (long i = 0; i < n; ++i) {
+      if (!V.sp[i].valid) continue;
+      for (int s = 0; s <= nu; ++s) {
+        const double* c = cot[s].data() + i * NQ;
+        bool any = false;
+        for (int q = 0; q < NQ; ++q) any = any || c[q] != 0.0;
+        if (!any) continue;
+        std::fill(g_acc.begin(), g_acc.end(), 0.0);
+        project_reverse(P, pitch, i, deg, V.cam, c, g_acc);
+        for (int r = 0; r < rows; ++r) {
+          if (s == 0) grad[(long)r * n + i] += g_acc[r];
+          else hz[(long)r * n + i] += z[s - 1][(size_t)r * pitch + i] * g_acc[r] / nu;
+        }
+      }
+    }
+    img_off += 3 * HW;
+  }
+  return f;
+}
+
+// Per-parameter trust-region radii (rows x n, row pitch n).
+// cfg: theta1, theta2, d_floor, color_floor, l, mean_exact.
+void or_shd_radius(const double* P, long pitch, long n, int deg, double eps, const double* cfg6,
+                   double* eta) {
+  TRConfig cfg = read_cfg(cfg6);
+  int rows = n_rows(deg);
+  double ymax[16];
+  sh_absmax(deg, ymax);
+  std::vector<double> e(rows);
+  for (long i = 0; i < n; ++i) {
+    shd_radius(P, pitch, i, deg, eps, cfg, ymax, e.data());
+    for (int r = 0; r < rows; ++r) eta[(long)r * n + i] = e[r];
+  }
+}
+
+// Algorithm 1, lines "update EMA of g", "update EMA of D every l steps", Newton
+// step, radius, clip, update, for step t (t >= 1).  Arrays are rows x pitch;
+// hz may be null on steps without a Hutchinson estimate.  The denominator is
+// max(D_hat, d_floor).  If eta_out is given it receives the radii (rows x pitch).
+void or_tr_update(double* x, double* g_ema, double* d_ema, const double* grad, const double* hz, long pitch,
+                  long n, int deg, const double* cfg6, int64_t t, double eps, double* eta_out) {
+  TRConfig cfg = read_cfg(cfg6);
+  int rows = n_rows(deg);
+  double ymax[16];
+  sh_absmax(deg, ymax);
+  bool hvp_step = ((t - 1) % cfg.l) == 0;
+  std::vector<double> eta(rows);
+  for (long i = 0; i < n; ++i) {
+    shd_radius(x, pitch, i, deg, eps, cfg, ymax, eta.data());  // from x_t, before the update
+    for (int r = 0; r < rows; ++r) {
+      long j = (long)r * pitch + i;
+      g_ema[j] = cfg.theta1 * g_ema[j] + (1.0 - cfg.theta1) * grad[j];
+      if (hvp_step && hz) d_ema[j] = cfg.theta2 * d_ema[j] + (1.0 - cfg.theta2) * hz[j];
+      double delta = -g_ema[j] / std::max(d_ema[j], cfg.d_floor);
+      double e = eta[r];
+      double dh = std::min(std::max(delta, -e), e);
+      if (eta_out) eta_out[j] = e;
+      x[j] += dh;
+    }
+  }
+}
+
+// Per-pixel signature (V x H x W) of every discrete decision the blend took:
+// which splats contributed, whether their alpha was capped, and which clamps of
+// their projection were active.  Two parameter vectors with equal signatures
+// lie on the same smooth piece of the objective.
+void or_signature(const double* P, long pitch, long n, int deg, const double* cams, int n_views, int tw,
+                  int th, uint64_t* sig) {
+  long off = 0;
+  for (int v = 0; v < n_views; ++v) {
+    View V = build_view(P, pitch, n, deg, cams + 24 * v, tw, th);
+    for_each_pixel(V, [&](int tx, int ty, int x, int y) {
+      double C[3], T;
+      int nc;
+      std::vector<Contrib> tr;
+      blend(V.lists[(size_t)ty * V.Tx + tx], V.sp, x + 0.5, y + 0.5, C, T, nc, nullptr, &tr);
+      uint64_t h = 0xcbf29ce484222325ULL;
+      auto mix = [&](uint64_t u) { h = (h ^ u) * 0x100000001b3ULL; };
+      for (const Contrib& e : tr) {
+        mix((uint64_t)e.i);
+        mix((uint64_t)(e.capped ? 1 : 0) | ((uint64_t)V.sp[e.i].flags << 1));
+      }
+      mix((uint64_t)nc);
+      sig[off + (long)y * V.cam.W + x] = h;
+    });
+    off += (long)V.cam.W * V.cam.H;
+  }
+}
+
+double or_hellinger(const double* mu1, const double* S1, double Z1, const double* mu2, const double* S2,
+                    double Z2) {
+  return hellinger(mu1, S1, Z1, mu2, S2, Z2);
+}
+
+void or_rotation_beta(const double* q, const double* s, double* beta) { rotation_beta(q, s, beta); }
+
+}  // extern "C"
