@@ -1,0 +1,398 @@
+#!/usr/bin/env python
+"""Benchmark: trust-region steps/s of the 3DGS^2-TR iteration on one GB300.
+
+Workload (the batched multi-view configuration): 1,000,000 Gaussians (FP32, SH
+degree 3) drawn from 20 isotropic clusters (sigma 0.3) in a radius-10 scene, 8
+views of 1920x1080 per step from a 64-camera jittered ring, 16x16 tiles, L1 loss,
+nu = 2 Rademacher probes and the Hutchinson diagonal on every step.  One step =
+projection + binning/sort + forward (with tangents) + reverse pass (gradient and
+z.Hz) + trust-region update over all 8 views.  Targets are rendered once, before
+timing, from a second seeded Gaussian set by the forward pass.
+
+Printed JSON line: value = whole-job steps/s with inputs resident in HBM; e2e =
+the same through the C ABI with the step's targets and cameras copied from
+pinned host memory and the loss read back inside the timed region; roofline of
+the dominant kernel; the FP64 oracle as a CPU baseline on a bounded sample.
+
+``--impl reference`` times the FP64 CPU oracle (the only reference this
+project has) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_GAUSS = 1_000_000
+SH_DEG = 3
+N_VIEWS = 8
+W, H = 1920, 1080
+NU = 2
+RING = 64
+TILE = (16, 16)
+METRIC = "TR steps/s (fwd+bwd+HVP+update) @1M Gaussians 1080p"
+UNIT = "steps/s"
+WORKLOAD = "batched multi-view: 1M Gaussians SH3, 20 clusters sigma 0.3 in radius-10 ball, 8 views 1920x1080 per step, nu=2"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="cuda", choices=["cuda", "reference"])
+    ap.add_argument("--n", type=int, default=N_GAUSS)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-steps", type=int, default=0, help="run N untimed steps only (for ncu)")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) >= 9 and p[1].replace(".", "").isdigit():
+                rows.append(p)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows]
+        mx = max(float(r[2]) for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "samples": len(rows), "reasons": reasons}
+
+
+# ------------------------------------------------------------------ workload
+def make_workload(n, device, rank=0):
+    import numpy as np
+    import torch
+    from paper_2602_00395_gb300 import synth as S
+    from paper_2602_00395_gb300.engine import TRConfig, TRStep
+    from paper_2602_00395_gb300 import gs3dtr as G
+
+    scene = S.make_scene(n, SH_DEG, seed=1000 + rank, kind="clusters", extent=10.0)
+    gt = S.make_scene(n, SH_DEG, seed=2000 + rank, kind="clusters", extent=10.0)
+    cams = S.camera_ring(RING, W, H, 10.0, seed=7)
+    batches = [[cams[b + RING // N_VIEWS * k] for k in range(N_VIEWS)] for b in range(RING // N_VIEWS)]
+    eng = TRStep(n, SH_DEG, N_VIEWS, W, H, nu=NU, tile=TILE, cfg=TRConfig(l=1), device=device)
+    # targets: the ground-truth set rendered by the forward pass, one batch of views at a time
+    eng.set_params(gt.params)
+    cam_dev, targets = [], []
+    need = 0
+    for bcams in batches:
+        eng.set_cameras(bcams)
+        need = max(need, eng.ensure_capacity())
+        eng.render()
+        targets.append(eng.image.clone())
+        cam_dev.append(eng.cams.clone())
+    eng.set_params(scene.params)
+    for cd in cam_dev:
+        eng.cams.copy_(cd)
+        need = max(need, eng.ensure_capacity())
+    if need * 1.15 > eng.capacity:
+        eng._alloc_pairs(int(need * 1.3))
+    torch.cuda.synchronize()
+    return eng, cam_dev, targets, batches, need
+
+
+def kernel_launches_per_step(eng) -> int:
+    tiles = N_VIEWS * eng.Tx * eng.Ty
+    bits = 1
+    while (1 << bits) < tiles:
+        bits += 1
+    npass = (32 + bits + 7) // 8
+    sort = 1 + 3 + 1 + npass * (1 + 3 + 1) + 1
+    return 1 + sort + 1 + 2 + 1  # project, sort, fwd, bwd + projection reverse, update
+
+
+def timed_steps(eng, cam_dev, targets, K, W0, t0, stream, per_call=False):
+    """K steps on `stream`; returns (ms total from events, per-call ms dict)."""
+    import torch
+    from paper_2602_00395_gb300.engine import eps_schedule
+    calls = ["project", "bin_sort", "raster_fwd", "raster_bwd", "update"]
+    ev = {c: [] for c in calls}
+    start = torch.cuda.Event(enable_timing=True)
+    stop = torch.cuda.Event(enable_timing=True)
+    nb = len(targets)
+    with torch.cuda.stream(stream):
+        start.record(stream)
+        for k in range(K):
+            t = t0 + k
+            b = (t - 1) % nb
+            eng.cams = cam_dev[b]
+            eng.target = targets[b]
+            eps = eps_schedule(t, 30000)
+            eng.loss_val.zero_()
+            seq = [("project", lambda: eng.project(t, True, stream)),
+                   ("bin_sort", lambda: eng.bin_sort(stream)),
+                   ("raster_fwd", lambda: eng.raster_fwd(t, True, stream)),
+                   ("raster_bwd", lambda: eng.raster_bwd(t, True, stream)),
+                   ("update", lambda: eng.update(t, eps, True, None, stream))]
+            for name, fn in seq:
+                if per_call:
+                    a = torch.cuda.Event(enable_timing=True)
+                    z = torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    fn()
+                    z.record(stream)
+                    ev[name].append((a, z))
+                else:
+                    fn()
+        stop.record(stream)
+    stop.synchronize()
+    total = start.elapsed_time(stop)
+    per = {c: (sum(a.elapsed_time(z) for a, z in ev[c]) / len(ev[c]) if ev[c] else None) for c in calls}
+    return total, per
+
+
+def e2e_steps(eng, batches, host_targets, K, t0, stream):
+    """K steps through the C ABI with the step's targets and cameras copied from
+    pinned host memory and the loss copied back, all inside the timed region."""
+    import numpy as np
+    import torch
+    from paper_2602_00395_gb300 import gs3dtr as G
+    from paper_2602_00395_gb300.engine import eps_schedule
+    host_cams = [torch.from_numpy(G.camera_bytes(bc)).pin_memory() for bc in batches]
+    loss_host = torch.zeros(K, dtype=torch.float32).pin_memory()
+    nb = len(batches)
+    start = torch.cuda.Event(enable_timing=True)
+    stop = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        start.record(stream)
+        for k in range(K):
+            t = t0 + k
+            b = (t - 1) % nb
+            eng.cams.copy_(host_cams[b], non_blocking=True)
+            eng.target.copy_(host_targets[b], non_blocking=True)
+            eng.step(t, eps_schedule(t, 30000), stream)
+            loss_host[k:k + 1].copy_(eng.loss_val, non_blocking=True)
+        stop.record(stream)
+    stop.synchronize()
+    wall = time.perf_counter() - w0
+    h2d = host_targets[0].numel() * 4 + host_cams[0].numel()
+    return start.elapsed_time(stop), wall, h2d, 4
+
+
+# ------------------------------------------------------------------ roofline
+def raster_bwd_flops_per_pair() -> int:
+    """FP32 operations per evaluated (pixel, splat) pair of the reverse kernel with
+    1 + nu cotangent streams: shared part (offsets, power, exp, alpha, T recovery,
+    dC/dalpha, suffix update) + per-stream part (dL/dalpha, power/opacity/colour
+    partials) + the warp reduce-scatter adds amortised per lane."""
+    shared = 2 + 7 + 1 + 2 + 3 + 9 + 6 + 3
+    per_stream = 5 + 2 + 10 + 1 + 3
+    return shared + (1 + NU) * per_stream + 31
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return d.get("hbm_gbs", 6800.0), d.get("sm_max_mhz", 2070.0), "measured"
+    return 6800.0, 2070.0, "fallback"
+
+
+# ------------------------------------------------------------------ CPU oracle
+def oracle_sample(seconds_hint=True):
+    """Bounded oracle sample: the same distributions at 1/100 of the Gaussians,
+    one of the 8 views at full 1080p, nu = 2, one full step (forward, reverse pass
+    with the Hutchinson product, update).  Scaled to the full step by x100 (Gaussians)
+    x8 (views)."""
+    import numpy as np
+    import oracle as O
+    from paper_2602_00395_gb300 import synth as S
+    n = N_GAUSS // 100
+    sc = S.make_scene(n, SH_DEG, seed=1000, kind="clusters", extent=10.0)
+    cam = S.camera_ring(RING, W, H, 10.0, seed=7)[:1]
+    target = S.noise_target(1, H, W, seed=2000).astype(np.float64)
+    P = O.params64(sc)
+    t0 = time.perf_counter()
+    out = O.backward(P, SH_DEG, cam, target, seed=42, t=1, nu=NU)
+    O.tr_update(P, np.zeros_like(P), np.zeros_like(P), out["grad"], out["hz"], SH_DEG, t=1, eps=1e-6,
+                cfg=O.tr_config(l=1))
+    dt = time.perf_counter() - t0
+    scale = 100 * N_VIEWS
+    return dt, scale, f"{n} Gaussians (1/100), 1 of {N_VIEWS} views at {W}x{H}, nu={NU}, one full step; x{scale}"
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import __graft_entry__  # noqa: F401
+    import oracle
+    oracle.build()
+    for _ in range(max(0, args.warmup)):
+        oracle_sample()
+        break  # one warm-up sample is enough for a CPU program
+    times = []
+    desc = ""
+    for _ in range(args.steps):
+        dt, scale, desc = oracle_sample()
+        times.append(dt * scale)
+    step_s = sum(times) / len(times)
+    val = 1.0 / step_s
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": desc},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+# ------------------------------------------------------------------ main
+def run_cuda(args):
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    device = f"cuda:{local}"
+    import __graft_entry__
+    __graft_entry__.build() if rank == 0 or ws == 1 else None
+    if ws > 1:
+        torch.distributed.barrier()
+    from paper_2602_00395_gb300 import gs3dtr as G
+    G.load()
+    eng, cam_dev, targets, batches, need = make_workload(args.n, device, rank)
+    stream = torch.cuda.Stream(device=device)
+    if args.profile_steps:
+        timed_steps(eng, cam_dev, targets, args.profile_steps, 0, 1, stream)
+        torch.cuda.synchronize()
+        return
+    # warm-up
+    timed_steps(eng, cam_dev, targets, max(args.warmup, 3), 0, 1, stream)
+    torch.cuda.synchronize()
+    eng.status.zero_()
+    # per-call breakdown (separate, untimed for the headline)
+    _, per_call = timed_steps(eng, cam_dev, targets, max(2, min(args.steps, 5)), 0, 100, stream, per_call=True)
+    # timed region
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ms, _ = timed_steps(eng, cam_dev, targets, args.steps, 0, 1000, stream)
+        torch.cuda.synchronize()
+    status = eng.read_status()
+    if ws > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([ms], device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+        dist.barrier()
+    ms_per_step = ms / args.steps
+    value = ws * args.steps / (ms / 1e3)
+    # end to end through the C ABI from pinned host buffers
+    host_targets = [tg.cpu().pin_memory() for tg in targets]
+    e2e_ms, e2e_wall, h2d, d2h = e2e_steps(eng, batches, host_targets, args.steps, 5000, stream)
+    e2e_val = ws * args.steps / (e2e_ms / 1e3)
+    # roofline of the dominant call
+    torch.cuda.synchronize()
+    sum_nc = float(eng.n_contrib.double().sum().item())
+    hbm, sm_mhz, src = peaks()
+    fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    bwd_ms = per_call["raster_bwd"]
+    flops = raster_bwd_flops_per_pair() * sum_nc
+    achieved = flops / (bwd_ms * 1e-3) / 1e12
+    roof = {"kernel": "gs_raster_bwd (reverse blend + projection reverse)", "bound": "alu", "achieved": achieved,
+            "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
+            "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz ({src} max clock)",
+            "work": f"{raster_bwd_flops_per_pair()} FLOP x {sum_nc:.3e} evaluated (pixel, splat) pairs"}
+    clocks = clk.summary()
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        try:
+            import oracle
+            oracle.build()
+            dt, scale, desc = oracle_sample()
+            cpu = {"value": 1.0 / (dt * scale), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
+                   "sample_seconds": dt}
+        except Exception as ex:  # pragma: no cover
+            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {ex}"}
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_gaussians": args.n, "views_per_step": N_VIEWS,
+                       "image": f"{W}x{H}", "nu": NU, "tile": f"{TILE[0]}x{TILE[1]}", "pairs_per_step": need,
+                       "parallelism": "replicas" if ws > 1 else "single GPU",
+                       "l2": "inputs larger than L2 (236 MB parameters, 199 MB targets per step)",
+                       "view_steps_per_s": value * N_VIEWS},
+            "per_call_ms": per_call, "status_word": status,
+            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "wall_s": e2e_wall},
+            "gpu_launches": kernel_launches_per_step(eng) * args.steps,
+            "roofline": roof, "clocks": clocks, "cpu_baseline": cpu,
+        }
+        print(json.dumps(out))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_cuda(args)
+
+
+if __name__ == "__main__":
+    main()

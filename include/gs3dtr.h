@@ -1,0 +1,220 @@
+/*
+ * gs3dtr.h - C ABI of the GB300 hot path of the 3DGS^2-TR optimiser
+ * (arXiv 2602.00395, "Scalable Second-Order Trust-Region Method for 3D
+ * Gaussian Splatting").
+ *
+ * One training iteration is six calls, all asynchronous on a caller stream:
+ *
+ *   gs_project      EWA projection of every Gaussian into every view   (Sec. 3.1)
+ *   gs_bin_sort     (tile, depth) keys and their radix sort, tile ranges (Sec. 3.1)
+ *   gs_raster_fwd   front-to-back alpha blending (+ forward-mode tangents J z)
+ *   gs_raster_bwd   reverse pass: gradient g = (1/m) J^T F           (Sec. 4.1)
+ *                   and, fused, the Hutchinson product (1/nu) sum z.(G z)
+ *   gs_hvp_diag     the Hutchinson product alone                      (Sec. 4.1)
+ *   gs_tr_update    Algorithm 1: EMAs, diagonal Newton step, squared-Hellinger
+ *                   radius per parameter, clip, update          (Sec. 4.2, App. B)
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Every pointer inside the structs and every array argument is DEVICE memory
+ *   owned by the caller, 16-byte aligned, unless marked "host".  The structs
+ *   themselves are host memory read during the call only.
+ * - No call allocates device memory or synchronises the stream.  Scratch
+ *   space comes from the caller through the *_workspace_size queries.
+ * - Calls return GS_OK or an error code for invalid arguments or a failed
+ *   launch; gs_last_error() then describes the first problem (thread-local).
+ *   Conditions found on the device (pair capacity exceeded, non-finite values,
+ *   a bounded wait that gave up) are OR-ed into the caller's device status word
+ *   (int32, may be NULL) as GS_FLAG_* bits, to be read after the stream completes.
+ * - No C++ exception crosses this boundary.
+ *
+ * Parameter layout (gs_params): one float32 matrix of `rows` rows and row
+ * pitch n_pad (n_pad >= n, n_pad % 4 == 0), grouped by type as in Sec. 3.1:
+ *     rows 0..2   mean mu                      rows 3..5   log-scale (s = exp)
+ *     rows 6..9   quaternion (x, y, z, w), unnormalised
+ *     row  10     opacity logit (alpha = sigmoid)
+ *     rows 11..   SH coefficient k of channel c at row 11 + 3k + c, K = (deg+1)^2
+ *     rows = 11 + 3K (14 for degree 0, 59 for degree 3)
+ * Gradient, Hutchinson, EMA and radius buffers use the same struct and layout.
+ * Global parameter index (used by the probes) j = row * n + column.
+ */
+#ifndef GS3DTR_H
+#define GS3DTR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ status */
+typedef int32_t gs_status;
+enum {
+  GS_OK = 0,
+  GS_ERR_INVALID_ARG = 1, /* a host-checked argument is out of range */
+  GS_ERR_CUDA = 2,        /* a kernel launch or async memset failed */
+  GS_ERR_UNSUPPORTED = 3  /* valid but not built (e.g. nu > 2, sh_degree > 3) */
+};
+/* bits of the device status word */
+enum {
+  GS_FLAG_CAPACITY = 1,  /* gs_bin_sort: more pairs than capacity; *n_pairs holds the need */
+  GS_FLAG_NONFINITE = 2, /* gs_tr_update: a non-finite value was written */
+  GS_FLAG_TIMEOUT = 4    /* a bounded wait on an asynchronous copy gave up */
+};
+
+const char* gs_last_error(void); /* host string, valid until the next call on this thread */
+int32_t gs_version(void);        /* major * 10000 + minor * 100 + patch */
+
+/* ------------------------------------------------------------ data */
+typedef struct gs_params {
+  int32_t n;         /* Gaussians */
+  int32_t n_pad;     /* row pitch in elements, multiple of 4, >= n */
+  int32_t sh_degree; /* 0..3 */
+  int32_t reserved;
+  float* data;       /* device, rows x n_pad */
+} gs_params;
+
+/* Pinhole camera, world -> camera viewmat (row-major, camera x right, y down,
+ * z forward).  Pixel (i, j) is sampled at (i + 0.5, j + 0.5).  Arrays of
+ * cameras are DEVICE arrays of this struct. */
+typedef struct gs_camera {
+  float viewmat[16];
+  float fx, fy, cx, cy;
+  float near_plane;
+  int32_t width, height;
+  int32_t reserved;
+} gs_camera;
+
+/* Views rendered by one call; every camera of the call has this size.
+ * tile_w * tile_h is 64, 128 or 256 and both are powers of two. */
+typedef struct gs_frame {
+  int32_t n_views, width, height, tile_w, tile_h;
+} gs_frame;
+
+/* Rademacher probes z_k (k < nu) of step t: entry j is +1 or -1 from bit 63 of
+ * SplitMix64(seed ^ t * 0x9E3779B97F4A7C15 ^ (k << 56) ^ j). */
+typedef struct gs_probe {
+  uint64_t seed;
+  int64_t t;
+  int32_t nu; /* 0, 1 or 2 */
+  int32_t reserved;
+} gs_probe;
+
+/* Projected splats of V views (device, caller-owned).
+ *   rec:     V x n_pad records of 12 floats (48 B):
+ *            (mx, my, A, B), (C, opacity, r, g), (b, depth, radius, tiles)
+ *            where (A, B, C) is the conic and radius / tiles are int32 bit patterns
+ *   tangent: NULL or V x nu x n_pad records of 12 floats, the forward-mode
+ *            derivative of (mx, my, A, B, C, opacity, r, g, b) along probe k */
+typedef struct gs_projected {
+  float* rec;
+  float* tangent;
+} gs_projected;
+
+/* Sorted (tile, splat) pairs (device, caller-owned).
+ *   keys:     capacity x uint64, key = (view * tiles + tile) << 32 | bits(depth)
+ *   vals:     capacity x uint32, splat index
+ *   ranges:   V * tiles x 2 uint32, [start, end) of each tile's pairs
+ *   n_pairs:  one uint32, number of pairs the views need (may exceed capacity) */
+typedef struct gs_sorted {
+  uint64_t* keys;
+  uint32_t* vals;
+  uint32_t* ranges;
+  uint32_t* n_pairs;
+  uint64_t capacity;
+} gs_sorted;
+
+enum { GS_LOSS_L1 = 0, GS_LOSS_L2 = 1 };
+
+/* Per-pixel loss of Sec. 3.2 in least-squares form f = 1/(2m) sum F^2 over the
+ * m = 3 H W V residual components r = render - target:
+ *   GS_LOSS_L1: F = sqrt(|r|); dL/dC = sign(r)/(2m); GN weight 1/(4 max(|r|, gn_floor)) / m
+ *   GS_LOSS_L2: F = r;         dL/dC = r/m;          GN weight 1/m */
+typedef struct gs_loss {
+  int32_t kind;
+  float gn_floor;
+} gs_loss;
+
+/* Algorithm 1 hyper-parameters.  The denominator of the Newton step is
+ * max(D_hat, d_floor); the colour radius uses max(DC colour, color_floor);
+ * mean_exact = 0 uses Sigma_cc as printed in Sec. 4.2, 1 uses 1/(Sigma^-1)_cc. */
+typedef struct gs_tr_config {
+  float theta1, theta2, d_floor, color_floor;
+  int32_t l, mean_exact;
+} gs_tr_config;
+
+/* ------------------------------------------------------------ calls */
+
+/* Sec. 3.1 (projection the paper defers to 3DGS): for every Gaussian and view,
+ *   t = W mu + t_w (culled if t_z <= near), Sigma = R diag(s^2) R^T,
+ *   Sigma' = J W Sigma W^T J^T + 0.3 I (J the perspective Jacobian with the
+ *   image-plane slope clamped at 1.3 x the half field of view), conic = Sigma'^-1,
+ *   radius = ceil(3 sqrt(lambda_max)), rgb = max(SH(view dir) + 0.5, 0),
+ *   opacity = sigmoid(logit), tile rectangle decided in FP32:
+ *   x0 = clamp(floor((mx - r)/tw), 0, Tx), x1 = clamp(floor((mx + (r+tw-1))/tw), 0, Tx).
+ * cams: device array of frame.n_views cameras.  probe may be NULL (no tangents);
+ * otherwise out->tangent receives probe->nu tangent records per view. */
+gs_status gs_project(const gs_params* x, const gs_camera* cams, gs_frame frame, const gs_probe* probe,
+                     gs_projected* out, int32_t* status, void* stream);
+
+/* Sec. 3.1 tile binning and depth order: all (tile, splat) pairs of all views
+ * sorted by (key, splat index), and each tile's [start, end).  If the pairs
+ * exceed out->capacity, GS_FLAG_CAPACITY is raised, *n_pairs holds the need,
+ * and the sorted arrays are incomplete (but every access stays in bounds). */
+size_t gs_bin_sort_workspace_size(int32_t n_pad, gs_frame frame, uint64_t capacity);
+gs_status gs_bin_sort(const gs_projected* proj, int32_t n_pad, gs_frame frame, void* workspace,
+                      size_t workspace_bytes, gs_sorted* out, int32_t* status, void* stream);
+
+/* Sec. 3.1 blending: C = sum_i c_i a_i T_i, T_i = prod_{j<i} (1 - a_j),
+ * a = min(0.99, o exp(power)), splats with a < 1/255 skipped, stop before T
+ * would fall below 1e-4, black background.
+ *   image V x 3 x H x W, final_T V x H x W, n_contrib V x H x W (1 + list
+ *   position of the last blended splat).  If proj->tangent and probe are given,
+ *   image_tangent (probe->nu x V x 3 x H x W) receives J z_k. */
+gs_status gs_raster_fwd(const gs_projected* proj, const gs_sorted* sorted, int32_t n_pad, gs_frame frame,
+                        const gs_probe* probe, float* image, float* final_T, uint32_t* n_contrib,
+                        float* image_tangent, int32_t* status, void* stream);
+
+/* Sec. 4.1: gradient g = (1/m) J^T F of the objective (Eq. objective) over the
+ * frame's views, written to grad (overwritten).  If image_tangent and probe are
+ * given (S2 = S1), the same reverse pass also writes the Hutchinson diagonal
+ * hz = (1/nu) sum_k z_k . ((1/m) J^T diag(w) J z_k) (overwritten).  loss_out
+ * (one float, may be NULL) gets the objective added.  workspace from
+ * gs_raster_bwd_workspace_size. */
+size_t gs_raster_bwd_workspace_size(int32_t n_pad, gs_frame frame, int32_t nu);
+gs_status gs_raster_bwd(const gs_params* x, const gs_camera* cams, gs_frame frame, const gs_projected* proj,
+                        const gs_sorted* sorted, const float* image, const float* target, const float* final_T,
+                        const uint32_t* n_contrib, const float* image_tangent, const gs_probe* probe,
+                        gs_loss loss, gs_params* grad, gs_params* hz, float* loss_out, void* workspace,
+                        size_t workspace_bytes, int32_t* status, void* stream);
+
+/* Sec. 4.1, Hutchinson's estimator alone (for a mini-batch S2 other than S1):
+ * hz = (1/nu) sum_k z_k . ((1/m) J^T diag(w) J z_k) (overwritten), from the
+ * image tangents J z_k of gs_raster_fwd with the same probe. */
+gs_status gs_hvp_diag(const gs_params* x, const gs_camera* cams, gs_frame frame, const gs_projected* proj,
+                      const gs_sorted* sorted, const float* image, const float* target, const float* final_T,
+                      const uint32_t* n_contrib, const float* image_tangent, const gs_probe* probe,
+                      gs_loss loss, gs_params* hz, void* workspace, size_t workspace_bytes, int32_t* status,
+                      void* stream);
+
+/* Algorithm 1 for step t >= 1 with radius parameter eps (Sec. 4.2, App. B):
+ *   g_ema = theta1 g_ema + (1 - theta1) grad
+ *   d_ema = theta2 d_ema + (1 - theta2) hz      when (t - 1) % l == 0 (hz may be NULL otherwise)
+ *   step  = clip(-g_ema / max(d_ema, d_floor), -eta, eta),  x += step
+ * with eta per parameter from x before the update:
+ *   mean       sqrt(-8 Sigma_cc ln(1 - eps/alpha))        (inf if alpha <= eps)
+ *   log-scale  sqrt(2 eps / alpha)
+ *   quaternion sqrt(-(8/beta_c) ln(1 - eps/alpha))        (inf if beta_c = 0 or alpha <= eps)
+ *   logit      sqrt(4 alpha eps) / (alpha (1 - alpha))
+ *   SH (k, c)  sqrt(4 C_c eps / alpha) / max|Y_k|         (C_c the floored DC colour)
+ * eta_out (may be NULL) receives the radii.  All gs_params share n, n_pad and degree.
+ * A non-finite result raises GS_FLAG_NONFINITE. */
+gs_status gs_tr_update(gs_params* x, gs_params* g_ema, gs_params* d_ema, const gs_params* grad,
+                       const gs_params* hz, const gs_tr_config* cfg, int64_t t, float eps, gs_params* eta_out,
+                       int32_t* status, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GS3DTR_H */

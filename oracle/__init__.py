@@ -62,6 +62,7 @@ def lib():
                                       P, P, P, P]
             L.or_shd_radius.argtypes = [P, i64, i64, i32, d, P, P]
             L.or_tr_update.argtypes = [P, P, P, P, P, i64, i64, i32, P, C.c_int64, d, P]
+            L.or_project_tangent.argtypes = [P, i64, i64, i32, P, P, P]
             L.or_signature.argtypes = [P, i64, i64, i32, P, i32, i32, i32, P]
             L.or_hellinger.restype = d
             L.or_hellinger.argtypes = [P, P, d, P, P, d]
@@ -145,6 +146,25 @@ def project(P: np.ndarray, deg: int, cam) -> dict:
     ca = camera_array([cam])
     lib().or_project(_p(P), n, n, deg, _p(ca), _p(out))
     return {f: out[:, k] for k, f in enumerate(SPLAT_FIELDS)}
+
+
+def project_tangent(P: np.ndarray, deg: int, cam, direction: np.ndarray) -> np.ndarray:
+    """n x 9 tangents of (mx, my, A, B, C, o, r, g, b) along a parameter direction (rows x n)."""
+    P = _f64(P)
+    rows, n = P.shape
+    d = _f64(direction)
+    out = np.zeros((n, 9))
+    lib().or_project_tangent(_p(P), n, n, deg, _p(camera_array([cam])), _p(d), _p(out))
+    return out
+
+
+def probe_matrix(seed: int, t: int, k: int, rows: int, n: int) -> np.ndarray:
+    """Rademacher probe k of step t as a rows x n matrix (entry j = r * n + i)."""
+    z = np.empty(rows * n)
+    L = lib()
+    for j in range(rows * n):
+        z[j] = L.or_rademacher(seed, t, k, j)
+    return z.reshape(rows, n)
 
 
 def bin_sort(mx, my, radius, depth, width: int, height: int, tw: int = 16, th: int = 16):

@@ -333,7 +333,12 @@ struct View {
   std::vector<int> lo, hi;
 };
 
+// Rounding envelopes of the FP32 inputs of a binning decision: the radius
+// (3 sqrt(lambda_max) from a chain of FP32 products, ~1e-6 relative, widened
+// 10x) and the splat centre (a few FP32 ulps of its coordinate).
 const double kAmbRel = 1e-5;
+const double kAmbCentreRel = 1e-6;
+const double kAmbCentreAbs = 1e-5;
 
 View build_view(const double* P, long pitch, long n, int deg, const double* cam24, int tw, int th) {
   View V;
@@ -356,8 +361,8 @@ View build_view(const double* P, long pitch, long n, int deg, const double* cam2
     double rr = s.radius_raw;
     int r_lo = (int)std::ceil(rr * (1.0 - kAmbRel) - 1e-6);
     int r_hi = (int)std::ceil(rr * (1.0 + kAmbRel) + 1e-6);
-    double ex = kAmbRel * (std::fabs(s.mx) + rr + tw) + 1e-4;
-    double ey = kAmbRel * (std::fabs(s.my) + rr + th) + 1e-4;
+    double ex = kAmbCentreRel * (std::fabs(s.mx) + rr + tw) + kAmbCentreAbs;
+    double ey = kAmbCentreRel * (std::fabs(s.my) + rr + th) + kAmbCentreAbs;
     int a0, a1, b0, b1, c0, c1, d0, d1;
     // shrunk rectangle: lower edges from the centre moved up, upper edges from it moved down
     rect_f32((float)(s.mx + ex), (float)(s.my + ey), r_lo, tw, th, V.Tx, V.Ty, a0, a1, b0, b1);
@@ -833,6 +838,23 @@ long or_render(const double* P, long pitch, long n, int deg, const double* cams,
     });
   }
   return pairs;
+}
+
+// Forward-mode tangents of the splat quantities (mx, my, A, B, C, o, r, g, b) of
+// every Gaussian for one camera along the parameter direction `dir`
+// (rows x pitch).  out: n x 9.
+void or_project_tangent(const double* P, long pitch, long n, int deg, const double* cam24, const double* dir,
+                        double* out) {
+  Cam cam = make_cam(cam24);
+  int rows = n_rows(deg);
+  std::vector<double> tan(rows);
+  for (long i = 0; i < n; ++i) {
+    for (int r = 0; r < rows; ++r) tan[r] = dir[(long)r * pitch + i];
+    Splat<Dual> s = project(load_gaussian<Dual>(P, pitch, i, deg, tan.data()), cam);
+    double v[9] = {s.mx.d, s.my.d, s.A.d, s.B.d, s.C.d, s.o.d, s.rgb[0].d, s.rgb[1].d, s.rgb[2].d};
+    if (!s.valid) for (int q = 0; q < 9; ++q) v[q] = 0.0;
+    std::memcpy(out + 9 * i, v, sizeof(v));
+  }
 }
 
 // Image tangent (V x 3 x H x W) along the parameter direction `dir` (rows x pitch).

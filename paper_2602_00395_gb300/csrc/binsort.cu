@@ -1,0 +1,422 @@
+// gs_bin_sort: tile binning and depth order of the tile-based rasteriser
+// (Sec. 3.1 of arXiv 2602.00395).
+//
+//   count   per (view, splat): tiles of its FP32 rectangle
+//   scan    exclusive prefix sum -> emission offsets and the pair count P
+//   emit    key = (view * tiles + tile) << 32 | bits(depth), value = splat index
+//   sort    LSD radix sort over the used key bits, 8 bits per pass: a per-block
+//           digit histogram, a device-wide scan of the histograms, then a
+//           scatter that ranks each block's keys stably in shared memory and
+//           writes every digit's run contiguously.  No block waits on another.
+//   ranges  [start, end) of every tile
+//
+// Emission is in splat order and every pass is stable, so equal keys stay in
+// splat-index order: the result is the total order (key, splat index).
+// Grids are sized by the pair capacity and read P from device memory, so the
+// whole call needs no host synchronisation (and can be captured in a graph).
+#include "common.cuh"
+
+namespace gs {
+namespace {
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanChunk = kScanThreads * kScanItems;  // 2048
+constexpr int kRadixThreads = 256;
+constexpr int kRadixItems = 8;
+constexpr int kRadixTile = kRadixThreads * kRadixItems;  // 2048
+constexpr int kRadixWarps = kRadixThreads / 32;
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// ------------------------------------------------------------------ count
+__global__ void count_kernel(const float4* __restrict__ rec, int n_pad, gs_frame fr, int Tx, int Ty,
+                             uint32_t* __restrict__ counts) {
+  const size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= (size_t)fr.n_views * n_pad) return;
+  const float4 a = rec[3 * g + 0];
+  const float4 c = rec[3 * g + 2];
+  const int r = __float_as_int(c.z);
+  uint32_t cnt = 0;
+  if (r > 0) {
+    int x0, x1, y0, y1;
+    tile_rect(a.x, a.y, r, fr.tile_w, fr.tile_h, Tx, Ty, x0, x1, y0, y1);
+    cnt = (uint32_t)max(0, x1 - x0) * (uint32_t)max(0, y1 - y0);
+  }
+  counts[g] = cnt;
+}
+
+// ------------------------------------------------------------------- scan
+// Block-wide exclusive scan of one value per thread; returns the block total.
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t& total, uint32_t* s_warp) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_warp[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = blockDim.x >> 5;
+    uint32_t w = lane < nw ? s_warp[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    if (lane < nw) s_warp[lane] = w;
+  }
+  __syncthreads();
+  total = s_warp[(blockDim.x >> 5) - 1];
+  const uint32_t before = warp > 0 ? s_warp[warp - 1] : 0;
+  __syncthreads();
+  return before + x - v;
+}
+
+// Length of a scan: n, or, when `pairs` is given, the radix histogram length
+// 256 * ceil(min(*pairs, capacity) / tile) of the pairs in use.
+__device__ __forceinline__ size_t scan_length(size_t n, const uint32_t* pairs, uint64_t capacity) {
+  if (!pairs) return n;
+  const uint64_t p = *pairs < capacity ? *pairs : capacity;
+  return (size_t)256 * (size_t)((p + kRadixTile - 1) / kRadixTile);
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const uint32_t* __restrict__ in, size_t n_host,
+                                                                   const uint32_t* pairs, uint64_t capacity,
+                                                                   uint32_t* __restrict__ block_sums) {
+  __shared__ uint32_t s_warp[32];
+  const size_t n = scan_length(n_host, pairs, capacity);
+  const size_t base = (size_t)blockIdx.x * kScanChunk;
+  if (base >= n) return;
+  uint32_t s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    size_t idx = base + (size_t)k * kScanThreads + threadIdx.x;
+    if (idx < n) s += in[idx];
+  }
+  uint32_t total;
+  block_exclusive_scan(s, total, s_warp);
+  if (threadIdx.x == 0) block_sums[blockIdx.x] = total;
+}
+
+// One block: exclusive scan of the block sums; the grand total goes to *total
+// (and, if capacity is non-zero, GS_FLAG_CAPACITY is raised when it exceeds it).
+__global__ void __launch_bounds__(1024) scan_blocks_kernel(uint32_t* __restrict__ sums, size_t n_host,
+                                                           const uint32_t* pairs, uint64_t pair_capacity,
+                                                           uint32_t* __restrict__ total, uint64_t capacity,
+                                                           int32_t* __restrict__ status) {
+  __shared__ uint32_t s_warp[32];
+  __shared__ uint32_t s_carry;
+  const int nb = (int)((scan_length(n_host, pairs, pair_capacity) + kScanChunk - 1) / kScanChunk);
+  if (threadIdx.x == 0) s_carry = 0;
+  __syncthreads();
+  for (int base = 0; base < nb; base += blockDim.x) {
+    const int idx = base + threadIdx.x;
+    const uint32_t v = idx < nb ? sums[idx] : 0;
+    uint32_t chunk_total;
+    const uint32_t ex = block_exclusive_scan(v, chunk_total, s_warp);
+    const uint32_t carry = s_carry;
+    if (idx < nb) sums[idx] = carry + ex;
+    __syncthreads();
+    if (threadIdx.x == 0) s_carry = carry + chunk_total;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    if (total) *total = s_carry;
+    if (capacity && (uint64_t)s_carry > capacity && status) atomicOr(status, GS_FLAG_CAPACITY);
+  }
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_apply_kernel(const uint32_t* in, uint32_t* out, size_t n_host,
+                                                                  const uint32_t* pairs, uint64_t capacity,
+                                                                  const uint32_t* __restrict__ block_sums) {
+  __shared__ uint32_t s_warp[32];
+  const size_t n = scan_length(n_host, pairs, capacity);
+  if ((size_t)blockIdx.x * kScanChunk >= n) return;
+  const size_t base = (size_t)blockIdx.x * kScanChunk + (size_t)threadIdx.x * kScanItems;
+  uint32_t v[kScanItems];
+  uint32_t s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    v[k] = (base + k < n) ? in[base + k] : 0u;
+    s += v[k];
+  }
+  uint32_t total;
+  uint32_t run = block_exclusive_scan(s, total, s_warp) + block_sums[blockIdx.x];
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    if (base + k < n) out[base + k] = run;
+    run += v[k];
+  }
+}
+
+inline int scan_blocks(size_t n) { return (int)((n + kScanChunk - 1) / kScanChunk); }
+
+// in -> out exclusive scan of n_max entries (in may equal out).  If `pairs` is
+// given, only the radix histogram of the pairs in use is scanned (n_max bounds
+// it).  The grand total goes to *total; GS_FLAG_CAPACITY is raised when it
+// exceeds a non-zero `capacity`.
+void exclusive_scan(const uint32_t* in, uint32_t* out, size_t n_max, const uint32_t* pairs, uint64_t pair_capacity,
+                    uint32_t* block_sums, uint32_t* total, uint64_t capacity, int32_t* status, cudaStream_t st) {
+  const int nb = scan_blocks(n_max);
+  if (nb == 0) return;
+  scan_reduce_kernel<<<nb, kScanThreads, 0, st>>>(in, n_max, pairs, pair_capacity, block_sums);
+  scan_blocks_kernel<<<1, 1024, 0, st>>>(block_sums, n_max, pairs, pair_capacity, total, capacity, status);
+  scan_apply_kernel<<<nb, kScanThreads, 0, st>>>(in, out, n_max, pairs, pair_capacity, block_sums);
+}
+
+// ------------------------------------------------------------------- emit
+__global__ void emit_kernel(const float4* __restrict__ rec, int n_pad, gs_frame fr, int Tx, int Ty,
+                            const uint32_t* __restrict__ offsets, uint64_t capacity, uint64_t* __restrict__ keys,
+                            uint32_t* __restrict__ vals) {
+  const size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= (size_t)fr.n_views * n_pad) return;
+  const float4 c = rec[3 * g + 2];
+  const int r = __float_as_int(c.z);
+  if (r <= 0) return;
+  const float4 a = rec[3 * g + 0];
+  int x0, x1, y0, y1;
+  tile_rect(a.x, a.y, r, fr.tile_w, fr.tile_h, Tx, Ty, x0, x1, y0, y1);
+  const int view = (int)(g / n_pad);
+  const uint32_t splat = (uint32_t)(g - (size_t)view * n_pad);
+  const uint64_t tiles = (uint64_t)Tx * Ty;
+  const uint64_t depth_bits = (uint64_t)__float_as_uint(c.y);
+  uint64_t p = offsets[g];
+  for (int ty = y0; ty < y1; ++ty)
+    for (int tx = x0; tx < x1; ++tx, ++p) {
+      if (p >= capacity) return;
+      const uint64_t tile = (uint64_t)view * tiles + (uint64_t)ty * Tx + tx;
+      keys[p] = (tile << 32) | depth_bits;
+      vals[p] = splat;
+    }
+}
+
+// ------------------------------------------------------------ radix passes
+__device__ __forceinline__ uint32_t pairs_in_use(const uint32_t* n_pairs, uint64_t capacity) {
+  const uint64_t p = *n_pairs;
+  return (uint32_t)(p < capacity ? p : capacity);
+}
+
+// Digit histograms are stored digit-major over the blocks in use,
+// hist[d * nbu + b] with nbu = ceil(P / tile), so that their exclusive scan
+// gives each (digit, block) its first output position.
+__global__ void __launch_bounds__(kRadixThreads) radix_hist_kernel(const uint64_t* __restrict__ keys,
+                                                                   const uint32_t* __restrict__ n_pairs,
+                                                                   uint64_t capacity, int shift,
+                                                                   uint32_t* __restrict__ hist) {
+  __shared__ uint32_t s_cnt[256];
+  const uint32_t P = pairs_in_use(n_pairs, capacity);
+  const size_t base = (size_t)blockIdx.x * kRadixTile;
+  if (base >= P) return;
+  const size_t nbu = ((size_t)P + kRadixTile - 1) / kRadixTile;
+  s_cnt[threadIdx.x] = 0;
+  __syncthreads();
+  {
+#pragma unroll 4
+    for (int k = 0; k < kRadixItems; ++k) {
+      const size_t idx = base + (size_t)k * kRadixThreads + threadIdx.x;
+      const bool ok = idx < P;
+      const uint32_t d = ok ? (uint32_t)(keys[idx] >> shift) & 255u : 256u;
+      const uint32_t peers = __match_any_sync(0xffffffffu, d);
+      if (ok && (peers & lanemask_lt()) == 0) atomicAdd(&s_cnt[d], (uint32_t)__popc(peers));
+    }
+  }
+  __syncthreads();
+  hist[(size_t)threadIdx.x * nbu + blockIdx.x] = s_cnt[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(kRadixThreads) radix_scatter_kernel(
+    const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint64_t* __restrict__ kout,
+    uint32_t* __restrict__ vout, const uint32_t* __restrict__ n_pairs, uint64_t capacity, int shift,
+    const uint32_t* __restrict__ hist_scanned) {
+  __shared__ uint64_t s_keys[kRadixTile];
+  __shared__ uint32_t s_vals[kRadixTile];
+  __shared__ uint32_t s_wcnt[kRadixWarps][256];
+  __shared__ uint32_t s_run[256];    // keys of each digit seen so far, then the digit count
+  __shared__ uint32_t s_start[256];  // local start of each digit's run
+  __shared__ uint32_t s_warp[32];
+  const uint32_t P = pairs_in_use(n_pairs, capacity);
+  const size_t base = (size_t)blockIdx.x * kRadixTile;
+  if (base >= P) return;
+  const size_t nb = ((size_t)P + kRadixTile - 1) / kRadixTile;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t lt = lanemask_lt();
+  s_run[tid] = 0;
+#pragma unroll
+  for (int w = 0; w < kRadixWarps; ++w) s_wcnt[w][tid] = 0;
+  __syncthreads();
+
+  uint64_t key[kRadixItems];
+  uint32_t vv[kRadixItems];
+  uint32_t rank[kRadixItems];
+#pragma unroll
+  for (int k = 0; k < kRadixItems; ++k) {
+    const size_t idx = base + (size_t)k * kRadixThreads + tid;
+    const bool ok = idx < P;
+    key[k] = ok ? kin[idx] : 0ull;
+    vv[k] = ok ? vin[idx] : 0u;
+    const uint32_t d = ok ? (uint32_t)(key[k] >> shift) & 255u : 256u;
+    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    const uint32_t below = (uint32_t)__popc(peers & lt);
+    if (ok && below == 0) s_wcnt[warp][d] = (uint32_t)__popc(peers);
+    __syncthreads();
+    if (ok) {
+      uint32_t pre = s_run[d];
+      for (int w = 0; w < warp; ++w) pre += s_wcnt[w][d];
+      rank[k] = pre + below;
+    } else {
+      rank[k] = 0;
+    }
+    __syncthreads();
+    uint32_t add = 0;
+#pragma unroll
+    for (int w = 0; w < kRadixWarps; ++w) {
+      add += s_wcnt[w][tid];
+      s_wcnt[w][tid] = 0;
+    }
+    s_run[tid] += add;
+    __syncthreads();
+  }
+  // local digit starts
+  const uint32_t cnt = s_run[tid];
+  uint32_t tot;
+  const uint32_t start = block_exclusive_scan(cnt, tot, s_warp);
+  s_start[tid] = start;
+  __syncthreads();
+  // reorder in shared memory by (digit, rank)
+#pragma unroll
+  for (int k = 0; k < kRadixItems; ++k) {
+    const size_t idx = base + (size_t)k * kRadixThreads + tid;
+    if (idx < P) {
+      const uint32_t d = (uint32_t)(key[k] >> shift) & 255u;
+      const uint32_t pos = s_start[d] + rank[k];
+      s_keys[pos] = key[k];
+      s_vals[pos] = vv[k];
+    }
+  }
+  __syncthreads();
+  // coalesced write of each digit's run
+  const uint32_t valid = tot;
+#pragma unroll 4
+  for (int k = 0; k < kRadixItems; ++k) {
+    const uint32_t p = (uint32_t)k * kRadixThreads + tid;
+    if (p < valid) {
+      const uint64_t kk = s_keys[p];
+      const uint32_t d = (uint32_t)(kk >> shift) & 255u;
+      const size_t g = (size_t)hist_scanned[(size_t)d * nb + blockIdx.x] + (p - s_start[d]);
+      kout[g] = kk;
+      vout[g] = s_vals[p];
+    }
+  }
+  (void)lane;
+}
+
+// ------------------------------------------------------------------ ranges
+__global__ void ranges_kernel(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ n_pairs,
+                              uint64_t capacity, uint32_t* __restrict__ ranges) {
+  const uint32_t P = pairs_in_use(n_pairs, capacity);
+  for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (size_t)gridDim.x * blockDim.x) {
+    const uint32_t tile = (uint32_t)(keys[p] >> 32);
+    if (p == 0 || (uint32_t)(keys[p - 1] >> 32) != tile) ranges[2 * (size_t)tile] = (uint32_t)p;
+    if (p + 1 == P || (uint32_t)(keys[p + 1] >> 32) != tile) ranges[2 * (size_t)tile + 1] = (uint32_t)(p + 1);
+  }
+}
+
+// ---------------------------------------------------------------- planning
+inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+struct SortPlan {
+  int Tx, Ty, npass, nb_radix;
+  size_t n_items;  // views x n_pad
+  size_t off_counts, off_sums, off_keys, off_vals, off_hist, total;
+};
+
+SortPlan plan_sort(int32_t n_pad, gs_frame fr, uint64_t capacity) {
+  SortPlan p;
+  p.Tx = (fr.width + fr.tile_w - 1) / fr.tile_w;
+  p.Ty = (fr.height + fr.tile_h - 1) / fr.tile_h;
+  const uint64_t tiles = (uint64_t)fr.n_views * p.Tx * p.Ty;
+  int tile_bits = 1;
+  while ((1ull << tile_bits) < tiles) ++tile_bits;
+  p.npass = (32 + tile_bits + 7) / 8;
+  p.nb_radix = (int)((capacity + kRadixTile - 1) / kRadixTile);
+  p.n_items = (size_t)fr.n_views * n_pad;
+  const size_t hist_n = (size_t)256 * p.nb_radix;
+  const size_t sums_n = (size_t)std::max(scan_blocks(p.n_items), scan_blocks(hist_n)) + 1;
+  size_t o = 0;
+  p.off_counts = o; o += align256(p.n_items * 4);
+  p.off_sums = o;   o += align256(sums_n * 4);
+  p.off_keys = o;   o += align256(capacity * 8);
+  p.off_vals = o;   o += align256(capacity * 4);
+  p.off_hist = o;   o += align256(hist_n * 4);
+  p.total = o;
+  return p;
+}
+
+bool frame_ok(gs_frame fr) {
+  auto pow2 = [](int v) { return v > 0 && (v & (v - 1)) == 0; };
+  const int tt = fr.tile_w * fr.tile_h;
+  return fr.n_views >= 1 && fr.width >= 1 && fr.height >= 1 && pow2(fr.tile_w) && pow2(fr.tile_h) &&
+         (tt == 64 || tt == 128 || tt == 256);
+}
+
+}  // namespace
+}  // namespace gs
+
+extern "C" size_t gs_bin_sort_workspace_size(int32_t n_pad, gs_frame frame, uint64_t capacity) {
+  if (n_pad < 0 || !gs::frame_ok(frame)) return 0;
+  return gs::plan_sort(n_pad, frame, capacity).total;
+}
+
+extern "C" gs_status gs_bin_sort(const gs_projected* proj, int32_t n_pad, gs_frame frame, void* workspace,
+                                 size_t workspace_bytes, gs_sorted* out, int32_t* status, void* stream) {
+  using namespace gs;
+  GS_REQUIRE(proj && out && proj->rec, "gs_bin_sort: null argument");
+  GS_REQUIRE(out->keys && out->vals && out->ranges && out->n_pairs, "gs_bin_sort: null output buffer");
+  GS_REQUIRE(n_pad >= 0 && n_pad % 4 == 0, "gs_bin_sort: bad n_pad=%d", n_pad);
+  GS_REQUIRE(frame_ok(frame), "gs_bin_sort: bad frame (tile %dx%d)", frame.tile_w, frame.tile_h);
+  GS_REQUIRE(out->capacity > 0 && out->capacity < (1ull << 32), "gs_bin_sort: capacity must be in [1, 2^32)");
+  const SortPlan p = plan_sort(n_pad, frame, out->capacity);
+  GS_REQUIRE(workspace && workspace_bytes >= p.total, "gs_bin_sort: workspace needs %zu bytes, got %zu", p.total,
+             workspace_bytes);
+  cudaStream_t st = (cudaStream_t)stream;
+  char* ws = (char*)workspace;
+  uint32_t* counts = (uint32_t*)(ws + p.off_counts);
+  uint32_t* sums = (uint32_t*)(ws + p.off_sums);
+  uint64_t* keys_b = (uint64_t*)(ws + p.off_keys);
+  uint32_t* vals_b = (uint32_t*)(ws + p.off_vals);
+  uint32_t* hist = (uint32_t*)(ws + p.off_hist);
+  const float4* rec = reinterpret_cast<const float4*>(proj->rec);
+  const uint64_t T = (uint64_t)p.Tx * p.Ty;
+
+  if (cudaMemsetAsync(out->ranges, 0, (size_t)frame.n_views * T * 2 * sizeof(uint32_t), st) != cudaSuccess ||
+      cudaMemsetAsync(out->n_pairs, 0, sizeof(uint32_t), st) != cudaSuccess)
+    return check_launch("gs_bin_sort: memset");
+  if (p.n_items == 0) return GS_OK;
+  const int eb = (int)((p.n_items + 255) / 256);
+  count_kernel<<<eb, 256, 0, st>>>(rec, n_pad, frame, p.Tx, p.Ty, counts);
+  exclusive_scan(counts, counts, p.n_items, nullptr, 0, sums, out->n_pairs, out->capacity, status, st);
+  // the last pass must land in the caller's arrays
+  uint64_t* kbuf[2] = {out->keys, keys_b};
+  uint32_t* vbuf[2] = {out->vals, vals_b};
+  int cur = (p.npass % 2 == 0) ? 0 : 1;
+  emit_kernel<<<eb, 256, 0, st>>>(rec, n_pad, frame, p.Tx, p.Ty, counts, out->capacity, kbuf[cur], vbuf[cur]);
+  const size_t hist_n = (size_t)256 * p.nb_radix;
+  for (int pass = 0; pass < p.npass; ++pass) {
+    const int shift = 8 * pass;
+    radix_hist_kernel<<<p.nb_radix, kRadixThreads, 0, st>>>(kbuf[cur], out->n_pairs, out->capacity, shift, hist);
+    exclusive_scan(hist, hist, hist_n, out->n_pairs, out->capacity, sums, nullptr, 0, nullptr, st);
+    radix_scatter_kernel<<<p.nb_radix, kRadixThreads, 0, st>>>(kbuf[cur], vbuf[cur], kbuf[cur ^ 1], vbuf[cur ^ 1],
+                                                               out->n_pairs, out->capacity, shift, hist);
+    cur ^= 1;
+  }
+  const int rb = (int)std::min<uint64_t>((out->capacity + 255) / 256, 152 * 16);
+  ranges_kernel<<<rb, 256, 0, st>>>(out->keys, out->n_pairs, out->capacity, out->ranges);
+  return check_launch("gs_bin_sort");
+}

@@ -1,0 +1,337 @@
+// Shared device helpers of the gs3dtr CUDA library (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdio>
+#include <type_traits>
+
+#include "gs3dtr.h"
+
+namespace gs {
+
+// ------------------------------------------------------------ constants
+// Blend thresholds of the 3DGS rasteriser the paper builds on (Sec. 3.1).
+constexpr float kAlphaMin = 1.0f / 255.0f;
+constexpr float kAlphaMax = 0.99f;
+constexpr float kTMin = 1e-4f;
+constexpr float kDilation = 0.3f;    // added to the 2-D covariance diagonal
+constexpr float kSlopeClamp = 1.3f;  // image-plane slope limit, x half field of view
+constexpr int kRowSH = 11;
+constexpr uint64_t kGolden = 0x9E3779B97F4A7C15ULL;
+constexpr int kMaxViews = 64;
+
+// Real SH normalisations, sqrt((2l+1)/(4pi) (l-m)!/(l+m)!) times the fixed
+// factor of each Cartesian polynomial (3DGS sign convention).
+constexpr float kY0 = 0.28209479177387814f;   // 1/(2 sqrt(pi))
+constexpr float kY1 = 0.48860251190291992f;   // sqrt(3/(4pi))
+constexpr float kY2a = 1.0925484305920792f;   // sqrt(15/pi)/2
+constexpr float kY2b = 0.31539156525252005f;  // sqrt(5/pi)/4
+constexpr float kY2c = 0.54627421529603959f;  // sqrt(15/pi)/4
+constexpr float kY3a = 0.59004358992664352f;  // sqrt(35/(2pi))/4
+constexpr float kY3b = 2.8906114426405538f;   // sqrt(105/pi)/2
+constexpr float kY3c = 0.45704579946446572f;  // sqrt(21/(2pi))/4
+constexpr float kY3d = 0.37317633259011540f;  // sqrt(7/pi)/4
+constexpr float kY3e = 1.4453057213202769f;   // sqrt(105/pi)/4
+
+inline __host__ __device__ int n_coeffs(int deg) { return (deg + 1) * (deg + 1); }
+inline __host__ __device__ int n_rows(int deg) { return kRowSH + 3 * n_coeffs(deg); }
+
+// ------------------------------------------------------------ RNG
+// SplitMix64 (Steele, Lea & Flood 2014): Weyl increment, then the finaliser
+// with shifts 30, 27, 31.
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+  uint64_t z = x + kGolden;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+// true where probe k's entry j at step t is -1
+__device__ __forceinline__ bool probe_negative(uint64_t seed, int64_t t, int k, uint64_t j) {
+  return (splitmix64(seed ^ ((uint64_t)t * kGolden) ^ ((uint64_t)k << 56) ^ j) >> 63) != 0;
+}
+
+// ------------------------------------------------ forward-mode dual numbers
+// Value plus N tangents; used to push the Rademacher directions through the
+// projection (the "forward-mode AD" half of the Hessian-vector product).
+template <int N>
+struct Dn {
+  float v;
+  float d[N];
+};
+
+template <class S>
+struct is_dual : std::false_type {};
+template <int N>
+struct is_dual<Dn<N>> : std::true_type {};
+
+__device__ __forceinline__ float val(float x) { return x; }
+template <int N>
+__device__ __forceinline__ float val(const Dn<N>& x) { return x.v; }
+
+template <int N>
+__device__ __forceinline__ Dn<N> cst(float v) {
+  Dn<N> r;
+  r.v = v;
+#pragma unroll
+  for (int k = 0; k < N; ++k) r.d[k] = 0.f;
+  return r;
+}
+template <int N>
+__device__ __forceinline__ Dn<N> operator+(const Dn<N>& a, const Dn<N>& b) {
+  Dn<N> r;
+  r.v = a.v + b.v;
+#pragma unroll
+  for (int k = 0; k < N; ++k) r.d[k] = a.d[k] + b.d[k];
+  return r;
+}
+template <int N>
+__device__ __forceinline__ Dn<N> operator-(const Dn<N>& a, const Dn<N>& b) {
+  Dn<N> r;
+  r.v = a.v - b.v;
+#pragma unroll
+  for (int k = 0; k < N; ++k) r.d[k] = a.d[k] - b.d[k];
+  return r;
+}
+template <int N>
+__device__ __forceinline__ Dn<N> operator-(const Dn<N>& a) {
+  Dn<N> r;
+  r.v = -a.v;
+#pragma unroll
+  for (int k = 0; k < N; ++k) r.d[k] = -a.d[k];
+  return r;
+}
+template <int N>
+__device__ __forceinline__ Dn<N> operator*(const Dn<N>& a, const Dn<N>& b) {
+  Dn<N> r;
+  r.v = a.v * b.v;
+#pragma unroll
+  for (int k = 0; k < N; ++k) r.d[k] = a.d[k] * b.v + a.v * b.d[k];
+  return r;
+}
+template <int N>
+__device__ __forceinline__ Dn<N> operator/(const Dn<N>& a, const Dn<N>& b) {
+  Dn<N> r;
+  float ib = 1.0f / b.v;
+  r.v = a.v * ib;
+#pragma unroll
+  for (int k = 0; k < N; ++k) r.d[k] = (a.d[k] - r.v * b.d[k]) * ib;
+  return r;
+}
+template <int N>
+__device__ __forceinline__ Dn<N> operator+(const Dn<N>& a, float b) {
+  Dn<N> r = a;
+  r.v += b;
+  return r;
+}
+template <int N>
+__device__ __forceinline__ Dn<N> operator+(float b, const Dn<N>& a) { return a + b; }
+template <int N>
+__device__ __forceinline__ Dn<N> operator-(const Dn<N>& a, float b) {
+  Dn<N> r = a;
+  r.v -= b;
+  return r;
+}
+template <int N>
+__device__ __forceinline__ Dn<N> operator-(float b, const Dn<N>& a) {
+  Dn<N> r = -a;
+  r.v += b;
+  return r;
+}
+template <int N>
+__device__ __forceinline__ Dn<N> operator*(const Dn<N>& a, float b) {
+  Dn<N> r;
+  r.v = a.v * b;
+#pragma unroll
+  for (int k = 0; k < N; ++k) r.d[k] = a.d[k] * b;
+  return r;
+}
+template <int N>
+__device__ __forceinline__ Dn<N> operator*(float b, const Dn<N>& a) { return a * b; }
+template <int N>
+__device__ __forceinline__ Dn<N> operator/(const Dn<N>& a, float b) { return a * (1.0f / b); }
+template <int N>
+__device__ __forceinline__ Dn<N> operator/(float a, const Dn<N>& b) { return cst<N>(a) / b; }
+
+__device__ __forceinline__ float sexp(float x) { return expf(x); }
+__device__ __forceinline__ float ssqrt(float x) { return sqrtf(x); }
+template <int N>
+__device__ __forceinline__ Dn<N> sexp(const Dn<N>& a) {
+  Dn<N> r;
+  r.v = expf(a.v);
+#pragma unroll
+  for (int k = 0; k < N; ++k) r.d[k] = r.v * a.d[k];
+  return r;
+}
+template <int N>
+__device__ __forceinline__ Dn<N> ssqrt(const Dn<N>& a) {
+  Dn<N> r;
+  r.v = sqrtf(a.v);
+  float h = 0.5f / r.v;
+#pragma unroll
+  for (int k = 0; k < N; ++k) r.d[k] = a.d[k] * h;
+  return r;
+}
+
+template <class S>
+__device__ __forceinline__ S constant(float v) {
+  if constexpr (is_dual<S>::value) {
+    return cst<sizeof(S::d) / sizeof(float)>(v);
+  } else {
+    return v;
+  }
+}
+
+// ------------------------------------------------------------ SH basis
+// Real spherical harmonics up to degree DEG at unit direction (x, y, z).
+template <int DEG, class S>
+__device__ __forceinline__ void sh_basis(const S& x, const S& y, const S& z, S* Y) {
+  Y[0] = constant<S>(kY0);
+  if constexpr (DEG >= 1) {
+    Y[1] = -kY1 * y;
+    Y[2] = kY1 * z;
+    Y[3] = -kY1 * x;
+  }
+  if constexpr (DEG >= 2) {
+    S xx = x * x, yy = y * y, zz = z * z;
+    Y[4] = kY2a * (x * y);
+    Y[5] = -kY2a * (y * z);
+    Y[6] = kY2b * (2.0f * zz - xx - yy);
+    Y[7] = -kY2a * (x * z);
+    Y[8] = kY2c * (xx - yy);
+    if constexpr (DEG >= 3) {
+      Y[9] = -kY3a * y * (3.0f * xx - yy);
+      Y[10] = kY3b * (x * y * z);
+      Y[11] = -kY3c * y * (4.0f * zz - xx - yy);
+      Y[12] = kY3d * z * (2.0f * zz - 3.0f * xx - 3.0f * yy);
+      Y[13] = -kY3c * x * (4.0f * zz - xx - yy);
+      Y[14] = kY3e * z * (xx - yy);
+      Y[15] = -kY3a * x * (xx - 3.0f * yy);
+    }
+  }
+}
+
+// sum_k w_k grad Y_k at (x, y, z), treating x, y, z as independent.
+template <int DEG>
+__device__ __forceinline__ void sh_basis_grad(float x, float y, float z, const float* w, float g[3]) {
+  g[0] = g[1] = g[2] = 0.f;
+  if constexpr (DEG >= 1) {
+    g[1] += -kY1 * w[1];
+    g[2] += kY1 * w[2];
+    g[0] += -kY1 * w[3];
+  }
+  if constexpr (DEG >= 2) {
+    g[0] += kY2a * y * w[4];
+    g[1] += kY2a * x * w[4];
+    g[1] += -kY2a * z * w[5];
+    g[2] += -kY2a * y * w[5];
+    g[0] += -2.f * kY2b * x * w[6];
+    g[1] += -2.f * kY2b * y * w[6];
+    g[2] += 4.f * kY2b * z * w[6];
+    g[0] += -kY2a * z * w[7];
+    g[2] += -kY2a * x * w[7];
+    g[0] += 2.f * kY2c * x * w[8];
+    g[1] += -2.f * kY2c * y * w[8];
+    if constexpr (DEG >= 3) {
+      float xx = x * x, yy = y * y, zz = z * z;
+      g[0] += -6.f * kY3a * x * y * w[9];
+      g[1] += -kY3a * (3.f * xx - 3.f * yy) * w[9];
+      g[0] += kY3b * y * z * w[10];
+      g[1] += kY3b * x * z * w[10];
+      g[2] += kY3b * x * y * w[10];
+      g[0] += 2.f * kY3c * x * y * w[11];
+      g[1] += -kY3c * (4.f * zz - xx - 3.f * yy) * w[11];
+      g[2] += -8.f * kY3c * y * z * w[11];
+      g[0] += -6.f * kY3d * x * z * w[12];
+      g[1] += -6.f * kY3d * y * z * w[12];
+      g[2] += kY3d * (6.f * zz - 3.f * xx - 3.f * yy) * w[12];
+      g[0] += -kY3c * (4.f * zz - 3.f * xx - yy) * w[13];
+      g[1] += 2.f * kY3c * x * y * w[13];
+      g[2] += -8.f * kY3c * x * z * w[13];
+      g[0] += 2.f * kY3e * x * z * w[14];
+      g[1] += -2.f * kY3e * y * z * w[14];
+      g[2] += kY3e * (xx - yy) * w[14];
+      g[0] += -kY3a * (3.f * xx - 3.f * yy) * w[15];
+      g[1] += 6.f * kY3a * x * y * w[15];
+    }
+  }
+}
+
+// ---------------------------------------------------------- tile rectangle
+// [x0, x1) x [y0, y1) of a splat, decided in FP32 with one rounding per step:
+//   x0 = clamp(floor((mx - r)/tw), 0, Tx),  x1 = clamp(floor((mx + (r + tw - 1))/tw), 0, Tx).
+__device__ __forceinline__ int clamp_floor(float q, int hi) {
+  float f = floorf(q);
+  if (!(f > 0.0f)) return 0;  // NaN -> 0
+  if (f > (float)hi) return hi;
+  return (int)f;
+}
+__device__ __forceinline__ void tile_rect(float mx, float my, int r, int tw, int th, int Tx, int Ty, int& x0,
+                                          int& x1, int& y0, int& y1) {
+  float lox = __fsub_rn(mx, (float)r), hix = __fadd_rn(mx, (float)(r + tw - 1));
+  float loy = __fsub_rn(my, (float)r), hiy = __fadd_rn(my, (float)(r + th - 1));
+  x0 = clamp_floor(__fdiv_rn(lox, (float)tw), Tx);
+  x1 = clamp_floor(__fdiv_rn(hix, (float)tw), Tx);
+  y0 = clamp_floor(__fdiv_rn(loy, (float)th), Ty);
+  y1 = clamp_floor(__fdiv_rn(hiy, (float)th), Ty);
+}
+
+// ------------------------------------------------- async copies (TMA bulk)
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+// One non-multicast bulk copy global -> this CTA's shared memory, completing on bar.
+// dst, src and bytes must be multiples of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for phase `parity` of bar.  Returns false (and raises
+// GS_FLAG_TIMEOUT) if the phase did not complete within the limit.
+constexpr uint32_t kWaitLimit = 1u << 22;
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int32_t* status) {
+  for (uint32_t it = 0; it < kWaitLimit; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  if (status) atomicOr(status, GS_FLAG_TIMEOUT);
+  return false;
+}
+
+// ---------------------------------------------------------- host errors
+void set_error(const char* fmt, ...);
+gs_status check_launch(const char* what);
+
+}  // namespace gs
+
+#define GS_REQUIRE(cond, ...)          \
+  do {                                 \
+    if (!(cond)) {                     \
+      gs::set_error(__VA_ARGS__);      \
+      return GS_ERR_INVALID_ARG;       \
+    }                                  \
+  } while (0)

@@ -1,0 +1,756 @@
+// Rasteriser forward and reverse passes of arXiv 2602.00395:
+//
+//   gs_raster_fwd  front-to-back alpha blending per pixel (Sec. 3.1), with the
+//                  forward-mode tangents J z_k of the Hutchinson probes fused in
+//                  (Sec. 4.1; the paper's forward-mode AD of the rasteriser, Sec. 5)
+//   gs_raster_bwd  reverse pass for the gradient g = (1/m) J^T F (Sec. 4.1) and,
+//                  in the same sweep, the Gauss-Newton products J^T diag(w) J z_k
+//   gs_hvp_diag    the Gauss-Newton products alone
+//
+// One CTA renders one tile of one view, one thread per pixel.  The tile's splat
+// records are staged through shared memory in batches of one record per thread,
+// each record moved by a 48-byte TMA bulk copy (cp.async.bulk, no multicast)
+// completing on an mbarrier, double-buffered so that the next batch lands while
+// the current one is blended.  The reverse pass walks the list back to front,
+// recovers T_i = T_{i+1} / (1 - a_i) from the final transmittance (nothing per
+// pair is stored), and merges each splat's 9 x streams partial derivatives over
+// the warp with a reduce-scatter butterfly before one global atomic per value.
+// The projection's reverse pass (2-D cotangents -> 11 + 3K parameter rows) runs
+// one thread per (Gaussian, stream) and sums over the views.
+#include "common.cuh"
+
+namespace gs {
+namespace {
+
+struct alignas(16) Rec {
+  float4 a;  // mx, my, A, B
+  float4 b;  // C, opacity, r, g
+  float4 c;  // b, depth, radius bits, unused
+};
+static_assert(sizeof(Rec) == 48, "record size");
+
+// Power and alpha of a splat at a pixel with a fixed rounding sequence, so that
+// the forward and reverse kernels take identical decisions.
+__device__ __forceinline__ float splat_power(const Rec& r, float dx, float dy) {
+  const float q = __fmaf_rn(r.b.x, __fmul_rn(dy, dy), __fmul_rn(r.a.z, __fmul_rn(dx, dx)));
+  return __fmaf_rn(-0.5f, q, -__fmul_rn(r.a.w, __fmul_rn(dx, dy)));
+}
+
+// Stage batch b of a tile list into buffer (b & 1): one bulk copy per record
+// (and per tangent record), all completing on the buffer's mbarrier.
+template <int NT>
+__device__ __forceinline__ void stage_batch(int b, int nthr, uint32_t start, int n, int view, int n_pad,
+                                            const uint32_t* __restrict__ vals, const float4* __restrict__ rec,
+                                            const float4* __restrict__ tan, Rec* buf, Rec* tbuf, uint32_t* s_idx,
+                                            uint64_t* bars) {
+  const int bi = b & 1;
+  const int cnt = min(nthr, n - b * nthr);
+  const int tid = threadIdx.x;
+  if (tid == 0) mbar_arrive_expect_tx(&bars[bi], (uint32_t)(cnt * (int)sizeof(Rec) * (1 + NT)));
+  if (tid < cnt) {
+    const uint32_t gi = vals[start + (uint32_t)(b * nthr + tid)];
+    if (s_idx) s_idx[bi * nthr + tid] = gi;
+    fence_proxy_async();
+    bulk_g2s(&buf[bi * nthr + tid], rec + 3 * ((size_t)view * n_pad + gi), sizeof(Rec), &bars[bi]);
+#pragma unroll
+    for (int k = 0; k < NT; ++k)
+      bulk_g2s(&tbuf[(bi * NT + k) * nthr + tid], tan + 3 * (((size_t)view * NT + k) * n_pad + gi), sizeof(Rec),
+               &bars[bi]);
+  }
+}
+
+// ------------------------------------------------------------------ forward
+template <int NU>
+__global__ void __launch_bounds__(256) raster_fwd_kernel(const float4* __restrict__ rec, const float4* __restrict__ tan,
+                                                         const uint32_t* __restrict__ vals,
+                                                         const uint32_t* __restrict__ ranges, int n_pad, gs_frame fr,
+                                                         int Tx, int T, float* __restrict__ image,
+                                                         float* __restrict__ final_T, uint32_t* __restrict__ n_contrib,
+                                                         float* __restrict__ image_tan, int32_t* status) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int nthr = blockDim.x;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
+  Rec* buf = reinterpret_cast<Rec*>(smem + 16);
+  Rec* tbuf = buf + 2 * nthr;
+  const int tid = threadIdx.x;
+  const int view = blockIdx.x / T, tile = blockIdx.x - view * T;
+  const int ty = tile / Tx, tx = tile - ty * Tx;
+  const int lx = tid & (fr.tile_w - 1), ly = tid / fr.tile_w;
+  const int px = tx * fr.tile_w + lx, py = ty * fr.tile_h + ly;
+  const bool inside = px < fr.width && py < fr.height;
+  const float pxc = (float)px + 0.5f, pyc = (float)py + 0.5f;
+  const size_t tslot = 2 * ((size_t)view * T + tile);
+  const uint32_t start = ranges[tslot], end = ranges[tslot + 1];
+  const int n = (int)(end - start);
+  if (tid == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  float C0 = 0.f, C1 = 0.f, C2 = 0.f, Tr = 1.f;
+  float Cd[NU > 0 ? NU : 1][3], Td[NU > 0 ? NU : 1];
+#pragma unroll
+  for (int k = 0; k < NU; ++k) Cd[k][0] = Cd[k][1] = Cd[k][2] = Td[k] = 0.f;
+  uint32_t last = 0;
+  bool done = !inside;
+  const int nb = (n + nthr - 1) / nthr;
+  if (nb > 0) stage_batch<NU>(0, nthr, start, n, view, n_pad, vals, rec, tan, buf, tbuf, nullptr, bars);
+  for (int b = 0; b < nb; ++b) {
+    if (b + 1 < nb) stage_batch<NU>(b + 1, nthr, start, n, view, n_pad, vals, rec, tan, buf, tbuf, nullptr, bars);
+    const int bi = b & 1;
+    const bool ok = mbar_wait_bounded(&bars[bi], (uint32_t)((b >> 1) & 1), status);
+    const int cnt = min(nthr, n - b * nthr);
+    if (!ok) done = true;
+    if (!done) {
+      const Rec* bb = buf + bi * nthr;
+      for (int j = 0; j < cnt; ++j) {
+        const Rec r = bb[j];
+        const float dx = __fsub_rn(r.a.x, pxc), dy = __fsub_rn(r.a.y, pyc);
+        const float power = splat_power(r, dx, dy);
+        if (power > 0.f) continue;
+        const float G = __expf(power);
+        const float oG = __fmul_rn(r.b.y, G);
+        const float alpha = fminf(kAlphaMax, oG);
+        if (alpha < kAlphaMin) continue;
+        const float Tn = Tr * (1.f - alpha);
+        if (Tn < kTMin) {
+          done = true;
+          break;
+        }
+        const float w = alpha * Tr;
+        if constexpr (NU > 0) {
+          const bool capped = oG > kAlphaMax;
+#pragma unroll
+          for (int k = 0; k < NU; ++k) {
+            const Rec t = tbuf[(bi * NU + k) * nthr + j];
+            const float pd = -0.5f * (t.a.z * dx * dx + 2.f * r.a.z * dx * t.a.x + t.b.x * dy * dy +
+                                      2.f * r.b.x * dy * t.a.y) -
+                             t.a.w * dx * dy - r.a.w * (t.a.x * dy + dx * t.a.y);
+            const float ad = capped ? 0.f : (t.b.y * G + alpha * pd);
+            Cd[k][0] += (t.b.z * alpha + r.b.z * ad) * Tr + r.b.z * alpha * Td[k];
+            Cd[k][1] += (t.b.w * alpha + r.b.w * ad) * Tr + r.b.w * alpha * Td[k];
+            Cd[k][2] += (t.c.x * alpha + r.c.x * ad) * Tr + r.c.x * alpha * Td[k];
+            Td[k] = Td[k] * (1.f - alpha) - Tr * ad;
+          }
+        }
+        C0 += r.b.z * w;
+        C1 += r.b.w * w;
+        C2 += r.c.x * w;
+        Tr = Tn;
+        last = (uint32_t)(b * nthr + j + 1);
+      }
+    }
+    if (__syncthreads_count(done) == nthr) {
+      if (b + 1 < nb) mbar_wait_bounded(&bars[(b + 1) & 1], (uint32_t)(((b + 1) >> 1) & 1), status);
+      break;
+    }
+  }
+  if (!inside) return;
+  const size_t HW = (size_t)fr.width * fr.height;
+  const size_t pix = (size_t)py * fr.width + px;
+  image[((size_t)view * 3 + 0) * HW + pix] = C0;
+  image[((size_t)view * 3 + 1) * HW + pix] = C1;
+  image[((size_t)view * 3 + 2) * HW + pix] = C2;
+  final_T[(size_t)view * HW + pix] = Tr;
+  n_contrib[(size_t)view * HW + pix] = last;
+  if constexpr (NU > 0) {
+#pragma unroll
+    for (int k = 0; k < NU; ++k)
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch)
+        image_tan[(((size_t)k * fr.n_views + view) * 3 + ch) * HW + pix] = Cd[k][ch];
+  }
+}
+
+// ------------------------------------------------------------------ reverse
+// Lane L ends with the warp-wide sum of v[L] (v has 32 slots).
+__device__ __forceinline__ float warp_reduce_scatter32(float (&v)[32]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < o; ++i) {
+      const float send = up ? v[i] : v[i + o];
+      const float keep = up ? v[i + o] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+  return v[0];
+}
+// Lane L (and L ^ 16) ends with the warp-wide sum of v[L & 15] (v has 16 slots).
+__device__ __forceinline__ float warp_reduce_scatter16(float (&v)[32]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], 16);
+#pragma unroll
+  for (int o = 8; o >= 1; o >>= 1) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < o; ++i) {
+      const float send = up ? v[i] : v[i + o];
+      const float keep = up ? v[i + o] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+  return v[0];
+}
+
+template <int NU, bool GRAD>
+__global__ void __launch_bounds__(256) raster_bwd_kernel(
+    const float4* __restrict__ rec, const uint32_t* __restrict__ vals, const uint32_t* __restrict__ ranges,
+    int n_pad, gs_frame fr, int Tx, int T, const float* __restrict__ image, const float* __restrict__ target,
+    const float* __restrict__ final_T, const uint32_t* __restrict__ n_contrib, const float* __restrict__ image_tan,
+    int loss_kind, float gn_floor, float inv_m, float* __restrict__ cot, float* __restrict__ loss_out,
+    int32_t* status) {
+  constexpr int S = (GRAD ? 1 : 0) + NU;  // cotangent streams
+  constexpr int NV = 9 * S;               // values per splat
+  static_assert(NV <= 32, "streams");
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int nthr = blockDim.x;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
+  Rec* buf = reinterpret_cast<Rec*>(smem + 16);
+  uint32_t* s_idx = reinterpret_cast<uint32_t*>(buf + 2 * nthr);
+  __shared__ uint32_t s_max;
+  __shared__ float s_loss[8];
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int view = blockIdx.x / T, tile = blockIdx.x - view * T;
+  const int ty = tile / Tx, tx = tile - ty * Tx;
+  const int lx = tid & (fr.tile_w - 1), ly = tid / fr.tile_w;
+  const int px = tx * fr.tile_w + lx, py = ty * fr.tile_h + ly;
+  const bool inside = px < fr.width && py < fr.height;
+  const float pxc = (float)px + 0.5f, pyc = (float)py + 0.5f;
+  const size_t tslot = 2 * ((size_t)view * T + tile);
+  const uint32_t start = ranges[tslot], list_len = ranges[tslot + 1] - start;
+  const size_t HW = (size_t)fr.width * fr.height;
+  const size_t pix = (size_t)py * fr.width + px;
+
+  // per-pixel cotangents dL/dC of each stream and the loss
+  float w[S > 0 ? S : 1][3];
+  float Tr = 0.f, lossp = 0.f;
+  uint32_t nc = 0;
+  if (inside) {
+    Tr = final_T[(size_t)view * HW + pix];
+    nc = n_contrib[(size_t)view * HW + pix];
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+      const size_t at = ((size_t)view * 3 + ch) * HW + pix;
+      const float r = image[at] - target[at];
+      const float ar = fabsf(r);
+      float lam;
+      if (loss_kind == GS_LOSS_L1) {
+        lossp += 0.5f * inv_m * ar;
+        lam = 0.25f / fmaxf(ar, gn_floor);
+      } else {
+        lossp += 0.5f * inv_m * r * r;
+        lam = 1.f;
+      }
+      if constexpr (GRAD) w[0][ch] = (loss_kind == GS_LOSS_L1) ? (0.5f * inv_m) * ((r > 0.f) - (r < 0.f)) : inv_m * r;
+#pragma unroll
+      for (int k = 0; k < NU; ++k)
+        w[(GRAD ? 1 : 0) + k][ch] = inv_m * lam * image_tan[(((size_t)k * fr.n_views + view) * 3 + ch) * HW + pix];
+    }
+  } else {
+#pragma unroll
+    for (int s = 0; s < S; ++s) w[s][0] = w[s][1] = w[s][2] = 0.f;
+  }
+  if (tid == 0) {
+    s_max = 0;
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (nc) atomicMax(&s_max, nc);
+  // objective: warp then block reduction, one atomic per CTA
+  if (loss_out) {
+    float lsum = lossp;
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+    if (lane == 0) s_loss[tid >> 5] = lsum;
+  }
+  __syncthreads();
+  if (loss_out && tid == 0) {
+    float tot = 0.f;
+    for (int k = 0; k < (nthr >> 5); ++k) tot += s_loss[k];
+    atomicAdd(loss_out, tot);
+  }
+  const int n = (int)min(s_max, list_len);  // n_contrib never exceeds the tile's list
+  const int nb = (n + nthr - 1) / nthr;
+  float suf0 = 0.f, suf1 = 0.f, suf2 = 0.f;
+  if (nb > 0)
+    stage_batch<0>(nb - 1, nthr, start, n, view, n_pad, vals, rec, nullptr, buf, nullptr, s_idx, bars);
+  __syncthreads();  // publish s_idx of the first batch
+  int uses = 0;  // batches waited on so far, for the barrier parity
+  for (int b = nb - 1; b >= 0; --b) {
+    if (b - 1 >= 0)
+      stage_batch<0>(b - 1, nthr, start, n, view, n_pad, vals, rec, nullptr, buf, nullptr, s_idx, bars);
+    const int bi = b & 1;
+    // batch b is the (nb - 1 - b)-th use overall; buffer bi has been used
+    // floor((nb - 1 - b) / 2) times before (buffers alternate)
+    // block-uniform, since the warps below shuffle with full masks
+    const bool ok = __syncthreads_and(mbar_wait_bounded(&bars[bi], (uint32_t)((uses >> 1) & 1), status)) != 0;
+    ++uses;
+    const int cnt = min(nthr, n - b * nthr);
+    if (ok) {
+      const Rec* bb = buf + bi * nthr;
+      for (int j = cnt - 1; j >= 0; --j) {
+        const uint32_t pos = (uint32_t)(b * nthr + j);
+        const Rec r = bb[j];
+        const float dx = __fsub_rn(r.a.x, pxc), dy = __fsub_rn(r.a.y, pyc);
+        bool on = pos < nc;
+        float power = 0.f, G = 0.f, alpha = 0.f, oG = 0.f;
+        if (on) {
+          power = splat_power(r, dx, dy);
+          on = power <= 0.f;
+        }
+        if (on) {
+          G = __expf(power);
+          oG = __fmul_rn(r.b.y, G);
+          alpha = fminf(kAlphaMax, oG);
+          on = alpha >= kAlphaMin;
+        }
+        if (!__any_sync(0xffffffffu, on)) continue;
+        float v[32];
+#pragma unroll
+        for (int q = 0; q < 32; ++q) v[q] = 0.f;
+        if (on) {
+          const float om = 1.f - alpha;
+          const float Ti = Tr / om;
+          const float rgb0 = r.b.z, rgb1 = r.b.w, rgb2 = r.c.x;
+          const float da0 = rgb0 * Ti - suf0 / om;
+          const float da1 = rgb1 * Ti - suf1 / om;
+          const float da2 = rgb2 * Ti - suf2 / om;
+          const float aT = alpha * Ti;
+          suf0 += rgb0 * aT;
+          suf1 += rgb1 * aT;
+          suf2 += rgb2 * aT;
+          Tr = Ti;
+          const bool capped = oG > kAlphaMax;
+#pragma unroll
+          for (int s = 0; s < S; ++s) {
+            const float ga = w[s][0] * da0 + w[s][1] * da1 + w[s][2] * da2;
+            const float gp = capped ? 0.f : ga * alpha;
+            v[9 * s + 0] = -(r.a.z * dx + r.a.w * dy) * gp;
+            v[9 * s + 1] = -(r.b.x * dy + r.a.w * dx) * gp;
+            v[9 * s + 2] = -0.5f * dx * dx * gp;
+            v[9 * s + 3] = -dx * dy * gp;
+            v[9 * s + 4] = -0.5f * dy * dy * gp;
+            v[9 * s + 5] = capped ? 0.f : ga * G;
+            v[9 * s + 6] = w[s][0] * aT;
+            v[9 * s + 7] = w[s][1] * aT;
+            v[9 * s + 8] = w[s][2] * aT;
+          }
+        }
+        const uint32_t gi = s_idx[bi * nthr + j];
+        float* dst = cot + ((size_t)view * n_pad + gi) * NV;
+        if constexpr (NV <= 16) {
+          const float mine = warp_reduce_scatter16(v);
+          if (lane < NV && mine != 0.f) atomicAdd(dst + lane, mine);
+        } else {
+          const float mine = warp_reduce_scatter32(v);
+          if (lane < NV && mine != 0.f) atomicAdd(dst + lane, mine);
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------ projection reverse pass
+// Reverse pass of the EWA projection and SH colour for one Gaussian, summed over
+// views; thread (i, s) handles cotangent stream s.  The chain rule, written out:
+//   conic = Sigma'^-1:   dA/da = -c^2/det^2, dA/db = 2bc/det^2, dA/dc = 1/det - ac/det^2,
+//                        dB/da = bc/det^2, dB/db = -1/det - 2b^2/det^2, dB/dc = ab/det^2,
+//                        dC/da = 1/det - ac/det^2, dC/db = 2ab/det^2, dC/dc = -a^2/det^2
+//   Sigma' = J Sc J^T:   dSc = J^T Gs J, dJ = 2 Gs J Sc, Gs = [[ga, gb/2], [gb/2, gc]]
+//   J(t):                slope clamp cuts the t_x (t_y) path, J02 = -fx uc / tz
+//   Sc = W Sigma W^T:    dSigma = W^T dSc W;   mean2D(t) and t = W mu + t_w
+//   Sigma = M M^T:       dM = 2 dSigma M, M = R diag(s), s = exp(log s)
+//   R(q / |q|):          dq = (dqn - qn (qn . dqn)) / |q|
+//   colour:              dSH_k = Y_k dc (0 where clamped), dmu += P_perp grad_Y . (sum sh dc) / |d|
+template <int DEG, int NU, bool GRAD>
+__global__ void __launch_bounds__(128) project_bwd_kernel(const float* __restrict__ P, int n, int n_pad,
+                                                          const gs_camera* __restrict__ cams, gs_frame fr,
+                                                          const float* __restrict__ cot, uint64_t seed, int64_t step,
+                                                          float* __restrict__ grad, float* __restrict__ hz) {
+  constexpr int S = (GRAD ? 1 : 0) + NU;
+  constexpr int NV = 9 * S;
+  constexpr int K = (DEG + 1) * (DEG + 1);
+  constexpr int ROWS = kRowSH + 3 * K;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int s = blockIdx.y;
+  if (i >= n) return;
+  auto ld = [&](int r) { return __ldg(P + (size_t)r * n_pad + i); };
+  const float mu[3] = {ld(0), ld(1), ld(2)};
+  float qx = ld(6), qy = ld(7), qz = ld(8), qw = ld(9);
+  const float qlen = sqrtf(qx * qx + qy * qy + qz * qz + qw * qw);
+  qx /= qlen; qy /= qlen; qz /= qlen; qw /= qlen;
+  float R[3][3];
+  R[0][0] = 1.f - 2.f * (qy * qy + qz * qz);
+  R[0][1] = 2.f * (qx * qy - qw * qz);
+  R[0][2] = 2.f * (qx * qz + qw * qy);
+  R[1][0] = 2.f * (qx * qy + qw * qz);
+  R[1][1] = 1.f - 2.f * (qz * qz + qx * qx);
+  R[1][2] = 2.f * (qy * qz - qw * qx);
+  R[2][0] = 2.f * (qx * qz - qw * qy);
+  R[2][1] = 2.f * (qy * qz + qw * qx);
+  R[2][2] = 1.f - 2.f * (qx * qx + qy * qy);
+  float sc[3], M[3][3], Sg[3][3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) sc[a] = expf(ld(3 + a));
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) M[a][b] = R[a][b] * sc[b];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) Sg[a][b] = M[a][0] * M[b][0] + M[a][1] * M[b][1] + M[a][2] * M[b][2];
+  const float opac = 1.f / (1.f + expf(-ld(10)));
+
+  float g_mu[3] = {0.f, 0.f, 0.f};
+  float g_S[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+  float g_ol = 0.f;
+  float g_sh[K][3];
+#pragma unroll
+  for (int k = 0; k < K; ++k) g_sh[k][0] = g_sh[k][1] = g_sh[k][2] = 0.f;
+
+  for (int v = 0; v < fr.n_views; ++v) {
+    const float* cv = cot + ((size_t)v * n_pad + i) * NV + 9 * s;
+    float c[9];
+    bool any = false;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+      c[q] = cv[q];
+      any = any || (c[q] != 0.f);
+    }
+    if (!any) continue;
+    const gs_camera* cam = cams + v;
+    float Rc[3][3], tc[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+#pragma unroll
+      for (int b = 0; b < 3; ++b) Rc[a][b] = cam->viewmat[4 * a + b];
+      tc[a] = cam->viewmat[4 * a + 3];
+    }
+    const float fx = cam->fx, fy = cam->fy;
+    float t[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) t[a] = Rc[a][0] * mu[0] + Rc[a][1] * mu[1] + Rc[a][2] * mu[2] + tc[a];
+    float Sc[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      float tmp[3];
+#pragma unroll
+      for (int b = 0; b < 3; ++b) tmp[b] = Rc[a][0] * Sg[0][b] + Rc[a][1] * Sg[1][b] + Rc[a][2] * Sg[2][b];
+#pragma unroll
+      for (int b = 0; b < 3; ++b) Sc[a][b] = tmp[0] * Rc[b][0] + tmp[1] * Rc[b][1] + tmp[2] * Rc[b][2];
+    }
+    const float limx = kSlopeClamp * 0.5f * (float)fr.width / fx;
+    const float limy = kSlopeClamp * 0.5f * (float)fr.height / fy;
+    const float itz = 1.f / t[2];
+    const float u = t[0] * itz, vv = t[1] * itz;
+    const bool clx = u < -limx || u > limx, cly = vv < -limy || vv > limy;
+    const float uc = fminf(fmaxf(u, -limx), limx), vc = fminf(fmaxf(vv, -limy), limy);
+    const float J00 = fx * itz, J02 = -fx * uc * itz, J11 = fy * itz, J12 = -fy * vc * itz;
+    const float a = J00 * J00 * Sc[0][0] + 2.f * J00 * J02 * Sc[0][2] + J02 * J02 * Sc[2][2] + kDilation;
+    const float bb = J00 * J11 * Sc[0][1] + J00 * J12 * Sc[0][2] + J02 * J11 * Sc[1][2] + J02 * J12 * Sc[2][2];
+    const float cc = J11 * J11 * Sc[1][1] + 2.f * J11 * J12 * Sc[1][2] + J12 * J12 * Sc[2][2] + kDilation;
+    const float det = a * cc - bb * bb;
+    const float idet = 1.f / det, id2 = idet * idet;
+    // conic -> Sigma' entries
+    const float gA = c[2], gB = c[3], gC = c[4];
+    const float ga = gA * (-cc * cc * id2) + gB * (bb * cc * id2) + gC * (idet - a * cc * id2);
+    const float gb = gA * (2.f * bb * cc * id2) + gB * (-idet - 2.f * bb * bb * id2) + gC * (2.f * a * bb * id2);
+    const float gc = gA * (idet - a * cc * id2) + gB * (a * bb * id2) + gC * (-a * a * id2);
+    // Sigma' = J Sc J^T
+    const float j0[3] = {J00, 0.f, J02}, j1[3] = {0.f, J11, J12};
+    float gSc[3][3];
+#pragma unroll
+    for (int p = 0; p < 3; ++p)
+#pragma unroll
+      for (int q = 0; q < 3; ++q)
+        gSc[p][q] = ga * j0[p] * j0[q] + 0.5f * gb * (j0[p] * j1[q] + j1[p] * j0[q]) + gc * j1[p] * j1[q];
+    float JS0[3], JS1[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      JS0[q] = J00 * Sc[0][q] + J02 * Sc[2][q];
+      JS1[q] = J11 * Sc[1][q] + J12 * Sc[2][q];
+    }
+    const float gJ00 = 2.f * (ga * JS0[0] + 0.5f * gb * JS1[0]);
+    const float gJ02 = 2.f * (ga * JS0[2] + 0.5f * gb * JS1[2]);
+    const float gJ11 = 2.f * (0.5f * gb * JS0[1] + gc * JS1[1]);
+    const float gJ12 = 2.f * (0.5f * gb * JS0[2] + gc * JS1[2]);
+    const float itz2 = itz * itz, itz3 = itz2 * itz;
+    float gt[3];
+    gt[0] = c[0] * fx * itz + (clx ? 0.f : gJ02 * (-fx * itz2));
+    gt[1] = c[1] * fy * itz + (cly ? 0.f : gJ12 * (-fy * itz2));
+    gt[2] = -c[0] * fx * t[0] * itz2 - c[1] * fy * t[1] * itz2 - gJ00 * fx * itz2 - gJ11 * fy * itz2 +
+            gJ02 * (clx ? fx * uc * itz2 : 2.f * fx * t[0] * itz3) +
+            gJ12 * (cly ? fy * vc * itz2 : 2.f * fy * t[1] * itz3);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) g_mu[q] += Rc[0][q] * gt[0] + Rc[1][q] * gt[1] + Rc[2][q] * gt[2];
+    // Sigma: W^T gSc W
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+      float tmp[3];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) tmp[q] = Rc[0][p] * gSc[0][q] + Rc[1][p] * gSc[1][q] + Rc[2][p] * gSc[2][q];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) g_S[p][q] += tmp[0] * Rc[0][q] + tmp[1] * Rc[1][q] + tmp[2] * Rc[2][q];
+    }
+    // opacity
+    g_ol += c[5] * opac * (1.f - opac);
+    // colour
+    float cp[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) cp[q] = -(Rc[0][q] * tc[0] + Rc[1][q] * tc[1] + Rc[2][q] * tc[2]);
+    const float d0r = mu[0] - cp[0], d1r = mu[1] - cp[1], d2r = mu[2] - cp[2];
+    const float dn = sqrtf(d0r * d0r + d1r * d1r + d2r * d2r);
+    const float d0 = d0r / dn, d1 = d1r / dn, d2 = d2r / dn;
+    float Y[K];
+    sh_basis<DEG>(d0, d1, d2, Y);
+    float gcol[3];
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+      float raw = 0.5f;
+#pragma unroll
+      for (int k = 0; k < K; ++k) raw += Y[k] * ld(kRowSH + 3 * k + ch);
+      gcol[ch] = raw < 0.f ? 0.f : c[6 + ch];
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) g_sh[k][ch] += Y[k] * gcol[ch];
+    if constexpr (DEG > 0) {
+      float wk[K];
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+        wk[k] = ld(kRowSH + 3 * k + 0) * gcol[0] + ld(kRowSH + 3 * k + 1) * gcol[1] + ld(kRowSH + 3 * k + 2) * gcol[2];
+      float gd[3];
+      sh_basis_grad<DEG>(d0, d1, d2, wk, gd);
+      const float dot = gd[0] * d0 + gd[1] * d1 + gd[2] * d2;
+      g_mu[0] += (gd[0] - d0 * dot) / dn;
+      g_mu[1] += (gd[1] - d1 * dot) / dn;
+      g_mu[2] += (gd[2] - d2 * dot) / dn;
+    }
+  }
+  // Sigma = M M^T, M = R diag(s)
+  float gM[3][3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) gM[a][b] = 2.f * (g_S[a][0] * M[0][b] + g_S[a][1] * M[1][b] + g_S[a][2] * M[2][b]);
+  float g_ls[3];
+  float gR[3][3];
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    g_ls[b] = (gM[0][b] * R[0][b] + gM[1][b] * R[1][b] + gM[2][b] * R[2][b]) * sc[b];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) gR[a][b] = gM[a][b] * sc[b];
+  }
+  const float x = qx, y = qy, z = qz, ww = qw;
+  float gq[4];
+  gq[0] = 2.f * y * gR[0][1] + 2.f * z * gR[0][2] + 2.f * y * gR[1][0] - 4.f * x * gR[1][1] - 2.f * ww * gR[1][2] +
+          2.f * z * gR[2][0] + 2.f * ww * gR[2][1] - 4.f * x * gR[2][2];
+  gq[1] = -4.f * y * gR[0][0] + 2.f * x * gR[0][1] + 2.f * ww * gR[0][2] + 2.f * x * gR[1][0] + 2.f * z * gR[1][2] -
+          2.f * ww * gR[2][0] + 2.f * z * gR[2][1] - 4.f * y * gR[2][2];
+  gq[2] = -4.f * z * gR[0][0] - 2.f * ww * gR[0][1] + 2.f * x * gR[0][2] + 2.f * ww * gR[1][0] - 4.f * z * gR[1][1] +
+          2.f * y * gR[1][2] + 2.f * x * gR[2][0] + 2.f * y * gR[2][1];
+  gq[3] = -2.f * z * gR[0][1] + 2.f * y * gR[0][2] + 2.f * z * gR[1][0] - 2.f * x * gR[1][2] - 2.f * y * gR[2][0] +
+          2.f * x * gR[2][1];
+  const float qd = gq[0] * x + gq[1] * y + gq[2] * z + gq[3] * ww;
+  const float qn[4] = {x, y, z, ww};
+
+  // scatter the rows: stream 0 (with GRAD) is the gradient, the others the
+  // probe products, averaged over the probes after multiplying by z_k
+  float rowv[ROWS];
+  rowv[0] = g_mu[0]; rowv[1] = g_mu[1]; rowv[2] = g_mu[2];
+  rowv[3] = g_ls[0]; rowv[4] = g_ls[1]; rowv[5] = g_ls[2];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) rowv[6 + c] = (gq[c] - qn[c] * qd) / qlen;
+  rowv[10] = g_ol;
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) rowv[kRowSH + 3 * k + ch] = g_sh[k][ch];
+  if (GRAD && s == 0) {
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) grad[(size_t)r * n_pad + i] = rowv[r];
+  } else {
+    const int k = s - (GRAD ? 1 : 0);
+    const float inv_nu = 1.f / (float)NU;
+#pragma unroll 4
+    for (int r = 0; r < ROWS; ++r) {
+      const bool neg = probe_negative(seed, step, k, (uint64_t)r * (uint64_t)n + (uint64_t)i);
+      const float val = (neg ? -rowv[r] : rowv[r]) * inv_nu;
+      if (NU == 1) hz[(size_t)r * n_pad + i] = val;
+      else atomicAdd(hz + (size_t)r * n_pad + i, val);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ host side
+struct TileGrid {
+  int Tx, Ty, T;
+};
+TileGrid tile_grid(gs_frame fr) {
+  TileGrid g;
+  g.Tx = (fr.width + fr.tile_w - 1) / fr.tile_w;
+  g.Ty = (fr.height + fr.tile_h - 1) / fr.tile_h;
+  g.T = g.Tx * g.Ty;
+  return g;
+}
+
+bool frame_ok(gs_frame fr) {
+  auto pow2 = [](int v) { return v > 0 && (v & (v - 1)) == 0; };
+  const int tt = fr.tile_w * fr.tile_h;
+  return fr.n_views >= 1 && fr.width >= 1 && fr.height >= 1 && pow2(fr.tile_w) && pow2(fr.tile_h) &&
+         (tt == 64 || tt == 128 || tt == 256);
+}
+
+template <class F>
+cudaError_t allow_smem(F* f, size_t bytes) {
+  return cudaFuncSetAttribute((const void*)f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <int NU>
+gs_status launch_fwd(const gs_projected* proj, const gs_sorted* sorted, int n_pad, gs_frame fr, float* image,
+                     float* final_T, uint32_t* n_contrib, float* image_tan, int32_t* status, cudaStream_t st) {
+  const TileGrid g = tile_grid(fr);
+  const int nthr = fr.tile_w * fr.tile_h;
+  const size_t smem = 16 + (size_t)2 * nthr * sizeof(Rec) * (1 + NU);
+  static bool attr = false;
+  if (!attr) {
+    if (allow_smem(raster_fwd_kernel<NU>, 16 + (size_t)2 * 256 * sizeof(Rec) * (1 + NU)) != cudaSuccess)
+      return check_launch("gs_raster_fwd: smem attribute");
+    attr = true;
+  }
+  const unsigned blocks = (unsigned)((size_t)fr.n_views * g.T);
+  raster_fwd_kernel<NU><<<blocks, nthr, smem, st>>>(reinterpret_cast<const float4*>(proj->rec),
+                                                    reinterpret_cast<const float4*>(proj->tangent), sorted->vals,
+                                                    sorted->ranges, n_pad, fr, g.Tx, g.T, image, final_T, n_contrib,
+                                                    image_tan, status);
+  return check_launch("gs_raster_fwd");
+}
+
+size_t bwd_cot_floats(int32_t n_pad, gs_frame fr, int streams) {
+  return (size_t)fr.n_views * n_pad * 9 * streams;
+}
+
+template <int NU, bool GRAD>
+void launch_bwd_kernels(const gs_params* x, const gs_camera* cams, const gs_projected* proj, const gs_sorted* sorted,
+                        gs_frame fr, const float* image, const float* target, const float* final_T,
+                        const uint32_t* n_contrib, const float* image_tan, const gs_probe* probe, gs_loss loss,
+                        float* grad, float* hz, float* loss_out, float* cot, int32_t* status, cudaStream_t st) {
+  const TileGrid g = tile_grid(fr);
+  const int nthr = fr.tile_w * fr.tile_h;
+  const size_t smem = 16 + (size_t)2 * nthr * (sizeof(Rec) + sizeof(uint32_t));
+  const float inv_m = (float)(1.0 / (3.0 * (double)fr.width * fr.height * fr.n_views));
+  const unsigned blocks = (unsigned)((size_t)fr.n_views * g.T);
+  raster_bwd_kernel<NU, GRAD><<<blocks, nthr, smem, st>>>(
+      reinterpret_cast<const float4*>(proj->rec), sorted->vals, sorted->ranges, x->n_pad, fr, g.Tx, g.T, image,
+      target, final_T, n_contrib, image_tan, loss.kind, loss.gn_floor, inv_m, cot, loss_out, status);
+  constexpr int S = (GRAD ? 1 : 0) + NU;
+  const dim3 pg((x->n + 127) / 128, S);
+  const uint64_t seed = probe ? probe->seed : 0;
+  const int64_t t = probe ? probe->t : 0;
+  switch (x->sh_degree) {
+    case 0: project_bwd_kernel<0, NU, GRAD><<<pg, 128, 0, st>>>(x->data, x->n, x->n_pad, cams, fr, cot, seed, t, grad, hz); break;
+    case 1: project_bwd_kernel<1, NU, GRAD><<<pg, 128, 0, st>>>(x->data, x->n, x->n_pad, cams, fr, cot, seed, t, grad, hz); break;
+    case 2: project_bwd_kernel<2, NU, GRAD><<<pg, 128, 0, st>>>(x->data, x->n, x->n_pad, cams, fr, cot, seed, t, grad, hz); break;
+    default: project_bwd_kernel<3, NU, GRAD><<<pg, 128, 0, st>>>(x->data, x->n, x->n_pad, cams, fr, cot, seed, t, grad, hz); break;
+  }
+}
+
+gs_status run_bwd(bool want_grad, const gs_params* x, const gs_camera* cams, gs_frame frame, const gs_projected* proj,
+                  const gs_sorted* sorted, const float* image, const float* target, const float* final_T,
+                  const uint32_t* n_contrib, const float* image_tangent, const gs_probe* probe, gs_loss loss,
+                  gs_params* grad, gs_params* hz, float* loss_out, void* workspace, size_t workspace_bytes,
+                  int32_t* status, void* stream, const char* name) {
+  GS_REQUIRE(x && cams && proj && sorted && image && target && final_T && n_contrib, "%s: null argument", name);
+  GS_REQUIRE(proj->rec && sorted->vals && sorted->ranges && x->data, "%s: null device buffer", name);
+  GS_REQUIRE(frame_ok(frame), "%s: bad frame", name);
+  GS_REQUIRE(x->n >= 0 && x->n_pad >= x->n && x->n_pad % 4 == 0, "%s: bad n/n_pad", name);
+  GS_REQUIRE(loss.kind == GS_LOSS_L1 || loss.kind == GS_LOSS_L2, "%s: bad loss kind %d", name, loss.kind);
+  const int nu = (image_tangent && probe) ? probe->nu : 0;
+  if (nu < 0 || nu > 2 || x->sh_degree < 0 || x->sh_degree > 3) {
+    set_error("%s: unsupported nu=%d sh_degree=%d", name, nu, x->sh_degree);
+    return GS_ERR_UNSUPPORTED;
+  }
+  GS_REQUIRE(want_grad || nu > 0, "%s: needs image_tangent and a probe with nu >= 1", name);
+  GS_REQUIRE(!want_grad || (grad && grad->data), "%s: null grad", name);
+  GS_REQUIRE(nu == 0 || (hz && hz->data), "%s: probes given but hz is NULL", name);
+  auto same = [&](const gs_params* p) { return !p || (p->n == x->n && p->n_pad == x->n_pad && p->sh_degree == x->sh_degree); };
+  GS_REQUIRE(same(grad) && same(hz), "%s: grad/hz layout differs from x", name);
+  const int streams = (want_grad ? 1 : 0) + nu;
+  const size_t need = bwd_cot_floats(x->n_pad, frame, streams) * sizeof(float);
+  GS_REQUIRE(workspace && workspace_bytes >= need, "%s: workspace needs %zu bytes, got %zu", name, need,
+             workspace_bytes);
+  cudaStream_t st = (cudaStream_t)stream;
+  float* cot = (float*)workspace;
+  if (cudaMemsetAsync(cot, 0, need, st) != cudaSuccess) return check_launch(name);
+  if (nu == 2 && cudaMemsetAsync(hz->data, 0, (size_t)n_rows(x->sh_degree) * x->n_pad * sizeof(float), st) != cudaSuccess)
+    return check_launch(name);
+  float* gptr = want_grad ? grad->data : nullptr;
+  float* hptr = nu ? hz->data : nullptr;
+  if (want_grad) {
+    if (nu == 0) launch_bwd_kernels<0, true>(x, cams, proj, sorted, frame, image, target, final_T, n_contrib, image_tangent, probe, loss, gptr, hptr, loss_out, cot, status, st);
+    else if (nu == 1) launch_bwd_kernels<1, true>(x, cams, proj, sorted, frame, image, target, final_T, n_contrib, image_tangent, probe, loss, gptr, hptr, loss_out, cot, status, st);
+    else launch_bwd_kernels<2, true>(x, cams, proj, sorted, frame, image, target, final_T, n_contrib, image_tangent, probe, loss, gptr, hptr, loss_out, cot, status, st);
+  } else {
+    if (nu == 1) launch_bwd_kernels<1, false>(x, cams, proj, sorted, frame, image, target, final_T, n_contrib, image_tangent, probe, loss, gptr, hptr, loss_out, cot, status, st);
+    else launch_bwd_kernels<2, false>(x, cams, proj, sorted, frame, image, target, final_T, n_contrib, image_tangent, probe, loss, gptr, hptr, loss_out, cot, status, st);
+  }
+  return check_launch(name);
+}
+
+}  // namespace
+}  // namespace gs
+
+extern "C" gs_status gs_raster_fwd(const gs_projected* proj, const gs_sorted* sorted, int32_t n_pad, gs_frame frame,
+                                   const gs_probe* probe, float* image, float* final_T, uint32_t* n_contrib,
+                                   float* image_tangent, int32_t* status, void* stream) {
+  using namespace gs;
+  GS_REQUIRE(proj && sorted && proj->rec && sorted->vals && sorted->ranges, "gs_raster_fwd: null argument");
+  GS_REQUIRE(image && final_T && n_contrib, "gs_raster_fwd: null output");
+  GS_REQUIRE(frame_ok(frame), "gs_raster_fwd: bad frame (tile %dx%d)", frame.tile_w, frame.tile_h);
+  GS_REQUIRE(n_pad >= 0 && n_pad % 4 == 0, "gs_raster_fwd: bad n_pad");
+  const int nu = (probe && image_tangent) ? probe->nu : 0;
+  if (nu < 0 || nu > 2) {
+    set_error("gs_raster_fwd: unsupported nu=%d", nu);
+    return GS_ERR_UNSUPPORTED;
+  }
+  GS_REQUIRE(nu == 0 || proj->tangent, "gs_raster_fwd: probes given but proj->tangent is NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (nu == 0) return launch_fwd<0>(proj, sorted, n_pad, frame, image, final_T, n_contrib, nullptr, status, st);
+  if (nu == 1) return launch_fwd<1>(proj, sorted, n_pad, frame, image, final_T, n_contrib, image_tangent, status, st);
+  return launch_fwd<2>(proj, sorted, n_pad, frame, image, final_T, n_contrib, image_tangent, status, st);
+}
+
+extern "C" size_t gs_raster_bwd_workspace_size(int32_t n_pad, gs_frame frame, int32_t nu) {
+  if (n_pad < 0 || nu < 0 || nu > 2 || !gs::frame_ok(frame)) return 0;
+  return gs::bwd_cot_floats(n_pad, frame, 1 + nu) * sizeof(float);
+}
+
+extern "C" gs_status gs_raster_bwd(const gs_params* x, const gs_camera* cams, gs_frame frame, const gs_projected* proj,
+                                   const gs_sorted* sorted, const float* image, const float* target,
+                                   const float* final_T, const uint32_t* n_contrib, const float* image_tangent,
+                                   const gs_probe* probe, gs_loss loss, gs_params* grad, gs_params* hz,
+                                   float* loss_out, void* workspace, size_t workspace_bytes, int32_t* status,
+                                   void* stream) {
+  return gs::run_bwd(true, x, cams, frame, proj, sorted, image, target, final_T, n_contrib, image_tangent, probe, loss,
+                     grad, hz, loss_out, workspace, workspace_bytes, status, stream, "gs_raster_bwd");
+}
+
+extern "C" gs_status gs_hvp_diag(const gs_params* x, const gs_camera* cams, gs_frame frame, const gs_projected* proj,
+                                 const gs_sorted* sorted, const float* image, const float* target, const float* final_T,
+                                 const uint32_t* n_contrib, const float* image_tangent, const gs_probe* probe,
+                                 gs_loss loss, gs_params* hz, void* workspace, size_t workspace_bytes, int32_t* status,
+                                 void* stream) {
+  return gs::run_bwd(false, x, cams, frame, proj, sorted, image, target, final_T, n_contrib, image_tangent, probe, loss,
+                     nullptr, hz, nullptr, workspace, workspace_bytes, status, stream, "gs_hvp_diag");
+}

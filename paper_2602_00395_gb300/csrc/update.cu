@@ -1,0 +1,176 @@
+// gs_tr_update: Algorithm 1 of arXiv 2602.00395 fused into one streaming pass,
+// with the per-parameter squared-Hellinger trust-region radius of Sec. 4.2 and
+// Appendix B.
+//
+// One thread per Gaussian: the per-Gaussian geometry the radii need (alpha,
+// scales, rotation, Sigma_cc, beta_c, DC colour) is computed once in registers
+// from x_t, then the thread streams its 11 + 3K rows (coalesced across the
+// warp): read x, g_ema, d_ema, grad (and hz on curvature steps), write x, g_ema
+// (and d_ema).  The kernel is HBM-bound.
+//
+// The rotation constant beta_c of Appendix B is evaluated in closed form:
+// beta_c = 2 ||S^-1 W_c S||_F^2 - 2 ||W_c||_F^2 = 2 sum_{i<j} W_ij^2 (s_i/s_j - s_j/s_i)^2,
+// where W_c = R^T dR/dq_c is skew (its trace term tr(E'') equals -||W_c||_F^2 for
+// an orthogonal curve) with axial vector omega_c = 2 vec(conj(q^) * e_c) / |q|.
+#include "common.cuh"
+
+namespace gs {
+namespace {
+
+// max over the unit sphere of |Y_k| (closed forms, one per basis polynomial):
+//   |xy|, |yz|, |xz| <= 1/2;  |3z^2 - 1| <= 2;  |x^2 - y^2| <= 1;  |rho^3 sin 3phi| <= 1;
+//   |xyz| <= 3^-3/2;  sqrt(1-z^2)|5z^2-1| <= 16/sqrt(135);  |z(5z^2-3)| <= 2;  |z|(1-z^2) <= 2/(3 sqrt 3)
+__device__ __forceinline__ float sh_absmax(int k) {
+  switch (k) {
+    case 0: return kY0;
+    case 1: case 2: case 3: return kY1;
+    case 4: case 5: case 7: return 0.5f * kY2a;
+    case 6: return 2.f * kY2b;
+    case 8: return kY2c;
+    case 9: case 15: return kY3a;
+    case 10: return kY3b * 0.19245008972987526f;       // 3^-3/2
+    case 11: case 13: return kY3c * 1.3770607453193149f;  // 16/sqrt(135)
+    case 12: return 2.f * kY3d;
+    default: return kY3e * 0.38490017945975052f;          // 2/(3 sqrt 3)
+  }
+}
+
+template <int DEG, bool HVP, bool ETA>
+__global__ void __launch_bounds__(256) tr_update_kernel(float* __restrict__ x, float* __restrict__ ge,
+                                                        float* __restrict__ de, const float* __restrict__ g,
+                                                        const float* __restrict__ hz, float* __restrict__ eta_out,
+                                                        int n, int n_pad, gs_tr_config cfg, float eps,
+                                                        int32_t* status) {
+  constexpr int K = (DEG + 1) * (DEG + 1);
+  constexpr int ROWS = kRowSH + 3 * K;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  auto at = [&](int r) { return (size_t)r * n_pad + i; };
+  // geometry from x_t
+  const float alpha = 1.f / (1.f + expf(-x[at(10)]));
+  float s[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) s[a] = expf(x[at(3 + a)]);
+  const float q0 = x[at(6)], q1 = x[at(7)], q2 = x[at(8)], q3 = x[at(9)];
+  const float qlen = sqrtf(q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3);
+  const float X = q0 / qlen, Y = q1 / qlen, Z = q2 / qlen, W = q3 / qlen;
+  float R[3][3];
+  R[0][0] = 1.f - 2.f * (Y * Y + Z * Z);
+  R[0][1] = 2.f * (X * Y - W * Z);
+  R[0][2] = 2.f * (X * Z + W * Y);
+  R[1][0] = 2.f * (X * Y + W * Z);
+  R[1][1] = 1.f - 2.f * (Z * Z + X * X);
+  R[1][2] = 2.f * (Y * Z - W * X);
+  R[2][0] = 2.f * (X * Z - W * Y);
+  R[2][1] = 2.f * (Y * Z + W * X);
+  R[2][2] = 1.f - 2.f * (X * X + Y * Y);
+  const bool logok = alpha > eps;
+  const float L = logok ? log1pf(-eps / alpha) : 0.f;  // ln(1 - eps/alpha)
+  float eta_fixed[11];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    float var;
+    if (cfg.mean_exact) {
+      const float inv = R[c][0] * R[c][0] / (s[0] * s[0]) + R[c][1] * R[c][1] / (s[1] * s[1]) +
+                        R[c][2] * R[c][2] / (s[2] * s[2]);
+      var = 1.f / inv;
+    } else {
+      var = R[c][0] * R[c][0] * s[0] * s[0] + R[c][1] * R[c][1] * s[1] * s[1] + R[c][2] * R[c][2] * s[2] * s[2];
+    }
+    eta_fixed[c] = logok ? sqrtf(-8.f * var * L) : INFINITY;
+    eta_fixed[3 + c] = sqrtf(2.f * eps / alpha);
+  }
+  {
+    // body-frame angular velocity per unit change of q_c (x, y, z, w)
+    const float k2 = 2.f / qlen;
+    const float om[4][3] = {{W, -Z, Y}, {Z, W, -X}, {-Y, X, W}, {-X, -Y, -Z}};
+    const float r01 = s[0] / s[1] - s[1] / s[0];
+    const float r02 = s[0] / s[2] - s[2] / s[0];
+    const float r12 = s[1] / s[2] - s[2] / s[1];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const float w0 = k2 * om[c][0], w1 = k2 * om[c][1], w2 = k2 * om[c][2];
+      const float beta = 2.f * (w2 * w2 * r01 * r01 + w1 * w1 * r02 * r02 + w0 * w0 * r12 * r12);
+      eta_fixed[6 + c] = (logok && beta > 0.f) ? sqrtf(-8.f / beta * L) : INFINITY;
+    }
+  }
+  eta_fixed[10] = sqrtf(4.f * alpha * eps) / (alpha * (1.f - alpha));
+  float col_eta[3];
+#pragma unroll
+  for (int ch = 0; ch < 3; ++ch) {
+    const float Cc = fmaxf(kY0 * x[at(kRowSH + ch)] + 0.5f, cfg.color_floor);
+    col_eta[ch] = sqrtf(4.f * Cc * eps / alpha);
+  }
+
+  const float a1 = cfg.theta1, b1 = 1.f - cfg.theta1;
+  const float a2 = cfg.theta2, b2 = 1.f - cfg.theta2;
+  bool bad = false;
+#pragma unroll 4
+  for (int r = 0; r < ROWS; ++r) {
+    const size_t j = at(r);
+    const float eta = r < kRowSH ? eta_fixed[r] : col_eta[(r - kRowSH) % 3] / sh_absmax((r - kRowSH) / 3);
+    const float gnew = a1 * ge[j] + b1 * g[j];
+    float dnew = de[j];
+    if (HVP) {
+      dnew = a2 * dnew + b2 * hz[j];
+      de[j] = dnew;
+    }
+    ge[j] = gnew;
+    const float step = -gnew / fmaxf(dnew, cfg.d_floor);
+    const float xn = x[j] + fminf(fmaxf(step, -eta), eta);
+    x[j] = xn;
+    if (ETA) eta_out[j] = eta;
+    bad = bad || !isfinite(xn) || !isfinite(gnew) || !isfinite(dnew);
+  }
+  if (bad && status) atomicOr(status, GS_FLAG_NONFINITE);
+}
+
+template <int DEG>
+void launch_update(bool hvp, bool eta, gs_params* x, gs_params* ge, gs_params* de, const gs_params* g,
+                   const gs_params* hz, gs_params* eta_out, gs_tr_config cfg, float eps, int32_t* status,
+                   cudaStream_t st) {
+  const int blocks = (x->n + 255) / 256;
+  const float* hp = hz ? hz->data : nullptr;
+  float* ep = eta_out ? eta_out->data : nullptr;
+#define GS_UPD(H, E) \
+  tr_update_kernel<DEG, H, E><<<blocks, 256, 0, st>>>(x->data, ge->data, de->data, g->data, hp, ep, x->n, x->n_pad, cfg, eps, status)
+  if (hvp) {
+    if (eta) GS_UPD(true, true); else GS_UPD(true, false);
+  } else {
+    if (eta) GS_UPD(false, true); else GS_UPD(false, false);
+  }
+#undef GS_UPD
+}
+
+}  // namespace
+}  // namespace gs
+
+extern "C" gs_status gs_tr_update(gs_params* x, gs_params* g_ema, gs_params* d_ema, const gs_params* grad,
+                                  const gs_params* hz, const gs_tr_config* cfg, int64_t t, float eps,
+                                  gs_params* eta_out, int32_t* status, void* stream) {
+  using namespace gs;
+  GS_REQUIRE(x && g_ema && d_ema && grad && cfg, "gs_tr_update: null argument");
+  GS_REQUIRE(x->data && g_ema->data && d_ema->data && grad->data, "gs_tr_update: null device buffer");
+  GS_REQUIRE(t >= 1 && cfg->l >= 1, "gs_tr_update: need t >= 1 and l >= 1");
+  GS_REQUIRE(eps > 0.f, "gs_tr_update: eps must be positive");
+  auto same = [&](const gs_params* p) {
+    return !p || (p->n == x->n && p->n_pad == x->n_pad && p->sh_degree == x->sh_degree);
+  };
+  GS_REQUIRE(same(g_ema) && same(d_ema) && same(grad) && same(hz) && same(eta_out),
+             "gs_tr_update: parameter buffers differ in layout");
+  if (x->sh_degree < 0 || x->sh_degree > 3) {
+    set_error("gs_tr_update: unsupported sh_degree=%d", x->sh_degree);
+    return GS_ERR_UNSUPPORTED;
+  }
+  const bool hvp = ((t - 1) % cfg->l) == 0 && hz && hz->data;
+  if (x->n == 0) return GS_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool eta = eta_out && eta_out->data;
+  switch (x->sh_degree) {
+    case 0: launch_update<0>(hvp, eta, x, g_ema, d_ema, grad, hz, eta_out, *cfg, eps, status, st); break;
+    case 1: launch_update<1>(hvp, eta, x, g_ema, d_ema, grad, hz, eta_out, *cfg, eps, status, st); break;
+    case 2: launch_update<2>(hvp, eta, x, g_ema, d_ema, grad, hz, eta_out, *cfg, eps, status, st); break;
+    default: launch_update<3>(hvp, eta, x, g_ema, d_ema, grad, hz, eta_out, *cfg, eps, status, st); break;
+  }
+  return check_launch("gs_tr_update");
+}

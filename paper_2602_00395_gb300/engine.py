@@ -1,0 +1,182 @@
+"""One 3DGS^2-TR training iteration over the C ABI (Algorithm 1 of arXiv 2602.00395).
+
+``TRStep`` owns the device buffers of one scene and one frame (views of a fixed
+size) and issues the six library calls of an iteration on a stream:
+
+    gs_project(x, probes)        -> splat records and probe tangents
+    gs_bin_sort                  -> sorted (tile, depth) pairs, tile ranges
+    gs_raster_fwd(probes)        -> image, final T, n_contrib, image tangents J z_k
+    gs_raster_bwd(+ tangents)    -> gradient g and Hutchinson diagonal hz (S2 = S1)
+    gs_tr_update                 -> EMAs, Newton step, SHD radius, clip, update
+
+All arithmetic runs in libgs3dtr.so; this module holds buffers and the host
+loop (step counter, eps schedule).  Nothing here synchronises the stream except
+``ensure_capacity``, which sizes the pair buffer once outside any timed region.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import torch
+
+from . import gs3dtr as G
+from . import synth
+
+
+@dataclass
+class TRConfig:
+    theta1: float = 0.9
+    theta2: float = 0.999
+    d_floor: float = 1e-12
+    color_floor: float = 1e-2
+    l: int = 10
+    mean_exact: int = 0
+
+    def struct(self) -> G.gs_tr_config:
+        return G.gs_tr_config(self.theta1, self.theta2, self.d_floor, self.color_floor, self.l, self.mean_exact)
+
+
+def eps_schedule(t: int, total: int, eps0: float = 1e-6, eps1: float = 1e-8) -> float:
+    """Exponential decay of the trust-region parameter from eps0 to eps1 over the run (Sec. 5)."""
+    if total <= 1:
+        return eps0
+    return eps0 * (eps1 / eps0) ** ((t - 1) / (total - 1))
+
+
+class TRStep:
+    def __init__(self, n: int, sh_degree: int, n_views: int, width: int, height: int, *, nu: int = 1,
+                 tile=(16, 16), capacity: int | None = None, loss_kind: int = G.GS_LOSS_L1,
+                 gn_floor: float = 1e-3, cfg: TRConfig | None = None, probe_seed: int = 42,
+                 device: str = "cuda"):
+        G.load()
+        self.n, self.deg, self.V, self.W, self.H, self.nu = n, sh_degree, n_views, width, height, nu
+        self.n_pad = synth.pad_count(n)
+        self.rows = synth.n_rows(sh_degree)
+        self.tile = tile
+        self.device = torch.device(device)
+        self.cfg = cfg or TRConfig()
+        self.loss = G.gs_loss(loss_kind, gn_floor)
+        self.probe_seed = probe_seed
+        self.frame = G.frame_struct(n_views, width, height, *tile)
+        self.Tx = -(-width // tile[0])
+        self.Ty = -(-height // tile[1])
+        f32 = dict(dtype=torch.float32, device=self.device)
+        z = lambda *s: torch.zeros(*s, **f32)
+        self.x = z(self.rows, self.n_pad)
+        self.g_ema = z(self.rows, self.n_pad)
+        self.d_ema = z(self.rows, self.n_pad)
+        self.grad = z(self.rows, self.n_pad)
+        self.hz = z(self.rows, self.n_pad)
+        self.cams = torch.zeros(96 * n_views, dtype=torch.uint8, device=self.device)
+        self.rec = z(n_views * self.n_pad * 12)
+        self.tan = z(max(nu, 1) * n_views * self.n_pad * 12)
+        HW = width * height
+        self.image = z(n_views * 3 * HW)
+        self.final_T = z(n_views * HW)
+        self.n_contrib = torch.zeros(n_views * HW, dtype=torch.int32, device=self.device)
+        self.image_tan = z(max(nu, 1) * n_views * 3 * HW)
+        self.target = z(n_views * 3 * HW)
+        self.status = torch.zeros(1, dtype=torch.int32, device=self.device)
+        self.loss_val = z(1)
+        self.ranges = torch.zeros(2 * n_views * self.Tx * self.Ty, dtype=torch.int32, device=self.device)
+        self.n_pairs = torch.zeros(1, dtype=torch.int32, device=self.device)
+        self.bwd_ws = torch.empty(G.gs_raster_bwd_workspace_size(self.n_pad, self.frame, nu), dtype=torch.uint8,
+                                  device=self.device)
+        self._alloc_pairs(capacity or max(1 << 16, 8 * n * n_views))
+        self.t = 0
+
+    # ------------------------------------------------------------ buffers
+    def _alloc_pairs(self, capacity: int) -> None:
+        self.capacity = int(capacity)
+        self.keys = torch.empty(self.capacity, dtype=torch.int64, device=self.device)
+        self.vals = torch.empty(self.capacity, dtype=torch.int32, device=self.device)
+        self.sort_ws = torch.empty(G.gs_bin_sort_workspace_size(self.n_pad, self.frame, self.capacity),
+                                   dtype=torch.uint8, device=self.device)
+
+    def set_params(self, params) -> None:
+        p = torch.as_tensor(params, dtype=torch.float32)
+        self.x.zero_()
+        self.x[:, : p.shape[1]].copy_(p[:, : self.n_pad].to(self.device))
+
+    def set_cameras(self, cams) -> None:
+        assert len(cams) == self.V and all(c.width == self.W and c.height == self.H for c in cams)
+        self.cams.copy_(torch.from_numpy(G.camera_bytes(cams)).to(self.device))
+
+    def set_target(self, target) -> None:
+        self.target.copy_(torch.as_tensor(target, dtype=torch.float32).reshape(-1).to(self.device))
+
+    # ------------------------------------------------------------ structs
+    def P(self, t) -> G.gs_params:
+        return G.params_struct(t, self.n, self.deg)
+
+    def proj(self) -> G.gs_projected:
+        return G.gs_projected(self.rec.data_ptr(), self.tan.data_ptr())
+
+    def sorted(self) -> G.gs_sorted:
+        return G.gs_sorted(self.keys.data_ptr(), self.vals.data_ptr(), self.ranges.data_ptr(),
+                           self.n_pairs.data_ptr(), self.capacity)
+
+    def probe(self, t: int) -> G.gs_probe | None:
+        return G.probe_struct(self.probe_seed, t, self.nu) if self.nu > 0 else None
+
+    # ------------------------------------------------------------ calls
+    def project(self, t: int | None = None, probes: bool = True, stream=None) -> None:
+        pr = self.probe(t) if (probes and t is not None) else None
+        G.gs_project(self.P(self.x), self.cams, self.frame, pr, self.proj(), self.status, stream)
+
+    def bin_sort(self, stream=None) -> None:
+        G.gs_bin_sort(self.proj(), self.n_pad, self.frame, self.sort_ws, self.sorted(), self.status, stream)
+
+    def raster_fwd(self, t: int | None = None, probes: bool = True, stream=None) -> None:
+        pr = self.probe(t) if (probes and t is not None) else None
+        G.gs_raster_fwd(self.proj(), self.sorted(), self.n_pad, self.frame, pr, self.image, self.final_T,
+                        self.n_contrib, self.image_tan if pr else None, self.status, stream)
+
+    def raster_bwd(self, t: int | None = None, probes: bool = True, stream=None) -> None:
+        pr = self.probe(t) if (probes and t is not None) else None
+        G.gs_raster_bwd(self.P(self.x), self.cams, self.frame, self.proj(), self.sorted(), self.image, self.target,
+                        self.final_T, self.n_contrib, self.image_tan if pr else None, pr, self.loss,
+                        self.P(self.grad), self.P(self.hz) if pr else None, self.loss_val, self.bwd_ws,
+                        self.status, stream)
+
+    def hvp_diag(self, t: int, stream=None) -> None:
+        pr = self.probe(t)
+        G.gs_hvp_diag(self.P(self.x), self.cams, self.frame, self.proj(), self.sorted(), self.image, self.target,
+                      self.final_T, self.n_contrib, self.image_tan, pr, self.loss, self.P(self.hz), self.bwd_ws,
+                      self.status, stream)
+
+    def update(self, t: int, eps: float, with_hz: bool = True, eta_out=None, stream=None) -> None:
+        G.gs_tr_update(self.P(self.x), self.P(self.g_ema), self.P(self.d_ema), self.P(self.grad),
+                       self.P(self.hz) if with_hz else None, self.cfg.struct(), t, eps,
+                       self.P(eta_out) if eta_out is not None else None, self.status, stream)
+
+    # ------------------------------------------------------------ composite
+    def render(self, stream=None) -> None:
+        self.project(None, probes=False, stream=stream)
+        self.bin_sort(stream)
+        self.raster_fwd(None, probes=False, stream=stream)
+
+    def step(self, t: int, eps: float, stream=None) -> None:
+        """One iteration of Algorithm 1 on the frame's views (S1 = S2)."""
+        hvp = self.nu > 0 and ((t - 1) % self.cfg.l) == 0
+        self.loss_val.zero_()
+        self.project(t, probes=hvp, stream=stream)
+        self.bin_sort(stream)
+        self.raster_fwd(t, probes=hvp, stream=stream)
+        self.raster_bwd(t, probes=hvp, stream=stream)
+        self.update(t, eps, with_hz=hvp, stream=stream)
+
+    def ensure_capacity(self, headroom: float = 1.25) -> int:
+        """Project and bin once, read the pair count (one host sync) and grow the pair buffer if needed."""
+        self.project(None, probes=False)
+        self.bin_sort()
+        torch.cuda.synchronize(self.device)
+        need = int(self.n_pairs.item())
+        if need > self.capacity:
+            self._alloc_pairs(int(need * headroom) + 1024)
+            self.status.zero_()
+        return need
+
+    def read_status(self) -> int:
+        return int(self.status.item())

@@ -1,0 +1,64 @@
+"""The C-ABI library loads and exports every entry point its header declares.
+
+No compute call is made here (no GPU is needed): this checks the boundary
+itself -- the symbols, the struct sizes the binding assumes, and that calls
+with invalid arguments are rejected on the host with an error string.
+"""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "gs3dtr.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(gs_[a-z0-9_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2602_00395_gb300 import build, gs3dtr
+    build.build()
+    return gs3dtr.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 10
+    for name in names:
+        assert hasattr(lib, name), name
+    from paper_2602_00395_gb300 import gs3dtr
+    assert set(gs3dtr.EXPORTED) == set(names)
+
+
+def test_struct_sizes_match_header_layout():
+    from paper_2602_00395_gb300 import gs3dtr as G
+    assert C.sizeof(G.gs_params) == 24
+    assert C.sizeof(G.gs_camera) == 96
+    assert C.sizeof(G.gs_frame) == 20
+    assert C.sizeof(G.gs_probe) == 24
+    assert C.sizeof(G.gs_sorted) == 40
+    assert C.sizeof(G.gs_tr_config) == 24
+
+
+def test_host_argument_checks_reject_without_touching_the_device(lib):
+    from paper_2602_00395_gb300 import gs3dtr as G
+    assert lib.gs_version() >= 100
+    # null arguments are rejected before any launch
+    rc = lib.gs_project(None, None, G.frame_struct(1, 8, 8), None, None, None, None)
+    assert rc == G.GS_ERR_INVALID_ARG
+    assert b"null" in lib.gs_last_error()
+    # unsupported tile shapes give a zero workspace size
+    assert lib.gs_bin_sort_workspace_size(32, G.frame_struct(1, 64, 64, 12, 16), 1000) == 0
+    assert lib.gs_bin_sort_workspace_size(32, G.frame_struct(1, 64, 64, 16, 16), 1000) > 0
+    assert lib.gs_raster_bwd_workspace_size(32, G.frame_struct(2, 64, 64), 3) == 0
+    assert lib.gs_raster_bwd_workspace_size(32, G.frame_struct(2, 64, 64), 2) == 2 * 32 * 27 * 4
+    cfg = G.gs_tr_config(0.9, 0.999, 1e-12, 1e-2, 0, 0)
+    x = G.gs_params(10, 32, 0, 0, 16)
+    rc = lib.gs_tr_update(C.byref(x), C.byref(x), C.byref(x), C.byref(x), None, C.byref(cfg), 1, 1e-6, None,
+                          None, None)
+    assert rc == G.GS_ERR_INVALID_ARG  # l = 0

@@ -1,0 +1,289 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Sizes span several tiles and ragged tails (partial edge tiles, Gaussian counts
+that are not multiples of the block size).  Tolerances, from the north-star
+contract: tile keys and sorted lists bit-exact on identical FP32 inputs; images
+1e-5 max-abs away from pixels whose value a legitimate FP32/FP64 difference can
+flip (a threshold or binning decision within 1e-5 relative, counted); gradients
+1e-4 relative per parameter group; z.Hz 1e-3 relative per group; the TR update
+1e-5 relative given identical inputs.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2602_00395_gb300 import synth as S
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+GROUPS = {"mean": slice(0, 3), "log_scale": slice(3, 6), "quat": slice(6, 10), "opacity": slice(10, 11),
+          "sh": slice(11, None)}
+
+
+def _engine(n, deg, cams, tile=(16, 16), nu=1, **kw):
+    from paper_2602_00395_gb300.engine import TRStep
+    e = TRStep(n, deg, len(cams), cams[0].width, cams[0].height, nu=nu, tile=tile, **kw)
+    e.set_cameras(cams)
+    return e
+
+
+def _cfg1():
+    sc = S.make_scene(1000, 0, seed=1000, kind="cube", extent=1.0)
+    return sc, [S.single_camera(128, 128)]
+
+
+def _ragged():
+    sc = S.make_scene(2999, 3, seed=1001, kind="cube", extent=1.0, log_scale_shift=math.log(1.5))
+    cams = S.camera_ring(2, 97, 75, 1.0, seed=7, ring_factor=3.0)
+    return sc, cams
+
+
+def _records(e):
+    return e.rec.view(e.V, e.n_pad, 12).cpu().numpy()
+
+
+def _group_close(gpu, ref, tol, what):
+    for name, sl in GROUPS.items():
+        g, r = gpu[sl], ref[sl]
+        scale = np.abs(r).max()
+        if scale == 0:
+            assert np.abs(g).max() == 0, (what, name)
+            continue
+        err = np.abs(g - r).max() / scale
+        assert err <= tol, f"{what}/{name}: group relative error {err:.3g} > {tol}"
+        big = np.abs(r) > 1e-3 * scale
+        rel = np.abs(g - r)[big] / np.abs(r)[big]
+        assert rel.max() <= 20 * tol, f"{what}/{name}: entry relative error {rel.max():.3g}"
+
+
+# ------------------------------------------------------------------ project
+@pytest.mark.parametrize("case", ["cfg1", "ragged"])
+def test_project_matches_oracle(case):
+    sc, cams = _cfg1() if case == "cfg1" else _ragged()
+    e = _engine(sc.n, sc.sh_degree, cams, nu=2)
+    e.set_params(sc.params)
+    t = 3
+    e.project(t, probes=True)
+    torch.cuda.synchronize()
+    rec = _records(e)
+    tan = e.tan.view(e.V, e.nu, e.n_pad, 12).cpu().numpy()
+    P = O.params64(sc)
+    fields = [("mx", 0), ("my", 1), ("A", 2), ("B", 3), ("C", 4), ("o", 5), ("r", 6), ("g", 7), ("b", 8),
+              ("depth", 9)]
+    for v, cam in enumerate(cams):
+        ref = O.project(P, sc.sh_degree, cam)
+        valid = ref["valid"] > 0
+        rad = rec[v, : sc.n, 10].view(np.int32)
+        near_int = np.abs(ref["radius_raw"] - np.round(ref["radius_raw"])) < 1e-4 * ref["radius_raw"]
+        assert np.array_equal((rad > 0), valid)
+        assert np.all((rad == ref["radius"].astype(np.int32)) | near_int)
+        for name, col in fields:
+            g = rec[v, : sc.n, col][valid]
+            r = ref[name][valid]
+            scale = np.abs(r).max()
+            np.testing.assert_allclose(g, r, rtol=2e-5, atol=2e-6 * scale, err_msg=name)
+        for k in range(e.nu):
+            z = O.probe_matrix(42, t, k, e.rows, sc.n)
+            rt = O.project_tangent(P, sc.sh_degree, cam, z)[valid]
+            gt = tan[v, k, : sc.n, :9][valid]
+            for q in range(9):
+                scale = np.abs(rt[:, q]).max()
+                assert np.abs(gt[:, q] - rt[:, q]).max() <= 1e-4 * scale + 1e-7, (k, q)
+        # padding columns are culled
+        assert np.all(rec[v, sc.n:, 10].view(np.int32) == 0)
+
+
+# ------------------------------------------------------------------ bin/sort
+def _write_records(e, mx, my, r, d):
+    rec = torch.zeros(e.V, e.n_pad, 12, dtype=torch.float32)
+    n = mx.shape[1]
+    rec[:, :n, 0] = torch.from_numpy(mx)
+    rec[:, :n, 1] = torch.from_numpy(my)
+    rec[:, :n, 9] = torch.from_numpy(d)
+    rec[:, :n, 10] = torch.from_numpy(r.astype(np.int32).view(np.float32))
+    e.rec.copy_(rec.reshape(-1).to(e.device))
+
+
+@pytest.mark.parametrize("W,H,tile,V,n,maxr", [
+    (128, 128, (16, 16), 1, 1000, 40),
+    (97, 53, (16, 8), 3, 4001, 30),
+    (61, 45, (8, 8), 2, 777, 60),
+    (1297, 840, (16, 16), 2, 150000, 80),  # ~ millions of pairs, many radix blocks
+])
+def test_bin_sort_bit_exact(W, H, tile, V, n, maxr):
+    recs = [S.projected_records(n, W, H, seed=100 + v, max_radius=maxr) for v in range(V)]
+    mx = np.stack([a[0] for a in recs]); my = np.stack([a[1] for a in recs])
+    r = np.stack([a[2] for a in recs]); d = np.stack([a[3] for a in recs])
+    keys, vals, ranges = O.bin_sort(mx, my, r, d, W, H, *tile)
+    cams = [S.single_camera(W, H)] * V
+    e = _engine(n, 0, cams, tile=tile, nu=0, capacity=len(keys) + 123)
+    _write_records(e, mx, my, r, d)
+    e.bin_sort()
+    torch.cuda.synchronize()
+    P = int(e.n_pairs.item())
+    assert P == len(keys)
+    assert e.read_status() == 0
+    np.testing.assert_array_equal(e.keys[:P].cpu().numpy().view(np.uint64), keys)
+    np.testing.assert_array_equal(e.vals[:P].cpu().numpy().view(np.uint32), vals)
+    np.testing.assert_array_equal(e.ranges.cpu().numpy().view(np.uint32).reshape(-1, 2), ranges)
+
+
+def test_bin_sort_capacity_overflow_is_flagged_and_in_bounds():
+    W, H, n = 128, 96, 3000
+    mx, my, r, d = S.projected_records(n, W, H, seed=5, max_radius=50)
+    keys, _, _ = O.bin_sort(mx, my, r, d, W, H)
+    e = _engine(n, 0, [S.single_camera(W, H)], nu=0, capacity=len(keys) // 3)
+    _write_records(e, mx[None], my[None], r[None], d[None])
+    e.bin_sort()
+    torch.cuda.synchronize()
+    from paper_2602_00395_gb300 import gs3dtr as G
+    assert int(e.n_pairs.item()) == len(keys)
+    assert e.read_status() & G.GS_FLAG_CAPACITY
+
+
+def test_bin_sort_empty_input():
+    W, H, n = 64, 64, 100
+    e = _engine(n, 0, [S.single_camera(W, H)], nu=0, capacity=1024)
+    e.rec.zero_()
+    e.bin_sort()
+    torch.cuda.synchronize()
+    assert int(e.n_pairs.item()) == 0
+    assert int(e.ranges.abs().sum().item()) == 0
+
+
+# ------------------------------------------------------------------ forward
+def _render_compare(sc, cams, tile=(16, 16)):
+    e = _engine(sc.n, sc.sh_degree, cams, tile=tile, nu=0)
+    e.set_params(sc.params)
+    e.ensure_capacity()
+    e.render()
+    torch.cuda.synchronize()
+    ref = O.render(O.params64(sc), sc.sh_degree, cams, *tile)
+    V, H, W = len(cams), cams[0].height, cams[0].width
+    img = e.image.view(V, 3, H, W).cpu().numpy()
+    T = e.final_T.view(V, H, W).cpu().numpy()
+    nc = e.n_contrib.view(V, H, W).cpu().numpy()
+    ok = ref["margin"] >= 1e-5
+    return e, ref, img, T, nc, ok
+
+
+@pytest.mark.parametrize("case,tile", [("cfg1", (16, 16)), ("ragged", (16, 8)), ("ragged", (8, 8))])
+def test_raster_fwd_matches_oracle(case, tile):
+    sc, cams = _cfg1() if case == "cfg1" else _ragged()
+    e, ref, img, T, nc, ok = _render_compare(sc, cams, tile)
+    assert int(e.n_pairs.item()) == ref["n_pairs"] or (~ok).any()
+    # pixels whose value FP32 may legitimately flip: here one splat per view has
+    # a radius within 1e-5 of an integer, and its ambiguous tile band is excluded
+    excluded = 1.0 - ok.mean()
+    assert excluded < 0.05, excluded
+    err = np.abs(img - ref["image"]).max(axis=1)[ok]
+    assert err.max() <= 1e-5, err.max()
+    assert np.abs(T - ref["final_T"])[ok].max() <= 1e-5
+    assert np.array_equal(nc[ok], ref["n_contrib"][ok])
+
+
+# ------------------------------------------------------------------ reverse
+def _grad_case(case, nu, loss_kind=0):
+    sc, cams = _cfg1() if case == "cfg1" else _ragged()
+    V, H, W = len(cams), cams[0].height, cams[0].width
+    target = S.noise_target(V, H, W, seed=2000)
+    e = _engine(sc.n, sc.sh_degree, cams, nu=nu, loss_kind=loss_kind)
+    e.set_params(sc.params)
+    e.set_target(target)
+    e.ensure_capacity()
+    t = 4
+    e.project(t, probes=nu > 0)
+    e.bin_sort()
+    e.raster_fwd(t, probes=nu > 0)
+    e.loss_val.zero_()
+    e.raster_bwd(t, probes=nu > 0)
+    torch.cuda.synchronize()
+    ref = O.backward(O.params64(sc), sc.sh_degree, cams, target.astype(np.float64), loss_kind=loss_kind,
+                     seed=42, t=t, nu=nu, want_tangents=nu > 0)
+    return sc, e, ref
+
+
+@pytest.mark.parametrize("case,nu,loss_kind", [("cfg1", 0, 0), ("cfg1", 1, 0), ("ragged", 2, 0), ("ragged", 1, 1)])
+def test_gradient_and_hutchinson_match_oracle(case, nu, loss_kind):
+    sc, e, ref = _grad_case(case, nu, loss_kind)
+    grad = e.grad[:, : sc.n].cpu().numpy()
+    _group_close(grad, ref["grad"], 1e-4, "grad")
+    assert abs(float(e.loss_val.item()) - ref["loss"]) <= 1e-5 * ref["loss"]
+    if nu:
+        hz = e.hz[:, : sc.n].cpu().numpy()
+        _group_close(hz, ref["hz"], 1e-3, "hz")
+        V, H, W = e.V, e.H, e.W
+        it = e.image_tan.view(nu, V, 3, H, W).cpu().numpy()
+        scale = np.abs(ref["image_tangent"]).max()
+        assert np.abs(it - ref["image_tangent"]).max() <= 1e-4 * scale
+
+
+def test_hvp_diag_standalone_equals_fused():
+    sc, e, ref = _grad_case("cfg1", 1)
+    fused = e.hz.clone()
+    e.hz.fill_(123.0)
+    e.hvp_diag(4)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(e.hz[:, : sc.n].cpu().numpy(), fused[:, : sc.n].cpu().numpy(), rtol=1e-5,
+                               atol=1e-6 * fused.abs().max().item())
+
+
+# ------------------------------------------------------------------ update
+@pytest.mark.parametrize("deg,t,l,mean_exact", [(0, 1, 10, 0), (3, 1, 1, 1), (3, 5, 2, 0), (1, 2, 3, 0)])
+def test_tr_update_matches_oracle(deg, t, l, mean_exact):
+    from paper_2602_00395_gb300.engine import TRConfig
+    n = 5003
+    sc = S.make_scene(n, deg, seed=77)
+    rng = np.random.default_rng(t + 10 * deg)
+    rows = sc.params.shape[0]
+    P32 = sc.params.copy()
+    P32[10, :n] = rng.normal(0, 4, n)  # includes alpha <= eps Gaussians
+    ge = (rng.normal(size=P32.shape) * 1e-3).astype(np.float32)
+    de = np.abs(rng.normal(size=P32.shape) * 1e-2).astype(np.float32)
+    de[:, ::7] = 0.0  # exercises the d_floor
+    g = (rng.normal(size=P32.shape) * 1e-3).astype(np.float32)
+    hz = (rng.normal(size=P32.shape) * 1e-2).astype(np.float32)
+    cfg = TRConfig(l=l, mean_exact=mean_exact)
+    eps = 1e-6 * (1e-2) ** ((t - 1) / 9)
+    e = _engine(n, deg, [S.single_camera(64, 64)], nu=1, cfg=cfg)
+    e.x.copy_(torch.from_numpy(P32)); e.g_ema.copy_(torch.from_numpy(ge)); e.d_ema.copy_(torch.from_numpy(de))
+    e.grad.copy_(torch.from_numpy(g)); e.hz.copy_(torch.from_numpy(hz))
+    eta = torch.zeros_like(e.x)
+    e.update(t, eps, with_hz=True, eta_out=eta)
+    torch.cuda.synchronize()
+    assert e.read_status() == 0
+    ocfg = O.tr_config(theta1=cfg.theta1, theta2=cfg.theta2, d_floor=cfg.d_floor, color_floor=cfg.color_floor,
+                       l=l, mean_exact=mean_exact)
+    rx, rg, rd, reta = O.tr_update(P32[:, :n], ge[:, :n], de[:, :n], g[:, :n], hz[:, :n], deg, t=t, eps=np.float32(eps),
+                                   cfg=ocfg)
+    # FP32 evaluates a x + b y with an error of a few ulps of |a x| + |b y|,
+    # so tolerances scale with the operands, not with the (cancelling) result
+    a1, a2 = cfg.theta1, cfg.theta2
+    g_scale = a1 * np.abs(ge[:, :n]) + (1 - a1) * np.abs(g[:, :n])
+    d_scale = a2 * np.abs(de[:, :n]) + (1 - a2) * np.abs(hz[:, :n])
+    hvp_step = (t - 1) % l == 0
+    if not hvp_step:
+        d_scale = np.abs(de[:, :n])
+    ge_gpu = e.g_ema[:, :n].cpu().numpy().astype(np.float64)
+    de_gpu = e.d_ema[:, :n].cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(ge_gpu - rg) <= 1e-6 * g_scale + 1e-30)
+    assert np.all(np.abs(de_gpu - rd) <= 1e-6 * d_scale + 1e-30)
+    eg = eta[:, :n].cpu().numpy()
+    fin = np.isfinite(reta)
+    assert np.array_equal(np.isfinite(eg), fin)
+    np.testing.assert_allclose(eg[fin], reta[fin], rtol=1e-5)
+    # the step x_{t+1} - x_t: clipped steps equal +-eta (1e-5 relative); unclipped
+    # ones inherit the operand-scaled error of g_ema / max(d_ema, d_floor)
+    den = np.maximum(rd, cfg.d_floor)
+    step_scale = np.minimum(np.where(fin, reta, np.inf), (g_scale + np.abs(rg) * d_scale / den) / den)
+    dx_gpu = e.x[:, :n].cpu().numpy().astype(np.float64) - P32[:, :n]
+    dx_ref = rx - P32[:, :n].astype(np.float64)
+    ulp = np.spacing(np.abs(e.x[:, :n].cpu().numpy())).astype(np.float64)
+    assert np.all(np.abs(dx_gpu - dx_ref) <= 1e-5 * step_scale + 2 * ulp)
+    # some steps are clipped and some are not
+    clipped = np.isclose(np.abs(dx_ref), np.where(fin, reta, -1), rtol=1e-12)
+    assert clipped.any() and (~clipped).any()
