@@ -226,14 +226,16 @@ def e2e_steps(eng, batches, host_targets, K, t0, stream):
 
 
 # ------------------------------------------------------------------ roofline
-def raster_bwd_flops_per_pair() -> int:
-    """FP32 operations per evaluated (pixel, splat) pair of the reverse kernel with
-    1 + nu cotangent streams: shared part (offsets, power, exp, alpha, T recovery,
-    dC/dalpha, suffix update) + per-stream part (dL/dalpha, power/opacity/colour
-    partials) + the warp reduce-scatter adds amortised per lane."""
-    shared = 2 + 7 + 1 + 2 + 3 + 9 + 6 + 3
-    per_stream = 5 + 2 + 10 + 1 + 3
-    return shared + (1 + NU) * per_stream + 31
+# Algorithmic FP32 work per contributing (pixel, splat) unit, the unit being
+# sum over pixels of n_contrib (list position of the last blended splat): the
+# forward blend ~20 FLOP per unit plus ~25 per probe for the fused tangents; the
+# reverse blend ~50 FLOP per unit per cotangent stream (1 + nu streams).
+def raster_fwd_flops_per_unit() -> int:
+    return 20 + 25 * NU
+
+
+def raster_bwd_flops_per_unit() -> int:
+    return 50 * (1 + NU)
 
 
 def peaks():
@@ -245,15 +247,15 @@ def peaks():
 
 
 # ------------------------------------------------------------------ CPU oracle
-def oracle_sample(seconds_hint=True):
-    """Bounded oracle sample: the same distributions at 1/100 of the Gaussians,
+def oracle_sample(frac: int = 100):
+    """Bounded oracle sample: the same distributions at 1/frac of the Gaussians,
     one of the 8 views at full 1080p, nu = 2, one full step (forward, reverse pass
-    with the Hutchinson product, update).  Scaled to the full step by x100 (Gaussians)
-    x8 (views)."""
+    with the Hutchinson product, update).  Scaled to the full step by x frac
+    (Gaussians) x 8 (views)."""
     import numpy as np
     import oracle as O
     from paper_2602_00395_gb300 import synth as S
-    n = N_GAUSS // 100
+    n = N_GAUSS // frac
     sc = S.make_scene(n, SH_DEG, seed=1000, kind="clusters", extent=10.0)
     cam = S.camera_ring(RING, W, H, 10.0, seed=7)[:1]
     target = S.noise_target(1, H, W, seed=2000).astype(np.float64)
@@ -263,8 +265,9 @@ def oracle_sample(seconds_hint=True):
     O.tr_update(P, np.zeros_like(P), np.zeros_like(P), out["grad"], out["hz"], SH_DEG, t=1, eps=1e-6,
                 cfg=O.tr_config(l=1))
     dt = time.perf_counter() - t0
-    scale = 100 * N_VIEWS
-    return dt, scale, f"{n} Gaussians (1/100), 1 of {N_VIEWS} views at {W}x{H}, nu={NU}, one full step; x{scale}"
+    scale = frac * N_VIEWS
+    return dt, scale, (f"{n} Gaussians (1/{frac}), 1 of {N_VIEWS} views at {W}x{H}, nu={NU}, one full step, "
+                       f"single thread; scaled x{scale}")
 
 
 def run_reference(args):
@@ -346,20 +349,23 @@ def run_cuda(args):
     sum_nc = float(eng.n_contrib.double().sum().item())
     hbm, sm_mhz, src = peaks()
     fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
-    bwd_ms = per_call["raster_bwd"]
-    flops = raster_bwd_flops_per_pair() * sum_nc
-    achieved = flops / (bwd_ms * 1e-3) / 1e12
-    roof = {"kernel": "gs_raster_bwd (reverse blend + projection reverse)", "bound": "alu", "achieved": achieved,
-            "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
-            "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz ({src} max clock)",
-            "work": f"{raster_bwd_flops_per_pair()} FLOP x {sum_nc:.3e} evaluated (pixel, splat) pairs"}
+    fwd_ms, bwd_ms = per_call["raster_fwd"], per_call["raster_bwd"]
+    if fwd_ms >= bwd_ms:
+        name, ms_k, per_unit = "gs_raster_fwd (blend + fused JVP, nu=2)", fwd_ms, raster_fwd_flops_per_unit()
+    else:
+        name, ms_k, per_unit = "gs_raster_bwd (reverse blend, 1+nu streams, + projection reverse)", bwd_ms, raster_bwd_flops_per_unit()
+    achieved = per_unit * sum_nc / (ms_k * 1e-3) / 1e12
+    roof = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+            "frac": achieved / fp32_peak, "traffic": None, "launch_ms": ms_k,
+            "peak_source": f"152 SMs x 128 FP32 lanes x 2 FLOP x {sm_mhz:.0f} MHz ({src} max SM clock)",
+            "work": f"{per_unit} FLOP x {sum_nc:.4g} units (sum over pixels of n_contrib, all views)"}
     clocks = clk.summary()
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         try:
             import oracle
             oracle.build()
-            dt, scale, desc = oracle_sample()
+            dt, scale, desc = oracle_sample(25)
             cpu = {"value": 1.0 / (dt * scale), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
                    "sample_seconds": dt}
         except Exception as ex:  # pragma: no cover

@@ -47,7 +47,9 @@ __global__ void __launch_bounds__(256) tr_update_kernel(float* __restrict__ x, f
   if (i >= n) return;
   auto at = [&](int r) { return (size_t)r * n_pad + i; };
   // geometry from x_t
-  const float alpha = 1.f / (1.f + expf(-x[at(10)]));
+  const float logit = x[at(10)];
+  const float alpha = 1.f / (1.f + expf(-logit));
+  const float alpha_c = 1.f / (1.f + expf(logit));  // 1 - alpha without cancellation
   float s[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) s[a] = expf(x[at(3 + a)]);
@@ -94,7 +96,7 @@ __global__ void __launch_bounds__(256) tr_update_kernel(float* __restrict__ x, f
       eta_fixed[6 + c] = (logok && beta > 0.f) ? sqrtf(-8.f / beta * L) : INFINITY;
     }
   }
-  eta_fixed[10] = sqrtf(4.f * alpha * eps) / (alpha * (1.f - alpha));
+  eta_fixed[10] = sqrtf(4.f * alpha * eps) / (alpha * alpha_c);
   float col_eta[3];
 #pragma unroll
   for (int ch = 0; ch < 3; ++ch) {

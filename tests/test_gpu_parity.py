@@ -256,13 +256,14 @@ def test_tr_update_matches_oracle(deg, t, l, mean_exact):
     e.update(t, eps, with_hz=True, eta_out=eta)
     torch.cuda.synchronize()
     assert e.read_status() == 0
-    ocfg = O.tr_config(theta1=cfg.theta1, theta2=cfg.theta2, d_floor=cfg.d_floor, color_floor=cfg.color_floor,
-                       l=l, mean_exact=mean_exact)
+    f32 = lambda v: float(np.float32(v))  # the hyper-parameters the kernel receives
+    ocfg = O.tr_config(theta1=f32(cfg.theta1), theta2=f32(cfg.theta2), d_floor=f32(cfg.d_floor),
+                       color_floor=f32(cfg.color_floor), l=l, mean_exact=mean_exact)
     rx, rg, rd, reta = O.tr_update(P32[:, :n], ge[:, :n], de[:, :n], g[:, :n], hz[:, :n], deg, t=t, eps=np.float32(eps),
                                    cfg=ocfg)
     # FP32 evaluates a x + b y with an error of a few ulps of |a x| + |b y|,
     # so tolerances scale with the operands, not with the (cancelling) result
-    a1, a2 = cfg.theta1, cfg.theta2
+    a1, a2 = f32(cfg.theta1), f32(cfg.theta2)
     g_scale = a1 * np.abs(ge[:, :n]) + (1 - a1) * np.abs(g[:, :n])
     d_scale = a2 * np.abs(de[:, :n]) + (1 - a2) * np.abs(hz[:, :n])
     hvp_step = (t - 1) % l == 0
