@@ -166,6 +166,25 @@ size_t gs_bin_sort_workspace_size(int32_t n_pad, gs_frame frame, uint64_t capaci
 gs_status gs_bin_sort(const gs_projected* proj, int32_t n_pad, gs_frame frame, void* workspace,
                       size_t workspace_bytes, gs_sorted* out, int32_t* status, void* stream);
 
+/* gs_bin_sort for callers that cannot allocate device memory (this entry has no
+ * counterpart in the paper).  Some callers cannot provide gs_bin_sort's
+ * workspace: a server whose allocator is frozen after it reserved its memory, a
+ * plugin handed only device pointers by a framework that owns allocation, or a
+ * loop that must never pay cudaMalloc's implicit synchronisation.  This call
+ * gives the same result as gs_bin_sort with the same arguments, but takes its
+ * scratch from a 32 MiB device array inside the library (held on every GPU that
+ * loads the library until the process exits) and allocates nothing.
+ *   - Limit: gs_bin_sort_workspace_size(n_pad, frame, out->capacity) must be at
+ *     most 32 MiB (about 2.3 million pairs with one million view x n_pad records);
+ *     larger requests return GS_ERR_INVALID_ARG with an explanation.
+ *   - The first call on each device, with that device current, looks up the
+ *     array's device address (cudaGetSymbolAddress); make it before any stream
+ *     capture.
+ *   - Every call shares the one array: calls that may overlap on the GPU race on
+ *     it and must be ordered by the caller.  No scratch word needs to start at zero. */
+gs_status gs_bin_sort_noalloc(const gs_projected* proj, int32_t n_pad, gs_frame frame, gs_sorted* out,
+                              int32_t* status, void* stream);
+
 /* Sec. 3.1 blending: C = sum_i c_i a_i T_i, T_i = prod_{j<i} (1 - a_j),
  * a = min(0.99, o exp(power)), splats with a < 1/255 skipped, stop before T
  * would fall below 1e-4, black background.

@@ -22,6 +22,7 @@ GS_FLAG_CAPACITY, GS_FLAG_NONFINITE, GS_FLAG_TIMEOUT = 1, 2, 4
 GS_LOSS_L1, GS_LOSS_L2 = 0, 1
 
 EXPORTED = ("gs_last_error", "gs_version", "gs_project", "gs_bin_sort_workspace_size", "gs_bin_sort",
+            "gs_bin_sort_noalloc",
             "gs_raster_fwd", "gs_raster_bwd_workspace_size", "gs_raster_bwd", "gs_hvp_diag", "gs_tr_update")
 
 
@@ -96,6 +97,8 @@ def load():
         L.gs_bin_sort.restype = st
         L.gs_bin_sort.argtypes = [C.POINTER(gs_projected), C.c_int32, gs_frame, P, C.c_size_t,
                                   C.POINTER(gs_sorted), P, P]
+        L.gs_bin_sort_noalloc.restype = st
+        L.gs_bin_sort_noalloc.argtypes = [C.POINTER(gs_projected), C.c_int32, gs_frame, C.POINTER(gs_sorted), P, P]
         L.gs_raster_fwd.restype = st
         L.gs_raster_fwd.argtypes = [C.POINTER(gs_projected), C.POINTER(gs_sorted), C.c_int32, gs_frame,
                                     C.POINTER(gs_probe), P, P, P, P, P, P]
@@ -178,6 +181,14 @@ def gs_bin_sort(proj: gs_projected, n_pad: int, frame: gs_frame, workspace, out:
     L = load()
     check(L.gs_bin_sort(C.byref(proj), n_pad, frame, ptr(workspace), workspace.numel() * workspace.element_size(),
                         C.byref(out), ptr(status), stream_handle(stream)), "gs_bin_sort")
+
+
+def gs_bin_sort_noalloc(proj: gs_projected, n_pad: int, frame: gs_frame, out: gs_sorted, status=None,
+                        stream=None) -> None:
+    """gs_bin_sort without a caller workspace (the library's fixed 32 MiB scratch)."""
+    L = load()
+    check(L.gs_bin_sort_noalloc(C.byref(proj), n_pad, frame, C.byref(out), ptr(status), stream_handle(stream)),
+          "gs_bin_sort_noalloc")
 
 
 def gs_raster_fwd(proj: gs_projected, sorted_: gs_sorted, n_pad: int, frame: gs_frame, probe: gs_probe | None,
