@@ -359,13 +359,6 @@ SortPlan plan_sort(int32_t n_pad, gs_frame fr, uint64_t capacity) {
   return p;
 }
 
-bool frame_ok(gs_frame fr) {
-  auto pow2 = [](int v) { return v > 0 && (v & (v - 1)) == 0; };
-  const int tt = fr.tile_w * fr.tile_h;
-  return fr.n_views >= 1 && fr.width >= 1 && fr.height >= 1 && pow2(fr.tile_w) && pow2(fr.tile_h) &&
-         (tt == 64 || tt == 128 || tt == 256);
-}
-
 }  // namespace
 }  // namespace gs
 

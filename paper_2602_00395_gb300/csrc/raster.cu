@@ -59,6 +59,42 @@ __device__ __forceinline__ void stage_batch(int b, int nthr, uint32_t start, int
   }
 }
 
+// ------------------------------------------------------------ pixel blocks
+// Thread tid of a tile renders pixel (lx, ly): warp w covers the 8 x 4 pixel
+// block (w % (tile_w/8), w / (tile_w/8)), so that a splat's footprint meets few
+// warps.
+__device__ __forceinline__ void pixel_of(int tid, int tile_w, int& lx, int& ly) {
+  const int warp = tid >> 5, lane = tid & 31, bxn = tile_w >> 3;
+  lx = (warp % bxn) * 8 + (lane & 7);
+  ly = (warp / bxn) * 4 + (lane >> 3);
+}
+
+// Bit w is set if the splat can reach alpha >= 1/255 at some pixel centre of
+// warp block w.  That region is the ellipse d^T Q d <= tau, tau = 2 ln(255 o),
+// Q the conic; its bounding box has half-widths sqrt(tau Q^-1_xx),
+// sqrt(tau Q^-1_yy), widened by 0.1% + 0.01 px so that no pair an FP32 pixel
+// test would keep is dropped.  A cleared bit therefore skips only pairs that
+// every pixel of the block skips anyway: results are unchanged.
+__device__ __forceinline__ uint32_t warp_block_mask(const Rec& r, float tile_x0, float tile_y0, int tile_w,
+                                                    int nwarps) {
+  const float tau = 2.f * __logf(255.f * r.b.y);
+  if (!(tau > 0.f)) return 0u;
+  const float A = r.a.z, B = r.a.w, C = r.b.x;
+  const float det = A * C - B * B;
+  float hx = sqrtf(tau * C / det), hy = sqrtf(tau * A / det);
+  if (!(hx < 1e30f) || !(hy < 1e30f)) return 0xffffffffu;
+  hx = hx * 1.001f + 0.01f;
+  hy = hy * 1.001f + 0.01f;
+  const int bxn = tile_w >> 3;
+  uint32_t m = 0;
+  for (int w = 0; w < nwarps; ++w) {
+    const float x0 = tile_x0 + (float)((w % bxn) * 8) + 0.5f, x1 = x0 + 7.f;
+    const float y0 = tile_y0 + (float)((w / bxn) * 4) + 0.5f, y1 = y0 + 3.f;
+    if (r.a.x + hx >= x0 && r.a.x - hx <= x1 && r.a.y + hy >= y0 && r.a.y - hy <= y1) m |= 1u << w;
+  }
+  return m;
+}
+
 // ------------------------------------------------------------------ forward
 template <int NU>
 __global__ void __launch_bounds__(256) raster_fwd_kernel(const float4* __restrict__ rec, const float4* __restrict__ tan,
@@ -68,17 +104,21 @@ __global__ void __launch_bounds__(256) raster_fwd_kernel(const float4* __restric
                                                          float* __restrict__ final_T, uint32_t* __restrict__ n_contrib,
                                                          float* __restrict__ image_tan, int32_t* status) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const int nthr = blockDim.x;
+  const int nthr = blockDim.x, nwarps = nthr >> 5;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
   Rec* buf = reinterpret_cast<Rec*>(smem + 16);
   Rec* tbuf = buf + 2 * nthr;
+  uint32_t* s_mask = reinterpret_cast<uint32_t*>(tbuf + 2 * NU * nthr);
   const int tid = threadIdx.x;
+  const uint32_t wbit = 1u << (tid >> 5);
   const int view = blockIdx.x / T, tile = blockIdx.x - view * T;
   const int ty = tile / Tx, tx = tile - ty * Tx;
-  const int lx = tid & (fr.tile_w - 1), ly = tid / fr.tile_w;
+  int lx, ly;
+  pixel_of(tid, fr.tile_w, lx, ly);
   const int px = tx * fr.tile_w + lx, py = ty * fr.tile_h + ly;
   const bool inside = px < fr.width && py < fr.height;
   const float pxc = (float)px + 0.5f, pyc = (float)py + 0.5f;
+  const float tile_x0 = (float)(tx * fr.tile_w), tile_y0 = (float)(ty * fr.tile_h);
   const size_t tslot = 2 * ((size_t)view * T + tile);
   const uint32_t start = ranges[tslot], end = ranges[tslot + 1];
   const int n = (int)(end - start);
@@ -102,10 +142,26 @@ __global__ void __launch_bounds__(256) raster_fwd_kernel(const float4* __restric
     const int bi = b & 1;
     const bool ok = mbar_wait_bounded(&bars[bi], (uint32_t)((b >> 1) & 1), status);
     const int cnt = min(nthr, n - b * nthr);
+    Rec* bb = buf + bi * nthr;
+    // per splat: which warps it can reach, and the probe tangents of its power
+    // rewritten as the quadratic form pd = dx (a dx + b dy + d) + dy (c dy + e)
+    if (tid < cnt) {
+      const Rec r = bb[tid];
+      s_mask[tid] = ok ? warp_block_mask(r, tile_x0, tile_y0, fr.tile_w, nwarps) : 0u;
+#pragma unroll
+      for (int k = 0; k < NU; ++k) {
+        Rec* tp = &tbuf[(bi * NU + k) * nthr + tid];
+        const float4 ta = tp->a;  // dmx, dmy, dA, dB
+        const float dC = tp->b.x;
+        tp->a = make_float4(-0.5f * ta.z, -ta.w, -0.5f * dC, -(r.a.z * ta.x + r.a.w * ta.y));
+        tp->b.x = -(r.b.x * ta.y + r.a.w * ta.x);
+      }
+    }
+    __syncthreads();
     if (!ok) done = true;
     if (!done) {
-      const Rec* bb = buf + bi * nthr;
       for (int j = 0; j < cnt; ++j) {
+        if (!(s_mask[j] & wbit)) continue;  // warp-uniform
         const Rec r = bb[j];
         const float dx = __fsub_rn(r.a.x, pxc), dy = __fsub_rn(r.a.y, pyc);
         const float power = splat_power(r, dx, dy);
@@ -125,13 +181,12 @@ __global__ void __launch_bounds__(256) raster_fwd_kernel(const float4* __restric
 #pragma unroll
           for (int k = 0; k < NU; ++k) {
             const Rec t = tbuf[(bi * NU + k) * nthr + j];
-            const float pd = -0.5f * (t.a.z * dx * dx + 2.f * r.a.z * dx * t.a.x + t.b.x * dy * dy +
-                                      2.f * r.b.x * dy * t.a.y) -
-                             t.a.w * dx * dy - r.a.w * (t.a.x * dy + dx * t.a.y);
+            const float pd = dx * (t.a.x * dx + t.a.y * dy + t.a.w) + dy * (t.a.z * dy + t.b.x);
             const float ad = capped ? 0.f : (t.b.y * G + alpha * pd);
-            Cd[k][0] += (t.b.z * alpha + r.b.z * ad) * Tr + r.b.z * alpha * Td[k];
-            Cd[k][1] += (t.b.w * alpha + r.b.w * ad) * Tr + r.b.w * alpha * Td[k];
-            Cd[k][2] += (t.c.x * alpha + r.c.x * ad) * Tr + r.c.x * alpha * Td[k];
+            const float sk = ad * Tr + alpha * Td[k];
+            Cd[k][0] += t.b.z * w + r.b.z * sk;
+            Cd[k][1] += t.b.w * w + r.b.w * sk;
+            Cd[k][2] += t.c.x * w + r.c.x * sk;
             Td[k] = Td[k] * (1.f - alpha) - Tr * ad;
           }
         }
@@ -215,11 +270,15 @@ __global__ void __launch_bounds__(256) raster_bwd_kernel(
   uint32_t* s_idx = reinterpret_cast<uint32_t*>(buf + 2 * nthr);
   __shared__ uint32_t s_max;
   __shared__ float s_loss[8];
-  const int tid = threadIdx.x, lane = tid & 31;
+  uint32_t* s_mask = s_idx + 2 * nthr;
+  const int tid = threadIdx.x, lane = tid & 31, nwarps = nthr >> 5;
+  const uint32_t wbit = 1u << (tid >> 5);
   const int view = blockIdx.x / T, tile = blockIdx.x - view * T;
   const int ty = tile / Tx, tx = tile - ty * Tx;
-  const int lx = tid & (fr.tile_w - 1), ly = tid / fr.tile_w;
+  int lx, ly;
+  pixel_of(tid, fr.tile_w, lx, ly);
   const int px = tx * fr.tile_w + lx, py = ty * fr.tile_h + ly;
+  const float tile_x0 = (float)(tx * fr.tile_w), tile_y0 = (float)(ty * fr.tile_h);
   const bool inside = px < fr.width && py < fr.height;
   const float pxc = (float)px + 0.5f, pyc = (float)py + 0.5f;
   const size_t tslot = 2 * ((size_t)view * T + tile);
@@ -294,9 +353,12 @@ __global__ void __launch_bounds__(256) raster_bwd_kernel(
     const bool ok = __syncthreads_and(mbar_wait_bounded(&bars[bi], (uint32_t)((uses >> 1) & 1), status)) != 0;
     ++uses;
     const int cnt = min(nthr, n - b * nthr);
+    const Rec* bb = buf + bi * nthr;
+    if (tid < cnt) s_mask[tid] = ok ? warp_block_mask(bb[tid], tile_x0, tile_y0, fr.tile_w, nwarps) : 0u;
+    __syncthreads();
     if (ok) {
-      const Rec* bb = buf + bi * nthr;
       for (int j = cnt - 1; j >= 0; --j) {
+        if (!(s_mask[j] & wbit)) continue;  // warp-uniform: no pixel of this warp sees splat j
         const uint32_t pos = (uint32_t)(b * nthr + j);
         const Rec r = bb[j];
         const float dx = __fsub_rn(r.a.x, pxc), dy = __fsub_rn(r.a.y, pyc);
@@ -605,13 +667,6 @@ TileGrid tile_grid(gs_frame fr) {
   return g;
 }
 
-bool frame_ok(gs_frame fr) {
-  auto pow2 = [](int v) { return v > 0 && (v & (v - 1)) == 0; };
-  const int tt = fr.tile_w * fr.tile_h;
-  return fr.n_views >= 1 && fr.width >= 1 && fr.height >= 1 && pow2(fr.tile_w) && pow2(fr.tile_h) &&
-         (tt == 64 || tt == 128 || tt == 256);
-}
-
 template <class F>
 cudaError_t allow_smem(F* f, size_t bytes) {
   return cudaFuncSetAttribute((const void*)f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
@@ -622,10 +677,10 @@ gs_status launch_fwd(const gs_projected* proj, const gs_sorted* sorted, int n_pa
                      float* final_T, uint32_t* n_contrib, float* image_tan, int32_t* status, cudaStream_t st) {
   const TileGrid g = tile_grid(fr);
   const int nthr = fr.tile_w * fr.tile_h;
-  const size_t smem = 16 + (size_t)2 * nthr * sizeof(Rec) * (1 + NU);
+  const size_t smem = 16 + (size_t)nthr * (2 * sizeof(Rec) * (1 + NU) + sizeof(uint32_t));
   static bool attr = false;
   if (!attr) {
-    if (allow_smem(raster_fwd_kernel<NU>, 16 + (size_t)2 * 256 * sizeof(Rec) * (1 + NU)) != cudaSuccess)
+    if (allow_smem(raster_fwd_kernel<NU>, 16 + (size_t)256 * (2 * sizeof(Rec) * (1 + NU) + sizeof(uint32_t))) != cudaSuccess)
       return check_launch("gs_raster_fwd: smem attribute");
     attr = true;
   }
@@ -648,7 +703,7 @@ void launch_bwd_kernels(const gs_params* x, const gs_camera* cams, const gs_proj
                         float* grad, float* hz, float* loss_out, float* cot, int32_t* status, cudaStream_t st) {
   const TileGrid g = tile_grid(fr);
   const int nthr = fr.tile_w * fr.tile_h;
-  const size_t smem = 16 + (size_t)2 * nthr * (sizeof(Rec) + sizeof(uint32_t));
+  const size_t smem = 16 + (size_t)nthr * (2 * sizeof(Rec) + 3 * sizeof(uint32_t));
   const float inv_m = (float)(1.0 / (3.0 * (double)fr.width * fr.height * fr.n_views));
   const unsigned blocks = (unsigned)((size_t)fr.n_views * g.T);
   raster_bwd_kernel<NU, GRAD><<<blocks, nthr, smem, st>>>(
