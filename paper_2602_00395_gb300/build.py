@@ -48,18 +48,21 @@ def _stale(target: str, deps: list[str]) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra_flags=(), out: str = LIB, build_dir: str = BUILD) -> str:
+    """Compile csrc/*.cu (changed files only) and link `out`.  `extra_flags` are
+    appended to every nvcc compile (e.g. -D tuning macros); use a separate
+    `build_dir` for each flag set."""
+    os.makedirs(build_dir, exist_ok=True)
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")]
     headers.append(os.path.join(INCLUDE, "gs3dtr.h"))
     srcs = sources()
-    objs = [os.path.join(BUILD, os.path.basename(s)[:-3] + ".o") for s in srcs]
+    objs = [os.path.join(build_dir, os.path.basename(s)[:-3] + ".o") for s in srcs]
     todo = [(s, o) for s, o in zip(srcs, objs) if force or _stale(o, [s] + headers)]
     cc = nvcc()
 
     def compile_one(so):
         s, o = so
-        cmd = [cc, *ARCH, *NVCC_FLAGS, "-c", s, "-o", o]
+        cmd = [cc, *ARCH, *NVCC_FLAGS, *extra_flags, "-c", s, "-o", o]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {os.path.basename(s)}:\n{r.stderr}")
@@ -70,15 +73,15 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if todo:
         with cf.ThreadPoolExecutor(max_workers=min(len(todo), os.cpu_count() or 4)) as ex:
             list(ex.map(compile_one, todo))
-    if force or todo or _stale(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+    if force or todo or _stale(out, objs):
+        tmp = out + f".tmp{os.getpid()}"
         cmd = [cc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs,
                "-Xlinker", "-rpath," + cuda_lib_dir()]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link of libgs3dtr.so failed:\n{r.stderr}")
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, out)
+    return out
 
 
 if __name__ == "__main__":

@@ -172,29 +172,72 @@ void exclusive_scan(const uint32_t* in, uint32_t* out, size_t n_max, const uint3
 }
 
 // ------------------------------------------------------------------- emit
+// One warp emits the pairs of 32 consecutive records.  Their output ranges are
+// contiguous (the offsets are an exclusive scan in record order), so the warp
+// writes its whole range with consecutive lanes on consecutive pairs; each lane
+// finds the record that owns its pair by a binary search over the warp's
+// prefix sums.
 __global__ void emit_kernel(const float4* __restrict__ rec, int n_pad, gs_frame fr, int Tx, int Ty,
                             const uint32_t* __restrict__ offsets, uint64_t capacity, uint64_t* __restrict__ keys,
                             uint32_t* __restrict__ vals) {
+  const size_t G = (size_t)fr.n_views * n_pad;
   const size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= (size_t)fr.n_views * n_pad) return;
-  const float4 c = rec[3 * g + 2];
-  const int r = __float_as_int(c.z);
-  if (r <= 0) return;
-  const float4 a = rec[3 * g + 0];
-  int x0, x1, y0, y1;
-  tile_rect(a.x, a.y, r, fr.tile_w, fr.tile_h, Tx, Ty, x0, x1, y0, y1);
-  const int view = (int)(g / n_pad);
-  const uint32_t splat = (uint32_t)(g - (size_t)view * n_pad);
-  const uint64_t tiles = (uint64_t)Tx * Ty;
-  const uint64_t depth_bits = (uint64_t)__float_as_uint(c.y);
-  uint64_t p = offsets[g];
-  for (int ty = y0; ty < y1; ++ty)
-    for (int tx = x0; tx < x1; ++tx, ++p) {
-      if (p >= capacity) return;
-      const uint64_t tile = (uint64_t)view * tiles + (uint64_t)ty * Tx + tx;
-      keys[p] = (tile << 32) | depth_bits;
-      vals[p] = splat;
+  const size_t g0 = g - (threadIdx.x & 31);
+  if (g0 >= G) return;  // whole warp
+  const int lane = threadIdx.x & 31;
+  int x0 = 0, x1 = 0, y0 = 0, y1 = 0;
+  uint32_t cnt = 0, depth_bits = 0;
+  if (g < G) {
+    const float4 c = rec[3 * g + 2];
+    const int r = __float_as_int(c.z);
+    if (r > 0) {
+      const float4 a = rec[3 * g + 0];
+      tile_rect(a.x, a.y, r, fr.tile_w, fr.tile_h, Tx, Ty, x0, x1, y0, y1);
+      cnt = (uint32_t)max(0, x1 - x0) * (uint32_t)max(0, y1 - y0);
     }
+    depth_bits = __float_as_uint(c.y);
+  }
+  // inclusive warp scan of the counts
+  uint32_t incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  const uint32_t start = incl - cnt;
+  const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+  const uint64_t base = offsets[g0];
+  const uint64_t tiles = (uint64_t)Tx * Ty;
+  const uint32_t rounds = (total + 31) / 32;
+  for (uint32_t rd = 0; rd < rounds; ++rd) {
+    const uint32_t p = rd * 32 + lane;
+    // owner = largest lane whose start <= p (lanes with no pairs never win over the next lane)
+    int lo = 0;
+#pragma unroll
+    for (int step = 16; step >= 1; step >>= 1) {
+      const int cand = lo + step;
+      const uint32_t sc = __shfl_sync(0xffffffffu, start, cand & 31);
+      if (cand < 32 && sc <= p) lo = cand;
+    }
+    const uint32_t o_start = __shfl_sync(0xffffffffu, start, lo);
+    const int ox0 = __shfl_sync(0xffffffffu, x0, lo);
+    const int ox1 = __shfl_sync(0xffffffffu, x1, lo);
+    const int oy0 = __shfl_sync(0xffffffffu, y0, lo);
+    const uint32_t od = __shfl_sync(0xffffffffu, depth_bits, lo);
+    if (p < total) {
+      const uint64_t at = base + p;
+      if (at < capacity) {
+        const size_t og = g0 + (size_t)lo;
+        const int oview = (int)(og / n_pad);
+        const uint32_t q = p - o_start;
+        const uint32_t w = (uint32_t)(ox1 - ox0);
+        const uint32_t tyy = (uint32_t)oy0 + q / w, txx = (uint32_t)ox0 + q % w;
+        const uint64_t tile = (uint64_t)oview * tiles + (uint64_t)tyy * Tx + txx;
+        keys[at] = (tile << 32) | (uint64_t)od;
+        vals[at] = (uint32_t)(og - (size_t)oview * n_pad);
+      }
+    }
+  }
 }
 
 // ------------------------------------------------------------ radix passes
@@ -218,11 +261,17 @@ __global__ void __launch_bounds__(kRadixThreads) radix_hist_kernel(const uint64_
   s_cnt[threadIdx.x] = 0;
   __syncthreads();
   {
-#pragma unroll 4
+    uint64_t kk[kRadixItems];
+#pragma unroll
+    for (int k = 0; k < kRadixItems; ++k) {
+      const size_t idx = base + (size_t)k * kRadixThreads + threadIdx.x;
+      kk[k] = idx < P ? keys[idx] : 0ull;
+    }
+#pragma unroll
     for (int k = 0; k < kRadixItems; ++k) {
       const size_t idx = base + (size_t)k * kRadixThreads + threadIdx.x;
       const bool ok = idx < P;
-      const uint32_t d = ok ? (uint32_t)(keys[idx] >> shift) & 255u : 256u;
+      const uint32_t d = ok ? (uint32_t)(kk[k] >> shift) & 255u : 256u;
       const uint32_t peers = __match_any_sync(0xffffffffu, d);
       if (ok && (peers & lanemask_lt()) == 0) atomicAdd(&s_cnt[d], (uint32_t)__popc(peers));
     }
@@ -255,12 +304,17 @@ __global__ void __launch_bounds__(kRadixThreads) radix_scatter_kernel(
   uint64_t key[kRadixItems];
   uint32_t vv[kRadixItems];
   uint32_t rank[kRadixItems];
+  // all loads first, so that they are in flight together
+#pragma unroll
+  for (int k = 0; k < kRadixItems; ++k) {
+    const size_t idx = base + (size_t)k * kRadixThreads + tid;
+    key[k] = idx < P ? kin[idx] : 0ull;
+    vv[k] = idx < P ? vin[idx] : 0u;
+  }
 #pragma unroll
   for (int k = 0; k < kRadixItems; ++k) {
     const size_t idx = base + (size_t)k * kRadixThreads + tid;
     const bool ok = idx < P;
-    key[k] = ok ? kin[idx] : 0ull;
-    vv[k] = ok ? vin[idx] : 0u;
     const uint32_t d = ok ? (uint32_t)(key[k] >> shift) & 255u : 256u;
     const uint32_t peers = __match_any_sync(0xffffffffu, d);
     const uint32_t below = (uint32_t)__popc(peers & lt);

@@ -159,9 +159,15 @@ __global__ void __launch_bounds__(256) raster_fwd_kernel(const float4* __restric
     }
     __syncthreads();
     if (!ok) done = true;
-    if (!done) {
-      for (int j = 0; j < cnt; ++j) {
-        if (!(s_mask[j] & wbit)) continue;  // warp-uniform
+    // The warp walks only the splats its block can see: one ballot per 32
+    // splats, then the set bits in list order.
+    const int lane = tid & 31;
+    for (int j0 = 0; j0 < cnt && !__all_sync(0xffffffffu, done); j0 += 32) {
+      uint32_t bits = __ballot_sync(0xffffffffu, j0 + lane < cnt && (s_mask[j0 + lane] & wbit));
+      while (bits) {
+        const int j = j0 + __ffs(bits) - 1;
+        bits &= bits - 1;
+        if (done) continue;
         const Rec r = bb[j];
         const float dx = __fsub_rn(r.a.x, pxc), dy = __fsub_rn(r.a.y, pyc);
         const float power = splat_power(r, dx, dy);
@@ -173,7 +179,7 @@ __global__ void __launch_bounds__(256) raster_fwd_kernel(const float4* __restric
         const float Tn = Tr * (1.f - alpha);
         if (Tn < kTMin) {
           done = true;
-          break;
+          continue;
         }
         const float w = alpha * Tr;
         if constexpr (NU > 0) {
@@ -253,8 +259,19 @@ __device__ __forceinline__ float warp_reduce_scatter16(float (&v)[32]) {
   return v[0];
 }
 
+// Minimum resident CTAs per SM requested from the compiler for the reverse
+// kernel (0: no request).
+#ifndef GS_BWD_MIN_BLOCKS
+#define GS_BWD_MIN_BLOCKS 0
+#endif
+#if GS_BWD_MIN_BLOCKS > 0
+#define GS_BWD_BOUNDS __launch_bounds__(256, GS_BWD_MIN_BLOCKS)
+#else
+#define GS_BWD_BOUNDS __launch_bounds__(256)
+#endif
+
 template <int NU, bool GRAD>
-__global__ void __launch_bounds__(256) raster_bwd_kernel(
+__global__ void GS_BWD_BOUNDS raster_bwd_kernel(
     const float4* __restrict__ rec, const uint32_t* __restrict__ vals, const uint32_t* __restrict__ ranges,
     int n_pad, gs_frame fr, int Tx, int T, const float* __restrict__ image, const float* __restrict__ target,
     const float* __restrict__ final_T, const uint32_t* __restrict__ n_contrib, const float* __restrict__ image_tan,
@@ -323,6 +340,7 @@ __global__ void __launch_bounds__(256) raster_bwd_kernel(
   }
   __syncthreads();
   if (nc) atomicMax(&s_max, nc);
+  const uint32_t warp_nc = __reduce_max_sync(0xffffffffu, nc);  // list positions this warp still needs
   // objective: warp then block reduction, one atomic per CTA
   if (loss_out) {
     float lsum = lossp;
@@ -356,9 +374,15 @@ __global__ void __launch_bounds__(256) raster_bwd_kernel(
     const Rec* bb = buf + bi * nthr;
     if (tid < cnt) s_mask[tid] = ok ? warp_block_mask(bb[tid], tile_x0, tile_y0, fr.tile_w, nwarps) : 0u;
     __syncthreads();
-    if (ok) {
-      for (int j = cnt - 1; j >= 0; --j) {
-        if (!(s_mask[j] & wbit)) continue;  // warp-uniform: no pixel of this warp sees splat j
+    // the warp walks, back to front, only the splats its block can see and
+    // that lie before its last contributor: one ballot per 32 splats
+    for (int j0 = ((cnt - 1) & ~31); ok && j0 >= 0; j0 -= 32) {
+      const int jl = j0 + lane;
+      uint32_t bits = __ballot_sync(0xffffffffu, jl < cnt && (uint32_t)(b * nthr + jl) < warp_nc && (s_mask[jl] & wbit));
+      while (bits) {
+        const int hb = 31 - __clz(bits);
+        bits &= ~(1u << hb);
+        const int j = j0 + hb;
         const uint32_t pos = (uint32_t)(b * nthr + j);
         const Rec r = bb[j];
         const float dx = __fsub_rn(r.a.x, pxc), dy = __fsub_rn(r.a.y, pyc);
@@ -423,30 +447,65 @@ __global__ void __launch_bounds__(256) raster_bwd_kernel(
 
 // ------------------------------------------------ projection reverse pass
 // Reverse pass of the EWA projection and SH colour for one Gaussian, summed over
-// views; thread (i, s) handles cotangent stream s.  The chain rule, written out:
+// views.  The chain rule, written out:
 //   conic = Sigma'^-1:   dA/da = -c^2/det^2, dA/db = 2bc/det^2, dA/dc = 1/det - ac/det^2,
 //                        dB/da = bc/det^2, dB/db = -1/det - 2b^2/det^2, dB/dc = ab/det^2,
 //                        dC/da = 1/det - ac/det^2, dC/db = 2ab/det^2, dC/dc = -a^2/det^2
 //   Sigma' = J Sc J^T:   dSc = J^T Gs J, dJ = 2 Gs J Sc, Gs = [[ga, gb/2], [gb/2, gc]]
-//   J(t):                slope clamp cuts the t_x (t_y) path, J02 = -fx uc / tz
+//   J(t):                the slope clamp cuts the t_x (t_y) path, J02 = -fx uc / tz
 //   Sc = W Sigma W^T:    dSigma = W^T dSc W;   mean2D(t) and t = W mu + t_w
 //   Sigma = M M^T:       dM = 2 dSigma M, M = R diag(s), s = exp(log s)
 //   R(q / |q|):          dq = (dqn - qn (qn . dqn)) / |q|
 //   colour:              dSH_k = Y_k dc (0 where clamped), dmu += P_perp grad_Y . (sum sh dc) / |d|
+// A block holds all cotangent streams (threadIdx.y) of 64 Gaussians so that
+// their shared parameter and cotangent reads hit L1.  Each thread sums over the
+// views twice: first the geometric rows, then the SH rows, which keeps few
+// accumulators alive at a time.  The probe streams are combined in shared
+// memory into hz = (1/nu) sum_k z_k . (G z_k).
+constexpr int kPbwdX = 64;
+
+struct ViewGeom {
+  float Rc[3][3], tc[3], fx, fy;
+};
+
+__device__ __forceinline__ void load_view(const gs_camera* cam, ViewGeom& v) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+#pragma unroll
+    for (int b = 0; b < 3; ++b) v.Rc[a][b] = cam->viewmat[4 * a + b];
+    v.tc[a] = cam->viewmat[4 * a + 3];
+  }
+  v.fx = cam->fx;
+  v.fy = cam->fy;
+}
+
+// Unit view direction and distance from the camera centre to mu.
+__device__ __forceinline__ void view_direction(const ViewGeom& v, const float mu[3], float d[3], float& dn) {
+  float cp[3];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) cp[q] = -(v.Rc[0][q] * v.tc[0] + v.Rc[1][q] * v.tc[1] + v.Rc[2][q] * v.tc[2]);
+  const float d0 = mu[0] - cp[0], d1 = mu[1] - cp[1], d2 = mu[2] - cp[2];
+  dn = sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+  d[0] = d0 / dn;
+  d[1] = d1 / dn;
+  d[2] = d2 / dn;
+}
+
 template <int DEG, int NU, bool GRAD>
-__global__ void __launch_bounds__(128) project_bwd_kernel(const float* __restrict__ P, int n, int n_pad,
-                                                          const gs_camera* __restrict__ cams, gs_frame fr,
-                                                          const float* __restrict__ cot, uint64_t seed, int64_t step,
-                                                          float* __restrict__ grad, float* __restrict__ hz) {
+__global__ void __launch_bounds__(kPbwdX * ((GRAD ? 1 : 0) + NU)) project_bwd_kernel(
+    const float* __restrict__ P, int n, int n_pad, const gs_camera* __restrict__ cams, gs_frame fr,
+    const float* __restrict__ cot, uint64_t seed, int64_t step, float* __restrict__ grad, float* __restrict__ hz) {
   constexpr int S = (GRAD ? 1 : 0) + NU;
   constexpr int NV = 9 * S;
   constexpr int K = (DEG + 1) * (DEG + 1);
   constexpr int ROWS = kRowSH + 3 * K;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int s = blockIdx.y;
-  if (i >= n) return;
-  auto ld = [&](int r) { return __ldg(P + (size_t)r * n_pad + i); };
-  const float mu[3] = {ld(0), ld(1), ld(2)};
+  __shared__ float s_hz[NU == 2 ? kPbwdX : 1][NU == 2 ? ROWS : 1];
+  const int i = blockIdx.x * kPbwdX + threadIdx.x;
+  const int s = threadIdx.y;
+  const bool active = i < n;
+  const int ii = active ? i : 0;
+  auto ld = [&](int r) { return __ldg(P + (size_t)r * n_pad + ii); };
+  float mu[3] = {ld(0), ld(1), ld(2)};
   float qx = ld(6), qy = ld(7), qz = ld(8), qw = ld(9);
   const float qlen = sqrtf(qx * qx + qy * qy + qz * qz + qw * qw);
   qx /= qlen; qy /= qlen; qz /= qlen; qw /= qlen;
@@ -473,14 +532,11 @@ __global__ void __launch_bounds__(128) project_bwd_kernel(const float* __restric
     for (int b = 0; b < 3; ++b) Sg[a][b] = M[a][0] * M[b][0] + M[a][1] * M[b][1] + M[a][2] * M[b][2];
   const float opac = 1.f / (1.f + expf(-ld(10)));
 
+  // ---- pass 1: geometric rows
   float g_mu[3] = {0.f, 0.f, 0.f};
   float g_S[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
   float g_ol = 0.f;
-  float g_sh[K][3];
-#pragma unroll
-  for (int k = 0; k < K; ++k) g_sh[k][0] = g_sh[k][1] = g_sh[k][2] = 0.f;
-
-  for (int v = 0; v < fr.n_views; ++v) {
+  for (int v = 0; active && v < fr.n_views; ++v) {
     const float* cv = cot + ((size_t)v * n_pad + i) * NV + 9 * s;
     float c[9];
     bool any = false;
@@ -490,26 +546,20 @@ __global__ void __launch_bounds__(128) project_bwd_kernel(const float* __restric
       any = any || (c[q] != 0.f);
     }
     if (!any) continue;
-    const gs_camera* cam = cams + v;
-    float Rc[3][3], tc[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-#pragma unroll
-      for (int b = 0; b < 3; ++b) Rc[a][b] = cam->viewmat[4 * a + b];
-      tc[a] = cam->viewmat[4 * a + 3];
-    }
-    const float fx = cam->fx, fy = cam->fy;
+    ViewGeom vg;
+    load_view(cams + v, vg);
+    const float fx = vg.fx, fy = vg.fy;
     float t[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) t[a] = Rc[a][0] * mu[0] + Rc[a][1] * mu[1] + Rc[a][2] * mu[2] + tc[a];
+    for (int a = 0; a < 3; ++a) t[a] = vg.Rc[a][0] * mu[0] + vg.Rc[a][1] * mu[1] + vg.Rc[a][2] * mu[2] + vg.tc[a];
     float Sc[3][3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       float tmp[3];
 #pragma unroll
-      for (int b = 0; b < 3; ++b) tmp[b] = Rc[a][0] * Sg[0][b] + Rc[a][1] * Sg[1][b] + Rc[a][2] * Sg[2][b];
+      for (int b = 0; b < 3; ++b) tmp[b] = vg.Rc[a][0] * Sg[0][b] + vg.Rc[a][1] * Sg[1][b] + vg.Rc[a][2] * Sg[2][b];
 #pragma unroll
-      for (int b = 0; b < 3; ++b) Sc[a][b] = tmp[0] * Rc[b][0] + tmp[1] * Rc[b][1] + tmp[2] * Rc[b][2];
+      for (int b = 0; b < 3; ++b) Sc[a][b] = tmp[0] * vg.Rc[b][0] + tmp[1] * vg.Rc[b][1] + tmp[2] * vg.Rc[b][2];
     }
     const float limx = kSlopeClamp * 0.5f * (float)fr.width / fx;
     const float limy = kSlopeClamp * 0.5f * (float)fr.height / fy;
@@ -523,12 +573,10 @@ __global__ void __launch_bounds__(128) project_bwd_kernel(const float* __restric
     const float cc = J11 * J11 * Sc[1][1] + 2.f * J11 * J12 * Sc[1][2] + J12 * J12 * Sc[2][2] + kDilation;
     const float det = a * cc - bb * bb;
     const float idet = 1.f / det, id2 = idet * idet;
-    // conic -> Sigma' entries
     const float gA = c[2], gB = c[3], gC = c[4];
     const float ga = gA * (-cc * cc * id2) + gB * (bb * cc * id2) + gC * (idet - a * cc * id2);
     const float gb = gA * (2.f * bb * cc * id2) + gB * (-idet - 2.f * bb * bb * id2) + gC * (2.f * a * bb * id2);
     const float gc = gA * (idet - a * cc * id2) + gB * (a * bb * id2) + gC * (-a * a * id2);
-    // Sigma' = J Sc J^T
     const float j0[3] = {J00, 0.f, J02}, j1[3] = {0.f, J11, J12};
     float gSc[3][3];
 #pragma unroll
@@ -554,60 +602,73 @@ __global__ void __launch_bounds__(128) project_bwd_kernel(const float* __restric
             gJ02 * (clx ? fx * uc * itz2 : 2.f * fx * t[0] * itz3) +
             gJ12 * (cly ? fy * vc * itz2 : 2.f * fy * t[1] * itz3);
 #pragma unroll
-    for (int q = 0; q < 3; ++q) g_mu[q] += Rc[0][q] * gt[0] + Rc[1][q] * gt[1] + Rc[2][q] * gt[2];
-    // Sigma: W^T gSc W
+    for (int q = 0; q < 3; ++q) g_mu[q] += vg.Rc[0][q] * gt[0] + vg.Rc[1][q] * gt[1] + vg.Rc[2][q] * gt[2];
 #pragma unroll
     for (int p = 0; p < 3; ++p) {
       float tmp[3];
 #pragma unroll
-      for (int q = 0; q < 3; ++q) tmp[q] = Rc[0][p] * gSc[0][q] + Rc[1][p] * gSc[1][q] + Rc[2][p] * gSc[2][q];
+      for (int q = 0; q < 3; ++q) tmp[q] = vg.Rc[0][p] * gSc[0][q] + vg.Rc[1][p] * gSc[1][q] + vg.Rc[2][p] * gSc[2][q];
 #pragma unroll
-      for (int q = 0; q < 3; ++q) g_S[p][q] += tmp[0] * Rc[0][q] + tmp[1] * Rc[1][q] + tmp[2] * Rc[2][q];
+      for (int q = 0; q < 3; ++q) g_S[p][q] += tmp[0] * vg.Rc[0][q] + tmp[1] * vg.Rc[1][q] + tmp[2] * vg.Rc[2][q];
     }
-    // opacity
     g_ol += c[5] * opac * (1.f - opac);
-    // colour
-    float cp[3];
-#pragma unroll
-    for (int q = 0; q < 3; ++q) cp[q] = -(Rc[0][q] * tc[0] + Rc[1][q] * tc[1] + Rc[2][q] * tc[2]);
-    const float d0r = mu[0] - cp[0], d1r = mu[1] - cp[1], d2r = mu[2] - cp[2];
-    const float dn = sqrtf(d0r * d0r + d1r * d1r + d2r * d2r);
-    const float d0 = d0r / dn, d1 = d1r / dn, d2 = d2r / dn;
-    float Y[K];
-    sh_basis<DEG>(d0, d1, d2, Y);
-    float gcol[3];
-#pragma unroll
-    for (int ch = 0; ch < 3; ++ch) {
-      float raw = 0.5f;
-#pragma unroll
-      for (int k = 0; k < K; ++k) raw += Y[k] * ld(kRowSH + 3 * k + ch);
-      gcol[ch] = raw < 0.f ? 0.f : c[6 + ch];
-    }
-#pragma unroll
-    for (int k = 0; k < K; ++k)
-#pragma unroll
-      for (int ch = 0; ch < 3; ++ch) g_sh[k][ch] += Y[k] * gcol[ch];
     if constexpr (DEG > 0) {
+      // the colour depends on mu through the view direction
+      float d[3], dn;
+      view_direction(vg, mu, d, dn);
+      float Y[K];
+      sh_basis<DEG>(d[0], d[1], d[2], Y);
+      float gcol[3];
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) {
+        float raw = 0.5f;
+#pragma unroll
+        for (int k = 0; k < K; ++k) raw += Y[k] * ld(kRowSH + 3 * k + ch);
+        gcol[ch] = raw < 0.f ? 0.f : c[6 + ch];
+      }
       float wk[K];
 #pragma unroll
       for (int k = 0; k < K; ++k)
         wk[k] = ld(kRowSH + 3 * k + 0) * gcol[0] + ld(kRowSH + 3 * k + 1) * gcol[1] + ld(kRowSH + 3 * k + 2) * gcol[2];
       float gd[3];
-      sh_basis_grad<DEG>(d0, d1, d2, wk, gd);
-      const float dot = gd[0] * d0 + gd[1] * d1 + gd[2] * d2;
-      g_mu[0] += (gd[0] - d0 * dot) / dn;
-      g_mu[1] += (gd[1] - d1 * dot) / dn;
-      g_mu[2] += (gd[2] - d2 * dot) / dn;
+      sh_basis_grad<DEG>(d[0], d[1], d[2], wk, gd);
+      const float dot = gd[0] * d[0] + gd[1] * d[1] + gd[2] * d[2];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) g_mu[q] += (gd[q] - d[q] * dot) / dn;
     }
   }
-  // Sigma = M M^T, M = R diag(s)
+  // ---- pass 2: SH rows
+  float g_sh[K][3];
+#pragma unroll
+  for (int k = 0; k < K; ++k) g_sh[k][0] = g_sh[k][1] = g_sh[k][2] = 0.f;
+  for (int v = 0; active && v < fr.n_views; ++v) {
+    const float* cv = cot + ((size_t)v * n_pad + i) * NV + 9 * s;
+    const float c6 = cv[6], c7 = cv[7], c8 = cv[8];
+    if (c6 == 0.f && c7 == 0.f && c8 == 0.f) continue;
+    ViewGeom vg;
+    load_view(cams + v, vg);
+    float d[3], dn;
+    view_direction(vg, mu, d, dn);
+    float Y[K];
+    sh_basis<DEG>(d[0], d[1], d[2], Y);
+    const float cin[3] = {c6, c7, c8};
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+      float raw = 0.5f;
+#pragma unroll
+      for (int k = 0; k < K; ++k) raw += Y[k] * ld(kRowSH + 3 * k + ch);
+      const float gcol = raw < 0.f ? 0.f : cin[ch];
+#pragma unroll
+      for (int k = 0; k < K; ++k) g_sh[k][ch] += Y[k] * gcol;
+    }
+  }
+  // ---- Sigma = M M^T, M = R diag(s);  R(q / |q|)
   float gM[3][3];
 #pragma unroll
   for (int a = 0; a < 3; ++a)
 #pragma unroll
     for (int b = 0; b < 3; ++b) gM[a][b] = 2.f * (g_S[a][0] * M[0][b] + g_S[a][1] * M[1][b] + g_S[a][2] * M[2][b]);
-  float g_ls[3];
-  float gR[3][3];
+  float g_ls[3], gR[3][3];
 #pragma unroll
   for (int b = 0; b < 3; ++b) {
     g_ls[b] = (gM[0][b] * R[0][b] + gM[1][b] * R[1][b] + gM[2][b] * R[2][b]) * sc[b];
@@ -626,31 +687,41 @@ __global__ void __launch_bounds__(128) project_bwd_kernel(const float* __restric
           2.f * x * gR[2][1];
   const float qd = gq[0] * x + gq[1] * y + gq[2] * z + gq[3] * ww;
   const float qn[4] = {x, y, z, ww};
-
-  // scatter the rows: stream 0 (with GRAD) is the gradient, the others the
-  // probe products, averaged over the probes after multiplying by z_k
-  float rowv[ROWS];
-  rowv[0] = g_mu[0]; rowv[1] = g_mu[1]; rowv[2] = g_mu[2];
-  rowv[3] = g_ls[0]; rowv[4] = g_ls[1]; rowv[5] = g_ls[2];
-#pragma unroll
-  for (int c = 0; c < 4; ++c) rowv[6 + c] = (gq[c] - qn[c] * qd) / qlen;
-  rowv[10] = g_ol;
-#pragma unroll
-  for (int k = 0; k < K; ++k)
-#pragma unroll
-    for (int ch = 0; ch < 3; ++ch) rowv[kRowSH + 3 * k + ch] = g_sh[k][ch];
+  auto row_value = [&](int r) -> float {
+    if (r < 3) return g_mu[r];
+    if (r < 6) return g_ls[r - 3];
+    if (r < 10) return (gq[r - 6] - qn[r - 6] * qd) / qlen;
+    if (r == 10) return g_ol;
+    return g_sh[(r - kRowSH) / 3][(r - kRowSH) % 3];
+  };
+  // ---- scatter: the gradient stream writes grad; probe streams write z_k . v / nu
   if (GRAD && s == 0) {
+    if (active) {
 #pragma unroll
-    for (int r = 0; r < ROWS; ++r) grad[(size_t)r * n_pad + i] = rowv[r];
-  } else {
+      for (int r = 0; r < ROWS; ++r) grad[(size_t)r * n_pad + i] = row_value(r);
+    }
+  }
+  if constexpr (NU > 0) {
     const int k = s - (GRAD ? 1 : 0);
     const float inv_nu = 1.f / (float)NU;
-#pragma unroll 4
-    for (int r = 0; r < ROWS; ++r) {
-      const bool neg = probe_negative(seed, step, k, (uint64_t)r * (uint64_t)n + (uint64_t)i);
-      const float val = (neg ? -rowv[r] : rowv[r]) * inv_nu;
-      if (NU == 1) hz[(size_t)r * n_pad + i] = val;
-      else atomicAdd(hz + (size_t)r * n_pad + i, val);
+    if (NU == 2 && k == 1 && active) {
+#pragma unroll
+      for (int r = 0; r < ROWS; ++r) {
+        const bool neg = probe_negative(seed, step, 1, (uint64_t)r * (uint64_t)n + (uint64_t)i);
+        const float v = row_value(r) * inv_nu;
+        s_hz[NU == 2 ? threadIdx.x : 0][NU == 2 ? r : 0] = neg ? -v : v;
+      }
+    }
+    if (NU == 2) __syncthreads();
+    if (k == 0 && active) {
+#pragma unroll
+      for (int r = 0; r < ROWS; ++r) {
+        const bool neg = probe_negative(seed, step, 0, (uint64_t)r * (uint64_t)n + (uint64_t)i);
+        const float v = row_value(r) * inv_nu;
+        float out = neg ? -v : v;
+        if (NU == 2) out += s_hz[NU == 2 ? threadIdx.x : 0][NU == 2 ? r : 0];
+        hz[(size_t)r * n_pad + i] = out;
+      }
     }
   }
 }
@@ -710,14 +781,15 @@ void launch_bwd_kernels(const gs_params* x, const gs_camera* cams, const gs_proj
       reinterpret_cast<const float4*>(proj->rec), sorted->vals, sorted->ranges, x->n_pad, fr, g.Tx, g.T, image,
       target, final_T, n_contrib, image_tan, loss.kind, loss.gn_floor, inv_m, cot, loss_out, status);
   constexpr int S = (GRAD ? 1 : 0) + NU;
-  const dim3 pg((x->n + 127) / 128, S);
+  const dim3 pg((x->n + kPbwdX - 1) / kPbwdX), pb(kPbwdX, S);
   const uint64_t seed = probe ? probe->seed : 0;
   const int64_t t = probe ? probe->t : 0;
+  if (x->n == 0) return;
   switch (x->sh_degree) {
-    case 0: project_bwd_kernel<0, NU, GRAD><<<pg, 128, 0, st>>>(x->data, x->n, x->n_pad, cams, fr, cot, seed, t, grad, hz); break;
-    case 1: project_bwd_kernel<1, NU, GRAD><<<pg, 128, 0, st>>>(x->data, x->n, x->n_pad, cams, fr, cot, seed, t, grad, hz); break;
-    case 2: project_bwd_kernel<2, NU, GRAD><<<pg, 128, 0, st>>>(x->data, x->n, x->n_pad, cams, fr, cot, seed, t, grad, hz); break;
-    default: project_bwd_kernel<3, NU, GRAD><<<pg, 128, 0, st>>>(x->data, x->n, x->n_pad, cams, fr, cot, seed, t, grad, hz); break;
+    case 0: project_bwd_kernel<0, NU, GRAD><<<pg, pb, 0, st>>>(x->data, x->n, x->n_pad, cams, fr, cot, seed, t, grad, hz); break;
+    case 1: project_bwd_kernel<1, NU, GRAD><<<pg, pb, 0, st>>>(x->data, x->n, x->n_pad, cams, fr, cot, seed, t, grad, hz); break;
+    case 2: project_bwd_kernel<2, NU, GRAD><<<pg, pb, 0, st>>>(x->data, x->n, x->n_pad, cams, fr, cot, seed, t, grad, hz); break;
+    default: project_bwd_kernel<3, NU, GRAD><<<pg, pb, 0, st>>>(x->data, x->n, x->n_pad, cams, fr, cot, seed, t, grad, hz); break;
   }
 }
 
@@ -748,8 +820,6 @@ gs_status run_bwd(bool want_grad, const gs_params* x, const gs_camera* cams, gs_
   cudaStream_t st = (cudaStream_t)stream;
   float* cot = (float*)workspace;
   if (cudaMemsetAsync(cot, 0, need, st) != cudaSuccess) return check_launch(name);
-  if (nu == 2 && cudaMemsetAsync(hz->data, 0, (size_t)n_rows(x->sh_degree) * x->n_pad * sizeof(float), st) != cudaSuccess)
-    return check_launch(name);
   float* gptr = want_grad ? grad->data : nullptr;
   float* hptr = nu ? hz->data : nullptr;
   if (want_grad) {
