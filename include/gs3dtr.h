@@ -176,7 +176,7 @@ gs_status gs_bin_sort(const gs_projected* proj, int32_t n_pad, gs_frame frame, v
  * scratch from a 32 MiB device array inside the library (held on every GPU that
  * loads the library until the process exits) and allocates nothing.
  *   - Limit: gs_bin_sort_workspace_size(n_pad, frame, out->capacity) must be at
- *     most 32 MiB (about 2.3 million pairs with one million view x n_pad records);
+ *     most 32 MiB (for example about 2 million pairs with 262,144 view x n_pad records);
  *     larger requests return GS_ERR_INVALID_ARG with an explanation.
  *   - The first call on each device, with that device current, looks up the
  *     array's device address (cudaGetSymbolAddress); make it before any stream

@@ -1,19 +1,24 @@
 // gs_bin_sort: tile binning and depth order of the tile-based rasteriser
 // (Sec. 3.1 of arXiv 2602.00395).
 //
-//   count   per (view, splat): tiles of its FP32 rectangle
-//   scan    exclusive prefix sum -> emission offsets and the pair count P
-//   emit    key = (view * tiles + tile) << 32 | bits(depth), value = splat index
-//   sort    LSD radix sort over the used key bits, 8 bits per pass: a per-block
-//           digit histogram, a device-wide scan of the histograms, then a
-//           scatter that ranks each block's keys stably in shared memory and
-//           writes every digit's run contiguously.  No block waits on another.
-//   ranges  [start, end) of every tile
+// Every pair of one splat shares its depth, so the order (tile, depth, splat)
+// is built in two stages instead of sorting 64-bit pair keys on all their bits:
 //
-// Emission is in splat order and every pass is stable, so equal keys stay in
-// splat-index order: the result is the total order (key, splat index).
-// Grids are sized by the pair capacity and read P from device memory, so the
-// whole call needs no host synchronisation (and can be captured in a graph).
+//   records  per (view, splat): tiles of its FP32 rectangle; the V x n_pad
+//            records are sorted by (view, depth bits) with a stable LSD radix
+//            sort (record index order breaks ties)
+//   scan     emission offsets in that order and the pair count P
+//   emit     key = (view * tiles + tile) << 32 | bits(depth), value = splat,
+//            written in (view, depth, splat) order
+//   sort     stable LSD radix sort of the pairs on the tile bits only
+//   ranges   [start, end) of every tile
+//
+// Each radix pass is a per-block digit histogram, a device-wide scan of the
+// histograms, and a scatter that ranks each block's keys stably in shared
+// memory and writes every digit's run contiguously; no block waits on another.
+// The result is the total order (key, splat index).  Grids are sized by the
+// pair capacity and read P from device memory, so the call needs no host
+// synchronisation (and can be captured in a graph).
 #include "common.cuh"
 
 namespace gs {
@@ -33,9 +38,12 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
   return m;
 }
 
-// ------------------------------------------------------------------ count
-__global__ void count_kernel(const float4* __restrict__ rec, int n_pad, gs_frame fr, int Tx, int Ty,
-                             uint32_t* __restrict__ counts) {
+// ------------------------------------------------------------------ records
+// counts[g] = tiles of record g's rectangle; rkeys[g] = view << 32 | bits(depth);
+// rvals[g] = g.
+__global__ void record_keys_kernel(const float4* __restrict__ rec, int n_pad, gs_frame fr, int Tx, int Ty,
+                                   uint32_t* __restrict__ counts, uint64_t* __restrict__ rkeys,
+                                   uint32_t* __restrict__ rvals) {
   const size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= (size_t)fr.n_views * n_pad) return;
   const float4 a = rec[3 * g + 0];
@@ -48,6 +56,18 @@ __global__ void count_kernel(const float4* __restrict__ rec, int n_pad, gs_frame
     cnt = (uint32_t)max(0, x1 - x0) * (uint32_t)max(0, y1 - y0);
   }
   counts[g] = cnt;
+  const uint64_t view = g / (size_t)n_pad;
+  rkeys[g] = (view << 32) | (uint64_t)__float_as_uint(c.y);
+  rvals[g] = (uint32_t)g;
+}
+
+__global__ void set_u32_kernel(uint32_t* p, uint32_t v) { *p = v; }
+
+// scnt[p] = counts of the record at sorted position p
+__global__ void gather_counts_kernel(const uint32_t* __restrict__ order, const uint32_t* __restrict__ counts,
+                                     uint32_t* __restrict__ scnt, size_t items) {
+  const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < items) scnt[p] = counts[order[p]];
 }
 
 // ------------------------------------------------------------------- scan
@@ -172,26 +192,28 @@ void exclusive_scan(const uint32_t* in, uint32_t* out, size_t n_max, const uint3
 }
 
 // ------------------------------------------------------------------- emit
-// One warp emits the pairs of 32 consecutive records.  Their output ranges are
-// contiguous (the offsets are an exclusive scan in record order), so the warp
+// One warp emits the pairs of 32 consecutive records in (view, depth) order.
+// Their output ranges are contiguous (the offsets are an exclusive scan in that
+// order), so the warp
 // writes its whole range with consecutive lanes on consecutive pairs; each lane
 // finds the record that owns its pair by a binary search over the warp's
 // prefix sums.
 __global__ void emit_kernel(const float4* __restrict__ rec, int n_pad, gs_frame fr, int Tx, int Ty,
-                            const uint32_t* __restrict__ offsets, uint64_t capacity, uint64_t* __restrict__ keys,
-                            uint32_t* __restrict__ vals) {
+                            const uint32_t* __restrict__ order, const uint32_t* __restrict__ offsets,
+                            uint64_t capacity, uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
   const size_t G = (size_t)fr.n_views * n_pad;
-  const size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const size_t g0 = g - (threadIdx.x & 31);
-  if (g0 >= G) return;  // whole warp
+  const size_t p0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x;  // sorted record position
+  const size_t w0 = p0 - (threadIdx.x & 31);
+  if (w0 >= G) return;  // whole warp
   const int lane = threadIdx.x & 31;
   int x0 = 0, x1 = 0, y0 = 0, y1 = 0;
-  uint32_t cnt = 0, depth_bits = 0;
-  if (g < G) {
-    const float4 c = rec[3 * g + 2];
+  uint32_t cnt = 0, depth_bits = 0, g = 0;
+  if (p0 < G) {
+    g = order[p0];
+    const float4 c = rec[3 * (size_t)g + 2];
     const int r = __float_as_int(c.z);
     if (r > 0) {
-      const float4 a = rec[3 * g + 0];
+      const float4 a = rec[3 * (size_t)g + 0];
       tile_rect(a.x, a.y, r, fr.tile_w, fr.tile_h, Tx, Ty, x0, x1, y0, y1);
       cnt = (uint32_t)max(0, x1 - x0) * (uint32_t)max(0, y1 - y0);
     }
@@ -206,7 +228,7 @@ __global__ void emit_kernel(const float4* __restrict__ rec, int n_pad, gs_frame 
   }
   const uint32_t start = incl - cnt;
   const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-  const uint64_t base = offsets[g0];
+  const uint64_t base = offsets[w0];
   const uint64_t tiles = (uint64_t)Tx * Ty;
   const uint32_t rounds = (total + 31) / 32;
   for (uint32_t rd = 0; rd < rounds; ++rd) {
@@ -224,10 +246,11 @@ __global__ void emit_kernel(const float4* __restrict__ rec, int n_pad, gs_frame 
     const int ox1 = __shfl_sync(0xffffffffu, x1, lo);
     const int oy0 = __shfl_sync(0xffffffffu, y0, lo);
     const uint32_t od = __shfl_sync(0xffffffffu, depth_bits, lo);
+    const uint32_t og32 = __shfl_sync(0xffffffffu, g, lo);
     if (p < total) {
       const uint64_t at = base + p;
       if (at < capacity) {
-        const size_t og = g0 + (size_t)lo;
+        const size_t og = og32;
         const int oview = (int)(og / n_pad);
         const uint32_t q = p - o_start;
         const uint32_t w = (uint32_t)(ox1 - ox0);
@@ -386,31 +409,59 @@ __global__ void ranges_kernel(const uint64_t* __restrict__ keys, const uint32_t*
 inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 struct SortPlan {
-  int Tx, Ty, npass, nb_radix;
+  int Tx, Ty, rec_pass, pair_pass, nb_pairs, nb_items;
   size_t n_items;  // views x n_pad
-  size_t off_counts, off_sums, off_keys, off_vals, off_hist, total;
+  size_t off_counts, off_scnt, off_sums, off_rk0, off_rk1, off_rv0, off_rv1, off_items, off_keys, off_vals,
+      off_hist, total;
 };
+
+inline int bits_for(uint64_t v) {  // smallest b with 2^b >= v
+  int b = 0;
+  while ((1ull << b) < v) ++b;
+  return b;
+}
 
 SortPlan plan_sort(int32_t n_pad, gs_frame fr, uint64_t capacity) {
   SortPlan p;
   p.Tx = (fr.width + fr.tile_w - 1) / fr.tile_w;
   p.Ty = (fr.height + fr.tile_h - 1) / fr.tile_h;
   const uint64_t tiles = (uint64_t)fr.n_views * p.Tx * p.Ty;
-  int tile_bits = 1;
-  while ((1ull << tile_bits) < tiles) ++tile_bits;
-  p.npass = (32 + tile_bits + 7) / 8;
-  p.nb_radix = (int)((capacity + kRadixTile - 1) / kRadixTile);
+  p.pair_pass = std::max(1, (bits_for(tiles) + 7) / 8);
+  p.rec_pass = (32 + bits_for((uint64_t)fr.n_views) + 7) / 8;
   p.n_items = (size_t)fr.n_views * n_pad;
-  const size_t hist_n = (size_t)256 * p.nb_radix;
+  p.nb_pairs = (int)((capacity + kRadixTile - 1) / kRadixTile);
+  p.nb_items = (int)((p.n_items + kRadixTile - 1) / kRadixTile);
+  const size_t hist_n = (size_t)256 * std::max(p.nb_pairs, p.nb_items);
   const size_t sums_n = (size_t)std::max(scan_blocks(p.n_items), scan_blocks(hist_n)) + 1;
   size_t o = 0;
   p.off_counts = o; o += align256(p.n_items * 4);
+  p.off_scnt = o;   o += align256(p.n_items * 4);
   p.off_sums = o;   o += align256(sums_n * 4);
+  p.off_rk0 = o;    o += align256(p.n_items * 8);
+  p.off_rk1 = o;    o += align256(p.n_items * 8);
+  p.off_rv0 = o;    o += align256(p.n_items * 4);
+  p.off_rv1 = o;    o += align256(p.n_items * 4);
+  p.off_items = o;  o += 256;
   p.off_keys = o;   o += align256(capacity * 8);
   p.off_vals = o;   o += align256(capacity * 4);
   p.off_hist = o;   o += align256(hist_n * 4);
   p.total = o;
   return p;
+}
+
+// Stable LSD passes over 8-bit digits starting at `shift0`; the keys/values
+// ping-pong between buffer 0 and 1 starting in `cur`, which is updated.
+void radix_passes(uint64_t** kbuf, uint32_t** vbuf, int& cur, int npass, int shift0, const uint32_t* count_dev,
+                  uint64_t count_cap, int nb, uint32_t* hist, uint32_t* sums, cudaStream_t st) {
+  const size_t hist_n = (size_t)256 * nb;
+  for (int pass = 0; pass < npass; ++pass) {
+    const int shift = shift0 + 8 * pass;
+    radix_hist_kernel<<<nb, kRadixThreads, 0, st>>>(kbuf[cur], count_dev, count_cap, shift, hist);
+    exclusive_scan(hist, hist, hist_n, count_dev, count_cap, sums, nullptr, 0, nullptr, st);
+    radix_scatter_kernel<<<nb, kRadixThreads, 0, st>>>(kbuf[cur], vbuf[cur], kbuf[cur ^ 1], vbuf[cur ^ 1],
+                                                       count_dev, count_cap, shift, hist);
+    cur ^= 1;
+  }
 }
 
 }  // namespace
@@ -435,9 +486,9 @@ extern "C" gs_status gs_bin_sort(const gs_projected* proj, int32_t n_pad, gs_fra
   cudaStream_t st = (cudaStream_t)stream;
   char* ws = (char*)workspace;
   uint32_t* counts = (uint32_t*)(ws + p.off_counts);
+  uint32_t* scnt = (uint32_t*)(ws + p.off_scnt);
   uint32_t* sums = (uint32_t*)(ws + p.off_sums);
-  uint64_t* keys_b = (uint64_t*)(ws + p.off_keys);
-  uint32_t* vals_b = (uint32_t*)(ws + p.off_vals);
+  uint32_t* items_dev = (uint32_t*)(ws + p.off_items);
   uint32_t* hist = (uint32_t*)(ws + p.off_hist);
   const float4* rec = reinterpret_cast<const float4*>(proj->rec);
   const uint64_t T = (uint64_t)p.Tx * p.Ty;
@@ -447,22 +498,23 @@ extern "C" gs_status gs_bin_sort(const gs_projected* proj, int32_t n_pad, gs_fra
     return check_launch("gs_bin_sort: memset");
   if (p.n_items == 0) return GS_OK;
   const int eb = (int)((p.n_items + 255) / 256);
-  count_kernel<<<eb, 256, 0, st>>>(rec, n_pad, frame, p.Tx, p.Ty, counts);
-  exclusive_scan(counts, counts, p.n_items, nullptr, 0, sums, out->n_pairs, out->capacity, status, st);
+  // records sorted by (view, depth)
+  uint64_t* rk[2] = {(uint64_t*)(ws + p.off_rk0), (uint64_t*)(ws + p.off_rk1)};
+  uint32_t* rv[2] = {(uint32_t*)(ws + p.off_rv0), (uint32_t*)(ws + p.off_rv1)};
+  record_keys_kernel<<<eb, 256, 0, st>>>(rec, n_pad, frame, p.Tx, p.Ty, counts, rk[0], rv[0]);
+  set_u32_kernel<<<1, 1, 0, st>>>(items_dev, (uint32_t)p.n_items);
+  int rcur = 0;
+  radix_passes(rk, rv, rcur, p.rec_pass, 0, items_dev, p.n_items, p.nb_items, hist, sums, st);
+  // emission offsets in that order, and the pair count
+  gather_counts_kernel<<<eb, 256, 0, st>>>(rv[rcur], counts, scnt, p.n_items);
+  exclusive_scan(scnt, scnt, p.n_items, nullptr, 0, sums, out->n_pairs, out->capacity, status, st);
+  // pairs in (view, depth, splat) order, then stable passes on the tile bits;
   // the last pass must land in the caller's arrays
-  uint64_t* kbuf[2] = {out->keys, keys_b};
-  uint32_t* vbuf[2] = {out->vals, vals_b};
-  int cur = (p.npass % 2 == 0) ? 0 : 1;
-  emit_kernel<<<eb, 256, 0, st>>>(rec, n_pad, frame, p.Tx, p.Ty, counts, out->capacity, kbuf[cur], vbuf[cur]);
-  const size_t hist_n = (size_t)256 * p.nb_radix;
-  for (int pass = 0; pass < p.npass; ++pass) {
-    const int shift = 8 * pass;
-    radix_hist_kernel<<<p.nb_radix, kRadixThreads, 0, st>>>(kbuf[cur], out->n_pairs, out->capacity, shift, hist);
-    exclusive_scan(hist, hist, hist_n, out->n_pairs, out->capacity, sums, nullptr, 0, nullptr, st);
-    radix_scatter_kernel<<<p.nb_radix, kRadixThreads, 0, st>>>(kbuf[cur], vbuf[cur], kbuf[cur ^ 1], vbuf[cur ^ 1],
-                                                               out->n_pairs, out->capacity, shift, hist);
-    cur ^= 1;
-  }
+  uint64_t* kbuf[2] = {out->keys, (uint64_t*)(ws + p.off_keys)};
+  uint32_t* vbuf[2] = {out->vals, (uint32_t*)(ws + p.off_vals)};
+  int cur = (p.pair_pass % 2 == 0) ? 0 : 1;
+  emit_kernel<<<eb, 256, 0, st>>>(rec, n_pad, frame, p.Tx, p.Ty, rv[rcur], scnt, out->capacity, kbuf[cur], vbuf[cur]);
+  radix_passes(kbuf, vbuf, cur, p.pair_pass, 32, out->n_pairs, out->capacity, p.nb_pairs, hist, sums, st);
   const int rb = (int)std::min<uint64_t>((out->capacity + 255) / 256, 152 * 16);
   ranges_kernel<<<rb, 256, 0, st>>>(out->keys, out->n_pairs, out->capacity, out->ranges);
   return check_launch("gs_bin_sort");
