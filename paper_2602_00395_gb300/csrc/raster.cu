@@ -270,6 +270,58 @@ __device__ __forceinline__ float warp_reduce_scatter16(float (&v)[32]) {
 #define GS_BWD_BOUNDS __launch_bounds__(256)
 #endif
 
+// Warp sums of v[0..31] delivered as quads: afterwards every lane L with
+// (L & 3) == 0 holds in q[0..3] the warp-wide sums of v[L .. L+3].  Three
+// reduce-scatter stages (lane bits 4, 3, 2) then a butterfly over bits 1, 0.
+__device__ __forceinline__ void warp_reduce_quads32(float (&v)[32], float (&q)[4]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 16; o >= 4; o >>= 1) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < o; ++i) {
+      const float send = up ? v[i] : v[i + o];
+      const float keep = up ? v[i + o] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    float x = v[i];
+    x += __shfl_xor_sync(0xffffffffu, x, 1);
+    x += __shfl_xor_sync(0xffffffffu, x, 2);
+    q[i] = x;
+  }
+}
+// Same for v[0..15] (slots 16..31 unused): lanes L < 16 with (L & 3) == 0 hold
+// the sums of v[L .. L+3].
+__device__ __forceinline__ void warp_reduce_quads16(float (&v)[32], float (&q)[4]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], 16);
+#pragma unroll
+  for (int o = 8; o >= 4; o >>= 1) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < o; ++i) {
+      const float send = up ? v[i] : v[i + o];
+      const float keep = up ? v[i + o] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    float x = v[i];
+    x += __shfl_xor_sync(0xffffffffu, x, 1);
+    x += __shfl_xor_sync(0xffffffffu, x, 2);
+    q[i] = x;
+  }
+}
+
+// Row stride (floats) of the per-view 2-D cotangents: 9 per stream, padded to
+// whole float4s so that rows can be added and read as vectors.
+__host__ __device__ constexpr int cot_stride(int streams) { return (9 * streams + 3) & ~3; }
+
 template <int NU, bool GRAD>
 __global__ void GS_BWD_BOUNDS raster_bwd_kernel(
     const float4* __restrict__ rec, const uint32_t* __restrict__ vals, const uint32_t* __restrict__ ranges,
@@ -279,7 +331,8 @@ __global__ void GS_BWD_BOUNDS raster_bwd_kernel(
     int32_t* status) {
   constexpr int S = (GRAD ? 1 : 0) + NU;  // cotangent streams
   constexpr int NV = 9 * S;               // values per splat
-  static_assert(NV <= 32, "streams");
+  constexpr int NVP = cot_stride(S);      // their padded row stride
+  static_assert(NVP <= 32, "streams");
   extern __shared__ __align__(16) unsigned char smem[];
   const int nthr = blockDim.x;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
@@ -431,14 +484,12 @@ __global__ void GS_BWD_BOUNDS raster_bwd_kernel(
           }
         }
         const uint32_t gi = s_idx[bi * nthr + j];
-        float* dst = cot + ((size_t)view * n_pad + gi) * NV;
-        if constexpr (NV <= 16) {
-          const float mine = warp_reduce_scatter16(v);
-          if (lane < NV && mine != 0.f) atomicAdd(dst + lane, mine);
-        } else {
-          const float mine = warp_reduce_scatter32(v);
-          if (lane < NV && mine != 0.f) atomicAdd(dst + lane, mine);
-        }
+        float* dst = cot + ((size_t)view * n_pad + gi) * NVP;
+        float q[4];
+        if constexpr (NVP <= 16) warp_reduce_quads16(v, q);
+        else warp_reduce_quads32(v, q);
+        if ((lane & 3) == 0 && lane < NVP && (q[0] != 0.f || q[1] != 0.f || q[2] != 0.f || q[3] != 0.f))
+          atomicAdd(reinterpret_cast<float4*>(dst + lane), make_float4(q[0], q[1], q[2], q[3]));
       }
     }
     __syncthreads();
@@ -457,12 +508,13 @@ __global__ void GS_BWD_BOUNDS raster_bwd_kernel(
 //   Sigma = M M^T:       dM = 2 dSigma M, M = R diag(s), s = exp(log s)
 //   R(q / |q|):          dq = (dqn - qn (qn . dqn)) / |q|
 //   colour:              dSH_k = Y_k dc (0 where clamped), dmu += P_perp grad_Y . (sum sh dc) / |d|
-// A block holds all cotangent streams (threadIdx.y) of 64 Gaussians so that
-// their shared parameter and cotangent reads hit L1.  Each thread sums over the
-// views twice: first the geometric rows, then the SH rows, which keeps few
-// accumulators alive at a time.  The probe streams are combined in shared
-// memory into hz = (1/nu) sum_k z_k . (G z_k).
-constexpr int kPbwdX = 64;
+// One thread per Gaussian.  A first pass over the views computes each view's
+// geometry once and applies it to every cotangent stream (geometric rows); a
+// second pass per stream accumulates the SH rows, reusing the clamp decisions
+// recorded in the first.  The probe streams are combined into
+// hz = (1/nu) sum_k z_k . (G z_k).
+constexpr int kPbwdThreads = 128;
+constexpr int kClampViews = 21;  // clamp bits kept for the first 21 views (3 per view)
 
 struct ViewGeom {
   float Rc[3][3], tc[3], fx, fy;
@@ -492,20 +544,18 @@ __device__ __forceinline__ void view_direction(const ViewGeom& v, const float mu
 }
 
 template <int DEG, int NU, bool GRAD>
-__global__ void __launch_bounds__(kPbwdX * ((GRAD ? 1 : 0) + NU)) project_bwd_kernel(
-    const float* __restrict__ P, int n, int n_pad, const gs_camera* __restrict__ cams, gs_frame fr,
-    const float* __restrict__ cot, uint64_t seed, int64_t step, float* __restrict__ grad, float* __restrict__ hz) {
+__global__ void __launch_bounds__(kPbwdThreads) project_bwd_kernel(const float* __restrict__ P, int n, int n_pad,
+                                                                   const gs_camera* __restrict__ cams, gs_frame fr,
+                                                                   const float* __restrict__ cot, uint64_t seed,
+                                                                   int64_t step, float* __restrict__ grad,
+                                                                   float* __restrict__ hz) {
   constexpr int S = (GRAD ? 1 : 0) + NU;
-  constexpr int NV = 9 * S;
+  constexpr int NVP = cot_stride(S);
   constexpr int K = (DEG + 1) * (DEG + 1);
-  constexpr int ROWS = kRowSH + 3 * K;
-  __shared__ float s_hz[NU == 2 ? kPbwdX : 1][NU == 2 ? ROWS : 1];
-  const int i = blockIdx.x * kPbwdX + threadIdx.x;
-  const int s = threadIdx.y;
-  const bool active = i < n;
-  const int ii = active ? i : 0;
-  auto ld = [&](int r) { return __ldg(P + (size_t)r * n_pad + ii); };
-  float mu[3] = {ld(0), ld(1), ld(2)};
+  const int i = blockIdx.x * kPbwdThreads + threadIdx.x;
+  if (i >= n) return;
+  auto ld = [&](int r) { return __ldg(P + (size_t)r * n_pad + i); };
+  const float mu[3] = {ld(0), ld(1), ld(2)};
   float qx = ld(6), qy = ld(7), qz = ld(8), qw = ld(9);
   const float qlen = sqrtf(qx * qx + qy * qy + qz * qz + qw * qw);
   qx /= qlen; qy /= qlen; qz /= qlen; qw /= qlen;
@@ -531,19 +581,30 @@ __global__ void __launch_bounds__(kPbwdX * ((GRAD ? 1 : 0) + NU)) project_bwd_ke
 #pragma unroll
     for (int b = 0; b < 3; ++b) Sg[a][b] = M[a][0] * M[b][0] + M[a][1] * M[b][1] + M[a][2] * M[b][2];
   const float opac = 1.f / (1.f + expf(-ld(10)));
+  const float dsig = opac * (1.f - opac);
 
-  // ---- pass 1: geometric rows
-  float g_mu[3] = {0.f, 0.f, 0.f};
-  float g_S[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
-  float g_ol = 0.f;
-  for (int v = 0; active && v < fr.n_views; ++v) {
-    const float* cv = cot + ((size_t)v * n_pad + i) * NV + 9 * s;
-    float c[9];
+  // ---- pass 1: geometric rows of every stream
+  float g_mu[S][3], g_S[S][3][3], g_ol[S];
+#pragma unroll
+  for (int st = 0; st < S; ++st) {
+    g_ol[st] = 0.f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      g_mu[st][a] = 0.f;
+#pragma unroll
+      for (int b = 0; b < 3; ++b) g_S[st][a][b] = 0.f;
+    }
+  }
+  uint64_t clamp_bits = 0;  // bit 3 v + c: colour channel c clamped at 0 in view v (v < kClampViews)
+  for (int v = 0; v < fr.n_views; ++v) {
+    const float4* row4 = reinterpret_cast<const float4*>(cot + ((size_t)v * n_pad + i) * NVP);
+    float c[NVP];
     bool any = false;
 #pragma unroll
-    for (int q = 0; q < 9; ++q) {
-      c[q] = cv[q];
-      any = any || (c[q] != 0.f);
+    for (int q = 0; q < NVP / 4; ++q) {
+      const float4 x4 = row4[q];
+      c[4 * q + 0] = x4.x; c[4 * q + 1] = x4.y; c[4 * q + 2] = x4.z; c[4 * q + 3] = x4.w;
+      any = any || x4.x != 0.f || x4.y != 0.f || x4.z != 0.f || x4.w != 0.f;
     }
     if (!any) continue;
     ViewGeom vg;
@@ -573,155 +634,196 @@ __global__ void __launch_bounds__(kPbwdX * ((GRAD ? 1 : 0) + NU)) project_bwd_ke
     const float cc = J11 * J11 * Sc[1][1] + 2.f * J11 * J12 * Sc[1][2] + J12 * J12 * Sc[2][2] + kDilation;
     const float det = a * cc - bb * bb;
     const float idet = 1.f / det, id2 = idet * idet;
-    const float gA = c[2], gB = c[3], gC = c[4];
-    const float ga = gA * (-cc * cc * id2) + gB * (bb * cc * id2) + gC * (idet - a * cc * id2);
-    const float gb = gA * (2.f * bb * cc * id2) + gB * (-idet - 2.f * bb * bb * id2) + gC * (2.f * a * bb * id2);
-    const float gc = gA * (idet - a * cc * id2) + gB * (a * bb * id2) + gC * (-a * a * id2);
     const float j0[3] = {J00, 0.f, J02}, j1[3] = {0.f, J11, J12};
-    float gSc[3][3];
-#pragma unroll
-    for (int p = 0; p < 3; ++p)
-#pragma unroll
-      for (int q = 0; q < 3; ++q)
-        gSc[p][q] = ga * j0[p] * j0[q] + 0.5f * gb * (j0[p] * j1[q] + j1[p] * j0[q]) + gc * j1[p] * j1[q];
     float JS0[3], JS1[3];
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
       JS0[q] = J00 * Sc[0][q] + J02 * Sc[2][q];
       JS1[q] = J11 * Sc[1][q] + J12 * Sc[2][q];
     }
-    const float gJ00 = 2.f * (ga * JS0[0] + 0.5f * gb * JS1[0]);
-    const float gJ02 = 2.f * (ga * JS0[2] + 0.5f * gb * JS1[2]);
-    const float gJ11 = 2.f * (0.5f * gb * JS0[1] + gc * JS1[1]);
-    const float gJ12 = 2.f * (0.5f * gb * JS0[2] + gc * JS1[2]);
     const float itz2 = itz * itz, itz3 = itz2 * itz;
-    float gt[3];
-    gt[0] = c[0] * fx * itz + (clx ? 0.f : gJ02 * (-fx * itz2));
-    gt[1] = c[1] * fy * itz + (cly ? 0.f : gJ12 * (-fy * itz2));
-    gt[2] = -c[0] * fx * t[0] * itz2 - c[1] * fy * t[1] * itz2 - gJ00 * fx * itz2 - gJ11 * fy * itz2 +
-            gJ02 * (clx ? fx * uc * itz2 : 2.f * fx * t[0] * itz3) +
-            gJ12 * (cly ? fy * vc * itz2 : 2.f * fy * t[1] * itz3);
+    const float dJ02_dtx = clx ? 0.f : -fx * itz2, dJ12_dty = cly ? 0.f : -fy * itz2;
+    const float dJ02_dtz = clx ? fx * uc * itz2 : 2.f * fx * t[0] * itz3;
+    const float dJ12_dtz = cly ? fy * vc * itz2 : 2.f * fy * t[1] * itz3;
 #pragma unroll
-    for (int q = 0; q < 3; ++q) g_mu[q] += vg.Rc[0][q] * gt[0] + vg.Rc[1][q] * gt[1] + vg.Rc[2][q] * gt[2];
+    for (int st = 0; st < S; ++st) {
+      const float* cs = c + 9 * st;
+      const float gA = cs[2], gB = cs[3], gC = cs[4];
+      const float ga = gA * (-cc * cc * id2) + gB * (bb * cc * id2) + gC * (idet - a * cc * id2);
+      const float gb = gA * (2.f * bb * cc * id2) + gB * (-idet - 2.f * bb * bb * id2) + gC * (2.f * a * bb * id2);
+      const float gc = gA * (idet - a * cc * id2) + gB * (a * bb * id2) + gC * (-a * a * id2);
+      float gSc[3][3];
 #pragma unroll
-    for (int p = 0; p < 3; ++p) {
-      float tmp[3];
+      for (int p2 = 0; p2 < 3; ++p2)
 #pragma unroll
-      for (int q = 0; q < 3; ++q) tmp[q] = vg.Rc[0][p] * gSc[0][q] + vg.Rc[1][p] * gSc[1][q] + vg.Rc[2][p] * gSc[2][q];
+        for (int q = 0; q < 3; ++q)
+          gSc[p2][q] = ga * j0[p2] * j0[q] + 0.5f * gb * (j0[p2] * j1[q] + j1[p2] * j0[q]) + gc * j1[p2] * j1[q];
+      const float gJ00 = 2.f * (ga * JS0[0] + 0.5f * gb * JS1[0]);
+      const float gJ02 = 2.f * (ga * JS0[2] + 0.5f * gb * JS1[2]);
+      const float gJ11 = 2.f * (0.5f * gb * JS0[1] + gc * JS1[1]);
+      const float gJ12 = 2.f * (0.5f * gb * JS0[2] + gc * JS1[2]);
+      float gt[3];
+      gt[0] = cs[0] * fx * itz + gJ02 * dJ02_dtx;
+      gt[1] = cs[1] * fy * itz + gJ12 * dJ12_dty;
+      gt[2] = -cs[0] * fx * t[0] * itz2 - cs[1] * fy * t[1] * itz2 - gJ00 * fx * itz2 - gJ11 * fy * itz2 +
+              gJ02 * dJ02_dtz + gJ12 * dJ12_dtz;
 #pragma unroll
-      for (int q = 0; q < 3; ++q) g_S[p][q] += tmp[0] * vg.Rc[0][q] + tmp[1] * vg.Rc[1][q] + tmp[2] * vg.Rc[2][q];
-    }
-    g_ol += c[5] * opac * (1.f - opac);
-    if constexpr (DEG > 0) {
-      // the colour depends on mu through the view direction
-      float d[3], dn;
-      view_direction(vg, mu, d, dn);
-      float Y[K];
-      sh_basis<DEG>(d[0], d[1], d[2], Y);
-      float gcol[3];
+      for (int q = 0; q < 3; ++q) g_mu[st][q] += vg.Rc[0][q] * gt[0] + vg.Rc[1][q] * gt[1] + vg.Rc[2][q] * gt[2];
 #pragma unroll
-      for (int ch = 0; ch < 3; ++ch) {
-        float raw = 0.5f;
+      for (int p2 = 0; p2 < 3; ++p2) {
+        float tmp[3];
 #pragma unroll
-        for (int k = 0; k < K; ++k) raw += Y[k] * ld(kRowSH + 3 * k + ch);
-        gcol[ch] = raw < 0.f ? 0.f : c[6 + ch];
+        for (int q = 0; q < 3; ++q)
+          tmp[q] = vg.Rc[0][p2] * gSc[0][q] + vg.Rc[1][p2] * gSc[1][q] + vg.Rc[2][p2] * gSc[2][q];
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+          g_S[st][p2][q] += tmp[0] * vg.Rc[0][q] + tmp[1] * vg.Rc[1][q] + tmp[2] * vg.Rc[2][q];
       }
-      float wk[K];
-#pragma unroll
-      for (int k = 0; k < K; ++k)
-        wk[k] = ld(kRowSH + 3 * k + 0) * gcol[0] + ld(kRowSH + 3 * k + 1) * gcol[1] + ld(kRowSH + 3 * k + 2) * gcol[2];
-      float gd[3];
-      sh_basis_grad<DEG>(d[0], d[1], d[2], wk, gd);
-      const float dot = gd[0] * d[0] + gd[1] * d[1] + gd[2] * d[2];
-#pragma unroll
-      for (int q = 0; q < 3; ++q) g_mu[q] += (gd[q] - d[q] * dot) / dn;
+      g_ol[st] += cs[5] * dsig;
     }
-  }
-  // ---- pass 2: SH rows
-  float g_sh[K][3];
-#pragma unroll
-  for (int k = 0; k < K; ++k) g_sh[k][0] = g_sh[k][1] = g_sh[k][2] = 0.f;
-  for (int v = 0; active && v < fr.n_views; ++v) {
-    const float* cv = cot + ((size_t)v * n_pad + i) * NV + 9 * s;
-    const float c6 = cv[6], c7 = cv[7], c8 = cv[8];
-    if (c6 == 0.f && c7 == 0.f && c8 == 0.f) continue;
-    ViewGeom vg;
-    load_view(cams + v, vg);
+    // colour: clamp decisions, and the dependence of colour on mu through the view direction
     float d[3], dn;
     view_direction(vg, mu, d, dn);
     float Y[K];
     sh_basis<DEG>(d[0], d[1], d[2], Y);
-    const float cin[3] = {c6, c7, c8};
+    float sh[K][3];
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) sh[k][ch] = ld(kRowSH + 3 * k + ch);
+    bool clamped[3];
 #pragma unroll
     for (int ch = 0; ch < 3; ++ch) {
       float raw = 0.5f;
 #pragma unroll
-      for (int k = 0; k < K; ++k) raw += Y[k] * ld(kRowSH + 3 * k + ch);
-      const float gcol = raw < 0.f ? 0.f : cin[ch];
+      for (int k = 0; k < K; ++k) raw += Y[k] * sh[k][ch];
+      clamped[ch] = raw < 0.f;
+      if (clamped[ch] && v < kClampViews) clamp_bits |= 1ull << (3 * v + ch);
+    }
+    if constexpr (DEG > 0) {
 #pragma unroll
-      for (int k = 0; k < K; ++k) g_sh[k][ch] += Y[k] * gcol;
+      for (int st = 0; st < S; ++st) {
+        float gcol[3];
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) gcol[ch] = clamped[ch] ? 0.f : c[9 * st + 6 + ch];
+        float wk[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) wk[k] = sh[k][0] * gcol[0] + sh[k][1] * gcol[1] + sh[k][2] * gcol[2];
+        float gd[3];
+        sh_basis_grad<DEG>(d[0], d[1], d[2], wk, gd);
+        const float dot = gd[0] * d[0] + gd[1] * d[1] + gd[2] * d[2];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) g_mu[st][q] += (gd[q] - d[q] * dot) / dn;
+      }
     }
   }
-  // ---- Sigma = M M^T, M = R diag(s);  R(q / |q|)
-  float gM[3][3];
+
+  // ---- geometric rows: Sigma = M M^T, M = R diag(s); R(q / |q|)
+  const float qn[4] = {qx, qy, qz, qw};
+  float hz_geo[kRowSH];
 #pragma unroll
-  for (int a = 0; a < 3; ++a)
+  for (int r = 0; r < kRowSH; ++r) hz_geo[r] = 0.f;
+  const float inv_nu = NU > 0 ? 1.f / (float)NU : 0.f;
 #pragma unroll
-    for (int b = 0; b < 3; ++b) gM[a][b] = 2.f * (g_S[a][0] * M[0][b] + g_S[a][1] * M[1][b] + g_S[a][2] * M[2][b]);
-  float g_ls[3], gR[3][3];
+  for (int st = 0; st < S; ++st) {
+    float gM[3][3];
 #pragma unroll
-  for (int b = 0; b < 3; ++b) {
-    g_ls[b] = (gM[0][b] * R[0][b] + gM[1][b] * R[1][b] + gM[2][b] * R[2][b]) * sc[b];
+    for (int a = 0; a < 3; ++a)
 #pragma unroll
-    for (int a = 0; a < 3; ++a) gR[a][b] = gM[a][b] * sc[b];
-  }
-  const float x = qx, y = qy, z = qz, ww = qw;
-  float gq[4];
-  gq[0] = 2.f * y * gR[0][1] + 2.f * z * gR[0][2] + 2.f * y * gR[1][0] - 4.f * x * gR[1][1] - 2.f * ww * gR[1][2] +
-          2.f * z * gR[2][0] + 2.f * ww * gR[2][1] - 4.f * x * gR[2][2];
-  gq[1] = -4.f * y * gR[0][0] + 2.f * x * gR[0][1] + 2.f * ww * gR[0][2] + 2.f * x * gR[1][0] + 2.f * z * gR[1][2] -
-          2.f * ww * gR[2][0] + 2.f * z * gR[2][1] - 4.f * y * gR[2][2];
-  gq[2] = -4.f * z * gR[0][0] - 2.f * ww * gR[0][1] + 2.f * x * gR[0][2] + 2.f * ww * gR[1][0] - 4.f * z * gR[1][1] +
-          2.f * y * gR[1][2] + 2.f * x * gR[2][0] + 2.f * y * gR[2][1];
-  gq[3] = -2.f * z * gR[0][1] + 2.f * y * gR[0][2] + 2.f * z * gR[1][0] - 2.f * x * gR[1][2] - 2.f * y * gR[2][0] +
-          2.f * x * gR[2][1];
-  const float qd = gq[0] * x + gq[1] * y + gq[2] * z + gq[3] * ww;
-  const float qn[4] = {x, y, z, ww};
-  auto row_value = [&](int r) -> float {
-    if (r < 3) return g_mu[r];
-    if (r < 6) return g_ls[r - 3];
-    if (r < 10) return (gq[r - 6] - qn[r - 6] * qd) / qlen;
-    if (r == 10) return g_ol;
-    return g_sh[(r - kRowSH) / 3][(r - kRowSH) % 3];
-  };
-  // ---- scatter: the gradient stream writes grad; probe streams write z_k . v / nu
-  if (GRAD && s == 0) {
-    if (active) {
+      for (int b = 0; b < 3; ++b)
+        gM[a][b] = 2.f * (g_S[st][a][0] * M[0][b] + g_S[st][a][1] * M[1][b] + g_S[st][a][2] * M[2][b]);
+    float rowv[kRowSH];
+    float gR[3][3];
 #pragma unroll
-      for (int r = 0; r < ROWS; ++r) grad[(size_t)r * n_pad + i] = row_value(r);
+    for (int b = 0; b < 3; ++b) {
+      rowv[3 + b] = (gM[0][b] * R[0][b] + gM[1][b] * R[1][b] + gM[2][b] * R[2][b]) * sc[b];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) gR[a][b] = gM[a][b] * sc[b];
+    }
+    const float x = qx, y = qy, z = qz, ww = qw;
+    float gq[4];
+    gq[0] = 2.f * y * gR[0][1] + 2.f * z * gR[0][2] + 2.f * y * gR[1][0] - 4.f * x * gR[1][1] - 2.f * ww * gR[1][2] +
+            2.f * z * gR[2][0] + 2.f * ww * gR[2][1] - 4.f * x * gR[2][2];
+    gq[1] = -4.f * y * gR[0][0] + 2.f * x * gR[0][1] + 2.f * ww * gR[0][2] + 2.f * x * gR[1][0] + 2.f * z * gR[1][2] -
+            2.f * ww * gR[2][0] + 2.f * z * gR[2][1] - 4.f * y * gR[2][2];
+    gq[2] = -4.f * z * gR[0][0] - 2.f * ww * gR[0][1] + 2.f * x * gR[0][2] + 2.f * ww * gR[1][0] - 4.f * z * gR[1][1] +
+            2.f * y * gR[1][2] + 2.f * x * gR[2][0] + 2.f * y * gR[2][1];
+    gq[3] = -2.f * z * gR[0][1] + 2.f * y * gR[0][2] + 2.f * z * gR[1][0] - 2.f * x * gR[1][2] - 2.f * y * gR[2][0] +
+            2.f * x * gR[2][1];
+    const float qd = gq[0] * x + gq[1] * y + gq[2] * z + gq[3] * ww;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) rowv[a] = g_mu[st][a];
+#pragma unroll
+    for (int cq = 0; cq < 4; ++cq) rowv[6 + cq] = (gq[cq] - qn[cq] * qd) / qlen;
+    rowv[10] = g_ol[st];
+    if (GRAD && st == 0) {
+#pragma unroll
+      for (int r = 0; r < kRowSH; ++r) grad[(size_t)r * n_pad + i] = rowv[r];
+    } else {
+      const int k = st - (GRAD ? 1 : 0);
+#pragma unroll
+      for (int r = 0; r < kRowSH; ++r) {
+        const bool neg = probe_negative(seed, step, k, (uint64_t)r * (uint64_t)n + (uint64_t)i);
+        hz_geo[r] += (neg ? -rowv[r] : rowv[r]) * inv_nu;
+      }
     }
   }
   if constexpr (NU > 0) {
-    const int k = s - (GRAD ? 1 : 0);
-    const float inv_nu = 1.f / (float)NU;
-    if (NU == 2 && k == 1 && active) {
 #pragma unroll
-      for (int r = 0; r < ROWS; ++r) {
-        const bool neg = probe_negative(seed, step, 1, (uint64_t)r * (uint64_t)n + (uint64_t)i);
-        const float v = row_value(r) * inv_nu;
-        s_hz[NU == 2 ? threadIdx.x : 0][NU == 2 ? r : 0] = neg ? -v : v;
+    for (int r = 0; r < kRowSH; ++r) hz[(size_t)r * n_pad + i] = hz_geo[r];
+  }
+
+  // ---- pass 2 per stream: SH rows
+#pragma unroll 1
+  for (int st = 0; st < S; ++st) {
+    float g_sh[K][3];
+#pragma unroll
+    for (int k = 0; k < K; ++k) g_sh[k][0] = g_sh[k][1] = g_sh[k][2] = 0.f;
+    for (int v = 0; v < fr.n_views; ++v) {
+      const float* cv = cot + ((size_t)v * n_pad + i) * NVP + 9 * st + 6;
+      float gcol[3] = {cv[0], cv[1], cv[2]};
+      if (gcol[0] == 0.f && gcol[1] == 0.f && gcol[2] == 0.f) continue;
+      ViewGeom vg;
+      load_view(cams + v, vg);
+      float d[3], dn;
+      view_direction(vg, mu, d, dn);
+      float Y[K];
+      sh_basis<DEG>(d[0], d[1], d[2], Y);
+      if (v < kClampViews) {
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch)
+          if ((clamp_bits >> (3 * v + ch)) & 1ull) gcol[ch] = 0.f;
+      } else {
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+          float raw = 0.5f;
+#pragma unroll
+          for (int k = 0; k < K; ++k) raw += Y[k] * ld(kRowSH + 3 * k + ch);
+          if (raw < 0.f) gcol[ch] = 0.f;
+        }
       }
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) g_sh[k][ch] += Y[k] * gcol[ch];
     }
-    if (NU == 2) __syncthreads();
-    if (k == 0 && active) {
+    if (GRAD && st == 0) {
 #pragma unroll
-      for (int r = 0; r < ROWS; ++r) {
-        const bool neg = probe_negative(seed, step, 0, (uint64_t)r * (uint64_t)n + (uint64_t)i);
-        const float v = row_value(r) * inv_nu;
-        float out = neg ? -v : v;
-        if (NU == 2) out += s_hz[NU == 2 ? threadIdx.x : 0][NU == 2 ? r : 0];
-        hz[(size_t)r * n_pad + i] = out;
-      }
+      for (int k = 0; k < K; ++k)
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) grad[(size_t)(kRowSH + 3 * k + ch) * n_pad + i] = g_sh[k][ch];
+    } else {
+      const int kp = st - (GRAD ? 1 : 0);
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+          const int r = kRowSH + 3 * k + ch;
+          const bool neg = probe_negative(seed, step, kp, (uint64_t)r * (uint64_t)n + (uint64_t)i);
+          const float val = (neg ? -g_sh[k][ch] : g_sh[k][ch]) * inv_nu;
+          float* dst = hz + (size_t)r * n_pad + i;
+          *dst = (kp == 0) ? val : *dst + val;
+        }
     }
   }
 }
@@ -764,7 +866,7 @@ gs_status launch_fwd(const gs_projected* proj, const gs_sorted* sorted, int n_pa
 }
 
 size_t bwd_cot_floats(int32_t n_pad, gs_frame fr, int streams) {
-  return (size_t)fr.n_views * n_pad * 9 * streams;
+  return (size_t)fr.n_views * n_pad * cot_stride(streams);
 }
 
 template <int NU, bool GRAD>
@@ -780,8 +882,7 @@ void launch_bwd_kernels(const gs_params* x, const gs_camera* cams, const gs_proj
   raster_bwd_kernel<NU, GRAD><<<blocks, nthr, smem, st>>>(
       reinterpret_cast<const float4*>(proj->rec), sorted->vals, sorted->ranges, x->n_pad, fr, g.Tx, g.T, image,
       target, final_T, n_contrib, image_tan, loss.kind, loss.gn_floor, inv_m, cot, loss_out, status);
-  constexpr int S = (GRAD ? 1 : 0) + NU;
-  const dim3 pg((x->n + kPbwdX - 1) / kPbwdX), pb(kPbwdX, S);
+  const dim3 pg((x->n + kPbwdThreads - 1) / kPbwdThreads), pb(kPbwdThreads);
   const uint64_t seed = probe ? probe->seed : 0;
   const int64_t t = probe ? probe->t : 0;
   if (x->n == 0) return;
