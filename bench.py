@@ -146,13 +146,17 @@ def make_workload(n, device, rank=0):
 
 
 def kernel_launches_per_step(eng) -> int:
-    tiles = N_VIEWS * eng.Tx * eng.Ty
-    bits = 1
-    while (1 << bits) < tiles:
-        bits += 1
-    npass = (32 + bits + 7) // 8
-    sort = 1 + 3 + 1 + npass * (1 + 3 + 1) + 1
-    return 1 + sort + 1 + 2 + 1  # project, sort, fwd, bwd + projection reverse, update
+    """Kernels of this library launched per step (the two memsets are not counted)."""
+    def bits(v):
+        b = 0
+        while (1 << b) < v:
+            b += 1
+        return b
+    rec_pass = (32 + bits(N_VIEWS) + 7) // 8
+    pair_pass = max(1, (bits(N_VIEWS * eng.Tx * eng.Ty) + 7) // 8)
+    radix = 1 + 3 + 1  # histogram, three-kernel scan, scatter
+    sort = 1 + 1 + rec_pass * radix + 1 + 3 + 1 + pair_pass * radix + 1
+    return 1 + sort + 1 + 2 + 1  # project, sort, fwd, reverse blend + projection reverse, update
 
 
 def timed_steps(eng, cam_dev, targets, K, W0, t0, stream, per_call=False):

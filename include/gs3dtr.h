@@ -87,8 +87,8 @@ typedef struct gs_camera {
 } gs_camera;
 
 /* Views rendered by one call; every camera of the call has this size.
- * tile_w is 8, 16 or 32, tile_h a power of two >= 4, tile_w * tile_h is 64, 128
- * or 256 (one thread per pixel; each warp covers an 8 x 4 pixel block). */
+ * tile_w is 8, 16 or 32, tile_h a power of two >= 8, tile_w * tile_h is 64, 128
+ * or 256 (two pixels per thread; each warp covers an 8 x 8 pixel block). */
 typedef struct gs_frame {
   int32_t n_views, width, height, tile_w, tile_h;
 } gs_frame;

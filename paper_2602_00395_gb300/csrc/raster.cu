@@ -7,16 +7,19 @@
 //                  in the same sweep, the Gauss-Newton products J^T diag(w) J z_k
 //   gs_hvp_diag    the Gauss-Newton products alone
 //
-// One CTA renders one tile of one view, one thread per pixel.  The tile's splat
-// records are staged through shared memory in batches of one record per thread,
-// each record moved by a 48-byte TMA bulk copy (cp.async.bulk, no multicast)
-// completing on an mbarrier, double-buffered so that the next batch lands while
-// the current one is blended.  The reverse pass walks the list back to front,
+// One CTA renders one tile of one view with two pixels per thread; each warp
+// owns an 8 x 8 pixel block.  The tile's splat records are staged through
+// shared memory in batches (one record per pixel of the tile), each record moved
+// by a 48-byte TMA bulk copy (cp.async.bulk, no multicast) completing on an
+// mbarrier, double-buffered so that the next batch lands while the current one
+// is blended.  Per batch every splat gets a mask of the warp blocks its
+// alpha >= 1/255 footprint can reach, and each warp walks only its own visible
+// splats (one ballot per 32).  The reverse pass walks the list back to front,
 // recovers T_i = T_{i+1} / (1 - a_i) from the final transmittance (nothing per
-// pair is stored), and merges each splat's 9 x streams partial derivatives over
-// the warp with a reduce-scatter butterfly before one global atomic per value.
-// The projection's reverse pass (2-D cotangents -> 11 + 3K parameter rows) runs
-// one thread per (Gaussian, stream) and sums over the views.
+// pair is stored), sums each splat's 9 x streams partial derivatives over the
+// warp's 64 pixels with a reduction that ends in quads, and adds them with float4
+// atomics.  The projection's reverse pass (2-D cotangents -> 11 + 3K parameter
+// rows) runs one thread per Gaussian and sums over the views.
 #include "common.cuh"
 
 namespace gs {
@@ -36,37 +39,45 @@ __device__ __forceinline__ float splat_power(const Rec& r, float dx, float dy) {
   return __fmaf_rn(-0.5f, q, -__fmul_rn(r.a.w, __fmul_rn(dx, dy)));
 }
 
-// Stage batch b of a tile list into buffer (b & 1): one bulk copy per record
-// (and per tangent record), all completing on the buffer's mbarrier.
+// Stage batch b of a tile list (records [b * batch, b * batch + batch)) into
+// buffer (b & 1): one bulk copy per record (and per tangent record), issued by
+// the block's threads in turn, all completing on the buffer's mbarrier.
 template <int NT>
-__device__ __forceinline__ void stage_batch(int b, int nthr, uint32_t start, int n, int view, int n_pad,
+__device__ __forceinline__ void stage_batch(int b, int batch, uint32_t start, int n, int view, int n_pad,
                                             const uint32_t* __restrict__ vals, const float4* __restrict__ rec,
                                             const float4* __restrict__ tan, Rec* buf, Rec* tbuf, uint32_t* s_idx,
                                             uint64_t* bars) {
   const int bi = b & 1;
-  const int cnt = min(nthr, n - b * nthr);
-  const int tid = threadIdx.x;
-  if (tid == 0) mbar_arrive_expect_tx(&bars[bi], (uint32_t)(cnt * (int)sizeof(Rec) * (1 + NT)));
-  if (tid < cnt) {
-    const uint32_t gi = vals[start + (uint32_t)(b * nthr + tid)];
-    if (s_idx) s_idx[bi * nthr + tid] = gi;
-    fence_proxy_async();
-    bulk_g2s(&buf[bi * nthr + tid], rec + 3 * ((size_t)view * n_pad + gi), sizeof(Rec), &bars[bi]);
+  const int cnt = min(batch, n - b * batch);
+  if (threadIdx.x == 0) mbar_arrive_expect_tx(&bars[bi], (uint32_t)(cnt * (int)sizeof(Rec) * (1 + NT)));
+  fence_proxy_async();
+  for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
+    const uint32_t gi = vals[start + (uint32_t)(b * batch + q)];
+    if (s_idx) s_idx[bi * batch + q] = gi;
+    bulk_g2s(&buf[bi * batch + q], rec + 3 * ((size_t)view * n_pad + gi), sizeof(Rec), &bars[bi]);
 #pragma unroll
     for (int k = 0; k < NT; ++k)
-      bulk_g2s(&tbuf[(bi * NT + k) * nthr + tid], tan + 3 * (((size_t)view * NT + k) * n_pad + gi), sizeof(Rec),
+      bulk_g2s(&tbuf[(bi * NT + k) * batch + q], tan + 3 * (((size_t)view * NT + k) * n_pad + gi), sizeof(Rec),
                &bars[bi]);
   }
 }
 
 // ------------------------------------------------------------ pixel blocks
-// Thread tid of a tile renders pixel (lx, ly): warp w covers the 8 x 4 pixel
-// block (w % (tile_w/8), w / (tile_w/8)), so that a splat's footprint meets few
-// warps.
+// A tile has tile_w x tile_h pixels and half as many threads: each warp covers
+// an 8 x 8 pixel block, warp w the block (w % (tile_w/8), w / (tile_w/8)), and
+// its lane renders pixels (lx, ly) and (lx, ly + 4) of it.  Compact blocks meet
+// few splats; two pixels per thread halve the per-splat warp overheads.
+constexpr int kPixPerThread = 2;
+// Records staged per batch, per thread.
+#ifndef GS_BATCH_PER_THREAD
+#define GS_BATCH_PER_THREAD 1
+#endif
+constexpr int kBatchPerThread = GS_BATCH_PER_THREAD;
+
 __device__ __forceinline__ void pixel_of(int tid, int tile_w, int& lx, int& ly) {
   const int warp = tid >> 5, lane = tid & 31, bxn = tile_w >> 3;
   lx = (warp % bxn) * 8 + (lane & 7);
-  ly = (warp / bxn) * 4 + (lane >> 3);
+  ly = (warp / bxn) * 8 + (lane >> 3);
 }
 
 // Bit w is set if the splat can reach alpha >= 1/255 at some pixel centre of
@@ -89,35 +100,83 @@ __device__ __forceinline__ uint32_t warp_block_mask(const Rec& r, float tile_x0,
   uint32_t m = 0;
   for (int w = 0; w < nwarps; ++w) {
     const float x0 = tile_x0 + (float)((w % bxn) * 8) + 0.5f, x1 = x0 + 7.f;
-    const float y0 = tile_y0 + (float)((w / bxn) * 4) + 0.5f, y1 = y0 + 3.f;
+    const float y0 = tile_y0 + (float)((w / bxn) * 8) + 0.5f, y1 = y0 + 7.f;
     if (r.a.x + hx >= x0 && r.a.x - hx <= x1 && r.a.y + hy >= y0 && r.a.y - hy <= y1) m |= 1u << w;
   }
   return m;
 }
 
 // ------------------------------------------------------------------ forward
+// Blend state of one pixel: colour, transmittance, the probe tangents of both,
+// and the list position after the last blended splat.
 template <int NU>
-__global__ void __launch_bounds__(256) raster_fwd_kernel(const float4* __restrict__ rec, const float4* __restrict__ tan,
+struct FwdPixel {
+  float C[3], T;
+  float Cd[NU > 0 ? NU : 1][3], Td[NU > 0 ? NU : 1];
+  float pxc, pyc;
+  uint32_t last;
+  bool done;
+};
+
+// One splat against one pixel (front to back).  `t0` points at the splat's
+// first rewritten tangent record; the records of further probes follow at
+// stride `tstride`.
+template <int NU>
+__device__ __forceinline__ void fwd_blend(FwdPixel<NU>& p, const Rec& r, const Rec* t0, int tstride, uint32_t pos) {
+  if (p.done) return;
+  const float dx = __fsub_rn(r.a.x, p.pxc), dy = __fsub_rn(r.a.y, p.pyc);
+  const float power = splat_power(r, dx, dy);
+  if (power > 0.f) return;
+  const float G = __expf(power);
+  const float oG = __fmul_rn(r.b.y, G);
+  const float alpha = fminf(kAlphaMax, oG);
+  if (alpha < kAlphaMin) return;
+  const float Tn = p.T * (1.f - alpha);
+  if (Tn < kTMin) {
+    p.done = true;
+    return;
+  }
+  const float w = alpha * p.T;
+  if constexpr (NU > 0) {
+    const bool capped = oG > kAlphaMax;
+#pragma unroll
+    for (int k = 0; k < NU; ++k) {
+      const Rec t = t0[k * tstride];
+      const float pd = dx * (t.a.x * dx + t.a.y * dy + t.a.w) + dy * (t.a.z * dy + t.b.x);
+      const float ad = capped ? 0.f : (t.b.y * G + alpha * pd);
+      const float sk = ad * p.T + alpha * p.Td[k];
+      p.Cd[k][0] += t.b.z * w + r.b.z * sk;
+      p.Cd[k][1] += t.b.w * w + r.b.w * sk;
+      p.Cd[k][2] += t.c.x * w + r.c.x * sk;
+      p.Td[k] = p.Td[k] * (1.f - alpha) - p.T * ad;
+    }
+  }
+  p.C[0] += r.b.z * w;
+  p.C[1] += r.b.w * w;
+  p.C[2] += r.c.x * w;
+  p.T = Tn;
+  p.last = pos + 1;
+}
+
+template <int NU>
+__global__ void __launch_bounds__(128) raster_fwd_kernel(const float4* __restrict__ rec, const float4* __restrict__ tan,
                                                          const uint32_t* __restrict__ vals,
                                                          const uint32_t* __restrict__ ranges, int n_pad, gs_frame fr,
                                                          int Tx, int T, float* __restrict__ image,
                                                          float* __restrict__ final_T, uint32_t* __restrict__ n_contrib,
                                                          float* __restrict__ image_tan, int32_t* status) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const int nthr = blockDim.x, nwarps = nthr >> 5;
+  const int nthr = blockDim.x, nwarps = nthr >> 5, batch = kBatchPerThread * nthr;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
   Rec* buf = reinterpret_cast<Rec*>(smem + 16);
-  Rec* tbuf = buf + 2 * nthr;
-  uint32_t* s_mask = reinterpret_cast<uint32_t*>(tbuf + 2 * NU * nthr);
-  const int tid = threadIdx.x;
+  Rec* tbuf = buf + 2 * batch;
+  uint32_t* s_mask = reinterpret_cast<uint32_t*>(tbuf + 2 * NU * batch);
+  const int tid = threadIdx.x, lane = tid & 31;
   const uint32_t wbit = 1u << (tid >> 5);
   const int view = blockIdx.x / T, tile = blockIdx.x - view * T;
   const int ty = tile / Tx, tx = tile - ty * Tx;
   int lx, ly;
   pixel_of(tid, fr.tile_w, lx, ly);
-  const int px = tx * fr.tile_w + lx, py = ty * fr.tile_h + ly;
-  const bool inside = px < fr.width && py < fr.height;
-  const float pxc = (float)px + 0.5f, pyc = (float)py + 0.5f;
   const float tile_x0 = (float)(tx * fr.tile_w), tile_y0 = (float)(ty * fr.tile_h);
   const size_t tslot = 2 * ((size_t)view * T + tile);
   const uint32_t start = ranges[tslot], end = ranges[tslot + 1];
@@ -127,30 +186,40 @@ __global__ void __launch_bounds__(256) raster_fwd_kernel(const float4* __restric
     mbar_init(&bars[1], 1);
     fence_mbar_init();
   }
+  FwdPixel<NU> pix[kPixPerThread];
+  int px[kPixPerThread], py[kPixPerThread];
+#pragma unroll
+  for (int q = 0; q < kPixPerThread; ++q) {
+    px[q] = tx * fr.tile_w + lx;
+    py[q] = ty * fr.tile_h + ly + 4 * q;
+    FwdPixel<NU>& p = pix[q];
+    p.C[0] = p.C[1] = p.C[2] = 0.f;
+    p.T = 1.f;
+#pragma unroll
+    for (int k = 0; k < NU; ++k) p.Cd[k][0] = p.Cd[k][1] = p.Cd[k][2] = p.Td[k] = 0.f;
+    p.pxc = (float)px[q] + 0.5f;
+    p.pyc = (float)py[q] + 0.5f;
+    p.last = 0;
+    p.done = !(px[q] < fr.width && py[q] < fr.height);
+  }
   __syncthreads();
 
-  float C0 = 0.f, C1 = 0.f, C2 = 0.f, Tr = 1.f;
-  float Cd[NU > 0 ? NU : 1][3], Td[NU > 0 ? NU : 1];
-#pragma unroll
-  for (int k = 0; k < NU; ++k) Cd[k][0] = Cd[k][1] = Cd[k][2] = Td[k] = 0.f;
-  uint32_t last = 0;
-  bool done = !inside;
-  const int nb = (n + nthr - 1) / nthr;
-  if (nb > 0) stage_batch<NU>(0, nthr, start, n, view, n_pad, vals, rec, tan, buf, tbuf, nullptr, bars);
+  const int nb = (n + batch - 1) / batch;
+  if (nb > 0) stage_batch<NU>(0, batch, start, n, view, n_pad, vals, rec, tan, buf, tbuf, nullptr, bars);
   for (int b = 0; b < nb; ++b) {
-    if (b + 1 < nb) stage_batch<NU>(b + 1, nthr, start, n, view, n_pad, vals, rec, tan, buf, tbuf, nullptr, bars);
+    if (b + 1 < nb) stage_batch<NU>(b + 1, batch, start, n, view, n_pad, vals, rec, tan, buf, tbuf, nullptr, bars);
     const int bi = b & 1;
     const bool ok = mbar_wait_bounded(&bars[bi], (uint32_t)((b >> 1) & 1), status);
-    const int cnt = min(nthr, n - b * nthr);
-    Rec* bb = buf + bi * nthr;
+    const int cnt = min(batch, n - b * batch);
+    Rec* bb = buf + bi * batch;
     // per splat: which warps it can reach, and the probe tangents of its power
     // rewritten as the quadratic form pd = dx (a dx + b dy + d) + dy (c dy + e)
-    if (tid < cnt) {
-      const Rec r = bb[tid];
-      s_mask[tid] = ok ? warp_block_mask(r, tile_x0, tile_y0, fr.tile_w, nwarps) : 0u;
+    for (int q = tid; q < cnt; q += nthr) {
+      const Rec r = bb[q];
+      s_mask[q] = ok ? warp_block_mask(r, tile_x0, tile_y0, fr.tile_w, nwarps) : 0u;
 #pragma unroll
       for (int k = 0; k < NU; ++k) {
-        Rec* tp = &tbuf[(bi * NU + k) * nthr + tid];
+        Rec* tp = &tbuf[(bi * NU + k) * batch + q];
         const float4 ta = tp->a;  // dmx, dmy, dA, dB
         const float dC = tp->b.x;
         tp->a = make_float4(-0.5f * ta.z, -ta.w, -0.5f * dC, -(r.a.z * ta.x + r.a.w * ta.y));
@@ -158,70 +227,44 @@ __global__ void __launch_bounds__(256) raster_fwd_kernel(const float4* __restric
       }
     }
     __syncthreads();
-    if (!ok) done = true;
+    if (!ok) {
+#pragma unroll
+      for (int q = 0; q < kPixPerThread; ++q) pix[q].done = true;
+    }
     // The warp walks only the splats its block can see: one ballot per 32
     // splats, then the set bits in list order.
-    const int lane = tid & 31;
-    for (int j0 = 0; j0 < cnt && !__all_sync(0xffffffffu, done); j0 += 32) {
+    for (int j0 = 0; j0 < cnt; j0 += 32) {
+      if (__all_sync(0xffffffffu, pix[0].done && pix[1].done)) break;
       uint32_t bits = __ballot_sync(0xffffffffu, j0 + lane < cnt && (s_mask[j0 + lane] & wbit));
       while (bits) {
         const int j = j0 + __ffs(bits) - 1;
         bits &= bits - 1;
-        if (done) continue;
         const Rec r = bb[j];
-        const float dx = __fsub_rn(r.a.x, pxc), dy = __fsub_rn(r.a.y, pyc);
-        const float power = splat_power(r, dx, dy);
-        if (power > 0.f) continue;
-        const float G = __expf(power);
-        const float oG = __fmul_rn(r.b.y, G);
-        const float alpha = fminf(kAlphaMax, oG);
-        if (alpha < kAlphaMin) continue;
-        const float Tn = Tr * (1.f - alpha);
-        if (Tn < kTMin) {
-          done = true;
-          continue;
-        }
-        const float w = alpha * Tr;
-        if constexpr (NU > 0) {
-          const bool capped = oG > kAlphaMax;
+        const Rec* t0 = tbuf + (size_t)bi * NU * batch + j;
+        const uint32_t pos = (uint32_t)(b * batch + j);
 #pragma unroll
-          for (int k = 0; k < NU; ++k) {
-            const Rec t = tbuf[(bi * NU + k) * nthr + j];
-            const float pd = dx * (t.a.x * dx + t.a.y * dy + t.a.w) + dy * (t.a.z * dy + t.b.x);
-            const float ad = capped ? 0.f : (t.b.y * G + alpha * pd);
-            const float sk = ad * Tr + alpha * Td[k];
-            Cd[k][0] += t.b.z * w + r.b.z * sk;
-            Cd[k][1] += t.b.w * w + r.b.w * sk;
-            Cd[k][2] += t.c.x * w + r.c.x * sk;
-            Td[k] = Td[k] * (1.f - alpha) - Tr * ad;
-          }
-        }
-        C0 += r.b.z * w;
-        C1 += r.b.w * w;
-        C2 += r.c.x * w;
-        Tr = Tn;
-        last = (uint32_t)(b * nthr + j + 1);
+        for (int q = 0; q < kPixPerThread; ++q) fwd_blend<NU>(pix[q], r, t0, batch, pos);
       }
     }
-    if (__syncthreads_count(done) == nthr) {
+    if (__syncthreads_count(pix[0].done && pix[1].done) == nthr) {
       if (b + 1 < nb) mbar_wait_bounded(&bars[(b + 1) & 1], (uint32_t)(((b + 1) >> 1) & 1), status);
       break;
     }
   }
-  if (!inside) return;
   const size_t HW = (size_t)fr.width * fr.height;
-  const size_t pix = (size_t)py * fr.width + px;
-  image[((size_t)view * 3 + 0) * HW + pix] = C0;
-  image[((size_t)view * 3 + 1) * HW + pix] = C1;
-  image[((size_t)view * 3 + 2) * HW + pix] = C2;
-  final_T[(size_t)view * HW + pix] = Tr;
-  n_contrib[(size_t)view * HW + pix] = last;
-  if constexpr (NU > 0) {
+#pragma unroll
+  for (int q = 0; q < kPixPerThread; ++q) {
+    if (!(px[q] < fr.width && py[q] < fr.height)) continue;
+    const FwdPixel<NU>& p = pix[q];
+    const size_t at = (size_t)py[q] * fr.width + px[q];
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) image[((size_t)view * 3 + ch) * HW + at] = p.C[ch];
+    final_T[(size_t)view * HW + at] = p.T;
+    n_contrib[(size_t)view * HW + at] = p.last;
 #pragma unroll
     for (int k = 0; k < NU; ++k)
 #pragma unroll
-      for (int ch = 0; ch < 3; ++ch)
-        image_tan[(((size_t)k * fr.n_views + view) * 3 + ch) * HW + pix] = Cd[k][ch];
+      for (int ch = 0; ch < 3; ++ch) image_tan[(((size_t)k * fr.n_views + view) * 3 + ch) * HW + at] = p.Cd[k][ch];
   }
 }
 
@@ -262,12 +305,12 @@ __device__ __forceinline__ float warp_reduce_scatter16(float (&v)[32]) {
 // Minimum resident CTAs per SM requested from the compiler for the reverse
 // kernel (0: no request).
 #ifndef GS_BWD_MIN_BLOCKS
-#define GS_BWD_MIN_BLOCKS 0
+#define GS_BWD_MIN_BLOCKS 8
 #endif
 #if GS_BWD_MIN_BLOCKS > 0
-#define GS_BWD_BOUNDS __launch_bounds__(256, GS_BWD_MIN_BLOCKS)
+#define GS_BWD_BOUNDS __launch_bounds__(128, GS_BWD_MIN_BLOCKS)
 #else
-#define GS_BWD_BOUNDS __launch_bounds__(256)
+#define GS_BWD_BOUNDS __launch_bounds__(128)
 #endif
 
 // Warp sums of v[0..31] delivered as quads: afterwards every lane L with
@@ -322,6 +365,53 @@ __device__ __forceinline__ void warp_reduce_quads16(float (&v)[32], float (&q)[4
 // whole float4s so that rows can be added and read as vectors.
 __host__ __device__ constexpr int cot_stride(int streams) { return (9 * streams + 3) & ~3; }
 
+// Reverse-pass state of one pixel: the cotangent dL/dC of each stream, the
+// transmittance being recovered back to front, the colour suffix
+// sum_{j>i} c_j a_j T_j, and the list position after its last blended splat.
+template <int S>
+struct BwdPixel {
+  float w[S][3];
+  float T, suf[3];
+  float pxc, pyc;
+  uint32_t nc;
+};
+
+// The reverse of one blended splat at one pixel: recover T_i = T_{i+1}/(1 - a),
+// dC/da = c T_i - suffix/(1 - a), and add the pixel's derivatives of the splat's
+// (mx, my, A, B, C, o, r, g, b) for every stream to v.
+template <int S>
+__device__ __forceinline__ void bwd_accumulate(BwdPixel<S>& p, const Rec& r, float dx, float dy, float G, float oG,
+                                               float alpha, float (&v)[32]) {
+  const float om = 1.f - alpha;
+  const float Ti = p.T / om;
+  const float rgb0 = r.b.z, rgb1 = r.b.w, rgb2 = r.c.x;
+  const float da0 = rgb0 * Ti - p.suf[0] / om;
+  const float da1 = rgb1 * Ti - p.suf[1] / om;
+  const float da2 = rgb2 * Ti - p.suf[2] / om;
+  const float aT = alpha * Ti;
+  p.suf[0] += rgb0 * aT;
+  p.suf[1] += rgb1 * aT;
+  p.suf[2] += rgb2 * aT;
+  p.T = Ti;
+  const bool capped = oG > kAlphaMax;
+  const float fmx = -(r.a.z * dx + r.a.w * dy), fmy = -(r.b.x * dy + r.a.w * dx);
+  const float fA = -0.5f * dx * dx, fB = -dx * dy, fC = -0.5f * dy * dy;
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    const float ga = p.w[s][0] * da0 + p.w[s][1] * da1 + p.w[s][2] * da2;
+    const float gp = capped ? 0.f : ga * alpha;
+    v[9 * s + 0] += fmx * gp;
+    v[9 * s + 1] += fmy * gp;
+    v[9 * s + 2] += fA * gp;
+    v[9 * s + 3] += fB * gp;
+    v[9 * s + 4] += fC * gp;
+    v[9 * s + 5] += capped ? 0.f : ga * G;
+    v[9 * s + 6] += p.w[s][0] * aT;
+    v[9 * s + 7] += p.w[s][1] * aT;
+    v[9 * s + 8] += p.w[s][2] * aT;
+  }
+}
+
 template <int NU, bool GRAD>
 __global__ void GS_BWD_BOUNDS raster_bwd_kernel(
     const float4* __restrict__ rec, const uint32_t* __restrict__ vals, const uint32_t* __restrict__ ranges,
@@ -330,42 +420,48 @@ __global__ void GS_BWD_BOUNDS raster_bwd_kernel(
     int loss_kind, float gn_floor, float inv_m, float* __restrict__ cot, float* __restrict__ loss_out,
     int32_t* status) {
   constexpr int S = (GRAD ? 1 : 0) + NU;  // cotangent streams
-  constexpr int NV = 9 * S;               // values per splat
-  constexpr int NVP = cot_stride(S);      // their padded row stride
+  constexpr int NVP = cot_stride(S);      // padded row stride of their 9 S values
   static_assert(NVP <= 32, "streams");
   extern __shared__ __align__(16) unsigned char smem[];
-  const int nthr = blockDim.x;
+  const int nthr = blockDim.x, nwarps = nthr >> 5, batch = kBatchPerThread * nthr;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
   Rec* buf = reinterpret_cast<Rec*>(smem + 16);
-  uint32_t* s_idx = reinterpret_cast<uint32_t*>(buf + 2 * nthr);
+  uint32_t* s_idx = reinterpret_cast<uint32_t*>(buf + 2 * batch);
+  uint32_t* s_mask = s_idx + 2 * batch;
   __shared__ uint32_t s_max;
   __shared__ float s_loss[8];
-  uint32_t* s_mask = s_idx + 2 * nthr;
-  const int tid = threadIdx.x, lane = tid & 31, nwarps = nthr >> 5;
+  const int tid = threadIdx.x, lane = tid & 31;
   const uint32_t wbit = 1u << (tid >> 5);
   const int view = blockIdx.x / T, tile = blockIdx.x - view * T;
   const int ty = tile / Tx, tx = tile - ty * Tx;
   int lx, ly;
   pixel_of(tid, fr.tile_w, lx, ly);
-  const int px = tx * fr.tile_w + lx, py = ty * fr.tile_h + ly;
   const float tile_x0 = (float)(tx * fr.tile_w), tile_y0 = (float)(ty * fr.tile_h);
-  const bool inside = px < fr.width && py < fr.height;
-  const float pxc = (float)px + 0.5f, pyc = (float)py + 0.5f;
   const size_t tslot = 2 * ((size_t)view * T + tile);
   const uint32_t start = ranges[tslot], list_len = ranges[tslot + 1] - start;
   const size_t HW = (size_t)fr.width * fr.height;
-  const size_t pix = (size_t)py * fr.width + px;
 
   // per-pixel cotangents dL/dC of each stream and the loss
-  float w[S > 0 ? S : 1][3];
-  float Tr = 0.f, lossp = 0.f;
-  uint32_t nc = 0;
-  if (inside) {
-    Tr = final_T[(size_t)view * HW + pix];
-    nc = n_contrib[(size_t)view * HW + pix];
+  BwdPixel<S> pix[kPixPerThread];
+  float lossp = 0.f;
+#pragma unroll
+  for (int q = 0; q < kPixPerThread; ++q) {
+    BwdPixel<S>& p = pix[q];
+    const int px = tx * fr.tile_w + lx, py = ty * fr.tile_h + ly + 4 * q;
+    p.pxc = (float)px + 0.5f;
+    p.pyc = (float)py + 0.5f;
+    p.suf[0] = p.suf[1] = p.suf[2] = 0.f;
+    p.T = 0.f;
+    p.nc = 0;
+#pragma unroll
+    for (int st = 0; st < S; ++st) p.w[st][0] = p.w[st][1] = p.w[st][2] = 0.f;
+    if (!(px < fr.width && py < fr.height)) continue;
+    const size_t at0 = (size_t)py * fr.width + px;
+    p.T = final_T[(size_t)view * HW + at0];
+    p.nc = n_contrib[(size_t)view * HW + at0];
 #pragma unroll
     for (int ch = 0; ch < 3; ++ch) {
-      const size_t at = ((size_t)view * 3 + ch) * HW + pix;
+      const size_t at = ((size_t)view * 3 + ch) * HW + at0;
       const float r = image[at] - target[at];
       const float ar = fabsf(r);
       float lam;
@@ -376,14 +472,11 @@ __global__ void GS_BWD_BOUNDS raster_bwd_kernel(
         lossp += 0.5f * inv_m * r * r;
         lam = 1.f;
       }
-      if constexpr (GRAD) w[0][ch] = (loss_kind == GS_LOSS_L1) ? (0.5f * inv_m) * ((r > 0.f) - (r < 0.f)) : inv_m * r;
+      if constexpr (GRAD) p.w[0][ch] = (loss_kind == GS_LOSS_L1) ? (0.5f * inv_m) * ((r > 0.f) - (r < 0.f)) : inv_m * r;
 #pragma unroll
       for (int k = 0; k < NU; ++k)
-        w[(GRAD ? 1 : 0) + k][ch] = inv_m * lam * image_tan[(((size_t)k * fr.n_views + view) * 3 + ch) * HW + pix];
+        p.w[(GRAD ? 1 : 0) + k][ch] = inv_m * lam * image_tan[(((size_t)k * fr.n_views + view) * 3 + ch) * HW + at0];
     }
-  } else {
-#pragma unroll
-    for (int s = 0; s < S; ++s) w[s][0] = w[s][1] = w[s][2] = 0.f;
   }
   if (tid == 0) {
     s_max = 0;
@@ -392,8 +485,9 @@ __global__ void GS_BWD_BOUNDS raster_bwd_kernel(
     fence_mbar_init();
   }
   __syncthreads();
-  if (nc) atomicMax(&s_max, nc);
-  const uint32_t warp_nc = __reduce_max_sync(0xffffffffu, nc);  // list positions this warp still needs
+  const uint32_t nc_thread = max(pix[0].nc, pix[1].nc);
+  if (nc_thread) atomicMax(&s_max, nc_thread);
+  const uint32_t warp_nc = __reduce_max_sync(0xffffffffu, nc_thread);  // list positions this warp still needs
   // objective: warp then block reduction, one atomic per CTA
   if (loss_out) {
     float lsum = lossp;
@@ -404,92 +498,72 @@ __global__ void GS_BWD_BOUNDS raster_bwd_kernel(
   __syncthreads();
   if (loss_out && tid == 0) {
     float tot = 0.f;
-    for (int k = 0; k < (nthr >> 5); ++k) tot += s_loss[k];
+    for (int k = 0; k < nwarps; ++k) tot += s_loss[k];
     atomicAdd(loss_out, tot);
   }
   const int n = (int)min(s_max, list_len);  // n_contrib never exceeds the tile's list
-  const int nb = (n + nthr - 1) / nthr;
-  float suf0 = 0.f, suf1 = 0.f, suf2 = 0.f;
-  if (nb > 0)
-    stage_batch<0>(nb - 1, nthr, start, n, view, n_pad, vals, rec, nullptr, buf, nullptr, s_idx, bars);
+  const int nb = (n + batch - 1) / batch;
+  if (nb > 0) stage_batch<0>(nb - 1, batch, start, n, view, n_pad, vals, rec, nullptr, buf, nullptr, s_idx, bars);
   __syncthreads();  // publish s_idx of the first batch
   int uses = 0;  // batches waited on so far, for the barrier parity
   for (int b = nb - 1; b >= 0; --b) {
     if (b - 1 >= 0)
-      stage_batch<0>(b - 1, nthr, start, n, view, n_pad, vals, rec, nullptr, buf, nullptr, s_idx, bars);
+      stage_batch<0>(b - 1, batch, start, n, view, n_pad, vals, rec, nullptr, buf, nullptr, s_idx, bars);
     const int bi = b & 1;
     // batch b is the (nb - 1 - b)-th use overall; buffer bi has been used
-    // floor((nb - 1 - b) / 2) times before (buffers alternate)
-    // block-uniform, since the warps below shuffle with full masks
+    // floor((nb - 1 - b) / 2) times before (buffers alternate).  Block-uniform,
+    // since the warps below shuffle with full masks.
     const bool ok = __syncthreads_and(mbar_wait_bounded(&bars[bi], (uint32_t)((uses >> 1) & 1), status)) != 0;
     ++uses;
-    const int cnt = min(nthr, n - b * nthr);
-    const Rec* bb = buf + bi * nthr;
-    if (tid < cnt) s_mask[tid] = ok ? warp_block_mask(bb[tid], tile_x0, tile_y0, fr.tile_w, nwarps) : 0u;
+    const int cnt = min(batch, n - b * batch);
+    const Rec* bb = buf + bi * batch;
+    for (int q = tid; q < cnt; q += nthr)
+      s_mask[q] = ok ? warp_block_mask(bb[q], tile_x0, tile_y0, fr.tile_w, nwarps) : 0u;
     __syncthreads();
     // the warp walks, back to front, only the splats its block can see and
     // that lie before its last contributor: one ballot per 32 splats
     for (int j0 = ((cnt - 1) & ~31); ok && j0 >= 0; j0 -= 32) {
       const int jl = j0 + lane;
-      uint32_t bits = __ballot_sync(0xffffffffu, jl < cnt && (uint32_t)(b * nthr + jl) < warp_nc && (s_mask[jl] & wbit));
+      uint32_t bits = __ballot_sync(0xffffffffu, jl < cnt && (uint32_t)(b * batch + jl) < warp_nc && (s_mask[jl] & wbit));
       while (bits) {
         const int hb = 31 - __clz(bits);
         bits &= ~(1u << hb);
         const int j = j0 + hb;
-        const uint32_t pos = (uint32_t)(b * nthr + j);
+        const uint32_t pos = (uint32_t)(b * batch + j);
         const Rec r = bb[j];
-        const float dx = __fsub_rn(r.a.x, pxc), dy = __fsub_rn(r.a.y, pyc);
-        bool on = pos < nc;
-        float power = 0.f, G = 0.f, alpha = 0.f, oG = 0.f;
-        if (on) {
-          power = splat_power(r, dx, dy);
-          on = power <= 0.f;
+        bool on[kPixPerThread];
+        float dx[kPixPerThread], dy[kPixPerThread], G[kPixPerThread], oG[kPixPerThread], alpha[kPixPerThread];
+#pragma unroll
+        for (int q = 0; q < kPixPerThread; ++q) {
+          dx[q] = __fsub_rn(r.a.x, pix[q].pxc);
+          dy[q] = __fsub_rn(r.a.y, pix[q].pyc);
+          on[q] = pos < pix[q].nc;
+          G[q] = oG[q] = alpha[q] = 0.f;
+          if (on[q]) {
+            const float power = splat_power(r, dx[q], dy[q]);
+            on[q] = power <= 0.f;
+            if (on[q]) {
+              G[q] = __expf(power);
+              oG[q] = __fmul_rn(r.b.y, G[q]);
+              alpha[q] = fminf(kAlphaMax, oG[q]);
+              on[q] = alpha[q] >= kAlphaMin;
+            }
+          }
         }
-        if (on) {
-          G = __expf(power);
-          oG = __fmul_rn(r.b.y, G);
-          alpha = fminf(kAlphaMax, oG);
-          on = alpha >= kAlphaMin;
-        }
-        if (!__any_sync(0xffffffffu, on)) continue;
+        if (!__any_sync(0xffffffffu, on[0] || on[1])) continue;
         float v[32];
 #pragma unroll
         for (int q = 0; q < 32; ++q) v[q] = 0.f;
-        if (on) {
-          const float om = 1.f - alpha;
-          const float Ti = Tr / om;
-          const float rgb0 = r.b.z, rgb1 = r.b.w, rgb2 = r.c.x;
-          const float da0 = rgb0 * Ti - suf0 / om;
-          const float da1 = rgb1 * Ti - suf1 / om;
-          const float da2 = rgb2 * Ti - suf2 / om;
-          const float aT = alpha * Ti;
-          suf0 += rgb0 * aT;
-          suf1 += rgb1 * aT;
-          suf2 += rgb2 * aT;
-          Tr = Ti;
-          const bool capped = oG > kAlphaMax;
 #pragma unroll
-          for (int s = 0; s < S; ++s) {
-            const float ga = w[s][0] * da0 + w[s][1] * da1 + w[s][2] * da2;
-            const float gp = capped ? 0.f : ga * alpha;
-            v[9 * s + 0] = -(r.a.z * dx + r.a.w * dy) * gp;
-            v[9 * s + 1] = -(r.b.x * dy + r.a.w * dx) * gp;
-            v[9 * s + 2] = -0.5f * dx * dx * gp;
-            v[9 * s + 3] = -dx * dy * gp;
-            v[9 * s + 4] = -0.5f * dy * dy * gp;
-            v[9 * s + 5] = capped ? 0.f : ga * G;
-            v[9 * s + 6] = w[s][0] * aT;
-            v[9 * s + 7] = w[s][1] * aT;
-            v[9 * s + 8] = w[s][2] * aT;
-          }
-        }
-        const uint32_t gi = s_idx[bi * nthr + j];
+        for (int q = 0; q < kPixPerThread; ++q)
+          if (on[q]) bwd_accumulate<S>(pix[q], r, dx[q], dy[q], G[q], oG[q], alpha[q], v);
+        const uint32_t gi = s_idx[bi * batch + j];
         float* dst = cot + ((size_t)view * n_pad + gi) * NVP;
-        float q[4];
-        if constexpr (NVP <= 16) warp_reduce_quads16(v, q);
-        else warp_reduce_quads32(v, q);
-        if ((lane & 3) == 0 && lane < NVP && (q[0] != 0.f || q[1] != 0.f || q[2] != 0.f || q[3] != 0.f))
-          atomicAdd(reinterpret_cast<float4*>(dst + lane), make_float4(q[0], q[1], q[2], q[3]));
+        float qs[4];
+        if constexpr (NVP <= 16) warp_reduce_quads16(v, qs);
+        else warp_reduce_quads32(v, qs);
+        if ((lane & 3) == 0 && lane < NVP && (qs[0] != 0.f || qs[1] != 0.f || qs[2] != 0.f || qs[3] != 0.f))
+          atomicAdd(reinterpret_cast<float4*>(dst + lane), make_float4(qs[0], qs[1], qs[2], qs[3]));
       }
     }
     __syncthreads();
@@ -849,11 +923,11 @@ template <int NU>
 gs_status launch_fwd(const gs_projected* proj, const gs_sorted* sorted, int n_pad, gs_frame fr, float* image,
                      float* final_T, uint32_t* n_contrib, float* image_tan, int32_t* status, cudaStream_t st) {
   const TileGrid g = tile_grid(fr);
-  const int nthr = fr.tile_w * fr.tile_h;
-  const size_t smem = 16 + (size_t)nthr * (2 * sizeof(Rec) * (1 + NU) + sizeof(uint32_t));
+  const int nthr = fr.tile_w * fr.tile_h / kPixPerThread, batch = kBatchPerThread * nthr;
+  const size_t smem = 16 + (size_t)batch * (2 * sizeof(Rec) * (1 + NU) + sizeof(uint32_t));
   static bool attr = false;
   if (!attr) {
-    if (allow_smem(raster_fwd_kernel<NU>, 16 + (size_t)256 * (2 * sizeof(Rec) * (1 + NU) + sizeof(uint32_t))) != cudaSuccess)
+    if (allow_smem(raster_fwd_kernel<NU>, 16 + (size_t)128 * kBatchPerThread * (2 * sizeof(Rec) * (1 + NU) + sizeof(uint32_t))) != cudaSuccess)
       return check_launch("gs_raster_fwd: smem attribute");
     attr = true;
   }
@@ -875,8 +949,8 @@ void launch_bwd_kernels(const gs_params* x, const gs_camera* cams, const gs_proj
                         const uint32_t* n_contrib, const float* image_tan, const gs_probe* probe, gs_loss loss,
                         float* grad, float* hz, float* loss_out, float* cot, int32_t* status, cudaStream_t st) {
   const TileGrid g = tile_grid(fr);
-  const int nthr = fr.tile_w * fr.tile_h;
-  const size_t smem = 16 + (size_t)nthr * (2 * sizeof(Rec) + 3 * sizeof(uint32_t));
+  const int nthr = fr.tile_w * fr.tile_h / kPixPerThread, batch = kBatchPerThread * nthr;
+  const size_t smem = 16 + (size_t)batch * (2 * sizeof(Rec) + 3 * sizeof(uint32_t));
   const float inv_m = (float)(1.0 / (3.0 * (double)fr.width * fr.height * fr.n_views));
   const unsigned blocks = (unsigned)((size_t)fr.n_views * g.T);
   raster_bwd_kernel<NU, GRAD><<<blocks, nthr, smem, st>>>(
