@@ -63,6 +63,10 @@ def lib():
             L.or_shd_radius.argtypes = [P, i64, i64, i32, d, P, P]
             L.or_tr_update.argtypes = [P, P, P, P, P, i64, i64, i32, P, C.c_int64, d, P]
             L.or_project_tangent.argtypes = [P, i64, i64, i32, P, P, P]
+            L.or_render_pixels.argtypes = [P, i64, i64, i32, P, i32, i32, i64, P, P, u64, C.c_int64, i32, P, P, P,
+                                           P, P]
+            L.or_backward_sampled.argtypes = [P, i64, i64, i32, P, i32, i32, i32, P, i32, d, u64, C.c_int64, i32,
+                                              i64, P, P, P, P]
             L.or_signature.argtypes = [P, i64, i64, i32, P, i32, i32, i32, P]
             L.or_hellinger.restype = d
             L.or_hellinger.argtypes = [P, P, d, P, P, d]
@@ -276,3 +280,38 @@ def tr_update(x, g_ema, d_ema, grad, hz, deg: int, t: int, eps: float, cfg=None)
     eta = np.zeros_like(x)
     lib().or_tr_update(_p(x), _p(g), _p(d), _p(gr), _p(h), n, n, deg, _p(cfg), t, eps, _p(eta))
     return x, g, d, eta
+
+
+# ------------------------------------------------------------- sampled outputs
+def render_pixels(P: np.ndarray, deg: int, cam, xs, ys, *, seed: int = 42, t: int = 1, nu: int = 0,
+                  tw: int = 16, th: int = 16):
+    """Colour, T, n_contrib, margin and (nu > 0) image tangents at chosen pixels of one view."""
+    P = _f64(P)
+    rows, n = P.shape
+    xs = np.ascontiguousarray(xs, np.int32)
+    ys = np.ascontiguousarray(ys, np.int32)
+    k = len(xs)
+    rgb = np.zeros((k, 3))
+    T = np.zeros(k)
+    nc = np.zeros(k, np.int32)
+    mg = np.zeros(k)
+    jz = np.zeros((k, max(nu, 1), 3))
+    lib().or_render_pixels(_p(P), n, n, deg, _p(camera_array([cam])), tw, th, k, _p(xs), _p(ys), seed, t, nu,
+                           _p(rgb), _p(T), _p(nc), _p(mg), _p(jz))
+    return dict(rgb=rgb, final_T=T, n_contrib=nc, margin=mg, jz=jz[:, :nu])
+
+
+def backward_sampled(P: np.ndarray, deg: int, cams, target: np.ndarray, samples, *, loss_kind: int = 0,
+                     gn_floor: float = 1e-3, seed: int = 42, t: int = 1, nu: int = 0, tw: int = 16, th: int = 16):
+    """Gradient and Hutchinson rows of chosen Gaussians over a full frame of views, with comparability flags."""
+    P = _f64(P)
+    rows, n = P.shape
+    tg = _f64(target)
+    smp = np.ascontiguousarray(samples, np.int64)
+    k = len(smp)
+    grad = np.zeros((k, rows))
+    hz = np.zeros((k, rows))
+    flag = np.zeros(k, np.int32)
+    lib().or_backward_sampled(_p(P), n, n, deg, _p(camera_array(cams)), len(cams), tw, th, _p(tg), loss_kind,
+                              gn_floor, seed, t, nu, k, _p(smp), _p(grad), _p(hz if nu > 0 else None), _p(flag))
+    return dict(grad=grad, hz=hz if nu > 0 else None, flag=flag)

@@ -331,6 +331,8 @@ struct View {
   // per splat, the tile rectangle when its FP32 inputs are moved to the edges of
   // their rounding uncertainty (lo shrinks, hi grows): x0, x1, y0, y1
   std::vector<int> lo, hi;
+  // per tile, the splats that may enter or leave it under rounding
+  std::vector<std::vector<int>> amb;
 };
 
 // Rounding envelopes of the FP32 inputs of a binning decision: the radius
@@ -376,17 +378,17 @@ View build_view(const double* P, long pitch, long n, int deg, const double* cam2
       bin_and_sort(1, n, mx.data(), my.data(), rad.data(), dp.data(), V.cam.W, V.cam.H, tw, th);
   V.lists.assign((size_t)V.Tx * V.Ty, {});
   for (const Pair& p : pairs) V.lists[p.key >> 32].push_back((int)p.val);
+  V.amb.assign((size_t)V.Tx * V.Ty, {});
+  for (long i = 0; i < n; ++i) {
+    if (!V.sp[i].valid) continue;
+    const int* h = &V.hi[4 * i];
+    const int* l = &V.lo[4 * i];
+    if (h[0] == l[0] && h[1] == l[1] && h[2] == l[2] && h[3] == l[3]) continue;
+    for (int ty = h[2]; ty < h[3]; ++ty)
+      for (int tx = h[0]; tx < h[1]; ++tx)
+        if (!(tx >= l[0] && tx < l[1] && ty >= l[2] && ty < l[3])) V.amb[(size_t)ty * V.Tx + tx].push_back((int)i);
+  }
   return V;
-}
-
-// A splat may enter or leave tile (tx, ty) under rounding if the tile lies in its
-// grown rectangle but not in its shrunk one.
-bool tile_ambiguous(const View& V, long i, int tx, int ty) {
-  const int* l = &V.lo[4 * i];
-  const int* h = &V.hi[4 * i];
-  bool in_hi = tx >= h[0] && tx < h[1] && ty >= h[2] && ty < h[3];
-  bool in_lo = tx >= l[0] && tx < l[1] && ty >= l[2] && ty < l[3];
-  return in_hi && !in_lo;
 }
 
 // --------------------------------------------------------------- blending
@@ -450,8 +452,8 @@ double binning_margin(const View& V, int tx, int ty, double pcx, double pcy) {
     double power = -0.5 * (g.A * dx * dx + g.C * dy * dy) - g.B * dx * dy;
     return g.o * std::exp(power) >= 0.5 * kAlphaMin;
   };
-  for (long i = 0; i < (long)V.sp.size(); ++i)
-    if (V.sp[i].valid && tile_ambiguous(V, i, tx, ty) && visible_at(i)) return 0.0;
+  for (int i : V.amb[(size_t)ty * V.Tx + tx])
+    if (visible_at(i)) return 0.0;
   for (size_t k = 1; k < list.size(); ++k) {
     double d0 = V.sp[list[k - 1]].depth, d1 = V.sp[list[k]].depth;
     if (std::fabs(d1 - d0) <= 1e-6 * std::fabs(d1) && visible_at(list[k - 1]) && visible_at(list[k]))
@@ -1049,6 +1051,165 @@ void or_signature(const double* P, long pitch, long n, int deg, const double* ca
       sig[off + (long)y * V.cam.W + x] = h;
     });
     off += (long)V.cam.W * V.cam.H;
+  }
+}
+
+// Tangent splats (probe k) of the splats listed for one tile, in list order.
+std::vector<Splat<Dual>> tile_tangents(const View& V, const std::vector<int>& list, const double* P, long pitch,
+                                       int deg, uint64_t seed, int64_t t, int k, long n) {
+  int rows = n_rows(deg);
+  std::vector<Splat<Dual>> out(list.size());
+  std::vector<double> tan(rows);
+  for (size_t q = 0; q < list.size(); ++q) {
+    long i = list[q];
+    for (int r = 0; r < rows; ++r) tan[r] = rademacher(seed, t, k, (uint64_t)r * n + i);
+    out[q] = project(load_gaussian<Dual>(P, pitch, i, deg, tan.data()), V.cam);
+  }
+  return out;
+}
+
+// Sampled pixels of one view (coordinates xs, ys): colour (npix x 3), final T,
+// n_contrib, the decision margin as in or_render, and, if nu > 0, the image
+// tangents J z_k (npix x nu x 3) for the probes of (seed, t).
+void or_render_pixels(const double* P, long pitch, long n, int deg, const double* cam24, int tw, int th, long npix,
+                      const int32_t* xs, const int32_t* ys, uint64_t seed, int64_t t, int nu, double* rgb,
+                      double* T_out, int32_t* nc_out, double* margin, double* jz) {
+  View V = build_view(P, pitch, n, deg, cam24, tw, th);
+  std::vector<int> local;
+  for (long q = 0; q < npix; ++q) {
+    int x = xs[q], y = ys[q], tx = x / tw, ty = y / th;
+    const std::vector<int>& list = V.lists[(size_t)ty * V.Tx + tx];
+    double C[3], T, mg;
+    int nc;
+    blend(list, V.sp, x + 0.5, y + 0.5, C, T, nc, &mg, nullptr);
+    for (int ch = 0; ch < 3; ++ch) rgb[3 * q + ch] = C[ch];
+    T_out[q] = T;
+    nc_out[q] = nc;
+    margin[q] = std::min(mg, binning_margin(V, tx, ty, x + 0.5, y + 0.5));
+    if (nu > 0) {
+      local.resize(list.size());
+      for (size_t u = 0; u < list.size(); ++u) local[u] = (int)u;
+      for (int k = 0; k < nu; ++k) {
+        std::vector<Splat<Dual>> sd = tile_tangents(V, list, P, pitch, deg, seed, t, k, n);
+        Dual Cd[3], Td;
+        int ncd;
+        blend(local, sd, x + 0.5, y + 0.5, Cd, Td, ncd, nullptr, nullptr);
+        for (int ch = 0; ch < 3; ++ch) jz[(q * nu + k) * 3 + ch] = Cd[ch].d;
+      }
+    }
+  }
+}
+
+// Gradient and Hutchinson rows (ns x rows each) of the sampled Gaussians of a
+// full frame of views, as or_backward would give for them: only pixels of the
+// tiles a Gaussian is listed in involve it.  flag[s] collects the reasons an
+// FP32 evaluation may legitimately take another discrete decision somewhere in
+// the sample's footprint: 1 its own tile set is within rounding of changing; at
+// a pixel where it is visible, 2 its own alpha / cap / power decision, 4 the
+// residual sign, 8 another splat's binning, 16 another splat's threshold decision
+// is within 1e-5 of flipping.
+void or_backward_sampled(const double* P, long pitch, long n, int deg, const double* cams, int n_views, int tw,
+                         int th, const double* target, int loss_kind, double gn_floor, uint64_t seed, int64_t t,
+                         int nu, long ns, const int64_t* samples, double* grad_out, double* hz_out, int32_t* flag) {
+  int rows = n_rows(deg);
+  double m = 0.0;
+  for (int v = 0; v < n_views; ++v) {
+    Cam c = make_cam(cams + 24 * v);
+    m += 3.0 * c.W * c.H;
+  }
+  for (long k = 0; k < ns * rows; ++k) {
+    grad_out[k] = 0.0;
+    if (hz_out) hz_out[k] = 0.0;
+  }
+  for (long sidx = 0; sidx < ns; ++sidx) flag[sidx] = 0;
+  long img_off = 0;
+  std::vector<double> g_acc(rows);
+  for (int v = 0; v < n_views; ++v) {
+    View V = build_view(P, pitch, n, deg, cams + 24 * v, tw, th);
+    long HW = (long)V.cam.W * V.cam.H;
+    const double* tg = target + img_off;
+    // tiles that list a sampled Gaussian
+    std::vector<char> need((size_t)V.Tx * V.Ty, 0);
+    for (long sidx = 0; sidx < ns; ++sidx) {
+      long i = samples[sidx];
+      if (!V.sp[i].valid) continue;
+      const int* h = &V.hi[4 * i];
+      const int* l = &V.lo[4 * i];
+      if (!(h[0] == l[0] && h[1] == l[1] && h[2] == l[2] && h[3] == l[3])) flag[sidx] |= 1;
+      for (int ty = h[2]; ty < h[3]; ++ty)
+        for (int tx = h[0]; tx < h[1]; ++tx) need[(size_t)ty * V.Tx + tx] = 1;
+    }
+    std::vector<std::vector<double>> cot(1 + nu, std::vector<double>((size_t)n * NQ, 0.0));
+    std::vector<int> local;
+    for (int ty = 0; ty < V.Ty; ++ty)
+      for (int tx = 0; tx < V.Tx; ++tx) {
+        if (!need[(size_t)ty * V.Tx + tx]) continue;
+        const std::vector<int>& list = V.lists[(size_t)ty * V.Tx + tx];
+        std::vector<std::vector<Splat<Dual>>> sd(nu);
+        for (int k = 0; k < nu; ++k) sd[k] = tile_tangents(V, list, P, pitch, deg, seed, t, k, n);
+        local.resize(list.size());
+        for (size_t u = 0; u < list.size(); ++u) local[u] = (int)u;
+        for (int y = ty * th; y < std::min((ty + 1) * th, V.cam.H); ++y)
+          for (int x = tx * tw; x < std::min((tx + 1) * tw, V.cam.W); ++x) {
+            double C[3], T, mg;
+            int nc;
+            std::vector<Contrib> tr;
+            blend(list, V.sp, x + 0.5, y + 0.5, C, T, nc, &mg, &tr);
+            long px = (long)y * V.cam.W + x;
+            double w[3], wgn[3], rmin = kInf;
+            for (int ch = 0; ch < 3; ++ch) {
+              double r = C[ch] - tg[ch * HW + px];
+              rmin = std::min(rmin, std::fabs(r));
+              if (loss_kind == 0) {
+                w[ch] = (r > 0 ? 1.0 : (r < 0 ? -1.0 : 0.0)) / (2.0 * m);
+                wgn[ch] = 1.0 / (4.0 * std::max(std::fabs(r), gn_floor)) / m;
+              } else {
+                w[ch] = r / m;
+                wgn[ch] = 1.0 / m;
+              }
+            }
+            const double mb = binning_margin(V, tx, ty, x + 0.5, y + 0.5);
+            // reasons a sample visible here may see another decision in FP32:
+            // 2 its own alpha / cap / power decision within 1e-5, 4 the residual
+            // sign, 8 another splat's binning, 16 another splat's threshold decision
+            for (long sidx = 0; sidx < ns; ++sidx) {
+              const Splat<double>& g = V.sp[samples[sidx]];
+              if (!g.valid) continue;
+              double dx = g.mx - (x + 0.5), dy = g.my - (y + 0.5);
+              double power = -0.5 * (g.A * dx * dx + g.C * dy * dy) - g.B * dx * dy;
+              double oG = g.o * std::exp(power);
+              if (oG < 0.5 * kAlphaMin) continue;
+              double own = std::min({std::fabs(std::min(oG, kAlphaMax) - kAlphaMin) / kAlphaMin,
+                                     std::fabs(oG - kAlphaMax) / kAlphaMax, std::fabs(power) * 1e6});
+              if (own < 1e-5) flag[sidx] |= 2;
+              if (rmin < 1e-5) flag[sidx] |= 4;
+              if (mb < 1e-5) flag[sidx] |= 8;
+              if (mg < 1e-5) flag[sidx] |= 16;
+            }
+            blend_reverse(tr, V.sp, w, cot[0].data());
+            for (int k = 0; k < nu; ++k) {
+              Dual Cd[3], Td;
+              int ncd;
+              blend(local, sd[k], x + 0.5, y + 0.5, Cd, Td, ncd, nullptr, nullptr);
+              double wk[3];
+              for (int ch = 0; ch < 3; ++ch) wk[ch] = wgn[ch] * Cd[ch].d;
+              blend_reverse(tr, V.sp, wk, cot[1 + k].data());
+            }
+          }
+      }
+    for (long sidx = 0; sidx < ns; ++sidx) {
+      long i = samples[sidx];
+      if (!V.sp[i].valid) continue;
+      for (int st = 0; st <= nu; ++st) {
+        std::fill(g_acc.begin(), g_acc.end(), 0.0);
+        project_reverse(P, pitch, i, deg, V.cam, cot[st].data() + i * NQ, g_acc);
+        for (int r = 0; r < rows; ++r) {
+          if (st == 0) grad_out[sidx * rows + r] += g_acc[r];
+          else hz_out[sidx * rows + r] += rademacher(seed, t, st - 1, (uint64_t)r * n + i) * g_acc[r] / nu;
+        }
+      }
+    }
+    img_off += 3 * HW;
   }
 }
 

@@ -174,3 +174,29 @@ def test_hvp_stream_uses_regenerated_probes():
     rows, n = P.shape
     z = np.array([O.rademacher(5, 2, 0, j) for j in range(rows * n)]).reshape(rows, n)
     np.testing.assert_allclose(out["image_tangent"][0], O.jvp(P, deg, [cam], z), atol=1e-13)
+
+
+def test_sampled_entry_points_reproduce_the_full_ones():
+    """The sampled pixel and sampled-Gaussian paths (used at full workload size)
+    agree with the full-frame oracle functions."""
+    deg, nu = 1, 2
+    sc = S.make_scene(200, deg, seed=44, extent=0.7, log_scale_shift=math.log(2.0))
+    cams = S.camera_ring(2, 48, 40, 0.7, seed=5, ring_factor=5.0)
+    tg = S.noise_target(2, 40, 48, seed=6).astype(np.float64)
+    P = O.params64(sc)
+    full = O.render(P, deg, cams)
+    bw = O.backward(P, deg, cams, tg, seed=9, t=3, nu=nu, want_tangents=True)
+    rng = np.random.default_rng(0)
+    xs, ys = rng.integers(0, 48, 60), rng.integers(0, 40, 60)
+    for v in range(2):
+        px = O.render_pixels(P, deg, cams[v], xs, ys, seed=9, t=3, nu=nu)
+        np.testing.assert_allclose(px["rgb"], full["image"][v][:, ys, xs].T, atol=1e-15)
+        np.testing.assert_allclose(px["final_T"], full["final_T"][v][ys, xs], atol=1e-15)
+        np.testing.assert_array_equal(px["n_contrib"], full["n_contrib"][v][ys, xs])
+        np.testing.assert_allclose(px["margin"], full["margin"][v][ys, xs])
+        for k in range(nu):
+            np.testing.assert_allclose(px["jz"][:, k, :], bw["image_tangent"][k, v][:, ys, xs].T, atol=1e-14)
+    smp = rng.choice(sc.n, 25, replace=False)
+    out = O.backward_sampled(P, deg, cams, tg, smp, seed=9, t=3, nu=nu)
+    np.testing.assert_allclose(out["grad"], bw["grad"][:, smp].T, rtol=1e-10, atol=1e-14)
+    np.testing.assert_allclose(out["hz"], bw["hz"][:, smp].T, rtol=1e-10, atol=1e-14)
