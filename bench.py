@@ -199,6 +199,54 @@ def timed_steps(eng, cam_dev, targets, K, W0, t0, stream, per_call=False):
     return total, per
 
 
+def plain_loop_steps(eng, cam_dev, targets, K, t0, stream, device):
+    """The same steps issued one view at a time (the plain loop): for each of the
+    8 views project / bin-sort / forward / reverse pass on a single-view frame,
+    then the per-view gradients and Hutchinson diagonals, each normalised by its
+    own residual count, are averaged, and one update is applied.  Returns ms per
+    step (device time, CUDA events)."""
+    import torch
+    from paper_2602_00395_gb300.engine import TRConfig, TRStep, eps_schedule
+    one = TRStep(eng.n, SH_DEG, 1, W, H, nu=NU, tile=TILE, cfg=TRConfig(l=1), capacity=eng.capacity, device=device)
+    one.x.copy_(eng.x)
+    g_acc = torch.zeros_like(one.grad)
+    h_acc = torch.zeros_like(one.hz)
+    HW3 = 3 * W * H
+    nb = len(targets)
+
+    def run(k0, k1):
+        for k in range(k0, k1):
+            t = t0 + k
+            b = (t - 1) % nb
+            g_acc.zero_()
+            h_acc.zero_()
+            for v in range(N_VIEWS):
+                one.cams = cam_dev[b][96 * v:96 * (v + 1)]
+                one.target = targets[b][HW3 * v:HW3 * (v + 1)]
+                one.project(t, True, stream)
+                one.bin_sort(stream)
+                one.raster_fwd(t, True, stream)
+                one.raster_bwd(t, True, stream)
+                g_acc.add_(one.grad, alpha=1.0 / N_VIEWS)
+                h_acc.add_(one.hz, alpha=1.0 / N_VIEWS)
+            one.grad.copy_(g_acc)
+            one.hz.copy_(h_acc)
+            one.update(t, eps_schedule(t, 30000), True, None, stream)
+
+    with torch.cuda.stream(stream):
+        run(0, 3)
+        start = torch.cuda.Event(enable_timing=True)
+        stop = torch.cuda.Event(enable_timing=True)
+        start.record(stream)
+        run(3, 3 + K)
+        stop.record(stream)
+    stop.synchronize()
+    ms = start.elapsed_time(stop) / K
+    del one
+    torch.cuda.empty_cache()
+    return ms
+
+
 def e2e_steps(eng, batches, host_targets, K, t0, stream):
     """K steps through the C ABI with the step's targets and cameras copied from
     pinned host memory and the loss copied back, all inside the timed region."""
@@ -348,6 +396,8 @@ def run_cuda(args):
     host_targets = [tg.cpu().pin_memory() for tg in targets]
     e2e_ms, e2e_wall, h2d, d2h = e2e_steps(eng, batches, host_targets, args.steps, 5000, stream)
     e2e_val = ws * args.steps / (e2e_ms / 1e3)
+    # the plain one-view-at-a-time loop on the same workload
+    plain_ms = plain_loop_steps(eng, cam_dev, targets, max(3, min(args.steps, 10)), 9000, stream, device)
     # roofline of the dominant call
     torch.cuda.synchronize()
     sum_nc = float(eng.n_contrib.double().sum().item())
@@ -387,6 +437,9 @@ def run_cuda(args):
             "per_call_ms": per_call, "status_word": status,
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "wall_s": e2e_wall},
+            "plain_loop": {"ms_per_step": plain_ms, "value": 1e3 / plain_ms, "unit": UNIT,
+                           "batched_speedup": (1e3 / ms_per_step) / (1e3 / plain_ms),
+                           "what": "8 single-view project/sort/fwd/bwd call sequences + averaged update, no batching"},
             "gpu_launches": kernel_launches_per_step(eng) * args.steps,
             "roofline": roof, "clocks": clocks, "cpu_baseline": cpu,
         }
