@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--n", type=int, default=N_GAUSS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-steps", type=int, default=0, help="run N untimed steps only (for ncu)")
+    ap.add_argument("--profile-views", type=int, default=N_VIEWS,
+                    help="views per step in a --profile-steps run (a smaller case for ncu captures)")
     return ap.parse_args()
 
 
@@ -113,7 +115,7 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ workload
-def make_workload(n, device, rank=0):
+def make_workload(n, device, rank=0, views=N_VIEWS, n_batches=None):
     import numpy as np
     import torch
     from paper_2602_00395_gb300 import synth as S
@@ -123,8 +125,9 @@ def make_workload(n, device, rank=0):
     scene = S.make_scene(n, SH_DEG, seed=1000 + rank, kind="clusters", extent=10.0)
     gt = S.make_scene(n, SH_DEG, seed=2000 + rank, kind="clusters", extent=10.0)
     cams = S.camera_ring(RING, W, H, 10.0, seed=7)
-    batches = [[cams[b + RING // N_VIEWS * k] for k in range(N_VIEWS)] for b in range(RING // N_VIEWS)]
-    eng = TRStep(n, SH_DEG, N_VIEWS, W, H, nu=NU, tile=TILE, cfg=TRConfig(l=1), device=device)
+    batches = [[cams[b + RING // views * k] for k in range(views)] for b in range(RING // views)]
+    batches = batches[:n_batches] if n_batches else batches
+    eng = TRStep(n, SH_DEG, views, W, H, nu=NU, tile=TILE, cfg=TRConfig(l=1), device=device)
     # targets: the ground-truth set rendered by the forward pass, one batch of views at a time
     eng.set_params(gt.params)
     cam_dev, targets = [], []
@@ -248,28 +251,51 @@ def plain_loop_steps(eng, cam_dev, targets, K, t0, stream, device):
 
 
 def e2e_steps(eng, batches, host_targets, K, t0, stream):
-    """K steps through the C ABI with the step's targets and cameras copied from
-    pinned host memory and the loss copied back, all inside the timed region."""
-    import numpy as np
+    """K steps through the C ABI with each step's targets and cameras copied from
+    pinned host memory and the loss copied back, all inside the timed region.
+    The copy of step k+1's inputs runs on a second stream into the other half of
+    a double buffer while step k computes."""
     import torch
     from paper_2602_00395_gb300 import gs3dtr as G
     from paper_2602_00395_gb300.engine import eps_schedule
     host_cams = [torch.from_numpy(G.camera_bytes(bc)).pin_memory() for bc in batches]
     loss_host = torch.zeros(K, dtype=torch.float32).pin_memory()
     nb = len(batches)
+    copy_stream = torch.cuda.Stream(device=stream.device)
+    dev_tg = [torch.empty_like(eng.target) for _ in range(2)]
+    dev_cams = [torch.empty_like(eng.cams) for _ in range(2)]
+    copied = [torch.cuda.Event() for _ in range(2)]
+    consumed = [torch.cuda.Event() for _ in range(2)]
     start = torch.cuda.Event(enable_timing=True)
     stop = torch.cuda.Event(enable_timing=True)
+
+    def prefetch(k):
+        b = (t0 + k - 1) % nb
+        with torch.cuda.stream(copy_stream):
+            if k >= 2:
+                copy_stream.wait_event(consumed[k % 2])
+            dev_tg[k % 2].copy_(host_targets[b], non_blocking=True)
+            dev_cams[k % 2].copy_(host_cams[b], non_blocking=True)
+            copied[k % 2].record(copy_stream)
+
     torch.cuda.synchronize()
     w0 = time.perf_counter()
+    start.record(stream)
+    copy_stream.wait_event(start)
+    prefetch(0)
+    if K > 1:
+        prefetch(1)
     with torch.cuda.stream(stream):
-        start.record(stream)
         for k in range(K):
             t = t0 + k
-            b = (t - 1) % nb
-            eng.cams.copy_(host_cams[b], non_blocking=True)
-            eng.target.copy_(host_targets[b], non_blocking=True)
+            stream.wait_event(copied[k % 2])
+            eng.target = dev_tg[k % 2]
+            eng.cams = dev_cams[k % 2]
             eng.step(t, eps_schedule(t, 30000), stream)
             loss_host[k:k + 1].copy_(eng.loss_val, non_blocking=True)
+            consumed[k % 2].record(stream)
+            if k + 2 < K:
+                prefetch(k + 2)
         stop.record(stream)
     stop.synchronize()
     wall = time.perf_counter() - w0
@@ -364,12 +390,17 @@ def run_cuda(args):
         torch.distributed.barrier()
     from paper_2602_00395_gb300 import gs3dtr as G
     G.load()
-    eng, cam_dev, targets, batches, need = make_workload(args.n, device, rank)
-    stream = torch.cuda.Stream(device=device)
     if args.profile_steps:
+        eng, cam_dev, targets, batches, need = make_workload(args.n, device, rank, args.profile_views, 2)
+        stream = torch.cuda.Stream(device=device)
         timed_steps(eng, cam_dev, targets, args.profile_steps, 0, 1, stream)
         torch.cuda.synchronize()
+        print(json.dumps({"profile_steps": args.profile_steps, "views": args.profile_views, "pairs": need,
+                          "sum_n_contrib": float(eng.n_contrib.double().sum().item()),
+                          "status_word": eng.read_status()}))
         return
+    eng, cam_dev, targets, batches, need = make_workload(args.n, device, rank)
+    stream = torch.cuda.Stream(device=device)
     # warm-up
     timed_steps(eng, cam_dev, targets, max(args.warmup, 3), 0, 1, stream)
     torch.cuda.synchronize()
@@ -403,6 +434,36 @@ def run_cuda(args):
     sum_nc = float(eng.n_contrib.double().sum().item())
     hbm, sm_mhz, src = peaks()
     fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    # every call against its own bound (HBM for the streaming calls, the FP32
+    # pipe for the blends); algorithmic work per unit as documented
+    R = N_VIEWS * eng.n_pad
+    rows = 11 + 3 * (SH_DEG + 1) ** 2
+
+    def bits(v):
+        b = 0
+        while (1 << b) < v:
+            b += 1
+        return b
+    rec_pass = (32 + bits(N_VIEWS) + 7) // 8
+    pair_pass = max(1, (bits(N_VIEWS * eng.Tx * eng.Ty) + 7) // 8)
+    work = {
+        "project": ("hbm", eng.n * rows * 4 + N_VIEWS * eng.n * 48 * (1 + NU)),
+        "bin_sort": ("hbm", need * (12 + 24 * pair_pass + 8) + R * (32 + 24 * rec_pass + 8)),
+        "raster_fwd": ("alu", raster_fwd_flops_per_unit() * sum_nc),
+        "raster_bwd": ("alu", raster_bwd_flops_per_unit() * sum_nc),
+        "update": ("hbm", eng.n * rows * 4 * (5 + 3)),
+    }
+    roof_calls = {}
+    for name, (kind, amount) in work.items():
+        ms_c = per_call[name]
+        if kind == "hbm":
+            ach = amount / (ms_c * 1e-3) / 1e9
+            roof_calls[name] = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                                "bytes": amount, "ms": ms_c}
+        else:
+            ach = amount / (ms_c * 1e-3) / 1e12
+            roof_calls[name] = {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
+                                "frac": ach / fp32_peak, "flop": amount, "ms": ms_c}
     fwd_ms, bwd_ms = per_call["raster_fwd"], per_call["raster_bwd"]
     if fwd_ms >= bwd_ms:
         name, ms_k, per_unit = "gs_raster_fwd (blend + fused JVP, nu=2)", fwd_ms, raster_fwd_flops_per_unit()
@@ -441,7 +502,7 @@ def run_cuda(args):
                            "batched_speedup": (1e3 / ms_per_step) / (1e3 / plain_ms),
                            "what": "8 single-view project/sort/fwd/bwd call sequences + averaged update, no batching"},
             "gpu_launches": kernel_launches_per_step(eng) * args.steps,
-            "roofline": roof, "clocks": clocks, "cpu_baseline": cpu,
+            "roofline": roof, "roofline_calls": roof_calls, "clocks": clocks, "cpu_baseline": cpu,
         }
         print(json.dumps(out))
     if ws > 1:
