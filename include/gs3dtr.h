@@ -104,8 +104,13 @@ typedef struct gs_probe {
 
 /* Projected splats of V views (device, caller-owned).
  *   rec:     V x n_pad records of 12 floats (48 B):
- *            (mx, my, A, B), (C, opacity, r, g), (b, depth, radius, tiles)
- *            where (A, B, C) is the conic and radius / tiles are int32 bit patterns
+ *            (mx, my, A, B), (C, opacity, r, g), (b, depth, radius, extents)
+ *            where (A, B, C) is the conic, radius is an int32 bit pattern
+ *            (0: culled) and extents packs two IEEE half floats (x low, y high):
+ *            half-widths of the bounding box of the alpha >= 1/255 footprint
+ *            d^T (A B; B C) d <= 2 ln(255 opacity), widened by 0.1% + 0.01 px and
+ *            rounded up (-inf: no pixel reaches 1/255; +inf: unbounded).  The
+ *            rasteriser skips a splat for an 8 x 8 pixel block outside that box.
  *   tangent: NULL or V x nu x n_pad records of 12 floats, the forward-mode
  *            derivative of (mx, my, A, B, C, opacity, r, g, b) along probe k */
 typedef struct gs_projected {

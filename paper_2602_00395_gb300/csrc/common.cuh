@@ -1,6 +1,7 @@
 // Shared device helpers of the gs3dtr CUDA library (sm_103a).
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -256,6 +257,33 @@ __device__ __forceinline__ void sh_basis_grad(float x, float y, float z, const f
       g[1] += 6.f * kY3a * x * y * w[15];
     }
   }
+}
+
+// ------------------------------------------------------ footprint extents
+// Half-extents of the bounding box of a splat's alpha >= 1/255 footprint, kept
+// in the last word of its record for the rasteriser's per-block visibility test.
+// The footprint is the ellipse d^T Q d <= tau, tau = 2 ln(255 o), Q = [[A, B],
+// [B, C]] the conic; its box has half-widths sqrt(tau C / det) and
+// sqrt(tau A / det).  They are widened by 0.1% + 0.01 px, so that no pair an
+// FP32 pixel test keeps falls outside, rounded up to half precision and packed
+// (x in the low 16 bits, y in the high).  tau <= 0 (no pixel can reach 1/255)
+// gives -inf, a non-finite half-width +inf.
+__device__ __forceinline__ uint32_t footprint_extents(float A, float B, float C, float o) {
+  const float tau = 2.f * __logf(255.f * o);
+  unsigned short hx, hy;
+  if (!(tau > 0.f)) {
+    hx = hy = 0xFC00u;  // -inf
+  } else {
+    const float det = A * C - B * B;
+    const float ex = sqrtf(tau * C / det), ey = sqrtf(tau * A / det);
+    if (!(ex < 1e30f) || !(ey < 1e30f)) {
+      hx = hy = 0x7C00u;  // +inf
+    } else {
+      hx = __half_as_ushort(__float2half_ru(ex * 1.001f + 0.01f));
+      hy = __half_as_ushort(__float2half_ru(ey * 1.001f + 0.01f));
+    }
+  }
+  return (uint32_t)hx | ((uint32_t)hy << 16);
 }
 
 // ---------------------------------------------------------- tile rectangle

@@ -173,7 +173,8 @@ __global__ void __launch_bounds__(128) project_kernel(const float* __restrict__ 
 
     rec[3 * at + 0] = make_float4(val(mx), val(my), val(cA), val(cB));
     rec[3 * at + 1] = make_float4(val(cC), val(opac), val(rgb[0]), val(rgb[1]));
-    rec[3 * at + 2] = make_float4(val(rgb[2]), val(t2), __int_as_float(radius), 0.f);
+    rec[3 * at + 2] = make_float4(val(rgb[2]), val(t2), __int_as_float(radius),
+                                  __uint_as_float(footprint_extents(val(cA), val(cB), val(cC), val(opac))));
     if constexpr (NU > 0) {
 #pragma unroll
       for (int k = 0; k < NU; ++k) {

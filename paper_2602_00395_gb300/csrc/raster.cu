@@ -81,21 +81,15 @@ __device__ __forceinline__ void pixel_of(int tid, int tile_w, int& lx, int& ly) 
 }
 
 // Bit w is set if the splat can reach alpha >= 1/255 at some pixel centre of
-// warp block w.  That region is the ellipse d^T Q d <= tau, tau = 2 ln(255 o),
-// Q the conic; its bounding box has half-widths sqrt(tau Q^-1_xx),
-// sqrt(tau Q^-1_yy), widened by 0.1% + 0.01 px so that no pair an FP32 pixel
-// test would keep is dropped.  A cleared bit therefore skips only pairs that
-// every pixel of the block skips anyway: results are unchanged.
+// warp block w.  The record's last word holds the half-extents of the bounding
+// box of that footprint, widened and rounded up by the projection
+// (footprint_extents), so a cleared bit skips only pairs that every pixel of
+// the block skips anyway: results are unchanged.
 __device__ __forceinline__ uint32_t warp_block_mask(const Rec& r, float tile_x0, float tile_y0, int tile_w,
                                                     int nwarps) {
-  const float tau = 2.f * __logf(255.f * r.b.y);
-  if (!(tau > 0.f)) return 0u;
-  const float A = r.a.z, B = r.a.w, C = r.b.x;
-  const float det = A * C - B * B;
-  float hx = sqrtf(tau * C / det), hy = sqrtf(tau * A / det);
-  if (!(hx < 1e30f) || !(hy < 1e30f)) return 0xffffffffu;
-  hx = hx * 1.001f + 0.01f;
-  hy = hy * 1.001f + 0.01f;
+  const uint32_t e = __float_as_uint(r.c.w);
+  const float hx = __half2float(__ushort_as_half((unsigned short)(e & 0xffffu)));
+  const float hy = __half2float(__ushort_as_half((unsigned short)(e >> 16)));
   const int bxn = tile_w >> 3;
   uint32_t m = 0;
   for (int w = 0; w < nwarps; ++w) {
@@ -269,39 +263,6 @@ __global__ void __launch_bounds__(128) raster_fwd_kernel(const float4* __restric
 }
 
 // ------------------------------------------------------------------ reverse
-// Lane L ends with the warp-wide sum of v[L] (v has 32 slots).
-__device__ __forceinline__ float warp_reduce_scatter32(float (&v)[32]) {
-  const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int o = 16; o >= 1; o >>= 1) {
-    const bool up = (lane & o) != 0;
-#pragma unroll
-    for (int i = 0; i < o; ++i) {
-      const float send = up ? v[i] : v[i + o];
-      const float keep = up ? v[i + o] : v[i];
-      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
-    }
-  }
-  return v[0];
-}
-// Lane L (and L ^ 16) ends with the warp-wide sum of v[L & 15] (v has 16 slots).
-__device__ __forceinline__ float warp_reduce_scatter16(float (&v)[32]) {
-  const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], 16);
-#pragma unroll
-  for (int o = 8; o >= 1; o >>= 1) {
-    const bool up = (lane & o) != 0;
-#pragma unroll
-    for (int i = 0; i < o; ++i) {
-      const float send = up ? v[i] : v[i + o];
-      const float keep = up ? v[i + o] : v[i];
-      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
-    }
-  }
-  return v[0];
-}
-
 // Minimum resident CTAs per SM requested from the compiler for the reverse
 // kernel (0: no request).
 #ifndef GS_BWD_MIN_BLOCKS
@@ -376,18 +337,21 @@ struct BwdPixel {
   uint32_t nc;
 };
 
-// The reverse of one blended splat at one pixel: recover T_i = T_{i+1}/(1 - a),
-// dC/da = c T_i - suffix/(1 - a), and add the pixel's derivatives of the splat's
-// (mx, my, A, B, C, o, r, g, b) for every stream to v.
-template <int S>
+// The reverse of one splat at one pixel: recover T_i = T_{i+1}/(1 - a),
+// dC/da = c T_i - suffix/(1 - a), and store (FIRST) or add the pixel's
+// derivatives of the splat's (mx, my, A, B, C, o, r, g, b) for every stream in
+// v.  A pixel the splat is not blended at passes alpha = G = oG = 0: its state
+// stays as it is and it contributes exact zeros, so the pixels of a thread need
+// no branches.  One reciprocal of 1 - a serves the four quotients.
+template <int S, bool FIRST>
 __device__ __forceinline__ void bwd_accumulate(BwdPixel<S>& p, const Rec& r, float dx, float dy, float G, float oG,
                                                float alpha, float (&v)[32]) {
-  const float om = 1.f - alpha;
-  const float Ti = p.T / om;
+  const float inv = __frcp_rn(1.f - alpha);
+  const float Ti = p.T * inv;
   const float rgb0 = r.b.z, rgb1 = r.b.w, rgb2 = r.c.x;
-  const float da0 = rgb0 * Ti - p.suf[0] / om;
-  const float da1 = rgb1 * Ti - p.suf[1] / om;
-  const float da2 = rgb2 * Ti - p.suf[2] / om;
+  const float da0 = rgb0 * Ti - p.suf[0] * inv;
+  const float da1 = rgb1 * Ti - p.suf[1] * inv;
+  const float da2 = rgb2 * Ti - p.suf[2] * inv;
   const float aT = alpha * Ti;
   p.suf[0] += rgb0 * aT;
   p.suf[1] += rgb1 * aT;
@@ -400,15 +364,13 @@ __device__ __forceinline__ void bwd_accumulate(BwdPixel<S>& p, const Rec& r, flo
   for (int s = 0; s < S; ++s) {
     const float ga = p.w[s][0] * da0 + p.w[s][1] * da1 + p.w[s][2] * da2;
     const float gp = capped ? 0.f : ga * alpha;
-    v[9 * s + 0] += fmx * gp;
-    v[9 * s + 1] += fmy * gp;
-    v[9 * s + 2] += fA * gp;
-    v[9 * s + 3] += fB * gp;
-    v[9 * s + 4] += fC * gp;
-    v[9 * s + 5] += capped ? 0.f : ga * G;
-    v[9 * s + 6] += p.w[s][0] * aT;
-    v[9 * s + 7] += p.w[s][1] * aT;
-    v[9 * s + 8] += p.w[s][2] * aT;
+    const float c[9] = {fmx * gp, fmy * gp, fA * gp, fB * gp, fC * gp, capped ? 0.f : ga * G,
+                        p.w[s][0] * aT, p.w[s][1] * aT, p.w[s][2] * aT};
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+      if constexpr (FIRST) v[9 * s + q] = c[q];
+      else v[9 * s + q] += c[q];
+    }
   }
 }
 
@@ -537,26 +499,19 @@ __global__ void GS_BWD_BOUNDS raster_bwd_kernel(
         for (int q = 0; q < kPixPerThread; ++q) {
           dx[q] = __fsub_rn(r.a.x, pix[q].pxc);
           dy[q] = __fsub_rn(r.a.y, pix[q].pyc);
-          on[q] = pos < pix[q].nc;
-          G[q] = oG[q] = alpha[q] = 0.f;
-          if (on[q]) {
-            const float power = splat_power(r, dx[q], dy[q]);
-            on[q] = power <= 0.f;
-            if (on[q]) {
-              G[q] = __expf(power);
-              oG[q] = __fmul_rn(r.b.y, G[q]);
-              alpha[q] = fminf(kAlphaMax, oG[q]);
-              on[q] = alpha[q] >= kAlphaMin;
-            }
-          }
+          const float power = splat_power(r, dx[q], dy[q]);
+          G[q] = __expf(power);
+          oG[q] = __fmul_rn(r.b.y, G[q]);
+          alpha[q] = fminf(kAlphaMax, oG[q]);
+          on[q] = pos < pix[q].nc && power <= 0.f && alpha[q] >= kAlphaMin;
+          if (!on[q]) G[q] = oG[q] = alpha[q] = 0.f;
         }
         if (!__any_sync(0xffffffffu, on[0] || on[1])) continue;
         float v[32];
+        bwd_accumulate<S, true>(pix[0], r, dx[0], dy[0], G[0], oG[0], alpha[0], v);
+        bwd_accumulate<S, false>(pix[1], r, dx[1], dy[1], G[1], oG[1], alpha[1], v);
 #pragma unroll
-        for (int q = 0; q < 32; ++q) v[q] = 0.f;
-#pragma unroll
-        for (int q = 0; q < kPixPerThread; ++q)
-          if (on[q]) bwd_accumulate<S>(pix[q], r, dx[q], dy[q], G[q], oG[q], alpha[q], v);
+        for (int q = 9 * S; q < 32; ++q) v[q] = 0.f;
         const uint32_t gi = s_idx[bi * batch + j];
         float* dst = cot + ((size_t)view * n_pad + gi) * NVP;
         float qs[4];

@@ -95,6 +95,18 @@ def test_project_matches_oracle(case):
                 assert np.abs(gt[:, q] - rt[:, q]).max() <= 1e-4 * scale + 1e-7, (k, q)
         # padding columns are culled
         assert np.all(rec[v, sc.n:, 10].view(np.int32) == 0)
+        # the packed half-extents bound the alpha >= 1/255 footprint of the
+        # record's own conic and opacity (computed here in FP64)
+        A, B, C, o = (rec[v, : sc.n, c][valid].astype(np.float64) for c in (2, 3, 4, 5))
+        ext = rec[v, : sc.n, 11][valid].view(np.uint32)
+        hx = (ext & 0xFFFF).astype(np.uint16).view(np.float16).astype(np.float64)
+        hy = (ext >> 16).astype(np.uint16).view(np.float16).astype(np.float64)
+        tau = 2.0 * np.log(255.0 * o)
+        det = A * C - B * B
+        reach = tau > 1e-6
+        assert np.all(np.isneginf(hx[tau < -1e-6])) and np.all(np.isneginf(hy[tau < -1e-6]))
+        assert np.all(hx[reach] >= np.sqrt(tau[reach] * C[reach] / det[reach]))
+        assert np.all(hy[reach] >= np.sqrt(tau[reach] * A[reach] / det[reach]))
 
 
 # ------------------------------------------------------------------ bin/sort
