@@ -39,10 +39,10 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
 }
 
 // ------------------------------------------------------------------ records
-// counts[g] = tiles of record g's rectangle; rkeys[g] = view << 32 | bits(depth);
-// rvals[g] = g.
+// counts[g] = tiles of record g's rectangle; rkeys[g] = bits(depth) (sorted
+// within each view's segment); rvals[g] = g.
 __global__ void record_keys_kernel(const float4* __restrict__ rec, int n_pad, gs_frame fr, int Tx, int Ty,
-                                   uint32_t* __restrict__ counts, uint64_t* __restrict__ rkeys,
+                                   uint32_t* __restrict__ counts, uint32_t* __restrict__ rkeys,
                                    uint32_t* __restrict__ rvals) {
   const size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= (size_t)fr.n_views * n_pad) return;
@@ -56,12 +56,9 @@ __global__ void record_keys_kernel(const float4* __restrict__ rec, int n_pad, gs
     cnt = (uint32_t)max(0, x1 - x0) * (uint32_t)max(0, y1 - y0);
   }
   counts[g] = cnt;
-  const uint64_t view = g / (size_t)n_pad;
-  rkeys[g] = (view << 32) | (uint64_t)__float_as_uint(c.y);
+  rkeys[g] = __float_as_uint(c.y);
   rvals[g] = (uint32_t)g;
 }
-
-__global__ void set_u32_kernel(uint32_t* p, uint32_t v) { *p = v; }
 
 // scnt[p] = counts of the record at sorted position p
 __global__ void gather_counts_kernel(const uint32_t* __restrict__ order, const uint32_t* __restrict__ counts,
@@ -264,137 +261,155 @@ __global__ void emit_kernel(const float4* __restrict__ rec, int n_pad, gs_frame 
 }
 
 // ------------------------------------------------------------ radix passes
-__device__ __forceinline__ uint32_t pairs_in_use(const uint32_t* n_pairs, uint64_t capacity) {
-  const uint64_t p = *n_pairs;
-  return (uint32_t)(p < capacity ? p : capacity);
+// A pass sorts nseg segments independently and stably on one 8-bit digit.
+// Segment g holds items [g * stride, g * stride + len): the record sort has one
+// segment per view (len = stride = n_pad), the pair sort one segment whose
+// length is the pair count P in device memory.  Each segment is cut into
+// tiles of kRadixTile items, tile t of segment g handled by block g * bpg + t
+// (blocks past the segment's tiles return).  The digit histograms are stored
+// segment-major, then digit, then tile: hist[(g * 256 + d) * bps + t], so that
+// one exclusive scan of all of them gives every (segment, digit, tile) its
+// first output position.
+struct Seg {
+  const uint32_t* len_dev;  // device length of the single segment, or null
+  uint64_t cap;             // clamp of *len_dev
+  uint32_t len;             // host length of every segment (len_dev == null)
+  uint32_t stride;          // items between segment starts
+};
+
+__device__ __forceinline__ uint32_t seg_len(const Seg& sg) {
+  if (!sg.len_dev) return sg.len;
+  const uint64_t p = *sg.len_dev;
+  return (uint32_t)(p < sg.cap ? p : sg.cap);
 }
 
-// Digit histograms are stored digit-major over the blocks in use,
-// hist[d * nbu + b] with nbu = ceil(P / tile), so that their exclusive scan
-// gives each (digit, block) its first output position.
-__global__ void __launch_bounds__(kRadixThreads) radix_hist_kernel(const uint64_t* __restrict__ keys,
-                                                                   const uint32_t* __restrict__ n_pairs,
-                                                                   uint64_t capacity, int shift,
-                                                                   uint32_t* __restrict__ hist) {
+template <typename K>
+__device__ __forceinline__ uint32_t digit_of(K key, int shift) {
+  return (uint32_t)(key >> shift) & 255u;
+}
+
+template <typename K>
+__global__ void __launch_bounds__(kRadixThreads) radix_hist_kernel(const K* __restrict__ keys, Seg sg, int bpg,
+                                                                   int shift, uint32_t* __restrict__ hist) {
   __shared__ uint32_t s_cnt[256];
-  const uint32_t P = pairs_in_use(n_pairs, capacity);
-  const size_t base = (size_t)blockIdx.x * kRadixTile;
-  if (base >= P) return;
-  const size_t nbu = ((size_t)P + kRadixTile - 1) / kRadixTile;
+  const uint32_t len = seg_len(sg);
+  const int g = blockIdx.x / bpg, t = blockIdx.x - g * bpg;
+  const uint32_t bps = (len + kRadixTile - 1) / kRadixTile;
+  if ((uint32_t)t >= bps) return;
   s_cnt[threadIdx.x] = 0;
   __syncthreads();
-  {
-    uint64_t kk[kRadixItems];
+  const K* kin = keys + (size_t)g * sg.stride;
+  const uint32_t base = (uint32_t)t * kRadixTile;
+  K kk[kRadixItems];
 #pragma unroll
-    for (int k = 0; k < kRadixItems; ++k) {
-      const size_t idx = base + (size_t)k * kRadixThreads + threadIdx.x;
-      kk[k] = idx < P ? keys[idx] : 0ull;
-    }
+  for (int k = 0; k < kRadixItems; ++k) {
+    const uint32_t idx = base + (uint32_t)k * kRadixThreads + threadIdx.x;
+    kk[k] = idx < len ? kin[idx] : (K)0;
+  }
 #pragma unroll
-    for (int k = 0; k < kRadixItems; ++k) {
-      const size_t idx = base + (size_t)k * kRadixThreads + threadIdx.x;
-      const bool ok = idx < P;
-      const uint32_t d = ok ? (uint32_t)(kk[k] >> shift) & 255u : 256u;
-      const uint32_t peers = __match_any_sync(0xffffffffu, d);
-      if (ok && (peers & lanemask_lt()) == 0) atomicAdd(&s_cnt[d], (uint32_t)__popc(peers));
-    }
+  for (int k = 0; k < kRadixItems; ++k) {
+    const uint32_t idx = base + (uint32_t)k * kRadixThreads + threadIdx.x;
+    const bool ok = idx < len;
+    const uint32_t d = ok ? digit_of(kk[k], shift) : 256u;
+    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    if (ok && (peers & lanemask_lt()) == 0) atomicAdd(&s_cnt[d], (uint32_t)__popc(peers));
   }
   __syncthreads();
-  hist[(size_t)threadIdx.x * nbu + blockIdx.x] = s_cnt[threadIdx.x];
+  hist[((size_t)g * 256 + threadIdx.x) * bps + t] = s_cnt[threadIdx.x];
 }
 
-__global__ void __launch_bounds__(kRadixThreads) radix_scatter_kernel(
-    const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint64_t* __restrict__ kout,
-    uint32_t* __restrict__ vout, const uint32_t* __restrict__ n_pairs, uint64_t capacity, int shift,
-    const uint32_t* __restrict__ hist_scanned) {
-  __shared__ uint64_t s_keys[kRadixTile];
+// Stable scatter of one tile.  Warp w owns the tile's items
+// [w * 32 * kRadixItems, (w + 1) * 32 * kRadixItems), item k of lane L at
+// offset k * 32 + L, so the warps' strips and the items within a strip are in
+// input order.  Each warp ranks its strip against private digit counters (one
+// match per item, no block barrier); the per-digit prefix over the warps and
+// the tile's digit starts follow from one block scan; the keys are reordered by
+// (digit, rank) in shared memory and each digit's run written contiguously.
+template <typename K>
+__global__ void __launch_bounds__(kRadixThreads, 4) radix_scatter_kernel(const K* __restrict__ kin_all,
+                                                                      const uint32_t* __restrict__ vin_all,
+                                                                      K* __restrict__ kout, uint32_t* __restrict__ vout,
+                                                                      Seg sg, int bpg, int shift,
+                                                                      const uint32_t* __restrict__ hist_scanned) {
+  __shared__ K s_keys[kRadixTile];
   __shared__ uint32_t s_vals[kRadixTile];
-  __shared__ uint32_t s_wcnt[kRadixWarps][256];
-  __shared__ uint32_t s_run[256];    // keys of each digit seen so far, then the digit count
-  __shared__ uint32_t s_start[256];  // local start of each digit's run
+  __shared__ uint32_t s_wc[kRadixWarps][256];  // per-warp digit counts, then their prefix over warps
+  __shared__ uint32_t s_start[256];           // first tile position of each digit
+  __shared__ uint32_t s_gofs[256];            // output position minus tile position, per digit
   __shared__ uint32_t s_warp[32];
-  const uint32_t P = pairs_in_use(n_pairs, capacity);
-  const size_t base = (size_t)blockIdx.x * kRadixTile;
-  if (base >= P) return;
-  const size_t nb = ((size_t)P + kRadixTile - 1) / kRadixTile;
+  const uint32_t len = seg_len(sg);
+  const int g = blockIdx.x / bpg, t = blockIdx.x - g * bpg;
+  const uint32_t bps = (len + kRadixTile - 1) / kRadixTile;
+  if ((uint32_t)t >= bps) return;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t lt = lanemask_lt();
-  s_run[tid] = 0;
-#pragma unroll
-  for (int w = 0; w < kRadixWarps; ++w) s_wcnt[w][tid] = 0;
-  __syncthreads();
-
-  uint64_t key[kRadixItems];
-  uint32_t vv[kRadixItems];
-  uint32_t rank[kRadixItems];
-  // all loads first, so that they are in flight together
+  const K* kin = kin_all + (size_t)g * sg.stride;
+  const uint32_t* vin = vin_all + (size_t)g * sg.stride;
+  const uint32_t base = (uint32_t)t * kRadixTile + (uint32_t)warp * 32 * kRadixItems + lane;
+  K key[kRadixItems];
+  uint32_t vv[kRadixItems], rank[kRadixItems], dg[kRadixItems];
 #pragma unroll
   for (int k = 0; k < kRadixItems; ++k) {
-    const size_t idx = base + (size_t)k * kRadixThreads + tid;
-    key[k] = idx < P ? kin[idx] : 0ull;
-    vv[k] = idx < P ? vin[idx] : 0u;
+    const uint32_t idx = base + (uint32_t)k * 32;
+    key[k] = idx < len ? kin[idx] : (K)0;
+    vv[k] = idx < len ? vin[idx] : 0u;
   }
 #pragma unroll
+  for (int q = lane; q < 256; q += 32) s_wc[warp][q] = 0;
+  __syncwarp();
+#pragma unroll
   for (int k = 0; k < kRadixItems; ++k) {
-    const size_t idx = base + (size_t)k * kRadixThreads + tid;
-    const bool ok = idx < P;
-    const uint32_t d = ok ? (uint32_t)(key[k] >> shift) & 255u : 256u;
+    const bool ok = base + (uint32_t)k * 32 < len;
+    const uint32_t d = ok ? digit_of(key[k], shift) : 256u;
+    dg[k] = d;
     const uint32_t peers = __match_any_sync(0xffffffffu, d);
-    const uint32_t below = (uint32_t)__popc(peers & lt);
-    if (ok && below == 0) s_wcnt[warp][d] = (uint32_t)__popc(peers);
-    __syncthreads();
-    if (ok) {
-      uint32_t pre = s_run[d];
-      for (int w = 0; w < warp; ++w) pre += s_wcnt[w][d];
-      rank[k] = pre + below;
-    } else {
-      rank[k] = 0;
-    }
-    __syncthreads();
-    uint32_t add = 0;
-#pragma unroll
-    for (int w = 0; w < kRadixWarps; ++w) {
-      add += s_wcnt[w][tid];
-      s_wcnt[w][tid] = 0;
-    }
-    s_run[tid] += add;
-    __syncthreads();
+    const uint32_t before = ok ? s_wc[warp][d] : 0u;
+    rank[k] = before + (uint32_t)__popc(peers & lt);
+    __syncwarp();
+    if (ok && (peers & lt) == 0) s_wc[warp][d] = before + (uint32_t)__popc(peers);
+    __syncwarp();
   }
-  // local digit starts
-  const uint32_t cnt = s_run[tid];
-  uint32_t tot;
-  const uint32_t start = block_exclusive_scan(cnt, tot, s_warp);
-  s_start[tid] = start;
   __syncthreads();
-  // reorder in shared memory by (digit, rank)
+  // digit tid: prefix of the warps' counts, the tile's count, its start
+  uint32_t run = 0;
+#pragma unroll
+  for (int w = 0; w < kRadixWarps; ++w) {
+    const uint32_t c = s_wc[w][tid];
+    s_wc[w][tid] = run;
+    run += c;
+  }
+  uint32_t tot;
+  const uint32_t start = block_exclusive_scan(run, tot, s_warp);
+  s_start[tid] = start;
+  s_gofs[tid] = hist_scanned[((size_t)g * 256 + tid) * bps + t] - start;
+  __syncthreads();
 #pragma unroll
   for (int k = 0; k < kRadixItems; ++k) {
-    const size_t idx = base + (size_t)k * kRadixThreads + tid;
-    if (idx < P) {
-      const uint32_t d = (uint32_t)(key[k] >> shift) & 255u;
-      const uint32_t pos = s_start[d] + rank[k];
+    if (dg[k] < 256u) {
+      const uint32_t pos = s_start[dg[k]] + s_wc[warp][dg[k]] + rank[k];
       s_keys[pos] = key[k];
       s_vals[pos] = vv[k];
     }
   }
   __syncthreads();
-  // coalesced write of each digit's run
-  const uint32_t valid = tot;
-#pragma unroll 4
+#pragma unroll
   for (int k = 0; k < kRadixItems; ++k) {
     const uint32_t p = (uint32_t)k * kRadixThreads + tid;
-    if (p < valid) {
-      const uint64_t kk = s_keys[p];
-      const uint32_t d = (uint32_t)(kk >> shift) & 255u;
-      const size_t g = (size_t)hist_scanned[(size_t)d * nb + blockIdx.x] + (p - s_start[d]);
-      kout[g] = kk;
-      vout[g] = s_vals[p];
+    if (p < tot) {
+      const K kk = s_keys[p];
+      const size_t at = (size_t)s_gofs[digit_of(kk, shift)] + p;
+      kout[at] = kk;
+      vout[at] = s_vals[p];
     }
   }
-  (void)lane;
 }
 
 // ------------------------------------------------------------------ ranges
+__device__ __forceinline__ uint32_t pairs_in_use(const uint32_t* n_pairs, uint64_t capacity) {
+  const uint64_t p = *n_pairs;
+  return (uint32_t)(p < capacity ? p : capacity);
+}
+
 __global__ void ranges_kernel(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ n_pairs,
                               uint64_t capacity, uint32_t* __restrict__ ranges) {
   const uint32_t P = pairs_in_use(n_pairs, capacity);
@@ -409,10 +424,9 @@ __global__ void ranges_kernel(const uint64_t* __restrict__ keys, const uint32_t*
 inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 struct SortPlan {
-  int Tx, Ty, rec_pass, pair_pass, nb_pairs, nb_items;
+  int Tx, Ty, rec_pass, pair_pass, nb_pairs, rec_bps;
   size_t n_items;  // views x n_pad
-  size_t off_counts, off_scnt, off_sums, off_rk0, off_rk1, off_rv0, off_rv1, off_items, off_keys, off_vals,
-      off_hist, total;
+  size_t off_counts, off_scnt, off_sums, off_rk0, off_rk1, off_rv0, off_rv1, off_keys, off_vals, off_hist, total;
 };
 
 inline int bits_for(uint64_t v) {  // smallest b with 2^b >= v
@@ -427,21 +441,20 @@ SortPlan plan_sort(int32_t n_pad, gs_frame fr, uint64_t capacity) {
   p.Ty = (fr.height + fr.tile_h - 1) / fr.tile_h;
   const uint64_t tiles = (uint64_t)fr.n_views * p.Tx * p.Ty;
   p.pair_pass = std::max(1, (bits_for(tiles) + 7) / 8);
-  p.rec_pass = (32 + bits_for((uint64_t)fr.n_views) + 7) / 8;
+  p.rec_pass = 4;  // 32 depth bits within each view
   p.n_items = (size_t)fr.n_views * n_pad;
   p.nb_pairs = (int)((capacity + kRadixTile - 1) / kRadixTile);
-  p.nb_items = (int)((p.n_items + kRadixTile - 1) / kRadixTile);
-  const size_t hist_n = (size_t)256 * std::max(p.nb_pairs, p.nb_items);
+  p.rec_bps = (int)(((size_t)n_pad + kRadixTile - 1) / kRadixTile);
+  const size_t hist_n = (size_t)256 * std::max((size_t)p.nb_pairs, (size_t)fr.n_views * p.rec_bps);
   const size_t sums_n = (size_t)std::max(scan_blocks(p.n_items), scan_blocks(hist_n)) + 1;
   size_t o = 0;
   p.off_counts = o; o += align256(p.n_items * 4);
   p.off_scnt = o;   o += align256(p.n_items * 4);
   p.off_sums = o;   o += align256(sums_n * 4);
-  p.off_rk0 = o;    o += align256(p.n_items * 8);
-  p.off_rk1 = o;    o += align256(p.n_items * 8);
+  p.off_rk0 = o;    o += align256(p.n_items * 4);
+  p.off_rk1 = o;    o += align256(p.n_items * 4);
   p.off_rv0 = o;    o += align256(p.n_items * 4);
   p.off_rv1 = o;    o += align256(p.n_items * 4);
-  p.off_items = o;  o += 256;
   p.off_keys = o;   o += align256(capacity * 8);
   p.off_vals = o;   o += align256(capacity * 4);
   p.off_hist = o;   o += align256(hist_n * 4);
@@ -449,17 +462,22 @@ SortPlan plan_sort(int32_t n_pad, gs_frame fr, uint64_t capacity) {
   return p;
 }
 
-// Stable LSD passes over 8-bit digits starting at `shift0`; the keys/values
-// ping-pong between buffer 0 and 1 starting in `cur`, which is updated.
-void radix_passes(uint64_t** kbuf, uint32_t** vbuf, int& cur, int npass, int shift0, const uint32_t* count_dev,
-                  uint64_t count_cap, int nb, uint32_t* hist, uint32_t* sums, cudaStream_t st) {
-  const size_t hist_n = (size_t)256 * nb;
+// Stable LSD passes over 8-bit digits starting at `shift0` on nseg segments of
+// bpg tiles each (see Seg); the keys/values ping-pong between buffer 0 and 1
+// starting in `cur`, which is updated.  The histogram scan runs over
+// nseg x 256 x bpg entries, or over the pairs in use when the length is on the
+// device.
+template <typename K>
+void radix_passes(K** kbuf, uint32_t** vbuf, int& cur, int npass, int shift0, Seg sg, int nseg, int bpg,
+                  uint32_t* hist, uint32_t* sums, cudaStream_t st) {
+  const size_t hist_n = (size_t)nseg * 256 * bpg;
+  const unsigned grid = (unsigned)((size_t)nseg * bpg);
   for (int pass = 0; pass < npass; ++pass) {
     const int shift = shift0 + 8 * pass;
-    radix_hist_kernel<<<nb, kRadixThreads, 0, st>>>(kbuf[cur], count_dev, count_cap, shift, hist);
-    exclusive_scan(hist, hist, hist_n, count_dev, count_cap, sums, nullptr, 0, nullptr, st);
-    radix_scatter_kernel<<<nb, kRadixThreads, 0, st>>>(kbuf[cur], vbuf[cur], kbuf[cur ^ 1], vbuf[cur ^ 1],
-                                                       count_dev, count_cap, shift, hist);
+    radix_hist_kernel<K><<<grid, kRadixThreads, 0, st>>>(kbuf[cur], sg, bpg, shift, hist);
+    exclusive_scan(hist, hist, hist_n, sg.len_dev, sg.cap, sums, nullptr, 0, nullptr, st);
+    radix_scatter_kernel<K><<<grid, kRadixThreads, 0, st>>>(kbuf[cur], vbuf[cur], kbuf[cur ^ 1], vbuf[cur ^ 1], sg,
+                                                            bpg, shift, hist);
     cur ^= 1;
   }
 }
@@ -488,7 +506,6 @@ extern "C" gs_status gs_bin_sort(const gs_projected* proj, int32_t n_pad, gs_fra
   uint32_t* counts = (uint32_t*)(ws + p.off_counts);
   uint32_t* scnt = (uint32_t*)(ws + p.off_scnt);
   uint32_t* sums = (uint32_t*)(ws + p.off_sums);
-  uint32_t* items_dev = (uint32_t*)(ws + p.off_items);
   uint32_t* hist = (uint32_t*)(ws + p.off_hist);
   const float4* rec = reinterpret_cast<const float4*>(proj->rec);
   const uint64_t T = (uint64_t)p.Tx * p.Ty;
@@ -498,13 +515,13 @@ extern "C" gs_status gs_bin_sort(const gs_projected* proj, int32_t n_pad, gs_fra
     return check_launch("gs_bin_sort: memset");
   if (p.n_items == 0) return GS_OK;
   const int eb = (int)((p.n_items + 255) / 256);
-  // records sorted by (view, depth)
-  uint64_t* rk[2] = {(uint64_t*)(ws + p.off_rk0), (uint64_t*)(ws + p.off_rk1)};
+  // records sorted by depth within each view's segment
+  uint32_t* rk[2] = {(uint32_t*)(ws + p.off_rk0), (uint32_t*)(ws + p.off_rk1)};
   uint32_t* rv[2] = {(uint32_t*)(ws + p.off_rv0), (uint32_t*)(ws + p.off_rv1)};
   record_keys_kernel<<<eb, 256, 0, st>>>(rec, n_pad, frame, p.Tx, p.Ty, counts, rk[0], rv[0]);
-  set_u32_kernel<<<1, 1, 0, st>>>(items_dev, (uint32_t)p.n_items);
   int rcur = 0;
-  radix_passes(rk, rv, rcur, p.rec_pass, 0, items_dev, p.n_items, p.nb_items, hist, sums, st);
+  const Seg rseg{nullptr, 0, (uint32_t)n_pad, (uint32_t)n_pad};
+  radix_passes<uint32_t>(rk, rv, rcur, p.rec_pass, 0, rseg, frame.n_views, p.rec_bps, hist, sums, st);
   // emission offsets in that order, and the pair count
   gather_counts_kernel<<<eb, 256, 0, st>>>(rv[rcur], counts, scnt, p.n_items);
   exclusive_scan(scnt, scnt, p.n_items, nullptr, 0, sums, out->n_pairs, out->capacity, status, st);
@@ -514,7 +531,8 @@ extern "C" gs_status gs_bin_sort(const gs_projected* proj, int32_t n_pad, gs_fra
   uint32_t* vbuf[2] = {out->vals, (uint32_t*)(ws + p.off_vals)};
   int cur = (p.pair_pass % 2 == 0) ? 0 : 1;
   emit_kernel<<<eb, 256, 0, st>>>(rec, n_pad, frame, p.Tx, p.Ty, rv[rcur], scnt, out->capacity, kbuf[cur], vbuf[cur]);
-  radix_passes(kbuf, vbuf, cur, p.pair_pass, 32, out->n_pairs, out->capacity, p.nb_pairs, hist, sums, st);
+  const Seg pseg{out->n_pairs, out->capacity, 0, 0};
+  radix_passes<uint64_t>(kbuf, vbuf, cur, p.pair_pass, 32, pseg, 1, p.nb_pairs, hist, sums, st);
   const int rb = (int)std::min<uint64_t>((out->capacity + 255) / 256, 152 * 16);
   ranges_kernel<<<rb, 256, 0, st>>>(out->keys, out->n_pairs, out->capacity, out->ranges);
   return check_launch("gs_bin_sort");
