@@ -163,12 +163,13 @@ def project_tangent(P: np.ndarray, deg: int, cam, direction: np.ndarray) -> np.n
 
 
 def probe_matrix(seed: int, t: int, k: int, rows: int, n: int) -> np.ndarray:
-    """Rademacher probe k of step t as a rows x n matrix (entry j = r * n + i)."""
+    """Rademacher probe k of step t as a rows x n matrix (row r of Gaussian i is
+    entry j = i * rows + r)."""
     z = np.empty(rows * n)
     L = lib()
     for j in range(rows * n):
         z[j] = L.or_rademacher(seed, t, k, j)
-    return z.reshape(rows, n)
+    return z.reshape(n, rows).T.copy()
 
 
 def bin_sort(mx, my, radius, depth, width: int, height: int, tw: int = 16, th: int = 16):

@@ -483,11 +483,17 @@ uint64_t splitmix64(uint64_t x) {
   return z ^ (z >> 31);
 }
 
-// Entry j of Rademacher probe k at step t: +1 or -1 from bit 63 of the hash.
+// Entry j of Rademacher probe k at step t (the paper leaves the generator open):
+// bit j mod 64 of the hash of word j / 64, so one hash gives 64 entries; a set
+// bit is -1.
 double rademacher(uint64_t seed, int64_t t, int k, uint64_t j) {
-  uint64_t h = splitmix64(seed ^ ((uint64_t)t * kGolden) ^ ((uint64_t)k << 56) ^ j);
-  return (h >> 63) ? -1.0 : 1.0;
+  uint64_t h = splitmix64(seed ^ ((uint64_t)t * kGolden) ^ ((uint64_t)k << 56) ^ (j >> 6));
+  return ((h >> (j & 63)) & 1ULL) ? -1.0 : 1.0;
 }
+
+// Probe entry of parameter row r of Gaussian i: the rows of one Gaussian are
+// consecutive entries, so they share one or two hashes.
+uint64_t probe_entry(long i, int r, int rows) { return (uint64_t)i * (uint64_t)rows + (uint64_t)r; }
 
 // ----------------------------------------------------------- reverse pass
 // Cotangents of the 2-D splat quantities, 9 per splat: (mx, my, A, B, C, o, r, g, b).
@@ -915,11 +921,11 @@ double or_backward(const double* P, long pitch, long n, int deg, const double* c
   for (long k = 0; k < (long)rows * n; ++k) grad[k] = 0.0;
   if (hz) for (long k = 0; k < (long)rows * n; ++k) hz[k] = 0.0;
 
-  // probe directions z_k over the parameter vector (index r * n + i)
+  // probe directions z_k over the parameter vector (entry i * rows + r)
   std::vector<std::vector<double>> z(nu, std::vector<double>((size_t)rows * pitch, 0.0));
   for (int k = 0; k < nu; ++k)
     for (int r = 0; r < rows; ++r)
-      for (long i = 0; i < n; ++i) z[k][(size_t)r * pitch + i] = rademacher(seed, t, k, (uint64_t)r * n + i);
+      for (long i = 0; i < n; ++i) z[k][(size_t)r * pitch + i] = rademacher(seed, t, k, probe_entry(i, r, rows));
 
   long total = (long)(m + 0.5);  // sum over views of 3 H W
   double f = 0.0;
@@ -1062,7 +1068,7 @@ std::vector<Splat<Dual>> tile_tangents(const View& V, const std::vector<int>& li
   std::vector<double> tan(rows);
   for (size_t q = 0; q < list.size(); ++q) {
     long i = list[q];
-    for (int r = 0; r < rows; ++r) tan[r] = rademacher(seed, t, k, (uint64_t)r * n + i);
+    for (int r = 0; r < rows; ++r) tan[r] = rademacher(seed, t, k, probe_entry(i, r, rows));
     out[q] = project(load_gaussian<Dual>(P, pitch, i, deg, tan.data()), V.cam);
   }
   return out;
@@ -1205,7 +1211,7 @@ void or_backward_sampled(const double* P, long pitch, long n, int deg, const dou
         project_reverse(P, pitch, i, deg, V.cam, cot[st].data() + i * NQ, g_acc);
         for (int r = 0; r < rows; ++r) {
           if (st == 0) grad_out[sidx * rows + r] += g_acc[r];
-          else hz_out[sidx * rows + r] += rademacher(seed, t, st - 1, (uint64_t)r * n + i) * g_acc[r] / nu;
+          else hz_out[sidx * rows + r] += rademacher(seed, t, st - 1, probe_entry(i, r, rows)) * g_acc[r] / nu;
         }
       }
     }

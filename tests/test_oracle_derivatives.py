@@ -118,7 +118,7 @@ def test_gradient_and_gn_product_agree_with_exact_jacobian(loss_kind):
     np.testing.assert_allclose(out["grad"], g, atol=1e-12 * np.abs(g).max() + 1e-15)
     hz = np.zeros(rows * n)
     for k in range(nu):
-        z = np.array([O.rademacher(77, 5, k, j) for j in range(rows * n)])
+        z = O.probe_matrix(77, 5, k, rows, n).ravel()
         np.testing.assert_allclose(out["image_tangent"][k].ravel(), J @ z, atol=1e-10)
         hz += z * (J.T @ (lam * (J @ z))) / nu
     np.testing.assert_allclose(out["hz"], hz.reshape(rows, n), atol=1e-10 * np.abs(hz).max())
@@ -172,7 +172,7 @@ def test_hvp_stream_uses_regenerated_probes():
     tg = S.noise_target(1, 16, 16, seed=9).astype(np.float64)
     out = O.backward(P, deg, [cam], tg, seed=5, t=2, nu=1, want_tangents=True)
     rows, n = P.shape
-    z = np.array([O.rademacher(5, 2, 0, j) for j in range(rows * n)]).reshape(rows, n)
+    z = O.probe_matrix(5, 2, 0, rows, n)
     np.testing.assert_allclose(out["image_tangent"][0], O.jvp(P, deg, [cam], z), atol=1e-13)
 
 
