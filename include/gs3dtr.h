@@ -36,7 +36,7 @@
  *     rows 11..   SH coefficient k of channel c at row 11 + 3k + c, K = (deg+1)^2
  *     rows = 11 + 3K (14 for degree 0, 59 for degree 3)
  * Gradient, Hutchinson, EMA and radius buffers use the same struct and layout.
- * Global parameter index (used by the probes) j = row * n + column.
+ * Probe entry of row r of Gaussian (column) i: j = i * rows + r (see gs_probe).
  */
 #ifndef GS3DTR_H
 #define GS3DTR_H
@@ -93,8 +93,10 @@ typedef struct gs_frame {
   int32_t n_views, width, height, tile_w, tile_h;
 } gs_frame;
 
-/* Rademacher probes z_k (k < nu) of step t: entry j is +1 or -1 from bit 63 of
- * SplitMix64(seed ^ t * 0x9E3779B97F4A7C15 ^ (k << 56) ^ j). */
+/* Rademacher probes z_k (k < nu) of step t: row r of Gaussian i is entry
+ * j = i * rows + r (rows = 11 + 3K), and entry j is -1 where bit (j mod 64) of
+ * SplitMix64(seed ^ t * 0x9E3779B97F4A7C15 ^ (k << 56) ^ (j / 64)) is set, +1
+ * otherwise: 64 entries per hash. */
 typedef struct gs_probe {
   uint64_t seed;
   int64_t t;

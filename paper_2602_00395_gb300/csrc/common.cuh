@@ -48,9 +48,17 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
   z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
   return z ^ (z >> 31);
 }
-// true where probe k's entry j at step t is -1
-__device__ __forceinline__ bool probe_negative(uint64_t seed, int64_t t, int k, uint64_t j) {
-  return (splitmix64(seed ^ ((uint64_t)t * kGolden) ^ ((uint64_t)k << 56) ^ j) >> 63) != 0;
+// Signs of Rademacher probe k at step t for the rows [0, rows) of Gaussian i:
+// bit r is set where entry j = i * rows + r is -1.  Entry j is bit j mod 64 of
+// the hash of word j / 64 (64 entries per hash), so the rows of one Gaussian
+// (rows <= 64) take one or two hashes.
+__device__ __forceinline__ uint64_t probe_signs(uint64_t seed, int64_t t, int k, uint64_t i, int rows) {
+  const uint64_t key = seed ^ ((uint64_t)t * kGolden) ^ ((uint64_t)k << 56);
+  const uint64_t j0 = i * (uint64_t)rows, w0 = j0 >> 6;
+  const int off = (int)(j0 & 63);
+  uint64_t bits = splitmix64(key ^ w0) >> off;
+  if (off + rows > 64) bits |= splitmix64(key ^ (w0 + 1)) << (64 - off);
+  return rows >= 64 ? bits : (bits & ((1ull << rows) - 1ull));
 }
 
 // ------------------------------------------------ forward-mode dual numbers
@@ -257,6 +265,15 @@ __device__ __forceinline__ void sh_basis_grad(float x, float y, float z, const f
       g[1] += 6.f * kY3a * x * y * w[15];
     }
   }
+}
+
+// A read-only global load the compiler may neither hoist out of a loop nor
+// merge with another: used for parameters re-read per view so that they do not
+// occupy registers across the view loop.
+__device__ __forceinline__ float ld_once(const float* p) {
+  float v;
+  asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(v) : "l"(p));
+  return v;
 }
 
 // ------------------------------------------------------ footprint extents

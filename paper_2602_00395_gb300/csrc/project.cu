@@ -27,8 +27,18 @@ __device__ __forceinline__ void store_culled(float4* rec, size_t at) {
   rec[3 * at + 2] = make_float4(0.f, 0.f, __int_as_float(0), 0.f);
 }
 
+// Minimum resident CTAs per SM requested for the projection (0: none).
+#ifndef GS_PROJ_MIN_BLOCKS
+#define GS_PROJ_MIN_BLOCKS 3
+#endif
+#if GS_PROJ_MIN_BLOCKS > 0
+#define GS_PROJ_BOUNDS __launch_bounds__(128, GS_PROJ_MIN_BLOCKS)
+#else
+#define GS_PROJ_BOUNDS __launch_bounds__(128)
+#endif
+
 template <int DEG, int NU>
-__global__ void __launch_bounds__(128) project_kernel(const float* __restrict__ P, int n, int n_pad,
+__global__ void GS_PROJ_BOUNDS project_kernel(const float* __restrict__ P, int n, int n_pad,
                                                       const gs_camera* __restrict__ cams, gs_frame fr,
                                                       uint64_t seed, int64_t step, float4* __restrict__ rec,
                                                       float4* __restrict__ tan) {
@@ -46,16 +56,10 @@ __global__ void __launch_bounds__(128) project_kernel(const float* __restrict__ 
     return;
   }
 
-  // probe signs: bit r of neg[k] is set where z_k(r * n + i) = -1
+  // probe signs: bit r of neg[k] is set where probe k is -1 on row r
   uint64_t neg[NU > 0 ? NU : 1];
 #pragma unroll
-  for (int k = 0; k < NU; ++k) {
-    uint64_t m = 0;
-#pragma unroll 4
-    for (int r = 0; r < ROWS; ++r)
-      if (probe_negative(seed, step, k, (uint64_t)r * (uint64_t)n + (uint64_t)i)) m |= 1ull << r;
-    neg[k] = m;
-  }
+  for (int k = 0; k < NU; ++k) neg[k] = probe_signs(seed, step, k, (uint64_t)i, ROWS);
   auto ld = [&](int r) -> S {
     float v = __ldg(P + (size_t)r * n_pad + i);
     if constexpr (NU == 0) {
@@ -100,6 +104,7 @@ __global__ void __launch_bounds__(128) project_kernel(const float* __restrict__ 
   Sg[2][1] = Sg[1][2];
   const S opac = 1.f / (1.f + sexp(-ld(10)));
 
+#pragma unroll 1
   for (int v = 0; v < V; ++v) {
     const gs_camera* c = cams + v;
     const size_t at = (size_t)v * n_pad + i;
@@ -162,12 +167,25 @@ __global__ void __launch_bounds__(128) project_kernel(const float* __restrict__ 
     d0 = d0 / dn; d1 = d1 / dn; d2 = d2 / dn;
     S Y[K];
     sh_basis<DEG>(d0, d1, d2, Y);
+    // rgb = 0.5 + sum_k Y_k sh_k; the coefficients are plain parameters whose
+    // probe tangents are the signs z, re-read per view (ld_once)
     S rgb[3];
 #pragma unroll
     for (int ch = 0; ch < 3; ++ch) {
       S acc = constant<S>(0.5f);
 #pragma unroll
-      for (int k = 0; k < K; ++k) acc = acc + Y[k] * ld(kRowSH + 3 * k + ch);
+      for (int k = 0; k < K; ++k) {
+        const int row = kRowSH + 3 * k + ch;
+        const float sh = ld_once(P + (size_t)row * n_pad + i);
+        if constexpr (NU == 0) {
+          acc = acc + Y[k] * sh;
+        } else {
+          acc.v += Y[k].v * sh;
+#pragma unroll
+          for (int p = 0; p < NU; ++p)
+            acc.d[p] += Y[k].d[p] * sh + (((neg[p] >> row) & 1ull) ? -Y[k].v : Y[k].v);
+        }
+      }
       rgb[ch] = (val(acc) < 0.f) ? constant<S>(0.f) : acc;
     }
 

@@ -543,6 +543,15 @@ __global__ void GS_BWD_BOUNDS raster_bwd_kernel(
 // recorded in the first.  The probe streams are combined into
 // hz = (1/nu) sum_k z_k . (G z_k).
 constexpr int kPbwdThreads = 128;
+// Minimum resident CTAs per SM requested for the projection reverse (0: none).
+#ifndef GS_PBWD_MIN_BLOCKS
+#define GS_PBWD_MIN_BLOCKS 3
+#endif
+#if GS_PBWD_MIN_BLOCKS > 0
+#define GS_PBWD_BOUNDS __launch_bounds__(kPbwdThreads, GS_PBWD_MIN_BLOCKS)
+#else
+#define GS_PBWD_BOUNDS __launch_bounds__(kPbwdThreads)
+#endif
 constexpr int kClampViews = 21;  // clamp bits kept for the first 21 views (3 per view)
 
 struct ViewGeom {
@@ -573,7 +582,7 @@ __device__ __forceinline__ void view_direction(const ViewGeom& v, const float mu
 }
 
 template <int DEG, int NU, bool GRAD>
-__global__ void __launch_bounds__(kPbwdThreads) project_bwd_kernel(const float* __restrict__ P, int n, int n_pad,
+__global__ void GS_PBWD_BOUNDS project_bwd_kernel(const float* __restrict__ P, int n, int n_pad,
                                                                    const gs_camera* __restrict__ cams, gs_frame fr,
                                                                    const float* __restrict__ cot, uint64_t seed,
                                                                    int64_t step, float* __restrict__ grad,
@@ -625,15 +634,27 @@ __global__ void __launch_bounds__(kPbwdThreads) project_bwd_kernel(const float* 
     }
   }
   uint64_t clamp_bits = 0;  // bit 3 v + c: colour channel c clamped at 0 in view v (v < kClampViews)
+  // the next view's cotangent row is loaded while this one is processed
+  float4 nxt[NVP / 4];
+  {
+    const float4* row4 = reinterpret_cast<const float4*>(cot + (size_t)i * NVP);
+#pragma unroll
+    for (int q = 0; q < NVP / 4; ++q) nxt[q] = row4[q];
+  }
+#pragma unroll 1
   for (int v = 0; v < fr.n_views; ++v) {
-    const float4* row4 = reinterpret_cast<const float4*>(cot + ((size_t)v * n_pad + i) * NVP);
     float c[NVP];
     bool any = false;
 #pragma unroll
     for (int q = 0; q < NVP / 4; ++q) {
-      const float4 x4 = row4[q];
+      const float4 x4 = nxt[q];
       c[4 * q + 0] = x4.x; c[4 * q + 1] = x4.y; c[4 * q + 2] = x4.z; c[4 * q + 3] = x4.w;
       any = any || x4.x != 0.f || x4.y != 0.f || x4.z != 0.f || x4.w != 0.f;
+    }
+    if (v + 1 < fr.n_views) {
+      const float4* row4 = reinterpret_cast<const float4*>(cot + ((size_t)(v + 1) * n_pad + i) * NVP);
+#pragma unroll
+      for (int q = 0; q < NVP / 4; ++q) nxt[q] = row4[q];
     }
     if (!any) continue;
     ViewGeom vg;
@@ -715,19 +736,22 @@ __global__ void __launch_bounds__(kPbwdThreads) project_bwd_kernel(const float* 
     view_direction(vg, mu, d, dn);
     float Y[K];
     sh_basis<DEG>(d[0], d[1], d[2], Y);
-    float sh[K][3];
-#pragma unroll
-    for (int k = 0; k < K; ++k)
-#pragma unroll
-      for (int ch = 0; ch < 3; ++ch) sh[k][ch] = ld(kRowSH + 3 * k + ch);
+    // per channel: the raw colour (its clamp decision) and, for the colour's
+    // dependence on mu, the direction gradient of sum_k sh_k Y_k; the SH
+    // coefficients are re-read per view (ld_once) instead of held in registers
     bool clamped[3];
+    float gdc[3][3];
 #pragma unroll
     for (int ch = 0; ch < 3; ++ch) {
+      float shc[K];
+#pragma unroll
+      for (int k = 0; k < K; ++k) shc[k] = ld_once(P + (size_t)(kRowSH + 3 * k + ch) * n_pad + i);
       float raw = 0.5f;
 #pragma unroll
-      for (int k = 0; k < K; ++k) raw += Y[k] * sh[k][ch];
+      for (int k = 0; k < K; ++k) raw += Y[k] * shc[k];
       clamped[ch] = raw < 0.f;
       if (clamped[ch] && v < kClampViews) clamp_bits |= 1ull << (3 * v + ch);
+      if constexpr (DEG > 0) sh_basis_grad<DEG>(d[0], d[1], d[2], shc, gdc[ch]);
     }
     if constexpr (DEG > 0) {
 #pragma unroll
@@ -735,11 +759,9 @@ __global__ void __launch_bounds__(kPbwdThreads) project_bwd_kernel(const float* 
         float gcol[3];
 #pragma unroll
         for (int ch = 0; ch < 3; ++ch) gcol[ch] = clamped[ch] ? 0.f : c[9 * st + 6 + ch];
-        float wk[K];
-#pragma unroll
-        for (int k = 0; k < K; ++k) wk[k] = sh[k][0] * gcol[0] + sh[k][1] * gcol[1] + sh[k][2] * gcol[2];
         float gd[3];
-        sh_basis_grad<DEG>(d[0], d[1], d[2], wk, gd);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) gd[q] = gcol[0] * gdc[0][q] + gcol[1] * gdc[1][q] + gcol[2] * gdc[2][q];
         const float dot = gd[0] * d[0] + gd[1] * d[1] + gd[2] * d[2];
 #pragma unroll
         for (int q = 0; q < 3; ++q) g_mu[st][q] += (gd[q] - d[q] * dot) / dn;
@@ -790,9 +812,10 @@ __global__ void __launch_bounds__(kPbwdThreads) project_bwd_kernel(const float* 
       for (int r = 0; r < kRowSH; ++r) grad[(size_t)r * n_pad + i] = rowv[r];
     } else {
       const int k = st - (GRAD ? 1 : 0);
+      const uint64_t zneg = probe_signs(seed, step, k, (uint64_t)i, kRowSH + 3 * K);
 #pragma unroll
       for (int r = 0; r < kRowSH; ++r) {
-        const bool neg = probe_negative(seed, step, k, (uint64_t)r * (uint64_t)n + (uint64_t)i);
+        const bool neg = (zneg >> r) & 1ull;
         hz_geo[r] += (neg ? -rowv[r] : rowv[r]) * inv_nu;
       }
     }
@@ -808,6 +831,7 @@ __global__ void __launch_bounds__(kPbwdThreads) project_bwd_kernel(const float* 
     float g_sh[K][3];
 #pragma unroll
     for (int k = 0; k < K; ++k) g_sh[k][0] = g_sh[k][1] = g_sh[k][2] = 0.f;
+#pragma unroll 1
     for (int v = 0; v < fr.n_views; ++v) {
       const float* cv = cot + ((size_t)v * n_pad + i) * NVP + 9 * st + 6;
       float gcol[3] = {cv[0], cv[1], cv[2]};
@@ -827,7 +851,7 @@ __global__ void __launch_bounds__(kPbwdThreads) project_bwd_kernel(const float* 
         for (int ch = 0; ch < 3; ++ch) {
           float raw = 0.5f;
 #pragma unroll
-          for (int k = 0; k < K; ++k) raw += Y[k] * ld(kRowSH + 3 * k + ch);
+          for (int k = 0; k < K; ++k) raw += Y[k] * ld_once(P + (size_t)(kRowSH + 3 * k + ch) * n_pad + i);
           if (raw < 0.f) gcol[ch] = 0.f;
         }
       }
@@ -843,12 +867,13 @@ __global__ void __launch_bounds__(kPbwdThreads) project_bwd_kernel(const float* 
         for (int ch = 0; ch < 3; ++ch) grad[(size_t)(kRowSH + 3 * k + ch) * n_pad + i] = g_sh[k][ch];
     } else {
       const int kp = st - (GRAD ? 1 : 0);
+      const uint64_t zneg = probe_signs(seed, step, kp, (uint64_t)i, kRowSH + 3 * K);
 #pragma unroll
       for (int k = 0; k < K; ++k)
 #pragma unroll
         for (int ch = 0; ch < 3; ++ch) {
           const int r = kRowSH + 3 * k + ch;
-          const bool neg = probe_negative(seed, step, kp, (uint64_t)r * (uint64_t)n + (uint64_t)i);
+          const bool neg = (zneg >> r) & 1ull;
           const float val = (neg ? -g_sh[k][ch] : g_sh[k][ch]) * inv_nu;
           float* dst = hz + (size_t)r * n_pad + i;
           *dst = (kp == 0) ? val : *dst + val;

@@ -107,7 +107,9 @@ __global__ void __launch_bounds__(256) tr_update_kernel(float* __restrict__ x, f
   const float a1 = cfg.theta1, b1 = 1.f - cfg.theta1;
   const float a2 = cfg.theta2, b2 = 1.f - cfg.theta2;
   bool bad = false;
-#pragma unroll 4
+  // fully unrolled: every row's radius is then a register, not a local-memory
+  // array element, and the loads of consecutive rows can be issued together
+#pragma unroll
   for (int r = 0; r < ROWS; ++r) {
     const size_t j = at(r);
     const float eta = r < kRowSH ? eta_fixed[r] : col_eta[(r - kRowSH) % 3] / sh_absmax((r - kRowSH) / 3);
