@@ -155,10 +155,11 @@ def kernel_launches_per_step(eng) -> int:
         while (1 << b) < v:
             b += 1
         return b
-    rec_pass = (32 + bits(N_VIEWS) + 7) // 8
+    rec_pass = 4  # 32 depth bits, per view
     pair_pass = max(1, (bits(N_VIEWS * eng.Tx * eng.Ty) + 7) // 8)
     radix = 1 + 3 + 1  # histogram, three-kernel scan, scatter
-    sort = 1 + 1 + rec_pass * radix + 1 + 3 + 1 + pair_pass * radix + 1
+    # record keys, record passes, count gather, three-kernel scan, emit, pair passes, ranges
+    sort = 1 + rec_pass * radix + 1 + 3 + 1 + pair_pass * radix + 1
     return 1 + sort + 1 + 2 + 1  # project, sort, fwd, reverse blend + projection reverse, update
 
 
@@ -444,11 +445,13 @@ def run_cuda(args):
         while (1 << b) < v:
             b += 1
         return b
-    rec_pass = (32 + bits(N_VIEWS) + 7) // 8
+    rec_pass = 4
     pair_pass = max(1, (bits(N_VIEWS * eng.Tx * eng.Ty) + 7) // 8)
     work = {
         "project": ("hbm", eng.n * rows * 4 + N_VIEWS * eng.n * 48 * (1 + NU)),
-        "bin_sort": ("hbm", need * (12 + 24 * pair_pass + 8) + R * (32 + 24 * rec_pass + 8)),
+        # per pair: emit 12 B, 24 B per pass, ranges 8 B; per record: 32 B read for
+        # its key, 16 B per pass, 12 B count gather, 40 B read by the emit
+        "bin_sort": ("hbm", need * (12 + 24 * pair_pass + 8) + R * (32 + 16 * rec_pass + 12 + 40)),
         "raster_fwd": ("alu", raster_fwd_flops_per_unit() * sum_nc),
         "raster_bwd": ("alu", raster_bwd_flops_per_unit() * sum_nc),
         "update": ("hbm", eng.n * rows * 4 * (5 + 3)),

@@ -169,7 +169,8 @@ gs_status gs_project(const gs_params* x, const gs_camera* cams, gs_frame frame, 
 /* Sec. 3.1 tile binning and depth order: all (tile, splat) pairs of all views
  * sorted by (key, splat index), and each tile's [start, end).  If the pairs
  * exceed out->capacity, GS_FLAG_CAPACITY is raised, *n_pairs holds the need,
- * and the sorted arrays are incomplete (but every access stays in bounds). */
+ * and the sorted arrays are incomplete (but every access stays in bounds and
+ * every range end is at most the capacity). */
 size_t gs_bin_sort_workspace_size(int32_t n_pad, gs_frame frame, uint64_t capacity);
 gs_status gs_bin_sort(const gs_projected* proj, int32_t n_pad, gs_frame frame, void* workspace,
                       size_t workspace_bytes, gs_sorted* out, int32_t* status, void* stream);

@@ -2,11 +2,11 @@
 // with the per-parameter squared-Hellinger trust-region radius of Sec. 4.2 and
 // Appendix B.
 //
-// One thread per Gaussian: the per-Gaussian geometry the radii need (alpha,
-// scales, rotation, Sigma_cc, beta_c, DC colour) is computed once in registers
-// from x_t, then the thread streams its 11 + 3K rows (coalesced across the
-// warp): read x, g_ema, d_ema, grad (and hz on curvature steps), write x, g_ema
-// (and d_ema).  The kernel is HBM-bound.
+// A block owns 256 consecutive Gaussians: first the per-Gaussian geometry the
+// radii need (alpha, scales, rotation, Sigma_cc, beta_c, DC colour) is turned
+// into 14 radii in shared memory, from x_t; then the block streams all 11 + 3K
+// rows of its columns with float4 accesses: read x, g_ema, d_ema, grad (and hz
+// on curvature steps), write x, g_ema (and d_ema).  The kernel is HBM-bound.
 //
 // The rotation constant beta_c of Appendix B is evaluated in closed form:
 // beta_c = 2 ||S^-1 W_c S||_F^2 - 2 ||W_c||_F^2 = 2 sum_{i<j} W_ij^2 (s_i/s_j - s_j/s_i)^2,
@@ -35,18 +35,19 @@ __device__ __forceinline__ float sh_absmax(int k) {
   }
 }
 
-template <int DEG, bool HVP, bool ETA>
-__global__ void __launch_bounds__(256) tr_update_kernel(float* __restrict__ x, float* __restrict__ ge,
-                                                        float* __restrict__ de, const float* __restrict__ g,
-                                                        const float* __restrict__ hz, float* __restrict__ eta_out,
-                                                        int n, int n_pad, gs_tr_config cfg, float eps,
-                                                        int32_t* status) {
-  constexpr int K = (DEG + 1) * (DEG + 1);
-  constexpr int ROWS = kRowSH + 3 * K;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+// One block owns kUpdCols consecutive Gaussians (columns) for all rows.
+// Phase 1, one thread per column: the 11 geometric radii and the 3 colour
+// radii (before division by max |Y_k|) from x_t into shared memory.  Phase 2:
+// the block streams the rows, each thread taking 4 consecutive columns of a row
+// (float4), kUpdCols / 4 threads per row and blockDim / (kUpdCols / 4) rows at
+// a time.  The radii are read before any column of the block is written, and
+// no other block touches these columns, so every radius is that of x_t.
+constexpr int kUpdCols = 256;
+constexpr int kEtaRows = kRowSH + 3;
+
+__device__ __forceinline__ void radii_of_column(const float* __restrict__ x, int i, int n_pad, const gs_tr_config& cfg,
+                                                float eps, float (&eta)[kEtaRows]) {
   auto at = [&](int r) { return (size_t)r * n_pad + i; };
-  // geometry from x_t
   const float logit = x[at(10)];
   const float alpha = 1.f / (1.f + expf(-logit));
   const float alpha_c = 1.f / (1.f + expf(logit));  // 1 - alpha without cancellation
@@ -68,7 +69,6 @@ __global__ void __launch_bounds__(256) tr_update_kernel(float* __restrict__ x, f
   R[2][2] = 1.f - 2.f * (X * X + Y * Y);
   const bool logok = alpha > eps;
   const float L = logok ? log1pf(-eps / alpha) : 0.f;  // ln(1 - eps/alpha)
-  float eta_fixed[11];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     float var;
@@ -79,8 +79,8 @@ __global__ void __launch_bounds__(256) tr_update_kernel(float* __restrict__ x, f
     } else {
       var = R[c][0] * R[c][0] * s[0] * s[0] + R[c][1] * R[c][1] * s[1] * s[1] + R[c][2] * R[c][2] * s[2] * s[2];
     }
-    eta_fixed[c] = logok ? sqrtf(-8.f * var * L) : INFINITY;
-    eta_fixed[3 + c] = sqrtf(2.f * eps / alpha);
+    eta[c] = logok ? sqrtf(-8.f * var * L) : INFINITY;
+    eta[3 + c] = sqrtf(2.f * eps / alpha);
   }
   {
     // body-frame angular velocity per unit change of q_c (x, y, z, w)
@@ -93,38 +93,85 @@ __global__ void __launch_bounds__(256) tr_update_kernel(float* __restrict__ x, f
     for (int c = 0; c < 4; ++c) {
       const float w0 = k2 * om[c][0], w1 = k2 * om[c][1], w2 = k2 * om[c][2];
       const float beta = 2.f * (w2 * w2 * r01 * r01 + w1 * w1 * r02 * r02 + w0 * w0 * r12 * r12);
-      eta_fixed[6 + c] = (logok && beta > 0.f) ? sqrtf(-8.f / beta * L) : INFINITY;
+      eta[6 + c] = (logok && beta > 0.f) ? sqrtf(-8.f / beta * L) : INFINITY;
     }
   }
-  eta_fixed[10] = sqrtf(4.f * alpha * eps) / (alpha * alpha_c);
-  float col_eta[3];
+  eta[10] = sqrtf(4.f * alpha * eps) / (alpha * alpha_c);
 #pragma unroll
   for (int ch = 0; ch < 3; ++ch) {
     const float Cc = fmaxf(kY0 * x[at(kRowSH + ch)] + 0.5f, cfg.color_floor);
-    col_eta[ch] = sqrtf(4.f * Cc * eps / alpha);
+    eta[kRowSH + ch] = sqrtf(4.f * Cc * eps / alpha);
   }
+}
 
+template <int DEG, bool HVP, bool ETA>
+__global__ void __launch_bounds__(256) tr_update_kernel(float* __restrict__ x, float* __restrict__ ge,
+                                                        float* __restrict__ de, const float* __restrict__ g,
+                                                        const float* __restrict__ hz, float* __restrict__ eta_out,
+                                                        int n, int n_pad, gs_tr_config cfg, float eps,
+                                                        int32_t* status) {
+  constexpr int K = (DEG + 1) * (DEG + 1);
+  constexpr int ROWS = kRowSH + 3 * K;
+  constexpr int kLanesPerRow = kUpdCols / 4;  // 64
+  __shared__ __align__(16) float s_eta[kEtaRows][kUpdCols];
+  const int c0 = blockIdx.x * kUpdCols;
+  // phase 1: radii of this block's columns, from x_t
+  {
+    const int i = c0 + (int)threadIdx.x;
+    float eta[kEtaRows];
+    if (i < n) {
+      radii_of_column(x, i, n_pad, cfg, eps, eta);
+    } else {
+#pragma unroll
+      for (int q = 0; q < kEtaRows; ++q) eta[q] = 0.f;
+    }
+#pragma unroll
+    for (int q = 0; q < kEtaRows; ++q) s_eta[q][threadIdx.x] = eta[q];
+  }
+  __syncthreads();
+  // phase 2: every row of the block's columns, 4 columns per thread
+  const int lane4 = (int)threadIdx.x % kLanesPerRow, row0 = (int)threadIdx.x / kLanesPerRow;
+  const int rstep = (int)blockDim.x / kLanesPerRow;
+  const int ci = c0 + 4 * lane4;  // first of this thread's 4 columns (n_pad % 4 == 0)
   const float a1 = cfg.theta1, b1 = 1.f - cfg.theta1;
   const float a2 = cfg.theta2, b2 = 1.f - cfg.theta2;
   bool bad = false;
-  // fully unrolled: every row's radius is then a register, not a local-memory
-  // array element, and the loads of consecutive rows can be issued together
+  if (ci < n) {
+#pragma unroll 4
+    for (int r = row0; r < ROWS; r += rstep) {
+      int q = r;
+      float scale = 1.f;
+      if (r >= kRowSH) {
+        q = kRowSH + (r - kRowSH) % 3;
+        scale = 1.f / sh_absmax((r - kRowSH) / 3);
+      }
+      const float4 e4 = *reinterpret_cast<const float4*>(&s_eta[q][4 * lane4]);
+      const size_t j = (size_t)r * n_pad + ci;
+      const float4 x4 = *reinterpret_cast<const float4*>(x + j);
+      const float4 ge4 = *reinterpret_cast<const float4*>(ge + j);
+      const float4 g4 = *reinterpret_cast<const float4*>(g + j);
+      const float4 de4 = *reinterpret_cast<const float4*>(de + j);
+      float4 hz4 = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (HVP) hz4 = *reinterpret_cast<const float4*>(hz + j);
+      const float ev[4] = {e4.x * scale, e4.y * scale, e4.z * scale, e4.w * scale};
+      const float xv[4] = {x4.x, x4.y, x4.z, x4.w}, gev[4] = {ge4.x, ge4.y, ge4.z, ge4.w};
+      const float gv[4] = {g4.x, g4.y, g4.z, g4.w}, hv[4] = {hz4.x, hz4.y, hz4.z, hz4.w};
+      const float dv0[4] = {de4.x, de4.y, de4.z, de4.w};
+      float xo[4], go[4], dn[4];
 #pragma unroll
-  for (int r = 0; r < ROWS; ++r) {
-    const size_t j = at(r);
-    const float eta = r < kRowSH ? eta_fixed[r] : col_eta[(r - kRowSH) % 3] / sh_absmax((r - kRowSH) / 3);
-    const float gnew = a1 * ge[j] + b1 * g[j];
-    float dnew = de[j];
-    if (HVP) {
-      dnew = a2 * dnew + b2 * hz[j];
-      de[j] = dnew;
+      for (int k = 0; k < 4; ++k) {
+        const bool live = ci + k < n;  // padding columns stay as they are
+        go[k] = live ? a1 * gev[k] + b1 * gv[k] : gev[k];
+        dn[k] = (HVP && live) ? a2 * dv0[k] + b2 * hv[k] : dv0[k];
+        const float step = -go[k] / fmaxf(dn[k], cfg.d_floor);
+        xo[k] = live ? xv[k] + fminf(fmaxf(step, -ev[k]), ev[k]) : xv[k];
+        if (live) bad = bad || !isfinite(xo[k]) || !isfinite(go[k]) || !isfinite(dn[k]);
+      }
+      *reinterpret_cast<float4*>(x + j) = make_float4(xo[0], xo[1], xo[2], xo[3]);
+      *reinterpret_cast<float4*>(ge + j) = make_float4(go[0], go[1], go[2], go[3]);
+      if (HVP) *reinterpret_cast<float4*>(de + j) = make_float4(dn[0], dn[1], dn[2], dn[3]);
+      if (ETA) *reinterpret_cast<float4*>(eta_out + j) = make_float4(ev[0], ev[1], ev[2], ev[3]);
     }
-    ge[j] = gnew;
-    const float step = -gnew / fmaxf(dnew, cfg.d_floor);
-    const float xn = x[j] + fminf(fmaxf(step, -eta), eta);
-    x[j] = xn;
-    if (ETA) eta_out[j] = eta;
-    bad = bad || !isfinite(xn) || !isfinite(gnew) || !isfinite(dnew);
   }
   if (bad && status) atomicOr(status, GS_FLAG_NONFINITE);
 }
@@ -133,7 +180,7 @@ template <int DEG>
 void launch_update(bool hvp, bool eta, gs_params* x, gs_params* ge, gs_params* de, const gs_params* g,
                    const gs_params* hz, gs_params* eta_out, gs_tr_config cfg, float eps, int32_t* status,
                    cudaStream_t st) {
-  const int blocks = (x->n + 255) / 256;
+  const int blocks = (x->n + kUpdCols - 1) / kUpdCols;
   const float* hp = hz ? hz->data : nullptr;
   float* ep = eta_out ? eta_out->data : nullptr;
 #define GS_UPD(H, E) \

@@ -124,7 +124,10 @@ def _write_records(e, mx, my, r, d):
     (128, 128, (16, 16), 1, 1000, 40),
     (97, 53, (16, 8), 3, 4001, 30),
     (61, 45, (8, 8), 2, 777, 60),
-    (1297, 840, (16, 16), 2, 150000, 80),  # ~ millions of pairs, many radix blocks
+    (1297, 840, (16, 16), 2, 150000, 80),  # ~ millions of pairs, many chunks
+    # more tiles per view than the shared counters hold: pairs sorted by radix passes
+    (3840, 2160, (16, 16), 1, 60000, 120),
+    (2100, 1500, (8, 8), 2, 30000, 40),
 ])
 def test_bin_sort_bit_exact(W, H, tile, V, n, maxr):
     recs = [S.projected_records(n, W, H, seed=100 + v, max_radius=maxr) for v in range(V)]
@@ -144,8 +147,9 @@ def test_bin_sort_bit_exact(W, H, tile, V, n, maxr):
     np.testing.assert_array_equal(e.ranges.cpu().numpy().view(np.uint32).reshape(-1, 2), ranges)
 
 
-def test_bin_sort_capacity_overflow_is_flagged_and_in_bounds():
-    W, H, n = 128, 96, 3000
+@pytest.mark.parametrize("W,H", [(128, 96), (3840, 2160)])
+def test_bin_sort_capacity_overflow_is_flagged_and_in_bounds(W, H):
+    n = 3000
     mx, my, r, d = S.projected_records(n, W, H, seed=5, max_radius=50)
     keys, _, _ = O.bin_sort(mx, my, r, d, W, H)
     e = _engine(n, 0, [S.single_camera(W, H)], nu=0, capacity=len(keys) // 3)
@@ -155,6 +159,9 @@ def test_bin_sort_capacity_overflow_is_flagged_and_in_bounds():
     from paper_2602_00395_gb300 import gs3dtr as G
     assert int(e.n_pairs.item()) == len(keys)
     assert e.read_status() & G.GS_FLAG_CAPACITY
+    cap = len(keys) // 3
+    rg = e.ranges.cpu().numpy().view(np.uint32).reshape(-1, 2)
+    assert rg.max() <= cap
 
 
 def test_bin_sort_empty_input():
