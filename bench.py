@@ -160,7 +160,22 @@ def kernel_launches_per_step(eng) -> int:
     radix = 1 + 3 + 1  # histogram, three-kernel scan, scatter
     # record keys, record passes, count gather, three-kernel scan, emit, pair passes, ranges
     sort = 1 + rec_pass * radix + 1 + 3 + 1 + pair_pass * radix + 1
-    return 1 + sort + 1 + 2 + 1  # project, sort, fwd, reverse blend + projection reverse, update
+    # step counter, project, sort, fwd, reverse blend + projection reverse, update
+    return 1 + 1 + sort + 1 + 2 + 1
+
+
+def retile_workload(eng, cam_dev, targets, batches, tile, device):
+    """The same workload (parameters, cameras, targets) on a step with another tile shape."""
+    from paper_2602_00395_gb300.engine import TRStep
+    e = TRStep(eng.n, SH_DEG, eng.V, W, H, nu=NU, tile=tile, cfg=eng.cfg, device=device)
+    e.x.copy_(eng.x)
+    need = 0
+    for cd in cam_dev:
+        e.cams.copy_(cd)
+        need = max(need, e.ensure_capacity())
+    if need * 1.15 > e.capacity:
+        e._alloc_pairs(int(need * 1.3))
+    return e, cam_dev, targets, batches, need
 
 
 def timed_steps(eng, cam_dev, targets, K, W0, t0, stream, per_call=False):
@@ -251,14 +266,31 @@ def plain_loop_steps(eng, cam_dev, targets, K, t0, stream, device):
     return ms
 
 
-def e2e_steps(eng, batches, host_targets, K, t0, stream):
+def graph_steps(eng, graphs, K, t0, stream):
+    """K steps replayed from the captured graphs (one per view batch); the step
+    index runs on the device from t0.  Returns ms from events on `stream`."""
+    import torch
+    nb = len(graphs)
+    eng.t_dev.fill_(t0 - 1)
+    torch.cuda.synchronize()
+    start = torch.cuda.Event(enable_timing=True)
+    stop = torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        start.record(stream)
+        for k in range(K):
+            graphs[(t0 + k - 1) % nb].replay()
+        stop.record(stream)
+    stop.synchronize()
+    return start.elapsed_time(stop)
+
+
+def e2e_steps(eng, batches, host_targets, K, t0, stream, schedule):
     """K steps through the C ABI with each step's targets and cameras copied from
     pinned host memory and the loss copied back, all inside the timed region.
     The copy of step k+1's inputs runs on a second stream into the other half of
-    a double buffer while step k computes."""
+    a double buffer while step k, a graph replay bound to that half, computes."""
     import torch
     from paper_2602_00395_gb300 import gs3dtr as G
-    from paper_2602_00395_gb300.engine import eps_schedule
     host_cams = [torch.from_numpy(G.camera_bytes(bc)).pin_memory() for bc in batches]
     loss_host = torch.zeros(K, dtype=torch.float32).pin_memory()
     nb = len(batches)
@@ -269,6 +301,12 @@ def e2e_steps(eng, batches, host_targets, K, t0, stream):
     consumed = [torch.cuda.Event() for _ in range(2)]
     start = torch.cuda.Event(enable_timing=True)
     stop = torch.cuda.Event(enable_timing=True)
+    graphs = []
+    for slot in range(2):
+        eng.target = dev_tg[slot]
+        eng.cams = dev_cams[slot]
+        graphs.append(eng.capture_step(True, schedule, stream))
+    eng.t_dev.fill_(t0 - 1)
 
     def prefetch(k):
         b = (t0 + k - 1) % nb
@@ -288,11 +326,8 @@ def e2e_steps(eng, batches, host_targets, K, t0, stream):
         prefetch(1)
     with torch.cuda.stream(stream):
         for k in range(K):
-            t = t0 + k
             stream.wait_event(copied[k % 2])
-            eng.target = dev_tg[k % 2]
-            eng.cams = dev_cams[k % 2]
-            eng.step(t, eps_schedule(t, 30000), stream)
+            graphs[k % 2].replay()
             loss_host[k:k + 1].copy_(eng.loss_val, non_blocking=True)
             consumed[k % 2].record(stream)
             if k + 2 < K:
@@ -402,18 +437,33 @@ def run_cuda(args):
         return
     eng, cam_dev, targets, batches, need = make_workload(args.n, device, rank)
     stream = torch.cuda.Stream(device=device)
+    # tile shape: measured on this workload (the step is rebuilt if another shape wins)
+    from paper_2602_00395_gb300.engine import autotune_tile
+    best_tile, tile_ms = autotune_tile(eng, stream=stream)
+    if best_tile != tuple(TILE):
+        eng, cam_dev, targets, batches, need = retile_workload(eng, cam_dev, targets, batches, best_tile, device)
     # warm-up
     timed_steps(eng, cam_dev, targets, max(args.warmup, 3), 0, 1, stream)
     torch.cuda.synchronize()
     eng.status.zero_()
     # per-call breakdown (separate, untimed for the headline)
     _, per_call = timed_steps(eng, cam_dev, targets, max(2, min(args.steps, 5)), 0, 100, stream, per_call=True)
+    # the eager step sequence (six calls per step from the host), for reference
+    eager_ms, _ = timed_steps(eng, cam_dev, targets, args.steps, 0, 500, stream)
+    # one captured graph per view batch; each replay is a whole step
+    sched = G.gs_eps_schedule(1e-6, 1e-8, 30000)
+    graphs = []
+    for b in range(len(cam_dev)):
+        eng.cams = cam_dev[b]
+        eng.target = targets[b]
+        graphs.append(eng.capture_step(True, sched, stream))
+    graph_steps(eng, graphs, max(args.warmup, 3), 700, stream)  # untimed replays
     # timed region
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
-        ms, _ = timed_steps(eng, cam_dev, targets, args.steps, 0, 1000, stream)
+        ms = graph_steps(eng, graphs, args.steps, 1000, stream)
         torch.cuda.synchronize()
     status = eng.read_status()
     if ws > 1:
@@ -426,7 +476,7 @@ def run_cuda(args):
     value = ws * args.steps / (ms / 1e3)
     # end to end through the C ABI from pinned host buffers
     host_targets = [tg.cpu().pin_memory() for tg in targets]
-    e2e_ms, e2e_wall, h2d, d2h = e2e_steps(eng, batches, host_targets, args.steps, 5000, stream)
+    e2e_ms, e2e_wall, h2d, d2h = e2e_steps(eng, batches, host_targets, args.steps, 5000, stream, sched)
     e2e_val = ws * args.steps / (e2e_ms / 1e3)
     # the plain one-view-at-a-time loop on the same workload
     plain_ms = plain_loop_steps(eng, cam_dev, targets, max(3, min(args.steps, 10)), 9000, stream, device)
@@ -494,7 +544,8 @@ def run_cuda(args):
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n_gaussians": args.n, "views_per_step": N_VIEWS,
-                       "image": f"{W}x{H}", "nu": NU, "tile": f"{TILE[0]}x{TILE[1]}", "pairs_per_step": need,
+                       "image": f"{W}x{H}", "nu": NU, "tile": f"{eng.tile[0]}x{eng.tile[1]}",
+                       "tile_autotune_ms": {f"{a}x{b}": round(v, 3) for (a, b), v in tile_ms.items()}, "pairs_per_step": need,
                        "parallelism": "replicas" if ws > 1 else "single GPU",
                        "l2": "inputs larger than L2 (236 MB parameters, 199 MB targets per step)",
                        "view_steps_per_s": value * N_VIEWS},
@@ -504,6 +555,9 @@ def run_cuda(args):
             "plain_loop": {"ms_per_step": plain_ms, "value": 1e3 / plain_ms, "unit": UNIT,
                            "batched_speedup": (1e3 / ms_per_step) / (1e3 / plain_ms),
                            "what": "8 single-view project/sort/fwd/bwd call sequences + averaged update, no batching"},
+            "eager": {"ms_per_step": eager_ms / args.steps, "value": 1e3 * args.steps / eager_ms, "unit": UNIT,
+                      "what": "the same steps as six C-ABI calls issued from the host per step, no graph"},
+            "graph": "one captured CUDA graph per view batch, step index and eps_t on the device",
             "gpu_launches": kernel_launches_per_step(eng) * args.steps,
             "roofline": roof, "roofline_calls": roof_calls, "clocks": clocks, "cpu_baseline": cpu,
         }

@@ -96,13 +96,23 @@ typedef struct gs_frame {
 /* Rademacher probes z_k (k < nu) of step t: row r of Gaussian i is entry
  * j = i * rows + r (rows = 11 + 3K), and entry j is -1 where bit (j mod 64) of
  * SplitMix64(seed ^ t * 0x9E3779B97F4A7C15 ^ (k << 56) ^ (j / 64)) is set, +1
- * otherwise: 64 entries per hash. */
+ * otherwise: 64 entries per hash.
+ * t_device (may be NULL): a device int64 read by the kernels in place of t, so
+ * that a captured CUDA graph replays successive steps (see gs_step_advance). */
 typedef struct gs_probe {
   uint64_t seed;
   int64_t t;
   int32_t nu; /* 0, 1 or 2 */
   int32_t reserved;
+  const int64_t* t_device;
 } gs_probe;
+
+/* The radius schedule of Sec. 5: eps_t = eps0 (eps1 / eps0)^((t - 1) / (total - 1))
+ * (eps0 for total <= 1), evaluated in double precision and rounded to float. */
+typedef struct gs_eps_schedule {
+  double eps0, eps1;
+  int64_t total;
+} gs_eps_schedule;
 
 /* Projected splats of V views (device, caller-owned).
  *   rec:     V x n_pad records of 12 floats (48 B):
@@ -241,6 +251,19 @@ gs_status gs_hvp_diag(const gs_params* x, const gs_camera* cams, gs_frame frame,
 gs_status gs_tr_update(gs_params* x, gs_params* g_ema, gs_params* d_ema, const gs_params* grad,
                        const gs_params* hz, const gs_tr_config* cfg, int64_t t, float eps, gs_params* eta_out,
                        int32_t* status, void* stream);
+
+/* gs_tr_update with the step index read on the device from *t_device (>= 1)
+ * and eps = eps_t of `schedule`, so that the call can sit in a captured CUDA
+ * graph.  Whether this step updates d_ema ((t - 1) % l == 0) is decided on the
+ * device; hz must then be given.  A t_device below 1 raises GS_FLAG_NONFINITE
+ * and leaves the buffers unchanged. */
+gs_status gs_tr_update_dev(gs_params* x, gs_params* g_ema, gs_params* d_ema, const gs_params* grad,
+                           const gs_params* hz, const gs_tr_config* cfg, const int64_t* t_device,
+                           const gs_eps_schedule* schedule, gs_params* eta_out, int32_t* status, void* stream);
+
+/* *t_device += 1 on the stream (no paper counterpart: the step counter of a
+ * training loop replayed as a CUDA graph). */
+gs_status gs_step_advance(int64_t* t_device, void* stream);
 
 #ifdef __cplusplus
 }

@@ -48,6 +48,22 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
   z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
   return z ^ (z >> 31);
 }
+// Probe seed and step as the kernels receive them: the step is read from device
+// memory when t_dev is set (a call captured in a CUDA graph), else it is t.
+struct ProbeArg {
+  uint64_t seed;
+  int64_t t;
+  const int64_t* t_dev;
+};
+inline ProbeArg probe_arg(const gs_probe* p) {
+  ProbeArg a;
+  a.seed = p ? p->seed : 0;
+  a.t = p ? p->t : 0;
+  a.t_dev = p ? p->t_device : nullptr;
+  return a;
+}
+__device__ __forceinline__ int64_t probe_step(const ProbeArg& a) { return a.t_dev ? *a.t_dev : a.t; }
+
 // Signs of Rademacher probe k at step t for the rows [0, rows) of Gaussian i:
 // bit r is set where entry j = i * rows + r is -1.  Entry j is bit j mod 64 of
 // the hash of word j / 64 (64 entries per hash), so the rows of one Gaussian

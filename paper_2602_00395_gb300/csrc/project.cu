@@ -40,7 +40,7 @@ __device__ __forceinline__ void store_culled(float4* rec, size_t at) {
 template <int DEG, int NU>
 __global__ void GS_PROJ_BOUNDS project_kernel(const float* __restrict__ P, int n, int n_pad,
                                                       const gs_camera* __restrict__ cams, gs_frame fr,
-                                                      uint64_t seed, int64_t step, float4* __restrict__ rec,
+                                                      ProbeArg pa, float4* __restrict__ rec,
                                                       float4* __restrict__ tan) {
   using S = typename std::conditional<NU == 0, float, Dn<(NU > 0 ? NU : 1)>>::type;
   constexpr int K = (DEG + 1) * (DEG + 1);
@@ -57,6 +57,8 @@ __global__ void GS_PROJ_BOUNDS project_kernel(const float* __restrict__ P, int n
   }
 
   // probe signs: bit r of neg[k] is set where probe k is -1 on row r
+  const uint64_t seed = pa.seed;
+  const int64_t step = NU > 0 ? probe_step(pa) : 0;
   uint64_t neg[NU > 0 ? NU : 1];
 #pragma unroll
   for (int k = 0; k < NU; ++k) neg[k] = probe_signs(seed, step, k, (uint64_t)i, ROWS);
@@ -208,21 +210,21 @@ __global__ void GS_PROJ_BOUNDS project_kernel(const float* __restrict__ P, int n
 }
 
 template <int DEG, int NU>
-void launch_project(const gs_params* x, const gs_camera* cams, gs_frame fr, uint64_t seed, int64_t t,
-                    gs_projected* out, cudaStream_t st) {
+void launch_project(const gs_params* x, const gs_camera* cams, gs_frame fr, ProbeArg pa, gs_projected* out,
+                    cudaStream_t st) {
   const int threads = 128;
   const int blocks = (x->n_pad + threads - 1) / threads;
-  project_kernel<DEG, NU><<<blocks, threads, 0, st>>>(x->data, x->n, x->n_pad, cams, fr, seed, t,
+  project_kernel<DEG, NU><<<blocks, threads, 0, st>>>(x->data, x->n, x->n_pad, cams, fr, pa,
                                                       reinterpret_cast<float4*>(out->rec),
                                                       reinterpret_cast<float4*>(out->tangent));
 }
 
 template <int DEG>
-void dispatch_nu(int nu, const gs_params* x, const gs_camera* cams, gs_frame fr, uint64_t seed, int64_t t,
-                 gs_projected* out, cudaStream_t st) {
-  if (nu == 0) launch_project<DEG, 0>(x, cams, fr, seed, t, out, st);
-  else if (nu == 1) launch_project<DEG, 1>(x, cams, fr, seed, t, out, st);
-  else launch_project<DEG, 2>(x, cams, fr, seed, t, out, st);
+void dispatch_nu(int nu, const gs_params* x, const gs_camera* cams, gs_frame fr, ProbeArg pa, gs_projected* out,
+                 cudaStream_t st) {
+  if (nu == 0) launch_project<DEG, 0>(x, cams, fr, pa, out, st);
+  else if (nu == 1) launch_project<DEG, 1>(x, cams, fr, pa, out, st);
+  else launch_project<DEG, 2>(x, cams, fr, pa, out, st);
 }
 
 }  // namespace
@@ -243,13 +245,12 @@ extern "C" gs_status gs_project(const gs_params* x, const gs_camera* cams, gs_fr
   GS_REQUIRE(nu == 0 || out->tangent, "gs_project: probes given but out->tangent is NULL");
   if (x->n_pad == 0) return GS_OK;
   cudaStream_t st = (cudaStream_t)stream;
-  const uint64_t seed = probe ? probe->seed : 0;
-  const int64_t t = probe ? probe->t : 0;
+  const gs::ProbeArg pa = gs::probe_arg(probe);
   switch (x->sh_degree) {
-    case 0: gs::dispatch_nu<0>(nu, x, cams, frame, seed, t, out, st); break;
-    case 1: gs::dispatch_nu<1>(nu, x, cams, frame, seed, t, out, st); break;
-    case 2: gs::dispatch_nu<2>(nu, x, cams, frame, seed, t, out, st); break;
-    default: gs::dispatch_nu<3>(nu, x, cams, frame, seed, t, out, st); break;
+    case 0: gs::dispatch_nu<0>(nu, x, cams, frame, pa, out, st); break;
+    case 1: gs::dispatch_nu<1>(nu, x, cams, frame, pa, out, st); break;
+    case 2: gs::dispatch_nu<2>(nu, x, cams, frame, pa, out, st); break;
+    default: gs::dispatch_nu<3>(nu, x, cams, frame, pa, out, st); break;
   }
   return gs::check_launch("gs_project");
 }

@@ -73,6 +73,21 @@ constexpr int kPixPerThread = 2;
 #define GS_BATCH_PER_THREAD 1
 #endif
 constexpr int kBatchPerThread = GS_BATCH_PER_THREAD;
+// The forward pass stages nthr / kFwdBatchDiv records per batch (its tangent
+// records triple the shared memory of a batch).
+#ifndef GS_FWD_BATCH_DIV
+#define GS_FWD_BATCH_DIV 1
+#endif
+constexpr int kFwdBatchDiv = GS_FWD_BATCH_DIV;
+// Minimum resident CTAs per SM requested for the forward kernel (0: none).
+#ifndef GS_FWD_MIN_BLOCKS
+#define GS_FWD_MIN_BLOCKS 0
+#endif
+#if GS_FWD_MIN_BLOCKS > 0
+#define GS_FWD_BOUNDS __launch_bounds__(128, GS_FWD_MIN_BLOCKS)
+#else
+#define GS_FWD_BOUNDS __launch_bounds__(128)
+#endif
 
 __device__ __forceinline__ void pixel_of(int tid, int tile_w, int& lx, int& ly) {
   const int warp = tid >> 5, lane = tid & 31, bxn = tile_w >> 3;
@@ -153,14 +168,14 @@ __device__ __forceinline__ void fwd_blend(FwdPixel<NU>& p, const Rec& r, const R
 }
 
 template <int NU>
-__global__ void __launch_bounds__(128) raster_fwd_kernel(const float4* __restrict__ rec, const float4* __restrict__ tan,
+__global__ void GS_FWD_BOUNDS raster_fwd_kernel(const float4* __restrict__ rec, const float4* __restrict__ tan,
                                                          const uint32_t* __restrict__ vals,
                                                          const uint32_t* __restrict__ ranges, int n_pad, gs_frame fr,
                                                          int Tx, int T, float* __restrict__ image,
                                                          float* __restrict__ final_T, uint32_t* __restrict__ n_contrib,
                                                          float* __restrict__ image_tan, int32_t* status) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const int nthr = blockDim.x, nwarps = nthr >> 5, batch = kBatchPerThread * nthr;
+  const int nthr = blockDim.x, nwarps = nthr >> 5, batch = kBatchPerThread * nthr / kFwdBatchDiv;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
   Rec* buf = reinterpret_cast<Rec*>(smem + 16);
   Rec* tbuf = buf + 2 * batch;
@@ -584,14 +599,16 @@ __device__ __forceinline__ void view_direction(const ViewGeom& v, const float mu
 template <int DEG, int NU, bool GRAD>
 __global__ void GS_PBWD_BOUNDS project_bwd_kernel(const float* __restrict__ P, int n, int n_pad,
                                                                    const gs_camera* __restrict__ cams, gs_frame fr,
-                                                                   const float* __restrict__ cot, uint64_t seed,
-                                                                   int64_t step, float* __restrict__ grad,
+                                                                   const float* __restrict__ cot, ProbeArg pa,
+                                                                   float* __restrict__ grad,
                                                                    float* __restrict__ hz) {
   constexpr int S = (GRAD ? 1 : 0) + NU;
   constexpr int NVP = cot_stride(S);
   constexpr int K = (DEG + 1) * (DEG + 1);
   const int i = blockIdx.x * kPbwdThreads + threadIdx.x;
   if (i >= n) return;
+  const uint64_t seed = pa.seed;
+  const int64_t step = NU > 0 ? probe_step(pa) : 0;
   auto ld = [&](int r) { return __ldg(P + (size_t)r * n_pad + i); };
   const float mu[3] = {ld(0), ld(1), ld(2)};
   float qx = ld(6), qy = ld(7), qz = ld(8), qw = ld(9);
@@ -903,11 +920,11 @@ template <int NU>
 gs_status launch_fwd(const gs_projected* proj, const gs_sorted* sorted, int n_pad, gs_frame fr, float* image,
                      float* final_T, uint32_t* n_contrib, float* image_tan, int32_t* status, cudaStream_t st) {
   const TileGrid g = tile_grid(fr);
-  const int nthr = fr.tile_w * fr.tile_h / kPixPerThread, batch = kBatchPerThread * nthr;
+  const int nthr = fr.tile_w * fr.tile_h / kPixPerThread, batch = kBatchPerThread * nthr / kFwdBatchDiv;
   const size_t smem = 16 + (size_t)batch * (2 * sizeof(Rec) * (1 + NU) + sizeof(uint32_t));
   static bool attr = false;
   if (!attr) {
-    if (allow_smem(raster_fwd_kernel<NU>, 16 + (size_t)128 * kBatchPerThread * (2 * sizeof(Rec) * (1 + NU) + sizeof(uint32_t))) != cudaSuccess)
+    if (allow_smem(raster_fwd_kernel<NU>, 16 + (size_t)128 * kBatchPerThread / kFwdBatchDiv * (2 * sizeof(Rec) * (1 + NU) + sizeof(uint32_t))) != cudaSuccess)
       return check_launch("gs_raster_fwd: smem attribute");
     attr = true;
   }
@@ -937,14 +954,13 @@ void launch_bwd_kernels(const gs_params* x, const gs_camera* cams, const gs_proj
       reinterpret_cast<const float4*>(proj->rec), sorted->vals, sorted->ranges, x->n_pad, fr, g.Tx, g.T, image,
       target, final_T, n_contrib, image_tan, loss.kind, loss.gn_floor, inv_m, cot, loss_out, status);
   const dim3 pg((x->n + kPbwdThreads - 1) / kPbwdThreads), pb(kPbwdThreads);
-  const uint64_t seed = probe ? probe->seed : 0;
-  const int64_t t = probe ? probe->t : 0;
+  const ProbeArg pa = probe_arg(probe);
   if (x->n == 0) return;
   switch (x->sh_degree) {
-    case 0: project_bwd_kernel<0, NU, GRAD><<<pg, pb, 0, st>>>(x->data, x->n, x->n_pad, cams, fr, cot, seed, t, grad, hz); break;
-    case 1: project_bwd_kernel<1, NU, GRAD><<<pg, pb, 0, st>>>(x->data, x->n, x->n_pad, cams, fr, cot, seed, t, grad, hz); break;
-    case 2: project_bwd_kernel<2, NU, GRAD><<<pg, pb, 0, st>>>(x->data, x->n, x->n_pad, cams, fr, cot, seed, t, grad, hz); break;
-    default: project_bwd_kernel<3, NU, GRAD><<<pg, pb, 0, st>>>(x->data, x->n, x->n_pad, cams, fr, cot, seed, t, grad, hz); break;
+    case 0: project_bwd_kernel<0, NU, GRAD><<<pg, pb, 0, st>>>(x->data, x->n, x->n_pad, cams, fr, cot, pa, grad, hz); break;
+    case 1: project_bwd_kernel<1, NU, GRAD><<<pg, pb, 0, st>>>(x->data, x->n, x->n_pad, cams, fr, cot, pa, grad, hz); break;
+    case 2: project_bwd_kernel<2, NU, GRAD><<<pg, pb, 0, st>>>(x->data, x->n, x->n_pad, cams, fr, cot, pa, grad, hz); break;
+    default: project_bwd_kernel<3, NU, GRAD><<<pg, pb, 0, st>>>(x->data, x->n, x->n_pad, cams, fr, cot, pa, grad, hz); break;
   }
 }
 

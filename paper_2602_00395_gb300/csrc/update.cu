@@ -104,17 +104,37 @@ __device__ __forceinline__ void radii_of_column(const float* __restrict__ x, int
   }
 }
 
+// eps_t of the schedule, in double precision, rounded to float
+__device__ __forceinline__ float eps_of(const gs_eps_schedule& sc, int64_t t) {
+  if (sc.total <= 1) return (float)sc.eps0;
+  return (float)(sc.eps0 * pow(sc.eps1 / sc.eps0, (double)(t - 1) / (double)(sc.total - 1)));
+}
+
+// HVP: hz is given.  With t_dev the step index is read on the device, eps is
+// eps_t of `sched` and d_ema is updated when (t - 1) % l == 0; otherwise eps is
+// as passed and d_ema is updated whenever HVP.
 template <int DEG, bool HVP, bool ETA>
 __global__ void __launch_bounds__(256) tr_update_kernel(float* __restrict__ x, float* __restrict__ ge,
                                                         float* __restrict__ de, const float* __restrict__ g,
                                                         const float* __restrict__ hz, float* __restrict__ eta_out,
                                                         int n, int n_pad, gs_tr_config cfg, float eps,
+                                                        const int64_t* __restrict__ t_dev, gs_eps_schedule sched,
                                                         int32_t* status) {
   constexpr int K = (DEG + 1) * (DEG + 1);
   constexpr int ROWS = kRowSH + 3 * K;
   constexpr int kLanesPerRow = kUpdCols / 4;  // 64
   __shared__ __align__(16) float s_eta[kEtaRows][kUpdCols];
   const int c0 = blockIdx.x * kUpdCols;
+  bool hvp_now = HVP;
+  if (t_dev) {
+    const int64_t t = *t_dev;
+    if (t < 1) {
+      if (blockIdx.x == 0 && threadIdx.x == 0 && status) atomicOr(status, GS_FLAG_NONFINITE);
+      return;
+    }
+    eps = eps_of(sched, t);
+    hvp_now = HVP && ((t - 1) % cfg.l) == 0;
+  }
   // phase 1: radii of this block's columns, from x_t
   {
     const int i = c0 + (int)threadIdx.x;
@@ -152,7 +172,7 @@ __global__ void __launch_bounds__(256) tr_update_kernel(float* __restrict__ x, f
       const float4 g4 = *reinterpret_cast<const float4*>(g + j);
       const float4 de4 = *reinterpret_cast<const float4*>(de + j);
       float4 hz4 = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (HVP) hz4 = *reinterpret_cast<const float4*>(hz + j);
+      if (HVP && hvp_now) hz4 = *reinterpret_cast<const float4*>(hz + j);
       const float ev[4] = {e4.x * scale, e4.y * scale, e4.z * scale, e4.w * scale};
       const float xv[4] = {x4.x, x4.y, x4.z, x4.w}, gev[4] = {ge4.x, ge4.y, ge4.z, ge4.w};
       const float gv[4] = {g4.x, g4.y, g4.z, g4.w}, hv[4] = {hz4.x, hz4.y, hz4.z, hz4.w};
@@ -162,14 +182,14 @@ __global__ void __launch_bounds__(256) tr_update_kernel(float* __restrict__ x, f
       for (int k = 0; k < 4; ++k) {
         const bool live = ci + k < n;  // padding columns stay as they are
         go[k] = live ? a1 * gev[k] + b1 * gv[k] : gev[k];
-        dn[k] = (HVP && live) ? a2 * dv0[k] + b2 * hv[k] : dv0[k];
+        dn[k] = (hvp_now && live) ? a2 * dv0[k] + b2 * hv[k] : dv0[k];
         const float step = -go[k] / fmaxf(dn[k], cfg.d_floor);
         xo[k] = live ? xv[k] + fminf(fmaxf(step, -ev[k]), ev[k]) : xv[k];
         if (live) bad = bad || !isfinite(xo[k]) || !isfinite(go[k]) || !isfinite(dn[k]);
       }
       *reinterpret_cast<float4*>(x + j) = make_float4(xo[0], xo[1], xo[2], xo[3]);
       *reinterpret_cast<float4*>(ge + j) = make_float4(go[0], go[1], go[2], go[3]);
-      if (HVP) *reinterpret_cast<float4*>(de + j) = make_float4(dn[0], dn[1], dn[2], dn[3]);
+      if (HVP && hvp_now) *reinterpret_cast<float4*>(de + j) = make_float4(dn[0], dn[1], dn[2], dn[3]);
       if (ETA) *reinterpret_cast<float4*>(eta_out + j) = make_float4(ev[0], ev[1], ev[2], ev[3]);
     }
   }
@@ -178,13 +198,14 @@ __global__ void __launch_bounds__(256) tr_update_kernel(float* __restrict__ x, f
 
 template <int DEG>
 void launch_update(bool hvp, bool eta, gs_params* x, gs_params* ge, gs_params* de, const gs_params* g,
-                   const gs_params* hz, gs_params* eta_out, gs_tr_config cfg, float eps, int32_t* status,
-                   cudaStream_t st) {
+                   const gs_params* hz, gs_params* eta_out, gs_tr_config cfg, float eps, const int64_t* t_dev,
+                   gs_eps_schedule sched, int32_t* status, cudaStream_t st) {
   const int blocks = (x->n + kUpdCols - 1) / kUpdCols;
   const float* hp = hz ? hz->data : nullptr;
   float* ep = eta_out ? eta_out->data : nullptr;
-#define GS_UPD(H, E) \
-  tr_update_kernel<DEG, H, E><<<blocks, 256, 0, st>>>(x->data, ge->data, de->data, g->data, hp, ep, x->n, x->n_pad, cfg, eps, status)
+#define GS_UPD(H, E)                                                                                         \
+  tr_update_kernel<DEG, H, E><<<blocks, 256, 0, st>>>(x->data, ge->data, de->data, g->data, hp, ep, x->n, \
+                                                      x->n_pad, cfg, eps, t_dev, sched, status)
   if (hvp) {
     if (eta) GS_UPD(true, true); else GS_UPD(true, false);
   } else {
@@ -196,32 +217,68 @@ void launch_update(bool hvp, bool eta, gs_params* x, gs_params* ge, gs_params* d
 }  // namespace
 }  // namespace gs
 
-extern "C" gs_status gs_tr_update(gs_params* x, gs_params* g_ema, gs_params* d_ema, const gs_params* grad,
-                                  const gs_params* hz, const gs_tr_config* cfg, int64_t t, float eps,
-                                  gs_params* eta_out, int32_t* status, void* stream) {
-  using namespace gs;
-  GS_REQUIRE(x && g_ema && d_ema && grad && cfg, "gs_tr_update: null argument");
-  GS_REQUIRE(x->data && g_ema->data && d_ema->data && grad->data, "gs_tr_update: null device buffer");
-  GS_REQUIRE(t >= 1 && cfg->l >= 1, "gs_tr_update: need t >= 1 and l >= 1");
-  GS_REQUIRE(eps > 0.f, "gs_tr_update: eps must be positive");
+namespace gs {
+namespace {
+__global__ void step_advance_kernel(int64_t* t) { *t += 1; }
+
+gs_status run_update(const char* name, gs_params* x, gs_params* g_ema, gs_params* d_ema, const gs_params* grad,
+                     const gs_params* hz, const gs_tr_config* cfg, bool hvp, float eps, const int64_t* t_dev,
+                     gs_eps_schedule sched, gs_params* eta_out, int32_t* status, void* stream) {
+  GS_REQUIRE(x && g_ema && d_ema && grad && cfg, "%s: null argument", name);
+  GS_REQUIRE(x->data && g_ema->data && d_ema->data && grad->data, "%s: null device buffer", name);
+  GS_REQUIRE(cfg->l >= 1, "%s: need l >= 1", name);
   auto same = [&](const gs_params* p) {
     return !p || (p->n == x->n && p->n_pad == x->n_pad && p->sh_degree == x->sh_degree);
   };
   GS_REQUIRE(same(g_ema) && same(d_ema) && same(grad) && same(hz) && same(eta_out),
-             "gs_tr_update: parameter buffers differ in layout");
+             "%s: parameter buffers differ in layout", name);
+  GS_REQUIRE(x->n_pad % 4 == 0, "%s: n_pad must be a multiple of 4", name);
   if (x->sh_degree < 0 || x->sh_degree > 3) {
-    set_error("gs_tr_update: unsupported sh_degree=%d", x->sh_degree);
+    set_error("%s: unsupported sh_degree=%d", name, x->sh_degree);
     return GS_ERR_UNSUPPORTED;
   }
-  const bool hvp = ((t - 1) % cfg->l) == 0 && hz && hz->data;
   if (x->n == 0) return GS_OK;
   cudaStream_t st = (cudaStream_t)stream;
   const bool eta = eta_out && eta_out->data;
   switch (x->sh_degree) {
-    case 0: launch_update<0>(hvp, eta, x, g_ema, d_ema, grad, hz, eta_out, *cfg, eps, status, st); break;
-    case 1: launch_update<1>(hvp, eta, x, g_ema, d_ema, grad, hz, eta_out, *cfg, eps, status, st); break;
-    case 2: launch_update<2>(hvp, eta, x, g_ema, d_ema, grad, hz, eta_out, *cfg, eps, status, st); break;
-    default: launch_update<3>(hvp, eta, x, g_ema, d_ema, grad, hz, eta_out, *cfg, eps, status, st); break;
+    case 0: launch_update<0>(hvp, eta, x, g_ema, d_ema, grad, hz, eta_out, *cfg, eps, t_dev, sched, status, st); break;
+    case 1: launch_update<1>(hvp, eta, x, g_ema, d_ema, grad, hz, eta_out, *cfg, eps, t_dev, sched, status, st); break;
+    case 2: launch_update<2>(hvp, eta, x, g_ema, d_ema, grad, hz, eta_out, *cfg, eps, t_dev, sched, status, st); break;
+    default: launch_update<3>(hvp, eta, x, g_ema, d_ema, grad, hz, eta_out, *cfg, eps, t_dev, sched, status, st); break;
   }
-  return check_launch("gs_tr_update");
+  return check_launch(name);
+}
+}  // namespace
+}  // namespace gs
+
+extern "C" gs_status gs_tr_update(gs_params* x, gs_params* g_ema, gs_params* d_ema, const gs_params* grad,
+                                  const gs_params* hz, const gs_tr_config* cfg, int64_t t, float eps,
+                                  gs_params* eta_out, int32_t* status, void* stream) {
+  using namespace gs;
+  GS_REQUIRE(cfg, "gs_tr_update: null argument");
+  GS_REQUIRE(t >= 1 && cfg->l >= 1, "gs_tr_update: need t >= 1 and l >= 1");
+  GS_REQUIRE(eps > 0.f, "gs_tr_update: eps must be positive");
+  const bool hvp = ((t - 1) % cfg->l) == 0 && hz && hz->data;
+  const gs_eps_schedule none{0.0, 0.0, 0};
+  return run_update("gs_tr_update", x, g_ema, d_ema, grad, hz, cfg, hvp, eps, nullptr, none, eta_out, status,
+                    stream);
+}
+
+extern "C" gs_status gs_tr_update_dev(gs_params* x, gs_params* g_ema, gs_params* d_ema, const gs_params* grad,
+                                      const gs_params* hz, const gs_tr_config* cfg, const int64_t* t_device,
+                                      const gs_eps_schedule* schedule, gs_params* eta_out, int32_t* status,
+                                      void* stream) {
+  using namespace gs;
+  GS_REQUIRE(cfg && t_device && schedule, "gs_tr_update_dev: null argument");
+  GS_REQUIRE(schedule->eps0 > 0.0 && schedule->eps1 > 0.0, "gs_tr_update_dev: eps0 and eps1 must be positive");
+  const bool hvp = hz && hz->data;
+  return run_update("gs_tr_update_dev", x, g_ema, d_ema, grad, hz, cfg, hvp, 0.f, t_device, *schedule, eta_out,
+                    status, stream);
+}
+
+extern "C" gs_status gs_step_advance(int64_t* t_device, void* stream) {
+  using namespace gs;
+  GS_REQUIRE(t_device, "gs_step_advance: null argument");
+  step_advance_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(t_device);
+  return check_launch("gs_step_advance");
 }

@@ -85,6 +85,7 @@ class TRStep:
                                   device=self.device)
         self._alloc_pairs(capacity or max(1 << 16, 8 * n * n_views))
         self.t = 0
+        self.t_dev = torch.zeros(1, dtype=torch.int64, device=self.device)  # step index of captured graphs
 
     # ------------------------------------------------------------ buffers
     def _alloc_pairs(self, capacity: int) -> None:
@@ -117,8 +118,10 @@ class TRStep:
         return G.gs_sorted(self.keys.data_ptr(), self.vals.data_ptr(), self.ranges.data_ptr(),
                            self.n_pairs.data_ptr(), self.capacity)
 
-    def probe(self, t: int) -> G.gs_probe | None:
-        return G.probe_struct(self.probe_seed, t, self.nu) if self.nu > 0 else None
+    def probe(self, t: int | None, device_t: bool = False) -> G.gs_probe | None:
+        if self.nu == 0:
+            return None
+        return G.probe_struct(self.probe_seed, t or 0, self.nu, self.t_dev if device_t else None)
 
     # ------------------------------------------------------------ calls
     def project(self, t: int | None = None, probes: bool = True, stream=None) -> None:
@@ -157,6 +160,38 @@ class TRStep:
         self.bin_sort(stream)
         self.raster_fwd(None, probes=False, stream=stream)
 
+    def step_device(self, hvp: bool, schedule: G.gs_eps_schedule, stream=None) -> None:
+        """One step of Algorithm 1 whose index lives in device memory (self.t_dev):
+        advance it, then the six calls reading it there, so that the sequence can
+        be captured once as a CUDA graph and replayed for successive steps.
+        `hvp` fixes whether the captured step carries the probes (every step for
+        l = 1; capture one graph of each kind for l > 1)."""
+        G.gs_step_advance(self.t_dev, stream)
+        self.loss_val.zero_()
+        pr = self.probe(None, device_t=True) if hvp else None
+        G.gs_project(self.P(self.x), self.cams, self.frame, pr, self.proj(), self.status, stream)
+        self.bin_sort(stream)
+        G.gs_raster_fwd(self.proj(), self.sorted(), self.n_pad, self.frame, pr, self.image, self.final_T,
+                        self.n_contrib, self.image_tan if pr else None, self.status, stream)
+        G.gs_raster_bwd(self.P(self.x), self.cams, self.frame, self.proj(), self.sorted(), self.image, self.target,
+                        self.final_T, self.n_contrib, self.image_tan if pr else None, pr, self.loss,
+                        self.P(self.grad), self.P(self.hz) if pr else None, self.loss_val, self.bwd_ws,
+                        self.status, stream)
+        G.gs_tr_update_dev(self.P(self.x), self.P(self.g_ema), self.P(self.d_ema), self.P(self.grad),
+                           self.P(self.hz) if pr else None, self.cfg.struct(), self.t_dev, schedule, None,
+                           self.status, stream)
+
+    def capture_step(self, hvp: bool, schedule: G.gs_eps_schedule, stream=None):
+        """A CUDA graph of step_device; each replay advances self.t_dev by one.
+        Capturing runs nothing.  Make one eager step first (it sets the kernels'
+        shared-memory attributes, which capture cannot record)."""
+        s = stream or torch.cuda.Stream(device=self.device)
+        g = torch.cuda.CUDAGraph()
+        torch.cuda.synchronize(self.device)
+        with torch.cuda.graph(g, stream=s):
+            self.step_device(hvp, schedule, s)
+        return g
+
     def step(self, t: int, eps: float, stream=None) -> None:
         """One iteration of Algorithm 1 on the frame's views (S1 = S2)."""
         hvp = self.nu > 0 and ((t - 1) % self.cfg.l) == 0
@@ -180,3 +215,35 @@ class TRStep:
 
     def read_status(self) -> int:
         return int(self.status.item())
+
+
+def autotune_tile(eng: TRStep, candidates=((16, 16), (32, 8), (8, 32), (16, 8)), steps: int = 3,
+                  stream=None) -> tuple[tuple[int, int], dict]:
+    """Pick the tile shape with the shortest step on the caller's own workload:
+    for each candidate a TRStep with the same parameters, cameras, targets and
+    probes runs one untimed and `steps` timed steps (CUDA events), starting from
+    copies of eng's state so that eng is left unchanged.  Returns the best shape
+    and the ms per step of every candidate."""
+    s = stream or torch.cuda.Stream(device=eng.device)
+    times = {}
+    for tile in candidates:
+        e = TRStep(eng.n, eng.deg, eng.V, eng.W, eng.H, nu=eng.nu, tile=tile, cfg=eng.cfg,
+                   probe_seed=eng.probe_seed, device=str(eng.device))
+        for dst, src in ((e.x, eng.x), (e.g_ema, eng.g_ema), (e.d_ema, eng.d_ema), (e.cams, eng.cams),
+                         (e.target, eng.target)):
+            dst.copy_(src)
+        e.ensure_capacity()
+        start = torch.cuda.Event(enable_timing=True)
+        stop = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(s):
+            e.step(1, 1e-6, s)
+            start.record(s)
+            for t in range(2, 2 + steps):
+                e.step(t, 1e-6, s)
+            stop.record(s)
+        stop.synchronize()
+        times[tile] = start.elapsed_time(stop) / steps
+        del e
+        torch.cuda.empty_cache()
+    best = min(times, key=times.get)
+    return best, times

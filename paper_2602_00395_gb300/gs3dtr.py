@@ -23,7 +23,8 @@ GS_LOSS_L1, GS_LOSS_L2 = 0, 1
 
 EXPORTED = ("gs_last_error", "gs_version", "gs_project", "gs_bin_sort_workspace_size", "gs_bin_sort",
             "gs_bin_sort_noalloc",
-            "gs_raster_fwd", "gs_raster_bwd_workspace_size", "gs_raster_bwd", "gs_hvp_diag", "gs_tr_update")
+            "gs_raster_fwd", "gs_raster_bwd_workspace_size", "gs_raster_bwd", "gs_hvp_diag", "gs_tr_update",
+            "gs_tr_update_dev", "gs_step_advance")
 
 
 class gs_params(C.Structure):
@@ -43,7 +44,12 @@ class gs_frame(C.Structure):
 
 
 class gs_probe(C.Structure):
-    _fields_ = [("seed", C.c_uint64), ("t", C.c_int64), ("nu", C.c_int32), ("reserved", C.c_int32)]
+    _fields_ = [("seed", C.c_uint64), ("t", C.c_int64), ("nu", C.c_int32), ("reserved", C.c_int32),
+                ("t_device", C.c_void_p)]
+
+
+class gs_eps_schedule(C.Structure):
+    _fields_ = [("eps0", C.c_double), ("eps1", C.c_double), ("total", C.c_int64)]
 
 
 class gs_projected(C.Structure):
@@ -116,6 +122,12 @@ def load():
         L.gs_tr_update.argtypes = [C.POINTER(gs_params), C.POINTER(gs_params), C.POINTER(gs_params),
                                    C.POINTER(gs_params), C.POINTER(gs_params), C.POINTER(gs_tr_config), C.c_int64,
                                    C.c_float, C.POINTER(gs_params), P, P]
+        L.gs_tr_update_dev.restype = st
+        L.gs_tr_update_dev.argtypes = [C.POINTER(gs_params), C.POINTER(gs_params), C.POINTER(gs_params),
+                                       C.POINTER(gs_params), C.POINTER(gs_params), C.POINTER(gs_tr_config), P,
+                                       C.POINTER(gs_eps_schedule), C.POINTER(gs_params), P, P]
+        L.gs_step_advance.restype = st
+        L.gs_step_advance.argtypes = [P, P]
         _lib = L
         return L
 
@@ -160,8 +172,10 @@ def frame_struct(n_views: int, width: int, height: int, tile_w: int = 16, tile_h
     return gs_frame(n_views, width, height, tile_w, tile_h)
 
 
-def probe_struct(seed: int, t: int, nu: int) -> gs_probe:
-    return gs_probe(seed, t, nu, 0)
+def probe_struct(seed: int, t: int, nu: int, t_device=None) -> gs_probe:
+    """Probe descriptor; t_device (a device int64 tensor) makes the kernels read
+    the step index from device memory (for calls captured in a CUDA graph)."""
+    return gs_probe(seed, t, nu, 0, ptr(t_device) if t_device is not None else None)
 
 
 # ------------------------------------------------------------ the six calls
@@ -231,3 +245,18 @@ def gs_tr_update(x: gs_params, g_ema: gs_params, d_ema: gs_params, grad: gs_para
     check(L.gs_tr_update(C.byref(x), C.byref(g_ema), C.byref(d_ema), C.byref(grad), C.byref(hz) if hz else None,
                          C.byref(cfg), t, eps, C.byref(eta_out) if eta_out else None, ptr(status),
                          stream_handle(stream)), "gs_tr_update")
+
+
+def gs_tr_update_dev(x: gs_params, g_ema: gs_params, d_ema: gs_params, grad: gs_params, hz: gs_params | None,
+                     cfg: gs_tr_config, t_device, schedule: gs_eps_schedule, eta_out: gs_params | None = None,
+                     status=None, stream=None) -> None:
+    L = load()
+    check(L.gs_tr_update_dev(C.byref(x), C.byref(g_ema), C.byref(d_ema), C.byref(grad),
+                             C.byref(hz) if hz else None, C.byref(cfg), ptr(t_device), C.byref(schedule),
+                             C.byref(eta_out) if eta_out else None, ptr(status), stream_handle(stream)),
+          "gs_tr_update_dev")
+
+
+def gs_step_advance(t_device, stream=None) -> None:
+    L = load()
+    check(L.gs_step_advance(ptr(t_device), stream_handle(stream)), "gs_step_advance")

@@ -35,14 +35,28 @@ def test_every_declared_symbol_is_exported(lib):
     assert set(gs3dtr.EXPORTED) == set(names)
 
 
-def test_struct_sizes_match_header_layout():
+STRUCTS = ["gs_params", "gs_camera", "gs_frame", "gs_probe", "gs_eps_schedule", "gs_projected", "gs_sorted",
+           "gs_loss", "gs_tr_config"]
+
+
+def test_struct_sizes_match_header_layout(tmp_path):
+    """The ctypes structs have the sizes a C compiler gives the header's structs."""
+    import shutil
+    import subprocess
     from paper_2602_00395_gb300 import gs3dtr as G
-    assert C.sizeof(G.gs_params) == 24
-    assert C.sizeof(G.gs_camera) == 96
-    assert C.sizeof(G.gs_frame) == 20
-    assert C.sizeof(G.gs_probe) == 24
-    assert C.sizeof(G.gs_sorted) == 40
-    assert C.sizeof(G.gs_tr_config) == 24
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "sizes.c"
+    body = "\n".join(f'  printf("{n} %zu\\n", sizeof({n}));' for n in STRUCTS)
+    src.write_text(f'#include <stdio.h>\n#include "gs3dtr.h"\nint main(void) {{\n{body}\n  return 0;\n}}\n')
+    exe = tmp_path / "sizes"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()
+    got = dict(zip(out[0::2], map(int, out[1::2])))
+    for n in STRUCTS:
+        assert C.sizeof(getattr(G, n)) == got[n], n
+    assert got["gs_probe"] == 32 and got["gs_camera"] == 96
 
 
 def test_host_argument_checks_reject_without_touching_the_device(lib):
@@ -62,3 +76,8 @@ def test_host_argument_checks_reject_without_touching_the_device(lib):
     rc = lib.gs_tr_update(C.byref(x), C.byref(x), C.byref(x), C.byref(x), None, C.byref(cfg), 1, 1e-6, None,
                           None, None)
     assert rc == G.GS_ERR_INVALID_ARG  # l = 0
+    sched = G.gs_eps_schedule(1e-6, 1e-8, 100)
+    rc = lib.gs_tr_update_dev(C.byref(x), C.byref(x), C.byref(x), C.byref(x), None, C.byref(cfg), None,
+                              C.byref(sched), None, None, None)
+    assert rc == G.GS_ERR_INVALID_ARG  # no device step counter
+    assert lib.gs_step_advance(None, None) == G.GS_ERR_INVALID_ARG
