@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--impl", default="cuda", choices=["cuda", "reference"])
     ap.add_argument("--n", type=int, default=N_GAUSS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serve", action="store_true", help="skip the served multi-scene measurement")
     ap.add_argument("--profile-steps", type=int, default=0, help="run N untimed steps only (for ncu)")
     ap.add_argument("--profile-views", type=int, default=N_VIEWS,
                     help="views per step in a --profile-steps run (a smaller case for ncu captures)")
@@ -339,6 +340,50 @@ def e2e_steps(eng, batches, host_targets, K, t0, stream, schedule):
     return start.elapsed_time(stop), wall, h2d, 4
 
 
+# ------------------------------------------------------------------ serving
+def served_metrics(device, n_requests=200, slots=16, budget_gb=40.0):
+    """The served multi-scene workload: 16 resident scenes (50k-2M Gaussians, SH 3,
+    image sizes from 256x256 to 1920x1080, 8 views each), a seeded Poisson stream
+    of 70 % training steps and 30 % renders.  The plain loop's capacity is measured
+    on back-to-back requests; the stream is then replayed at 0.5, 0.8, 1.0 and
+    1.2 x that rate through the plain loop and through the server (continuous
+    batching on `slots` streams, in-flight working sets within `budget_gb`)."""
+    import torch
+    from paper_2602_00395_gb300 import serve as SV
+    from paper_2602_00395_gb300 import synth as S
+    scenes = SV.make_scenes(16, device=device)
+    nv = 8
+    budget = int(budget_gb * 1e9)
+    # warm-up: every scene once per request kind (allocator, kernel attributes)
+    SV.plain_loop(scenes, [(0.0, k, s, 0) for s in range(len(scenes)) for k in ("train", "render")])
+    # saturation: every request waiting at time 0
+    burst = [(0.0, k, s, v) for (_, k, s, v) in S.request_stream(n_requests, 1.0, len(scenes), nv, seed=98)]
+    sat_plain = SV.plain_loop(scenes, burst).summary()
+    sat_served = SV.Server(scenes, slots=slots, budget_bytes=budget).run(burst).summary()
+    capacity = sat_plain["requests_per_s"]
+    sweep = []
+    for f in (0.5, 0.8, 1.0, 1.2):
+        spec = S.request_stream(n_requests, f * capacity, len(scenes), nv, seed=99)
+        p = SV.plain_loop(scenes, spec).summary()
+        q = SV.Server(scenes, slots=slots, budget_bytes=budget).run(spec).summary()
+        keep = ("p50_ms", "p99_ms", "train_steps_per_s", "requests_per_s", "status_words")
+        sweep.append({"rate_x_plain_capacity": f, "rate_per_s": round(f * capacity, 2),
+                      "plain": {k: p[k] for k in keep}, "served": {k: q[k] for k in keep},
+                      "served_peak_inflight_GB": q["peak_inflight_GB"]})
+    info = {"scenes": [{"n": sc.n, "image": f"{sc.W}x{sc.H}"} for sc in scenes], "slots": slots,
+            "budget_GB": budget_gb, "requests_per_run": n_requests,
+            "plain_capacity_requests_per_s": capacity,
+            "saturated": {"plain_train_steps_per_s": sat_plain["train_steps_per_s"],
+                          "served_train_steps_per_s": sat_served["train_steps_per_s"],
+                          "served_speedup": sat_served["train_steps_per_s"] / sat_plain["train_steps_per_s"],
+                          "plain_p50_ms": sat_plain["p50_ms"], "plain_p99_ms": sat_plain["p99_ms"],
+                          "served_p50_ms": sat_served["p50_ms"], "served_p99_ms": sat_served["p99_ms"]},
+            "sweep": sweep}
+    del scenes
+    torch.cuda.empty_cache()
+    return info
+
+
 # ------------------------------------------------------------------ roofline
 # Algorithmic FP32 work per contributing (pixel, splat) unit, the unit being
 # sum over pixels of n_contrib (list position of the last blended splat): the
@@ -560,7 +605,12 @@ def run_cuda(args):
             "graph": "one captured CUDA graph per view batch, step index and eps_t on the device",
             "gpu_launches": kernel_launches_per_step(eng) * args.steps,
             "roofline": roof, "roofline_calls": roof_calls, "clocks": clocks, "cpu_baseline": cpu,
+            "served": None,
         }
+        if not args.no_serve:
+            del eng, cam_dev, targets, graphs
+            torch.cuda.empty_cache()
+            out["served"] = served_metrics(device)
         print(json.dumps(out))
     if ws > 1:
         import torch.distributed as dist

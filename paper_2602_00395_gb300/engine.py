@@ -48,7 +48,13 @@ class TRStep:
     def __init__(self, n: int, sh_degree: int, n_views: int, width: int, height: int, *, nu: int = 1,
                  tile=(16, 16), capacity: int | None = None, loss_kind: int = G.GS_LOSS_L1,
                  gn_floor: float = 1e-3, cfg: TRConfig | None = None, probe_seed: int = 42,
-                 device: str = "cuda"):
+                 device: str = "cuda", state=None, zero_init: bool = True):
+        """state: optional (x, g_ema, d_ema) tensors of shape rows x n_pad that the
+        step uses in place of its own (a scene's resident parameters and trust-region
+        state, shared by the short-lived steps of a serving loop).  zero_init=False
+        leaves the buffers that the calls overwrite before reading (records,
+        images, gradient, curvature, target, cameras) uninitialised, which saves a
+        fill per buffer when steps are created per request."""
         G.load()
         self.n, self.deg, self.V, self.W, self.H, self.nu = n, sh_degree, n_views, width, height, nu
         self.n_pad = synth.pad_count(n)
@@ -63,20 +69,26 @@ class TRStep:
         self.Ty = -(-height // tile[1])
         f32 = dict(dtype=torch.float32, device=self.device)
         z = lambda *s: torch.zeros(*s, **f32)
-        self.x = z(self.rows, self.n_pad)
-        self.g_ema = z(self.rows, self.n_pad)
-        self.d_ema = z(self.rows, self.n_pad)
-        self.grad = z(self.rows, self.n_pad)
-        self.hz = z(self.rows, self.n_pad)
-        self.cams = torch.zeros(96 * n_views, dtype=torch.uint8, device=self.device)
-        self.rec = z(n_views * self.n_pad * 12)
-        self.tan = z(max(nu, 1) * n_views * self.n_pad * 12)
+        w = z if zero_init else (lambda *s: torch.empty(*s, **f32))  # buffers written before read
+        if state is not None:
+            self.x, self.g_ema, self.d_ema = state
+            assert all(t.shape == (self.rows, self.n_pad) and t.dtype == torch.float32 for t in state)
+        else:
+            self.x = z(self.rows, self.n_pad)
+            self.g_ema = z(self.rows, self.n_pad)
+            self.d_ema = z(self.rows, self.n_pad)
+        self.grad = w(self.rows, self.n_pad)
+        self.hz = w(self.rows, self.n_pad)
+        self.cams = (torch.zeros if zero_init else torch.empty)(96 * n_views, dtype=torch.uint8, device=self.device)
+        self.rec = w(n_views * self.n_pad * 12)
+        self.tan = w(max(nu, 1) * n_views * self.n_pad * 12)
         HW = width * height
-        self.image = z(n_views * 3 * HW)
-        self.final_T = z(n_views * HW)
-        self.n_contrib = torch.zeros(n_views * HW, dtype=torch.int32, device=self.device)
-        self.image_tan = z(max(nu, 1) * n_views * 3 * HW)
-        self.target = z(n_views * 3 * HW)
+        self.image = w(n_views * 3 * HW)
+        self.final_T = w(n_views * HW)
+        self.n_contrib = (torch.zeros if zero_init else torch.empty)(n_views * HW, dtype=torch.int32,
+                                                                    device=self.device)
+        self.image_tan = w(max(nu, 1) * n_views * 3 * HW)
+        self.target = w(n_views * 3 * HW)
         self.status = torch.zeros(1, dtype=torch.int32, device=self.device)
         self.loss_val = z(1)
         self.ranges = torch.zeros(2 * n_views * self.Tx * self.Ty, dtype=torch.int32, device=self.device)

@@ -1,0 +1,264 @@
+"""Serving loop: many resident scenes, training-step and render requests,
+continuous batching on the GPU.
+
+* A Scene keeps its parameters and trust-region state (x, g_ema, d_ema), its
+  cameras and its target images resident in HBM, and a host step counter.
+* A request is one training step of Algorithm 1 on one view of a scene
+  (projection, binning, forward, reverse pass with the Hutchinson probes,
+  update) or one render (projection, binning, forward).  Its working buffers
+  (records, pairs, images, cotangents, gradient, curvature) are allocated for
+  the request from PyTorch's caching allocator on the request's stream and
+  released when it completes.
+* Admission: a request that has arrived is started when a slot (a CUDA stream)
+  is free, its scene has no request in flight (a training step changes the
+  scene), and its working set fits the HBM budget left by the requests in
+  flight.  Requests are taken in arrival order; one that cannot start does not
+  hold back later ones for other scenes.
+* Continuous batching: every started request runs on its own stream, so the
+  kernels of requests of different scenes overlap on the device; a request that
+  arrives while others run starts as soon as a slot and memory free up.
+* Latency of a request = completion (its end event observed by the host) minus
+  arrival, both on the host clock.
+
+The plain loop serves the same stream one request at a time on one stream.
+"""
+from __future__ import annotations
+
+import math
+import time
+from collections import deque
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+from . import gs3dtr as G
+from . import synth
+from .engine import TRConfig, TRStep, eps_schedule
+
+
+@dataclass
+class Request:
+    rid: int
+    arrival: float
+    kind: str  # "train" or "render"
+    scene: int
+    view: int
+    start: float = math.nan
+    done: float = math.nan
+    nbytes: int = 0
+    image: object = None  # rendered image (device tensor), when results are kept
+    rejected: bool = False  # working set larger than the whole budget
+
+    @property
+    def latency(self) -> float:
+        return self.done - self.arrival
+
+
+class Scene:
+    """A resident scene: parameters and trust-region state, cameras and targets."""
+
+    def __init__(self, sid: int, n: int, width: int, height: int, *, n_views: int = 8, nu: int = 1,
+                 tile=(16, 16), total_steps: int = 30000, device: str = "cuda"):
+        self.sid, self.n, self.W, self.H, self.nu, self.tile = sid, n, width, height, nu, tile
+        self.deg, self.total_steps, self.device = 3, total_steps, torch.device(device)
+        self.cfg = TRConfig(l=1)
+        self.t = 0
+        # the served-workload recipe: uniform cube of radius 5, log-scales shifted
+        # by (1/3) ln(1e5 / N) so that the pairs per Gaussian stay comparable
+        shift = math.log(5.0) + math.log(1e5 / n) / 3.0
+        sc = synth.make_scene(n, self.deg, seed=1000 + sid, kind="cube", extent=5.0, log_scale_shift=shift)
+        gt = synth.make_scene(n, self.deg, seed=2000 + sid, kind="cube", extent=5.0, log_scale_shift=shift)
+        cams = synth.camera_ring(64, width, height, 5.0, seed=7 + sid)[:: 64 // n_views][:n_views]
+        self.cams = torch.from_numpy(G.camera_bytes(cams)).to(self.device)
+        # targets rendered from the ground-truth set, one view at a time
+        eng = TRStep(n, self.deg, 1, width, height, nu=nu, tile=tile, cfg=self.cfg, device=device)
+        eng.set_params(gt.params)
+        self.targets = []
+        self.need = 0
+        for v in range(n_views):
+            eng.cams = self.cams[96 * v: 96 * (v + 1)]
+            self.need = max(self.need, eng.ensure_capacity())
+            eng.render()
+            self.targets.append(eng.image.clone())
+        eng.set_params(sc.params)
+        for v in range(n_views):
+            eng.cams = self.cams[96 * v: 96 * (v + 1)]
+            self.need = max(self.need, eng.ensure_capacity())
+        self.capacity = int(self.need * 1.25) + 1024
+        self.x, self.g_ema, self.d_ema = eng.x, eng.g_ema, eng.d_ema
+        del eng
+        torch.cuda.synchronize(self.device)
+
+    @property
+    def resident_bytes(self) -> int:
+        return sum(t.numel() * t.element_size() for t in (self.x, self.g_ema, self.d_ema, self.cams, *self.targets))
+
+    def working_bytes(self, kind: str) -> int:
+        """Device bytes of one request's working buffers (as TRStep allocates them)."""
+        n_pad, rows, HW = synth.pad_count(self.n), synth.n_rows(self.deg), self.W * self.H
+        frame = G.frame_struct(1, self.W, self.H, *self.tile)
+        b = n_pad * 12 * 4 * (1 + max(self.nu, 1))                       # records + tangents
+        b += HW * 4 * (3 + 1 + 1 + 3 * max(self.nu, 1) + 3)              # image, T, n_contrib, tangents, target slot
+        b += self.capacity * 12 + G.gs_bin_sort_workspace_size(n_pad, frame, self.capacity)
+        b += G.gs_raster_bwd_workspace_size(n_pad, frame, self.nu) + 2 * rows * n_pad * 4  # cotangents, grad, hz
+        return int(b)
+
+    def make_step(self) -> TRStep:
+        """Working buffers for one request, on the current stream, sharing the resident state."""
+        return TRStep(self.n, self.deg, 1, self.W, self.H, nu=self.nu, tile=self.tile, capacity=self.capacity,
+                      cfg=self.cfg, device=str(self.device), state=(self.x, self.g_ema, self.d_ema),
+                      zero_init=False)
+
+    def enqueue(self, req: Request, stream) -> TRStep:
+        """Issue the request's calls on `stream`; returns the step that owns its buffers."""
+        with torch.cuda.stream(stream):
+            e = self.make_step()
+            e.cams = self.cams[96 * req.view: 96 * (req.view + 1)]
+            e.target = self.targets[req.view]
+            if req.kind == "train":
+                self.t += 1
+                e.step(self.t, eps_schedule(self.t, self.total_steps), stream)
+            else:
+                e.render(stream)
+        return e
+
+
+@dataclass
+class ServeResult:
+    requests: list
+    wall_s: float
+    mode: str
+    slots: int = 1
+    budget_bytes: int = 0
+    peak_inflight_bytes: int = 0
+    statuses: list = field(default_factory=list)
+
+    def summary(self) -> dict:
+        served = [r for r in self.requests if not r.rejected]
+        lat = np.array([r.latency for r in served]) * 1e3
+        n_train = sum(r.kind == "train" for r in served)
+        return {"mode": self.mode, "requests": len(served), "rejected": len(self.requests) - len(served),
+                "train_steps": n_train,
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "mean_ms": float(lat.mean()), "wall_s": self.wall_s,
+                "train_steps_per_s": n_train / self.wall_s, "requests_per_s": len(self.requests) / self.wall_s,
+                "slots": self.slots, "budget_GB": self.budget_bytes / 1e9,
+                "peak_inflight_GB": self.peak_inflight_bytes / 1e9,
+                "status_words": sorted(set(self.statuses))}
+
+
+def _requests(stream_spec) -> list[Request]:
+    return [Request(i, a, k, s, v) for i, (a, k, s, v) in enumerate(stream_spec)]
+
+
+def plain_loop(scenes: list[Scene], stream_spec, stream=None, keep_results: bool = False) -> ServeResult:
+    """One request at a time, in arrival order, on one stream (each waits for the
+    previous to finish and for its own arrival)."""
+    s = stream or torch.cuda.Stream()
+    reqs = _requests(stream_spec)
+    statuses = []
+    t0 = time.perf_counter()
+    for r in reqs:
+        while time.perf_counter() - t0 < r.arrival:
+            pass
+        r.start = time.perf_counter() - t0
+        e = scenes[r.scene].enqueue(r, s)
+        s.synchronize()
+        r.done = time.perf_counter() - t0
+        statuses.append(e.read_status())
+        if keep_results and r.kind == "render":
+            r.image = e.image
+        del e
+    return ServeResult(reqs, time.perf_counter() - t0, "plain", statuses=statuses)
+
+
+class Server:
+    """Continuous batching of requests over resident scenes (see the module text)."""
+
+    def __init__(self, scenes: list[Scene], slots: int = 4, budget_bytes: int | None = None):
+        self.scenes = scenes
+        self.streams = [torch.cuda.Stream() for _ in range(slots)]
+        self.budget = budget_bytes if budget_bytes is not None else 1 << 62
+        # each slot's status word lands here by an asynchronous copy on the slot's
+        # stream, so that reading it never synchronises with requests in flight
+        self.status_host = torch.zeros(slots, dtype=torch.int32).pin_memory()
+
+    def run(self, stream_spec, keep_results: bool = False) -> ServeResult:
+        reqs = _requests(stream_spec)
+        waiting = deque()
+        upcoming = deque(reqs)
+        free = list(range(len(self.streams)))
+        inflight = {}  # slot -> (request, step, end event)
+        busy = set()
+        used = peak = 0
+        statuses = []
+        t0 = time.perf_counter()
+        while upcoming or waiting or inflight:
+            now = time.perf_counter() - t0
+            # completions
+            for slot in list(inflight):
+                r, e, ev = inflight[slot]
+                if ev.query():
+                    r.done = time.perf_counter() - t0
+                    statuses.append(int(self.status_host[slot]))
+                    if keep_results and r.kind == "render":
+                        r.image = e.image
+                    busy.discard(r.scene)
+                    used -= r.nbytes
+                    free.append(slot)
+                    del inflight[slot]
+            while upcoming and upcoming[0].arrival <= now:
+                waiting.append(upcoming.popleft())
+            # admissions, in arrival order
+            started = False
+            for r in list(waiting):
+                if not free:
+                    break
+                sc = self.scenes[r.scene]
+                nb = sc.working_bytes(r.kind)
+                if nb > self.budget:  # can never fit: rejected at once
+                    r.rejected = True
+                    r.start = r.done = time.perf_counter() - t0
+                    waiting.remove(r)
+                    continue
+                if r.scene in busy or used + nb > self.budget:
+                    continue
+                slot = free.pop()
+                st = self.streams[slot]
+                r.nbytes = nb
+                r.start = time.perf_counter() - t0
+                e = sc.enqueue(r, st)
+                with torch.cuda.stream(st):
+                    self.status_host[slot: slot + 1].copy_(e.status, non_blocking=True)
+                ev = torch.cuda.Event()
+                ev.record(st)
+                inflight[slot] = (r, e, ev)
+                busy.add(r.scene)
+                used += nb
+                peak = max(peak, used)
+                waiting.remove(r)
+                started = True
+            if not started and not inflight and waiting and not free:
+                raise RuntimeError("no slot can ever be freed")  # unreachable: inflight empty means free slots
+            if not started:
+                time.sleep(2e-5)
+        res = ServeResult(reqs, time.perf_counter() - t0, "served", len(self.streams), min(self.budget, 1 << 62),
+                          peak, statuses)
+        return res
+
+
+def make_scenes(n_scenes: int = 16, *, device: str = "cuda", budget_bytes: int | None = None, seed: int = 5000,
+                n_views: int = 8, n_max: int = 2_000_000) -> list[Scene]:
+    """The served workload's resident scenes; scenes are admitted in order while
+    their resident bytes fit `budget_bytes` (the rest are not loaded)."""
+    scenes = []
+    used = 0
+    for sid, (n, W, H) in enumerate(synth.served_scene_specs(n_scenes, seed=seed, n_max=n_max)):
+        sc = Scene(sid, n, W, H, n_views=n_views, device=device)
+        if budget_bytes is not None and used + sc.resident_bytes > budget_bytes:
+            del sc
+            break
+        used += sc.resident_bytes
+        scenes.append(sc)
+    return scenes

@@ -198,3 +198,30 @@ def projected_records(n: int, width: int, height: int, *, seed: int = 11,
     if n > 1 and dup.any():
         depth[dup] = depth[rng.integers(0, n, size=int(dup.sum()))]
     return mx, my, r, depth
+
+
+# --------------------------------------------------------------- serving
+SERVED_SIZES = ((256, 256), (800, 600), (1297, 840), (1920, 1080))
+
+
+def served_scene_specs(n_scenes: int = 16, *, seed: int = 5000, n_min: int = 50_000,
+                       n_max: int = 2_000_000) -> list[tuple[int, int, int]]:
+    """(Gaussians, width, height) of each resident scene of the served workload:
+    counts log-uniform in [n_min, n_max], image size uniform over SERVED_SIZES."""
+    rng = np.random.default_rng(seed)
+    ns = np.exp(rng.uniform(np.log(n_min), np.log(n_max), n_scenes)).astype(np.int64)
+    sizes = rng.integers(0, len(SERVED_SIZES), n_scenes)
+    return [(int(n), *SERVED_SIZES[s]) for n, s in zip(ns, sizes)]
+
+
+def request_stream(n_requests: int, rate: float, n_scenes: int, n_views: int, *, seed: int = 99,
+                   train_fraction: float = 0.7) -> list[tuple[float, str, int, int]]:
+    """Seeded Poisson arrivals at `rate` per second: (arrival time s, kind
+    'train' or 'render', scene, view), scenes and views uniform."""
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(1.0 / rate, n_requests)
+    kinds = np.where(rng.uniform(size=n_requests) < train_fraction, "train", "render")
+    scenes = rng.integers(0, n_scenes, n_requests)
+    views = rng.integers(0, n_views, n_requests)
+    t = np.cumsum(gaps)
+    return [(float(a), str(k), int(s), int(v)) for a, k, s, v in zip(t, kinds, scenes, views)]
