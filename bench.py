@@ -340,6 +340,53 @@ def e2e_steps(eng, batches, host_targets, K, t0, stream, schedule):
     return start.elapsed_time(stop), wall, h2d, 4
 
 
+# ------------------------------------------------------------------ curvature cost
+def curvature_costs(eng, cam_dev, targets, K, stream):
+    """ms per step of (a) the gradient-only step (no probes, no curvature),
+    (b) Algorithm 1 with l = 10 and the curvature batch S2 = the next view batch
+    (Sec. 4.1; the paper's default interval), averaged over K steps, and the
+    resulting overheads of curvature relative to (a)."""
+    import torch
+    from paper_2602_00395_gb300.engine import eps_schedule
+    nb = len(targets)
+    cfg_l = eng.cfg.l
+
+    def run(kind, t0):
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            for phase in (0, 1):
+                if phase == 1:
+                    ev0.record(stream)
+                for k in range(K if phase else 2):
+                    t = t0 + k
+                    b = (t - 1) % nb
+                    eng.cams, eng.target = cam_dev[b], targets[b]
+                    eps = eps_schedule(t, 30000)
+                    if kind == "grad":
+                        eng.loss_val.zero_()
+                        eng.project(t, False, stream)
+                        eng.bin_sort(stream)
+                        eng.raster_fwd(t, False, stream)
+                        eng.raster_bwd(t, False, stream)
+                        eng.update(t, eps, False, None, stream)
+                    else:
+                        b2 = (b + 1) % nb
+                        eng.step_s2(t, eps, cam_dev[b2], targets[b2], stream)
+            ev1.record(stream)
+        ev1.synchronize()
+        return ev0.elapsed_time(ev1) / K
+
+    grad_ms = run("grad", 3000)
+    eng.cfg.l = 10
+    try:
+        l10_ms = run("s2", 4001)  # t = 4001 is a curvature step: K = 20 covers two of them
+    finally:
+        eng.cfg.l = cfg_l
+    return {"gradient_only_ms": grad_ms, "l10_separate_s2_ms": l10_ms,
+            "overhead_l10": l10_ms / grad_ms - 1.0}
+
+
 # ------------------------------------------------------------------ serving
 def served_metrics(device, n_requests=200, slots=16, budget_gb=40.0):
     """The served multi-scene workload: 16 resident scenes (50k-2M Gaussians, SH 3,
@@ -523,6 +570,8 @@ def run_cuda(args):
     host_targets = [tg.cpu().pin_memory() for tg in targets]
     e2e_ms, e2e_wall, h2d, d2h = e2e_steps(eng, batches, host_targets, args.steps, 5000, stream, sched)
     e2e_val = ws * args.steps / (e2e_ms / 1e3)
+    # the cost of curvature: gradient-only steps, and l = 10 with S2 != S1
+    curv = curvature_costs(eng, cam_dev, targets, 20, stream)
     # the plain one-view-at-a-time loop on the same workload
     plain_ms = plain_loop_steps(eng, cam_dev, targets, max(3, min(args.steps, 10)), 9000, stream, device)
     # roofline of the dominant call
@@ -603,6 +652,7 @@ def run_cuda(args):
             "eager": {"ms_per_step": eager_ms / args.steps, "value": 1e3 * args.steps / eager_ms, "unit": UNIT,
                       "what": "the same steps as six C-ABI calls issued from the host per step, no graph"},
             "graph": "one captured CUDA graph per view batch, step index and eps_t on the device",
+            "curvature": {**curv, "l1_fused_ms": ms_per_step, "overhead_l1_fused": ms_per_step / curv["gradient_only_ms"] - 1.0},
             "gpu_launches": kernel_launches_per_step(eng) * args.steps,
             "roofline": roof, "roofline_calls": roof_calls, "clocks": clocks, "cpu_baseline": cpu,
             "served": None,

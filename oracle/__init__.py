@@ -62,6 +62,7 @@ def lib():
                                       P, P, P, P]
             L.or_shd_radius.argtypes = [P, i64, i64, i32, d, P, P]
             L.or_tr_update.argtypes = [P, P, P, P, P, i64, i64, i32, P, C.c_int64, d, P]
+            L.or_adam_tr_update.argtypes = [P, P, P, P, i64, i64, i32, P, P, C.c_int64, d, P]
             L.or_project_tangent.argtypes = [P, i64, i64, i32, P, P, P]
             L.or_render_pixels.argtypes = [P, i64, i64, i32, P, i32, i32, i64, P, P, u64, C.c_int64, i32, P, P, P,
                                            P, P]
@@ -281,6 +282,25 @@ def tr_update(x, g_ema, d_ema, grad, hz, deg: int, t: int, eps: float, cfg=None)
     eta = np.zeros_like(x)
     lib().or_tr_update(_p(x), _p(g), _p(d), _p(gr), _p(h), n, n, deg, _p(cfg), t, eps, _p(eta))
     return x, g, d, eta
+
+
+def adam_config(beta1=0.9, beta2=0.999, eps_adam=1e-15,
+                lr=(1.6e-4, 5e-3, 1e-3, 2.5e-2, 2.5e-3, 1.25e-4)) -> np.ndarray:
+    """beta1, beta2, eps_adam and the learning rates of the row groups (mean,
+    log-scale, quaternion, opacity logit, SH DC, SH rest)."""
+    return np.array([beta1, beta2, eps_adam, *lr], np.float64)
+
+
+def adam_tr_update(x, m, v, grad, deg: int, t: int, eps: float, cfg=None, adam=None):
+    """ADAM-TR update for step t; returns new (x, m, v, eta) as float64 copies."""
+    x, m, v = _f64(x).copy(), _f64(m).copy(), _f64(v).copy()
+    gr = _f64(grad)
+    rows, n = x.shape
+    cfg = tr_config() if cfg is None else _f64(cfg)
+    adam = adam_config() if adam is None else _f64(adam)
+    eta = np.zeros_like(x)
+    lib().or_adam_tr_update(_p(x), _p(m), _p(v), _p(gr), n, n, deg, _p(cfg), _p(adam), t, eps, _p(eta))
+    return x, m, v, eta
 
 
 # ------------------------------------------------------------- sampled outputs

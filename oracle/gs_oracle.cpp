@@ -1033,6 +1033,37 @@ void or_tr_update(double* x, double* g_ema, double* d_ema, const double* grad, c
   }
 }
 
+// ADAM-TR (Sec. 5, ablation): the Hellinger trust-region clip of Sec. 4.2
+// applied to an Adam step instead of the Newton step.  For step t >= 1, per
+// parameter j of row group q (mean, log-scale, quaternion, opacity, SH DC, SH
+// rest; adam9 = beta1, beta2, eps_adam, lr[q] for q = 0..5):
+//   m = beta1 m + (1 - beta1) g,   v = beta2 v + (1 - beta2) g^2
+//   delta = -lr[q] (m / (1 - beta1^t)) / (sqrt(v / (1 - beta2^t)) + eps_adam)
+//   x += clip(delta, -eta, eta), eta the radius of x_t as in or_tr_update.
+void or_adam_tr_update(double* x, double* m, double* v, const double* grad, long pitch, long n, int deg,
+                       const double* cfg6, const double* adam9, int64_t t, double eps, double* eta_out) {
+  TRConfig cfg = read_cfg(cfg6);
+  int rows = n_rows(deg);
+  double ymax[16];
+  sh_absmax(deg, ymax);
+  const double b1 = adam9[0], b2 = adam9[1], ea = adam9[2];
+  const double bc1 = 1.0 - std::pow(b1, (double)t), bc2 = 1.0 - std::pow(b2, (double)t);
+  std::vector<double> eta(rows);
+  for (long i = 0; i < n; ++i) {
+    shd_radius(x, pitch, i, deg, eps, cfg, ymax, eta.data());  // from x_t, before the update
+    for (int r = 0; r < rows; ++r) {
+      const int q = r < 3 ? 0 : r < 6 ? 1 : r < 10 ? 2 : r < 11 ? 3 : r < 14 ? 4 : 5;
+      long j = (long)r * pitch + i;
+      m[j] = b1 * m[j] + (1.0 - b1) * grad[j];
+      v[j] = b2 * v[j] + (1.0 - b2) * grad[j] * grad[j];
+      double delta = -adam9[3 + q] * (m[j] / bc1) / (std::sqrt(v[j] / bc2) + ea);
+      double e = eta[r];
+      if (eta_out) eta_out[j] = e;
+      x[j] += std::min(std::max(delta, -e), e);
+    }
+  }
+}
+
 // Per-pixel signature (V x H x W) of every discrete decision the blend took:
 // which splats contributed, whether their alpha was capped, and which clamps of
 // their projection were active.  Two parameter vectors with equal signatures

@@ -172,6 +172,32 @@ class TRStep:
         self.bin_sort(stream)
         self.raster_fwd(None, probes=False, stream=stream)
 
+    def step_s2(self, t: int, eps: float, s2_cams, s2_target, stream=None) -> None:
+        """One iteration of Algorithm 1 with the curvature mini-batch S2 drawn
+        apart from S1 (Sec. 4.1): the gradient comes from the frame's views
+        (self.cams / self.target); on curvature steps ((t - 1) % l == 0) the
+        Hutchinson product comes from S2's views (same count, so the |S| factors
+        cancel), by a second projection with the probes, a forward pass with the
+        tangents and gs_hvp_diag.  s2_cams / s2_target are device tensors laid out
+        as self.cams / self.target."""
+        hvp = self.nu > 0 and ((t - 1) % self.cfg.l) == 0
+        self.loss_val.zero_()
+        self.project(t, probes=False, stream=stream)
+        self.bin_sort(stream)
+        self.raster_fwd(t, probes=False, stream=stream)
+        self.raster_bwd(t, probes=False, stream=stream)
+        if hvp:
+            cams1, target1 = self.cams, self.target
+            self.cams, self.target = s2_cams, s2_target
+            try:
+                self.project(t, probes=True, stream=stream)
+                self.bin_sort(stream)
+                self.raster_fwd(t, probes=True, stream=stream)
+                self.hvp_diag(t, stream)
+            finally:
+                self.cams, self.target = cams1, target1
+        self.update(t, eps, with_hz=hvp, stream=stream)
+
     def step_device(self, hvp: bool, schedule: G.gs_eps_schedule, stream=None) -> None:
         """One step of Algorithm 1 whose index lives in device memory (self.t_dev):
         advance it, then the six calls reading it there, so that the sequence can

@@ -241,6 +241,40 @@ def test_gradient_and_hutchinson_match_oracle(case, nu, loss_kind):
         assert np.abs(it - ref["image_tangent"]).max() <= 1e-4 * scale
 
 
+def test_step_with_separate_curvature_batch_matches_oracle():
+    """Algorithm 1 with S2 != S1 (Sec. 4.1): the gradient from S1's view, the
+    Hutchinson product from S2's view, then the update; l = 2 so that the next
+    step takes no curvature and keeps d_ema."""
+    from paper_2602_00395_gb300.engine import TRConfig
+    sc, cams2 = _ragged()
+    s1, s2 = [cams2[0]], [cams2[1]]
+    H, W = s1[0].height, s1[0].width
+    tg = S.noise_target(2, H, W, seed=2001)
+    e = _engine(sc.n, sc.sh_degree, s1, nu=2, cfg=TRConfig(l=2))
+    e.set_params(sc.params)
+    e.set_target(tg[:1])
+    from paper_2602_00395_gb300 import gs3dtr as G
+    cams_s2 = torch.from_numpy(G.camera_bytes(s2)).cuda()
+    tg_s2 = torch.from_numpy(tg[1:].reshape(-1)).cuda()
+    e.ensure_capacity()
+    e.cams, c1 = cams_s2, e.cams
+    e.ensure_capacity()
+    e.cams = c1
+    t, eps = 1, 1e-6
+    e.step_s2(t, eps, cams_s2, tg_s2)
+    torch.cuda.synchronize()
+    assert e.read_status() == 0
+    P = O.params64(sc)
+    r1 = O.backward(P, sc.sh_degree, s1, tg[:1].astype(np.float64), seed=42, t=t, nu=2)
+    r2 = O.backward(P, sc.sh_degree, s2, tg[1:].astype(np.float64), seed=42, t=t, nu=2)
+    _group_close(e.grad[:, : sc.n].cpu().numpy(), r1["grad"], 1e-4, "grad(S1)")
+    _group_close(e.hz[:, : sc.n].cpu().numpy(), r2["hz"], 1e-3, "hz(S2)")
+    d1 = e.d_ema.clone()
+    e.step_s2(2, eps, cams_s2, tg_s2)  # (2 - 1) % 2 != 0: no curvature, d_ema kept
+    torch.cuda.synchronize()
+    assert torch.equal(e.d_ema, d1)
+
+
 def test_hvp_diag_standalone_equals_fused():
     sc, e, ref = _grad_case("cfg1", 1)
     fused = e.hz.clone()
