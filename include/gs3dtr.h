@@ -261,6 +261,27 @@ gs_status gs_tr_update_dev(gs_params* x, gs_params* g_ema, gs_params* d_ema, con
                            const gs_params* hz, const gs_tr_config* cfg, const int64_t* t_device,
                            const gs_eps_schedule* schedule, gs_params* eta_out, int32_t* status, void* stream);
 
+/* Adam hyper-parameters of the ADAM-TR update: beta1, beta2, eps_adam and the
+ * learning rate of each row group: lr[0] means, lr[1] log-scales, lr[2]
+ * quaternions, lr[3] opacity logit, lr[4] SH DC (rows 11..13), lr[5] the other
+ * SH rows. */
+typedef struct gs_adam_config {
+  float beta1, beta2, eps_adam;
+  float lr[6];
+} gs_adam_config;
+
+/* ADAM-TR (the ablation of Sec. 5): the trust-region clip of Sec. 4.2 applied
+ * to an Adam step, for step t >= 1 with radius parameter eps:
+ *   m = beta1 m + (1 - beta1) grad,  v = beta2 v + (1 - beta2) grad^2
+ *   step = clip(-lr (m / (1 - beta1^t)) / (sqrt(v / (1 - beta2^t)) + eps_adam), -eta, eta),  x += step
+ * with eta from x before the update as in gs_tr_update (cfg supplies
+ * color_floor and mean_exact).  m and v are caller-owned state with the layout
+ * of x (zero before the first step).  eta_out may be NULL.  A non-finite result
+ * raises GS_FLAG_NONFINITE. */
+gs_status gs_adam_tr_update(gs_params* x, gs_params* m, gs_params* v, const gs_params* grad,
+                            const gs_tr_config* cfg, const gs_adam_config* adam, int64_t t, float eps,
+                            gs_params* eta_out, int32_t* status, void* stream);
+
 /* *t_device += 1 on the stream (no paper counterpart: the step counter of a
  * training loop replayed as a CUDA graph). */
 gs_status gs_step_advance(int64_t* t_device, void* stream);

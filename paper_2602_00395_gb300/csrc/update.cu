@@ -12,6 +12,8 @@
 // beta_c = 2 ||S^-1 W_c S||_F^2 - 2 ||W_c||_F^2 = 2 sum_{i<j} W_ij^2 (s_i/s_j - s_j/s_i)^2,
 // where W_c = R^T dR/dq_c is skew (its trace term tr(E'') equals -||W_c||_F^2 for
 // an orthogonal curve) with axial vector omega_c = 2 vec(conj(q^) * e_c) / |q|.
+#include <cmath>
+
 #include "common.cuh"
 
 namespace gs {
@@ -113,13 +115,23 @@ __device__ __forceinline__ float eps_of(const gs_eps_schedule& sc, int64_t t) {
 // HVP: hz is given.  With t_dev the step index is read on the device, eps is
 // eps_t of `sched` and d_ema is updated when (t - 1) % l == 0; otherwise eps is
 // as passed and d_ema is updated whenever HVP.
-template <int DEG, bool HVP, bool ETA>
+// Adam state of the ADAM-TR step (ge holds m, de holds v).
+struct AdamArg {
+  float b1, b2, eps_adam, inv_bc1, inv_bc2;
+  float lr[6];
+};
+
+__device__ __forceinline__ int row_group(int r) {
+  return r < 3 ? 0 : r < 6 ? 1 : r < 10 ? 2 : r < 11 ? 3 : r < 14 ? 4 : 5;
+}
+
+template <int DEG, bool HVP, bool ETA, bool ADAM = false>
 __global__ void __launch_bounds__(256) tr_update_kernel(float* __restrict__ x, float* __restrict__ ge,
                                                         float* __restrict__ de, const float* __restrict__ g,
                                                         const float* __restrict__ hz, float* __restrict__ eta_out,
                                                         int n, int n_pad, gs_tr_config cfg, float eps,
                                                         const int64_t* __restrict__ t_dev, gs_eps_schedule sched,
-                                                        int32_t* status) {
+                                                        AdamArg adam, int32_t* status) {
   constexpr int K = (DEG + 1) * (DEG + 1);
   constexpr int ROWS = kRowSH + 3 * K;
   constexpr int kLanesPerRow = kUpdCols / 4;  // 64
@@ -181,15 +193,22 @@ __global__ void __launch_bounds__(256) tr_update_kernel(float* __restrict__ x, f
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         const bool live = ci + k < n;  // padding columns stay as they are
-        go[k] = live ? a1 * gev[k] + b1 * gv[k] : gev[k];
-        dn[k] = (hvp_now && live) ? a2 * dv0[k] + b2 * hv[k] : dv0[k];
-        const float step = -go[k] / fmaxf(dn[k], cfg.d_floor);
+        float step;
+        if constexpr (ADAM) {
+          go[k] = live ? adam.b1 * gev[k] + (1.f - adam.b1) * gv[k] : gev[k];
+          dn[k] = live ? adam.b2 * dv0[k] + (1.f - adam.b2) * gv[k] * gv[k] : dv0[k];
+          step = -adam.lr[row_group(r)] * (go[k] * adam.inv_bc1) / (sqrtf(dn[k] * adam.inv_bc2) + adam.eps_adam);
+        } else {
+          go[k] = live ? a1 * gev[k] + b1 * gv[k] : gev[k];
+          dn[k] = (hvp_now && live) ? a2 * dv0[k] + b2 * hv[k] : dv0[k];
+          step = -go[k] / fmaxf(dn[k], cfg.d_floor);
+        }
         xo[k] = live ? xv[k] + fminf(fmaxf(step, -ev[k]), ev[k]) : xv[k];
         if (live) bad = bad || !isfinite(xo[k]) || !isfinite(go[k]) || !isfinite(dn[k]);
       }
       *reinterpret_cast<float4*>(x + j) = make_float4(xo[0], xo[1], xo[2], xo[3]);
       *reinterpret_cast<float4*>(ge + j) = make_float4(go[0], go[1], go[2], go[3]);
-      if (HVP && hvp_now) *reinterpret_cast<float4*>(de + j) = make_float4(dn[0], dn[1], dn[2], dn[3]);
+      if (ADAM || (HVP && hvp_now)) *reinterpret_cast<float4*>(de + j) = make_float4(dn[0], dn[1], dn[2], dn[3]);
       if (ETA) *reinterpret_cast<float4*>(eta_out + j) = make_float4(ev[0], ev[1], ev[2], ev[3]);
     }
   }
@@ -205,7 +224,7 @@ void launch_update(bool hvp, bool eta, gs_params* x, gs_params* ge, gs_params* d
   float* ep = eta_out ? eta_out->data : nullptr;
 #define GS_UPD(H, E)                                                                                         \
   tr_update_kernel<DEG, H, E><<<blocks, 256, 0, st>>>(x->data, ge->data, de->data, g->data, hp, ep, x->n, \
-                                                      x->n_pad, cfg, eps, t_dev, sched, status)
+                                                      x->n_pad, cfg, eps, t_dev, sched, AdamArg{}, status)
   if (hvp) {
     if (eta) GS_UPD(true, true); else GS_UPD(true, false);
   } else {
@@ -219,6 +238,22 @@ void launch_update(bool hvp, bool eta, gs_params* x, gs_params* ge, gs_params* d
 
 namespace gs {
 namespace {
+template <int DEG>
+void launch_adam(bool eta, gs_params* x, gs_params* m, gs_params* v, const gs_params* g, gs_params* eta_out,
+                 gs_tr_config cfg, float eps, AdamArg adam, int32_t* status, cudaStream_t st) {
+  const int blocks = (x->n + kUpdCols - 1) / kUpdCols;
+  float* ep = eta_out ? eta_out->data : nullptr;
+  const gs_eps_schedule none{0.0, 0.0, 0};
+  if (eta)
+    tr_update_kernel<DEG, false, true, true><<<blocks, 256, 0, st>>>(x->data, m->data, v->data, g->data, nullptr, ep,
+                                                                    x->n, x->n_pad, cfg, eps, nullptr, none, adam,
+                                                                    status);
+  else
+    tr_update_kernel<DEG, false, false, true><<<blocks, 256, 0, st>>>(x->data, m->data, v->data, g->data, nullptr,
+                                                                     nullptr, x->n, x->n_pad, cfg, eps, nullptr, none,
+                                                                     adam, status);
+}
+
 __global__ void step_advance_kernel(int64_t* t) { *t += 1; }
 
 gs_status run_update(const char* name, gs_params* x, gs_params* g_ema, gs_params* d_ema, const gs_params* grad,
@@ -281,4 +316,43 @@ extern "C" gs_status gs_step_advance(int64_t* t_device, void* stream) {
   GS_REQUIRE(t_device, "gs_step_advance: null argument");
   step_advance_kernel<<<1, 1, 0, (cudaStream_t)stream>>>(t_device);
   return check_launch("gs_step_advance");
+}
+
+extern "C" gs_status gs_adam_tr_update(gs_params* x, gs_params* m, gs_params* v, const gs_params* grad,
+                                       const gs_tr_config* cfg, const gs_adam_config* adam, int64_t t, float eps,
+                                       gs_params* eta_out, int32_t* status, void* stream) {
+  using namespace gs;
+  GS_REQUIRE(x && m && v && grad && cfg && adam, "gs_adam_tr_update: null argument");
+  GS_REQUIRE(x->data && m->data && v->data && grad->data, "gs_adam_tr_update: null device buffer");
+  GS_REQUIRE(t >= 1, "gs_adam_tr_update: need t >= 1");
+  GS_REQUIRE(eps > 0.f, "gs_adam_tr_update: eps must be positive");
+  GS_REQUIRE(adam->beta1 >= 0.f && adam->beta1 < 1.f && adam->beta2 >= 0.f && adam->beta2 < 1.f,
+             "gs_adam_tr_update: betas must be in [0, 1)");
+  auto same = [&](const gs_params* p) {
+    return !p || (p->n == x->n && p->n_pad == x->n_pad && p->sh_degree == x->sh_degree);
+  };
+  GS_REQUIRE(same(m) && same(v) && same(grad) && same(eta_out), "gs_adam_tr_update: buffers differ in layout");
+  GS_REQUIRE(x->n_pad % 4 == 0, "gs_adam_tr_update: n_pad must be a multiple of 4");
+  if (x->sh_degree < 0 || x->sh_degree > 3) {
+    set_error("gs_adam_tr_update: unsupported sh_degree=%d", x->sh_degree);
+    return GS_ERR_UNSUPPORTED;
+  }
+  if (x->n == 0) return GS_OK;
+  AdamArg a;
+  a.b1 = adam->beta1;
+  a.b2 = adam->beta2;
+  a.eps_adam = adam->eps_adam;
+  // bias corrections of step t, in double precision on the host
+  a.inv_bc1 = (float)(1.0 / (1.0 - std::pow((double)adam->beta1, (double)t)));
+  a.inv_bc2 = (float)(1.0 / (1.0 - std::pow((double)adam->beta2, (double)t)));
+  for (int q = 0; q < 6; ++q) a.lr[q] = adam->lr[q];
+  const bool eta = eta_out && eta_out->data;
+  cudaStream_t st = (cudaStream_t)stream;
+  switch (x->sh_degree) {
+    case 0: launch_adam<0>(eta, x, m, v, grad, eta_out, *cfg, eps, a, status, st); break;
+    case 1: launch_adam<1>(eta, x, m, v, grad, eta_out, *cfg, eps, a, status, st); break;
+    case 2: launch_adam<2>(eta, x, m, v, grad, eta_out, *cfg, eps, a, status, st); break;
+    default: launch_adam<3>(eta, x, m, v, grad, eta_out, *cfg, eps, a, status, st); break;
+  }
+  return check_launch("gs_adam_tr_update");
 }

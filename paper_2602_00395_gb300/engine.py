@@ -166,6 +166,22 @@ class TRStep:
                        self.P(self.hz) if with_hz else None, self.cfg.struct(), t, eps,
                        self.P(eta_out) if eta_out is not None else None, self.status, stream)
 
+    def update_adam(self, t: int, eps: float, adam=None, eta_out=None, stream=None) -> None:
+        """ADAM-TR update (Sec. 5 ablation); g_ema and d_ema hold Adam's m and v."""
+        G.gs_adam_tr_update(self.P(self.x), self.P(self.g_ema), self.P(self.d_ema), self.P(self.grad),
+                            self.cfg.struct(), adam or G.adam_struct(), t, eps,
+                            self.P(eta_out) if eta_out is not None else None, self.status, stream)
+
+    def step_adam(self, t: int, eps: float, adam=None, stream=None) -> None:
+        """One ADAM-TR iteration: the gradient of the frame's views, then the
+        Adam step clipped by the Hellinger trust region (no curvature)."""
+        self.loss_val.zero_()
+        self.project(t, probes=False, stream=stream)
+        self.bin_sort(stream)
+        self.raster_fwd(t, probes=False, stream=stream)
+        self.raster_bwd(t, probes=False, stream=stream)
+        self.update_adam(t, eps, adam, None, stream)
+
     # ------------------------------------------------------------ composite
     def render(self, stream=None) -> None:
         self.project(None, probes=False, stream=stream)

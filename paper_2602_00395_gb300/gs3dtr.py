@@ -24,7 +24,7 @@ GS_LOSS_L1, GS_LOSS_L2 = 0, 1
 EXPORTED = ("gs_last_error", "gs_version", "gs_project", "gs_bin_sort_workspace_size", "gs_bin_sort",
             "gs_bin_sort_noalloc",
             "gs_raster_fwd", "gs_raster_bwd_workspace_size", "gs_raster_bwd", "gs_hvp_diag", "gs_tr_update",
-            "gs_tr_update_dev", "gs_step_advance")
+            "gs_tr_update_dev", "gs_step_advance", "gs_adam_tr_update")
 
 
 class gs_params(C.Structure):
@@ -50,6 +50,16 @@ class gs_probe(C.Structure):
 
 class gs_eps_schedule(C.Structure):
     _fields_ = [("eps0", C.c_double), ("eps1", C.c_double), ("total", C.c_int64)]
+
+
+class gs_adam_config(C.Structure):
+    _fields_ = [("beta1", C.c_float), ("beta2", C.c_float), ("eps_adam", C.c_float), ("lr", C.c_float * 6)]
+
+
+def adam_struct(beta1=0.9, beta2=0.999, eps_adam=1e-15, lr=(1.6e-4, 5e-3, 1e-3, 2.5e-2, 2.5e-3, 1.25e-4)):
+    """Adam hyper-parameters; learning rates of the row groups mean, log-scale,
+    quaternion, opacity logit, SH DC, other SH."""
+    return gs_adam_config(beta1, beta2, eps_adam, (C.c_float * 6)(*lr))
 
 
 class gs_projected(C.Structure):
@@ -128,6 +138,10 @@ def load():
                                        C.POINTER(gs_eps_schedule), C.POINTER(gs_params), P, P]
         L.gs_step_advance.restype = st
         L.gs_step_advance.argtypes = [P, P]
+        L.gs_adam_tr_update.restype = st
+        L.gs_adam_tr_update.argtypes = [C.POINTER(gs_params), C.POINTER(gs_params), C.POINTER(gs_params),
+                                        C.POINTER(gs_params), C.POINTER(gs_tr_config), C.POINTER(gs_adam_config),
+                                        C.c_int64, C.c_float, C.POINTER(gs_params), P, P]
         _lib = L
         return L
 
@@ -260,3 +274,12 @@ def gs_tr_update_dev(x: gs_params, g_ema: gs_params, d_ema: gs_params, grad: gs_
 def gs_step_advance(t_device, stream=None) -> None:
     L = load()
     check(L.gs_step_advance(ptr(t_device), stream_handle(stream)), "gs_step_advance")
+
+
+def gs_adam_tr_update(x: gs_params, m: gs_params, v: gs_params, grad: gs_params, cfg: gs_tr_config,
+                      adam: gs_adam_config, t: int, eps: float, eta_out: gs_params | None = None, status=None,
+                      stream=None) -> None:
+    L = load()
+    check(L.gs_adam_tr_update(C.byref(x), C.byref(m), C.byref(v), C.byref(grad), C.byref(cfg), C.byref(adam), t,
+                              eps, C.byref(eta_out) if eta_out else None, ptr(status), stream_handle(stream)),
+          "gs_adam_tr_update")

@@ -341,3 +341,45 @@ def test_tr_update_matches_oracle(deg, t, l, mean_exact):
     # some steps are clipped and some are not
     clipped = np.isclose(np.abs(dx_ref), np.where(fin, reta, -1), rtol=1e-12)
     assert clipped.any() and (~clipped).any()
+
+
+@pytest.mark.parametrize("deg,t", [(3, 1), (1, 7)])
+def test_adam_tr_update_matches_oracle(deg, t):
+    """ADAM-TR (Sec. 5): the Adam step clipped by the trust region, vs the oracle."""
+    from paper_2602_00395_gb300 import gs3dtr as G
+    n = 4001
+    sc = S.make_scene(n, deg, seed=91)
+    rng = np.random.default_rng(t)
+    P32 = sc.params.copy()
+    m = (rng.normal(size=P32.shape) * 1e-3).astype(np.float32)
+    v = (np.abs(rng.normal(size=P32.shape)) * 1e-6).astype(np.float32)
+    g = (rng.normal(size=P32.shape) * 1e-3).astype(np.float32)
+    eps = 1e-6
+    e = _engine(n, deg, [S.single_camera(64, 64)], nu=0)
+    e.x.copy_(torch.from_numpy(P32)); e.g_ema.copy_(torch.from_numpy(m)); e.d_ema.copy_(torch.from_numpy(v))
+    e.grad.copy_(torch.from_numpy(g))
+    adam = G.adam_struct()
+    eta = torch.zeros_like(e.x)
+    e.update_adam(t, eps, adam, eta)
+    torch.cuda.synchronize()
+    assert e.read_status() == 0
+    f32 = lambda a: np.float64(np.float32(a))  # the hyper-parameters the kernel receives
+    oadam = O.adam_config(f32(adam.beta1), f32(adam.beta2), f32(adam.eps_adam), [f32(x) for x in adam.lr])
+    ocfg = O.tr_config(theta1=f32(e.cfg.theta1), theta2=f32(e.cfg.theta2), d_floor=f32(e.cfg.d_floor),
+                       color_floor=f32(e.cfg.color_floor), l=e.cfg.l, mean_exact=e.cfg.mean_exact)
+    rx, rm, rv, reta = O.adam_tr_update(P32[:, :n], m[:, :n], v[:, :n], g[:, :n], deg, t=t, eps=np.float32(eps),
+                                        cfg=ocfg, adam=oadam)
+    mg = e.g_ema[:, :n].cpu().numpy().astype(np.float64)
+    vg = e.d_ema[:, :n].cpu().numpy().astype(np.float64)
+    b1, b2 = f32(adam.beta1), f32(adam.beta2)
+    assert np.all(np.abs(mg - rm) <= 1e-6 * (b1 * np.abs(m[:, :n]) + (1 - b1) * np.abs(g[:, :n])) + 1e-30)
+    assert np.all(np.abs(vg - rv) <= 1e-6 * (b2 * np.abs(v[:, :n]) + (1 - b2) * g[:, :n] ** 2) + 1e-30)
+    eg = eta[:, :n].cpu().numpy()
+    fin = np.isfinite(reta)
+    assert np.array_equal(np.isfinite(eg), fin)
+    np.testing.assert_allclose(eg[fin], reta[fin], rtol=1e-5)
+    # x moves by the clipped step: at most the radius, and the Adam step where unclipped
+    dx_gpu = e.x[:, :n].cpu().numpy().astype(np.float64) - P32[:, :n]
+    dx_ref = rx - P32[:, :n]
+    tol = 1e-4 * np.abs(dx_ref) + 2e-7 * np.abs(P32[:, :n]) + 1e-12
+    assert np.all(np.abs(dx_gpu - dx_ref) <= tol)
