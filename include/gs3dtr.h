@@ -143,12 +143,19 @@ typedef struct gs_sorted {
   uint64_t capacity;
 } gs_sorted;
 
-enum { GS_LOSS_L1 = 0, GS_LOSS_L2 = 1 };
+enum { GS_LOSS_L1 = 0, GS_LOSS_L2 = 1, GS_LOSS_COTANGENT = 2 };
 
 /* Per-pixel loss of Sec. 3.2 in least-squares form f = 1/(2m) sum F^2 over the
  * m = 3 H W V residual components r = render - target:
  *   GS_LOSS_L1: F = sqrt(|r|); dL/dC = sign(r)/(2m); GN weight 1/(4 max(|r|, gn_floor)) / m
- *   GS_LOSS_L2: F = r;         dL/dC = r/m;          GN weight 1/m */
+ *   GS_LOSS_L2: F = r;         dL/dC = r/m;          GN weight 1/m
+ *   GS_LOSS_COTANGENT: any objective whose image-space vectors the caller forms:
+ *       `target` then holds S cotangent images, S x V x 3 x H x W: first dL/dC
+ *       (when the gradient is requested), then for each probe k the vector
+ *       u_k whose pull-back J^T u_k is the Gauss-Newton product G z_k (for the
+ *       objective of Sec. 3.2, u_k = (1/m) sum_j grad_C F_j (grad_C F_j . J z_k)).
+ *       The image is not read, loss_out is left as it is, and the probe count
+ *       comes from `probe` alone (image_tangent is not read). */
 typedef struct gs_loss {
   int32_t kind;
   float gn_floor;

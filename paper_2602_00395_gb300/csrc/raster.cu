@@ -436,6 +436,13 @@ __global__ void GS_BWD_BOUNDS raster_bwd_kernel(
     const size_t at0 = (size_t)py * fr.width + px;
     p.T = final_T[(size_t)view * HW + at0];
     p.nc = n_contrib[(size_t)view * HW + at0];
+    if (loss_kind == GS_LOSS_COTANGENT) {  // the caller's cotangent images, one per stream
+#pragma unroll
+      for (int st = 0; st < S; ++st)
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) p.w[st][ch] = target[(((size_t)st * fr.n_views + view) * 3 + ch) * HW + at0];
+      continue;
+    }
 #pragma unroll
     for (int ch = 0; ch < 3; ++ch) {
       const size_t at = ((size_t)view * 3 + ch) * HW + at0;
@@ -973,8 +980,10 @@ gs_status run_bwd(bool want_grad, const gs_params* x, const gs_camera* cams, gs_
   GS_REQUIRE(proj->rec && sorted->vals && sorted->ranges && x->data, "%s: null device buffer", name);
   GS_REQUIRE(frame_ok(frame), "%s: bad frame", name);
   GS_REQUIRE(x->n >= 0 && x->n_pad >= x->n && x->n_pad % 4 == 0, "%s: bad n/n_pad", name);
-  GS_REQUIRE(loss.kind == GS_LOSS_L1 || loss.kind == GS_LOSS_L2, "%s: bad loss kind %d", name, loss.kind);
-  const int nu = (image_tangent && probe) ? probe->nu : 0;
+  GS_REQUIRE(loss.kind == GS_LOSS_L1 || loss.kind == GS_LOSS_L2 || loss.kind == GS_LOSS_COTANGENT,
+             "%s: bad loss kind %d", name, loss.kind);
+  const bool given = loss.kind == GS_LOSS_COTANGENT;
+  const int nu = ((image_tangent || given) && probe) ? probe->nu : 0;
   if (nu < 0 || nu > 2 || x->sh_degree < 0 || x->sh_degree > 3) {
     set_error("%s: unsupported nu=%d sh_degree=%d", name, nu, x->sh_degree);
     return GS_ERR_UNSUPPORTED;

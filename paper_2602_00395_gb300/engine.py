@@ -155,6 +155,21 @@ class TRStep:
                         self.P(self.grad), self.P(self.hz) if pr else None, self.loss_val, self.bwd_ws,
                         self.status, stream)
 
+    def raster_bwd_cotangent(self, cot, t: int | None = None, want_grad: bool = True, stream=None) -> None:
+        """Reverse pass from caller-formed cotangent images (GS_LOSS_COTANGENT):
+        cot is S x V x 3 x H x W (dL/dC first when want_grad, then one vector per
+        probe when t is given); grad and/or hz are written."""
+        pr = self.probe(t) if t is not None else None
+        loss = G.gs_loss(G.GS_LOSS_COTANGENT, self.loss.gn_floor)
+        if want_grad:
+            G.gs_raster_bwd(self.P(self.x), self.cams, self.frame, self.proj(), self.sorted(), self.image, cot,
+                            self.final_T, self.n_contrib, None, pr, loss, self.P(self.grad),
+                            self.P(self.hz) if pr else None, None, self.bwd_ws, self.status, stream)
+        else:
+            G.gs_hvp_diag(self.P(self.x), self.cams, self.frame, self.proj(), self.sorted(), self.image, cot,
+                          self.final_T, self.n_contrib, None, pr, loss, self.P(self.hz), self.bwd_ws, self.status,
+                          stream)
+
     def hvp_diag(self, t: int, stream=None) -> None:
         pr = self.probe(t)
         G.gs_hvp_diag(self.P(self.x), self.cams, self.frame, self.proj(), self.sorted(), self.image, self.target,

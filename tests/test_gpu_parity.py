@@ -275,6 +275,34 @@ def test_step_with_separate_curvature_batch_matches_oracle():
     assert torch.equal(e.d_ema, d1)
 
 
+@pytest.mark.parametrize("want_grad", [True, False])
+def test_reverse_pass_from_given_cotangents_matches_oracle(want_grad):
+    """GS_LOSS_COTANGENT: with dL/dC = c and u_k = (1/m) J z_k the reverse pass
+    gives J^T c and the Hutchinson diagonal of (1/m) J^T J, which the oracle
+    computes as the L2 objective of the target image - m c."""
+    sc, cams = _ragged()
+    V, H, W, nu, t = len(cams), cams[0].height, cams[0].width, 2, 6
+    e = _engine(sc.n, sc.sh_degree, cams, nu=nu)
+    e.set_params(sc.params)
+    e.ensure_capacity()
+    e.project(t, probes=True)
+    e.bin_sort()
+    e.raster_fwd(t, probes=True)
+    P = O.params64(sc)
+    img = O.render(P, sc.sh_degree, cams, with_margin=False)["image"]
+    m = 3 * H * W * V
+    c = np.random.default_rng(3).normal(size=img.shape) * (1.0 / m)
+    ref = O.backward(P, sc.sh_degree, cams, img - m * c, loss_kind=1, seed=42, t=t, nu=nu, want_tangents=True)
+    streams = ([c] if want_grad else []) + [ref["image_tangent"][k] / m for k in range(nu)]
+    cot = torch.from_numpy(np.stack(streams).astype(np.float32).reshape(-1)).cuda()
+    e.raster_bwd_cotangent(cot, t, want_grad)
+    torch.cuda.synchronize()
+    assert e.read_status() == 0
+    if want_grad:
+        _group_close(e.grad[:, : sc.n].cpu().numpy(), ref["grad"], 1e-4, "grad")
+    _group_close(e.hz[:, : sc.n].cpu().numpy(), ref["hz"], 1e-3, "hz")
+
+
 def test_hvp_diag_standalone_equals_fused():
     sc, e, ref = _grad_case("cfg1", 1)
     fused = e.hz.clone()
