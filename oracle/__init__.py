@@ -57,6 +57,12 @@ def lib():
             L.or_render.argtypes = [P, i64, i64, i32, P, i32, i32, i32, P, P, P, P]
             L.or_jvp.argtypes = [P, i64, i64, i32, P, i32, i32, i32, P, P]
             L.or_jacobian.argtypes = [P, i64, i64, i32, P, i32, i32, i32, P]
+            L.or_backward_dssim.restype = d
+            L.or_backward_dssim.argtypes = [P, i64, i64, i32, P, i32, i32, i32, P, d, d, u64, C.c_int64, i32,
+                                            P, P, P]
+            L.or_ssim.argtypes = [P, P, i32, i32, P, P, P, P]
+            L.or_ssim_vjp.argtypes = [P, P, i32, i32, P, P]
+            L.or_ssim_jvp.argtypes = [P, P, i32, i32, P, P]
             L.or_backward.restype = d
             L.or_backward.argtypes = [P, i64, i64, i32, P, i32, i32, i32, P, i32, d, u64, C.c_int64, i32,
                                       P, P, P, P]
@@ -242,8 +248,9 @@ def jacobian(P: np.ndarray, deg: int, cams, tw: int = 16, th: int = 16) -> np.nd
 
 def backward(P: np.ndarray, deg: int, cams, target: np.ndarray, *, loss_kind: int = 0,
              gn_floor: float = 1e-3, seed: int = 42, t: int = 1, nu: int = 0,
-             tw: int = 16, th: int = 16, want_tangents: bool = False):
-    """Objective, gradient (rows x n) and, if nu > 0, the Hutchinson diagonal (rows x n)."""
+             tw: int = 16, th: int = 16, want_tangents: bool = False, lam: float = 0.2):
+    """Objective, gradient (rows x n) and, if nu > 0, the Hutchinson diagonal (rows x n).
+    loss_kind 0: L1, 1: L2, 2: (1 - lam) L1 + lam D-SSIM (res_margin not computed)."""
     P = _f64(P)
     rows, n = P.shape
     ca = camera_array(cams)
@@ -254,9 +261,37 @@ def backward(P: np.ndarray, deg: int, cams, target: np.ndarray, *, loss_kind: in
     hz = np.zeros((rows, n)) if nu > 0 else None
     it = np.zeros((nu, V, 3, H, W)) if (want_tangents and nu > 0) else None
     rm = np.zeros((V, H, W))
-    f = lib().or_backward(_p(P), n, n, deg, _p(ca), V, tw, th, _p(tg), loss_kind, gn_floor, seed, t, nu,
-                          _p(grad), _p(hz), _p(it), _p(rm))
+    if loss_kind == 2:
+        f = lib().or_backward_dssim(_p(P), n, n, deg, _p(ca), V, tw, th, _p(tg), lam, gn_floor, seed, t, nu,
+                                    _p(grad), _p(hz), _p(it))
+        rm = None
+    else:
+        f = lib().or_backward(_p(P), n, n, deg, _p(ca), V, tw, th, _p(tg), loss_kind, gn_floor, seed, t, nu,
+                              _p(grad), _p(hz), _p(it), _p(rm))
     return dict(loss=float(f), grad=grad, hz=hz, image_tangent=it, res_margin=rm)
+
+
+def ssim(x: np.ndarray, y: np.ndarray):
+    """SSIM map of one channel (H x W) and its partials by mx, E[x^2], E[xy]."""
+    x, y = _f64(x), _f64(y)
+    H, W = x.shape
+    out = [np.zeros((H, W)) for _ in range(4)]
+    lib().or_ssim(_p(x), _p(y), H, W, *[_p(o) for o in out])
+    return tuple(out)
+
+
+def ssim_vjp(x: np.ndarray, y: np.ndarray, a: np.ndarray) -> np.ndarray:
+    x, y, a = _f64(x), _f64(y), _f64(a)
+    out = np.zeros_like(x)
+    lib().or_ssim_vjp(_p(x), _p(y), x.shape[0], x.shape[1], _p(a), _p(out))
+    return out
+
+
+def ssim_jvp(x: np.ndarray, y: np.ndarray, d: np.ndarray) -> np.ndarray:
+    x, y, d = _f64(x), _f64(y), _f64(d)
+    out = np.zeros_like(x)
+    lib().or_ssim_jvp(_p(x), _p(y), x.shape[0], x.shape[1], _p(d), _p(out))
+    return out
 
 
 def tr_config(theta1=0.9, theta2=0.999, d_floor=1e-12, color_floor=1e-2, l=10, mean_exact=0) -> np.ndarray:

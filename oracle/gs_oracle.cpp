@@ -495,6 +495,113 @@ double rademacher(uint64_t seed, int64_t t, int k, uint64_t j) {
 // consecutive entries, so they share one or two hashes.
 uint64_t probe_entry(long i, int r, int rows) { return (uint64_t)i * (uint64_t)rows + (uint64_t)r; }
 
+// ------------------------------------------------------------------ SSIM
+// Per-pixel structural similarity of one channel x (rendered) against y
+// (target), H x W row-major: local statistics under the 11 x 11 Gaussian window
+// of standard deviation 1.5 (normalised over the whole window; pixels outside
+// the image count as 0), C1 = 0.01^2, C2 = 0.03^2:
+//   S = (2 mx my + C1)(2 sxy + C2) / ((mx^2 + my^2 + C1)(sx2 + sy2 + C2))
+// with mx = G*x, sx2 = G*(x^2) - mx^2, sxy = G*(xy) - mx my.  As a function of
+// the filtered raw moments (mx, Ex2 = G*(x^2), Exy = G*(xy)) its partials are
+//   dS/dmx  = 2 A2/(B1 B2) (my - mx A1/B1) + 2 mx A1 A2/(B1 B2^2) - 2 my A1/(B1 B2)
+//   dS/dEx2 = -A1 A2/(B1 B2^2),   dS/dExy = 2 A1/(B1 B2)
+// (A1 = 2 mx my + C1, A2 = 2 sxy + C2, B1 = mx^2 + my^2 + C1, B2 = sx2 + sy2 + C2).
+const int kSsimR = 5;
+const double kSsimC1 = 1e-4, kSsimC2 = 9e-4;
+
+std::vector<double> ssim_window() {
+  std::vector<double> g(2 * kSsimR + 1);
+  double s = 0.0;
+  for (int i = -kSsimR; i <= kSsimR; ++i) s += g[i + kSsimR] = std::exp(-(double)(i * i) / (2.0 * 1.5 * 1.5));
+  for (double& v : g) v /= s;
+  return g;
+}
+
+// G * f at every pixel (zero outside the image), by direct window sums.
+std::vector<double> ssim_filter(const double* f, int H, int W) {
+  const std::vector<double> g = ssim_window();
+  std::vector<double> out((size_t)H * W, 0.0);
+  for (int y = 0; y < H; ++y)
+    for (int x = 0; x < W; ++x) {
+      double acc = 0.0;
+      for (int dy = -kSsimR; dy <= kSsimR; ++dy)
+        for (int dx = -kSsimR; dx <= kSsimR; ++dx) {
+          int yy = y + dy, xx = x + dx;
+          if (yy < 0 || yy >= H || xx < 0 || xx >= W) continue;
+          acc += g[dy + kSsimR] * g[dx + kSsimR] * f[(size_t)yy * W + xx];
+        }
+      out[(size_t)y * W + x] = acc;
+    }
+  return out;
+}
+
+struct SsimMaps {
+  std::vector<double> S, dmx, dex2, dexy;
+};
+
+SsimMaps ssim_maps(const double* x, const double* y, int H, int W) {
+  const size_t N = (size_t)H * W;
+  std::vector<double> x2(N), y2(N), xy(N);
+  for (size_t i = 0; i < N; ++i) {
+    x2[i] = x[i] * x[i];
+    y2[i] = y[i] * y[i];
+    xy[i] = x[i] * y[i];
+  }
+  std::vector<double> mx = ssim_filter(x, H, W), my = ssim_filter(y, H, W);
+  std::vector<double> ex2 = ssim_filter(x2.data(), H, W), ey2 = ssim_filter(y2.data(), H, W);
+  std::vector<double> exy = ssim_filter(xy.data(), H, W);
+  SsimMaps M;
+  M.S.resize(N);
+  M.dmx.resize(N);
+  M.dex2.resize(N);
+  M.dexy.resize(N);
+  for (size_t i = 0; i < N; ++i) {
+    const double sx2 = ex2[i] - mx[i] * mx[i], sy2 = ey2[i] - my[i] * my[i], sxy = exy[i] - mx[i] * my[i];
+    const double A1 = 2 * mx[i] * my[i] + kSsimC1, A2 = 2 * sxy + kSsimC2;
+    const double B1 = mx[i] * mx[i] + my[i] * my[i] + kSsimC1, B2 = sx2 + sy2 + kSsimC2;
+    M.S[i] = A1 * A2 / (B1 * B2);
+    // partials with respect to mx, sx2, sxy, then to the raw moments
+    const double d_mx = 2 * A2 / (B1 * B2) * (my[i] - mx[i] * A1 / B1);
+    const double d_sx2 = -A1 * A2 / (B1 * B2 * B2);
+    const double d_sxy = 2 * A1 / (B1 * B2);
+    M.dmx[i] = d_mx - 2 * mx[i] * d_sx2 - my[i] * d_sxy;
+    M.dex2[i] = d_sx2;
+    M.dexy[i] = d_sxy;
+  }
+  return M;
+}
+
+// sum_p a_p dS_p/dx_q for every q (the adjoint of the map x -> S).
+std::vector<double> ssim_vjp(const double* x, const double* y, int H, int W, const SsimMaps& M, const double* a) {
+  const size_t N = (size_t)H * W;
+  std::vector<double> p1(N), p2(N), p3(N);
+  for (size_t i = 0; i < N; ++i) {
+    p1[i] = a[i] * M.dmx[i];
+    p2[i] = a[i] * M.dex2[i];
+    p3[i] = a[i] * M.dexy[i];
+  }
+  // the window is symmetric, so the adjoint filter is the filter itself
+  std::vector<double> f1 = ssim_filter(p1.data(), H, W), f2 = ssim_filter(p2.data(), H, W);
+  std::vector<double> f3 = ssim_filter(p3.data(), H, W);
+  std::vector<double> out(N);
+  for (size_t q = 0; q < N; ++q) out[q] = f1[q] + 2 * x[q] * f2[q] + y[q] * f3[q];
+  return out;
+}
+
+// The directional derivative of S along the image direction d.
+std::vector<double> ssim_jvp(const double* x, const double* y, int H, int W, const SsimMaps& M, const double* d) {
+  const size_t N = (size_t)H * W;
+  std::vector<double> xd(N), yd(N);
+  for (size_t i = 0; i < N; ++i) {
+    xd[i] = 2 * x[i] * d[i];
+    yd[i] = y[i] * d[i];
+  }
+  std::vector<double> f1 = ssim_filter(d, H, W), f2 = ssim_filter(xd.data(), H, W), f3 = ssim_filter(yd.data(), H, W);
+  std::vector<double> out(N);
+  for (size_t i = 0; i < N; ++i) out[i] = M.dmx[i] * f1[i] + M.dex2[i] * f2[i] + M.dexy[i] * f3[i];
+  return out;
+}
+
 // ----------------------------------------------------------- reverse pass
 // Cotangents of the 2-D splat quantities, 9 per splat: (mx, my, A, B, C, o, r, g, b).
 enum { Q_MX, Q_MY, Q_A, Q_B, Q_C, Q_O, Q_R, Q_G, Q_BL, NQ };
@@ -908,15 +1015,21 @@ void or_jacobian(const double* P, long pitch, long n, int deg, const double* cam
 // Rademacher probes of (seed, t, k), and img_tan (nu x V x 3 x H x W, may be null) the
 // tangents J z_k.  res_margin (V x H x W, may be null) receives min over channels of |r|.
 // Returns the objective f = (1/2m) sum F^2.
-double or_backward(const double* P, long pitch, long n, int deg, const double* cams, int n_views, int tw,
-                   int th, const double* target, int loss_kind, double gn_floor, uint64_t seed, int64_t t,
-                   int nu, double* grad, double* hz, double* img_tan, double* res_margin) {
+//   loss_kind 2 (or_backward_dssim): per pixel and channel the two components
+//     F = sqrt((1 - lambda) |r|) and F = sqrt(lambda (1 - S)) (Eq. pixel_loss
+//     with D-SSIM = 1 - S), m = sum over views of 6 H W; dL/dC = (1/2m)
+//     ((1 - lambda) sign(r) - lambda sum_p dS_p/dC), and the Gauss-Newton
+//     vector of probe k is (1 - lambda)/(4 max(|r|, gn_floor))/m . J z_k plus
+//     the adjoint of S applied to lambda/(4 max(1 - S, gn_floor))/m . dS[J z_k].
+double backward_impl(const double* P, long pitch, long n, int deg, const double* cams, int n_views, int tw,
+                     int th, const double* target, int loss_kind, double lambda, double gn_floor, uint64_t seed,
+                     int64_t t, int nu, double* grad, double* hz, double* img_tan, double* res_margin) {
   int rows = n_rows(deg);
   double m = 0.0;
   std::vector<View> views;
   for (int v = 0; v < n_views; ++v) {
     views.push_back(build_view(P, pitch, n, deg, cams + 24 * v, tw, th));
-    m += 3.0 * views.back().cam.W * views.back().cam.H;
+    m += (loss_kind == 2 ? 6.0 : 3.0) * views.back().cam.W * views.back().cam.H;
   }
   for (long k = 0; k < (long)rows * n; ++k) grad[k] = 0.0;
   if (hz) for (long k = 0; k < (long)rows * n; ++k) hz[k] = 0.0;
@@ -927,7 +1040,8 @@ double or_backward(const double* P, long pitch, long n, int deg, const double* c
     for (int r = 0; r < rows; ++r)
       for (long i = 0; i < n; ++i) z[k][(size_t)r * pitch + i] = rademacher(seed, t, k, probe_entry(i, r, rows));
 
-  long total = (long)(m + 0.5);  // sum over views of 3 H W
+  long total = 0;  // sum over views of 3 H W
+  for (const View& V : views) total += 3L * V.cam.W * V.cam.H;
   double f = 0.0;
   long img_off = 0;
   std::vector<double> g_acc(rows);
@@ -943,6 +1057,43 @@ double or_backward(const double* P, long pitch, long n, int deg, const double* c
       render_tangent(V, sd, jz[k].data());
       if (img_tan) std::memcpy(img_tan + (long)k * total + img_off, jz[k].data(), 3 * HW * sizeof(double));
     }
+    // D-SSIM: the whole image's cotangents first (SSIM couples neighbouring pixels)
+    std::vector<double> cw, cu;
+    if (loss_kind == 2) {
+      const int H = V.cam.H, W = V.cam.W;
+      std::vector<double> img(3 * HW, 0.0);
+      for_each_pixel(V, [&](int tx, int ty, int x, int y) {
+        double C[3], T;
+        int nc;
+        blend(V.lists[(size_t)ty * V.Tx + tx], V.sp, x + 0.5, y + 0.5, C, T, nc, nullptr, nullptr);
+        for (int ch = 0; ch < 3; ++ch) img[ch * HW + (long)y * W + x] = C[ch];
+      });
+      cw.assign(3 * HW, 0.0);
+      cu.assign((size_t)nu * 3 * HW, 0.0);
+      std::vector<double> ones(HW, 1.0), a(HW);
+      for (int ch = 0; ch < 3; ++ch) {
+        const double* xc = img.data() + ch * HW;
+        const double* yc = tg + ch * HW;
+        SsimMaps M = ssim_maps(xc, yc, H, W);
+        std::vector<double> gS = ssim_vjp(xc, yc, H, W, M, ones.data());
+        for (long px = 0; px < HW; ++px) {
+          const double r = xc[px] - yc[px];
+          f += ((1.0 - lambda) * std::fabs(r) + lambda * (1.0 - M.S[px])) / (2.0 * m);
+          cw[ch * HW + px] = ((1.0 - lambda) * (r > 0 ? 1.0 : (r < 0 ? -1.0 : 0.0)) - lambda * gS[px]) / (2.0 * m);
+        }
+        for (int k = 0; k < nu; ++k) {
+          const double* d = jz[k].data() + ch * HW;
+          std::vector<double> dS = ssim_jvp(xc, yc, H, W, M, d);
+          for (long px = 0; px < HW; ++px) a[px] = lambda / (4.0 * std::max(1.0 - M.S[px], gn_floor)) / m * dS[px];
+          std::vector<double> back = ssim_vjp(xc, yc, H, W, M, a.data());
+          for (long px = 0; px < HW; ++px) {
+            const double r = xc[px] - yc[px];
+            cu[((size_t)k * 3 + ch) * HW + px] =
+                (1.0 - lambda) / (4.0 * std::max(std::fabs(r), gn_floor)) / m * d[px] + back[px];
+          }
+        }
+      }
+    }
     for_each_pixel(V, [&](int tx, int ty, int x, int y) {
       double C[3], T;
       int nc;
@@ -953,7 +1104,10 @@ double or_backward(const double* P, long pitch, long n, int deg, const double* c
       for (int ch = 0; ch < 3; ++ch) {
         double r = C[ch] - tg[ch * HW + px];
         rmin = std::min(rmin, std::fabs(r));
-        if (loss_kind == 0) {
+        if (loss_kind == 2) {
+          w[ch] = cw[ch * HW + px];
+          wgn[ch] = 0.0;  // the probe vectors come whole from cu
+        } else if (loss_kind == 0) {
           f += std::fabs(r) / (2.0 * m);
           w[ch] = (r > 0 ? 1.0 : (r < 0 ? -1.0 : 0.0)) / (2.0 * m);
           wgn[ch] = 1.0 / (4.0 * std::max(std::fabs(r), gn_floor)) / m;
@@ -967,7 +1121,8 @@ double or_backward(const double* P, long pitch, long n, int deg, const double* c
       blend_reverse(tr, V.sp, w, cot[0].data());
       for (int k = 0; k < nu; ++k) {
         double wk[3];
-        for (int ch = 0; ch < 3; ++ch) wk[ch] = wgn[ch] * jz[k][ch * HW + px];
+        for (int ch = 0; ch < 3; ++ch)
+          wk[ch] = loss_kind == 2 ? cu[((size_t)k * 3 + ch) * HW + px] : wgn[ch] * jz[k][ch * HW + px];
         blend_reverse(tr, V.sp, wk, cot[1 + k].data());
       }
     });
@@ -989,6 +1144,40 @@ double or_backward(const double* P, long pitch, long n, int deg, const double* c
     img_off += 3 * HW;
   }
   return f;
+}
+
+double or_backward(const double* P, long pitch, long n, int deg, const double* cams, int n_views, int tw,
+                   int th, const double* target, int loss_kind, double gn_floor, uint64_t seed, int64_t t,
+                   int nu, double* grad, double* hz, double* img_tan, double* res_margin) {
+  return backward_impl(P, pitch, n, deg, cams, n_views, tw, th, target, loss_kind, 0.0, gn_floor, seed, t, nu,
+                       grad, hz, img_tan, res_margin);
+}
+
+double or_backward_dssim(const double* P, long pitch, long n, int deg, const double* cams, int n_views, int tw,
+                         int th, const double* target, double lambda, double gn_floor, uint64_t seed, int64_t t,
+                         int nu, double* grad, double* hz, double* img_tan) {
+  return backward_impl(P, pitch, n, deg, cams, n_views, tw, th, target, 2, lambda, gn_floor, seed, t, nu, grad, hz,
+                       img_tan, nullptr);
+}
+
+// SSIM map of one channel and its partials (for the pins), and the adjoint and
+// directional derivative of the map.
+void or_ssim(const double* x, const double* y, int H, int W, double* S, double* dmx, double* dex2, double* dexy) {
+  SsimMaps M = ssim_maps(x, y, H, W);
+  std::copy(M.S.begin(), M.S.end(), S);
+  if (dmx) std::copy(M.dmx.begin(), M.dmx.end(), dmx);
+  if (dex2) std::copy(M.dex2.begin(), M.dex2.end(), dex2);
+  if (dexy) std::copy(M.dexy.begin(), M.dexy.end(), dexy);
+}
+void or_ssim_vjp(const double* x, const double* y, int H, int W, const double* a, double* out) {
+  SsimMaps M = ssim_maps(x, y, H, W);
+  std::vector<double> g = ssim_vjp(x, y, H, W, M, a);
+  std::copy(g.begin(), g.end(), out);
+}
+void or_ssim_jvp(const double* x, const double* y, int H, int W, const double* d, double* out) {
+  SsimMaps M = ssim_maps(x, y, H, W);
+  std::vector<double> g = ssim_jvp(x, y, H, W, M, d);
+  std::copy(g.begin(), g.end(), out);
 }
 
 // Per-parameter trust-region radii (rows x n, row pitch n).
