@@ -268,6 +268,26 @@ gs_status gs_tr_update_dev(gs_params* x, gs_params* g_ema, gs_params* d_ema, con
                            const gs_params* hz, const gs_tr_config* cfg, const int64_t* t_device,
                            const gs_eps_schedule* schedule, gs_params* eta_out, int32_t* status, void* stream);
 
+/* Eq. pixel_loss of Sec. 3.2 with the D-SSIM term: per pixel and channel the two
+ * residual components F = sqrt((1 - lambda) |r|) and F = sqrt(lambda (1 - S)),
+ * S the SSIM of the channel at the pixel (11 x 11 Gaussian window of standard
+ * deviation 1.5, zeros outside the image, C1 = 0.01^2, C2 = 0.03^2), and
+ * m = 6 H W per view.  Writes the cotangent images that gs_raster_bwd and
+ * gs_hvp_diag take with GS_LOSS_COTANGENT (S = want_grad + nu streams,
+ * S x V x 3 x H x W):
+ *   dL/dC = ((1 - lambda) sign(r) - lambda sum_p dS_p/dC) / (2m)
+ *   u_k   = (1 - lambda)/(4 max(|r|, gn_floor))/m . d_k
+ *           + A[lambda/(4 max(1 - S, gn_floor))/m . dS[d_k]]
+ * with d_k = J z_k from image_tangent (nu x V x 3 x H x W; may be NULL when nu
+ * is 0), dS[d] the derivative of the SSIM map along d and A its adjoint.
+ * loss_out (one float, may be NULL) gets the objective added.  workspace from
+ * gs_dssim_workspace_size. */
+size_t gs_dssim_workspace_size(gs_frame frame, int32_t nu);
+gs_status gs_dssim_cotangents(gs_frame frame, const float* image, const float* target, const float* image_tangent,
+                              int32_t nu, float lambda, float gn_floor, int32_t want_grad, float* cot,
+                              float* loss_out, void* workspace, size_t workspace_bytes, int32_t* status,
+                              void* stream);
+
 /* Adam hyper-parameters of the ADAM-TR update: beta1, beta2, eps_adam and the
  * learning rate of each row group: lr[0] means, lr[1] log-scales, lr[2]
  * quaternions, lr[3] opacity logit, lr[4] SH DC (rows 11..13), lr[5] the other

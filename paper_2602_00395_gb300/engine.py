@@ -48,13 +48,14 @@ class TRStep:
     def __init__(self, n: int, sh_degree: int, n_views: int, width: int, height: int, *, nu: int = 1,
                  tile=(16, 16), capacity: int | None = None, loss_kind: int = G.GS_LOSS_L1,
                  gn_floor: float = 1e-3, cfg: TRConfig | None = None, probe_seed: int = 42,
-                 device: str = "cuda", state=None, zero_init: bool = True):
+                 device: str = "cuda", state=None, zero_init: bool = True, dssim_lambda: float | None = None):
         """state: optional (x, g_ema, d_ema) tensors of shape rows x n_pad that the
         step uses in place of its own (a scene's resident parameters and trust-region
         state, shared by the short-lived steps of a serving loop).  zero_init=False
         leaves the buffers that the calls overwrite before reading (records,
         images, gradient, curvature, target, cameras) uninitialised, which saves a
-        fill per buffer when steps are created per request."""
+        fill per buffer when steps are created per request.  dssim_lambda: the
+        pixel loss (1 - lambda) L1 + lambda D-SSIM of Eq. pixel_loss instead of L1."""
         G.load()
         self.n, self.deg, self.V, self.W, self.H, self.nu = n, sh_degree, n_views, width, height, nu
         self.n_pad = synth.pad_count(n)
@@ -95,6 +96,11 @@ class TRStep:
         self.n_pairs = torch.zeros(1, dtype=torch.int32, device=self.device)
         self.bwd_ws = torch.empty(G.gs_raster_bwd_workspace_size(self.n_pad, self.frame, nu), dtype=torch.uint8,
                                   device=self.device)
+        self.dssim_lambda = dssim_lambda
+        if dssim_lambda is not None:
+            self.cot_img = torch.empty((1 + nu) * n_views * 3 * HW, dtype=torch.float32, device=self.device)
+            self.dssim_ws = torch.empty(G.gs_dssim_workspace_size(self.frame, nu), dtype=torch.uint8,
+                                        device=self.device)
         self._alloc_pairs(capacity or max(1 << 16, 8 * n * n_views))
         self.t = 0
         self.t_dev = torch.zeros(1, dtype=torch.int64, device=self.device)  # step index of captured graphs
@@ -150,6 +156,13 @@ class TRStep:
 
     def raster_bwd(self, t: int | None = None, probes: bool = True, stream=None) -> None:
         pr = self.probe(t) if (probes and t is not None) else None
+        if self.dssim_lambda is not None:  # D-SSIM: the cotangent images first, then the reverse pass
+            nu = pr.nu if pr else 0
+            G.gs_dssim_cotangents(self.frame, self.image, self.target, self.image_tan if pr else None, nu,
+                                  self.dssim_lambda, self.loss.gn_floor, True, self.cot_img, self.loss_val,
+                                  self.dssim_ws, self.status, stream)
+            self.raster_bwd_cotangent(self.cot_img, t if pr else None, True, stream)
+            return
         G.gs_raster_bwd(self.P(self.x), self.cams, self.frame, self.proj(), self.sorted(), self.image, self.target,
                         self.final_T, self.n_contrib, self.image_tan if pr else None, pr, self.loss,
                         self.P(self.grad), self.P(self.hz) if pr else None, self.loss_val, self.bwd_ws,
@@ -172,6 +185,11 @@ class TRStep:
 
     def hvp_diag(self, t: int, stream=None) -> None:
         pr = self.probe(t)
+        if self.dssim_lambda is not None:
+            G.gs_dssim_cotangents(self.frame, self.image, self.target, self.image_tan, pr.nu, self.dssim_lambda,
+                                  self.loss.gn_floor, False, self.cot_img, None, self.dssim_ws, self.status, stream)
+            self.raster_bwd_cotangent(self.cot_img, t, False, stream)
+            return
         G.gs_hvp_diag(self.P(self.x), self.cams, self.frame, self.proj(), self.sorted(), self.image, self.target,
                       self.final_T, self.n_contrib, self.image_tan, pr, self.loss, self.P(self.hz), self.bwd_ws,
                       self.status, stream)

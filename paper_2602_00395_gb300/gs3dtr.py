@@ -24,7 +24,8 @@ GS_LOSS_L1, GS_LOSS_L2, GS_LOSS_COTANGENT = 0, 1, 2
 EXPORTED = ("gs_last_error", "gs_version", "gs_project", "gs_bin_sort_workspace_size", "gs_bin_sort",
             "gs_bin_sort_noalloc",
             "gs_raster_fwd", "gs_raster_bwd_workspace_size", "gs_raster_bwd", "gs_hvp_diag", "gs_tr_update",
-            "gs_tr_update_dev", "gs_step_advance", "gs_adam_tr_update")
+            "gs_tr_update_dev", "gs_step_advance", "gs_adam_tr_update", "gs_dssim_workspace_size",
+            "gs_dssim_cotangents")
 
 
 class gs_params(C.Structure):
@@ -138,6 +139,11 @@ def load():
                                        C.POINTER(gs_eps_schedule), C.POINTER(gs_params), P, P]
         L.gs_step_advance.restype = st
         L.gs_step_advance.argtypes = [P, P]
+        L.gs_dssim_workspace_size.restype = C.c_size_t
+        L.gs_dssim_workspace_size.argtypes = [gs_frame, C.c_int32]
+        L.gs_dssim_cotangents.restype = st
+        L.gs_dssim_cotangents.argtypes = [gs_frame, P, P, P, C.c_int32, C.c_float, C.c_float, C.c_int32, P, P, P,
+                                          C.c_size_t, P, P]
         L.gs_adam_tr_update.restype = st
         L.gs_adam_tr_update.argtypes = [C.POINTER(gs_params), C.POINTER(gs_params), C.POINTER(gs_params),
                                         C.POINTER(gs_params), C.POINTER(gs_tr_config), C.POINTER(gs_adam_config),
@@ -283,3 +289,16 @@ def gs_adam_tr_update(x: gs_params, m: gs_params, v: gs_params, grad: gs_params,
     check(L.gs_adam_tr_update(C.byref(x), C.byref(m), C.byref(v), C.byref(grad), C.byref(cfg), C.byref(adam), t,
                               eps, C.byref(eta_out) if eta_out else None, ptr(status), stream_handle(stream)),
           "gs_adam_tr_update")
+
+
+def gs_dssim_workspace_size(frame: gs_frame, nu: int) -> int:
+    return int(load().gs_dssim_workspace_size(frame, nu))
+
+
+def gs_dssim_cotangents(frame: gs_frame, image, target, image_tangent, nu: int, lam: float, gn_floor: float,
+                        want_grad: bool, cot, loss_out, workspace, status=None, stream=None) -> None:
+    L = load()
+    check(L.gs_dssim_cotangents(frame, ptr(image), ptr(target), ptr(image_tangent), nu, lam, gn_floor,
+                                int(want_grad), ptr(cot), ptr(loss_out), ptr(workspace),
+                                workspace.numel() * workspace.element_size(), ptr(status), stream_handle(stream)),
+          "gs_dssim_cotangents")

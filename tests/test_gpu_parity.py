@@ -411,3 +411,35 @@ def test_adam_tr_update_matches_oracle(deg, t):
     dx_ref = rx - P32[:, :n]
     tol = 1e-4 * np.abs(dx_ref) + 2e-7 * np.abs(P32[:, :n]) + 1e-12
     assert np.all(np.abs(dx_gpu - dx_ref) <= tol)
+
+
+@pytest.mark.parametrize("case,nu", [("cfg1", 1), ("ragged", 2)])
+def test_dssim_gradient_and_hutchinson_match_oracle(case, nu):
+    """The D-SSIM pixel loss (Eq. pixel_loss, lambda = 0.2): objective, gradient and
+    Hutchinson diagonal through gs_dssim_cotangents and the reverse pass."""
+    sc, cams = _cfg1() if case == "cfg1" else _ragged()
+    V, H, W = len(cams), cams[0].height, cams[0].width
+    target = S.smooth_target(V, H, W, seed=2002)
+    e = _engine(sc.n, sc.sh_degree, cams, nu=nu, dssim_lambda=0.2)
+    e.set_params(sc.params)
+    e.set_target(target)
+    e.ensure_capacity()
+    t = 5
+    e.loss_val.zero_()
+    e.project(t, probes=True)
+    e.bin_sort()
+    e.raster_fwd(t, probes=True)
+    e.raster_bwd(t, probes=True)
+    torch.cuda.synchronize()
+    assert e.read_status() == 0
+    ref = O.backward(O.params64(sc), sc.sh_degree, cams, target.astype(np.float64), loss_kind=2, lam=0.2, seed=42,
+                     t=t, nu=nu)
+    assert abs(float(e.loss_val.item()) - ref["loss"]) <= 1e-5 * ref["loss"]
+    _group_close(e.grad[:, : sc.n].cpu().numpy(), ref["grad"], 1e-4, "grad")
+    _group_close(e.hz[:, : sc.n].cpu().numpy(), ref["hz"], 1e-3, "hz")
+    fused = e.hz.clone()
+    e.hz.fill_(7.0)
+    e.hvp_diag(t)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(e.hz[:, : sc.n].cpu().numpy(), fused[:, : sc.n].cpu().numpy(), rtol=1e-5,
+                               atol=1e-6 * fused.abs().max().item())
