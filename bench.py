@@ -387,6 +387,67 @@ def curvature_costs(eng, cam_dev, targets, K, stream):
             "overhead_l10": l10_ms / grad_ms - 1.0}
 
 
+# ------------------------------------------------------------------ variants
+def variant_costs(eng, cam_dev, targets, K, stream):
+    """ms per step, same workload, of (a) ADAM-TR (Sec. 5 ablation: gradient
+    only, Adam step clipped by the trust region) and (b) Algorithm 1 with the
+    pixel loss (1 - 0.2) L1 + 0.2 D-SSIM (Eq. pixel_loss), with the time of the
+    D-SSIM cotangent call alone."""
+    import torch
+    from paper_2602_00395_gb300 import gs3dtr as G
+    from paper_2602_00395_gb300.engine import eps_schedule
+    nb = len(targets)
+    adam = G.adam_struct()
+
+    def timed(fn, t0):
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            for k in range(2):
+                fn(t0 + k)
+            ev0.record(stream)
+            for k in range(K):
+                fn(t0 + k)
+            ev1.record(stream)
+        ev1.synchronize()
+        return ev0.elapsed_time(ev1) / K
+
+    def batch(t):
+        b = (t - 1) % nb
+        eng.cams, eng.target = cam_dev[b], targets[b]
+
+    def adam_step(t):
+        batch(t)
+        eng.step_adam(t, eps_schedule(t, 30000), adam, stream)
+
+    def dssim_step(t):
+        batch(t)
+        eng.step(t, eps_schedule(t, 30000), stream)
+
+    out = {"adam_tr_ms": timed(adam_step, 6000)}
+    HW = W * H
+    eng.dssim_lambda = 0.2
+    eng.cot_img = torch.empty((1 + NU) * N_VIEWS * 3 * HW, dtype=torch.float32, device=eng.device)
+    eng.dssim_ws = torch.empty(G.gs_dssim_workspace_size(eng.frame, NU), dtype=torch.uint8, device=eng.device)
+    try:
+        out["dssim_l1_mix_ms"] = timed(dssim_step, 7000)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            ev0.record(stream)
+            for _ in range(K):
+                G.gs_dssim_cotangents(eng.frame, eng.image, eng.target, eng.image_tan, NU, 0.2, eng.loss.gn_floor,
+                                      True, eng.cot_img, eng.loss_val, eng.dssim_ws, eng.status, stream)
+            ev1.record(stream)
+        ev1.synchronize()
+        out["dssim_cotangents_ms"] = ev0.elapsed_time(ev1) / K
+    finally:
+        eng.dssim_lambda = None
+        del eng.cot_img, eng.dssim_ws
+        torch.cuda.empty_cache()
+    return out
+
+
 # ------------------------------------------------------------------ serving
 def served_metrics(device, n_requests=200, slots=16, budget_gb=40.0):
     """The served multi-scene workload: 16 resident scenes (50k-2M Gaussians, SH 3,
@@ -572,6 +633,7 @@ def run_cuda(args):
     e2e_val = ws * args.steps / (e2e_ms / 1e3)
     # the cost of curvature: gradient-only steps, and l = 10 with S2 != S1
     curv = curvature_costs(eng, cam_dev, targets, 20, stream)
+    variants = variant_costs(eng, cam_dev, targets, 10, stream)
     # the plain one-view-at-a-time loop on the same workload
     plain_ms = plain_loop_steps(eng, cam_dev, targets, max(3, min(args.steps, 10)), 9000, stream, device)
     # roofline of the dominant call
@@ -653,6 +715,7 @@ def run_cuda(args):
                       "what": "the same steps as six C-ABI calls issued from the host per step, no graph"},
             "graph": "one captured CUDA graph per view batch, step index and eps_t on the device",
             "curvature": {**curv, "l1_fused_ms": ms_per_step, "overhead_l1_fused": ms_per_step / curv["gradient_only_ms"] - 1.0},
+            "variants": variants,
             "gpu_launches": kernel_launches_per_step(eng) * args.steps,
             "roofline": roof, "roofline_calls": roof_calls, "clocks": clocks, "cpu_baseline": cpu,
             "served": None,
