@@ -353,9 +353,11 @@ struct BwdPixel {
 };
 
 // The reverse of one splat at one pixel: recover T_i = T_{i+1}/(1 - a),
-// dC/da = c T_i - suffix/(1 - a), and store (FIRST) or add the pixel's
-// derivatives of the splat's (mx, my, A, B, C, o, r, g, b) for every stream in
-// v.  A pixel the splat is not blended at passes alpha = G = oG = 0: its state
+// dC/da = c T_i - suffix/(1 - a), and store (FIRST) or add, for every stream,
+// the pixel's terms of the splat's cotangent row in v: the moments
+// (dx g, dy g, dx^2 g, dx dy g, dy^2 g) of g = dL/d(power), then dL/do,
+// dL/d(r, g, b).  power = -(A dx^2 + C dy^2)/2 - B dx dy, so dL/dA = -M2/2,
+// dL/dB = -M3, dL/dC = -M4/2, dL/dmx = -(A M0 + B M1), dL/dmy = -(B M0 + C M1).  A pixel the splat is not blended at passes alpha = G = oG = 0: its state
 // stays as it is and it contributes exact zeros, so the pixels of a thread need
 // no branches.  One reciprocal of 1 - a serves the four quotients.
 template <int S, bool FIRST>
@@ -372,14 +374,17 @@ __device__ __forceinline__ void bwd_accumulate(BwdPixel<S>& p, const Rec& r, flo
   p.suf[1] += rgb1 * aT;
   p.suf[2] += rgb2 * aT;
   p.T = Ti;
+  // a capped alpha has zero derivative: both of its factors vanish at once
   const bool capped = oG > kAlphaMax;
-  const float fmx = -(r.a.z * dx + r.a.w * dy), fmy = -(r.b.x * dy + r.a.w * dx);
-  const float fA = -0.5f * dx * dx, fB = -dx * dy, fC = -0.5f * dy * dy;
+  const float ac = capped ? 0.f : alpha, Gc = capped ? 0.f : G;
+  const float dxx = dx * dx, dxy = dx * dy, dyy = dy * dy;
 #pragma unroll
   for (int s = 0; s < S; ++s) {
     const float ga = p.w[s][0] * da0 + p.w[s][1] * da1 + p.w[s][2] * da2;
-    const float gp = capped ? 0.f : ga * alpha;
-    const float c[9] = {fmx * gp, fmy * gp, fA * gp, fB * gp, fC * gp, capped ? 0.f : ga * G,
+    const float gp = ga * ac;  // dL/d(power)
+    // the power's partials are linear in the conic, so the warp sums moments of
+    // (dx, dy) and the projection's reverse pass applies the conic
+    const float c[9] = {dx * gp, dy * gp, dxx * gp, dxy * gp, dyy * gp, ga * Gc,
                         p.w[s][0] * aT, p.w[s][1] * aT, p.w[s][2] * aT};
 #pragma unroll
     for (int q = 0; q < 9; ++q) {
@@ -719,9 +724,13 @@ __global__ void GS_PBWD_BOUNDS project_bwd_kernel(const float* __restrict__ P, i
     const float dJ02_dtx = clx ? 0.f : -fx * itz2, dJ12_dty = cly ? 0.f : -fy * itz2;
     const float dJ02_dtz = clx ? fx * uc * itz2 : 2.f * fx * t[0] * itz3;
     const float dJ12_dtz = cly ? fy * vc * itz2 : 2.f * fy * t[1] * itz3;
+    // conic of this view, to turn the blend's moments into dL/d(mx, my, A, B, C)
+    const float cA = cc * idet, cB = -bb * idet, cCc = a * idet;
 #pragma unroll
     for (int st = 0; st < S; ++st) {
-      const float* cs = c + 9 * st;
+      const float* mo = c + 9 * st;
+      const float cs[5] = {-(cA * mo[0] + cB * mo[1]), -(cB * mo[0] + cCc * mo[1]), -0.5f * mo[2], -mo[3],
+                           -0.5f * mo[4]};
       const float gA = cs[2], gB = cs[3], gC = cs[4];
       const float ga = gA * (-cc * cc * id2) + gB * (bb * cc * id2) + gC * (idet - a * cc * id2);
       const float gb = gA * (2.f * bb * cc * id2) + gB * (-idet - 2.f * bb * bb * id2) + gC * (2.f * a * bb * id2);
@@ -753,7 +762,7 @@ __global__ void GS_PBWD_BOUNDS project_bwd_kernel(const float* __restrict__ P, i
         for (int q = 0; q < 3; ++q)
           g_S[st][p2][q] += tmp[0] * vg.Rc[0][q] + tmp[1] * vg.Rc[1][q] + tmp[2] * vg.Rc[2][q];
       }
-      g_ol[st] += cs[5] * dsig;
+      g_ol[st] += mo[5] * dsig;
     }
     // colour: clamp decisions, and the dependence of colour on mu through the view direction
     float d[3], dn;
