@@ -283,15 +283,6 @@ __device__ __forceinline__ void sh_basis_grad(float x, float y, float z, const f
   }
 }
 
-// A read-only global load the compiler may neither hoist out of a loop nor
-// merge with another: used for parameters re-read per view so that they do not
-// occupy registers across the view loop.
-__device__ __forceinline__ float ld_once(const float* p) {
-  float v;
-  asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(v) : "l"(p));
-  return v;
-}
-
 // ------------------------------------------------------ footprint extents
 // Half-extents of the bounding box of a splat's alpha >= 1/255 footprint, kept
 // in the last word of its record for the rasteriser's per-block visibility test.

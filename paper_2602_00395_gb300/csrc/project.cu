@@ -29,7 +29,7 @@ __device__ __forceinline__ void store_culled(float4* rec, size_t at) {
 
 // Minimum resident CTAs per SM requested for the projection (0: none).
 #ifndef GS_PROJ_MIN_BLOCKS
-#define GS_PROJ_MIN_BLOCKS 3
+#define GS_PROJ_MIN_BLOCKS 4
 #endif
 #if GS_PROJ_MIN_BLOCKS > 0
 #define GS_PROJ_BOUNDS __launch_bounds__(128, GS_PROJ_MIN_BLOCKS)
@@ -46,6 +46,12 @@ __global__ void GS_PROJ_BOUNDS project_kernel(const float* __restrict__ P, int n
   constexpr int K = (DEG + 1) * (DEG + 1);
   constexpr int ROWS = kRowSH + 3 * K;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  // the block's SH coefficients, staged once and read per view from shared
+  // memory (volatile: re-read, not held in registers across the view loop)
+  __shared__ float s_sh[3 * K][128];
+  for (int r = 0; r < 3 * K; ++r) s_sh[r][threadIdx.x] = i < n ? P[(size_t)(kRowSH + r) * n_pad + i] : 0.f;
+  __syncthreads();
+  const volatile float* vsh = &s_sh[0][0];
   if (i >= n_pad) return;
   const int V = fr.n_views;
   if (i >= n) {
@@ -170,7 +176,7 @@ __global__ void GS_PROJ_BOUNDS project_kernel(const float* __restrict__ P, int n
     S Y[K];
     sh_basis<DEG>(d0, d1, d2, Y);
     // rgb = 0.5 + sum_k Y_k sh_k; the coefficients are plain parameters whose
-    // probe tangents are the signs z, re-read per view (ld_once)
+    // probe tangents are the signs z, read per view from the staged copy
     S rgb[3];
 #pragma unroll
     for (int ch = 0; ch < 3; ++ch) {
@@ -178,7 +184,7 @@ __global__ void GS_PROJ_BOUNDS project_kernel(const float* __restrict__ P, int n
 #pragma unroll
       for (int k = 0; k < K; ++k) {
         const int row = kRowSH + 3 * k + ch;
-        const float sh = ld_once(P + (size_t)row * n_pad + i);
+        const float sh = vsh[(3 * k + ch) * 128 + threadIdx.x];
         if constexpr (NU == 0) {
           acc = acc + Y[k] * sh;
         } else {
@@ -212,7 +218,7 @@ __global__ void GS_PROJ_BOUNDS project_kernel(const float* __restrict__ P, int n
 template <int DEG, int NU>
 void launch_project(const gs_params* x, const gs_camera* cams, gs_frame fr, ProbeArg pa, gs_projected* out,
                     cudaStream_t st) {
-  const int threads = 128;
+  const int threads = 128;  // the kernel's shared staging is sized for 128 threads
   const int blocks = (x->n_pad + threads - 1) / threads;
   project_kernel<DEG, NU><<<blocks, threads, 0, st>>>(x->data, x->n, x->n_pad, cams, fr, pa,
                                                       reinterpret_cast<float4*>(out->rec),

@@ -618,6 +618,13 @@ __global__ void GS_PBWD_BOUNDS project_bwd_kernel(const float* __restrict__ P, i
   constexpr int NVP = cot_stride(S);
   constexpr int K = (DEG + 1) * (DEG + 1);
   const int i = blockIdx.x * kPbwdThreads + threadIdx.x;
+  // the block's SH coefficients, staged once and read per view from shared
+  // memory (volatile: re-read, not held in registers across the view loops)
+  __shared__ float s_sh[3 * K][kPbwdThreads];
+  for (int r = 0; r < 3 * K; ++r) s_sh[r][threadIdx.x] = i < n ? P[(size_t)(kRowSH + r) * n_pad + i] : 0.f;
+  __syncthreads();
+  const volatile float* vsh = &s_sh[0][0];
+  auto sh_of = [&](int k, int ch) { return vsh[(3 * k + ch) * kPbwdThreads + threadIdx.x]; };
   if (i >= n) return;
   const uint64_t seed = pa.seed;
   const int64_t step = NU > 0 ? probe_step(pa) : 0;
@@ -771,14 +778,14 @@ __global__ void GS_PBWD_BOUNDS project_bwd_kernel(const float* __restrict__ P, i
     sh_basis<DEG>(d[0], d[1], d[2], Y);
     // per channel: the raw colour (its clamp decision) and, for the colour's
     // dependence on mu, the direction gradient of sum_k sh_k Y_k; the SH
-    // coefficients are re-read per view (ld_once) instead of held in registers
+    // coefficients come from the staged copy instead of registers
     bool clamped[3];
     float gdc[3][3];
 #pragma unroll
     for (int ch = 0; ch < 3; ++ch) {
       float shc[K];
 #pragma unroll
-      for (int k = 0; k < K; ++k) shc[k] = ld_once(P + (size_t)(kRowSH + 3 * k + ch) * n_pad + i);
+      for (int k = 0; k < K; ++k) shc[k] = sh_of(k, ch);
       float raw = 0.5f;
 #pragma unroll
       for (int k = 0; k < K; ++k) raw += Y[k] * shc[k];
@@ -884,7 +891,7 @@ __global__ void GS_PBWD_BOUNDS project_bwd_kernel(const float* __restrict__ P, i
         for (int ch = 0; ch < 3; ++ch) {
           float raw = 0.5f;
 #pragma unroll
-          for (int k = 0; k < K; ++k) raw += Y[k] * ld_once(P + (size_t)(kRowSH + 3 * k + ch) * n_pad + i);
+          for (int k = 0; k < K; ++k) raw += Y[k] * sh_of(k, ch);
           if (raw < 0.f) gcol[ch] = 0.f;
         }
       }
