@@ -121,8 +121,9 @@ typedef struct gs_eps_schedule {
  *            (0: culled) and extents packs two IEEE half floats (x low, y high):
  *            half-widths of the bounding box of the alpha >= 1/255 footprint
  *            d^T (A B; B C) d <= 2 ln(255 opacity), widened by 0.1% + 0.01 px and
- *            rounded up (-inf: no pixel reaches 1/255; +inf: unbounded).  The
- *            rasteriser skips a splat for an 8 x 8 pixel block outside that box.
+ *            rounded up (-inf: no pixel reaches 1/255; +inf: unbounded).
+ *            Binning narrows the splat's tile square to that box, and the
+ *            rasteriser skips the splat for an 8 x 8 pixel block outside it.
  *   tangent: NULL or V x nu x n_pad records of 12 floats, the forward-mode
  *            derivative of (mx, my, A, B, C, opacity, r, g, b) along probe k */
 typedef struct gs_projected {
@@ -176,15 +177,20 @@ typedef struct gs_tr_config {
  *   Sigma' = J W Sigma W^T J^T + 0.3 I (J the perspective Jacobian with the
  *   image-plane slope clamped at 1.3 x the half field of view), conic = Sigma'^-1,
  *   radius = ceil(3 sqrt(lambda_max)), rgb = max(SH(view dir) + 0.5, 0),
- *   opacity = sigmoid(logit), tile rectangle decided in FP32:
- *   x0 = clamp(floor((mx - r)/tw), 0, Tx), x1 = clamp(floor((mx + (r+tw-1))/tw), 0, Tx).
+ *   opacity = sigmoid(logit), and the footprint extents described with gs_projected.
  * cams: device array of frame.n_views cameras.  probe may be NULL (no tangents);
  * otherwise out->tangent receives probe->nu tangent records per view. */
 gs_status gs_project(const gs_params* x, const gs_camera* cams, gs_frame frame, const gs_probe* probe,
                      gs_projected* out, int32_t* status, void* stream);
 
 /* Sec. 3.1 tile binning and depth order: all (tile, splat) pairs of all views
- * sorted by (key, splat index), and each tile's [start, end).  If the pairs
+ * sorted by (key, splat index), and each tile's [start, end).  A splat's tiles
+ * are its 3DGS square intersected with its footprint box, decided in FP32 with
+ * one rounding per operation (hx, hy the record's extents; the same for y):
+ *   x0 = clamp(max(floor((mx - r)/tw), floor((mx - hx)/tw)), 0, Tx)
+ *   x1 = clamp(min(floor((mx + (r + tw - 1))/tw), floor((mx + hx)/tw) + 1), 0, Tx).
+ * A tile outside the box holds no pixel where the splat is blended (its alpha
+ * stays below 1/255 there), so the box removes pairs but changes no image.  If the pairs
  * exceed out->capacity, GS_FLAG_CAPACITY is raised, *n_pairs holds the need,
  * and the sorted arrays are incomplete (but every access stays in bounds and
  * every range end is at most the capacity). */

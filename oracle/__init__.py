@@ -52,7 +52,7 @@ def lib():
             L.or_quat_to_rotmat.argtypes = [P, P]
             L.or_project.argtypes = [P, i64, i64, i32, P, P]
             L.or_bin_sort.restype = i64
-            L.or_bin_sort.argtypes = [i32, i64, P, P, P, P, i32, i32, i32, i32, P, P, i64, P]
+            L.or_bin_sort.argtypes = [i32, i64, P, P, P, P, P, i32, i32, i32, i32, P, P, i64, P]
             L.or_render.restype = i64
             L.or_render.argtypes = [P, i64, i64, i32, P, i32, i32, i32, P, P, P, P]
             L.or_jvp.argtypes = [P, i64, i64, i32, P, i32, i32, i32, P, P]
@@ -179,20 +179,25 @@ def probe_matrix(seed: int, t: int, k: int, rows: int, n: int) -> np.ndarray:
     return z.reshape(n, rows).T.copy()
 
 
-def bin_sort(mx, my, radius, depth, width: int, height: int, tw: int = 16, th: int = 16):
-    """Pairs and tile ranges from FP32 splat records; arrays are [V, n] (or [n])."""
+def bin_sort(mx, my, radius, depth, width: int, height: int, tw: int = 16, th: int = 16, extents=None):
+    """Pairs and tile ranges from FP32 splat records; arrays are [V, n] (or [n]).
+    `extents` are the records' footprint half-extents as packed halves (uint32,
+    x in the low 16 bits), None for unbounded."""
     mx = np.ascontiguousarray(np.atleast_2d(mx), np.float32)
     my = np.ascontiguousarray(np.atleast_2d(my), np.float32)
     rad = np.ascontiguousarray(np.atleast_2d(radius), np.int32)
     dp = np.ascontiguousarray(np.atleast_2d(depth), np.float32)
+    ext = None if extents is None else np.ascontiguousarray(np.atleast_2d(extents), np.uint32)
     V, n = mx.shape
     T = ((width + tw - 1) // tw) * ((height + th - 1) // th)
     ranges = np.zeros((V * T, 2), np.uint32)
     L = lib()
-    P = L.or_bin_sort(V, n, _p(mx), _p(my), _p(rad), _p(dp), width, height, tw, th, None, None, 0, _p(ranges))
+    pe = None if ext is None else _p(ext)
+    P = L.or_bin_sort(V, n, _p(mx), _p(my), _p(rad), pe, _p(dp), width, height, tw, th, None, None, 0, _p(ranges))
     keys = np.zeros(max(P, 1), np.uint64)
     vals = np.zeros(max(P, 1), np.uint32)
-    L.or_bin_sort(V, n, _p(mx), _p(my), _p(rad), _p(dp), width, height, tw, th, _p(keys), _p(vals), P, _p(ranges))
+    L.or_bin_sort(V, n, _p(mx), _p(my), _p(rad), pe, _p(dp), width, height, tw, th, _p(keys), _p(vals), P,
+                  _p(ranges))
     return keys[:P], vals[:P], ranges
 
 

@@ -265,25 +265,85 @@ Splat<S> project(const G3<S>& g, const Cam& cam) {
 }
 
 // ---------------------------------------------------------------- binning
-// Tile rectangle [x0, x1) x [y0, y1) of a splat, decided in FP32 from FP32 inputs:
+// Value of the IEEE half with bits h, as a float (exact).
+float half_to_float(uint16_t h) {
+  const int e = (h >> 10) & 31, m = h & 1023;
+  float v;
+  if (e == 31)
+    v = m ? NAN : INFINITY;
+  else if (e == 0)
+    v = std::ldexp((float)m, -24);
+  else
+    v = std::ldexp((float)(m | 1024), e - 25);
+  return (h & 0x8000) ? -v : v;
+}
+
+// Smallest half-precision value >= x (x >= 0), as a float; +inf above 65504.
+float half_round_up(double x) {
+  if (!(x <= 65504.0)) return INFINITY;
+  if (x <= 0.0) return 0.0f;
+  int e;
+  std::frexp(x, &e);  // x in [2^(e-1), 2^e)
+  const double q = e - 1 < -14 ? std::ldexp(1.0, -24) : std::ldexp(1.0, e - 11);
+  const double r = std::ceil(x / q) * q;
+  return r > 65504.0 ? INFINITY : (float)r;
+}
+
+// Half-extents of the box around a splat's alpha >= 1/255 footprint.  Sec. 3.1
+// skips a splat at a pixel where o G < 1/255, i.e. outside the ellipse
+// d^T Q d <= tau with tau = 2 ln(255 o) and Q the conic [[A, B], [B, C]]; the box
+// of that ellipse has half-widths sqrt(tau C / det Q) and sqrt(tau A / det Q).
+// They are widened by 0.1% + 0.01 px and rounded up to half precision, the form
+// in which the rasteriser keeps them; tau <= 0 gives -inf (no pixel reaches
+// 1/255), a non-finite half-width +inf.  `s` scales tau and the ratios by
+// (1 + s) (s < 0 shrinks): the rounding envelope of an FP32 evaluation.
+void footprint_half_extents(double A, double B, double C, double o, double s, float& hx, float& hy) {
+  const double tau0 = 2.0 * std::log(255.0 * o);
+  const double tau = tau0 + s * (std::fabs(tau0) + 1.0);
+  if (!(tau > 0.0)) {
+    hx = hy = -INFINITY;
+    return;
+  }
+  const double det = A * C - B * B;
+  const double ex = std::sqrt(tau * C / det * (1.0 + s)), ey = std::sqrt(tau * A / det * (1.0 + s));
+  if (!(ex < 1e30) || !(ey < 1e30)) {
+    hx = hy = INFINITY;
+    return;
+  }
+  hx = half_round_up(ex * 1.001 + 0.01);
+  hy = half_round_up(ey * 1.001 + 0.01);
+}
+
+// Tile rectangle [x0, x1) x [y0, y1) of a splat, decided in FP32 from FP32 inputs.
+// The 3DGS rule (Sec. 3.1) takes the tiles of the square of half-width r around
+// the centre:
 //   x0 = clamp(floor((mx - r) / tw), 0, Tx),  x1 = clamp(floor((mx + (r + tw - 1)) / tw), 0, Tx)
-// (and the same for y).  Each FP32 operation below rounds once.
-void rect_f32(float mx, float my, int r, int tw, int th, int Tx, int Ty, int& x0, int& x1,
+// (and the same for y); it is intersected with the tiles that the footprint box
+// [mx - hx, mx + hx] x [my - hy, my + hy] reaches:
+//   x0 >= floor((mx - hx) / tw),  x1 <= floor((mx + hx) / tw) + 1.
+// A tile outside that box has no pixel where the splat is blended, so the
+// intersection changes no image.  Each FP32 operation below rounds once.
+void rect_f32(float mx, float my, int r, float hx, float hy, int tw, int th, int Tx, int Ty, int& x0, int& x1,
               int& y0, int& y1) {
   volatile float lo_x = mx - (float)r;
   volatile float hi_x = mx + (float)(r + tw - 1);
   volatile float lo_y = my - (float)r;
   volatile float hi_y = my + (float)(r + th - 1);
+  volatile float flo_x = mx - hx, fhi_x = mx + hx;
+  volatile float flo_y = my - hy, fhi_y = my + hy;
   float qx0 = lo_x / (float)tw, qx1 = hi_x / (float)tw;
   float qy0 = lo_y / (float)th, qy1 = hi_y / (float)th;
-  auto cl = [](float q, int hi) {
-    float f = std::floor(q);
+  float fx0 = flo_x / (float)tw, fx1 = fhi_x / (float)tw;
+  float fy0 = flo_y / (float)th, fy1 = fhi_y / (float)th;
+  auto cl = [](float f, int hi) {
     if (!(f > 0.0f)) return 0;  // also maps NaN to 0
     if (f > (float)hi) return hi;
     return (int)f;
   };
-  x0 = cl(qx0, Tx); x1 = cl(qx1, Tx);
-  y0 = cl(qy0, Ty); y1 = cl(qy1, Ty);
+  x0 = std::max(cl(std::floor(qx0), Tx), cl(std::floor(fx0), Tx));
+  x1 = std::min(cl(std::floor(qx1), Tx), cl(std::floor(fx1) + 1.0f, Tx));
+  y0 = std::max(cl(std::floor(qy0), Ty), cl(std::floor(fy0), Ty));
+  y1 = std::min(cl(std::floor(qy1), Ty), cl(std::floor(fy1) + 1.0f, Ty));
 }
 
 uint32_t f32_bits(float f) {
@@ -300,7 +360,7 @@ struct Pair {
 // All (tile, splat) pairs of all views, sorted by (key, splat index); key =
 // (view * tiles_per_view + tile) << 32 | bits(depth).
 std::vector<Pair> bin_and_sort(int n_views, long n, const float* mx, const float* my, const int* rad,
-                               const float* depth, int W, int H, int tw, int th) {
+                               const float* hx, const float* hy, const float* depth, int W, int H, int tw, int th) {
   int Tx = (W + tw - 1) / tw, Ty = (H + th - 1) / th;
   long T = (long)Tx * Ty;
   std::vector<Pair> pairs;
@@ -309,7 +369,7 @@ std::vector<Pair> bin_and_sort(int n_views, long n, const float* mx, const float
       long gi = (long)v * n + i;
       if (rad[gi] <= 0) continue;
       int x0, x1, y0, y1;
-      rect_f32(mx[gi], my[gi], rad[gi], tw, th, Tx, Ty, x0, x1, y0, y1);
+      rect_f32(mx[gi], my[gi], rad[gi], hx[gi], hy[gi], tw, th, Tx, Ty, x0, x1, y0, y1);
       for (int ty = y0; ty < y1; ++ty)
         for (int tx = x0; tx < x1; ++tx) {
           uint64_t tile = (uint64_t)v * T + (uint64_t)ty * Tx + tx;
@@ -337,10 +397,13 @@ struct View {
 
 // Rounding envelopes of the FP32 inputs of a binning decision: the radius
 // (3 sqrt(lambda_max) from a chain of FP32 products, ~1e-6 relative, widened
-// 10x) and the splat centre (a few FP32 ulps of its coordinate).
+// 10x), the splat centre (a few FP32 ulps of its coordinate) and the footprint
+// half-extents (tau and the conic ratios to 1e-4, plus the cancellation in the
+// conic's determinant at FP32 precision).
 const double kAmbRel = 1e-5;
 const double kAmbCentreRel = 1e-6;
 const double kAmbCentreAbs = 1e-5;
+const double kAmbExtRel = 1e-4;
 
 View build_view(const double* P, long pitch, long n, int deg, const double* cam24, int tw, int th) {
   View V;
@@ -349,7 +412,7 @@ View build_view(const double* P, long pitch, long n, int deg, const double* cam2
   V.Tx = (V.cam.W + tw - 1) / tw;
   V.Ty = (V.cam.H + th - 1) / th;
   V.sp.resize(n);
-  std::vector<float> mx(n), my(n), dp(n);
+  std::vector<float> mx(n), my(n), dp(n), hx(n), hy(n);
   std::vector<int> rad(n);
   V.lo.assign(4 * n, 0);
   V.hi.assign(4 * n, 0);
@@ -360,6 +423,12 @@ View build_view(const double* P, long pitch, long n, int deg, const double* cam2
     mx[i] = (float)s.mx; my[i] = (float)s.my; dp[i] = (float)s.depth;
     rad[i] = s.valid ? s.radius : 0;
     if (!s.valid) continue;
+    footprint_half_extents(s.A, s.B, s.C, s.o, 0.0, hx[i], hy[i]);
+    const double cancel = (s.A * s.C + s.B * s.B) / std::fabs(s.A * s.C - s.B * s.B);
+    const double se = kAmbExtRel + 1e-6 * (std::isfinite(cancel) ? cancel : 1e30);
+    float hx_lo, hy_lo, hx_hi, hy_hi;
+    footprint_half_extents(s.A, s.B, s.C, s.o, -se, hx_lo, hy_lo);
+    footprint_half_extents(s.A, s.B, s.C, s.o, se, hx_hi, hy_hi);
     double rr = s.radius_raw;
     int r_lo = (int)std::ceil(rr * (1.0 - kAmbRel) - 1e-6);
     int r_hi = (int)std::ceil(rr * (1.0 + kAmbRel) + 1e-6);
@@ -367,15 +436,15 @@ View build_view(const double* P, long pitch, long n, int deg, const double* cam2
     double ey = kAmbCentreRel * (std::fabs(s.my) + rr + th) + kAmbCentreAbs;
     int a0, a1, b0, b1, c0, c1, d0, d1;
     // shrunk rectangle: lower edges from the centre moved up, upper edges from it moved down
-    rect_f32((float)(s.mx + ex), (float)(s.my + ey), r_lo, tw, th, V.Tx, V.Ty, a0, a1, b0, b1);
-    rect_f32((float)(s.mx - ex), (float)(s.my - ey), r_lo, tw, th, V.Tx, V.Ty, c0, c1, d0, d1);
+    rect_f32((float)(s.mx + ex), (float)(s.my + ey), r_lo, hx_lo, hy_lo, tw, th, V.Tx, V.Ty, a0, a1, b0, b1);
+    rect_f32((float)(s.mx - ex), (float)(s.my - ey), r_lo, hx_lo, hy_lo, tw, th, V.Tx, V.Ty, c0, c1, d0, d1);
     V.lo[4 * i + 0] = a0; V.lo[4 * i + 1] = c1; V.lo[4 * i + 2] = b0; V.lo[4 * i + 3] = d1;
-    rect_f32((float)(s.mx - ex), (float)(s.my - ey), r_hi, tw, th, V.Tx, V.Ty, a0, a1, b0, b1);
-    rect_f32((float)(s.mx + ex), (float)(s.my + ey), r_hi, tw, th, V.Tx, V.Ty, c0, c1, d0, d1);
+    rect_f32((float)(s.mx - ex), (float)(s.my - ey), r_hi, hx_hi, hy_hi, tw, th, V.Tx, V.Ty, a0, a1, b0, b1);
+    rect_f32((float)(s.mx + ex), (float)(s.my + ey), r_hi, hx_hi, hy_hi, tw, th, V.Tx, V.Ty, c0, c1, d0, d1);
     V.hi[4 * i + 0] = a0; V.hi[4 * i + 1] = c1; V.hi[4 * i + 2] = b0; V.hi[4 * i + 3] = d1;
   }
-  std::vector<Pair> pairs =
-      bin_and_sort(1, n, mx.data(), my.data(), rad.data(), dp.data(), V.cam.W, V.cam.H, tw, th);
+  std::vector<Pair> pairs = bin_and_sort(1, n, mx.data(), my.data(), rad.data(), hx.data(), hy.data(), dp.data(),
+                                         V.cam.W, V.cam.H, tw, th);
   V.lists.assign((size_t)V.Tx * V.Ty, {});
   for (const Pair& p : pairs) V.lists[p.key >> 32].push_back((int)p.val);
   V.amb.assign((size_t)V.Tx * V.Ty, {});
@@ -443,8 +512,11 @@ void blend(const std::vector<int>& list, const std::vector<Splat<S>>& sp, double
 
 // 0 for pixels whose value may legitimately differ between an FP32 and an FP64
 // evaluation because a splat's tile set, or the depth order of two splats, lies
-// within rounding of a boundary; +inf otherwise.
-double binning_margin(const View& V, int tx, int ty, double pcx, double pcy) {
+// within rounding of a boundary; +inf otherwise.  `nc` is the pixel's n_contrib:
+// a splat whose tile membership is ambiguous moves the list position of every
+// later splat, so it also makes n_contrib ambiguous when it sorts before the
+// pixel's last blended splat, visible or not.
+double binning_margin(const View& V, int tx, int ty, double pcx, double pcy, int nc = 0) {
   const std::vector<int>& list = V.lists[(size_t)ty * V.Tx + tx];
   auto visible_at = [&](long i) {
     const Splat<double>& g = V.sp[i];
@@ -452,8 +524,14 @@ double binning_margin(const View& V, int tx, int ty, double pcx, double pcy) {
     double power = -0.5 * (g.A * dx * dx + g.C * dy * dy) - g.B * dx * dy;
     return g.o * std::exp(power) >= 0.5 * kAlphaMin;
   };
+  auto before_last = [&](long i) {
+    if (nc <= 0) return false;
+    const long j = list[nc - 1];
+    const float di = (float)V.sp[i].depth, dj = (float)V.sp[j].depth;
+    return di < dj || (di == dj && i <= j);
+  };
   for (int i : V.amb[(size_t)ty * V.Tx + tx])
-    if (visible_at(i)) return 0.0;
+    if (visible_at(i) || before_last(i)) return 0.0;
   for (size_t k = 1; k < list.size(); ++k) {
     double d0 = V.sp[list[k - 1]].depth, d1 = V.sp[list[k]].depth;
     if (std::fabs(d1 - d0) <= 1e-6 * std::fabs(d1) && visible_at(list[k - 1]) && visible_at(list[k]))
@@ -913,11 +991,19 @@ void or_project(const double* P, long pitch, long n, int deg, const double* cam2
 }
 
 // Binning and depth sort from FP32 splat records of n_views views (arrays are
-// n_views x n).  Writes up to `cap` pairs and the [start, end) range of every
+// n_views x n).  `ext` holds each record's footprint half-extents as packed
+// halves (x low, y high), or is null for +inf.  Writes up to `cap` pairs and the [start, end) range of every
 // tile (2 x n_views x tiles); returns the number of pairs.
-long or_bin_sort(int n_views, long n, const float* mx, const float* my, const int* rad, const float* depth,
-                 int W, int H, int tw, int th, uint64_t* keys, uint32_t* vals, long cap, uint32_t* ranges) {
-  std::vector<Pair> pairs = bin_and_sort(n_views, n, mx, my, rad, depth, W, H, tw, th);
+long or_bin_sort(int n_views, long n, const float* mx, const float* my, const int* rad, const uint32_t* ext,
+                 const float* depth, int W, int H, int tw, int th, uint64_t* keys, uint32_t* vals, long cap,
+                 uint32_t* ranges) {
+  std::vector<float> hx((size_t)n_views * n, INFINITY), hy((size_t)n_views * n, INFINITY);
+  if (ext)
+    for (long g = 0; g < (long)n_views * n; ++g) {
+      hx[g] = half_to_float((uint16_t)(ext[g] & 0xffffu));
+      hy[g] = half_to_float((uint16_t)(ext[g] >> 16));
+    }
+  std::vector<Pair> pairs = bin_and_sort(n_views, n, mx, my, rad, hx.data(), hy.data(), depth, W, H, tw, th);
   long T = (long)((W + tw - 1) / tw) * ((H + th - 1) / th);
   for (long k = 0; k < 2 * T * n_views; ++k) ranges[k] = 0;
   for (long p = 0; p < (long)pairs.size(); ++p) {
@@ -949,7 +1035,7 @@ long or_render(const double* P, long pitch, long n, int deg, const double* cams,
       for (int ch = 0; ch < 3; ++ch) img[ch * HW + px] = C[ch];
       final_T[v * HW + px] = T;
       n_contrib[v * HW + px] = nc;
-      if (margin) margin[v * HW + px] = std::min(mg, binning_margin(V, tx, ty, x + 0.5, y + 0.5));
+      if (margin) margin[v * HW + px] = std::min(mg, binning_margin(V, tx, ty, x + 0.5, y + 0.5, nc));
     });
   }
   return pairs;
@@ -1311,7 +1397,7 @@ void or_render_pixels(const double* P, long pitch, long n, int deg, const double
     for (int ch = 0; ch < 3; ++ch) rgb[3 * q + ch] = C[ch];
     T_out[q] = T;
     nc_out[q] = nc;
-    margin[q] = std::min(mg, binning_margin(V, tx, ty, x + 0.5, y + 0.5));
+    margin[q] = std::min(mg, binning_margin(V, tx, ty, x + 0.5, y + 0.5, nc));
     if (nu > 0) {
       local.resize(list.size());
       for (size_t u = 0; u < list.size(); ++u) local[u] = (int)u;

@@ -285,7 +285,8 @@ __device__ __forceinline__ void sh_basis_grad(float x, float y, float z, const f
 
 // ------------------------------------------------------ footprint extents
 // Half-extents of the bounding box of a splat's alpha >= 1/255 footprint, kept
-// in the last word of its record for the rasteriser's per-block visibility test.
+// in the last word of its record; binning narrows the splat's tile square to
+// this box and the rasteriser tests its 8 x 8 pixel blocks against it.
 // The footprint is the ellipse d^T Q d <= tau, tau = 2 ln(255 o), Q = [[A, B],
 // [B, C]] the conic; its box has half-widths sqrt(tau C / det) and
 // sqrt(tau A / det).  They are widened by 0.1% + 0.01 px, so that no pair an
@@ -311,22 +312,32 @@ __device__ __forceinline__ uint32_t footprint_extents(float A, float B, float C,
 }
 
 // ---------------------------------------------------------- tile rectangle
-// [x0, x1) x [y0, y1) of a splat, decided in FP32 with one rounding per step:
-//   x0 = clamp(floor((mx - r)/tw), 0, Tx),  x1 = clamp(floor((mx + (r + tw - 1))/tw), 0, Tx).
-__device__ __forceinline__ int clamp_floor(float q, int hi) {
-  float f = floorf(q);
+// [x0, x1) x [y0, y1) of a splat, decided in FP32 with one rounding per step.
+// The 3DGS square of half-width r:
+//   x0 = clamp(floor((mx - r)/tw), 0, Tx),  x1 = clamp(floor((mx + (r + tw - 1))/tw), 0, Tx),
+// intersected with the tiles the footprint box [mx - hx, mx + hx] reaches:
+//   x0 >= floor((mx - hx)/tw),  x1 <= floor((mx + hx)/tw) + 1
+// (the same for y; hx, hy the packed halves of `ext`).  A tile outside the box
+// has no pixel centre where the splat's alpha reaches 1/255, so dropping it
+// changes no image; -inf extents give an empty rectangle, +inf the square.
+__device__ __forceinline__ int clamp_floor(float f, int hi) {
   if (!(f > 0.0f)) return 0;  // NaN -> 0
   if (f > (float)hi) return hi;
   return (int)f;
 }
-__device__ __forceinline__ void tile_rect(float mx, float my, int r, int tw, int th, int Tx, int Ty, int& x0,
-                                          int& x1, int& y0, int& y1) {
-  float lox = __fsub_rn(mx, (float)r), hix = __fadd_rn(mx, (float)(r + tw - 1));
-  float loy = __fsub_rn(my, (float)r), hiy = __fadd_rn(my, (float)(r + th - 1));
-  x0 = clamp_floor(__fdiv_rn(lox, (float)tw), Tx);
-  x1 = clamp_floor(__fdiv_rn(hix, (float)tw), Tx);
-  y0 = clamp_floor(__fdiv_rn(loy, (float)th), Ty);
-  y1 = clamp_floor(__fdiv_rn(hiy, (float)th), Ty);
+__device__ __forceinline__ void tile_rect(float mx, float my, int r, uint32_t ext, int tw, int th, int Tx, int Ty,
+                                          int& x0, int& x1, int& y0, int& y1) {
+  const float hx = __half2float(__ushort_as_half((unsigned short)(ext & 0xffffu)));
+  const float hy = __half2float(__ushort_as_half((unsigned short)(ext >> 16)));
+  const float ftw = (float)tw, fth = (float)th;
+  x0 = max(clamp_floor(floorf(__fdiv_rn(__fsub_rn(mx, (float)r), ftw)), Tx),
+           clamp_floor(floorf(__fdiv_rn(__fsub_rn(mx, hx), ftw)), Tx));
+  x1 = min(clamp_floor(floorf(__fdiv_rn(__fadd_rn(mx, (float)(r + tw - 1)), ftw)), Tx),
+           clamp_floor(__fadd_rn(floorf(__fdiv_rn(__fadd_rn(mx, hx), ftw)), 1.0f), Tx));
+  y0 = max(clamp_floor(floorf(__fdiv_rn(__fsub_rn(my, (float)r), fth)), Ty),
+           clamp_floor(floorf(__fdiv_rn(__fsub_rn(my, hy), fth)), Ty));
+  y1 = min(clamp_floor(floorf(__fdiv_rn(__fadd_rn(my, (float)(r + th - 1)), fth)), Ty),
+           clamp_floor(__fadd_rn(floorf(__fdiv_rn(__fadd_rn(my, hy), fth)), 1.0f), Ty));
 }
 
 // ------------------------------------------------- async copies (TMA bulk)

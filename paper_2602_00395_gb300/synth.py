@@ -184,9 +184,12 @@ def projected_records(n: int, width: int, height: int, *, seed: int = 11,
                       max_radius: int = 120):
     """Seeded stand-ins for projected splats, as the binning step receives them.
 
-    Returns float32 means (x, y), int32 radii and float32 depths.  Some radii are 0
-    (culled), some centres lie off-screen, and a fraction of depths are exact
-    duplicates of others so that ties are exercised.
+    Returns float32 means (x, y), int32 radii, float32 depths and the footprint
+    half-extents (x, y) as packed halves (uint32, x in the low 16 bits).  Some
+    radii are 0 (culled), some centres lie off-screen, a fraction of depths are
+    exact duplicates of others so that ties are exercised, and the half-extents
+    range from 0 to beyond the radius, with some -inf (no pixel reached) and
+    some +inf (unbounded).
     """
     rng = np.random.default_rng(seed)
     mx = rng.uniform(-60.0, width + 60.0, size=n).astype(np.float32)
@@ -197,7 +200,14 @@ def projected_records(n: int, width: int, height: int, *, seed: int = 11,
     dup = rng.uniform(size=n) < dup_depth_frac
     if n > 1 and dup.any():
         depth[dup] = depth[rng.integers(0, n, size=int(dup.sum()))]
-    return mx, my, r, depth
+    h = (np.maximum(r, 1)[None, :] * rng.uniform(0.1, 1.4, size=(2, n))).astype(np.float16)
+    kind = rng.uniform(size=n)
+    h[:, kind < 0.04] = -np.inf
+    h[:, (kind >= 0.04) & (kind < 0.08)] = np.inf
+    h[:, (kind >= 0.08) & (kind < 0.11)] = 0.0
+    bits = h.view(np.uint16).astype(np.uint32)
+    ext = bits[0] | (bits[1] << np.uint32(16))
+    return mx, my, r, depth, ext
 
 
 # --------------------------------------------------------------- serving

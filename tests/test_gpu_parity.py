@@ -110,13 +110,14 @@ def test_project_matches_oracle(case):
 
 
 # ------------------------------------------------------------------ bin/sort
-def _write_records(e, mx, my, r, d):
+def _write_records(e, mx, my, r, d, ext):
     rec = torch.zeros(e.V, e.n_pad, 12, dtype=torch.float32)
     n = mx.shape[1]
     rec[:, :n, 0] = torch.from_numpy(mx)
     rec[:, :n, 1] = torch.from_numpy(my)
     rec[:, :n, 9] = torch.from_numpy(d)
     rec[:, :n, 10] = torch.from_numpy(r.astype(np.int32).view(np.float32))
+    rec[:, :n, 11] = torch.from_numpy(ext.astype(np.uint32).view(np.float32))
     e.rec.copy_(rec.reshape(-1).to(e.device))
 
 
@@ -133,10 +134,11 @@ def test_bin_sort_bit_exact(W, H, tile, V, n, maxr):
     recs = [S.projected_records(n, W, H, seed=100 + v, max_radius=maxr) for v in range(V)]
     mx = np.stack([a[0] for a in recs]); my = np.stack([a[1] for a in recs])
     r = np.stack([a[2] for a in recs]); d = np.stack([a[3] for a in recs])
-    keys, vals, ranges = O.bin_sort(mx, my, r, d, W, H, *tile)
+    ext = np.stack([a[4] for a in recs])
+    keys, vals, ranges = O.bin_sort(mx, my, r, d, W, H, *tile, extents=ext)
     cams = [S.single_camera(W, H)] * V
     e = _engine(n, 0, cams, tile=tile, nu=0, capacity=len(keys) + 123)
-    _write_records(e, mx, my, r, d)
+    _write_records(e, mx, my, r, d, ext)
     e.bin_sort()
     torch.cuda.synchronize()
     P = int(e.n_pairs.item())
@@ -150,10 +152,10 @@ def test_bin_sort_bit_exact(W, H, tile, V, n, maxr):
 @pytest.mark.parametrize("W,H", [(128, 96), (3840, 2160)])
 def test_bin_sort_capacity_overflow_is_flagged_and_in_bounds(W, H):
     n = 3000
-    mx, my, r, d = S.projected_records(n, W, H, seed=5, max_radius=50)
-    keys, _, _ = O.bin_sort(mx, my, r, d, W, H)
+    mx, my, r, d, ext = S.projected_records(n, W, H, seed=5, max_radius=50)
+    keys, _, _ = O.bin_sort(mx, my, r, d, W, H, extents=ext)
     e = _engine(n, 0, [S.single_camera(W, H)], nu=0, capacity=len(keys) // 3)
-    _write_records(e, mx[None], my[None], r[None], d[None])
+    _write_records(e, mx[None], my[None], r[None], d[None], ext[None])
     e.bin_sort()
     torch.cuda.synchronize()
     from paper_2602_00395_gb300 import gs3dtr as G

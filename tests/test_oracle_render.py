@@ -3,7 +3,9 @@
 Projection: the exact pinhole image of the mean, the closed-form footprint of
 an isotropic Gaussian on the optical axis, and a Monte-Carlo projection of
 samples (EWA is the linearisation of that projection).  Binning: a brute-force
-interval test over every tile and numpy's lexicographic sort.  Blending: single
+interval test over every tile and numpy's lexicographic sort; the footprint box
+that narrows the 3DGS tile square leaves every image equal to a per-pixel blend
+over the depth-sorted splats with the square alone.  Blending: single
 splat, two coincident splats, and the telescoping identity C = c (1 - T) for
 splats that share one colour.
 """
@@ -110,29 +112,39 @@ def test_behind_near_plane_is_culled():
 
 
 # ---------------------------------------------------------------- binning
-def _brute_tiles(mx, my, r, W, H, tw, th):
-    """Tiles whose pixel interval [t*tw, (t+1)*tw) meets (m - r, m + r - 1] on both axes."""
+def _half(bits):
+    return float(np.array([bits], np.uint16).view(np.float16)[0])
+
+
+def _brute_tiles(mx, my, r, ext, W, H, tw, th):
+    """Tiles whose pixel interval [t*tw, (t+1)*tw) meets (m - r, m + r - 1] and
+    [m - h, m + h] on both axes (h the footprint half-extent; FP32 sums)."""
     Tx, Ty = -(-W // tw), -(-H // th)
     out = []
     if r <= 0:
         return out
+    hx, hy = np.float32(_half(int(ext) & 0xFFFF)), np.float32(_half(int(ext) >> 16))
     lo_x, hi_x = np.float32(mx) - np.float32(r), np.float32(mx) + np.float32(r - 1)
     lo_y, hi_y = np.float32(my) - np.float32(r), np.float32(my) + np.float32(r - 1)
+    with np.errstate(invalid="ignore", over="ignore"):
+        flo_x, fhi_x = np.float32(mx) - hx, np.float32(mx) + hx
+        flo_y, fhi_y = np.float32(my) - hy, np.float32(my) + hy
     for ty in range(Ty):
         for tx in range(Tx):
-            if tx * tw <= hi_x and (tx + 1) * tw > lo_x and ty * th <= hi_y and (ty + 1) * th > lo_y:
+            if (tx * tw <= hi_x and (tx + 1) * tw > lo_x and ty * th <= hi_y and (ty + 1) * th > lo_y
+                    and tx * tw <= fhi_x and (tx + 1) * tw > flo_x and ty * th <= fhi_y and (ty + 1) * th > flo_y):
                 out.append(ty * Tx + tx)
     return out
 
 
 @pytest.mark.parametrize("W,H,tw,th,n", [(128, 128, 16, 16, 300), (97, 53, 16, 8, 200), (61, 45, 8, 8, 150)])
 def test_binning_against_brute_force_and_lexsort(W, H, tw, th, n):
-    mx, my, r, d = S.projected_records(n, W, H, seed=W + n, max_radius=40)
-    keys, vals, ranges = O.bin_sort(mx, my, r, d, W, H, tw, th)
+    mx, my, r, d, ext = S.projected_records(n, W, H, seed=W + n, max_radius=40)
+    keys, vals, ranges = O.bin_sort(mx, my, r, d, W, H, tw, th, extents=ext)
     Tx, Ty = -(-W // tw), -(-H // th)
     expect = []
     for i in range(n):
-        for tile in _brute_tiles(mx[i], my[i], int(r[i]), W, H, tw, th):
+        for tile in _brute_tiles(mx[i], my[i], int(r[i]), ext[i], W, H, tw, th):
             key = (tile << 32) | int(np.float32(d[i]).view(np.uint32))
             expect.append((key, i))
     ek = np.array([k for k, _ in expect], np.uint64)
@@ -149,6 +161,65 @@ def test_binning_against_brute_force_and_lexsort(W, H, tw, th, n):
             assert s == e
         else:
             assert (s, e) == (sel[0], sel[-1] + 1)
+    # unbounded half-extents leave the 3DGS square alone
+    k2, _, _ = O.bin_sort(mx, my, r, d, W, H, tw, th)
+    n_square = sum(len(_brute_tiles(mx[i], my[i], int(r[i]), 0x7C007C00, W, H, tw, th)) for i in range(n))
+    assert len(k2) == n_square > len(keys)
+
+
+def _square_blend(s, W, H, tw, th):
+    """Per-pixel front-to-back blend (Sec. 3.1) over every valid splat in (FP32
+    depth, index) order whose 3DGS tile square holds the pixel's tile: no lists."""
+    valid = np.nonzero(s["valid"] > 0)[0]
+    order = valid[np.lexsort((valid, s["depth"][valid].astype(np.float32)))]
+    img, T_out = np.zeros((3, H, W)), np.ones((H, W))
+    tiles = {int(i): set(_brute_tiles(s["mx"][i], s["my"][i], int(s["radius"][i]), 0x7C007C00, W, H, tw, th))
+             for i in order}
+    Tx = -(-W // tw)
+    rgb = np.stack([s["r"], s["g"], s["b"]])
+    for y in range(H):
+        for x in range(W):
+            tile = (y // th) * Tx + x // tw
+            T = 1.0
+            for i in order:
+                if tile not in tiles[int(i)]:
+                    continue
+                dx, dy = s["mx"][i] - (x + 0.5), s["my"][i] - (y + 0.5)
+                power = -0.5 * (s["A"][i] * dx * dx + s["C"][i] * dy * dy) - s["B"][i] * dx * dy
+                if power > 0:
+                    continue
+                alpha = min(0.99, s["o"][i] * math.exp(power))
+                if alpha < 1 / 255:
+                    continue
+                Tn = T * (1 - alpha)
+                if Tn < 1e-4:
+                    break
+                img[:, y, x] += rgb[:, i] * alpha * T
+                T = Tn
+            T_out[y, x] = T
+    return img, T_out
+
+
+@pytest.mark.parametrize("tw,th", [(16, 16), (8, 8)])
+def test_footprint_box_binning_leaves_the_image_unchanged(tw, th):
+    """Elongated, rotated splats of all opacities: the footprint box drops tiles
+    (fewer pairs than the 3DGS square gives) and no pixel changes."""
+    W, H = 56, 44
+    sc = S.make_scene(120, 1, seed=77, extent=0.7, log_scale_shift=math.log(2.5))
+    P = O.params64(sc)
+    rng = np.random.default_rng(3)
+    P[3, :] += rng.uniform(-1.2, 1.2, sc.n)  # anisotropy
+    P[10, :] = rng.uniform(-6.0, 5.0, sc.n)  # opacities from 0.0025 to 0.993
+    cam = S.Camera(S.look_at((3.2, 0.5, -0.4)), **S.pinhole(W, H))
+    s = O.project(P, 1, cam)
+    out = O.render(P, 1, [cam], tw, th)
+    img, T = _square_blend(s, W, H, tw, th)
+    n_square = sum(len(_brute_tiles(s["mx"][i], s["my"][i], int(s["radius"][i]), 0x7C007C00, W, H, tw, th))
+                   for i in np.nonzero(s["valid"] > 0)[0])
+    assert out["n_pairs"] < 0.9 * n_square
+    assert T.min() < 0.2 and np.abs(img).max() > 0.3
+    np.testing.assert_allclose(out["image"][0], img, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(out["final_T"][0], T, rtol=0, atol=1e-12)
 
 
 # ----------------------------------------------------------------- blending
