@@ -88,9 +88,12 @@ typedef struct gs_camera {
 
 /* Views rendered by one call; every camera of the call has this size.
  * tile_w is 8, 16 or 32, tile_h a power of two >= 8, tile_w * tile_h is 64, 128
- * or 256 (two pixels per thread; each warp covers an 8 x 8 pixel block). */
+ * or 256 (two pixels per thread; each warp covers an 8 x 8 pixel block).
+ * footprint_bins selects the tiles of a splat (see gs_bin_sort): 0 its 3DGS tile
+ * square, 1 that square narrowed to the box of its alpha >= 1/255 footprint.
+ * Both give the same images and derivatives; 1 gives fewer pairs. */
 typedef struct gs_frame {
-  int32_t n_views, width, height, tile_w, tile_h;
+  int32_t n_views, width, height, tile_w, tile_h, footprint_bins;
 } gs_frame;
 
 /* Rademacher probes z_k (k < nu) of step t: row r of Gaussian i is entry
@@ -185,12 +188,13 @@ gs_status gs_project(const gs_params* x, const gs_camera* cams, gs_frame frame, 
 
 /* Sec. 3.1 tile binning and depth order: all (tile, splat) pairs of all views
  * sorted by (key, splat index), and each tile's [start, end).  A splat's tiles
- * are its 3DGS square intersected with its footprint box, decided in FP32 with
- * one rounding per operation (hx, hy the record's extents; the same for y):
- *   x0 = clamp(max(floor((mx - r)/tw), floor((mx - hx)/tw)), 0, Tx)
- *   x1 = clamp(min(floor((mx + (r + tw - 1))/tw), floor((mx + hx)/tw) + 1), 0, Tx).
- * A tile outside the box holds no pixel where the splat is blended (its alpha
- * stays below 1/255 there), so the box removes pairs but changes no image.  If the pairs
+ * are its 3DGS square, decided in FP32 with one rounding per operation:
+ *   x0 = clamp(floor((mx - r)/tw), 0, Tx), x1 = clamp(floor((mx + (r + tw - 1))/tw), 0, Tx)
+ * (the same for y); with frame.footprint_bins = 1 also
+ *   x0 >= clamp(floor((mx - hx)/tw), 0, Tx), x1 <= clamp(floor((mx + hx)/tw) + 1, 0, Tx)
+ * with hx, hy the record's footprint extents.  A tile outside that box holds no
+ * pixel where the splat is blended (its alpha stays below 1/255 there), so the
+ * box removes pairs but changes no image.  If the pairs
  * exceed out->capacity, GS_FLAG_CAPACITY is raised, *n_pairs holds the need,
  * and the sorted arrays are incomplete (but every access stays in bounds and
  * every range end is at most the capacity). */

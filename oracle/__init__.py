@@ -10,6 +10,7 @@ package's synthetic-scene layout: 0..2 mean, 3..5 log-scale, 6..9 quaternion
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes as C
 import os
 import subprocess
@@ -51,6 +52,7 @@ def lib():
             L.or_sh_absmax.argtypes = [i32, P]
             L.or_quat_to_rotmat.argtypes = [P, P]
             L.or_project.argtypes = [P, i64, i64, i32, P, P]
+            L.or_set_footprint_bins.argtypes = [i32]
             L.or_bin_sort.restype = i64
             L.or_bin_sort.argtypes = [i32, i64, P, P, P, P, P, i32, i32, i32, i32, P, P, i64, P]
             L.or_render.restype = i64
@@ -177,6 +179,19 @@ def probe_matrix(seed: int, t: int, k: int, rows: int, n: int) -> np.ndarray:
     for j in range(rows * n):
         z[j] = L.or_rademacher(seed, t, k, j)
     return z.reshape(n, rows).T.copy()
+
+
+@contextlib.contextmanager
+def footprint_bins(on: bool = True):
+    """Within the block, renders, JVPs, Jacobians and backward passes bin each
+    splat into its 3DGS tile square narrowed to its footprint box (the GPU
+    frame's footprint_bins = 1); outside it, into the whole square."""
+    L = lib()
+    L.or_set_footprint_bins(int(on))
+    try:
+        yield
+    finally:
+        L.or_set_footprint_bins(0)
 
 
 def bin_sort(mx, my, radius, depth, width: int, height: int, tw: int = 16, th: int = 16, extents=None):

@@ -405,6 +405,10 @@ const double kAmbCentreRel = 1e-6;
 const double kAmbCentreAbs = 1e-5;
 const double kAmbExtRel = 1e-4;
 
+// Tiles of a splat in the renders: 0 its 3DGS square, 1 the square narrowed to
+// its footprint box (set by or_set_footprint_bins).
+int g_footprint_bins = 0;
+
 View build_view(const double* P, long pitch, long n, int deg, const double* cam24, int tw, int th) {
   View V;
   V.cam = make_cam(cam24);
@@ -423,12 +427,15 @@ View build_view(const double* P, long pitch, long n, int deg, const double* cam2
     mx[i] = (float)s.mx; my[i] = (float)s.my; dp[i] = (float)s.depth;
     rad[i] = s.valid ? s.radius : 0;
     if (!s.valid) continue;
-    footprint_half_extents(s.A, s.B, s.C, s.o, 0.0, hx[i], hy[i]);
-    const double cancel = (s.A * s.C + s.B * s.B) / std::fabs(s.A * s.C - s.B * s.B);
-    const double se = kAmbExtRel + 1e-6 * (std::isfinite(cancel) ? cancel : 1e30);
-    float hx_lo, hy_lo, hx_hi, hy_hi;
-    footprint_half_extents(s.A, s.B, s.C, s.o, -se, hx_lo, hy_lo);
-    footprint_half_extents(s.A, s.B, s.C, s.o, se, hx_hi, hy_hi);
+    float hx_lo = INFINITY, hy_lo = INFINITY, hx_hi = INFINITY, hy_hi = INFINITY;
+    hx[i] = hy[i] = INFINITY;
+    if (g_footprint_bins) {
+      footprint_half_extents(s.A, s.B, s.C, s.o, 0.0, hx[i], hy[i]);
+      const double cancel = (s.A * s.C + s.B * s.B) / std::fabs(s.A * s.C - s.B * s.B);
+      const double se = kAmbExtRel + 1e-6 * (std::isfinite(cancel) ? cancel : 1e30);
+      footprint_half_extents(s.A, s.B, s.C, s.o, -se, hx_lo, hy_lo);
+      footprint_half_extents(s.A, s.B, s.C, s.o, se, hx_hi, hy_hi);
+    }
     double rr = s.radius_raw;
     int r_lo = (int)std::ceil(rr * (1.0 - kAmbRel) - 1e-6);
     int r_hi = (int)std::ceil(rr * (1.0 + kAmbRel) + 1e-6);
@@ -989,6 +996,10 @@ void or_project(const double* P, long pitch, long n, int deg, const double* cam2
     std::memcpy(o, v, sizeof(v));
   }
 }
+
+// Selects the tiles of a splat in every later render, JVP, Jacobian and backward
+// call: 0 (the default) its 3DGS square, 1 the square narrowed to its footprint box.
+void or_set_footprint_bins(int on) { g_footprint_bins = on ? 1 : 0; }
 
 // Binning and depth sort from FP32 splat records of n_views views (arrays are
 // n_views x n).  `ext` holds each record's footprint half-extents as packed

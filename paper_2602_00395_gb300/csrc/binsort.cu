@@ -38,6 +38,11 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
   return m;
 }
 
+// The extents word binning uses: the record's, or +inf (the 3DGS square alone).
+__device__ __forceinline__ uint32_t bin_extents(const gs_frame& fr, float w) {
+  return fr.footprint_bins ? __float_as_uint(w) : 0x7C007C00u;
+}
+
 // ------------------------------------------------------------------ records
 // counts[g] = tiles of record g's rectangle; rkeys[g] = bits(depth) (sorted
 // within each view's segment); rvals[g] = g.
@@ -52,7 +57,7 @@ __global__ void record_keys_kernel(const float4* __restrict__ rec, int n_pad, gs
   uint32_t cnt = 0;
   if (r > 0) {
     int x0, x1, y0, y1;
-    tile_rect(a.x, a.y, r, __float_as_uint(c.w), fr.tile_w, fr.tile_h, Tx, Ty, x0, x1, y0, y1);
+    tile_rect(a.x, a.y, r, bin_extents(fr, c.w), fr.tile_w, fr.tile_h, Tx, Ty, x0, x1, y0, y1);
     cnt = (uint32_t)max(0, x1 - x0) * (uint32_t)max(0, y1 - y0);
   }
   counts[g] = cnt;
@@ -211,7 +216,7 @@ __global__ void emit_kernel(const float4* __restrict__ rec, int n_pad, gs_frame 
     const int r = __float_as_int(c.z);
     if (r > 0) {
       const float4 a = rec[3 * (size_t)g + 0];
-      tile_rect(a.x, a.y, r, __float_as_uint(c.w), fr.tile_w, fr.tile_h, Tx, Ty, x0, x1, y0, y1);
+      tile_rect(a.x, a.y, r, bin_extents(fr, c.w), fr.tile_w, fr.tile_h, Tx, Ty, x0, x1, y0, y1);
       cnt = (uint32_t)max(0, x1 - x0) * (uint32_t)max(0, y1 - y0);
     }
     depth_bits = __float_as_uint(c.y);

@@ -319,7 +319,8 @@ __device__ __forceinline__ uint32_t footprint_extents(float A, float B, float C,
 //   x0 >= floor((mx - hx)/tw),  x1 <= floor((mx + hx)/tw) + 1
 // (the same for y; hx, hy the packed halves of `ext`).  A tile outside the box
 // has no pixel centre where the splat's alpha reaches 1/255, so dropping it
-// changes no image; -inf extents give an empty rectangle, +inf the square.
+// changes no image; -inf extents give an empty rectangle, +inf the square
+// (binning passes +inf when the frame asks for the square alone).
 __device__ __forceinline__ int clamp_floor(float f, int hi) {
   if (!(f > 0.0f)) return 0;  // NaN -> 0
   if (f > (float)hi) return hi;
@@ -393,7 +394,8 @@ inline bool frame_ok(gs_frame fr) {
   auto pow2 = [](int v) { return v > 0 && (v & (v - 1)) == 0; };
   const int tt = fr.tile_w * fr.tile_h;
   return fr.n_views >= 1 && fr.width >= 1 && fr.height >= 1 && (fr.tile_w == 8 || fr.tile_w == 16 || fr.tile_w == 32) &&
-         pow2(fr.tile_h) && fr.tile_h >= 8 && (tt == 64 || tt == 128 || tt == 256);
+         pow2(fr.tile_h) && fr.tile_h >= 8 && (tt == 64 || tt == 128 || tt == 256) &&
+         (fr.footprint_bins == 0 || fr.footprint_bins == 1);
 }
 
 // ---------------------------------------------------------- host errors

@@ -48,14 +48,18 @@ class TRStep:
     def __init__(self, n: int, sh_degree: int, n_views: int, width: int, height: int, *, nu: int = 1,
                  tile=(16, 16), capacity: int | None = None, loss_kind: int = G.GS_LOSS_L1,
                  gn_floor: float = 1e-3, cfg: TRConfig | None = None, probe_seed: int = 42,
-                 device: str = "cuda", state=None, zero_init: bool = True, dssim_lambda: float | None = None):
+                 device: str = "cuda", state=None, zero_init: bool = True, dssim_lambda: float | None = None,
+                 footprint_bins: bool = True):
         """state: optional (x, g_ema, d_ema) tensors of shape rows x n_pad that the
         step uses in place of its own (a scene's resident parameters and trust-region
         state, shared by the short-lived steps of a serving loop).  zero_init=False
         leaves the buffers that the calls overwrite before reading (records,
         images, gradient, curvature, target, cameras) uninitialised, which saves a
         fill per buffer when steps are created per request.  dssim_lambda: the
-        pixel loss (1 - lambda) L1 + lambda D-SSIM of Eq. pixel_loss instead of L1."""
+        pixel loss (1 - lambda) L1 + lambda D-SSIM of Eq. pixel_loss instead of L1.
+        footprint_bins: bin each splat into the tiles its alpha >= 1/255 footprint
+        box reaches within its 3DGS tile square (False: the whole square); the
+        images and derivatives are the same, the pairs fewer."""
         G.load()
         self.n, self.deg, self.V, self.W, self.H, self.nu = n, sh_degree, n_views, width, height, nu
         self.n_pad = synth.pad_count(n)
@@ -65,7 +69,7 @@ class TRStep:
         self.cfg = cfg or TRConfig()
         self.loss = G.gs_loss(loss_kind, gn_floor)
         self.probe_seed = probe_seed
-        self.frame = G.frame_struct(n_views, width, height, *tile)
+        self.frame = G.frame_struct(n_views, width, height, *tile, footprint_bins=footprint_bins)
         self.Tx = -(-width // tile[0])
         self.Ty = -(-height // tile[1])
         f32 = dict(dtype=torch.float32, device=self.device)
@@ -315,7 +319,8 @@ def autotune_tile(eng: TRStep, candidates=((16, 16), (32, 8), (8, 32), (16, 8)),
     times = {}
     for tile in candidates:
         e = TRStep(eng.n, eng.deg, eng.V, eng.W, eng.H, nu=eng.nu, tile=tile, cfg=eng.cfg,
-                   probe_seed=eng.probe_seed, device=str(eng.device))
+                   probe_seed=eng.probe_seed, device=str(eng.device),
+                   footprint_bins=bool(eng.frame.footprint_bins))
         for dst, src in ((e.x, eng.x), (e.g_ema, eng.g_ema), (e.d_ema, eng.d_ema), (e.cams, eng.cams),
                          (e.target, eng.target)):
             dst.copy_(src)

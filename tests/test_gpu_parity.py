@@ -121,23 +121,27 @@ def _write_records(e, mx, my, r, d, ext):
     e.rec.copy_(rec.reshape(-1).to(e.device))
 
 
-@pytest.mark.parametrize("W,H,tile,V,n,maxr", [
-    (128, 128, (16, 16), 1, 1000, 40),
-    (97, 53, (16, 8), 3, 4001, 30),
-    (61, 45, (8, 8), 2, 777, 60),
-    (1297, 840, (16, 16), 2, 150000, 80),  # ~ millions of pairs, many chunks
+@pytest.mark.parametrize("W,H,tile,V,n,maxr,box", [
+    (128, 128, (16, 16), 1, 1000, 40, True),
+    (128, 128, (16, 16), 1, 1000, 40, False),
+    (97, 53, (16, 8), 3, 4001, 30, True),
+    (61, 45, (8, 8), 2, 777, 60, False),
+    (1297, 840, (16, 16), 2, 150000, 80, True),  # ~ millions of pairs, many chunks
+    (1297, 840, (16, 16), 2, 150000, 80, False),
     # more tiles per view than the shared counters hold: pairs sorted by radix passes
-    (3840, 2160, (16, 16), 1, 60000, 120),
-    (2100, 1500, (8, 8), 2, 30000, 40),
+    (3840, 2160, (16, 16), 1, 60000, 120, True),
+    (2100, 1500, (8, 8), 2, 30000, 40, False),
 ])
-def test_bin_sort_bit_exact(W, H, tile, V, n, maxr):
+def test_bin_sort_bit_exact(W, H, tile, V, n, maxr, box):
+    """Keys, values and ranges equal the oracle's from the same FP32 records, with
+    the 3DGS tile square (box False) and with it narrowed to the footprint box."""
     recs = [S.projected_records(n, W, H, seed=100 + v, max_radius=maxr) for v in range(V)]
     mx = np.stack([a[0] for a in recs]); my = np.stack([a[1] for a in recs])
     r = np.stack([a[2] for a in recs]); d = np.stack([a[3] for a in recs])
     ext = np.stack([a[4] for a in recs])
-    keys, vals, ranges = O.bin_sort(mx, my, r, d, W, H, *tile, extents=ext)
+    keys, vals, ranges = O.bin_sort(mx, my, r, d, W, H, *tile, extents=ext if box else None)
     cams = [S.single_camera(W, H)] * V
-    e = _engine(n, 0, cams, tile=tile, nu=0, capacity=len(keys) + 123)
+    e = _engine(n, 0, cams, tile=tile, nu=0, capacity=len(keys) + 123, footprint_bins=box)
     _write_records(e, mx, my, r, d, ext)
     e.bin_sort()
     torch.cuda.synchronize()
@@ -177,13 +181,14 @@ def test_bin_sort_empty_input():
 
 
 # ------------------------------------------------------------------ forward
-def _render_compare(sc, cams, tile=(16, 16)):
-    e = _engine(sc.n, sc.sh_degree, cams, tile=tile, nu=0)
+def _render_compare(sc, cams, tile=(16, 16), box=True):
+    e = _engine(sc.n, sc.sh_degree, cams, tile=tile, nu=0, footprint_bins=box)
     e.set_params(sc.params)
     e.ensure_capacity()
     e.render()
     torch.cuda.synchronize()
-    ref = O.render(O.params64(sc), sc.sh_degree, cams, *tile)
+    with O.footprint_bins(box):
+        ref = O.render(O.params64(sc), sc.sh_degree, cams, *tile)
     V, H, W = len(cams), cams[0].height, cams[0].width
     img = e.image.view(V, 3, H, W).cpu().numpy()
     T = e.final_T.view(V, H, W).cpu().numpy()
@@ -192,10 +197,14 @@ def _render_compare(sc, cams, tile=(16, 16)):
     return e, ref, img, T, nc, ok
 
 
-@pytest.mark.parametrize("case,tile", [("cfg1", (16, 16)), ("ragged", (16, 8)), ("ragged", (8, 8))])
-def test_raster_fwd_matches_oracle(case, tile):
+@pytest.mark.parametrize("case,tile,box", [("cfg1", (16, 16), True), ("cfg1", (16, 16), False),
+                                          ("ragged", (16, 8), True), ("ragged", (8, 8), True),
+                                          ("ragged", (16, 16), False)])
+def test_raster_fwd_matches_oracle(case, tile, box):
+    """Image, final T, n_contrib and the pair count equal the oracle's, binning by
+    the footprint box (box True) or by the whole 3DGS tile square."""
     sc, cams = _cfg1() if case == "cfg1" else _ragged()
-    e, ref, img, T, nc, ok = _render_compare(sc, cams, tile)
+    e, ref, img, T, nc, ok = _render_compare(sc, cams, tile, box)
     assert int(e.n_pairs.item()) == ref["n_pairs"] or (~ok).any()
     # pixels whose value FP32 may legitimately flip: here one splat per view has
     # a radius within 1e-5 of an integer, and its ambiguous tile band is excluded

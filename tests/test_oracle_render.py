@@ -212,14 +212,18 @@ def test_footprint_box_binning_leaves_the_image_unchanged(tw, th):
     P[10, :] = rng.uniform(-6.0, 5.0, sc.n)  # opacities from 0.0025 to 0.993
     cam = S.Camera(S.look_at((3.2, 0.5, -0.4)), **S.pinhole(W, H))
     s = O.project(P, 1, cam)
-    out = O.render(P, 1, [cam], tw, th)
+    square = O.render(P, 1, [cam], tw, th)
+    with O.footprint_bins():
+        box = O.render(P, 1, [cam], tw, th)
     img, T = _square_blend(s, W, H, tw, th)
     n_square = sum(len(_brute_tiles(s["mx"][i], s["my"][i], int(s["radius"][i]), 0x7C007C00, W, H, tw, th))
                    for i in np.nonzero(s["valid"] > 0)[0])
-    assert out["n_pairs"] < 0.9 * n_square
+    assert square["n_pairs"] == n_square
+    assert box["n_pairs"] < 0.9 * n_square
     assert T.min() < 0.2 and np.abs(img).max() > 0.3
-    np.testing.assert_allclose(out["image"][0], img, rtol=0, atol=1e-12)
-    np.testing.assert_allclose(out["final_T"][0], T, rtol=0, atol=1e-12)
+    for out in (square, box):
+        np.testing.assert_allclose(out["image"][0], img, rtol=0, atol=1e-12)
+        np.testing.assert_allclose(out["final_T"][0], T, rtol=0, atol=1e-12)
 
 
 # ----------------------------------------------------------------- blending
