@@ -293,6 +293,21 @@ __device__ __forceinline__ uint32_t digit_of(K key, int shift) {
   return (uint32_t)(key >> shift) & 255u;
 }
 
+// Digit counts of one tile.  A thread counts kRadixItems consecutive keys (read
+// as 16-byte vectors) and adds each run of equal digits to the block's
+// counters with one shared atomic: a splat's pairs are adjacent and share their
+// high tile digit, so runs are common.
+template <typename K>
+__device__ __forceinline__ void load_run(const K* p, K (&kk)[kRadixItems]) {
+  static_assert((kRadixItems * sizeof(K)) % 16 == 0, "vector loads");
+  const uint4* q = reinterpret_cast<const uint4*>(p);
+#pragma unroll
+  for (int v = 0; v < (int)(kRadixItems * sizeof(K) / 16); ++v) {
+    const uint4 w = __ldg(q + v);
+    memcpy(reinterpret_cast<char*>(kk) + 16 * v, &w, 16);
+  }
+}
+
 template <typename K>
 __global__ void __launch_bounds__(kRadixThreads) radix_hist_kernel(const K* __restrict__ keys, Seg sg, int bpg,
                                                                    int shift, uint32_t* __restrict__ hist) {
@@ -304,21 +319,26 @@ __global__ void __launch_bounds__(kRadixThreads) radix_hist_kernel(const K* __re
   s_cnt[threadIdx.x] = 0;
   __syncthreads();
   const K* kin = keys + (size_t)g * sg.stride;
-  const uint32_t base = (uint32_t)t * kRadixTile;
+  const uint32_t base = (uint32_t)t * kRadixTile + threadIdx.x * kRadixItems;
   K kk[kRadixItems];
+  if (base + kRadixItems <= len) {
+    load_run(kin + base, kk);
+  } else {
+#pragma unroll
+    for (int k = 0; k < kRadixItems; ++k) kk[k] = base + k < len ? kin[base + k] : (K)0;
+  }
+  uint32_t prev = 256u, run = 0;
 #pragma unroll
   for (int k = 0; k < kRadixItems; ++k) {
-    const uint32_t idx = base + (uint32_t)k * kRadixThreads + threadIdx.x;
-    kk[k] = idx < len ? kin[idx] : (K)0;
+    const uint32_t d = base + k < len ? digit_of(kk[k], shift) : 256u;
+    if (d != prev) {
+      if (run) atomicAdd(&s_cnt[prev], run);
+      prev = d;
+      run = 0;
+    }
+    run += d < 256u;
   }
-#pragma unroll
-  for (int k = 0; k < kRadixItems; ++k) {
-    const uint32_t idx = base + (uint32_t)k * kRadixThreads + threadIdx.x;
-    const bool ok = idx < len;
-    const uint32_t d = ok ? digit_of(kk[k], shift) : 256u;
-    const uint32_t peers = __match_any_sync(0xffffffffu, d);
-    if (ok && (peers & lanemask_lt()) == 0) atomicAdd(&s_cnt[d], (uint32_t)__popc(peers));
-  }
+  if (run) atomicAdd(&s_cnt[prev], run);
   __syncthreads();
   hist[((size_t)g * 256 + threadIdx.x) * bps + t] = s_cnt[threadIdx.x];
 }
@@ -415,13 +435,35 @@ __device__ __forceinline__ uint32_t pairs_in_use(const uint32_t* n_pairs, uint64
   return (uint32_t)(p < capacity ? p : capacity);
 }
 
+// A thread looks at four consecutive keys (two 16-byte loads) and the key after
+// them; a tile starts where its key differs from the previous one and ends
+// where it differs from the next.
 __global__ void ranges_kernel(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ n_pairs,
                               uint64_t capacity, uint32_t* __restrict__ ranges) {
   const uint32_t P = pairs_in_use(n_pairs, capacity);
-  for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (size_t)gridDim.x * blockDim.x) {
-    const uint32_t tile = (uint32_t)(keys[p] >> 32);
-    if (p == 0 || (uint32_t)(keys[p - 1] >> 32) != tile) ranges[2 * (size_t)tile] = (uint32_t)p;
-    if (p + 1 == P || (uint32_t)(keys[p + 1] >> 32) != tile) ranges[2 * (size_t)tile + 1] = (uint32_t)(p + 1);
+  const size_t step = (size_t)gridDim.x * blockDim.x * 4;
+  for (size_t p0 = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) * 4; p0 < P; p0 += step) {
+    uint32_t tl[5];
+    if (p0 + 4 <= P) {
+      const ulonglong2 a = __ldg(reinterpret_cast<const ulonglong2*>(keys + p0));
+      const ulonglong2 b = __ldg(reinterpret_cast<const ulonglong2*>(keys + p0) + 1);
+      tl[0] = (uint32_t)(a.x >> 32); tl[1] = (uint32_t)(a.y >> 32);
+      tl[2] = (uint32_t)(b.x >> 32); tl[3] = (uint32_t)(b.y >> 32);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) tl[k] = p0 + k < P ? (uint32_t)(keys[p0 + k] >> 32) : 0xffffffffu;
+    }
+    tl[4] = p0 + 4 < P ? (uint32_t)(keys[p0 + 4] >> 32) : 0xffffffffu;
+    uint32_t prev = p0 > 0 ? (uint32_t)(keys[p0 - 1] >> 32) : 0xffffffffu;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const size_t p = p0 + k;
+      if (p < P) {
+        if (tl[k] != prev) ranges[2 * (size_t)tl[k]] = (uint32_t)p;
+        if (tl[k + 1] != tl[k]) ranges[2 * (size_t)tl[k] + 1] = (uint32_t)(p + 1);
+      }
+      prev = tl[k];
+    }
   }
 }
 
