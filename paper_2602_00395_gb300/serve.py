@@ -13,10 +13,15 @@ continuous batching on the GPU.
   is free, its scene has no request in flight (a training step changes the
   scene), and its working set fits the HBM budget left by the requests in
   flight.  Requests are taken in arrival order; one that cannot start does not
-  hold back later ones for other scenes.
+  hold back later ones for other scenes, and no later request of its own scene
+  overtakes it.
 * Continuous batching: every started request runs on its own stream, so the
   kernels of requests of different scenes overlap on the device; a request that
-  arrives while others run starts as soon as a slot and memory free up.
+  arrives while others run starts as soon as a slot and memory free up.  Render
+  requests of one scene that wait together (with no training step of that scene
+  between them) start as one multi-view render: one projection over their
+  views, one sort, one blend launch.  Each keeps its own image, equal to the one
+  it gets alone (the forward pass has no cross-view arithmetic).
 * Latency of a request = completion (its end event observed by the host) minus
   arrival, both on the host clock.
 
@@ -49,6 +54,7 @@ class Request:
     nbytes: int = 0
     image: object = None  # rendered image (device tensor), when results are kept
     rejected: bool = False  # working set larger than the whole budget
+    batch: int = 1  # requests started together with this one (itself included)
 
     @property
     def latency(self) -> float:
@@ -94,21 +100,24 @@ class Scene:
     def resident_bytes(self) -> int:
         return sum(t.numel() * t.element_size() for t in (self.x, self.g_ema, self.d_ema, self.cams, *self.targets))
 
-    def working_bytes(self, kind: str) -> int:
-        """Device bytes of one request's working buffers (as TRStep allocates them)."""
-        n_pad, rows, HW = synth.pad_count(self.n), synth.n_rows(self.deg), self.W * self.H
-        frame = G.frame_struct(1, self.W, self.H, *self.tile)
-        b = n_pad * 12 * 4 * (1 + max(self.nu, 1))                       # records + tangents
-        b += HW * 4 * (3 + 1 + 1 + 3 * max(self.nu, 1) + 3)              # image, T, n_contrib, tangents, target slot
-        b += self.capacity * 12 + G.gs_bin_sort_workspace_size(n_pad, frame, self.capacity)
+    def working_bytes(self, kind: str, n_views: int = 1) -> int:
+        """Device bytes of the working buffers of a request over n_views views (as
+        TRStep allocates them)."""
+        n_pad, rows, HW, V = synth.pad_count(self.n), synth.n_rows(self.deg), self.W * self.H, n_views
+        frame = G.frame_struct(V, self.W, self.H, *self.tile)
+        cap = self.capacity * V
+        b = V * n_pad * 12 * 4 * (1 + max(self.nu, 1))                   # records + tangents
+        b += V * HW * 4 * (3 + 1 + 1 + 3 * max(self.nu, 1) + 3)          # image, T, n_contrib, tangents, target slot
+        b += cap * 12 + G.gs_bin_sort_workspace_size(n_pad, frame, cap)
         b += G.gs_raster_bwd_workspace_size(n_pad, frame, self.nu) + 2 * rows * n_pad * 4  # cotangents, grad, hz
         return int(b)
 
-    def make_step(self) -> TRStep:
-        """Working buffers for one request, on the current stream, sharing the resident state."""
-        return TRStep(self.n, self.deg, 1, self.W, self.H, nu=self.nu, tile=self.tile, capacity=self.capacity,
-                      cfg=self.cfg, device=str(self.device), state=(self.x, self.g_ema, self.d_ema),
-                      zero_init=False)
+    def make_step(self, n_views: int = 1) -> TRStep:
+        """Working buffers for one request over n_views views, on the current
+        stream, sharing the resident state."""
+        return TRStep(self.n, self.deg, n_views, self.W, self.H, nu=self.nu, tile=self.tile,
+                      capacity=self.capacity * n_views, cfg=self.cfg, device=str(self.device),
+                      state=(self.x, self.g_ema, self.d_ema), zero_init=False)
 
     def enqueue(self, req: Request, stream) -> TRStep:
         """Issue the request's calls on `stream`; returns the step that owns its buffers."""
@@ -121,6 +130,15 @@ class Scene:
                 e.step(self.t, eps_schedule(self.t, self.total_steps), stream)
             else:
                 e.render(stream)
+        return e
+
+    def enqueue_renders(self, reqs: list, stream) -> TRStep:
+        """One multi-view render of the requests' views on `stream`; image j of
+        the returned step belongs to reqs[j]."""
+        with torch.cuda.stream(stream):
+            e = self.make_step(len(reqs))
+            e.cams = torch.cat([self.cams[96 * r.view: 96 * (r.view + 1)] for r in reqs])
+            e.render(stream)
         return e
 
 
@@ -184,12 +202,12 @@ class Server:
         # stream, so that reading it never synchronises with requests in flight
         self.status_host = torch.zeros(slots, dtype=torch.int32).pin_memory()
 
-    def run(self, stream_spec, keep_results: bool = False) -> ServeResult:
+    def run(self, stream_spec, keep_results: bool = False, max_render_batch: int = 8) -> ServeResult:
         reqs = _requests(stream_spec)
         waiting = deque()
         upcoming = deque(reqs)
         free = list(range(len(self.streams)))
-        inflight = {}  # slot -> (request, step, end event)
+        inflight = {}  # slot -> (requests, step, end event, bytes)
         busy = set()
         used = peak = 0
         statuses = []
@@ -198,23 +216,30 @@ class Server:
             now = time.perf_counter() - t0
             # completions
             for slot in list(inflight):
-                r, e, ev = inflight[slot]
+                batch, e, ev, nb = inflight[slot]
                 if ev.query():
-                    r.done = time.perf_counter() - t0
+                    done = time.perf_counter() - t0
                     statuses.append(int(self.status_host[slot]))
-                    if keep_results and r.kind == "render":
-                        r.image = e.image
-                    busy.discard(r.scene)
-                    used -= r.nbytes
+                    for j, r in enumerate(batch):
+                        r.done = done
+                        if keep_results and r.kind == "render":
+                            r.image = e.image.view(len(batch), -1)[j]
+                    busy.discard(batch[0].scene)
+                    used -= nb
                     free.append(slot)
                     del inflight[slot]
             while upcoming and upcoming[0].arrival <= now:
                 waiting.append(upcoming.popleft())
-            # admissions, in arrival order
+            # admissions, in arrival order; a scene whose request cannot start
+            # admits none of its later ones in this pass
             started = False
+            blocked = set()
+            taken = set()
             for r in list(waiting):
                 if not free:
                     break
+                if r.rid in taken:
+                    continue
                 sc = self.scenes[r.scene]
                 nb = sc.working_bytes(r.kind)
                 if nb > self.budget:  # can never fit: rejected at once
@@ -222,22 +247,45 @@ class Server:
                     r.start = r.done = time.perf_counter() - t0
                     waiting.remove(r)
                     continue
-                if r.scene in busy or used + nb > self.budget:
+                if r.scene in busy or r.scene in blocked or used + nb > self.budget:
+                    blocked.add(r.scene)
                     continue
+                batch = [r]
+                if r.kind == "render":
+                    # later renders of this scene up to its next training step
+                    after = False
+                    for q in waiting:
+                        if len(batch) >= max_render_batch:
+                            break
+                        if q is r:
+                            after = True
+                            continue
+                        if not after or q.scene != r.scene:
+                            continue
+                        if q.kind != "render":
+                            break
+                        nb2 = sc.working_bytes("render", len(batch) + 1)
+                        if used + nb2 > self.budget:
+                            break
+                        batch.append(q)
+                        nb = nb2
                 slot = free.pop()
                 st = self.streams[slot]
-                r.nbytes = nb
-                r.start = time.perf_counter() - t0
-                e = sc.enqueue(r, st)
+                start = time.perf_counter() - t0
+                for q in batch:
+                    q.nbytes, q.start, q.batch = nb, start, len(batch)
+                e = sc.enqueue(r, st) if len(batch) == 1 else sc.enqueue_renders(batch, st)
                 with torch.cuda.stream(st):
                     self.status_host[slot: slot + 1].copy_(e.status, non_blocking=True)
                 ev = torch.cuda.Event()
                 ev.record(st)
-                inflight[slot] = (r, e, ev)
+                inflight[slot] = (batch, e, ev, nb)
                 busy.add(r.scene)
                 used += nb
                 peak = max(peak, used)
-                waiting.remove(r)
+                for q in batch:
+                    waiting.remove(q)
+                    taken.add(q.rid)
                 started = True
             if not started and not inflight and waiting and not free:
                 raise RuntimeError("no slot can ever be freed")  # unreachable: inflight empty means free slots

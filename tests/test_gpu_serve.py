@@ -61,6 +61,32 @@ def test_results_equal_alone_and_in_the_mix(scenes):
         _restore(sc, sn)
 
 
+def test_waiting_renders_of_a_scene_start_as_one_multi_view_render(scenes):
+    """Renders of one scene that wait together start as one launch sequence and
+    each image equals the one the plain loop renders alone; a training step of
+    that scene between them splits the batch, and the render after it starts
+    only when the step is done."""
+    from paper_2602_00395_gb300.serve import Server, plain_loop
+    snaps = [_snapshot(sc) for sc in scenes]
+    spec = [(0.0, "render", 0, 0), (0.0, "render", 1, 2), (0.0, "render", 0, 3), (0.0, "render", 0, 1),
+            (0.0, "train", 0, 2), (0.0, "render", 0, 0)]
+    res = Server(scenes, slots=4).run(spec, keep_results=True)
+    assert set(res.summary()["status_words"]) == {0}
+    assert res.requests[5].start >= res.requests[4].done >= res.requests[4].start >= res.requests[0].done
+    batch = {r.rid: r.batch for r in res.requests}
+    assert batch[0] == batch[2] == batch[3] == 3 and batch[1] == 1 and batch[5] == 1
+    after_train = res.requests[5].image.clone()
+    for sc, sn in zip(scenes, snaps):
+        _restore(sc, sn)
+    ref = plain_loop(scenes, spec, keep_results=True)
+    for r, q in zip(res.requests, ref.requests):
+        if r.kind == "render" and r.rid != 5:
+            assert torch.equal(r.image.view(-1), q.image.view(-1)), r.rid
+    assert float((after_train.view(-1) - ref.requests[5].image.view(-1)).abs().max()) <= 1e-5
+    for sc, sn in zip(scenes, snaps):
+        _restore(sc, sn)
+
+
 def test_admission_keeps_working_sets_within_the_budget(scenes):
     from paper_2602_00395_gb300.serve import Server
     snaps = [_snapshot(sc) for sc in scenes]
