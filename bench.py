@@ -46,7 +46,7 @@ WORKLOAD = "batched multi-view: 1M Gaussians SH3, 20 clusters sigma 0.3 in radiu
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="cuda", choices=["cuda", "reference"])
     ap.add_argument("--n", type=int, default=N_GAUSS)
@@ -505,6 +505,28 @@ def raster_bwd_flops_per_unit() -> int:
     return 50 * (1 + NU)
 
 
+# DRAM bytes of one gs_raster_bwd call on this workload (its two kernels, read
+# plus write; the workspace clear is a memset, not counted) from one ncu capture
+# (profiles/raster_bwd_traffic_1M_8x1080p_nu2.md), valid while the kernel
+# sources are the ones captured (their SHA-256 below); otherwise null.
+RASTER_BWD_TRAFFIC = {
+    "bytes": 1527271936 + 200948992 + 1237430528 + 457128448,
+    "sources": {
+        "paper_2602_00395_gb300/csrc/raster.cu": "d7d704049fa50ff7ab51dcbcf30afeaa87a8d115d566d25585005b65c2036f98",
+        "paper_2602_00395_gb300/csrc/common.cuh": "bfe6a3217f01070a19f5ef6a2fdcd1c857224c8d9a736e2941a278567ea2aeac",
+    },
+}
+
+
+def raster_bwd_traffic():
+    import hashlib
+    for rel, digest in RASTER_BWD_TRAFFIC["sources"].items():
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest() != digest:
+                return None
+    return RASTER_BWD_TRAFFIC["bytes"]
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -676,11 +698,13 @@ def run_cuda(args):
     fwd_ms, bwd_ms = per_call["raster_fwd"], per_call["raster_bwd"]
     if fwd_ms >= bwd_ms:
         name, ms_k, per_unit = "gs_raster_fwd (blend + fused JVP, nu=2)", fwd_ms, raster_fwd_flops_per_unit()
+        traffic = None
     else:
         name, ms_k, per_unit = "gs_raster_bwd (reverse blend, 1+nu streams, + projection reverse)", bwd_ms, raster_bwd_flops_per_unit()
+        traffic = raster_bwd_traffic() if args.n == N_GAUSS else None
     achieved = per_unit * sum_nc / (ms_k * 1e-3) / 1e12
     roof = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-            "frac": achieved / fp32_peak, "traffic": None, "launch_ms": ms_k,
+            "frac": achieved / fp32_peak, "traffic": traffic, "launch_ms": ms_k,
             "peak_source": f"152 SMs x 128 FP32 lanes x 2 FLOP x {sm_mhz:.0f} MHz ({src} max SM clock)",
             "work": f"{per_unit} FLOP x {sum_nc:.4g} units (sum over pixels of n_contrib, all views)"}
     clocks = clk.summary()

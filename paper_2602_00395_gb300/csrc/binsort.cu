@@ -178,6 +178,41 @@ __global__ void __launch_bounds__(kScanThreads) scan_apply_kernel(const uint32_t
   }
 }
 
+// The whole scan in one block of 1024 threads (chunks of 8192 entries with a
+// carried total), for lengths where three dependent launches would cost more
+// than the work: the short histograms of small scenes.
+constexpr size_t kSingleScanMax = 65536;
+__global__ void __launch_bounds__(1024) scan_single_kernel(const uint32_t* in, uint32_t* out, size_t n_host,
+                                                           const uint32_t* pairs, uint64_t pair_capacity,
+                                                           uint32_t* __restrict__ total, uint64_t capacity,
+                                                           int32_t* __restrict__ status) {
+  __shared__ uint32_t s_warp[32];
+  const size_t n = scan_length(n_host, pairs, pair_capacity);
+  uint32_t carry = 0;
+  for (size_t base = 0; base < n; base += (size_t)1024 * kScanItems) {
+    const size_t b = base + (size_t)threadIdx.x * kScanItems;
+    uint32_t v[kScanItems];
+    uint32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+      v[k] = b + k < n ? in[b + k] : 0u;
+      s += v[k];
+    }
+    uint32_t tot;
+    uint32_t run = block_exclusive_scan(s, tot, s_warp) + carry;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+      if (b + k < n) out[b + k] = run;
+      run += v[k];
+    }
+    carry += tot;
+  }
+  if (threadIdx.x == 0) {
+    if (total) *total = carry;
+    if (capacity && (uint64_t)carry > capacity && status) atomicOr(status, GS_FLAG_CAPACITY);
+  }
+}
+
 inline int scan_blocks(size_t n) { return (int)((n + kScanChunk - 1) / kScanChunk); }
 
 // in -> out exclusive scan of n_max entries (in may equal out).  If `pairs` is
@@ -188,6 +223,10 @@ void exclusive_scan(const uint32_t* in, uint32_t* out, size_t n_max, const uint3
                     uint32_t* block_sums, uint32_t* total, uint64_t capacity, int32_t* status, cudaStream_t st) {
   const int nb = scan_blocks(n_max);
   if (nb == 0) return;
+  if (n_max <= kSingleScanMax) {
+    scan_single_kernel<<<1, 1024, 0, st>>>(in, out, n_max, pairs, pair_capacity, total, capacity, status);
+    return;
+  }
   scan_reduce_kernel<<<nb, kScanThreads, 0, st>>>(in, n_max, pairs, pair_capacity, block_sums);
   scan_blocks_kernel<<<1, 1024, 0, st>>>(block_sums, n_max, pairs, pair_capacity, total, capacity, status);
   scan_apply_kernel<<<nb, kScanThreads, 0, st>>>(in, out, n_max, pairs, pair_capacity, block_sums);

@@ -96,8 +96,9 @@ class TRStep:
         self.target = w(n_views * 3 * HW)
         self.status = torch.zeros(1, dtype=torch.int32, device=self.device)
         self.loss_val = z(1)
-        self.ranges = torch.zeros(2 * n_views * self.Tx * self.Ty, dtype=torch.int32, device=self.device)
-        self.n_pairs = torch.zeros(1, dtype=torch.int32, device=self.device)
+        zi = torch.zeros if zero_init else torch.empty  # gs_bin_sort clears both before use
+        self.ranges = zi(2 * n_views * self.Tx * self.Ty, dtype=torch.int32, device=self.device)
+        self.n_pairs = zi(1, dtype=torch.int32, device=self.device)
         self.bwd_ws = torch.empty(G.gs_raster_bwd_workspace_size(self.n_pad, self.frame, nu), dtype=torch.uint8,
                                   device=self.device)
         self.dssim_lambda = dssim_lambda
