@@ -1,0 +1,111 @@
+"""The large-scene configuration: 6M Gaussians (SH degree 3, the 20-cluster
+generator), one 1920x1080 view per step, one probe, the step's backward and
+Hutchinson product through torch.autograd.
+
+The render is `autograd.render`; the L1 objective of Sec. 3.2 is formed in
+PyTorch on its output, and `loss.backward()` runs the reverse pass from the
+image gradient (recomputing each T_i from the final T: nothing per pair is kept
+between the passes).  The Gauss-Newton diagonal comes from `gn_diagonal` with
+the L1 weights 1/(4 max(|r|, delta))/m.  Compared with the FP64 oracle on what
+it computes one by one:
+  * sampled pixels: colour (1e-5), final T and n_contrib, away from pixels with a
+    decision within rounding of a threshold;
+  * sampled Gaussians: gradient rows (1e-4 of the group's largest sampled
+    entry) and Hutchinson rows (1e-3 + 1e-6/delta, as at the benchmark size),
+    unless their own decisions are within rounding of flipping.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2602_00395_gb300 import synth as S
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+N, W, H, DEG = 6_000_000, 1920, 1080, 3
+GROUPS = {"mean": slice(0, 3), "log_scale": slice(3, 6), "quat": slice(6, 10), "opacity": slice(10, 11),
+          "sh": slice(11, None)}
+
+
+@pytest.fixture(scope="module")
+def large():
+    from paper_2602_00395_gb300.autograd import gn_diagonal, render
+    from paper_2602_00395_gb300.engine import TRConfig, TRStep
+    sc = S.make_scene(N, DEG, seed=1004, kind="clusters", extent=10.0)
+    cam = S.camera_ring(64, W, H, 10.0, seed=7)[5]
+    target = S.smooth_target(1, H, W, seed=2004)
+    torch.cuda.empty_cache()
+    torch.cuda.reset_peak_memory_stats()
+    e = TRStep(N, DEG, 1, W, H, nu=1, cfg=TRConfig(l=1))
+    e.set_cameras([cam])
+    e.set_params(sc.params)
+    e.ensure_capacity()
+    t = 3
+    tg = torch.from_numpy(target).cuda()
+    m = 3 * H * W
+    params = e.x.clone().requires_grad_(True)
+    img = render(params, e)
+    loss = (img - tg).abs().sum() / (2 * m)
+    loss.backward()
+    r = (img.detach() - tg)
+    w = 1.0 / (4.0 * torch.clamp(r.abs(), min=1e-3)) / m
+    hz = gn_diagonal(e, t, w)
+    torch.cuda.synchronize()
+    peak = torch.cuda.max_memory_allocated()
+    assert e.read_status() == 0
+    out = dict(sc=sc, cam=cam, target=target, t=t, img=img.detach()[0].cpu().numpy(),
+               final_T=e.final_T.view(H, W).cpu().numpy(), n_contrib=None, grad=params.grad[:, :N].cpu().numpy(),
+               hz=hz[:, :N].cpu().numpy(), radius=e.rec.view(1, e.n_pad, 12)[0, :N, 10].cpu().numpy().view(np.int32),
+               peak=peak, state_bytes=5 * e.rows * e.n_pad * 4, loss=float(loss.detach()))
+    # n_contrib of the plain render (gn_diagonal re-renders with the same lists)
+    out["n_contrib"] = e.n_contrib.view(H, W).cpu().numpy()
+    del e, params, img, hz
+    torch.cuda.empty_cache()
+    return out
+
+
+def test_memory_holds_no_per_pair_state(large):
+    """Peak device memory of the whole step: the five parameter-sized arrays
+    (x, two EMAs, gradient, z . Gz: 7.1 GB at 6M) plus the records, the pair
+    lists and the images; well under the 280 GB of the device."""
+    f = large
+    extra = f["peak"] - f["state_bytes"]
+    print(f"\nlarge scene: peak {f['peak'] / 1e9:.2f} GB, parameter-sized arrays {f['state_bytes'] / 1e9:.2f} GB")
+    assert f["peak"] < 24e9, f["peak"]
+    assert extra < 8e9, extra
+
+
+def test_sampled_pixels_match_oracle(large):
+    f = large
+    P = O.params64(f["sc"])
+    rng = np.random.default_rng(8)
+    xs = rng.integers(0, W, 48)
+    ys = rng.integers(0, H, 48)
+    with O.footprint_bins():  # the engine's default binning
+        ref = O.render_pixels(P, DEG, f["cam"], xs, ys)
+    ok = ref["margin"] >= 1e-5
+    assert ok.sum() >= 24
+    img = f["img"][:, ys, xs].T
+    assert np.abs(img - ref["rgb"])[ok].max() <= 1e-5
+    assert np.abs(f["final_T"][ys, xs] - ref["final_T"])[ok].max() <= 1e-5
+    assert np.array_equal(f["n_contrib"][ys, xs][ok], ref["n_contrib"][ok])
+
+
+def test_sampled_gaussians_match_oracle(large):
+    f = large
+    P = O.params64(f["sc"])
+    visible = np.nonzero(f["radius"] > 0)[0]
+    rng = np.random.default_rng(9)
+    smp = rng.choice(visible, 8, replace=False)
+    ref = O.backward_sampled(P, DEG, [f["cam"]], f["target"].astype(np.float64), smp, seed=42, t=f["t"], nu=1)
+    keep = (ref["flag"] & 7) == 0
+    assert keep.sum() >= 4, ref["flag"]
+    g_gpu, h_gpu = f["grad"][:, smp].T[keep], f["hz"][:, smp].T[keep]
+    g_ref, h_ref = ref["grad"][keep], ref["hz"][keep]
+    hz_tol = 1e-3 + 1e-6 / 1e-3
+    for name, sl in GROUPS.items():
+        gs = np.abs(g_ref[:, sl]).max()
+        hs = np.abs(h_ref[:, sl]).max()
+        assert np.abs(g_gpu[:, sl] - g_ref[:, sl]).max() <= 1e-4 * gs, name
+        assert np.abs(h_gpu[:, sl] - h_ref[:, sl]).max() <= hz_tol * hs, name
