@@ -90,8 +90,9 @@ typedef struct gs_camera {
  * tile_w is 8, 16 or 32, tile_h a power of two >= 8, tile_w * tile_h is 64, 128
  * or 256 (two pixels per thread; each warp covers an 8 x 8 pixel block).
  * footprint_bins selects the tiles of a splat (see gs_bin_sort): 0 its 3DGS tile
- * square, 1 that square narrowed to the box of its alpha >= 1/255 footprint.
- * Both give the same images and derivatives; 1 gives fewer pairs. */
+ * square, 1 that square narrowed to its alpha >= 1/255 footprint (its box, then
+ * row by row its ellipse).  Both give the same images and derivatives; 1 gives
+ * fewer pairs. */
 typedef struct gs_frame {
   int32_t n_views, width, height, tile_w, tile_h, footprint_bins;
 } gs_frame;
@@ -192,9 +193,14 @@ gs_status gs_project(const gs_params* x, const gs_camera* cams, gs_frame frame, 
  *   x0 = clamp(floor((mx - r)/tw), 0, Tx), x1 = clamp(floor((mx + (r + tw - 1))/tw), 0, Tx)
  * (the same for y); with frame.footprint_bins = 1 also
  *   x0 >= clamp(floor((mx - hx)/tw), 0, Tx), x1 <= clamp(floor((mx + hx)/tw) + 1, 0, Tx)
- * with hx, hy the record's footprint extents.  A tile outside that box holds no
- * pixel where the splat is blended (its alpha stays below 1/255 there), so the
- * box removes pairs but changes no image.  If the pairs
+ * with hx, hy the record's footprint extents, and then each tile row ty keeps
+ * the tiles from floor(xl/tw) to floor(xr/tw), where [xl, xr] is the footprint
+ * ellipse's extent over the row's band [ty th, (ty + 1) th], widened by 1 % of hx
+ * + 0.5 px: with rho = -B/sqrt(A C), v = (y - my)/hy, the ends are
+ * mx + hx (rho v +- sqrt((1 - rho^2)(1 - v^2))) at v = +-rho clamped into the
+ * band (a band outside |v| <= 1 keeps nothing), each step one FP32 rounding.
+ * A tile outside the footprint holds no pixel where the splat is blended (its
+ * alpha stays below 1/255 there), so this removes pairs but changes no image.  If the pairs
  * exceed out->capacity, GS_FLAG_CAPACITY is raised, *n_pairs holds the need,
  * and the sorted arrays are incomplete (but every access stays in bounds and
  * every range end is at most the capacity). */
@@ -211,7 +217,7 @@ gs_status gs_bin_sort(const gs_projected* proj, int32_t n_pad, gs_frame frame, v
  * scratch from a 32 MiB device array inside the library (held on every GPU that
  * loads the library until the process exits) and allocates nothing.
  *   - Limit: gs_bin_sort_workspace_size(n_pad, frame, out->capacity) must be at
- *     most 32 MiB (for example about 2 million pairs with 262,144 view x n_pad records);
+ *     most 32 MiB (for example 1 million pairs with 131,072 view x n_pad records);
  *     larger requests return GS_ERR_INVALID_ARG with an explanation.
  *   - The first call on each device, with that device current, looks up the
  *     array's device address (cudaGetSymbolAddress); make it before any stream

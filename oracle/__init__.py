@@ -54,9 +54,9 @@ def lib():
             L.or_project.argtypes = [P, i64, i64, i32, P, P]
             L.or_set_footprint_bins.argtypes = [i32]
             L.or_bin_sort.restype = i64
-            L.or_bin_sort.argtypes = [i32, i64, P, P, P, P, P, i32, i32, i32, i32, P, P, i64, P]
+            L.or_bin_sort.argtypes = [i32, i64, P, P, P, P, P, P, P, P, i32, i32, i32, i32, P, P, i64, P]
             L.or_render.restype = i64
-            L.or_render.argtypes = [P, i64, i64, i32, P, i32, i32, i32, P, P, P, P]
+            L.or_render.argtypes = [P, i64, i64, i32, P, i32, i32, i32, P, P, P, P, P]
             L.or_jvp.argtypes = [P, i64, i64, i32, P, i32, i32, i32, P, P]
             L.or_jacobian.argtypes = [P, i64, i64, i32, P, i32, i32, i32, P]
             L.or_backward_dssim.restype = d
@@ -73,7 +73,7 @@ def lib():
             L.or_adam_tr_update.argtypes = [P, P, P, P, i64, i64, i32, P, P, C.c_int64, d, P]
             L.or_project_tangent.argtypes = [P, i64, i64, i32, P, P, P]
             L.or_render_pixels.argtypes = [P, i64, i64, i32, P, i32, i32, i64, P, P, u64, C.c_int64, i32, P, P, P,
-                                           P, P]
+                                           P, P, P]
             L.or_backward_sampled.argtypes = [P, i64, i64, i32, P, i32, i32, i32, P, i32, d, u64, C.c_int64, i32,
                                               i64, P, P, P, P]
             L.or_signature.argtypes = [P, i64, i64, i32, P, i32, i32, i32, P]
@@ -194,25 +194,31 @@ def footprint_bins(on: bool = True):
         L.or_set_footprint_bins(0)
 
 
-def bin_sort(mx, my, radius, depth, width: int, height: int, tw: int = 16, th: int = 16, extents=None):
+def bin_sort(mx, my, radius, depth, width: int, height: int, tw: int = 16, th: int = 16, extents=None,
+             conic=None):
     """Pairs and tile ranges from FP32 splat records; arrays are [V, n] (or [n]).
     `extents` are the records' footprint half-extents as packed halves (uint32,
-    x in the low 16 bits), None for unbounded."""
+    x in the low 16 bits) and `conic` their (A, B, C), [3, V, n] (or [3, n]);
+    without extents the 3DGS square is binned."""
     mx = np.ascontiguousarray(np.atleast_2d(mx), np.float32)
     my = np.ascontiguousarray(np.atleast_2d(my), np.float32)
     rad = np.ascontiguousarray(np.atleast_2d(radius), np.int32)
     dp = np.ascontiguousarray(np.atleast_2d(depth), np.float32)
     ext = None if extents is None else np.ascontiguousarray(np.atleast_2d(extents), np.uint32)
     V, n = mx.shape
+    if conic is None:
+        cA, cB, cC = (np.zeros((V, n), np.float32) for _ in range(3))
+    else:
+        cA, cB, cC = (np.ascontiguousarray(np.asarray(c, np.float32).reshape(V, n)) for c in conic)
     T = ((width + tw - 1) // tw) * ((height + th - 1) // th)
     ranges = np.zeros((V * T, 2), np.uint32)
     L = lib()
     pe = None if ext is None else _p(ext)
-    P = L.or_bin_sort(V, n, _p(mx), _p(my), _p(rad), pe, _p(dp), width, height, tw, th, None, None, 0, _p(ranges))
+    args = (V, n, _p(mx), _p(my), _p(cA), _p(cB), _p(cC), _p(rad), pe, _p(dp), width, height, tw, th)
+    P = L.or_bin_sort(*args, None, None, 0, _p(ranges))
     keys = np.zeros(max(P, 1), np.uint64)
     vals = np.zeros(max(P, 1), np.uint32)
-    L.or_bin_sort(V, n, _p(mx), _p(my), _p(rad), pe, _p(dp), width, height, tw, th, _p(keys), _p(vals), P,
-                  _p(ranges))
+    L.or_bin_sort(*args, _p(keys), _p(vals), P, _p(ranges))
     return keys[:P], vals[:P], ranges
 
 
@@ -226,8 +232,12 @@ def render(P: np.ndarray, deg: int, cams, tw: int = 16, th: int = 16, with_margi
     T = np.zeros((V, H, W))
     nc = np.zeros((V, H, W), np.int32)
     mg = np.zeros((V, H, W)) if with_margin else None
-    pairs = lib().or_render(_p(P), n, n, deg, _p(ca), V, tw, th, _p(img), _p(T), _p(nc), _p(mg))
-    return dict(image=img, final_T=T, n_contrib=nc, margin=mg, n_pairs=int(pairs))
+    rng = np.zeros((V, H, W, 2), np.int32) if with_margin else None
+    pairs = lib().or_render(_p(P), n, n, deg, _p(ca), V, tw, th, _p(img), _p(T), _p(nc), _p(mg), _p(rng))
+    out = dict(image=img, final_T=T, n_contrib=nc, margin=mg, n_pairs=int(pairs))
+    if with_margin:
+        out["n_contrib_lo"], out["n_contrib_hi"] = rng[..., 0], rng[..., 1]
+    return out
 
 
 def jvp(P: np.ndarray, deg: int, cams, direction: np.ndarray, tw: int = 16, th: int = 16) -> np.ndarray:
@@ -361,7 +371,8 @@ def adam_tr_update(x, m, v, grad, deg: int, t: int, eps: float, cfg=None, adam=N
 # ------------------------------------------------------------- sampled outputs
 def render_pixels(P: np.ndarray, deg: int, cam, xs, ys, *, seed: int = 42, t: int = 1, nu: int = 0,
                   tw: int = 16, th: int = 16):
-    """Colour, T, n_contrib, margin and (nu > 0) image tangents at chosen pixels of one view."""
+    """Colour, T, n_contrib (and the range the tile sets within rounding allow),
+    margin and (nu > 0) image tangents at chosen pixels of one view."""
     P = _f64(P)
     rows, n = P.shape
     xs = np.ascontiguousarray(xs, np.int32)
@@ -372,9 +383,11 @@ def render_pixels(P: np.ndarray, deg: int, cam, xs, ys, *, seed: int = 42, t: in
     nc = np.zeros(k, np.int32)
     mg = np.zeros(k)
     jz = np.zeros((k, max(nu, 1), 3))
+    rng = np.zeros((k, 2), np.int32)
     lib().or_render_pixels(_p(P), n, n, deg, _p(camera_array([cam])), tw, th, k, _p(xs), _p(ys), seed, t, nu,
-                           _p(rgb), _p(T), _p(nc), _p(mg), _p(jz))
-    return dict(rgb=rgb, final_T=T, n_contrib=nc, margin=mg, jz=jz[:, :nu])
+                           _p(rgb), _p(T), _p(nc), _p(mg), _p(jz), _p(rng))
+    return dict(rgb=rgb, final_T=T, n_contrib=nc, margin=mg, jz=jz[:, :nu], n_contrib_lo=rng[:, 0],
+                n_contrib_hi=rng[:, 1])
 
 
 def backward_sampled(P: np.ndarray, deg: int, cams, target: np.ndarray, samples, *, loss_kind: int = 0,

@@ -352,15 +352,106 @@ uint32_t f32_bits(float f) {
   return u;
 }
 
+// Per-row tiles of a splat within its rectangle (Sec. 3.1 skip rule, as for
+// the box above): in units of the half-extents, u = dx/hx and v = dy/hy, the
+// footprint ellipse d^T Q d <= tau reads u^2 - 2 rho u v + v^2 <= 1 - rho^2 with
+// rho = -B / sqrt(A C) (hx^2 = tau C/det, hy^2 = tau A/det and the off-diagonal
+// of tau Q^-1 is rho hx hy).  For a tile row, whose band is its full height
+// [ty th, (ty + 1) th] in pixels, the ellipse's right end is
+// rho v + sqrt((1 - rho^2)(1 - v^2)) at v = rho clamped into the band, the left
+// end rho v - sqrt(...) at v = -rho clamped; both are widened by 1 % of hx +
+// 0.5 px, and the row keeps the tiles from floor(left / tw) to floor(right / tw)
+// within the rectangle.  A band outside |v| <= 1 keeps nothing.  Decided in
+// FP32, one rounding per operation, in this order.  Without finite positive
+// extents (or in the 3DGS-square mode) every row keeps the rectangle's row.
+struct FootRowsF {
+  float mx, my, hx, hy, rho, q, mgn;
+  int x0, x1, y0, y1;
+  bool exact;
+};
+
+FootRowsF foot_rows_f32(float mx, float my, float A, float B, float C, int r, float hx, float hy, bool footprint,
+                        int tw, int th, int Tx, int Ty) {
+  FootRowsF f;
+  rect_f32(mx, my, r, footprint ? hx : INFINITY, footprint ? hy : INFINITY, tw, th, Tx, Ty, f.x0, f.x1, f.y0, f.y1);
+  if (r <= 0) f.x1 = f.x0;
+  f.mx = mx;
+  f.my = my;
+  f.hx = hx;
+  f.hy = hy;
+  f.exact = footprint && hx > 0.0f && hy > 0.0f && hx < 65536.0f && hy < 65536.0f && A > 0.0f && C > 0.0f;
+  volatile float ac = A * C;
+  volatile float sq = std::sqrt((float)ac);
+  volatile float rho = -B / (float)sq;
+  const float rc = std::fmin(std::fmax((float)rho, -1.0f), 1.0f);
+  f.rho = f.exact ? rc : 0.0f;
+  volatile float r2 = f.rho * f.rho;
+  volatile float q = 1.0f - (float)r2;
+  f.q = std::fmax(0.0f, (float)q);
+  volatile float m1 = 0.01f * hx;
+  volatile float m2 = (float)m1 + 0.5f;
+  f.mgn = m2;
+  return f;
+}
+
+int clamp_floor_f32(float f, int hi) {
+  if (!(f > 0.0f)) return 0;  // also maps NaN to 0
+  if (f > (float)hi) return hi;
+  return (int)f;
+}
+
+// Tiles [a, b) of row ty.
+void row_span_f32(const FootRowsF& f, int ty, int tw, int th, int Tx, int& a, int& b) {
+  a = f.x0;
+  b = f.x1;
+  if (!f.exact) return;
+  volatile float ylo = (float)(ty * th) - f.my;
+  volatile float vlo = (float)ylo / f.hy;
+  volatile float yhi = (float)((ty + 1) * th) - f.my;
+  volatile float vhi = (float)yhi / f.hy;
+  if ((float)vhi < -1.0f || (float)vlo > 1.0f) {
+    b = a;
+    return;
+  }
+  const float vr = std::fmin(std::fmax(f.rho, (float)vlo), (float)vhi);
+  const float vl = std::fmin(std::fmax(-f.rho, (float)vlo), (float)vhi);
+  volatile float vr2 = vr * vr;
+  volatile float omr = 1.0f - (float)vr2;
+  volatile float tr = f.q * (float)omr;
+  volatile float sr = std::sqrt(std::fmax(0.0f, (float)tr));
+  volatile float vl2 = vl * vl;
+  volatile float oml = 1.0f - (float)vl2;
+  volatile float tl = f.q * (float)oml;
+  volatile float sl = std::sqrt(std::fmax(0.0f, (float)tl));
+  volatile float pr = f.rho * vr;
+  volatile float ur = (float)pr + (float)sr;
+  volatile float hr = f.hx * (float)ur;
+  volatile float xr0 = f.mx + (float)hr;
+  volatile float xr = (float)xr0 + f.mgn;
+  volatile float pl = f.rho * vl;
+  volatile float ul = (float)pl - (float)sl;
+  volatile float hl = f.hx * (float)ul;
+  volatile float xl0 = f.mx + (float)hl;
+  volatile float xl = (float)xl0 - f.mgn;
+  volatile float qa = (float)xl / (float)tw;
+  volatile float qb = (float)xr / (float)tw;
+  a = std::max(a, clamp_floor_f32(std::floor((float)qa), Tx));
+  b = std::min(b, clamp_floor_f32(std::floor((float)qb) + 1.0f, Tx));
+  if (b < a) b = a;
+}
+
 struct Pair {
   uint64_t key;
   uint32_t val;
 };
 
 // All (tile, splat) pairs of all views, sorted by (key, splat index); key =
-// (view * tiles_per_view + tile) << 32 | bits(depth).
-std::vector<Pair> bin_and_sort(int n_views, long n, const float* mx, const float* my, const int* rad,
-                               const float* hx, const float* hy, const float* depth, int W, int H, int tw, int th) {
+// (view * tiles_per_view + tile) << 32 | bits(depth).  `footprint`: the
+// rectangle narrowed to the extents' box and row by row to the ellipse;
+// otherwise the 3DGS square.
+std::vector<Pair> bin_and_sort(int n_views, long n, const float* mx, const float* my, const float* A,
+                               const float* B, const float* C, const int* rad, const float* hx, const float* hy,
+                               const float* depth, int W, int H, int tw, int th, bool footprint) {
   int Tx = (W + tw - 1) / tw, Ty = (H + th - 1) / th;
   long T = (long)Tx * Ty;
   std::vector<Pair> pairs;
@@ -368,13 +459,16 @@ std::vector<Pair> bin_and_sort(int n_views, long n, const float* mx, const float
     for (long i = 0; i < n; ++i) {
       long gi = (long)v * n + i;
       if (rad[gi] <= 0) continue;
-      int x0, x1, y0, y1;
-      rect_f32(mx[gi], my[gi], rad[gi], hx[gi], hy[gi], tw, th, Tx, Ty, x0, x1, y0, y1);
-      for (int ty = y0; ty < y1; ++ty)
-        for (int tx = x0; tx < x1; ++tx) {
+      const FootRowsF f =
+          foot_rows_f32(mx[gi], my[gi], A[gi], B[gi], C[gi], rad[gi], hx[gi], hy[gi], footprint, tw, th, Tx, Ty);
+      for (int ty = f.y0; ty < f.y1; ++ty) {
+        int a, b;
+        row_span_f32(f, ty, tw, th, Tx, a, b);
+        for (int tx = a; tx < b; ++tx) {
           uint64_t tile = (uint64_t)v * T + (uint64_t)ty * Tx + tx;
           pairs.push_back({(tile << 32) | f32_bits(depth[gi]), (uint32_t)i});
         }
+      }
     }
   std::sort(pairs.begin(), pairs.end(), [](const Pair& a, const Pair& b) {
     return a.key < b.key || (a.key == b.key && a.val < b.val);
@@ -393,7 +487,58 @@ struct View {
   std::vector<int> lo, hi;
   // per tile, the splats that may enter or leave it under rounding
   std::vector<std::vector<int>> amb;
+  // per splat: some tile of its own may enter or leave under rounding
+  std::vector<char> own_amb;
 };
+
+// Tiles whose membership in a splat's per-row spans may differ between the
+// oracle's FP32 decision and the GPU's (their inputs differ by rounding): for
+// every row of the grown rectangle, the tiles whose inclusion changes when the
+// FP64 left or right end moves by delta (those just outside the end: the tile
+// that holds the end is kept either way), and the whole row when its band is
+// within rounding of |v| = 1.
+// delta covers the half-precision step of hx (2^-10 relative), the error of rho
+// from the FP32 conic (growing as 1 - rho^2 shrinks), the shift of the clamped
+// v under the error of hy, and the centre's error.
+void row_end_ambiguity(const Splat<double>& s, float hx, float hy, const int* hi_rect, int tw, int th,
+                       std::vector<int>& tiles, int Tx) {
+  if (!(hx > 0.0f && hy > 0.0f && hx < 65536.0f && hy < 65536.0f && s.A > 0.0 && s.C > 0.0)) return;
+  const double rho = std::fmin(std::fmax(-s.B / std::sqrt(s.A * s.C), -1.0), 1.0);
+  const double q = std::fmax(0.0, 1.0 - rho * rho);
+  const double drho = 2e-6 / std::fmax(q, 1e-12) + 1e-6;
+  const double mgn = 0.01 * hx + 0.5;
+  // tiles [lo, hi] (clamped to the grown rectangle)
+  auto add_tiles = [&](double lo, double hi, int ty) {
+    const int a = std::max(hi_rect[0], (int)lo), b = std::min(hi_rect[1] - 1, (int)hi);
+    for (int tx = a; tx <= b; ++tx) tiles.push_back(ty * Tx + tx);
+  };
+  const double dv1 = 1.5e-3 + 1e-5;  // rounding of v near |v| = 1
+  for (int ty = hi_rect[2]; ty < hi_rect[3]; ++ty) {
+    const double vlo = (ty * th - s.my) / hy, vhi = ((ty + 1) * th - s.my) / hy;
+    if (vhi < -1.0 - dv1 || vlo > 1.0 + dv1) continue;
+    if (std::fabs(vhi + 1.0) <= dv1 || std::fabs(vlo - 1.0) <= dv1) {
+      for (int tx = hi_rect[0]; tx < hi_rect[1]; ++tx) tiles.push_back(ty * Tx + tx);
+      continue;
+    }
+    for (int side = 0; side < 2; ++side) {
+      const double sg = side == 0 ? 1.0 : -1.0;  // right end, then left end
+      const double v = std::fmin(std::fmax(sg * rho, vlo), vhi);
+      const double dv = 1.5e-3 * std::fabs(v) + 1e-5;
+      const double root = std::sqrt(std::fmax(0.0, 1.0 - v * v));
+      const double u = rho * v + sg * std::sqrt(q) * root;
+      const double va = std::fmax(0.0, std::fabs(v) - dv);
+      const double dsq = std::sqrt(std::fmax(0.0, 1.0 - va * va)) - root;
+      const double d = hx * (1.5e-3 + drho * (1.0 + 1.0 / std::sqrt(std::fmax(q, 1e-12))) +
+                             std::fabs(rho) * dv + std::sqrt(q) * dsq) +
+                       1e-5 * (1.0 + std::fabs(s.mx)) + 1e-4;
+      const double x = s.mx + hx * u + sg * mgn;
+      if (side == 0)  // right end: tiles up to floor(x / tw) are kept
+        add_tiles(std::floor((x - d) / tw) + 1, std::floor((x + d) / tw), ty);
+      else  // left end: tiles from floor(x / tw) on are kept
+        add_tiles(std::floor((x - d) / tw), std::floor((x + d) / tw) - 1, ty);
+    }
+  }
+}
 
 // Rounding envelopes of the FP32 inputs of a binning decision: the radius
 // (3 sqrt(lambda_max) from a chain of FP32 products, ~1e-6 relative, widened
@@ -416,15 +561,17 @@ View build_view(const double* P, long pitch, long n, int deg, const double* cam2
   V.Tx = (V.cam.W + tw - 1) / tw;
   V.Ty = (V.cam.H + th - 1) / th;
   V.sp.resize(n);
-  std::vector<float> mx(n), my(n), dp(n), hx(n), hy(n);
+  std::vector<float> mx(n), my(n), dp(n), hx(n), hy(n), cA(n), cB(n), cC(n);
   std::vector<int> rad(n);
   V.lo.assign(4 * n, 0);
   V.hi.assign(4 * n, 0);
+  V.own_amb.assign(n, 0);
   for (long i = 0; i < n; ++i) {
     G3<double> g = load_gaussian<double>(P, pitch, i, deg, nullptr);
     V.sp[i] = project(g, V.cam);
     const Splat<double>& s = V.sp[i];
     mx[i] = (float)s.mx; my[i] = (float)s.my; dp[i] = (float)s.depth;
+    cA[i] = (float)s.A; cB[i] = (float)s.B; cC[i] = (float)s.C;
     rad[i] = s.valid ? s.radius : 0;
     if (!s.valid) continue;
     float hx_lo = INFINITY, hy_lo = INFINITY, hx_hi = INFINITY, hy_hi = INFINITY;
@@ -450,19 +597,28 @@ View build_view(const double* P, long pitch, long n, int deg, const double* cam2
     rect_f32((float)(s.mx + ex), (float)(s.my + ey), r_hi, hx_hi, hy_hi, tw, th, V.Tx, V.Ty, c0, c1, d0, d1);
     V.hi[4 * i + 0] = a0; V.hi[4 * i + 1] = c1; V.hi[4 * i + 2] = b0; V.hi[4 * i + 3] = d1;
   }
-  std::vector<Pair> pairs = bin_and_sort(1, n, mx.data(), my.data(), rad.data(), hx.data(), hy.data(), dp.data(),
-                                         V.cam.W, V.cam.H, tw, th);
+  std::vector<Pair> pairs = bin_and_sort(1, n, mx.data(), my.data(), cA.data(), cB.data(), cC.data(), rad.data(),
+                                         hx.data(), hy.data(), dp.data(), V.cam.W, V.cam.H, tw, th,
+                                         g_footprint_bins != 0);
   V.lists.assign((size_t)V.Tx * V.Ty, {});
   for (const Pair& p : pairs) V.lists[p.key >> 32].push_back((int)p.val);
   V.amb.assign((size_t)V.Tx * V.Ty, {});
+  std::vector<int> tiles;
   for (long i = 0; i < n; ++i) {
     if (!V.sp[i].valid) continue;
     const int* h = &V.hi[4 * i];
     const int* l = &V.lo[4 * i];
-    if (h[0] == l[0] && h[1] == l[1] && h[2] == l[2] && h[3] == l[3]) continue;
-    for (int ty = h[2]; ty < h[3]; ++ty)
-      for (int tx = h[0]; tx < h[1]; ++tx)
-        if (!(tx >= l[0] && tx < l[1] && ty >= l[2] && ty < l[3])) V.amb[(size_t)ty * V.Tx + tx].push_back((int)i);
+    tiles.clear();
+    if (!(h[0] == l[0] && h[1] == l[1] && h[2] == l[2] && h[3] == l[3]))
+      for (int ty = h[2]; ty < h[3]; ++ty)
+        for (int tx = h[0]; tx < h[1]; ++tx)
+          if (!(tx >= l[0] && tx < l[1] && ty >= l[2] && ty < l[3])) tiles.push_back(ty * V.Tx + tx);
+    if (g_footprint_bins) row_end_ambiguity(V.sp[i], hx[i], hy[i], h, tw, th, tiles, V.Tx);
+    if (tiles.empty()) continue;
+    V.own_amb[i] = 1;
+    std::sort(tiles.begin(), tiles.end());
+    tiles.erase(std::unique(tiles.begin(), tiles.end()), tiles.end());
+    for (int t : tiles) V.amb[(size_t)t].push_back((int)i);
   }
   return V;
 }
@@ -522,8 +678,13 @@ void blend(const std::vector<int>& list, const std::vector<Splat<S>>& sp, double
 // within rounding of a boundary; +inf otherwise.  `nc` is the pixel's n_contrib:
 // a splat whose tile membership is ambiguous moves the list position of every
 // later splat, so it also makes n_contrib ambiguous when it sorts before the
-// pixel's last blended splat, visible or not.
-double binning_margin(const View& V, int tx, int ty, double pcx, double pcy, int nc = 0) {
+// pixel's last blended splat.  If it is not visible at the pixel (alpha below
+// half the skip threshold, so skipped on both sides) only n_contrib moves: with
+// nc_lo / nc_hi given, the range of n_contrib that the possible tile sets give
+// is written there ([nc - ambiguous splats in the list before it, nc + those not
+// in the list]) and the pixel is kept; without them it is excluded.
+double binning_margin(const View& V, int tx, int ty, double pcx, double pcy, int nc = 0, int* nc_lo = nullptr,
+                      int* nc_hi = nullptr) {
   const std::vector<int>& list = V.lists[(size_t)ty * V.Tx + tx];
   auto visible_at = [&](long i) {
     const Splat<double>& g = V.sp[i];
@@ -537,8 +698,20 @@ double binning_margin(const View& V, int tx, int ty, double pcx, double pcy, int
     const float di = (float)V.sp[i].depth, dj = (float)V.sp[j].depth;
     return di < dj || (di == dj && i <= j);
   };
-  for (int i : V.amb[(size_t)ty * V.Tx + tx])
-    if (visible_at(i) || before_last(i)) return 0.0;
+  int in_list = 0, off_list = 0;
+  for (int i : V.amb[(size_t)ty * V.Tx + tx]) {
+    if (visible_at(i)) return 0.0;
+    if (!before_last(i)) continue;
+    if (!nc_lo) return 0.0;
+    if (std::find(list.begin(), list.end(), i) != list.end())
+      ++in_list;
+    else
+      ++off_list;
+  }
+  if (nc_lo) {
+    *nc_lo = nc - in_list;
+    *nc_hi = nc + off_list;
+  }
   for (size_t k = 1; k < list.size(); ++k) {
     double d0 = V.sp[list[k - 1]].depth, d1 = V.sp[list[k]].depth;
     if (std::fabs(d1 - d0) <= 1e-6 * std::fabs(d1) && visible_at(list[k - 1]) && visible_at(list[k]))
@@ -1002,19 +1175,20 @@ void or_project(const double* P, long pitch, long n, int deg, const double* cam2
 void or_set_footprint_bins(int on) { g_footprint_bins = on ? 1 : 0; }
 
 // Binning and depth sort from FP32 splat records of n_views views (arrays are
-// n_views x n).  `ext` holds each record's footprint half-extents as packed
-// halves (x low, y high), or is null for +inf.  Writes up to `cap` pairs and the [start, end) range of every
+// n_views x n; A, B, C the conic).  `ext` holds each record's footprint
+// half-extents as packed halves (x low, y high); null bins by the 3DGS square.  Writes up to `cap` pairs and the [start, end) range of every
 // tile (2 x n_views x tiles); returns the number of pairs.
-long or_bin_sort(int n_views, long n, const float* mx, const float* my, const int* rad, const uint32_t* ext,
-                 const float* depth, int W, int H, int tw, int th, uint64_t* keys, uint32_t* vals, long cap,
-                 uint32_t* ranges) {
+long or_bin_sort(int n_views, long n, const float* mx, const float* my, const float* A, const float* B,
+                 const float* C, const int* rad, const uint32_t* ext, const float* depth, int W, int H, int tw,
+                 int th, uint64_t* keys, uint32_t* vals, long cap, uint32_t* ranges) {
   std::vector<float> hx((size_t)n_views * n, INFINITY), hy((size_t)n_views * n, INFINITY);
   if (ext)
     for (long g = 0; g < (long)n_views * n; ++g) {
       hx[g] = half_to_float((uint16_t)(ext[g] & 0xffffu));
       hy[g] = half_to_float((uint16_t)(ext[g] >> 16));
     }
-  std::vector<Pair> pairs = bin_and_sort(n_views, n, mx, my, rad, hx.data(), hy.data(), depth, W, H, tw, th);
+  std::vector<Pair> pairs =
+      bin_and_sort(n_views, n, mx, my, A, B, C, rad, hx.data(), hy.data(), depth, W, H, tw, th, ext != nullptr);
   long T = (long)((W + tw - 1) / tw) * ((H + th - 1) / th);
   for (long k = 0; k < 2 * T * n_views; ++k) ranges[k] = 0;
   for (long p = 0; p < (long)pairs.size(); ++p) {
@@ -1029,9 +1203,11 @@ long or_bin_sort(int n_views, long n, const float* mx, const float* my, const in
 // Render every view.  image: V x 3 x H x W, final_T and margin: V x H x W,
 // n_contrib: V x H x W.  margin is the smallest relative distance of a threshold
 // decision at the pixel, or 0 where binning is within rounding of a boundary.
-// Returns the total number of (tile, splat) pairs.
+// nc_range (V x H x W x 2, may be null): the range of n_contrib that the tile
+// sets within rounding give (see binning_margin).  Returns the total number of
+// (tile, splat) pairs.
 long or_render(const double* P, long pitch, long n, int deg, const double* cams, int n_views, int tw, int th,
-               double* image, double* final_T, int32_t* n_contrib, double* margin) {
+               double* image, double* final_T, int32_t* n_contrib, double* margin, int32_t* nc_range) {
   long pairs = 0;
   for (int v = 0; v < n_views; ++v) {
     View V = build_view(P, pitch, n, deg, cams + 24 * v, tw, th);
@@ -1046,7 +1222,13 @@ long or_render(const double* P, long pitch, long n, int deg, const double* cams,
       for (int ch = 0; ch < 3; ++ch) img[ch * HW + px] = C[ch];
       final_T[v * HW + px] = T;
       n_contrib[v * HW + px] = nc;
-      if (margin) margin[v * HW + px] = std::min(mg, binning_margin(V, tx, ty, x + 0.5, y + 0.5, nc));
+      int lo = nc, hi = nc;
+      if (margin)
+        margin[v * HW + px] = std::min(mg, binning_margin(V, tx, ty, x + 0.5, y + 0.5, nc, &lo, &hi));
+      if (nc_range) {
+        nc_range[2 * (v * HW + px)] = lo;
+        nc_range[2 * (v * HW + px) + 1] = hi;
+      }
     });
   }
   return pairs;
@@ -1392,11 +1574,11 @@ std::vector<Splat<Dual>> tile_tangents(const View& V, const std::vector<int>& li
 }
 
 // Sampled pixels of one view (coordinates xs, ys): colour (npix x 3), final T,
-// n_contrib, the decision margin as in or_render, and, if nu > 0, the image
-// tangents J z_k (npix x nu x 3) for the probes of (seed, t).
+// n_contrib, the decision margin and n_contrib range as in or_render, and, if
+// nu > 0, the image tangents J z_k (npix x nu x 3) for the probes of (seed, t).
 void or_render_pixels(const double* P, long pitch, long n, int deg, const double* cam24, int tw, int th, long npix,
                       const int32_t* xs, const int32_t* ys, uint64_t seed, int64_t t, int nu, double* rgb,
-                      double* T_out, int32_t* nc_out, double* margin, double* jz) {
+                      double* T_out, int32_t* nc_out, double* margin, double* jz, int32_t* nc_range) {
   View V = build_view(P, pitch, n, deg, cam24, tw, th);
   std::vector<int> local;
   for (long q = 0; q < npix; ++q) {
@@ -1408,7 +1590,12 @@ void or_render_pixels(const double* P, long pitch, long n, int deg, const double
     for (int ch = 0; ch < 3; ++ch) rgb[3 * q + ch] = C[ch];
     T_out[q] = T;
     nc_out[q] = nc;
-    margin[q] = std::min(mg, binning_margin(V, tx, ty, x + 0.5, y + 0.5, nc));
+    int lo = nc, hi = nc;
+    margin[q] = std::min(mg, binning_margin(V, tx, ty, x + 0.5, y + 0.5, nc, &lo, &hi));
+    if (nc_range) {
+      nc_range[2 * q] = lo;
+      nc_range[2 * q + 1] = hi;
+    }
     if (nu > 0) {
       local.resize(list.size());
       for (size_t u = 0; u < list.size(); ++u) local[u] = (int)u;

@@ -4,7 +4,8 @@
 // Every pair of one splat shares its depth, so the order (tile, depth, splat)
 // is built in two stages instead of sorting 64-bit pair keys on all their bits:
 //
-//   records  per (view, splat): tiles of its FP32 rectangle; the V x n_pad
+//   records  per (view, splat): its tiles (the FP32 rectangle, narrowed row
+//            by row to the footprint ellipse, see row_span); the V x n_pad
 //            records are sorted by (view, depth bits) with a stable LSD radix
 //            sort (record index order breaks ties)
 //   scan     emission offsets in that order and the pair count P
@@ -38,41 +39,20 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
   return m;
 }
 
-// The extents word binning uses: the record's, or +inf (the 3DGS square alone).
-__device__ __forceinline__ uint32_t bin_extents(const gs_frame& fr, float w) {
-  return fr.footprint_bins ? __float_as_uint(w) : 0x7C007C00u;
-}
-
-// ------------------------------------------------------------------ records
-// counts[g] = tiles of record g's rectangle; rkeys[g] = bits(depth) (sorted
-// within each view's segment); rvals[g] = g.
-__global__ void record_keys_kernel(const float4* __restrict__ rec, int n_pad, gs_frame fr, int Tx, int Ty,
-                                   uint32_t* __restrict__ counts, uint32_t* __restrict__ rkeys,
-                                   uint32_t* __restrict__ rvals) {
-  const size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= (size_t)fr.n_views * n_pad) return;
+// The tile rows of record g (see foot_rows).
+__device__ __forceinline__ FootRows record_rows(const float4* __restrict__ rec, size_t g, const gs_frame& fr, int Tx,
+                                                int Ty, float& depth) {
   const float4 a = rec[3 * g + 0];
+  const float4 b = rec[3 * g + 1];
   const float4 c = rec[3 * g + 2];
+  depth = c.y;
   const int r = __float_as_int(c.z);
-  uint32_t cnt = 0;
-  if (r > 0) {
-    int x0, x1, y0, y1;
-    tile_rect(a.x, a.y, r, bin_extents(fr, c.w), fr.tile_w, fr.tile_h, Tx, Ty, x0, x1, y0, y1);
-    cnt = (uint32_t)max(0, x1 - x0) * (uint32_t)max(0, y1 - y0);
-  }
-  counts[g] = cnt;
-  rkeys[g] = __float_as_uint(c.y);
-  rvals[g] = (uint32_t)g;
+  FootRows f = foot_rows(a.x, a.y, a.z, a.w, b.x, r, __float_as_uint(c.w), fr.footprint_bins != 0, fr.tile_w,
+                         fr.tile_h, Tx, Ty);
+  if (r <= 0) f.x1 = f.x0;  // culled: no tiles
+  return f;
 }
 
-// scnt[p] = counts of the record at sorted position p
-__global__ void gather_counts_kernel(const uint32_t* __restrict__ order, const uint32_t* __restrict__ counts,
-                                     uint32_t* __restrict__ scnt, size_t items) {
-  const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p < items) scnt[p] = counts[order[p]];
-}
-
-// ------------------------------------------------------------------- scan
 // Block-wide exclusive scan of one value per thread; returns the block total.
 __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t& total, uint32_t* s_warp) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -101,6 +81,63 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t& t
   return before + x - v;
 }
 
+// ------------------------------------------------------------------ records
+// Per record g: counts[g] = its pairs; rkeys[g] = bits(depth) (then sorted
+// within each view's segment); rvals[g] = g; and its row table for the emit:
+// one entry per row of its rectangle, (pairs in the rows above, first tile),
+// allocated from `rows` by one atomic per block, and the header
+// hdr[g] = (bits(depth), first row | rows << 16, table offset, pairs).  The
+// table holds at most 2 empty rows per record beyond its pairs (non-empty rows
+// are contiguous), so rows_cap = pair capacity + 2 x records overflows only with
+// the pairs; then the record keeps no table and GS_FLAG_CAPACITY is raised.
+__global__ void record_keys_kernel(const float4* __restrict__ rec, int n_pad, gs_frame fr, int Tx, int Ty,
+                                   uint32_t* __restrict__ counts, uint32_t* __restrict__ rkeys,
+                                   uint32_t* __restrict__ rvals, uint4* __restrict__ hdr, uint2* __restrict__ rows,
+                                   uint64_t rows_cap, uint32_t* __restrict__ rows_used, int32_t* __restrict__ status) {
+  __shared__ uint32_t s_warp[32];
+  __shared__ uint32_t s_base;
+  const size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool in = g < (size_t)fr.n_views * n_pad;
+  float depth = 0.f;
+  FootRows f{};
+  uint32_t R = 0;
+  if (in) {
+    f = record_rows(rec, g, fr, Tx, Ty, depth);
+    if (f.x1 > f.x0 && f.y1 > f.y0) R = (uint32_t)(f.y1 - f.y0);
+  }
+  uint32_t total;
+  const uint32_t ex = block_exclusive_scan(R, total, s_warp);
+  if (threadIdx.x == 0) s_base = total ? atomicAdd(rows_used, total) : 0u;
+  __syncthreads();
+  if (!in) return;
+  const uint32_t off = s_base + ex;
+  uint32_t cnt = 0;
+  if (R && (uint64_t)off + R <= rows_cap) {
+    for (uint32_t k = 0; k < R; ++k) {
+      int a, b;
+      row_span(f, f.y0 + (int)k, fr.tile_w, fr.tile_h, Tx, a, b);
+      rows[(size_t)off + k] = make_uint2(cnt, (uint32_t)a);
+      cnt += (uint32_t)(b - a);
+    }
+  } else if (R) {
+    cnt = foot_count(f, fr.tile_w, fr.tile_h, Tx);
+    R = 0;
+    if (status) atomicOr(status, GS_FLAG_CAPACITY);
+  }
+  counts[g] = cnt;
+  hdr[g] = make_uint4(__float_as_uint(depth), (uint32_t)f.y0 | (R << 16), off, cnt);
+  rkeys[g] = __float_as_uint(depth);
+  rvals[g] = (uint32_t)g;
+}
+
+// scnt[p] = counts of the record at sorted position p
+__global__ void gather_counts_kernel(const uint32_t* __restrict__ order, const uint32_t* __restrict__ counts,
+                                     uint32_t* __restrict__ scnt, size_t items) {
+  const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < items) scnt[p] = counts[order[p]];
+}
+
+// ------------------------------------------------------------------- scan
 // Length of a scan: n, or, when `pairs` is given, the radix histogram length
 // 256 * ceil(min(*pairs, capacity) / tile) of the pairs in use.
 __device__ __forceinline__ size_t scan_length(size_t n, const uint32_t* pairs, uint64_t capacity) {
@@ -235,31 +272,25 @@ void exclusive_scan(const uint32_t* in, uint32_t* out, size_t n_max, const uint3
 // ------------------------------------------------------------------- emit
 // One warp emits the pairs of 32 consecutive records in (view, depth) order.
 // Their output ranges are contiguous (the offsets are an exclusive scan in that
-// order), so the warp
-// writes its whole range with consecutive lanes on consecutive pairs; each lane
-// finds the record that owns its pair by a binary search over the warp's
-// prefix sums.
-__global__ void emit_kernel(const float4* __restrict__ rec, int n_pad, gs_frame fr, int Tx, int Ty,
-                            const uint32_t* __restrict__ order, const uint32_t* __restrict__ offsets,
+// order), so the warp writes its whole range with consecutive lanes on
+// consecutive pairs; each lane finds the record that owns its pair by a binary
+// search over the warp's prefix sums, and the pair's row by a binary search
+// over that record's row table (see record_keys_kernel).
+__global__ void emit_kernel(const uint4* __restrict__ hdr, const uint2* __restrict__ rows, int n_pad, gs_frame fr,
+                            int Tx, int Ty, const uint32_t* __restrict__ order, const uint32_t* __restrict__ offsets,
                             uint64_t capacity, uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
   const size_t G = (size_t)fr.n_views * n_pad;
   const size_t p0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x;  // sorted record position
   const size_t w0 = p0 - (threadIdx.x & 31);
   if (w0 >= G) return;  // whole warp
   const int lane = threadIdx.x & 31;
-  int x0 = 0, x1 = 0, y0 = 0, y1 = 0;
-  uint32_t cnt = 0, depth_bits = 0, g = 0;
+  uint32_t g = 0;
+  uint4 h = make_uint4(0u, 0u, 0u, 0u);
   if (p0 < G) {
     g = order[p0];
-    const float4 c = rec[3 * (size_t)g + 2];
-    const int r = __float_as_int(c.z);
-    if (r > 0) {
-      const float4 a = rec[3 * (size_t)g + 0];
-      tile_rect(a.x, a.y, r, bin_extents(fr, c.w), fr.tile_w, fr.tile_h, Tx, Ty, x0, x1, y0, y1);
-      cnt = (uint32_t)max(0, x1 - x0) * (uint32_t)max(0, y1 - y0);
-    }
-    depth_bits = __float_as_uint(c.y);
+    h = hdr[g];
   }
+  const uint32_t cnt = h.w;
   // inclusive warp scan of the counts
   uint32_t incl = cnt;
 #pragma unroll
@@ -283,23 +314,36 @@ __global__ void emit_kernel(const float4* __restrict__ rec, int n_pad, gs_frame 
       if (cand < 32 && sc <= p) lo = cand;
     }
     const uint32_t o_start = __shfl_sync(0xffffffffu, start, lo);
-    const int ox0 = __shfl_sync(0xffffffffu, x0, lo);
-    const int ox1 = __shfl_sync(0xffffffffu, x1, lo);
-    const int oy0 = __shfl_sync(0xffffffffu, y0, lo);
-    const uint32_t od = __shfl_sync(0xffffffffu, depth_bits, lo);
     const uint32_t og32 = __shfl_sync(0xffffffffu, g, lo);
-    if (p < total) {
-      const uint64_t at = base + p;
-      if (at < capacity) {
-        const size_t og = og32;
-        const int oview = (int)(og / n_pad);
+    const uint32_t od = __shfl_sync(0xffffffffu, h.x, lo);
+    const uint32_t oyr = __shfl_sync(0xffffffffu, h.y, lo);
+    const uint32_t ooff = __shfl_sync(0xffffffffu, h.z, lo);
+    const uint32_t R = oyr >> 16;
+    const uint64_t at = base + p;
+    if (p < total && at < capacity) {
+      const size_t og = og32;
+      const int oview = (int)(og / n_pad);
+      uint64_t tile = (uint64_t)oview * tiles;
+      if (R > 0) {
         const uint32_t q = p - o_start;
-        const uint32_t w = (uint32_t)(ox1 - ox0);
-        const uint32_t tyy = (uint32_t)oy0 + q / w, txx = (uint32_t)ox0 + q % w;
-        const uint64_t tile = (uint64_t)oview * tiles + (uint64_t)tyy * Tx + txx;
-        keys[at] = (tile << 32) | (uint64_t)od;
-        vals[at] = (uint32_t)(og - (size_t)oview * n_pad);
+        // last row whose pairs above are <= q (empty rows repeat the count before them)
+        uint32_t a = 0, b = R - 1;
+        while (a < b) {
+          const uint32_t mid = (a + b + 1) >> 1;
+          if (__ldg(&rows[(size_t)ooff + mid].x) <= q) a = mid; else b = mid - 1;
+        }
+        const uint2 e = __ldg(&rows[(size_t)ooff + a]);
+        // q - e.x < the row's pairs, so txx stays in the row; the clamp only
+        // keeps every tile index inside the view if that ever failed
+        const uint32_t txx = min(e.y + (q - e.x), (uint32_t)(Tx - 1));
+        tile += (uint64_t)((oyr & 0xffffu) + a) * Tx + txx;
       }
+      // (R == 0 with pairs: the record's row table did not fit, which happens
+      // only when the pairs exceed the capacity and GS_FLAG_CAPACITY is raised;
+      // its slots still get a valid tile and splat so that every slot below the
+      // capacity holds an in-range pair)
+      keys[at] = (tile << 32) | (uint64_t)od;
+      vals[at] = (uint32_t)(og - (size_t)oview * n_pad);
     }
   }
 }
@@ -478,7 +522,7 @@ __device__ __forceinline__ uint32_t pairs_in_use(const uint32_t* n_pairs, uint64
 // them; a tile starts where its key differs from the previous one and ends
 // where it differs from the next.
 __global__ void ranges_kernel(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ n_pairs,
-                              uint64_t capacity, uint32_t* __restrict__ ranges) {
+                              uint64_t capacity, uint64_t n_tiles, uint32_t* __restrict__ ranges) {
   const uint32_t P = pairs_in_use(n_pairs, capacity);
   const size_t step = (size_t)gridDim.x * blockDim.x * 4;
   for (size_t p0 = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) * 4; p0 < P; p0 += step) {
@@ -497,7 +541,7 @@ __global__ void ranges_kernel(const uint64_t* __restrict__ keys, const uint32_t*
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const size_t p = p0 + k;
-      if (p < P) {
+      if (p < P && tl[k] < n_tiles) {  // every emitted tile is below n_tiles; the test guards the writes
         if (tl[k] != prev) ranges[2 * (size_t)tl[k]] = (uint32_t)p;
         if (tl[k + 1] != tl[k]) ranges[2 * (size_t)tl[k] + 1] = (uint32_t)(p + 1);
       }
@@ -512,7 +556,9 @@ inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 struct SortPlan {
   int Tx, Ty, rec_pass, pair_pass, nb_pairs, rec_bps;
   size_t n_items;  // views x n_pad
-  size_t off_counts, off_scnt, off_sums, off_rk0, off_rk1, off_rv0, off_rv1, off_keys, off_vals, off_hist, total;
+  size_t off_counts, off_scnt, off_sums, off_rk0, off_rk1, off_rv0, off_rv1, off_keys, off_vals, off_hist, off_hdr,
+      off_rows, off_used, total;
+  uint64_t rows_cap;
 };
 
 inline int bits_for(uint64_t v) {  // smallest b with 2^b >= v
@@ -544,6 +590,10 @@ SortPlan plan_sort(int32_t n_pad, gs_frame fr, uint64_t capacity) {
   p.off_keys = o;   o += align256(capacity * 8);
   p.off_vals = o;   o += align256(capacity * 4);
   p.off_hist = o;   o += align256(hist_n * 4);
+  p.rows_cap = std::min<uint64_t>(capacity + 2 * (uint64_t)p.n_items, 0xffffffffull);
+  p.off_hdr = o;    o += align256(p.n_items * 16);
+  p.off_rows = o;   o += align256(p.rows_cap * 8);
+  p.off_used = o;   o += 256;
   p.total = o;
   return p;
 }
@@ -585,6 +635,7 @@ extern "C" gs_status gs_bin_sort(const gs_projected* proj, int32_t n_pad, gs_fra
   GS_REQUIRE(frame_ok(frame), "gs_bin_sort: bad frame (tile %dx%d)", frame.tile_w, frame.tile_h);
   GS_REQUIRE(out->capacity > 0 && out->capacity < (1ull << 32), "gs_bin_sort: capacity must be in [1, 2^32)");
   const SortPlan p = plan_sort(n_pad, frame, out->capacity);
+  GS_REQUIRE(p.Tx < 65536 && p.Ty < 65536, "gs_bin_sort: at most 65535 tiles per row and column");
   GS_REQUIRE(workspace && workspace_bytes >= p.total, "gs_bin_sort: workspace needs %zu bytes, got %zu", p.total,
              workspace_bytes);
   cudaStream_t st = (cudaStream_t)stream;
@@ -596,15 +647,20 @@ extern "C" gs_status gs_bin_sort(const gs_projected* proj, int32_t n_pad, gs_fra
   const float4* rec = reinterpret_cast<const float4*>(proj->rec);
   const uint64_t T = (uint64_t)p.Tx * p.Ty;
 
+  uint4* hdr = (uint4*)(ws + p.off_hdr);
+  uint2* rows = (uint2*)(ws + p.off_rows);
+  uint32_t* rows_used = (uint32_t*)(ws + p.off_used);
   if (cudaMemsetAsync(out->ranges, 0, (size_t)frame.n_views * T * 2 * sizeof(uint32_t), st) != cudaSuccess ||
-      cudaMemsetAsync(out->n_pairs, 0, sizeof(uint32_t), st) != cudaSuccess)
+      cudaMemsetAsync(out->n_pairs, 0, sizeof(uint32_t), st) != cudaSuccess ||
+      cudaMemsetAsync(rows_used, 0, sizeof(uint32_t), st) != cudaSuccess)
     return check_launch("gs_bin_sort: memset");
   if (p.n_items == 0) return GS_OK;
   const int eb = (int)((p.n_items + 255) / 256);
   // records sorted by depth within each view's segment
   uint32_t* rk[2] = {(uint32_t*)(ws + p.off_rk0), (uint32_t*)(ws + p.off_rk1)};
   uint32_t* rv[2] = {(uint32_t*)(ws + p.off_rv0), (uint32_t*)(ws + p.off_rv1)};
-  record_keys_kernel<<<eb, 256, 0, st>>>(rec, n_pad, frame, p.Tx, p.Ty, counts, rk[0], rv[0]);
+  record_keys_kernel<<<eb, 256, 0, st>>>(rec, n_pad, frame, p.Tx, p.Ty, counts, rk[0], rv[0], hdr, rows, p.rows_cap,
+                                         rows_used, status);
   int rcur = 0;
   const Seg rseg{nullptr, 0, (uint32_t)n_pad, (uint32_t)n_pad};
   radix_passes<uint32_t>(rk, rv, rcur, p.rec_pass, 0, rseg, frame.n_views, p.rec_bps, hist, sums, st);
@@ -616,10 +672,12 @@ extern "C" gs_status gs_bin_sort(const gs_projected* proj, int32_t n_pad, gs_fra
   uint64_t* kbuf[2] = {out->keys, (uint64_t*)(ws + p.off_keys)};
   uint32_t* vbuf[2] = {out->vals, (uint32_t*)(ws + p.off_vals)};
   int cur = (p.pair_pass % 2 == 0) ? 0 : 1;
-  emit_kernel<<<eb, 256, 0, st>>>(rec, n_pad, frame, p.Tx, p.Ty, rv[rcur], scnt, out->capacity, kbuf[cur], vbuf[cur]);
+  emit_kernel<<<eb, 256, 0, st>>>(hdr, rows, n_pad, frame, p.Tx, p.Ty, rv[rcur], scnt, out->capacity, kbuf[cur],
+                                  vbuf[cur]);
   const Seg pseg{out->n_pairs, out->capacity, 0, 0};
   radix_passes<uint64_t>(kbuf, vbuf, cur, p.pair_pass, 32, pseg, 1, p.nb_pairs, hist, sums, st);
   const int rb = (int)std::min<uint64_t>((out->capacity + 255) / 256, 152 * 16);
-  ranges_kernel<<<rb, 256, 0, st>>>(out->keys, out->n_pairs, out->capacity, out->ranges);
+  ranges_kernel<<<rb, 256, 0, st>>>(out->keys, out->n_pairs, out->capacity, (uint64_t)frame.n_views * T,
+                                    out->ranges);
   return check_launch("gs_bin_sort");
 }

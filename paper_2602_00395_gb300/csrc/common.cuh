@@ -341,6 +341,77 @@ __device__ __forceinline__ void tile_rect(float mx, float my, int r, uint32_t ex
            clamp_floor(__fadd_rn(floorf(__fdiv_rn(__fadd_rn(my, hy), fth)), 1.0f), Ty));
 }
 
+// ------------------------------------------------------- per-row tile spans
+// Within the rectangle above, each tile row keeps only the tiles that the
+// footprint ellipse reaches.  In units of the half-extents (u = dx/hx,
+// v = dy/hy) the ellipse d^T Q d <= tau is u^2 - 2 rho u v + v^2 <= 1 - rho^2
+// with rho = -B / sqrt(A C), because hx^2 = tau C/det, hy^2 = tau A/det and the
+// off-diagonal of tau Q^-1 is rho hx hy.  Over the row's band of v the right
+// end u = rho v + sqrt((1 - rho^2)(1 - v^2)) peaks at v = rho and the left end
+// at v = -rho, so each is taken at that v clamped into the band.  The band is
+// the tile row's full height; the ends are widened by 1 % of hx + 0.5 px, which
+// covers the different rounding-up of hx and hy.  Every operation is one FP32
+// rounding (the order is part of the binning rule).  Without finite positive
+// extents (or with footprint_bins = 0) a row keeps the whole rectangle row.
+struct FootRows {
+  float mx, my, hx, hy, rho, q, mgn;
+  int x0, x1, y0, y1;
+  bool exact;
+};
+
+__device__ __forceinline__ FootRows foot_rows(float mx, float my, float A, float B, float C, int r, uint32_t ext,
+                                              bool footprint, int tw, int th, int Tx, int Ty) {
+  FootRows f;
+  tile_rect(mx, my, r, footprint ? ext : 0x7C007C00u, tw, th, Tx, Ty, f.x0, f.x1, f.y0, f.y1);
+  f.mx = mx;
+  f.my = my;
+  f.hx = __half2float(__ushort_as_half((unsigned short)(ext & 0xffffu)));
+  f.hy = __half2float(__ushort_as_half((unsigned short)(ext >> 16)));
+  f.exact = footprint && f.hx > 0.f && f.hy > 0.f && f.hx < 65536.f && f.hy < 65536.f && A > 0.f && C > 0.f;
+  float rho = __fdiv_rn(-B, __fsqrt_rn(__fmul_rn(A, C)));
+  rho = fminf(fmaxf(rho, -1.f), 1.f);
+  f.rho = f.exact ? rho : 0.f;
+  f.q = fmaxf(0.f, __fsub_rn(1.f, __fmul_rn(f.rho, f.rho)));
+  f.mgn = __fadd_rn(__fmul_rn(0.01f, f.hx), 0.5f);
+  return f;
+}
+
+// Tiles [a, b) of row ty.
+__device__ __forceinline__ void row_span(const FootRows& f, int ty, int tw, int th, int Tx, int& a, int& b) {
+  a = f.x0;
+  b = f.x1;
+  if (!f.exact) return;
+  const float vlo = __fdiv_rn(__fsub_rn((float)(ty * th), f.my), f.hy);
+  const float vhi = __fdiv_rn(__fsub_rn((float)((ty + 1) * th), f.my), f.hy);
+  if (vhi < -1.f || vlo > 1.f) {
+    b = a;
+    return;
+  }
+  const float vr = fminf(fmaxf(f.rho, vlo), vhi);
+  const float vl = fminf(fmaxf(-f.rho, vlo), vhi);
+  const float sr = __fsqrt_rn(fmaxf(0.f, __fmul_rn(f.q, __fsub_rn(1.f, __fmul_rn(vr, vr)))));
+  const float sl = __fsqrt_rn(fmaxf(0.f, __fmul_rn(f.q, __fsub_rn(1.f, __fmul_rn(vl, vl)))));
+  const float xr = __fadd_rn(__fadd_rn(f.mx, __fmul_rn(f.hx, __fadd_rn(__fmul_rn(f.rho, vr), sr))), f.mgn);
+  const float xl = __fsub_rn(__fadd_rn(f.mx, __fmul_rn(f.hx, __fsub_rn(__fmul_rn(f.rho, vl), sl))), f.mgn);
+  const float ftw = (float)tw;
+  a = max(a, clamp_floor(floorf(__fdiv_rn(xl, ftw)), Tx));
+  b = min(b, clamp_floor(__fadd_rn(floorf(__fdiv_rn(xr, ftw)), 1.0f), Tx));
+  if (b < a) b = a;
+}
+
+// Number of (tile, splat) pairs of a splat.
+__device__ __forceinline__ uint32_t foot_count(const FootRows& f, int tw, int th, int Tx) {
+  if (f.x1 <= f.x0 || f.y1 <= f.y0) return 0;
+  if (!f.exact) return (uint32_t)(f.x1 - f.x0) * (uint32_t)(f.y1 - f.y0);
+  uint32_t n = 0;
+  for (int ty = f.y0; ty < f.y1; ++ty) {
+    int a, b;
+    row_span(f, ty, tw, th, Tx, a, b);
+    n += (uint32_t)(b - a);
+  }
+  return n;
+}
+
 // ------------------------------------------------- async copies (TMA bulk)
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);

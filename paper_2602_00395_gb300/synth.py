@@ -184,12 +184,14 @@ def projected_records(n: int, width: int, height: int, *, seed: int = 11,
                       max_radius: int = 120):
     """Seeded stand-ins for projected splats, as the binning step receives them.
 
-    Returns float32 means (x, y), int32 radii, float32 depths and the footprint
-    half-extents (x, y) as packed halves (uint32, x in the low 16 bits).  Some
-    radii are 0 (culled), some centres lie off-screen, a fraction of depths are
-    exact duplicates of others so that ties are exercised, and the half-extents
-    range from 0 to beyond the radius, with some -inf (no pixel reached) and
-    some +inf (unbounded).
+    Returns float32 means (x, y), int32 radii, float32 depths, the footprint
+    half-extents (x, y) as packed halves (uint32, x in the low 16 bits) and the
+    conics (A, B, C) as a float32 [3, n] array.  Some radii are 0 (culled), some
+    centres lie off-screen, a fraction of depths are exact duplicates of others
+    so that ties are exercised, the half-extents range from 0 to beyond the
+    radius, with some -inf (no pixel reached) and some +inf (unbounded), and the
+    conics are positive definite with correlations up to +-0.999 (and a few with
+    A = 0, not positive definite).
     """
     rng = np.random.default_rng(seed)
     mx = rng.uniform(-60.0, width + 60.0, size=n).astype(np.float32)
@@ -207,7 +209,13 @@ def projected_records(n: int, width: int, height: int, *, seed: int = 11,
     h[:, (kind >= 0.08) & (kind < 0.11)] = 0.0
     bits = h.view(np.uint16).astype(np.uint32)
     ext = bits[0] | (bits[1] << np.uint32(16))
-    return mx, my, r, depth, ext
+    A = np.exp(rng.uniform(np.log(2e-3), np.log(3.3), size=n))
+    C = np.exp(rng.uniform(np.log(2e-3), np.log(3.3), size=n))
+    rho = rng.uniform(-0.999, 0.999, size=n)
+    B = -rho * np.sqrt(A * C)
+    A[rng.uniform(size=n) < 0.01] = 0.0
+    conic = np.stack([A, B, C]).astype(np.float32)
+    return mx, my, r, depth, ext, conic
 
 
 # --------------------------------------------------------------- serving

@@ -3,9 +3,10 @@
 1M Gaussians (SH degree 3, 20 clusters), 8 views of 1920x1080, 16x16 tiles,
 nu = 2 probes: one projection / bin-sort / forward / reverse pass through the C
 ABI, compared with the FP64 oracle on outputs it can compute one by one:
-  * sampled pixels of every view: colour (1e-5 max-abs), final T, n_contrib and
-    the probe tangents J z_k, away from pixels whose decisions are within
-    rounding of a threshold (counted);
+  * sampled pixels of every view: colour (1e-5 max-abs), final T, n_contrib
+    (within the range that tile sets within rounding allow) and the probe
+    tangents J z_k, away from pixels whose decisions are within rounding of a
+    threshold (counted);
   * sampled Gaussians: their gradient rows (1e-4 relative to the group's largest
     sampled entry) and Hutchinson rows (1e-3 + 1e-6/delta, see below), unless their own tile set, their
     own threshold decision or a residual sign in their footprint is within
@@ -74,7 +75,8 @@ def test_sampled_pixels_match_oracle(fullsize):
         img = f["image"][v][:, ys, xs].T
         assert np.abs(img - ref["rgb"])[ok].max(initial=0.0) <= 1e-5
         assert np.abs(f["final_T"][v][ys, xs] - ref["final_T"])[ok].max(initial=0.0) <= 1e-5
-        assert np.array_equal(f["n_contrib"][v][ys, xs][ok], ref["n_contrib"][ok])
+        nc = f["n_contrib"][v][ys, xs]
+        assert np.all(((nc >= ref["n_contrib_lo"]) & (nc <= ref["n_contrib_hi"]))[ok])
         for k in range(f["nu"]):
             jz = f["image_tan"][k, v][:, ys, xs].T
             scale = max(np.abs(ref["jz"][:, k, :]).max(), 1e-6)

@@ -89,7 +89,8 @@ def test_sampled_pixels_match_oracle(large):
     img = f["img"][:, ys, xs].T
     assert np.abs(img - ref["rgb"])[ok].max() <= 1e-5
     assert np.abs(f["final_T"][ys, xs] - ref["final_T"])[ok].max() <= 1e-5
-    assert np.array_equal(f["n_contrib"][ys, xs][ok], ref["n_contrib"][ok])
+    nc = f["n_contrib"][ys, xs]
+    assert np.all(((nc >= ref["n_contrib_lo"]) & (nc <= ref["n_contrib_hi"]))[ok])
 
 
 def test_sampled_gaussians_match_oracle(large):

@@ -110,11 +110,13 @@ def test_project_matches_oracle(case):
 
 
 # ------------------------------------------------------------------ bin/sort
-def _write_records(e, mx, my, r, d, ext):
+def _write_records(e, mx, my, r, d, ext, conic):
     rec = torch.zeros(e.V, e.n_pad, 12, dtype=torch.float32)
     n = mx.shape[1]
     rec[:, :n, 0] = torch.from_numpy(mx)
     rec[:, :n, 1] = torch.from_numpy(my)
+    for k in range(3):
+        rec[:, :n, 2 + k] = torch.from_numpy(np.ascontiguousarray(conic[k]))
     rec[:, :n, 9] = torch.from_numpy(d)
     rec[:, :n, 10] = torch.from_numpy(r.astype(np.int32).view(np.float32))
     rec[:, :n, 11] = torch.from_numpy(ext.astype(np.uint32).view(np.float32))
@@ -139,10 +141,11 @@ def test_bin_sort_bit_exact(W, H, tile, V, n, maxr, box):
     mx = np.stack([a[0] for a in recs]); my = np.stack([a[1] for a in recs])
     r = np.stack([a[2] for a in recs]); d = np.stack([a[3] for a in recs])
     ext = np.stack([a[4] for a in recs])
-    keys, vals, ranges = O.bin_sort(mx, my, r, d, W, H, *tile, extents=ext if box else None)
+    conic = np.stack([a[5] for a in recs], axis=1)  # 3 x V x n
+    keys, vals, ranges = O.bin_sort(mx, my, r, d, W, H, *tile, extents=ext if box else None, conic=conic)
     cams = [S.single_camera(W, H)] * V
     e = _engine(n, 0, cams, tile=tile, nu=0, capacity=len(keys) + 123, footprint_bins=box)
-    _write_records(e, mx, my, r, d, ext)
+    _write_records(e, mx, my, r, d, ext, conic)
     e.bin_sort()
     torch.cuda.synchronize()
     P = int(e.n_pairs.item())
@@ -156,16 +159,39 @@ def test_bin_sort_bit_exact(W, H, tile, V, n, maxr, box):
 @pytest.mark.parametrize("W,H", [(128, 96), (3840, 2160)])
 def test_bin_sort_capacity_overflow_is_flagged_and_in_bounds(W, H):
     n = 3000
-    mx, my, r, d, ext = S.projected_records(n, W, H, seed=5, max_radius=50)
-    keys, _, _ = O.bin_sort(mx, my, r, d, W, H, extents=ext)
+    mx, my, r, d, ext, conic = S.projected_records(n, W, H, seed=5, max_radius=50)
+    keys, _, _ = O.bin_sort(mx, my, r, d, W, H, extents=ext, conic=conic)
     e = _engine(n, 0, [S.single_camera(W, H)], nu=0, capacity=len(keys) // 3)
-    _write_records(e, mx[None], my[None], r[None], d[None], ext[None])
+    _write_records(e, mx[None], my[None], r[None], d[None], ext[None], conic[:, None])
     e.bin_sort()
     torch.cuda.synchronize()
     from paper_2602_00395_gb300 import gs3dtr as G
     assert int(e.n_pairs.item()) == len(keys)
     assert e.read_status() & G.GS_FLAG_CAPACITY
     cap = len(keys) // 3
+    rg = e.ranges.cpu().numpy().view(np.uint32).reshape(-1, 2)
+    assert rg.max() <= cap
+
+
+@pytest.mark.parametrize("W,H,maxr", [(1297, 840, 120), (256, 256, 60)])
+def test_bin_sort_far_past_capacity_keeps_every_slot_in_range(W, H, maxr):
+    """Pairs far beyond the capacity (some records' row tables do not fit either):
+    the overflow is flagged, the pair count is the need, and every stored pair and
+    range is in range, so that later calls read nothing out of bounds."""
+    n = 20000
+    mx, my, r, d, ext, conic = S.projected_records(n, W, H, seed=17, max_radius=maxr)
+    keys, _, _ = O.bin_sort(mx, my, r, d, W, H, extents=ext, conic=conic)
+    cap = 64
+    e = _engine(n, 0, [S.single_camera(W, H)], nu=0, capacity=cap)
+    _write_records(e, mx[None], my[None], r[None], d[None], ext[None], conic[:, None])
+    e.bin_sort()
+    torch.cuda.synchronize()
+    from paper_2602_00395_gb300 import gs3dtr as G
+    assert int(e.n_pairs.item()) == len(keys) > 100 * cap
+    assert e.read_status() & G.GS_FLAG_CAPACITY
+    k = e.keys[:cap].cpu().numpy().view(np.uint64)
+    v = e.vals[:cap].cpu().numpy().view(np.uint32)
+    assert np.all((k >> np.uint64(32)) < e.Tx * e.Ty) and np.all(v < n)
     rg = e.ranges.cpu().numpy().view(np.uint32).reshape(-1, 2)
     assert rg.max() <= cap
 
@@ -213,7 +239,11 @@ def test_raster_fwd_matches_oracle(case, tile, box):
     err = np.abs(img - ref["image"]).max(axis=1)[ok]
     assert err.max() <= 1e-5, err.max()
     assert np.abs(T - ref["final_T"])[ok].max() <= 1e-5
-    assert np.array_equal(nc[ok], ref["n_contrib"][ok])
+    # n_contrib within the range that tile sets within rounding give (equal to
+    # the oracle's wherever no such tile set is in front of the last blend)
+    in_range = (nc >= ref["n_contrib_lo"]) & (nc <= ref["n_contrib_hi"])
+    assert np.all(in_range[ok])
+    assert np.mean((nc == ref["n_contrib"])[ok]) >= 0.95
 
 
 # ------------------------------------------------------------------ reverse

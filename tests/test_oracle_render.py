@@ -116,35 +116,71 @@ def _half(bits):
     return float(np.array([bits], np.uint16).view(np.float16)[0])
 
 
-def _brute_tiles(mx, my, r, ext, W, H, tw, th):
+F = np.float32
+
+
+def _row_span(mx, my, A, B, C, hx, hy, x0, x1, ty, tw, th, Tx):
+    """Tiles [a, b) of row ty narrowed to the footprint ellipse, in FP32 with one
+    rounding per operation in the order of the binning rule."""
+    if not (hx > 0 and hy > 0 and hx < 65536 and hy < 65536 and A > 0 and C > 0):
+        return x0, x1
+    rho = min(max(F(-B) / F(np.sqrt(F(A) * F(C))), F(-1)), F(1))
+    q = max(F(0), F(1) - rho * rho)
+    mgn = F(F(0.01) * hx) + F(0.5)
+    vlo = F(F(ty * th) - my) / hy
+    vhi = F(F((ty + 1) * th) - my) / hy
+    if vhi < -1 or vlo > 1:
+        return x0, x0
+    vr = min(max(rho, vlo), vhi)
+    vl = min(max(-rho, vlo), vhi)
+    sr = F(np.sqrt(max(F(0), q * F(F(1) - vr * vr))))
+    sl = F(np.sqrt(max(F(0), q * F(F(1) - vl * vl))))
+    xr = F(F(mx + F(hx * F(rho * vr + sr))) + mgn)
+    xl = F(F(mx + F(hx * F(rho * vl - sl))) - mgn)
+    cl = lambda f: 0 if not f > 0 else (Tx if f > Tx else int(f))
+    a = max(x0, cl(np.floor(F(xl / F(tw)))))
+    b = min(x1, cl(F(np.floor(F(xr / F(tw))) + F(1))))
+    return a, max(a, b)
+
+
+def _brute_tiles(mx, my, r, ext, conic, W, H, tw, th):
     """Tiles whose pixel interval [t*tw, (t+1)*tw) meets (m - r, m + r - 1] and
-    [m - h, m + h] on both axes (h the footprint half-extent; FP32 sums)."""
+    [m - h, m + h] on both axes (h the footprint half-extent; FP32 sums), each
+    row then narrowed to the ellipse (conic None: the rectangle)."""
     Tx, Ty = -(-W // tw), -(-H // th)
     out = []
     if r <= 0:
         return out
-    hx, hy = np.float32(_half(int(ext) & 0xFFFF)), np.float32(_half(int(ext) >> 16))
-    lo_x, hi_x = np.float32(mx) - np.float32(r), np.float32(mx) + np.float32(r - 1)
-    lo_y, hi_y = np.float32(my) - np.float32(r), np.float32(my) + np.float32(r - 1)
+    hx, hy = F(_half(int(ext) & 0xFFFF)), F(_half(int(ext) >> 16))
+    mx, my = F(mx), F(my)
+    lo_x, hi_x = mx - F(r), mx + F(r - 1)
+    lo_y, hi_y = my - F(r), my + F(r - 1)
     with np.errstate(invalid="ignore", over="ignore"):
-        flo_x, fhi_x = np.float32(mx) - hx, np.float32(mx) + hx
-        flo_y, fhi_y = np.float32(my) - hy, np.float32(my) + hy
-    for ty in range(Ty):
-        for tx in range(Tx):
-            if (tx * tw <= hi_x and (tx + 1) * tw > lo_x and ty * th <= hi_y and (ty + 1) * th > lo_y
-                    and tx * tw <= fhi_x and (tx + 1) * tw > flo_x and ty * th <= fhi_y and (ty + 1) * th > flo_y):
-                out.append(ty * Tx + tx)
+        flo_x, fhi_x = mx - hx, mx + hx
+        flo_y, fhi_y = my - hy, my + hy
+    cols = [tx for tx in range(Tx) if tx * tw <= hi_x and (tx + 1) * tw > lo_x and tx * tw <= fhi_x
+            and (tx + 1) * tw > flo_x]
+    rows = [ty for ty in range(Ty) if ty * th <= hi_y and (ty + 1) * th > lo_y and ty * th <= fhi_y
+            and (ty + 1) * th > flo_y]
+    if not cols or not rows:
+        return out
+    for ty in rows:
+        a, b = cols[0], cols[-1] + 1
+        if conic is not None:
+            with np.errstate(invalid="ignore", over="ignore", divide="ignore"):
+                a, b = _row_span(mx, my, F(conic[0]), F(conic[1]), F(conic[2]), hx, hy, a, b, ty, tw, th, Tx)
+        out.extend(ty * Tx + tx for tx in range(a, b))
     return out
 
 
 @pytest.mark.parametrize("W,H,tw,th,n", [(128, 128, 16, 16, 300), (97, 53, 16, 8, 200), (61, 45, 8, 8, 150)])
 def test_binning_against_brute_force_and_lexsort(W, H, tw, th, n):
-    mx, my, r, d, ext = S.projected_records(n, W, H, seed=W + n, max_radius=40)
-    keys, vals, ranges = O.bin_sort(mx, my, r, d, W, H, tw, th, extents=ext)
+    mx, my, r, d, ext, conic = S.projected_records(n, W, H, seed=W + n, max_radius=40)
+    keys, vals, ranges = O.bin_sort(mx, my, r, d, W, H, tw, th, extents=ext, conic=conic)
     Tx, Ty = -(-W // tw), -(-H // th)
     expect = []
     for i in range(n):
-        for tile in _brute_tiles(mx[i], my[i], int(r[i]), ext[i], W, H, tw, th):
+        for tile in _brute_tiles(mx[i], my[i], int(r[i]), ext[i], conic[:, i], W, H, tw, th):
             key = (tile << 32) | int(np.float32(d[i]).view(np.uint32))
             expect.append((key, i))
     ek = np.array([k for k, _ in expect], np.uint64)
@@ -161,10 +197,67 @@ def test_binning_against_brute_force_and_lexsort(W, H, tw, th, n):
             assert s == e
         else:
             assert (s, e) == (sel[0], sel[-1] + 1)
-    # unbounded half-extents leave the 3DGS square alone
+    # the rows narrow the box, and without extents the 3DGS square is binned
+    n_box = sum(len(_brute_tiles(mx[i], my[i], int(r[i]), ext[i], None, W, H, tw, th)) for i in range(n))
+    assert len(keys) < n_box
     k2, _, _ = O.bin_sort(mx, my, r, d, W, H, tw, th)
-    n_square = sum(len(_brute_tiles(mx[i], my[i], int(r[i]), 0x7C007C00, W, H, tw, th)) for i in range(n))
-    assert len(k2) == n_square > len(keys)
+    n_square = sum(len(_brute_tiles(mx[i], my[i], int(r[i]), 0x7C007C00, None, W, H, tw, th)) for i in range(n))
+    assert len(k2) == n_square > n_box
+
+
+def _extents(A, B, C, o):
+    """Footprint half-extents as the projection stores them: sqrt(tau C/det) and
+    sqrt(tau A/det), tau = 2 ln(255 o), widened 0.1 % + 0.01 px, rounded up to
+    half precision, packed (x low)."""
+    tau = 2 * np.log(255 * o)
+    det = A * C - B * B
+    h = []
+    for v in (np.sqrt(tau * C / det), np.sqrt(tau * A / det)):
+        x = v * 1.001 + 0.01
+        hv = np.float16(x)
+        hv = np.where(hv.astype(np.float64) < x, np.nextafter(hv, np.float16(np.inf)), hv)
+        h.append(np.asarray(hv, np.float16).view(np.uint16).astype(np.uint32))
+    return h[0] | (h[1] << np.uint32(16))
+
+
+def test_footprint_tiles_cover_every_pixel_the_splat_reaches():
+    """Random splats (correlations up to 0.995, opacities up to 0.99): every tile
+    with a pixel centre where o exp(-d^T Q d / 2) >= 1/255 (FP64) is among the
+    splat's tiles, and the tiles are fewer than the 3DGS square's."""
+    rng = np.random.default_rng(12)
+    W, H, tw, th, n = 256, 192, 16, 16, 400
+    sig = np.exp(rng.uniform(np.log(0.7), np.log(40.0), size=(2, n)))
+    corr = rng.uniform(-0.995, 0.995, size=n)
+    cov = np.array([[sig[0] ** 2, corr * sig[0] * sig[1]], [corr * sig[0] * sig[1], sig[1] ** 2]])
+    cov[0, 0] += 0.3
+    cov[1, 1] += 0.3
+    det = cov[0, 0] * cov[1, 1] - cov[0, 1] ** 2
+    A, B, C = cov[1, 1] / det, -cov[0, 1] / det, cov[0, 0] / det
+    o = rng.uniform(0.005, 0.99, size=n)
+    mid = 0.5 * (cov[0, 0] + cov[1, 1])
+    lam = mid + np.sqrt(np.maximum(0.1, mid * mid - det))
+    r = np.ceil(3 * np.sqrt(lam)).astype(np.int32)
+    mx = rng.uniform(-20, W + 20, n).astype(np.float32)
+    my = rng.uniform(-20, H + 20, n).astype(np.float32)
+    ext = _extents(A, B, C, o)
+    conic = np.stack([A, B, C]).astype(np.float32)
+    keys, vals, _ = O.bin_sort(mx, my, r, np.ones(n, np.float32), W, H, tw, th, extents=ext, conic=conic)
+    have = set(zip(vals.tolist(), (keys >> np.uint64(32)).astype(np.int64).tolist()))
+    Tx = -(-W // tw)
+    ys, xs = np.mgrid[0:H, 0:W] + 0.5
+    n_square = 0
+    for i in range(n):
+        dx, dy = mx[i] - xs, my[i] - ys
+        a = o[i] * np.exp(-0.5 * (A[i] * dx * dx + C[i] * dy * dy) - B[i] * dx * dy)
+        # the 3DGS square bounds where a splat is blended at all
+        x0, x1 = max(0, int(np.floor((mx[i] - r[i]) / tw))), min(Tx, int(np.floor((mx[i] + r[i] + tw - 1) / tw)))
+        y0, y1 = max(0, int(np.floor((my[i] - r[i]) / th))), min(-(-H // th), int(np.floor((my[i] + r[i] + th - 1) / th)))
+        n_square += max(0, x1 - x0) * max(0, y1 - y0)
+        for ty in range(y0, y1):
+            for tx in range(x0, x1):
+                if (a[ty * th:(ty + 1) * th, tx * tw:(tx + 1) * tw] >= 1 / 255).any():
+                    assert (i, ty * Tx + tx) in have, (i, tx, ty)
+    assert len(keys) < 0.8 * n_square
 
 
 def _square_blend(s, W, H, tw, th):
@@ -173,7 +266,7 @@ def _square_blend(s, W, H, tw, th):
     valid = np.nonzero(s["valid"] > 0)[0]
     order = valid[np.lexsort((valid, s["depth"][valid].astype(np.float32)))]
     img, T_out = np.zeros((3, H, W)), np.ones((H, W))
-    tiles = {int(i): set(_brute_tiles(s["mx"][i], s["my"][i], int(s["radius"][i]), 0x7C007C00, W, H, tw, th))
+    tiles = {int(i): set(_brute_tiles(s["mx"][i], s["my"][i], int(s["radius"][i]), 0x7C007C00, None, W, H, tw, th))
              for i in order}
     Tx = -(-W // tw)
     rgb = np.stack([s["r"], s["g"], s["b"]])
@@ -216,7 +309,7 @@ def test_footprint_box_binning_leaves_the_image_unchanged(tw, th):
     with O.footprint_bins():
         box = O.render(P, 1, [cam], tw, th)
     img, T = _square_blend(s, W, H, tw, th)
-    n_square = sum(len(_brute_tiles(s["mx"][i], s["my"][i], int(s["radius"][i]), 0x7C007C00, W, H, tw, th))
+    n_square = sum(len(_brute_tiles(s["mx"][i], s["my"][i], int(s["radius"][i]), 0x7C007C00, None, W, H, tw, th))
                    for i in np.nonzero(s["valid"] > 0)[0])
     assert square["n_pairs"] == n_square
     assert box["n_pairs"] < 0.9 * n_square

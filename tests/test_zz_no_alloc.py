@@ -22,9 +22,11 @@ torch = pytest.importorskip("torch")
 def _records_into(e, n, W, H, V, seed, max_radius):
     recs = [S.projected_records(n, W, H, seed=seed + v, max_radius=max_radius) for v in range(V)]
     rec = torch.zeros(V, e.n_pad, 12, dtype=torch.float32)
-    for v, (mx, my, r, d, ext) in enumerate(recs):
+    for v, (mx, my, r, d, ext, conic) in enumerate(recs):
         rec[v, :n, 0] = torch.from_numpy(mx)
         rec[v, :n, 1] = torch.from_numpy(my)
+        for k in range(3):
+            rec[v, :n, 2 + k] = torch.from_numpy(np.ascontiguousarray(conic[k]))
         rec[v, :n, 9] = torch.from_numpy(d)
         rec[v, :n, 10] = torch.from_numpy(r.astype(np.int32).view(np.float32))
         rec[v, :n, 11] = torch.from_numpy(ext.view(np.float32))
