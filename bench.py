@@ -665,9 +665,19 @@ def run_cuda(args):
     timed_steps(eng, cam_dev, targets, max(args.warmup, 3), 0, 1, stream)
     torch.cuda.synchronize()
     eng.status.zero_()
+    # every measured sequence below starts from this state, so that each times
+    # the same stretch of training (the pair count drifts as the scene trains)
+    state0 = [b.clone() for b in (eng.x, eng.g_ema, eng.d_ema)]
+
+    def restore():
+        torch.cuda.synchronize()
+        for b, v in zip((eng.x, eng.g_ema, eng.d_ema), state0):
+            b.copy_(v)
+        torch.cuda.synchronize()
     # per-call breakdown (separate, untimed for the headline)
     _, per_call = timed_steps(eng, cam_dev, targets, max(2, min(args.steps, 5)), 0, 100, stream, per_call=True)
     # the eager step sequence (six calls per step from the host), for reference
+    restore()
     eager_ms, _ = timed_steps(eng, cam_dev, targets, args.steps, 0, 500, stream)
     # one captured graph per view batch; each replay is a whole step
     sched = G.gs_eps_schedule(1e-6, 1e-8, 30000)
@@ -676,6 +686,7 @@ def run_cuda(args):
         eng.cams = cam_dev[b]
         eng.target = targets[b]
         graphs.append(eng.capture_step(True, sched, stream))
+    restore()
     graph_steps(eng, graphs, max(args.warmup, 3), 700, stream)  # untimed replays
     # timed region
     if ws > 1:
@@ -695,11 +706,15 @@ def run_cuda(args):
     value = ws * args.steps / (ms / 1e3)
     # end to end through the C ABI from pinned host buffers
     host_targets = [tg.cpu().pin_memory() for tg in targets]
+    restore()
     e2e_ms, e2e_wall, h2d, d2h = e2e_steps(eng, batches, host_targets, args.steps, 5000, stream, sched)
     e2e_val = ws * args.steps / (e2e_ms / 1e3)
     # the cost of curvature: gradient-only steps, and l = 10 with S2 != S1
+    restore()
     curv = curvature_costs(eng, cam_dev, targets, 20, stream)
+    restore()
     variants = variant_costs(eng, cam_dev, targets, 10, stream)
+    restore()
     # the plain one-view-at-a-time loop on the same workload
     plain_ms = plain_loop_steps(eng, cam_dev, targets, max(3, min(args.steps, 10)), 9000, stream, device)
     # roofline of the dominant call

@@ -113,9 +113,17 @@ __global__ void record_keys_kernel(const float4* __restrict__ rec, int n_pad, gs
   const uint32_t off = s_base + ex;
   uint32_t cnt = 0;
   if (R && (uint64_t)off + R <= rows_cap) {
+    float vlo = f.exact ? band_v(f, f.y0 * fr.tile_h) : 0.f;
     for (uint32_t k = 0; k < R; ++k) {
       int a, b;
-      row_span(f, f.y0 + (int)k, fr.tile_w, fr.tile_h, Tx, a, b);
+      if (f.exact) {
+        const float vhi = band_v(f, (f.y0 + (int)k + 1) * fr.tile_h);
+        row_span_v(f, vlo, vhi, fr.tile_w, Tx, a, b);
+        vlo = vhi;
+      } else {
+        a = f.x0;
+        b = f.x1;
+      }
       rows[(size_t)off + k] = make_uint2(cnt, (uint32_t)a);
       cnt += (uint32_t)(b - a);
     }

@@ -376,13 +376,15 @@ __device__ __forceinline__ FootRows foot_rows(float mx, float my, float A, float
   return f;
 }
 
-// Tiles [a, b) of row ty.
-__device__ __forceinline__ void row_span(const FootRows& f, int ty, int tw, int th, int Tx, int& a, int& b) {
+// v of the band edge at pixel row y.
+__device__ __forceinline__ float band_v(const FootRows& f, int y) { return __fdiv_rn(__fsub_rn((float)y, f.my), f.hy); }
+
+// Tiles [a, b) of row ty, given the v of its band's edges (band_v at ty th and
+// (ty + 1) th).  tw is a power of two, so x / tw is the exact product by 1 / tw.
+__device__ __forceinline__ void row_span_v(const FootRows& f, float vlo, float vhi, int tw, int Tx, int& a, int& b) {
   a = f.x0;
   b = f.x1;
   if (!f.exact) return;
-  const float vlo = __fdiv_rn(__fsub_rn((float)(ty * th), f.my), f.hy);
-  const float vhi = __fdiv_rn(__fsub_rn((float)((ty + 1) * th), f.my), f.hy);
   if (vhi < -1.f || vlo > 1.f) {
     b = a;
     return;
@@ -393,10 +395,20 @@ __device__ __forceinline__ void row_span(const FootRows& f, int ty, int tw, int 
   const float sl = __fsqrt_rn(fmaxf(0.f, __fmul_rn(f.q, __fsub_rn(1.f, __fmul_rn(vl, vl)))));
   const float xr = __fadd_rn(__fadd_rn(f.mx, __fmul_rn(f.hx, __fadd_rn(__fmul_rn(f.rho, vr), sr))), f.mgn);
   const float xl = __fsub_rn(__fadd_rn(f.mx, __fmul_rn(f.hx, __fsub_rn(__fmul_rn(f.rho, vl), sl))), f.mgn);
-  const float ftw = (float)tw;
-  a = max(a, clamp_floor(floorf(__fdiv_rn(xl, ftw)), Tx));
-  b = min(b, clamp_floor(__fadd_rn(floorf(__fdiv_rn(xr, ftw)), 1.0f), Tx));
+  const float itw = 1.0f / (float)tw;
+  a = max(a, clamp_floor(floorf(__fmul_rn(xl, itw)), Tx));
+  b = min(b, clamp_floor(__fadd_rn(floorf(__fmul_rn(xr, itw)), 1.0f), Tx));
   if (b < a) b = a;
+}
+
+// Tiles [a, b) of row ty.
+__device__ __forceinline__ void row_span(const FootRows& f, int ty, int tw, int th, int Tx, int& a, int& b) {
+  if (!f.exact) {
+    a = f.x0;
+    b = f.x1;
+    return;
+  }
+  row_span_v(f, band_v(f, ty * th), band_v(f, (ty + 1) * th), tw, Tx, a, b);
 }
 
 // Number of (tile, splat) pairs of a splat.
@@ -404,10 +416,13 @@ __device__ __forceinline__ uint32_t foot_count(const FootRows& f, int tw, int th
   if (f.x1 <= f.x0 || f.y1 <= f.y0) return 0;
   if (!f.exact) return (uint32_t)(f.x1 - f.x0) * (uint32_t)(f.y1 - f.y0);
   uint32_t n = 0;
+  float vlo = band_v(f, f.y0 * th);
   for (int ty = f.y0; ty < f.y1; ++ty) {
+    const float vhi = band_v(f, (ty + 1) * th);
     int a, b;
-    row_span(f, ty, tw, th, Tx, a, b);
+    row_span_v(f, vlo, vhi, tw, Tx, a, b);
     n += (uint32_t)(b - a);
+    vlo = vhi;
   }
   return n;
 }
