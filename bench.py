@@ -510,10 +510,10 @@ def raster_bwd_flops_per_unit() -> int:
 # (profiles/raster_bwd_traffic_1M_8x1080p_nu2.md), valid while the kernel
 # sources are the ones captured (their SHA-256 below); otherwise null.
 RASTER_BWD_TRAFFIC = {
-    "bytes": 1527271936 + 200948992 + 1237430528 + 457128448,
+    "bytes": 1492575232 + 196726016 + 1238292480 + 457368064,
     "sources": {
         "paper_2602_00395_gb300/csrc/raster.cu": "d7d704049fa50ff7ab51dcbcf30afeaa87a8d115d566d25585005b65c2036f98",
-        "paper_2602_00395_gb300/csrc/common.cuh": "bfe6a3217f01070a19f5ef6a2fdcd1c857224c8d9a736e2941a278567ea2aeac",
+        "paper_2602_00395_gb300/csrc/common.cuh": "e9c7cdd51f8a9cf92e5afea66c46559ac7794416c807fd793a7a7c70ceee2c23",
     },
 }
 
@@ -736,9 +736,11 @@ def run_cuda(args):
     pair_pass = max(1, (bits(N_VIEWS * eng.Tx * eng.Ty) + 7) // 8)
     work = {
         "project": ("hbm", eng.n * rows * 4 + N_VIEWS * eng.n * 48 * (1 + NU)),
-        # per pair: emit 12 B, 24 B per pass, ranges 8 B; per record: 32 B read for
-        # its key, 16 B per pass, 12 B count gather, 40 B read by the emit
-        "bin_sort": ("hbm", need * (12 + 24 * pair_pass + 8) + R * (32 + 16 * rec_pass + 12 + 40)),
+        # per pair: emit 12 B, 24 B per pass, ranges 8 B; per record: 48 B read and
+        # 28 B written by the count pass (count, key, value, row-table header; the
+        # row entries are not counted), 16 B per pass, 12 B count gather, 16 B
+        # header read by the emit
+        "bin_sort": ("hbm", need * (12 + 24 * pair_pass + 8) + R * (48 + 28 + 16 * rec_pass + 12 + 16)),
         "raster_fwd": ("alu", raster_fwd_flops_per_unit() * sum_nc),
         "raster_bwd": ("alu", raster_bwd_flops_per_unit() * sum_nc),
         "update": ("hbm", eng.n * rows * 4 * (5 + 3)),
