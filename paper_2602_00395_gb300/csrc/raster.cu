@@ -670,27 +670,16 @@ __global__ void GS_PBWD_BOUNDS project_bwd_kernel(const float* __restrict__ P, i
     }
   }
   uint64_t clamp_bits = 0;  // bit 3 v + c: colour channel c clamped at 0 in view v (v < kClampViews)
-  // the next view's cotangent row is loaded while this one is processed
-  float4 nxt[NVP / 4];
-  {
-    const float4* row4 = reinterpret_cast<const float4*>(cot + (size_t)i * NVP);
-#pragma unroll
-    for (int q = 0; q < NVP / 4; ++q) nxt[q] = row4[q];
-  }
 #pragma unroll 1
   for (int v = 0; v < fr.n_views; ++v) {
     float c[NVP];
     bool any = false;
+    const float4* row4 = reinterpret_cast<const float4*>(cot + ((size_t)v * n_pad + i) * NVP);
 #pragma unroll
     for (int q = 0; q < NVP / 4; ++q) {
-      const float4 x4 = nxt[q];
+      const float4 x4 = row4[q];
       c[4 * q + 0] = x4.x; c[4 * q + 1] = x4.y; c[4 * q + 2] = x4.z; c[4 * q + 3] = x4.w;
       any = any || x4.x != 0.f || x4.y != 0.f || x4.z != 0.f || x4.w != 0.f;
-    }
-    if (v + 1 < fr.n_views) {
-      const float4* row4 = reinterpret_cast<const float4*>(cot + ((size_t)(v + 1) * n_pad + i) * NVP);
-#pragma unroll
-      for (int q = 0; q < NVP / 4; ++q) nxt[q] = row4[q];
     }
     if (!any) continue;
     ViewGeom vg;
