@@ -45,39 +45,71 @@ __device__ __forceinline__ void load_tile(const float* const (&src)[NIN], size_t
   }
 }
 
-// horizontal window sums of NOUT products (prod(in values at (ty, tx))) for all
-// kIn rows and the kTile output columns, then vertical sums at output (oy, ox)
+// Horizontal window sums of NOUT products (prod of the NIN inputs at (ty, tx))
+// for all kIn rows and the kTile output columns.  A thread covers kCols adjacent
+// columns of one row and reads each input value once; every sum still adds its
+// 11 terms in window order.
+constexpr int kCols = 4, kRows = 4;
 template <int NIN, int NOUT, class Prod>
 __device__ __forceinline__ void filter_tile(float (*s_in)[kIn][kIn], float (*s_h)[kIn][kTile], Prod prod) {
-  for (int q = threadIdx.x; q < kIn * kTile; q += blockDim.x) {
-    const int ty = q / kTile, ox = q - ty * kTile;
-    float acc[NOUT];
+  for (int q = threadIdx.x; q < kIn * (kTile / kCols); q += blockDim.x) {
+    const int ty = q / (kTile / kCols), ox0 = (q - ty * (kTile / kCols)) * kCols;
+    float acc[NOUT][kCols];
 #pragma unroll
-    for (int o = 0; o < NOUT; ++o) acc[o] = 0.f;
+    for (int o = 0; o < NOUT; ++o)
 #pragma unroll
-    for (int d = 0; d <= 2 * kR; ++d) {
+      for (int j = 0; j < kCols; ++j) acc[o][j] = 0.f;
+#pragma unroll
+    for (int c = 0; c < kCols + 2 * kR; ++c) {
       float v[NIN];
 #pragma unroll
-      for (int k = 0; k < NIN; ++k) v[k] = s_in[k][ty][ox + d];
+      for (int k = 0; k < NIN; ++k) v[k] = s_in[k][ty][ox0 + c];
       float p[NOUT];
       prod(v, p);
 #pragma unroll
-      for (int o = 0; o < NOUT; ++o) acc[o] += c_win[d] * p[o];
+      for (int j = 0; j < kCols; ++j) {
+        const int dd = c - j;
+        if (dd >= 0 && dd <= 2 * kR) {
+#pragma unroll
+          for (int o = 0; o < NOUT; ++o) acc[o][j] += c_win[dd] * p[o];
+        }
+      }
     }
 #pragma unroll
-    for (int o = 0; o < NOUT; ++o) s_h[o][ty][ox] = acc[o];
+    for (int o = 0; o < NOUT; ++o)
+#pragma unroll
+      for (int j = 0; j < kCols; ++j) s_h[o][ty][ox0 + j] = acc[o][j];
   }
 }
 
+// Vertical window sums at output rows oy0 .. oy0 + kRows - 1 of column ox, each
+// horizontal sum read once.
 template <int NOUT>
-__device__ __forceinline__ void vertical(float (*s_h)[kIn][kTile], int oy, int ox, float (&out)[NOUT]) {
+__device__ __forceinline__ void vertical(float (*s_h)[kIn][kTile], int oy0, int ox, float (&out)[NOUT][kRows]) {
 #pragma unroll
-  for (int o = 0; o < NOUT; ++o) out[o] = 0.f;
+  for (int o = 0; o < NOUT; ++o)
 #pragma unroll
-  for (int d = 0; d <= 2 * kR; ++d)
+    for (int j = 0; j < kRows; ++j) out[o][j] = 0.f;
 #pragma unroll
-    for (int o = 0; o < NOUT; ++o) out[o] += c_win[d] * s_h[o][oy + d][ox];
+  for (int c = 0; c < kRows + 2 * kR; ++c) {
+#pragma unroll
+    for (int o = 0; o < NOUT; ++o) {
+      const float hv = s_h[o][oy0 + c][ox];
+#pragma unroll
+      for (int j = 0; j < kRows; ++j) {
+        const int dd = c - j;
+        if (dd >= 0 && dd <= 2 * kR) out[o][j] += c_win[dd] * hv;
+      }
+    }
+  }
 }
+
+// The output pixels of a thread: rows oy0 .. oy0 + kRows - 1 of column ox.
+__device__ __forceinline__ void out_block(int& oy0, int& ox) {
+  ox = threadIdx.x % kTile;
+  oy0 = (threadIdx.x / kTile) * kRows;
+}
+static_assert(kSsimThreads * kRows == kTile * kTile, "one block of kRows pixels per thread");
 
 // SSIM and its partials by the raw window moments at one pixel
 __device__ __forceinline__ void ssim_at(float mx, float my, float ex2, float ey2, float exy, float& S, float& dmx,
@@ -119,14 +151,17 @@ __global__ void __launch_bounds__(kSsimThreads) ssim_stats_kernel(const float* _
   });
   __syncthreads();
   float lsum = 0.f;
-  for (int q = threadIdx.x; q < kTile * kTile; q += blockDim.x) {
-    const int oy = q / kTile, ox = q - oy * kTile;
+  int oy0, ox;
+  out_block(oy0, ox);
+  float fb[5][kRows];
+  vertical<5>(s_h, oy0, ox, fb);
+#pragma unroll
+  for (int j = 0; j < kRows; ++j) {
+    const int oy = oy0 + j;
     const int gx = x0 + ox, gy = y0 + oy;
     if (gx >= pl.W || gy >= pl.H) continue;
-    float f[5];
-    vertical<5>(s_h, oy, ox, f);
     float s, d1, d2, d3;
-    ssim_at(f[0], f[1], f[2], f[3], f[4], s, d1, d2, d3);
+    ssim_at(fb[0][j], fb[1][j], fb[2][j], fb[3][j], fb[4][j], s, d1, d2, d3);
     const size_t at = off + (size_t)gy * pl.W + gx;
     S[at] = s;
     P1[at] = d1;
@@ -148,10 +183,13 @@ __global__ void __launch_bounds__(kSsimThreads) ssim_stats_kernel(const float* _
   }
 }
 
-// pass 2, per probe: a = lambda/(4 max(1 - S, floor))/m . dS[d]
+// pass 2, all NP probes of the step in one launch (the image, target, S and
+// partials read once): a_k = lambda/(4 max(1 - S, floor))/m . dS[d_k]; the
+// probes' planes are `stride` floats apart
+template <int NP>
 __global__ void __launch_bounds__(kSsimThreads) ssim_jvp_kernel(const float* __restrict__ d,
                                                                 const float* __restrict__ img,
-                                                                const float* __restrict__ tgt, Plane pl,
+                                                                const float* __restrict__ tgt, Plane pl, size_t stride,
                                                                 const float* __restrict__ S,
                                                                 const float* __restrict__ P1,
                                                                 const float* __restrict__ P2,
@@ -159,76 +197,100 @@ __global__ void __launch_bounds__(kSsimThreads) ssim_jvp_kernel(const float* __r
                                                                 float floor_, float* __restrict__ a) {
   extern __shared__ __align__(16) float smem[];
   float(*s_in)[kIn][kIn] = reinterpret_cast<float(*)[kIn][kIn]>(smem);
-  float(*s_h)[kIn][kTile] = reinterpret_cast<float(*)[kIn][kTile]>(smem + 3 * kIn * kIn);
+  float(*s_h)[kIn][kTile] = reinterpret_cast<float(*)[kIn][kTile]>(smem + (NP + 2) * kIn * kIn);
   const int x0 = blockIdx.x * kTile, y0 = blockIdx.y * kTile;
   const size_t off = (size_t)blockIdx.z * pl.W * pl.H;
-  const float* src[3] = {d, img, tgt};
-  load_tile<3>(src, off, pl.W, pl.H, x0, y0, s_in);
+  const float* src[NP + 2];
+#pragma unroll
+  for (int k = 0; k < NP; ++k) src[k] = d + (size_t)k * stride;
+  src[NP] = img;
+  src[NP + 1] = tgt;
+  load_tile<NP + 2>(src, off, pl.W, pl.H, x0, y0, s_in);
   __syncthreads();
-  filter_tile<3, 3>(s_in, s_h, [](const float (&v)[3], float (&p)[3]) {
-    p[0] = v[0];
-    p[1] = 2.f * v[1] * v[0];
-    p[2] = v[2] * v[0];
+  filter_tile<NP + 2, 3 * NP>(s_in, s_h, [](const float (&v)[NP + 2], float (&p)[3 * NP]) {
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+      p[3 * k] = v[k];
+      p[3 * k + 1] = 2.f * v[NP] * v[k];
+      p[3 * k + 2] = v[NP + 1] * v[k];
+    }
   });
   __syncthreads();
-  for (int q = threadIdx.x; q < kTile * kTile; q += blockDim.x) {
-    const int oy = q / kTile, ox = q - oy * kTile;
+  int oy0, ox;
+  out_block(oy0, ox);
+  float fb[3 * NP][kRows];
+  vertical<3 * NP>(s_h, oy0, ox, fb);
+#pragma unroll
+  for (int j = 0; j < kRows; ++j) {
+    const int oy = oy0 + j;
     const int gx = x0 + ox, gy = y0 + oy;
     if (gx >= pl.W || gy >= pl.H) continue;
-    float f[3];
-    vertical<3>(s_h, oy, ox, f);
     const size_t at = off + (size_t)gy * pl.W + gx;
-    const float dS = P1[at] * f[0] + P2[at] * f[1] + P3[at] * f[2];
-    a[at] = wscale / (4.f * fmaxf(1.f - S[at], floor_)) * dS;
+    const float p1 = P1[at], p2 = P2[at], p3 = P3[at];
+    const float w = wscale / (4.f * fmaxf(1.f - S[at], floor_));
+#pragma unroll
+    for (int k = 0; k < NP; ++k)
+      a[(size_t)k * stride + at] = w * (p1 * fb[3 * k][j] + p2 * fb[3 * k + 1][j] + p3 * fb[3 * k + 2][j]);
   }
 }
 
-// pass 3, per stream: the adjoint of the weights a (a == NULL: all ones), plus
-// the L1 part, into the stream's cotangent image
+// pass 3: the adjoint of NA weight planes a_k (NA = 0: one stream with weights
+// all 1, the gradient) plus the L1 part, into NA (or 1) cotangent images; the
+// planes of a, d and cot are `stride` floats apart
+template <int NA>
 __global__ void __launch_bounds__(kSsimThreads) ssim_vjp_kernel(const float* __restrict__ a,
                                                                 const float* __restrict__ img,
-                                                                const float* __restrict__ tgt, Plane pl,
+                                                                const float* __restrict__ tgt, Plane pl, size_t stride,
                                                                 const float* __restrict__ P1,
                                                                 const float* __restrict__ P2,
                                                                 const float* __restrict__ P3,
                                                                 const float* __restrict__ d, float lambda,
                                                                 float inv_m, float floor_, float* __restrict__ cot) {
+  constexpr int NS = NA > 0 ? NA : 1;  // output streams
+  constexpr int NIN = NA + 3;
   extern __shared__ __align__(16) float smem[];
   float(*s_in)[kIn][kIn] = reinterpret_cast<float(*)[kIn][kIn]>(smem);
-  float(*s_h)[kIn][kTile] = reinterpret_cast<float(*)[kIn][kTile]>(smem + 4 * kIn * kIn);
+  float(*s_h)[kIn][kTile] = reinterpret_cast<float(*)[kIn][kTile]>(smem + NIN * kIn * kIn);
   const int x0 = blockIdx.x * kTile, y0 = blockIdx.y * kTile;
   const size_t off = (size_t)blockIdx.z * pl.W * pl.H;
-  const bool grad = a == nullptr;
-  const float* src[4] = {grad ? P1 : a, P1, P2, P3};
-  load_tile<4>(src, off, pl.W, pl.H, x0, y0, s_in);
+  const float* src[NIN];
+#pragma unroll
+  for (int k = 0; k < NA; ++k) src[k] = a + (size_t)k * stride;
+  src[NA] = P1;
+  src[NA + 1] = P2;
+  src[NA + 2] = P3;
+  load_tile<NIN>(src, off, pl.W, pl.H, x0, y0, s_in);
   __syncthreads();
-  if (grad) {  // weights all 1: src[0] duplicates P1, and the products are the partials
-    filter_tile<4, 3>(s_in, s_h, [](const float (&v)[4], float (&p)[3]) {
-      p[0] = v[1];
-      p[1] = v[2];
-      p[2] = v[3];
-    });
-  } else {
-    filter_tile<4, 3>(s_in, s_h, [](const float (&v)[4], float (&p)[3]) {
-      p[0] = v[0] * v[1];
-      p[1] = v[0] * v[2];
-      p[2] = v[0] * v[3];
-    });
-  }
+  filter_tile<NIN, 3 * NS>(s_in, s_h, [](const float (&v)[NIN], float (&p)[3 * NS]) {
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+      const float wk = NA > 0 ? v[k] : 1.f;  // weights all 1: the products are the partials
+      p[3 * k] = wk * v[NA];
+      p[3 * k + 1] = wk * v[NA + 1];
+      p[3 * k + 2] = wk * v[NA + 2];
+    }
+  });
   __syncthreads();
-  for (int q = threadIdx.x; q < kTile * kTile; q += blockDim.x) {
-    const int oy = q / kTile, ox = q - oy * kTile;
+  int oy0, ox;
+  out_block(oy0, ox);
+  float fb[3 * NS][kRows];
+  vertical<3 * NS>(s_h, oy0, ox, fb);
+#pragma unroll
+  for (int j = 0; j < kRows; ++j) {
+    const int oy = oy0 + j;
     const int gx = x0 + ox, gy = y0 + oy;
     if (gx >= pl.W || gy >= pl.H) continue;
-    float f[3];
-    vertical<3>(s_h, oy, ox, f);
     const size_t at = off + (size_t)gy * pl.W + gx;
     const float x = img[at], y = tgt[at], r = x - y;
-    const float A = f[0] + 2.f * x * f[1] + y * f[2];
-    if (grad)
-      cot[at] = 0.5f * inv_m * ((1.f - lambda) * (float)((r > 0.f) - (r < 0.f)) - lambda * A);
-    else
-      cot[at] = (1.f - lambda) * inv_m / (4.f * fmaxf(fabsf(r), floor_)) * d[at] + A;
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+      const float A = fb[3 * k][j] + 2.f * x * fb[3 * k + 1][j] + y * fb[3 * k + 2][j];
+      if (NA == 0)
+        cot[at] = 0.5f * inv_m * ((1.f - lambda) * (float)((r > 0.f) - (r < 0.f)) - lambda * A);
+      else
+        cot[(size_t)k * stride + at] =
+            (1.f - lambda) * inv_m / (4.f * fmaxf(fabsf(r), floor_)) * d[(size_t)k * stride + at] + A;
+    }
   }
 }
 
@@ -246,11 +308,20 @@ cudaError_t set_window() {
     e = cudaFuncSetAttribute((const void*)ssim_stats_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem_bytes(2, 5));
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute((const void*)ssim_jvp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      e = cudaFuncSetAttribute((const void*)ssim_jvp_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)smem_bytes(3, 3));
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute((const void*)ssim_vjp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      e = cudaFuncSetAttribute((const void*)ssim_jvp_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem_bytes(4, 6));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute((const void*)ssim_vjp_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem_bytes(3, 3));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute((const void*)ssim_vjp_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)smem_bytes(4, 3));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute((const void*)ssim_vjp_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem_bytes(5, 6));
   }
   done = e == cudaSuccess;
   return e;
@@ -290,17 +361,23 @@ extern "C" gs_status gs_dssim_cotangents(gs_frame frame, const float* image, con
   const dim3 grid((pl.W + kTile - 1) / kTile, (pl.H + kTile - 1) / kTile, pl.planes);
   ssim_stats_kernel<<<grid, kSsimThreads, smem_bytes(2, 5), st>>>(image, target, pl, lambda, inv_2m, S, P1, P2, P3,
                                                                    loss_out);
-  for (int k = 0; k < nu; ++k)
-    ssim_jvp_kernel<<<grid, kSsimThreads, smem_bytes(3, 3), st>>>(image_tangent + (size_t)k * plane, image, target,
-                                                                   pl, S, P1, P2, P3, lambda * inv_m, gn_floor,
-                                                                   A + (size_t)k * plane);
-  int s = 0;
-  if (want_grad)
-    ssim_vjp_kernel<<<grid, kSsimThreads, smem_bytes(4, 3), st>>>(nullptr, image, target, pl, P1, P2, P3, nullptr,
-                                                                   lambda, inv_m, gn_floor, cot + (size_t)(s++) * plane);
-  for (int k = 0; k < nu; ++k)
-    ssim_vjp_kernel<<<grid, kSsimThreads, smem_bytes(4, 3), st>>>(A + (size_t)k * plane, image, target, pl, P1, P2,
-                                                                   P3, image_tangent + (size_t)k * plane, lambda,
-                                                                   inv_m, gn_floor, cot + (size_t)(s++) * plane);
+  if (nu == 1)
+    ssim_jvp_kernel<1><<<grid, kSsimThreads, smem_bytes(3, 3), st>>>(image_tangent, image, target, pl, plane, S, P1,
+                                                                      P2, P3, lambda * inv_m, gn_floor, A);
+  else if (nu == 2)
+    ssim_jvp_kernel<2><<<grid, kSsimThreads, smem_bytes(4, 6), st>>>(image_tangent, image, target, pl, plane, S, P1,
+                                                                      P2, P3, lambda * inv_m, gn_floor, A);
+  float* cot_p = cot;
+  if (want_grad) {
+    ssim_vjp_kernel<0><<<grid, kSsimThreads, smem_bytes(3, 3), st>>>(nullptr, image, target, pl, plane, P1, P2, P3,
+                                                                      nullptr, lambda, inv_m, gn_floor, cot_p);
+    cot_p += plane;
+  }
+  if (nu == 1)
+    ssim_vjp_kernel<1><<<grid, kSsimThreads, smem_bytes(4, 3), st>>>(A, image, target, pl, plane, P1, P2, P3,
+                                                                      image_tangent, lambda, inv_m, gn_floor, cot_p);
+  else if (nu == 2)
+    ssim_vjp_kernel<2><<<grid, kSsimThreads, smem_bytes(5, 6), st>>>(A, image, target, pl, plane, P1, P2, P3,
+                                                                      image_tangent, lambda, inv_m, gn_floor, cot_p);
   return check_launch("gs_dssim_cotangents");
 }

