@@ -440,7 +440,15 @@ def variant_costs(eng, cam_dev, targets, K, stream):
                                       True, eng.cot_img, eng.loss_val, eng.dssim_ws, eng.status, stream)
             ev1.record(stream)
         ev1.synchronize()
-        out["dssim_cotangents_ms"] = ev0.elapsed_time(ev1) / K
+        out["dssim_cotangents_ms"] = ms = ev0.elapsed_time(ev1) / K
+        # algorithmic bytes per pixel and channel: statistics 8 read + 16 written;
+        # the probes' derivative pass 32 + 8; the gradient's adjoint 20 + 4; the
+        # probes' adjoint 36 + 8 (nu = 2)
+        nbytes = 132 * N_VIEWS * 3 * HW
+        hbm, _, src = peaks()
+        out["dssim_cotangents_roofline"] = {"bound": "hbm", "achieved": nbytes / (ms * 1e-3) / 1e9, "peak": hbm,
+                                            "unit": "GB/s", "frac": nbytes / (ms * 1e-3) / 1e9 / hbm,
+                                            "bytes": nbytes}
     finally:
         eng.dssim_lambda = None
         del eng.cot_img, eng.dssim_ws
