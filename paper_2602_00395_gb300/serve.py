@@ -26,6 +26,11 @@ continuous batching on the GPU.
   arrival, both on the host clock.
 
 The plain loop serves the same stream one request at a time on one stream.
+
+Across GPUs the served workload shards by scene with no collective: rank r
+holds the scenes whose id is r modulo the world size (`scene_shard`) and serves
+the requests for them (`shard_requests`); a request names its scene by its
+global id.
 """
 from __future__ import annotations
 
@@ -166,6 +171,21 @@ class ServeResult:
                 "status_words": sorted(set(self.statuses))}
 
 
+def scene_shard(n_scenes: int, rank: int = 0, world: int = 1) -> list[int]:
+    """Scene ids held by `rank` of `world` ranks: id % world == rank."""
+    return [s for s in range(n_scenes) if s % world == rank]
+
+
+def shard_requests(stream_spec, rank: int = 0, world: int = 1) -> list:
+    """The requests (arrival, kind, scene, view) that `rank` serves: those for
+    its scenes, in arrival order."""
+    return [q for q in stream_spec if q[2] % world == rank]
+
+
+def _by_sid(scenes) -> dict:
+    return {sc.sid: sc for sc in scenes}
+
+
 def _requests(stream_spec) -> list[Request]:
     return [Request(i, a, k, s, v) for i, (a, k, s, v) in enumerate(stream_spec)]
 
@@ -175,6 +195,7 @@ def plain_loop(scenes: list[Scene], stream_spec, stream=None, keep_results: bool
     previous to finish and for its own arrival)."""
     s = stream or torch.cuda.Stream()
     reqs = _requests(stream_spec)
+    scenes = _by_sid(scenes)
     statuses = []
     t0 = time.perf_counter()
     for r in reqs:
@@ -195,7 +216,7 @@ class Server:
     """Continuous batching of requests over resident scenes (see the module text)."""
 
     def __init__(self, scenes: list[Scene], slots: int = 4, budget_bytes: int | None = None):
-        self.scenes = scenes
+        self.scenes = _by_sid(scenes)
         self.streams = [torch.cuda.Stream() for _ in range(slots)]
         self.budget = budget_bytes if budget_bytes is not None else 1 << 62
         # each slot's status word lands here by an asynchronous copy on the slot's
@@ -297,12 +318,16 @@ class Server:
 
 
 def make_scenes(n_scenes: int = 16, *, device: str = "cuda", budget_bytes: int | None = None, seed: int = 5000,
-                n_views: int = 8, n_max: int = 2_000_000) -> list[Scene]:
-    """The served workload's resident scenes; scenes are admitted in order while
-    their resident bytes fit `budget_bytes` (the rest are not loaded)."""
+                n_views: int = 8, n_max: int = 2_000_000, rank: int = 0, world: int = 1) -> list[Scene]:
+    """The served workload's resident scenes of `rank` (see scene_shard); scenes
+    are admitted in order while their resident bytes fit `budget_bytes` (the
+    rest are not loaded)."""
     scenes = []
     used = 0
+    mine = set(scene_shard(n_scenes, rank, world))
     for sid, (n, W, H) in enumerate(synth.served_scene_specs(n_scenes, seed=seed, n_max=n_max)):
+        if sid not in mine:
+            continue
         sc = Scene(sid, n, W, H, n_views=n_views, device=device)
         if budget_bytes is not None and used + sc.resident_bytes > budget_bytes:
             del sc
