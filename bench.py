@@ -518,9 +518,9 @@ def raster_bwd_flops_per_unit() -> int:
 # (profiles/raster_bwd_traffic_1M_8x1080p_nu2.md), valid while the kernel
 # sources are the ones captured (their SHA-256 below); otherwise null.
 RASTER_BWD_TRAFFIC = {
-    "bytes": 1492575232 + 196726016 + 1238292480 + 457368064,
+    "bytes": 1495004672 + 197197824 + 1212876544 + 447431936,
     "sources": {
-        "paper_2602_00395_gb300/csrc/raster.cu": "d7d704049fa50ff7ab51dcbcf30afeaa87a8d115d566d25585005b65c2036f98",
+        "paper_2602_00395_gb300/csrc/raster.cu": "1ad12889e6f1421d2551527fea5745d8af226bdcb1da3ebf0fd6fea9889428ee",
         "paper_2602_00395_gb300/csrc/common.cuh": "e9c7cdd51f8a9cf92e5afea66c46559ac7794416c807fd793a7a7c70ceee2c23",
     },
 }
