@@ -165,10 +165,11 @@ def kernel_launches_per_step(eng) -> int:
     return 1 + 1 + sort + 1 + 2 + 1
 
 
-def retile_workload(eng, cam_dev, targets, batches, tile, device):
-    """The same workload (parameters, cameras, targets) on a step with another tile shape."""
+def retile_workload(eng, cam_dev, targets, batches, tile, device, batch=0):
+    """The same workload (parameters, cameras, targets) on a step with another
+    tile shape and blend batch."""
     from paper_2602_00395_gb300.engine import TRStep
-    e = TRStep(eng.n, SH_DEG, eng.V, W, H, nu=NU, tile=tile, cfg=eng.cfg, device=device)
+    e = TRStep(eng.n, SH_DEG, eng.V, W, H, nu=NU, tile=tile, cfg=eng.cfg, device=device, batch=batch)
     e.x.copy_(eng.x)
     need = 0
     for cd in cam_dev:
@@ -666,9 +667,10 @@ def run_cuda(args):
     stream = torch.cuda.Stream(device=device)
     # tile shape: measured on this workload (the step is rebuilt if another shape wins)
     from paper_2602_00395_gb300.engine import autotune_tile
-    best_tile, tile_ms = autotune_tile(eng, stream=stream)
-    if best_tile != tuple(TILE):
-        eng, cam_dev, targets, batches, need = retile_workload(eng, cam_dev, targets, batches, best_tile, device)
+    (bw, bh, best_batch), tile_ms = autotune_tile(eng, stream=stream)
+    if (bw, bh, best_batch) != (*TILE, 0):
+        eng, cam_dev, targets, batches, need = retile_workload(eng, cam_dev, targets, batches, (bw, bh), device,
+                                                               best_batch)
     # warm-up
     timed_steps(eng, cam_dev, targets, max(args.warmup, 3), 0, 1, stream)
     torch.cuda.synchronize()
@@ -797,7 +799,9 @@ def run_cuda(args):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n_gaussians": args.n, "views_per_step": N_VIEWS,
                        "image": f"{W}x{H}", "nu": NU, "tile": f"{eng.tile[0]}x{eng.tile[1]}",
-                       "tile_autotune_ms": {f"{a}x{b}": round(v, 3) for (a, b), v in tile_ms.items()}, "pairs_per_step": need,
+                       "blend_batch": eng.frame.batch or "one per thread",
+                       "tile_autotune_ms": {f"{a}x{b}" + (f"/{c}" if c else ""): round(v, 3)
+                                            for (a, b, c), v in tile_ms.items()}, "pairs_per_step": need,
                        "parallelism": "replicas" if ws > 1 else "single GPU",
                        "l2": "inputs larger than L2 (236 MB parameters, 199 MB targets per step)",
                        "view_steps_per_s": value * N_VIEWS},

@@ -92,9 +92,12 @@ typedef struct gs_camera {
  * footprint_bins selects the tiles of a splat (see gs_bin_sort): 0 its 3DGS tile
  * square, 1 that square narrowed to its alpha >= 1/255 footprint (its box, then
  * row by row its ellipse).  Both give the same images and derivatives; 1 gives
- * fewer pairs. */
+ * fewer pairs.
+ * batch: records a tile's block stages in shared memory per step of its list in
+ * the blends (gs_raster_fwd, gs_raster_bwd, gs_hvp_diag): 0 for one per thread,
+ * else a multiple of 32 from 32 to 512.  It changes speed, not results. */
 typedef struct gs_frame {
-  int32_t n_views, width, height, tile_w, tile_h, footprint_bins;
+  int32_t n_views, width, height, tile_w, tile_h, footprint_bins, batch;
 } gs_frame;
 
 /* Rademacher probes z_k (k < nu) of step t: row r of Gaussian i is entry

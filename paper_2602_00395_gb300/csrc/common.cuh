@@ -481,7 +481,8 @@ inline bool frame_ok(gs_frame fr) {
   const int tt = fr.tile_w * fr.tile_h;
   return fr.n_views >= 1 && fr.width >= 1 && fr.height >= 1 && (fr.tile_w == 8 || fr.tile_w == 16 || fr.tile_w == 32) &&
          pow2(fr.tile_h) && fr.tile_h >= 8 && (tt == 64 || tt == 128 || tt == 256) &&
-         (fr.footprint_bins == 0 || fr.footprint_bins == 1);
+         (fr.footprint_bins == 0 || fr.footprint_bins == 1) &&
+         (fr.batch == 0 || (fr.batch % 32 == 0 && fr.batch >= 32 && fr.batch <= 512));
 }
 
 // ---------------------------------------------------------- host errors

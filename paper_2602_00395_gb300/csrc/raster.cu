@@ -68,7 +68,7 @@ __device__ __forceinline__ void stage_batch(int b, int batch, uint32_t start, in
 // its lane renders pixels (lx, ly) and (lx, ly + 4) of it.  Compact blocks meet
 // few splats; two pixels per thread halve the per-splat warp overheads.
 constexpr int kPixPerThread = 2;
-// Records staged per batch, per thread.
+// Records staged per batch, per thread (when the frame leaves the batch at 0).
 #ifndef GS_BATCH_PER_THREAD
 #define GS_BATCH_PER_THREAD 1
 #endif
@@ -79,6 +79,12 @@ constexpr int kBatchPerThread = GS_BATCH_PER_THREAD;
 #define GS_FWD_BATCH_DIV 1
 #endif
 constexpr int kFwdBatchDiv = GS_FWD_BATCH_DIV;
+__host__ __device__ __forceinline__ int fwd_batch(const gs_frame& fr, int nthr) {
+  return fr.batch ? fr.batch : kBatchPerThread * nthr / kFwdBatchDiv;
+}
+__host__ __device__ __forceinline__ int bwd_batch(const gs_frame& fr, int nthr) {
+  return fr.batch ? fr.batch : kBatchPerThread * nthr;
+}
 // Minimum resident CTAs per SM requested for the forward kernel (0: none).
 #ifndef GS_FWD_MIN_BLOCKS
 #define GS_FWD_MIN_BLOCKS 0
@@ -167,7 +173,9 @@ __device__ __forceinline__ void fwd_blend(FwdPixel<NU>& p, const Rec& r, const R
   p.last = pos + 1;
 }
 
-template <int NU>
+// CB: the frame sets its own batch (else one record per thread, known to the
+// compiler as the block size).
+template <int NU, bool CB>
 __global__ void GS_FWD_BOUNDS raster_fwd_kernel(const float4* __restrict__ rec, const float4* __restrict__ tan,
                                                          const uint32_t* __restrict__ vals,
                                                          const uint32_t* __restrict__ ranges, int n_pad, gs_frame fr,
@@ -175,7 +183,7 @@ __global__ void GS_FWD_BOUNDS raster_fwd_kernel(const float4* __restrict__ rec, 
                                                          float* __restrict__ final_T, uint32_t* __restrict__ n_contrib,
                                                          float* __restrict__ image_tan, int32_t* status) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const int nthr = blockDim.x, nwarps = nthr >> 5, batch = kBatchPerThread * nthr / kFwdBatchDiv;
+  const int nthr = blockDim.x, nwarps = nthr >> 5, batch = CB ? fr.batch : kBatchPerThread * nthr / kFwdBatchDiv;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
   Rec* buf = reinterpret_cast<Rec*>(smem + 16);
   Rec* tbuf = buf + 2 * batch;
@@ -394,7 +402,7 @@ __device__ __forceinline__ void bwd_accumulate(BwdPixel<S>& p, const Rec& r, flo
   }
 }
 
-template <int NU, bool GRAD>
+template <int NU, bool GRAD, bool CB>
 __global__ void GS_BWD_BOUNDS raster_bwd_kernel(
     const float4* __restrict__ rec, const uint32_t* __restrict__ vals, const uint32_t* __restrict__ ranges,
     int n_pad, gs_frame fr, int Tx, int T, const float* __restrict__ image, const float* __restrict__ target,
@@ -405,7 +413,7 @@ __global__ void GS_BWD_BOUNDS raster_bwd_kernel(
   constexpr int NVP = cot_stride(S);      // padded row stride of their 9 S values
   static_assert(NVP <= 32, "streams");
   extern __shared__ __align__(16) unsigned char smem[];
-  const int nthr = blockDim.x, nwarps = nthr >> 5, batch = kBatchPerThread * nthr;
+  const int nthr = blockDim.x, nwarps = nthr >> 5, batch = CB ? fr.batch : kBatchPerThread * nthr;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
   Rec* buf = reinterpret_cast<Rec*>(smem + 16);
   uint32_t* s_idx = reinterpret_cast<uint32_t*>(buf + 2 * batch);
@@ -932,19 +940,21 @@ template <int NU>
 gs_status launch_fwd(const gs_projected* proj, const gs_sorted* sorted, int n_pad, gs_frame fr, float* image,
                      float* final_T, uint32_t* n_contrib, float* image_tan, int32_t* status, cudaStream_t st) {
   const TileGrid g = tile_grid(fr);
-  const int nthr = fr.tile_w * fr.tile_h / kPixPerThread, batch = kBatchPerThread * nthr / kFwdBatchDiv;
+  const int nthr = fr.tile_w * fr.tile_h / kPixPerThread, batch = fwd_batch(fr, nthr);
   const size_t smem = 16 + (size_t)batch * (2 * sizeof(Rec) * (1 + NU) + sizeof(uint32_t));
-  static bool attr = false;
-  if (!attr) {
-    if (allow_smem(raster_fwd_kernel<NU>, 16 + (size_t)128 * kBatchPerThread / kFwdBatchDiv * (2 * sizeof(Rec) * (1 + NU) + sizeof(uint32_t))) != cudaSuccess)
+  // the dynamic shared-memory limit, raised as far as a launch needs
+  const bool cb = fr.batch != 0;
+  static size_t attr[2] = {0, 0};
+  if (smem > attr[cb]) {
+    if (allow_smem(cb ? raster_fwd_kernel<NU, true> : raster_fwd_kernel<NU, false>, smem) != cudaSuccess)
       return check_launch("gs_raster_fwd: smem attribute");
-    attr = true;
+    attr[cb] = smem;
   }
   const unsigned blocks = (unsigned)((size_t)fr.n_views * g.T);
-  raster_fwd_kernel<NU><<<blocks, nthr, smem, st>>>(reinterpret_cast<const float4*>(proj->rec),
-                                                    reinterpret_cast<const float4*>(proj->tangent), sorted->vals,
-                                                    sorted->ranges, n_pad, fr, g.Tx, g.T, image, final_T, n_contrib,
-                                                    image_tan, status);
+  auto* kern = cb ? raster_fwd_kernel<NU, true> : raster_fwd_kernel<NU, false>;
+  kern<<<blocks, nthr, smem, st>>>(reinterpret_cast<const float4*>(proj->rec),
+                                   reinterpret_cast<const float4*>(proj->tangent), sorted->vals, sorted->ranges, n_pad,
+                                   fr, g.Tx, g.T, image, final_T, n_contrib, image_tan, status);
   return check_launch("gs_raster_fwd");
 }
 
@@ -958,11 +968,18 @@ void launch_bwd_kernels(const gs_params* x, const gs_camera* cams, const gs_proj
                         const uint32_t* n_contrib, const float* image_tan, const gs_probe* probe, gs_loss loss,
                         float* grad, float* hz, float* loss_out, float* cot, int32_t* status, cudaStream_t st) {
   const TileGrid g = tile_grid(fr);
-  const int nthr = fr.tile_w * fr.tile_h / kPixPerThread, batch = kBatchPerThread * nthr;
+  const int nthr = fr.tile_w * fr.tile_h / kPixPerThread, batch = bwd_batch(fr, nthr);
   const size_t smem = 16 + (size_t)batch * (2 * sizeof(Rec) + 3 * sizeof(uint32_t));
+  const bool cb = fr.batch != 0;
+  auto* kern = cb ? raster_bwd_kernel<NU, GRAD, true> : raster_bwd_kernel<NU, GRAD, false>;
+  static size_t attr[2] = {0, 0};
+  if (smem > 48 * 1024 && smem > attr[cb]) {
+    if (allow_smem(kern, smem) != cudaSuccess) return;  // the caller reports the error
+    attr[cb] = smem;
+  }
   const float inv_m = (float)(1.0 / (3.0 * (double)fr.width * fr.height * fr.n_views));
   const unsigned blocks = (unsigned)((size_t)fr.n_views * g.T);
-  raster_bwd_kernel<NU, GRAD><<<blocks, nthr, smem, st>>>(
+  kern<<<blocks, nthr, smem, st>>>(
       reinterpret_cast<const float4*>(proj->rec), sorted->vals, sorted->ranges, x->n_pad, fr, g.Tx, g.T, image,
       target, final_T, n_contrib, image_tan, loss.kind, loss.gn_floor, inv_m, cot, loss_out, status);
   const dim3 pg((x->n + kPbwdThreads - 1) / kPbwdThreads), pb(kPbwdThreads);

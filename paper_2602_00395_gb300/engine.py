@@ -49,7 +49,7 @@ class TRStep:
                  tile=(16, 16), capacity: int | None = None, loss_kind: int = G.GS_LOSS_L1,
                  gn_floor: float = 1e-3, cfg: TRConfig | None = None, probe_seed: int = 42,
                  device: str = "cuda", state=None, zero_init: bool = True, dssim_lambda: float | None = None,
-                 footprint_bins: bool = True):
+                 footprint_bins: bool = True, batch: int = 0):
         """state: optional (x, g_ema, d_ema) tensors of shape rows x n_pad that the
         step uses in place of its own (a scene's resident parameters and trust-region
         state, shared by the short-lived steps of a serving loop).  zero_init=False
@@ -59,7 +59,9 @@ class TRStep:
         pixel loss (1 - lambda) L1 + lambda D-SSIM of Eq. pixel_loss instead of L1.
         footprint_bins: bin each splat into the tiles its alpha >= 1/255 footprint
         box reaches within its 3DGS tile square (False: the whole square); the
-        images and derivatives are the same, the pairs fewer."""
+        images and derivatives are the same, the pairs fewer.  batch: records a
+        tile's block stages per step of its list in the blends (0: one per
+        thread; else a multiple of 32 up to 512)."""
         G.load()
         self.n, self.deg, self.V, self.W, self.H, self.nu = n, sh_degree, n_views, width, height, nu
         self.n_pad = synth.pad_count(n)
@@ -69,7 +71,7 @@ class TRStep:
         self.cfg = cfg or TRConfig()
         self.loss = G.gs_loss(loss_kind, gn_floor)
         self.probe_seed = probe_seed
-        self.frame = G.frame_struct(n_views, width, height, *tile, footprint_bins=footprint_bins)
+        self.frame = G.frame_struct(n_views, width, height, *tile, footprint_bins=footprint_bins, batch=batch)
         self.Tx = -(-width // tile[0])
         self.Ty = -(-height // tile[1])
         f32 = dict(dtype=torch.float32, device=self.device)
@@ -309,19 +311,21 @@ class TRStep:
         return int(self.status.item())
 
 
-def autotune_tile(eng: TRStep, candidates=((16, 16), (32, 8), (8, 32), (16, 8)), steps: int = 3,
-                  stream=None) -> tuple[tuple[int, int], dict]:
-    """Pick the tile shape with the shortest step on the caller's own workload:
-    for each candidate a TRStep with the same parameters, cameras, targets and
-    probes runs one untimed and `steps` timed steps (CUDA events), starting from
-    copies of eng's state so that eng is left unchanged.  Returns the best shape
-    and the ms per step of every candidate."""
+def autotune_tile(eng: TRStep, candidates=((16, 16), (32, 8), (8, 32), (16, 8)), batches=(0, 64, 256),
+                  steps: int = 3, stream=None) -> tuple[tuple[int, int, int], dict]:
+    """Pick the tile shape, then the blends' per-block record batch for it, with
+    the shortest step on the caller's own workload: each candidate is a TRStep
+    with the same parameters, cameras, targets and probes that runs one untimed
+    and `steps` timed steps (CUDA events), starting from copies of eng's state so
+    that eng is left unchanged.  Returns (tile_w, tile_h, batch) and the ms per
+    step of every candidate, keyed (tile_w, tile_h, batch)."""
     s = stream or torch.cuda.Stream(device=eng.device)
     times = {}
-    for tile in candidates:
+
+    def run(tile, batch):
         e = TRStep(eng.n, eng.deg, eng.V, eng.W, eng.H, nu=eng.nu, tile=tile, cfg=eng.cfg,
                    probe_seed=eng.probe_seed, device=str(eng.device),
-                   footprint_bins=bool(eng.frame.footprint_bins))
+                   footprint_bins=bool(eng.frame.footprint_bins), batch=batch)
         for dst, src in ((e.x, eng.x), (e.g_ema, eng.g_ema), (e.d_ema, eng.d_ema), (e.cams, eng.cams),
                          (e.target, eng.target)):
             dst.copy_(src)
@@ -335,8 +339,15 @@ def autotune_tile(eng: TRStep, candidates=((16, 16), (32, 8), (8, 32), (16, 8)),
                 e.step(t, 1e-6, s)
             stop.record(s)
         stop.synchronize()
-        times[tile] = start.elapsed_time(stop) / steps
+        times[(tile[0], tile[1], batch)] = start.elapsed_time(stop) / steps
         del e
         torch.cuda.empty_cache()
-    best = min(times, key=times.get)
+
+    for tile in candidates:
+        run(tile, 0)
+    best_tile = min(candidates, key=lambda t: times[(t[0], t[1], 0)])
+    for batch in batches:
+        if batch:
+            run(best_tile, batch)
+    best = min((k for k in times if (k[0], k[1]) == tuple(best_tile)), key=times.get)
     return best, times

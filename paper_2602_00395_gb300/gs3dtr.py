@@ -41,7 +41,7 @@ class gs_camera(C.Structure):
 
 class gs_frame(C.Structure):
     _fields_ = [("n_views", C.c_int32), ("width", C.c_int32), ("height", C.c_int32), ("tile_w", C.c_int32),
-                ("tile_h", C.c_int32), ("footprint_bins", C.c_int32)]
+                ("tile_h", C.c_int32), ("footprint_bins", C.c_int32), ("batch", C.c_int32)]
 
 
 class gs_probe(C.Structure):
@@ -189,8 +189,8 @@ def camera_bytes(cams) -> np.ndarray:
 
 
 def frame_struct(n_views: int, width: int, height: int, tile_w: int = 16, tile_h: int = 16,
-                 footprint_bins: bool = True) -> gs_frame:
-    return gs_frame(n_views, width, height, tile_w, tile_h, int(footprint_bins))
+                 footprint_bins: bool = True, batch: int = 0) -> gs_frame:
+    return gs_frame(n_views, width, height, tile_w, tile_h, int(footprint_bins), int(batch))
 
 
 def probe_struct(seed: int, t: int, nu: int, t_device=None) -> gs_probe:

@@ -94,11 +94,16 @@ def test_device_schedule_matches_host_schedule():
 
 
 def test_tile_autotuner_times_every_shape_and_leaves_the_step_unchanged():
+    """Every tile shape with the default batch, then the batches for the fastest
+    shape; the pick is the fastest of those."""
     from paper_2602_00395_gb300.engine import autotune_tile
     e = _engine(1)
     before = _state(e)
-    best, times = autotune_tile(e, candidates=((16, 16), (32, 8), (16, 8)), steps=2)
-    assert set(times) == {(16, 16), (32, 8), (16, 8)}
-    assert all(v > 0 for v in times.values()) and times[best] == min(times.values())
+    best, times = autotune_tile(e, candidates=((16, 16), (32, 8), (16, 8)), batches=(0, 32, 256), steps=2)
+    shapes = [(16, 16), (32, 8), (16, 8)]
+    fastest = min(shapes, key=lambda s: times[(*s, 0)])
+    assert set(times) == {(*s, 0) for s in shapes} | {(*fastest, 32), (*fastest, 256)}
+    assert all(v > 0 for v in times.values())
+    assert (best[0], best[1]) == fastest and times[best] == min(v for k, v in times.items() if k[:2] == fastest)
     for u, v in zip(_state(e), before):
         assert torch.equal(u, v)

@@ -207,8 +207,8 @@ def test_bin_sort_empty_input():
 
 
 # ------------------------------------------------------------------ forward
-def _render_compare(sc, cams, tile=(16, 16), box=True):
-    e = _engine(sc.n, sc.sh_degree, cams, tile=tile, nu=0, footprint_bins=box)
+def _render_compare(sc, cams, tile=(16, 16), box=True, batch=0):
+    e = _engine(sc.n, sc.sh_degree, cams, tile=tile, nu=0, footprint_bins=box, batch=batch)
     e.set_params(sc.params)
     e.ensure_capacity()
     e.render()
@@ -223,14 +223,16 @@ def _render_compare(sc, cams, tile=(16, 16), box=True):
     return e, ref, img, T, nc, ok
 
 
-@pytest.mark.parametrize("case,tile,box", [("cfg1", (16, 16), True), ("cfg1", (16, 16), False),
-                                          ("ragged", (16, 8), True), ("ragged", (8, 8), True),
-                                          ("ragged", (16, 16), False)])
-def test_raster_fwd_matches_oracle(case, tile, box):
+@pytest.mark.parametrize("case,tile,box,batch", [("cfg1", (16, 16), True, 0), ("cfg1", (16, 16), False, 0),
+                                                ("ragged", (16, 8), True, 0), ("ragged", (8, 8), True, 0),
+                                                ("ragged", (16, 16), False, 0), ("ragged", (16, 16), True, 32),
+                                                ("cfg1", (16, 16), True, 512)])
+def test_raster_fwd_matches_oracle(case, tile, box, batch):
     """Image, final T, n_contrib and the pair count equal the oracle's, binning by
-    the footprint box (box True) or by the whole 3DGS tile square."""
+    the footprint (box True) or by the whole 3DGS tile square, with the default
+    and other per-block record batches."""
     sc, cams = _cfg1() if case == "cfg1" else _ragged()
-    e, ref, img, T, nc, ok = _render_compare(sc, cams, tile, box)
+    e, ref, img, T, nc, ok = _render_compare(sc, cams, tile, box, batch)
     assert int(e.n_pairs.item()) == ref["n_pairs"] or (~ok).any()
     # pixels whose value FP32 may legitimately flip: here one splat per view has
     # a radius within 1e-5 of an integer, and its ambiguous tile band is excluded
@@ -247,11 +249,11 @@ def test_raster_fwd_matches_oracle(case, tile, box):
 
 
 # ------------------------------------------------------------------ reverse
-def _grad_case(case, nu, loss_kind=0):
+def _grad_case(case, nu, loss_kind=0, batch=0):
     sc, cams = _cfg1() if case == "cfg1" else _ragged()
     V, H, W = len(cams), cams[0].height, cams[0].width
     target = S.noise_target(V, H, W, seed=2000)
-    e = _engine(sc.n, sc.sh_degree, cams, nu=nu, loss_kind=loss_kind)
+    e = _engine(sc.n, sc.sh_degree, cams, nu=nu, loss_kind=loss_kind, batch=batch)
     e.set_params(sc.params)
     e.set_target(target)
     e.ensure_capacity()
@@ -267,9 +269,11 @@ def _grad_case(case, nu, loss_kind=0):
     return sc, e, ref
 
 
-@pytest.mark.parametrize("case,nu,loss_kind", [("cfg1", 0, 0), ("cfg1", 1, 0), ("ragged", 2, 0), ("ragged", 1, 1)])
-def test_gradient_and_hutchinson_match_oracle(case, nu, loss_kind):
-    sc, e, ref = _grad_case(case, nu, loss_kind)
+@pytest.mark.parametrize("case,nu,loss_kind,batch", [("cfg1", 0, 0, 0), ("cfg1", 1, 0, 0), ("ragged", 2, 0, 0),
+                                                     ("ragged", 1, 1, 0), ("ragged", 2, 0, 64),
+                                                     ("cfg1", 1, 0, 512)])
+def test_gradient_and_hutchinson_match_oracle(case, nu, loss_kind, batch):
+    sc, e, ref = _grad_case(case, nu, loss_kind, batch)
     grad = e.grad[:, : sc.n].cpu().numpy()
     _group_close(grad, ref["grad"], 1e-4, "grad")
     assert abs(float(e.loss_val.item()) - ref["loss"]) <= 1e-5 * ref["loss"]
