@@ -5,7 +5,7 @@
 // is built in two stages instead of sorting 64-bit pair keys on all their bits:
 //
 //   records  per (view, splat): its tiles (the FP32 rectangle, narrowed row
-//            by row to the footprint ellipse, see row_span); the V x n_pad
+//            by row to the footprint ellipse, see row_span_v); the V x n_pad
 //            records are sorted by (view, depth bits) with a stable LSD radix
 //            sort (record index order breaks ties)
 //   scan     emission offsets in that order and the pair count P

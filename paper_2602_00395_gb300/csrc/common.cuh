@@ -379,8 +379,10 @@ __device__ __forceinline__ FootRows foot_rows(float mx, float my, float A, float
 // v of the band edge at pixel row y.
 __device__ __forceinline__ float band_v(const FootRows& f, int y) { return __fdiv_rn(__fsub_rn((float)y, f.my), f.hy); }
 
-// Tiles [a, b) of row ty, given the v of its band's edges (band_v at ty th and
-// (ty + 1) th).  tw is a power of two, so x / tw is the exact product by 1 / tw.
+// Tiles [a, b) of tile row ty, given the v of its band's edges (band_v at ty th
+// and (ty + 1) th; a row's lower edge is the next row's upper edge, so the
+// callers walk the rows computing each edge once).  tw is a power of two, so
+// x / tw is the exact product by 1 / tw.
 __device__ __forceinline__ void row_span_v(const FootRows& f, float vlo, float vhi, int tw, int Tx, int& a, int& b) {
   a = f.x0;
   b = f.x1;
@@ -399,16 +401,6 @@ __device__ __forceinline__ void row_span_v(const FootRows& f, float vlo, float v
   a = max(a, clamp_floor(floorf(__fmul_rn(xl, itw)), Tx));
   b = min(b, clamp_floor(__fadd_rn(floorf(__fmul_rn(xr, itw)), 1.0f), Tx));
   if (b < a) b = a;
-}
-
-// Tiles [a, b) of row ty.
-__device__ __forceinline__ void row_span(const FootRows& f, int ty, int tw, int th, int Tx, int& a, int& b) {
-  if (!f.exact) {
-    a = f.x0;
-    b = f.x1;
-    return;
-  }
-  row_span_v(f, band_v(f, ty * th), band_v(f, (ty + 1) * th), tw, Tx, a, b);
 }
 
 // Number of (tile, splat) pairs of a splat.
