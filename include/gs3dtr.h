@@ -142,13 +142,19 @@ typedef struct gs_projected {
  *   keys:     capacity x uint64, key = (view * tiles + tile) << 32 | bits(depth)
  *   vals:     capacity x uint32, splat index
  *   ranges:   V * tiles x 2 uint32, [start, end) of each tile's pairs
- *   n_pairs:  one uint32, number of pairs the views need (may exceed capacity) */
+ *   n_pairs:  one uint32, number of pairs the views need (may exceed capacity)
+ *   order:    NULL, or V * tiles uint32 that gs_bin_sort fills with the tiles
+ *             (view * tiles + tile) from the longest list to the shortest
+ *             (lengths grouped in steps of 1/8 of a power of two, any order
+ *             within a group); the blends then start the heaviest tiles first.
+ *             It changes when a tile runs, never its result. */
 typedef struct gs_sorted {
   uint64_t* keys;
   uint32_t* vals;
   uint32_t* ranges;
   uint32_t* n_pairs;
   uint64_t capacity;
+  uint32_t* order;
 } gs_sorted;
 
 enum { GS_LOSS_L1 = 0, GS_LOSS_L2 = 1, GS_LOSS_COTANGENT = 2 };

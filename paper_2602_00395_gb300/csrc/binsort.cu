@@ -558,6 +558,52 @@ __global__ void ranges_kernel(const uint64_t* __restrict__ keys, const uint32_t*
   }
 }
 
+// ------------------------------------------------------------- tile order
+// The blends run one block per tile; starting the longest lists first keeps a
+// few heavy tiles from running alone at the end.  A tile's class is
+// 8 * floor(log2 len) + the next 3 bits of len (256 classes, 0 for an empty
+// list); the order is a counting sort by class, heaviest first.
+__device__ __forceinline__ uint32_t tile_class(uint32_t len) {
+  if (len == 0) return 0;
+  const int e = 31 - __clz(len);
+  const uint32_t m = e >= 3 ? (len >> (e - 3)) & 7u : (len << (3 - e)) & 7u;
+  return min(255u, 1u + 8u * (uint32_t)e + m);
+}
+
+__global__ void tile_class_count_kernel(const uint32_t* __restrict__ ranges, uint32_t n_tiles,
+                                        uint32_t* __restrict__ cls_count) {
+  __shared__ uint32_t s_cnt[256];
+  s_cnt[threadIdx.x] = 0;
+  __syncthreads();
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n_tiles) atomicAdd(&s_cnt[tile_class(ranges[2 * t + 1] - ranges[2 * t])], 1u);
+  __syncthreads();
+  if (s_cnt[threadIdx.x]) atomicAdd(&cls_count[threadIdx.x], s_cnt[threadIdx.x]);
+}
+
+// cls_count -> the first slot of each class, heaviest class first (one block of 256)
+__global__ void tile_class_starts_kernel(uint32_t* __restrict__ cls_count) {
+  __shared__ uint32_t s_warp[32];
+  const uint32_t c = cls_count[255 - threadIdx.x];  // thread k holds class 255 - k
+  uint32_t total;
+  const uint32_t ex = block_exclusive_scan(c, total, s_warp);
+  cls_count[255 - threadIdx.x] = ex;
+}
+
+__global__ void tile_order_kernel(const uint32_t* __restrict__ ranges, uint32_t n_tiles,
+                                  uint32_t* __restrict__ cls_next, uint32_t* __restrict__ order) {
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n_tiles) order[atomicAdd(&cls_next[tile_class(ranges[2 * t + 1] - ranges[2 * t])], 1u)] = t;
+}
+
+void fill_tile_order(const uint32_t* ranges, uint32_t n_tiles, uint32_t* cls, uint32_t* order, cudaStream_t st) {
+  const unsigned tb = (n_tiles + 255) / 256;
+  if (tb == 0 || cudaMemsetAsync(cls, 0, 256 * sizeof(uint32_t), st) != cudaSuccess) return;  // reported by the caller
+  tile_class_count_kernel<<<tb, 256, 0, st>>>(ranges, n_tiles, cls);
+  tile_class_starts_kernel<<<1, 256, 0, st>>>(cls);
+  tile_order_kernel<<<tb, 256, 0, st>>>(ranges, n_tiles, cls, order);
+}
+
 // ---------------------------------------------------------------- planning
 inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
@@ -565,7 +611,7 @@ struct SortPlan {
   int Tx, Ty, rec_pass, pair_pass, nb_pairs, rec_bps;
   size_t n_items;  // views x n_pad
   size_t off_counts, off_scnt, off_sums, off_rk0, off_rk1, off_rv0, off_rv1, off_keys, off_vals, off_hist, off_hdr,
-      off_rows, off_used, total;
+      off_rows, off_used, off_cls, total;
   uint64_t rows_cap;
 };
 
@@ -602,6 +648,7 @@ SortPlan plan_sort(int32_t n_pad, gs_frame fr, uint64_t capacity) {
   p.off_hdr = o;    o += align256(p.n_items * 16);
   p.off_rows = o;   o += align256(p.rows_cap * 8);
   p.off_used = o;   o += 256;
+  p.off_cls = o;    o += 256 * 4;
   p.total = o;
   return p;
 }
@@ -662,7 +709,10 @@ extern "C" gs_status gs_bin_sort(const gs_projected* proj, int32_t n_pad, gs_fra
       cudaMemsetAsync(out->n_pairs, 0, sizeof(uint32_t), st) != cudaSuccess ||
       cudaMemsetAsync(rows_used, 0, sizeof(uint32_t), st) != cudaSuccess)
     return check_launch("gs_bin_sort: memset");
-  if (p.n_items == 0) return GS_OK;
+  if (p.n_items == 0) {  // no splats: every range is empty
+    if (out->order) fill_tile_order(out->ranges, (uint32_t)(frame.n_views * T), (uint32_t*)(ws + p.off_cls), out->order, st);
+    return check_launch("gs_bin_sort");
+  }
   const int eb = (int)((p.n_items + 255) / 256);
   // records sorted by depth within each view's segment
   uint32_t* rk[2] = {(uint32_t*)(ws + p.off_rk0), (uint32_t*)(ws + p.off_rk1)};
@@ -687,5 +737,6 @@ extern "C" gs_status gs_bin_sort(const gs_projected* proj, int32_t n_pad, gs_fra
   const int rb = (int)std::min<uint64_t>((out->capacity + 255) / 256, 152 * 16);
   ranges_kernel<<<rb, 256, 0, st>>>(out->keys, out->n_pairs, out->capacity, (uint64_t)frame.n_views * T,
                                     out->ranges);
+  if (out->order) fill_tile_order(out->ranges, (uint32_t)(frame.n_views * T), (uint32_t*)(ws + p.off_cls), out->order, st);
   return check_launch("gs_bin_sort");
 }

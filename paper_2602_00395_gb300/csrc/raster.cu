@@ -178,7 +178,8 @@ __device__ __forceinline__ void fwd_blend(FwdPixel<NU>& p, const Rec& r, const R
 template <int NU, bool CB>
 __global__ void GS_FWD_BOUNDS raster_fwd_kernel(const float4* __restrict__ rec, const float4* __restrict__ tan,
                                                          const uint32_t* __restrict__ vals,
-                                                         const uint32_t* __restrict__ ranges, int n_pad, gs_frame fr,
+                                                         const uint32_t* __restrict__ ranges,
+                                                         const uint32_t* __restrict__ order, int n_pad, gs_frame fr,
                                                          int Tx, int T, float* __restrict__ image,
                                                          float* __restrict__ final_T, uint32_t* __restrict__ n_contrib,
                                                          float* __restrict__ image_tan, int32_t* status) {
@@ -190,7 +191,9 @@ __global__ void GS_FWD_BOUNDS raster_fwd_kernel(const float4* __restrict__ rec, 
   uint32_t* s_mask = reinterpret_cast<uint32_t*>(tbuf + 2 * NU * batch);
   const int tid = threadIdx.x, lane = tid & 31;
   const uint32_t wbit = 1u << (tid >> 5);
-  const int view = blockIdx.x / T, tile = blockIdx.x - view * T;
+  // the tile of this block: the heaviest tiles first when an order is given
+  const int blk = order ? (int)min(__ldg(order + blockIdx.x), gridDim.x - 1) : (int)blockIdx.x;
+  const int view = blk / T, tile = blk - view * T;
   const int ty = tile / Tx, tx = tile - ty * Tx;
   int lx, ly;
   pixel_of(tid, fr.tile_w, lx, ly);
@@ -405,7 +408,8 @@ __device__ __forceinline__ void bwd_accumulate(BwdPixel<S>& p, const Rec& r, flo
 template <int NU, bool GRAD, bool CB>
 __global__ void GS_BWD_BOUNDS raster_bwd_kernel(
     const float4* __restrict__ rec, const uint32_t* __restrict__ vals, const uint32_t* __restrict__ ranges,
-    int n_pad, gs_frame fr, int Tx, int T, const float* __restrict__ image, const float* __restrict__ target,
+    const uint32_t* __restrict__ order, int n_pad, gs_frame fr, int Tx, int T, const float* __restrict__ image,
+    const float* __restrict__ target,
     const float* __restrict__ final_T, const uint32_t* __restrict__ n_contrib, const float* __restrict__ image_tan,
     int loss_kind, float gn_floor, float inv_m, float* __restrict__ cot, float* __restrict__ loss_out,
     int32_t* status) {
@@ -422,7 +426,9 @@ __global__ void GS_BWD_BOUNDS raster_bwd_kernel(
   __shared__ float s_loss[8];
   const int tid = threadIdx.x, lane = tid & 31;
   const uint32_t wbit = 1u << (tid >> 5);
-  const int view = blockIdx.x / T, tile = blockIdx.x - view * T;
+  // the tile of this block: the heaviest tiles first when an order is given
+  const int blk = order ? (int)min(__ldg(order + blockIdx.x), gridDim.x - 1) : (int)blockIdx.x;
+  const int view = blk / T, tile = blk - view * T;
   const int ty = tile / Tx, tx = tile - ty * Tx;
   int lx, ly;
   pixel_of(tid, fr.tile_w, lx, ly);
@@ -953,7 +959,8 @@ gs_status launch_fwd(const gs_projected* proj, const gs_sorted* sorted, int n_pa
   const unsigned blocks = (unsigned)((size_t)fr.n_views * g.T);
   auto* kern = cb ? raster_fwd_kernel<NU, true> : raster_fwd_kernel<NU, false>;
   kern<<<blocks, nthr, smem, st>>>(reinterpret_cast<const float4*>(proj->rec),
-                                   reinterpret_cast<const float4*>(proj->tangent), sorted->vals, sorted->ranges, n_pad,
+                                   reinterpret_cast<const float4*>(proj->tangent), sorted->vals, sorted->ranges,
+                                   sorted->order, n_pad,
                                    fr, g.Tx, g.T, image, final_T, n_contrib, image_tan, status);
   return check_launch("gs_raster_fwd");
 }
@@ -980,7 +987,8 @@ void launch_bwd_kernels(const gs_params* x, const gs_camera* cams, const gs_proj
   const float inv_m = (float)(1.0 / (3.0 * (double)fr.width * fr.height * fr.n_views));
   const unsigned blocks = (unsigned)((size_t)fr.n_views * g.T);
   kern<<<blocks, nthr, smem, st>>>(
-      reinterpret_cast<const float4*>(proj->rec), sorted->vals, sorted->ranges, x->n_pad, fr, g.Tx, g.T, image,
+      reinterpret_cast<const float4*>(proj->rec), sorted->vals, sorted->ranges, sorted->order, x->n_pad, fr, g.Tx,
+      g.T, image,
       target, final_T, n_contrib, image_tan, loss.kind, loss.gn_floor, inv_m, cot, loss_out, status);
   const dim3 pg((x->n + kPbwdThreads - 1) / kPbwdThreads), pb(kPbwdThreads);
   const ProbeArg pa = probe_arg(probe);

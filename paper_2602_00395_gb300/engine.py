@@ -101,6 +101,7 @@ class TRStep:
         zi = torch.zeros if zero_init else torch.empty  # gs_bin_sort clears both before use
         self.ranges = zi(2 * n_views * self.Tx * self.Ty, dtype=torch.int32, device=self.device)
         self.n_pairs = zi(1, dtype=torch.int32, device=self.device)
+        self.order = zi(n_views * self.Tx * self.Ty, dtype=torch.int32, device=self.device)  # heaviest tiles first
         self.bwd_ws = torch.empty(G.gs_raster_bwd_workspace_size(self.n_pad, self.frame, nu), dtype=torch.uint8,
                                   device=self.device)
         self.dssim_lambda = dssim_lambda
@@ -141,7 +142,7 @@ class TRStep:
 
     def sorted(self) -> G.gs_sorted:
         return G.gs_sorted(self.keys.data_ptr(), self.vals.data_ptr(), self.ranges.data_ptr(),
-                           self.n_pairs.data_ptr(), self.capacity)
+                           self.n_pairs.data_ptr(), self.capacity, self.order.data_ptr())
 
     def probe(self, t: int | None, device_t: bool = False) -> G.gs_probe | None:
         if self.nu == 0:

@@ -69,7 +69,7 @@ class gs_projected(C.Structure):
 
 class gs_sorted(C.Structure):
     _fields_ = [("keys", C.c_void_p), ("vals", C.c_void_p), ("ranges", C.c_void_p), ("n_pairs", C.c_void_p),
-                ("capacity", C.c_uint64)]
+                ("capacity", C.c_uint64), ("order", C.c_void_p)]
 
 
 class gs_loss(C.Structure):
@@ -81,7 +81,7 @@ class gs_tr_config(C.Structure):
                 ("l", C.c_int32), ("mean_exact", C.c_int32)]
 
 
-assert C.sizeof(gs_camera) == 96 and C.sizeof(gs_params) == 24 and C.sizeof(gs_sorted) == 40
+assert C.sizeof(gs_camera) == 96 and C.sizeof(gs_params) == 24 and C.sizeof(gs_sorted) == 48
 
 
 class GSError(RuntimeError):

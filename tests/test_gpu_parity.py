@@ -110,6 +110,17 @@ def test_project_matches_oracle(case):
 
 
 # ------------------------------------------------------------------ bin/sort
+def _tile_class(n):
+    """8 floor(log2 n) + the next 3 bits of n, + 1 (0 for an empty list), at most 255."""
+    n = np.asarray(n, np.int64)
+    out = np.zeros(n.shape, np.int64)
+    nz = n > 0
+    e = np.floor(np.log2(n[nz])).astype(np.int64)
+    m = np.where(e >= 3, (n[nz] >> np.maximum(e - 3, 0)) & 7, (n[nz] << np.maximum(3 - e, 0)) & 7)
+    out[nz] = np.minimum(255, 1 + 8 * e + m)
+    return out
+
+
 def _write_records(e, mx, my, r, d, ext, conic):
     rec = torch.zeros(e.V, e.n_pad, 12, dtype=torch.float32)
     n = mx.shape[1]
@@ -154,6 +165,11 @@ def test_bin_sort_bit_exact(W, H, tile, V, n, maxr, box):
     np.testing.assert_array_equal(e.keys[:P].cpu().numpy().view(np.uint64), keys)
     np.testing.assert_array_equal(e.vals[:P].cpu().numpy().view(np.uint32), vals)
     np.testing.assert_array_equal(e.ranges.cpu().numpy().view(np.uint32).reshape(-1, 2), ranges)
+    # the blends' tile order: every tile once, list lengths by class heaviest first
+    order = e.order.cpu().numpy().view(np.uint32)
+    assert np.array_equal(np.sort(order), np.arange(len(order)))
+    cls = _tile_class(ranges[:, 1].astype(np.int64) - ranges[:, 0])
+    assert np.all(np.diff(cls[order]) <= 0)
 
 
 @pytest.mark.parametrize("W,H", [(128, 96), (3840, 2160)])
