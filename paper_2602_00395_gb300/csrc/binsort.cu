@@ -592,8 +592,16 @@ __global__ void tile_class_starts_kernel(uint32_t* __restrict__ cls_count) {
 
 __global__ void tile_order_kernel(const uint32_t* __restrict__ ranges, uint32_t n_tiles,
                                   uint32_t* __restrict__ cls_next, uint32_t* __restrict__ order) {
-  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < n_tiles) order[atomicAdd(&cls_next[tile_class(ranges[2 * t + 1] - ranges[2 * t])], 1u)] = t;
+  // one atomic per class present in the warp (most tiles share class 0, the
+  // empty lists); a warp's tiles of one class keep their index order
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x, lane = threadIdx.x & 31;
+  const uint32_t c = t < n_tiles ? tile_class(ranges[2 * t + 1] - ranges[2 * t]) : 0xffffffffu;
+  const uint32_t peers = __match_any_sync(0xffffffffu, c);
+  const int leader = __ffs(peers) - 1;
+  uint32_t base = 0;
+  if ((int)lane == leader && c != 0xffffffffu) base = atomicAdd(&cls_next[c], (uint32_t)__popc(peers));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (c != 0xffffffffu) order[base + __popc(peers & ((1u << lane) - 1u))] = t;
 }
 
 void fill_tile_order(const uint32_t* ranges, uint32_t n_tiles, uint32_t* cls, uint32_t* order, cudaStream_t st) {

@@ -581,7 +581,9 @@ __global__ void GS_BWD_BOUNDS raster_bwd_kernel(
 // One thread per Gaussian.  A first pass over the views computes each view's
 // geometry once and applies it to every cotangent stream (geometric rows); a
 // second pass per stream accumulates the SH rows, reusing the clamp decisions
-// recorded in the first.  The probe streams are combined into
+// recorded in the first.  The first pass also keeps the clamped colour
+// cotangents of the first kStashViews views in shared memory, so the second
+// pass reads them there instead of from L2.  The probe streams are combined into
 // hz = (1/nu) sum_k z_k . (G z_k).
 constexpr int kPbwdThreads = 128;
 // Minimum resident CTAs per SM requested for the projection reverse (0: none).
@@ -594,6 +596,12 @@ constexpr int kPbwdThreads = 128;
 #define GS_PBWD_BOUNDS __launch_bounds__(kPbwdThreads)
 #endif
 constexpr int kClampViews = 21;  // clamp bits kept for the first 21 views (3 per view)
+constexpr int kStashViews = 8;   // views whose colour cotangents pass 2 reads from shared memory
+
+// dynamic shared memory of the projection reverse: min(V, kStashViews) x 3S x kPbwdThreads floats
+__host__ __device__ constexpr size_t pbwd_stash_bytes(int n_views, int streams) {
+  return (size_t)(n_views < kStashViews ? n_views : kStashViews) * 3 * streams * kPbwdThreads * sizeof(float);
+}
 
 struct ViewGeom {
   float Rc[3][3], tc[3], fx, fy;
@@ -639,6 +647,9 @@ __global__ void GS_PBWD_BOUNDS project_bwd_kernel(const float* __restrict__ P, i
   __syncthreads();
   const volatile float* vsh = &s_sh[0][0];
   auto sh_of = [&](int k, int ch) { return vsh[(3 * k + ch) * kPbwdThreads + threadIdx.x]; };
+  // colour cotangents (0 where clamped) of views v < kStashViews, one column per thread
+  extern __shared__ float s_pbwd_stash[];
+  auto stash = [&](int v, int j) -> float& { return s_pbwd_stash[(v * 3 * S + j) * kPbwdThreads + threadIdx.x]; };
   if (i >= n) return;
   const uint64_t seed = pa.seed;
   const int64_t step = NU > 0 ? probe_step(pa) : 0;
@@ -695,7 +706,13 @@ __global__ void GS_PBWD_BOUNDS project_bwd_kernel(const float* __restrict__ P, i
       c[4 * q + 0] = x4.x; c[4 * q + 1] = x4.y; c[4 * q + 2] = x4.z; c[4 * q + 3] = x4.w;
       any = any || x4.x != 0.f || x4.y != 0.f || x4.z != 0.f || x4.w != 0.f;
     }
-    if (!any) continue;
+    if (!any) {
+      if (v < kStashViews) {
+#pragma unroll
+        for (int j = 0; j < 3 * S; ++j) stash(v, j) = 0.f;
+      }
+      continue;
+    }
     ViewGeom vg;
     load_view(cams + v, vg);
     const float fx = vg.fx, fy = vg.fy;
@@ -796,6 +813,12 @@ __global__ void GS_PBWD_BOUNDS project_bwd_kernel(const float* __restrict__ P, i
       if (clamped[ch] && v < kClampViews) clamp_bits |= 1ull << (3 * v + ch);
       if constexpr (DEG > 0) sh_basis_grad<DEG>(d[0], d[1], d[2], shc, gdc[ch]);
     }
+    if (v < kStashViews) {
+#pragma unroll
+      for (int st = 0; st < S; ++st)
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) stash(v, 3 * st + ch) = clamped[ch] ? 0.f : c[9 * st + 6 + ch];
+    }
     if constexpr (DEG > 0) {
 #pragma unroll
       for (int st = 0; st < S; ++st) {
@@ -876,8 +899,15 @@ __global__ void GS_PBWD_BOUNDS project_bwd_kernel(const float* __restrict__ P, i
     for (int k = 0; k < K; ++k) g_sh[k][0] = g_sh[k][1] = g_sh[k][2] = 0.f;
 #pragma unroll 1
     for (int v = 0; v < fr.n_views; ++v) {
-      const float* cv = cot + ((size_t)v * n_pad + i) * NVP + 9 * st + 6;
-      float gcol[3] = {cv[0], cv[1], cv[2]};
+      float gcol[3];
+      if (v < kStashViews) {
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) gcol[ch] = stash(v, 3 * st + ch);  // clamps applied
+      } else {
+        const float* cv = cot + ((size_t)v * n_pad + i) * NVP + 9 * st + 6;
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) gcol[ch] = cv[ch];
+      }
       if (gcol[0] == 0.f && gcol[1] == 0.f && gcol[2] == 0.f) continue;
       ViewGeom vg;
       load_view(cams + v, vg);
@@ -885,7 +915,9 @@ __global__ void GS_PBWD_BOUNDS project_bwd_kernel(const float* __restrict__ P, i
       view_direction(vg, mu, d, dn);
       float Y[K];
       sh_basis<DEG>(d[0], d[1], d[2], Y);
-      if (v < kClampViews) {
+      if (v < kStashViews) {
+        // clamps already applied
+      } else if (v < kClampViews) {
 #pragma unroll
         for (int ch = 0; ch < 3; ++ch)
           if ((clamp_bits >> (3 * v + ch)) & 1ull) gcol[ch] = 0.f;
@@ -969,6 +1001,21 @@ size_t bwd_cot_floats(int32_t n_pad, gs_frame fr, int streams) {
   return (size_t)fr.n_views * n_pad * cot_stride(streams);
 }
 
+template <int DEG, int NU, bool GRAD>
+void launch_pbwd(const gs_params* x, const gs_camera* cams, gs_frame fr, const float* cot, const gs_probe* probe,
+                 float* grad, float* hz, cudaStream_t st) {
+  constexpr int S = (GRAD ? 1 : 0) + NU;
+  const size_t smem = pbwd_stash_bytes(fr.n_views, S);
+  static size_t attr = 0;
+  if (smem > attr) {
+    if (allow_smem(project_bwd_kernel<DEG, NU, GRAD>, smem) != cudaSuccess) return;  // the caller reports the error
+    attr = smem;
+  }
+  const dim3 pg((x->n + kPbwdThreads - 1) / kPbwdThreads), pb(kPbwdThreads);
+  project_bwd_kernel<DEG, NU, GRAD><<<pg, pb, smem, st>>>(x->data, x->n, x->n_pad, cams, fr, cot, probe_arg(probe),
+                                                          grad, hz);
+}
+
 template <int NU, bool GRAD>
 void launch_bwd_kernels(const gs_params* x, const gs_camera* cams, const gs_projected* proj, const gs_sorted* sorted,
                         gs_frame fr, const float* image, const float* target, const float* final_T,
@@ -990,14 +1037,12 @@ void launch_bwd_kernels(const gs_params* x, const gs_camera* cams, const gs_proj
       reinterpret_cast<const float4*>(proj->rec), sorted->vals, sorted->ranges, sorted->order, x->n_pad, fr, g.Tx,
       g.T, image,
       target, final_T, n_contrib, image_tan, loss.kind, loss.gn_floor, inv_m, cot, loss_out, status);
-  const dim3 pg((x->n + kPbwdThreads - 1) / kPbwdThreads), pb(kPbwdThreads);
-  const ProbeArg pa = probe_arg(probe);
   if (x->n == 0) return;
   switch (x->sh_degree) {
-    case 0: project_bwd_kernel<0, NU, GRAD><<<pg, pb, 0, st>>>(x->data, x->n, x->n_pad, cams, fr, cot, pa, grad, hz); break;
-    case 1: project_bwd_kernel<1, NU, GRAD><<<pg, pb, 0, st>>>(x->data, x->n, x->n_pad, cams, fr, cot, pa, grad, hz); break;
-    case 2: project_bwd_kernel<2, NU, GRAD><<<pg, pb, 0, st>>>(x->data, x->n, x->n_pad, cams, fr, cot, pa, grad, hz); break;
-    default: project_bwd_kernel<3, NU, GRAD><<<pg, pb, 0, st>>>(x->data, x->n, x->n_pad, cams, fr, cot, pa, grad, hz); break;
+    case 0: launch_pbwd<0, NU, GRAD>(x, cams, fr, cot, probe, grad, hz, st); break;
+    case 1: launch_pbwd<1, NU, GRAD>(x, cams, fr, cot, probe, grad, hz, st); break;
+    case 2: launch_pbwd<2, NU, GRAD>(x, cams, fr, cot, probe, grad, hz, st); break;
+    default: launch_pbwd<3, NU, GRAD>(x, cams, fr, cot, probe, grad, hz, st); break;
   }
 }
 
