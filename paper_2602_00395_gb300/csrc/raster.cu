@@ -891,45 +891,57 @@ __global__ void GS_PBWD_BOUNDS project_bwd_kernel(const float* __restrict__ P, i
     for (int r = 0; r < kRowSH; ++r) hz[(size_t)r * n_pad + i] = hz_geo[r];
   }
 
-  // ---- pass 2 per stream: SH rows
-#pragma unroll 1
-  for (int st = 0; st < S; ++st) {
+  // ---- pass 2: SH rows, dSH_k = sum_v Y_k(d_v) dc_v.  The gradient stream
+  // alone; two probe streams in one walk over the views: z1 . G1 + z2 . G2 =
+  // z1 . (G1 + (z1 z2) G2), so the sums of Y (dc1 + dc2) and Y (dc1 - dc2) are
+  // kept and each row's sign product picks one.
+  // colour cotangent of view v, stream st (clamps applied for v < kStashViews)
+  auto colour_cot = [&](int v, int st, float (&g)[3]) {
+    if (v < kStashViews) {
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) g[ch] = stash(v, 3 * st + ch);
+    } else {
+      const float* cv = cot + ((size_t)v * n_pad + i) * NVP + 9 * st + 6;
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) g[ch] = cv[ch];
+    }
+  };
+  // basis of view v and its clamp decisions (true: channel clamped at 0)
+  auto view_basis = [&](int v, float (&Y)[K], bool (&cl)[3]) {
+    ViewGeom vg;
+    load_view(cams + v, vg);
+    float d[3], dn;
+    view_direction(vg, mu, d, dn);
+    sh_basis<DEG>(d[0], d[1], d[2], Y);
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+      if (v < kStashViews) {
+        cl[ch] = false;  // already applied
+      } else if (v < kClampViews) {
+        cl[ch] = (clamp_bits >> (3 * v + ch)) & 1ull;
+      } else {
+        float raw = 0.5f;
+#pragma unroll
+        for (int k = 0; k < K; ++k) raw += Y[k] * sh_of(k, ch);
+        cl[ch] = raw < 0.f;
+      }
+    }
+  };
+  auto sh_rows_single = [&](int st) {
     float g_sh[K][3];
 #pragma unroll
     for (int k = 0; k < K; ++k) g_sh[k][0] = g_sh[k][1] = g_sh[k][2] = 0.f;
 #pragma unroll 1
     for (int v = 0; v < fr.n_views; ++v) {
       float gcol[3];
-      if (v < kStashViews) {
-#pragma unroll
-        for (int ch = 0; ch < 3; ++ch) gcol[ch] = stash(v, 3 * st + ch);  // clamps applied
-      } else {
-        const float* cv = cot + ((size_t)v * n_pad + i) * NVP + 9 * st + 6;
-#pragma unroll
-        for (int ch = 0; ch < 3; ++ch) gcol[ch] = cv[ch];
-      }
+      colour_cot(v, st, gcol);
       if (gcol[0] == 0.f && gcol[1] == 0.f && gcol[2] == 0.f) continue;
-      ViewGeom vg;
-      load_view(cams + v, vg);
-      float d[3], dn;
-      view_direction(vg, mu, d, dn);
       float Y[K];
-      sh_basis<DEG>(d[0], d[1], d[2], Y);
-      if (v < kStashViews) {
-        // clamps already applied
-      } else if (v < kClampViews) {
+      bool cl[3];
+      view_basis(v, Y, cl);
 #pragma unroll
-        for (int ch = 0; ch < 3; ++ch)
-          if ((clamp_bits >> (3 * v + ch)) & 1ull) gcol[ch] = 0.f;
-      } else {
-#pragma unroll
-        for (int ch = 0; ch < 3; ++ch) {
-          float raw = 0.5f;
-#pragma unroll
-          for (int k = 0; k < K; ++k) raw += Y[k] * sh_of(k, ch);
-          if (raw < 0.f) gcol[ch] = 0.f;
-        }
-      }
+      for (int ch = 0; ch < 3; ++ch)
+        if (cl[ch]) gcol[ch] = 0.f;
 #pragma unroll
       for (int k = 0; k < K; ++k)
 #pragma unroll
@@ -941,19 +953,60 @@ __global__ void GS_PBWD_BOUNDS project_bwd_kernel(const float* __restrict__ P, i
 #pragma unroll
         for (int ch = 0; ch < 3; ++ch) grad[(size_t)(kRowSH + 3 * k + ch) * n_pad + i] = g_sh[k][ch];
     } else {
-      const int kp = st - (GRAD ? 1 : 0);
-      const uint64_t zneg = probe_signs(seed, step, kp, (uint64_t)i, kRowSH + 3 * K);
+      const uint64_t zneg = probe_signs(seed, step, st - (GRAD ? 1 : 0), (uint64_t)i, kRowSH + 3 * K);
 #pragma unroll
       for (int k = 0; k < K; ++k)
 #pragma unroll
         for (int ch = 0; ch < 3; ++ch) {
           const int r = kRowSH + 3 * k + ch;
           const bool neg = (zneg >> r) & 1ull;
-          const float val = (neg ? -g_sh[k][ch] : g_sh[k][ch]) * inv_nu;
-          float* dst = hz + (size_t)r * n_pad + i;
-          *dst = (kp == 0) ? val : *dst + val;
+          hz[(size_t)r * n_pad + i] = (neg ? -g_sh[k][ch] : g_sh[k][ch]) * inv_nu;
         }
     }
+  };
+  if constexpr (GRAD) sh_rows_single(0);
+  if constexpr (NU == 1) sh_rows_single(GRAD ? 1 : 0);
+  if constexpr (NU == 2) {
+    constexpr int s1 = GRAD ? 1 : 0, s2 = s1 + 1;
+    float sp[K][3], sm[K][3];  // sums of Y (dc1 + dc2) and Y (dc1 - dc2)
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) sp[k][ch] = sm[k][ch] = 0.f;
+#pragma unroll 1
+    for (int v = 0; v < fr.n_views; ++v) {
+      float g1[3], g2[3];
+      colour_cot(v, s1, g1);
+      colour_cot(v, s2, g2);
+      if (g1[0] == 0.f && g1[1] == 0.f && g1[2] == 0.f && g2[0] == 0.f && g2[1] == 0.f && g2[2] == 0.f) continue;
+      float Y[K];
+      bool cl[3];
+      view_basis(v, Y, cl);
+      float gp[3], gm[3];
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) {
+        gp[ch] = cl[ch] ? 0.f : g1[ch] + g2[ch];
+        gm[ch] = cl[ch] ? 0.f : g1[ch] - g2[ch];
+      }
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+          sp[k][ch] += Y[k] * gp[ch];
+          sm[k][ch] += Y[k] * gm[ch];
+        }
+    }
+    const uint64_t zn1 = probe_signs(seed, step, 0, (uint64_t)i, kRowSH + 3 * K);
+    const uint64_t zn2 = probe_signs(seed, step, 1, (uint64_t)i, kRowSH + 3 * K);
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) {
+        const int r = kRowSH + 3 * k + ch;
+        const bool n1 = (zn1 >> r) & 1ull, same = ((zn1 ^ zn2) >> r & 1ull) == 0;
+        const float val = same ? sp[k][ch] : sm[k][ch];
+        hz[(size_t)r * n_pad + i] = (n1 ? -val : val) * inv_nu;
+      }
   }
 }
 
