@@ -574,7 +574,9 @@ __global__ void GS_BWD_BOUNDS raster_bwd_kernel(
 //                        dC/da = 1/det - ac/det^2, dC/db = 2ab/det^2, dC/dc = -a^2/det^2
 //   Sigma' = J Sc J^T:   dSc = J^T Gs J, dJ = 2 Gs J Sc, Gs = [[ga, gb/2], [gb/2, gc]]
 //   J(t):                the slope clamp cuts the t_x (t_y) path, J02 = -fx uc / tz
-//   Sc = W Sigma W^T:    dSigma = W^T dSc W;   mean2D(t) and t = W mu + t_w
+//   Sc = W Sigma W^T:    dSigma = W^T dSc W = (W^T J^T) Gs (J W), summed as the 6
+//                        entries of a symmetric matrix from a0 = W^T j0, a1 = W^T j1
+//                        (j0, j1 the rows of J);   mean2D(t) and t = W mu + t_w
 //   Sigma = M M^T:       dM = 2 dSigma M, M = R diag(s), s = exp(log s)
 //   R(q / |q|):          dq = (dqn - qn (qn . dqn)) / |q|
 //   colour:              dSH_k = Y_k dc (0 where clamped), dmu += P_perp grad_Y . (sum sh dc) / |d|
@@ -683,16 +685,16 @@ __global__ void GS_PBWD_BOUNDS project_bwd_kernel(const float* __restrict__ P, i
   const float dsig = opac * (1.f - opac);
 
   // ---- pass 1: geometric rows of every stream
-  float g_mu[S][3], g_S[S][3][3], g_ol[S];
+  // g_S: dL/dSigma, symmetric, entries (0,0) (0,1) (0,2) (1,1) (1,2) (2,2)
+  constexpr int kSymP[6] = {0, 0, 0, 1, 1, 2}, kSymQ[6] = {0, 1, 2, 1, 2, 2};
+  float g_mu[S][3], g_S[S][6], g_ol[S];
 #pragma unroll
   for (int st = 0; st < S; ++st) {
     g_ol[st] = 0.f;
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      g_mu[st][a] = 0.f;
+    for (int a = 0; a < 3; ++a) g_mu[st][a] = 0.f;
 #pragma unroll
-      for (int b = 0; b < 3; ++b) g_S[st][a][b] = 0.f;
-    }
+    for (int e = 0; e < 6; ++e) g_S[st][e] = 0.f;
   }
   uint64_t clamp_bits = 0;  // bit 3 v + c: colour channel c clamped at 0 in view v (v < kClampViews)
 #pragma unroll 1
@@ -740,7 +742,13 @@ __global__ void GS_PBWD_BOUNDS project_bwd_kernel(const float* __restrict__ P, i
     const float cc = J11 * J11 * Sc[1][1] + 2.f * J11 * J12 * Sc[1][2] + J12 * J12 * Sc[2][2] + kDilation;
     const float det = a * cc - bb * bb;
     const float idet = 1.f / det, id2 = idet * idet;
-    const float j0[3] = {J00, 0.f, J02}, j1[3] = {0.f, J11, J12};
+    // rows of J taken back to world axes: a0 = W^T j0, a1 = W^T j1
+    float a0[3], a1[3];
+#pragma unroll
+    for (int p2 = 0; p2 < 3; ++p2) {
+      a0[p2] = vg.Rc[0][p2] * J00 + vg.Rc[2][p2] * J02;
+      a1[p2] = vg.Rc[1][p2] * J11 + vg.Rc[2][p2] * J12;
+    }
     float JS0[3], JS1[3];
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
@@ -762,12 +770,6 @@ __global__ void GS_PBWD_BOUNDS project_bwd_kernel(const float* __restrict__ P, i
       const float ga = gA * (-cc * cc * id2) + gB * (bb * cc * id2) + gC * (idet - a * cc * id2);
       const float gb = gA * (2.f * bb * cc * id2) + gB * (-idet - 2.f * bb * bb * id2) + gC * (2.f * a * bb * id2);
       const float gc = gA * (idet - a * cc * id2) + gB * (a * bb * id2) + gC * (-a * a * id2);
-      float gSc[3][3];
-#pragma unroll
-      for (int p2 = 0; p2 < 3; ++p2)
-#pragma unroll
-        for (int q = 0; q < 3; ++q)
-          gSc[p2][q] = ga * j0[p2] * j0[q] + 0.5f * gb * (j0[p2] * j1[q] + j1[p2] * j0[q]) + gc * j1[p2] * j1[q];
       const float gJ00 = 2.f * (ga * JS0[0] + 0.5f * gb * JS1[0]);
       const float gJ02 = 2.f * (ga * JS0[2] + 0.5f * gb * JS1[2]);
       const float gJ11 = 2.f * (0.5f * gb * JS0[1] + gc * JS1[1]);
@@ -779,15 +781,17 @@ __global__ void GS_PBWD_BOUNDS project_bwd_kernel(const float* __restrict__ P, i
               gJ02 * dJ02_dtz + gJ12 * dJ12_dtz;
 #pragma unroll
       for (int q = 0; q < 3; ++q) g_mu[st][q] += vg.Rc[0][q] * gt[0] + vg.Rc[1][q] * gt[1] + vg.Rc[2][q] * gt[2];
+      // dSigma += ga a0 a0^T + gb/2 (a0 a1^T + a1 a0^T) + gc a1 a1^T = u a0^T + w a1^T
+      {
+        const float hb = 0.5f * gb;
+        float u[3], w[3];
 #pragma unroll
-      for (int p2 = 0; p2 < 3; ++p2) {
-        float tmp[3];
+        for (int p2 = 0; p2 < 3; ++p2) {
+          u[p2] = ga * a0[p2] + hb * a1[p2];
+          w[p2] = hb * a0[p2] + gc * a1[p2];
+        }
 #pragma unroll
-        for (int q = 0; q < 3; ++q)
-          tmp[q] = vg.Rc[0][p2] * gSc[0][q] + vg.Rc[1][p2] * gSc[1][q] + vg.Rc[2][p2] * gSc[2][q];
-#pragma unroll
-        for (int q = 0; q < 3; ++q)
-          g_S[st][p2][q] += tmp[0] * vg.Rc[0][q] + tmp[1] * vg.Rc[1][q] + tmp[2] * vg.Rc[2][q];
+        for (int e = 0; e < 6; ++e) g_S[st][e] += u[kSymP[e]] * a0[kSymQ[e]] + w[kSymP[e]] * a1[kSymQ[e]];
       }
       g_ol[st] += mo[5] * dsig;
     }
@@ -843,12 +847,14 @@ __global__ void GS_PBWD_BOUNDS project_bwd_kernel(const float* __restrict__ P, i
   const float inv_nu = NU > 0 ? 1.f / (float)NU : 0.f;
 #pragma unroll
   for (int st = 0; st < S; ++st) {
+    const float gS[3][3] = {{g_S[st][0], g_S[st][1], g_S[st][2]},
+                            {g_S[st][1], g_S[st][3], g_S[st][4]},
+                            {g_S[st][2], g_S[st][4], g_S[st][5]}};
     float gM[3][3];
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
-      for (int b = 0; b < 3; ++b)
-        gM[a][b] = 2.f * (g_S[st][a][0] * M[0][b] + g_S[st][a][1] * M[1][b] + g_S[st][a][2] * M[2][b]);
+      for (int b = 0; b < 3; ++b) gM[a][b] = 2.f * (gS[a][0] * M[0][b] + gS[a][1] * M[1][b] + gS[a][2] * M[2][b]);
     float rowv[kRowSH];
     float gR[3][3];
 #pragma unroll
