@@ -14,7 +14,9 @@
 // mbarrier, double-buffered so that the next batch lands while the current one
 // is blended.  Per batch every splat gets a mask of the warp blocks its
 // alpha >= 1/255 footprint can reach, and each warp walks only its own visible
-// splats (one ballot per 32).  The reverse pass walks the list back to front,
+// splats (one ballot per 32).  In the reverse pass the warps release the two
+// buffers one by one instead of meeting at block barriers, and the last warp
+// out refills a buffer.  The reverse pass walks the list back to front,
 // recovers T_i = T_{i+1} / (1 - a_i) from the final transmittance (nothing per
 // pair is stored), sums each splat's 9 x streams partial derivatives over the
 // warp's 64 pixels with a reduction that ends in quads, and adds them with float4
@@ -289,6 +291,55 @@ __global__ void GS_FWD_BOUNDS raster_fwd_kernel(const float4* __restrict__ rec, 
 }
 
 // ------------------------------------------------------------------ reverse
+// The reverse pass stages its batches in a ring of kBwdStages buffers that the
+// warps release one by one, instead of block barriers per batch: a warp moves
+// on to the next batch as soon as it has landed and tests only its own block's
+// visibility, so a warp with little work in a batch does not wait for the
+// others.  The last warp to release a buffer refills it with the batch
+// kBwdStages further on.  Two stages measured fastest (deeper rings take
+// shared memory from L1 or from resident CTAs).
+#ifndef GS_BWD_STAGES
+#define GS_BWD_STAGES 2
+#endif
+constexpr int kBwdStages = GS_BWD_STAGES;
+// ring header: one mbarrier and one release counter per stage, 16-byte aligned
+constexpr size_t kBwdRingHdr = (kBwdStages * (sizeof(uint64_t) + sizeof(uint32_t)) + 15) / 16 * 16;
+__host__ __device__ constexpr size_t bwd_smem_bytes(int batch) {
+  return kBwdRingHdr + (size_t)kBwdStages * batch * (sizeof(Rec) + sizeof(uint32_t));
+}
+
+// The calling warp fills ring stage s with batch b of the list: its lanes store
+// the Gaussian indices and issue one bulk copy per record, then lane 0 arms the
+// stage's barrier with the byte count.  The copies may complete before that
+// arrival (the phase cannot complete while the arrival is pending), and the
+// arrival releases the index stores to the warps that wait on the phase.
+__device__ __forceinline__ void stage_batch_warp(int s, int b, int batch, uint32_t start, int n, int view,
+                                                 int n_pad, const uint32_t* __restrict__ vals,
+                                                 const float4* __restrict__ rec, Rec* buf, uint32_t* s_idx,
+                                                 uint64_t* full) {
+  const int lane = threadIdx.x & 31;
+  const int cnt = min(batch, n - b * batch);
+  __syncwarp();
+  fence_proxy_async();  // the ring slot's earlier reads come before the copies' writes
+  for (int q = lane; q < cnt; q += 32) {
+    const uint32_t gi = __ldg(vals + start + (uint32_t)(b * batch + q));
+    s_idx[s * batch + q] = gi;
+    bulk_g2s(&buf[s * batch + q], rec + 3 * ((size_t)view * n_pad + gi), sizeof(Rec), &full[s]);
+  }
+  __syncwarp();
+  if (lane == 0) mbar_arrive_expect_tx(&full[s], (uint32_t)(cnt * (int)sizeof(Rec)));
+}
+
+// True if the splat can reach alpha >= 1/255 at some pixel centre of the 8 x 8
+// block whose first pixel centre is (x0, y0) (the test of warp_block_mask for
+// one block).
+__device__ __forceinline__ bool block_sees(const Rec& r, float x0, float y0) {
+  const uint32_t e = __float_as_uint(r.c.w);
+  const float hx = __half2float(__ushort_as_half((unsigned short)(e & 0xffffu)));
+  const float hy = __half2float(__ushort_as_half((unsigned short)(e >> 16)));
+  return r.a.x + hx >= x0 && r.a.x - hx <= x0 + 7.f && r.a.y + hy >= y0 && r.a.y - hy <= y0 + 7.f;
+}
+
 // Minimum resident CTAs per SM requested from the compiler for the reverse
 // kernel (0: no request).
 #ifndef GS_BWD_MIN_BLOCKS
@@ -418,24 +469,27 @@ __global__ void GS_BWD_BOUNDS raster_bwd_kernel(
   static_assert(NVP <= 32, "streams");
   extern __shared__ __align__(16) unsigned char smem[];
   const int nthr = blockDim.x, nwarps = nthr >> 5, batch = CB ? fr.batch : kBatchPerThread * nthr;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
-  Rec* buf = reinterpret_cast<Rec*>(smem + 16);
-  uint32_t* s_idx = reinterpret_cast<uint32_t*>(buf + 2 * batch);
-  uint32_t* s_mask = s_idx + 2 * batch;
+  constexpr int K = kBwdStages;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem);                     // K phase barriers
+  uint32_t* released = reinterpret_cast<uint32_t*>(smem + K * sizeof(uint64_t));  // K release counters
+  Rec* buf = reinterpret_cast<Rec*>(smem + kBwdRingHdr);
+  uint32_t* s_idx = reinterpret_cast<uint32_t*>(buf + K * batch);
   __shared__ uint32_t s_max;
+  __shared__ int s_abort;
   __shared__ float s_loss[8];
-  const int tid = threadIdx.x, lane = tid & 31;
-  const uint32_t wbit = 1u << (tid >> 5);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   // the tile of this block: the heaviest tiles first when an order is given
   const int blk = order ? (int)min(__ldg(order + blockIdx.x), gridDim.x - 1) : (int)blockIdx.x;
   const int view = blk / T, tile = blk - view * T;
   const int ty = tile / Tx, tx = tile - ty * Tx;
   int lx, ly;
   pixel_of(tid, fr.tile_w, lx, ly);
-  const float tile_x0 = (float)(tx * fr.tile_w), tile_y0 = (float)(ty * fr.tile_h);
   const size_t tslot = 2 * ((size_t)view * T + tile);
   const uint32_t start = ranges[tslot], list_len = ranges[tslot + 1] - start;
   const size_t HW = (size_t)fr.width * fr.height;
+  // first pixel centre of this warp's 8 x 8 block
+  const float wx0 = (float)(tx * fr.tile_w + (warp % (fr.tile_w >> 3)) * 8) + 0.5f;
+  const float wy0 = (float)(ty * fr.tile_h + (warp / (fr.tile_w >> 3)) * 8) + 0.5f;
 
   // per-pixel cotangents dL/dC of each stream and the loss
   BwdPixel<S> pix[kPixPerThread];
@@ -483,8 +537,12 @@ __global__ void GS_BWD_BOUNDS raster_bwd_kernel(
   }
   if (tid == 0) {
     s_max = 0;
-    mbar_init(&bars[0], 1);
-    mbar_init(&bars[1], 1);
+    // a stage wait that ran out in an earlier block: skip the list walk
+    s_abort = status ? (*(volatile int32_t*)status & GS_FLAG_TIMEOUT) : 0;
+    for (int k = 0; k < K; ++k) {
+      mbar_init(&full[k], 1);
+      released[k] = 0;
+    }
     fence_mbar_init();
   }
   __syncthreads();
@@ -504,30 +562,26 @@ __global__ void GS_BWD_BOUNDS raster_bwd_kernel(
     for (int k = 0; k < nwarps; ++k) tot += s_loss[k];
     atomicAdd(loss_out, tot);
   }
-  const int n = (int)min(s_max, list_len);  // n_contrib never exceeds the tile's list
+  const int n = s_abort ? 0 : (int)min(s_max, list_len);  // n_contrib never exceeds the tile's list
   const int nb = (n + batch - 1) / batch;
-  if (nb > 0) stage_batch<0>(nb - 1, batch, start, n, view, n_pad, vals, rec, nullptr, buf, nullptr, s_idx, bars);
-  __syncthreads();  // publish s_idx of the first batch
-  int uses = 0;  // batches waited on so far, for the barrier parity
-  for (int b = nb - 1; b >= 0; --b) {
-    if (b - 1 >= 0)
-      stage_batch<0>(b - 1, batch, start, n, view, n_pad, vals, rec, nullptr, buf, nullptr, s_idx, bars);
-    const int bi = b & 1;
-    // batch b is the (nb - 1 - b)-th use overall; buffer bi has been used
-    // floor((nb - 1 - b) / 2) times before (buffers alternate).  Block-uniform,
-    // since the warps below shuffle with full masks.
-    const bool ok = __syncthreads_and(mbar_wait_bounded(&bars[bi], (uint32_t)((uses >> 1) & 1), status)) != 0;
-    ++uses;
+  // batch b is use u = nb - 1 - b of the ring: stage u % K, its (u / K)-th fill
+  for (int u = warp; u < min(K, nb); u += nwarps)
+    stage_batch_warp(u, nb - 1 - u, batch, start, n, view, n_pad, vals, rec, buf, s_idx, full);
+  bool ok = true;
+  for (int u = 0; u < nb; ++u) {
+    const int st = u % K, b = nb - 1 - u;
+    // every lane waits (bounded) for the stage's phase: each acquires the copies
+    // and indices; after a wait ran out the warp waits no more
+    const bool landed = ok && mbar_wait_bounded(&full[st], (uint32_t)((u / K) & 1), status);
+    ok = __all_sync(0xffffffffu, ok && landed) != 0;
     const int cnt = min(batch, n - b * batch);
-    const Rec* bb = buf + bi * batch;
-    for (int q = tid; q < cnt; q += nthr)
-      s_mask[q] = ok ? warp_block_mask(bb[q], tile_x0, tile_y0, fr.tile_w, nwarps) : 0u;
-    __syncthreads();
+    const Rec* bb = buf + st * batch;
     // the warp walks, back to front, only the splats its block can see and
     // that lie before its last contributor: one ballot per 32 splats
-    for (int j0 = ((cnt - 1) & ~31); ok && j0 >= 0; j0 -= 32) {
+    for (int j0 = ((cnt - 1) & ~31); ok && (uint32_t)(b * batch) < warp_nc && j0 >= 0; j0 -= 32) {
       const int jl = j0 + lane;
-      uint32_t bits = __ballot_sync(0xffffffffu, jl < cnt && (uint32_t)(b * batch + jl) < warp_nc && (s_mask[jl] & wbit));
+      uint32_t bits =
+          __ballot_sync(0xffffffffu, jl < cnt && (uint32_t)(b * batch + jl) < warp_nc && block_sees(bb[jl], wx0, wy0));
       while (bits) {
         const int hb = 31 - __clz(bits);
         bits &= ~(1u << hb);
@@ -553,7 +607,7 @@ __global__ void GS_BWD_BOUNDS raster_bwd_kernel(
         bwd_accumulate<S, false>(pix[1], r, dx[1], dy[1], G[1], oG[1], alpha[1], v);
 #pragma unroll
         for (int q = 9 * S; q < 32; ++q) v[q] = 0.f;
-        const uint32_t gi = s_idx[bi * batch + j];
+        const uint32_t gi = s_idx[st * batch + j];
         float* dst = cot + ((size_t)view * n_pad + gi) * NVP;
         float qs[4];
         if constexpr (NVP <= 16) warp_reduce_quads16(v, qs);
@@ -562,7 +616,21 @@ __global__ void GS_BWD_BOUNDS raster_bwd_kernel(
           atomicAdd(reinterpret_cast<float4*>(dst + lane), make_float4(qs[0], qs[1], qs[2], qs[3]));
       }
     }
-    __syncthreads();
+    // release the stage: the warp's reads of it are ordered before its count,
+    // and the last warp to count it, ordered after all counts, refills it
+    __syncwarp();
+    uint32_t last = 0;
+    if (lane == 0) {
+      __threadfence_block();
+      last = atomicAdd(&released[st], 1u) == (uint32_t)(nwarps - 1);
+      if (last) {
+        released[st] = 0;
+        __threadfence_block();
+      }
+    }
+    last = __shfl_sync(0xffffffffu, last, 0);
+    if (last && ok && u + K < nb)
+      stage_batch_warp(st, nb - 1 - (u + K), batch, start, n, view, n_pad, vals, rec, buf, s_idx, full);
   }
 }
 
@@ -1082,7 +1150,7 @@ void launch_bwd_kernels(const gs_params* x, const gs_camera* cams, const gs_proj
                         float* grad, float* hz, float* loss_out, float* cot, int32_t* status, cudaStream_t st) {
   const TileGrid g = tile_grid(fr);
   const int nthr = fr.tile_w * fr.tile_h / kPixPerThread, batch = bwd_batch(fr, nthr);
-  const size_t smem = 16 + (size_t)batch * (2 * sizeof(Rec) + 3 * sizeof(uint32_t));
+  const size_t smem = bwd_smem_bytes(batch);
   const bool cb = fr.batch != 0;
   auto* kern = cb ? raster_bwd_kernel<NU, GRAD, true> : raster_bwd_kernel<NU, GRAD, false>;
   static size_t attr[2] = {0, 0};
