@@ -519,10 +519,10 @@ def raster_bwd_flops_per_unit() -> int:
 # (profiles/raster_bwd_traffic_1M_8x1080p_nu2.md), valid while the kernel
 # sources are the ones captured (their SHA-256 below); otherwise null.
 RASTER_BWD_TRAFFIC = {
-    "bytes": 1495004672 + 197197824 + 1212876544 + 447431936,
+    "bytes": 2279968768 + 389579264 + 1132157696 + 433244928,
     "sources": {
-        "paper_2602_00395_gb300/csrc/raster.cu": "1ad12889e6f1421d2551527fea5745d8af226bdcb1da3ebf0fd6fea9889428ee",
-        "paper_2602_00395_gb300/csrc/common.cuh": "e9c7cdd51f8a9cf92e5afea66c46559ac7794416c807fd793a7a7c70ceee2c23",
+        "paper_2602_00395_gb300/csrc/raster.cu": "eb90a0c9bb4c07a24990a87a9ecccd620e6dceb039ae214b8e6b62508a2439f2",
+        "paper_2602_00395_gb300/csrc/common.cuh": "f6b0e9b6b861641997b64475b07485e6e52b5fe48da9e63867facaa5cffb4c58",
     },
 }
 
