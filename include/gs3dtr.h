@@ -338,6 +338,14 @@ gs_status gs_adam_tr_update(gs_params* x, gs_params* m, gs_params* v, const gs_p
  * training loop replayed as a CUDA graph). */
 gs_status gs_step_advance(int64_t* t_device, void* stream);
 
+/* Diagnostics (no paper counterpart): runs, in one warp, the bounded wait that
+ * every kernel uses on its asynchronous copies, on an mbarrier that nothing
+ * completes, giving up after `limit` tries (1 <= limit <= 2^20).  Raises
+ * GS_FLAG_TIMEOUT in *status (device int32) as a kernel does when a staged copy
+ * never lands; the kernel then returns and the context stays usable.  Lets
+ * the failure path be tested without a fault. */
+gs_status gs_wait_check(uint32_t limit, int32_t* status, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -25,7 +25,7 @@ EXPORTED = ("gs_last_error", "gs_version", "gs_project", "gs_bin_sort_workspace_
             "gs_bin_sort_noalloc",
             "gs_raster_fwd", "gs_raster_bwd_workspace_size", "gs_raster_bwd", "gs_hvp_diag", "gs_tr_update",
             "gs_tr_update_dev", "gs_step_advance", "gs_adam_tr_update", "gs_dssim_workspace_size",
-            "gs_dssim_cotangents")
+            "gs_dssim_cotangents", "gs_wait_check")
 
 
 class gs_params(C.Structure):
@@ -139,6 +139,8 @@ def load():
                                        C.POINTER(gs_eps_schedule), C.POINTER(gs_params), P, P]
         L.gs_step_advance.restype = st
         L.gs_step_advance.argtypes = [P, P]
+        L.gs_wait_check.restype = st
+        L.gs_wait_check.argtypes = [C.c_uint32, P, P]
         L.gs_dssim_workspace_size.restype = C.c_size_t
         L.gs_dssim_workspace_size.argtypes = [gs_frame, C.c_int32]
         L.gs_dssim_cotangents.restype = st
@@ -281,6 +283,11 @@ def gs_tr_update_dev(x: gs_params, g_ema: gs_params, d_ema: gs_params, grad: gs_
 def gs_step_advance(t_device, stream=None) -> None:
     L = load()
     check(L.gs_step_advance(ptr(t_device), stream_handle(stream)), "gs_step_advance")
+
+
+def gs_wait_check(limit: int, status, stream=None) -> None:
+    L = load()
+    check(L.gs_wait_check(limit, ptr(status), stream_handle(stream)), "gs_wait_check")
 
 
 def gs_adam_tr_update(x: gs_params, m: gs_params, v: gs_params, grad: gs_params, cfg: gs_tr_config,

@@ -62,6 +62,11 @@ def test_struct_sizes_match_header_layout(tmp_path):
 def test_host_argument_checks_reject_without_touching_the_device(lib):
     from paper_2602_00395_gb300 import gs3dtr as G
     assert lib.gs_version() >= 100
+    # the wait diagnostic checks its limit and status pointer on the host
+    assert lib.gs_wait_check(0, C.c_void_p(16), None) == G.GS_ERR_INVALID_ARG
+    assert lib.gs_wait_check((1 << 20) + 1, C.c_void_p(16), None) == G.GS_ERR_INVALID_ARG
+    assert lib.gs_wait_check(100, None, None) == G.GS_ERR_INVALID_ARG
+    assert b"gs_wait_check" in lib.gs_last_error()
     # null arguments are rejected before any launch
     rc = lib.gs_project(None, None, G.frame_struct(1, 8, 8), None, None, None, None)
     assert rc == G.GS_ERR_INVALID_ARG
