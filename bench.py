@@ -159,8 +159,9 @@ def kernel_launches_per_step(eng) -> int:
     rec_pass = 4  # 32 depth bits, per view
     pair_pass = max(1, (bits(N_VIEWS * eng.Tx * eng.Ty) + 7) // 8)
     radix = 1 + 3 + 1  # histogram, three-kernel scan, scatter
-    # record keys, record passes, count gather, three-kernel scan, emit, pair passes, ranges
-    sort = 1 + rec_pass * radix + 1 + 3 + 1 + pair_pass * radix + 1
+    # record keys, record passes, count gather, three-kernel scan, emit, pair passes, ranges,
+    # heaviest-first tile order (class counts, class starts, placement)
+    sort = 1 + rec_pass * radix + 1 + 3 + 1 + pair_pass * radix + 1 + 3
     # step counter, project, sort, fwd, reverse blend + projection reverse, update
     return 1 + 1 + sort + 1 + 2 + 1
 
