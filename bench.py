@@ -26,6 +26,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -76,7 +77,7 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.idx = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"gs3dtr_clocks_{os.getpid()}_gpu{gpu_index}.csv")
 
     def __enter__(self):
         try:
@@ -102,10 +103,15 @@ class ClockSampler:
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         rows = []
-        for line in open(self.path):
-            p = [x.strip() for x in line.split(",")]
-            if len(p) >= 9 and p[1].replace(".", "").isdigit():
-                rows.append(p)
+        with open(self.path) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) >= 9 and p[1].replace(".", "").isdigit():
+                    rows.append(p)
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
         sm = [float(r[1]) for r in rows]
@@ -517,7 +523,7 @@ def raster_bwd_flops_per_unit() -> int:
 
 # DRAM bytes of one gs_raster_bwd call on this workload (its two kernels, read
 # plus write; the workspace clear is a memset, not counted) from one ncu capture
-# (profiles/raster_bwd_traffic_1M_8x1080p_nu2.md), valid while the kernel
+# (its summary is kept under profiles/), valid while the kernel
 # sources are the ones captured (their SHA-256 below); otherwise null.
 RASTER_BWD_TRAFFIC = {
     "bytes": 2279968768 + 389579264 + 1132157696 + 433244928,
