@@ -526,9 +526,9 @@ def raster_bwd_flops_per_unit() -> int:
 # (its summary is kept under profiles/), valid while the kernel
 # sources are the ones captured (their SHA-256 below); otherwise null.
 RASTER_BWD_TRAFFIC = {
-    "bytes": 2279968768 + 389579264 + 1132157696 + 433244928,
+    "bytes": 2279314432 + 389193728 + 1132078848 + 432877056,
     "sources": {
-        "paper_2602_00395_gb300/csrc/raster.cu": "eb90a0c9bb4c07a24990a87a9ecccd620e6dceb039ae214b8e6b62508a2439f2",
+        "paper_2602_00395_gb300/csrc/raster.cu": "8c736d14d0e1081a966c2f9a5bfddffcc802b091da2ed210c8a3c7728ab54b50",
         "paper_2602_00395_gb300/csrc/common.cuh": "f6b0e9b6b861641997b64475b07485e6e52b5fe48da9e63867facaa5cffb4c58",
     },
 }
