@@ -1,0 +1,45 @@
+"""Host-side logic of bench.py that needs no GPU: the traffic figure's source
+guard, the clock-sample summary and the per-step kernel count."""
+import os
+import types
+
+import bench
+
+
+def test_traffic_is_reported_only_for_the_captured_sources(monkeypatch):
+    assert bench.raster_bwd_traffic() == bench.RASTER_BWD_TRAFFIC["bytes"]
+    changed = dict(bench.RASTER_BWD_TRAFFIC)
+    changed["sources"] = dict(changed["sources"])
+    first = next(iter(changed["sources"]))
+    changed["sources"][first] = "0" * 64
+    monkeypatch.setattr(bench, "RASTER_BWD_TRAFFIC", changed)
+    assert bench.raster_bwd_traffic() is None
+
+
+def test_clock_summary_reads_samples_and_removes_them(tmp_path):
+    c = bench.ClockSampler(0)
+    c.path = str(tmp_path / "clocks.csv")
+    rows = [
+        "0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "0, 2055, 2070, 1390.5, 0x4, Not Active, Not Active, Not Active, Active",
+        "0, 2070, 2070, 1401.0, 0x4, Not Active, Not Active, Not Active, Active",
+        "garbled line",
+    ]
+    with open(c.path, "w") as f:
+        f.write("\n".join(rows) + "\n")
+    c.proc = object()  # as if nvidia-smi had been started
+    s = c.summary()
+    assert s["sm_mhz"] == 2070.0 and s["sm_max_mhz"] == 2070.0 and s["samples"] == 3
+    assert s["reasons"] == ["sw_power_cap"]
+    assert not os.path.exists(c.path)
+    # without nvidia-smi the summary says so instead of inventing clocks
+    c2 = bench.ClockSampler(0)
+    assert c2.summary()["reasons"] == ["nvidia-smi unavailable"]
+
+
+def test_kernel_count_per_step():
+    # 1920 x 1080 in 16 x 16 tiles: 120 x 68 tiles per view, 8 views -> 16 tile
+    # bits, two 8-bit pair passes; 4 record passes
+    eng = types.SimpleNamespace(Tx=120, Ty=68)
+    # step counter 1, projection 1, sort 40, forward 1, reverse 2, update 1
+    assert bench.kernel_launches_per_step(eng) == 46
