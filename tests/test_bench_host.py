@@ -43,3 +43,24 @@ def test_kernel_count_per_step():
     eng = types.SimpleNamespace(Tx=120, Ty=68)
     # step counter 1, projection 1, sort 40, forward 1, reverse 2, update 1
     assert bench.kernel_launches_per_step(eng) == 46
+
+
+def test_reference_arm_prints_one_json_line():
+    """`bench.py --impl reference`: the oracle on the host cores, one bounded
+    sample per step, in the same JSON contract as the CUDA arm."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.abspath(bench.__file__))
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "0"], capture_output=True, text=True, timeout=600, cwd=root)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
+    assert d["value"] > 0 and d["higher_is_better"] is True and d["steps"] == 1 and d["warmup"] == 0
+    assert d["config"]["workload"] == bench.WORKLOAD
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
