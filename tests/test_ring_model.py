@@ -81,7 +81,7 @@ def run_ring(n_warps, K, nb, seed, refill_by_first=False):
     assert fills == nb
 
 
-@pytest.mark.parametrize("n_warps,K", [(4, 2), (4, 3), (2, 2), (8, 4), (4, 1)])
+@pytest.mark.parametrize("n_warps,K", [(4, 2), (4, 3), (2, 2), (8, 4), (4, 1), (1, 2)])
 def test_ring_protocol_under_random_interleavings(n_warps, K):
     for seed in range(200):
         for nb in (0, 1, 2, 3, 5, 9):
