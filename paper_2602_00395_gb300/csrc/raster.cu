@@ -229,9 +229,16 @@ __global__ void GS_FWD_BOUNDS raster_fwd_kernel(const float4* __restrict__ rec, 
   __syncthreads();
 
   const int nb = (n + batch - 1) / batch;
-  if (nb > 0) stage_batch<NU>(0, batch, start, n, view, n_pad, vals, rec, tan, buf, tbuf, nullptr, bars);
+  int issued = 0;  // batches staged so far (block-uniform)
+  if (nb > 0) {
+    stage_batch<NU>(0, batch, start, n, view, n_pad, vals, rec, tan, buf, tbuf, nullptr, bars);
+    issued = 1;
+  }
   for (int b = 0; b < nb; ++b) {
-    if (b + 1 < nb) stage_batch<NU>(b + 1, batch, start, n, view, n_pad, vals, rec, tan, buf, tbuf, nullptr, bars);
+    if (b + 1 < nb) {
+      stage_batch<NU>(b + 1, batch, start, n, view, n_pad, vals, rec, tan, buf, tbuf, nullptr, bars);
+      issued = b + 2;
+    }
     const int bi = b & 1;
     const bool ok = mbar_wait_bounded(&bars[bi], (uint32_t)((b >> 1) & 1), status);
     const int cnt = min(batch, n - b * batch);
@@ -270,9 +277,19 @@ __global__ void GS_FWD_BOUNDS raster_fwd_kernel(const float4* __restrict__ rec, 
         for (int q = 0; q < kPixPerThread; ++q) fwd_blend<NU>(pix[q], r, t0, batch, pos);
       }
     }
-    if (__syncthreads_count(pix[0].done && pix[1].done) == nthr) {
-      if (b + 1 < nb) mbar_wait_bounded(&bars[(b + 1) & 1], (uint32_t)(((b + 1) >> 1) & 1), status);
-      break;
+    if (__syncthreads_count(pix[0].done && pix[1].done) == nthr) break;
+  }
+  // Drain: a buffer is refilled only after a barrier that follows every
+  // thread's wait on its previous fill, and only when some wait saw that fill
+  // land, so each buffer has at most one fill in flight, its last.  Thread 0
+  // waits (bounded) for the last fill of both buffers, so that no bulk copy is
+  // still writing into this block's shared memory when it exits: the batch
+  // staged ahead of an early finish, or a fill whose waits ran out.
+  if (tid == 0) {
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      const int last = issued - 1 - (((issued - 1) ^ s) & 1);  // largest batch < issued in buffer s
+      if (last >= 0) mbar_wait_bounded(&bars[s], (uint32_t)((last >> 1) & 1), status);
     }
   }
   const size_t HW = (size_t)fr.width * fr.height;
@@ -310,15 +327,16 @@ __host__ __device__ constexpr size_t bwd_smem_bytes(int batch) {
   return kBwdRingHdr + (size_t)kBwdStages * batch * (sizeof(Rec) + sizeof(uint32_t));
 }
 
-// The calling warp fills ring stage s with batch b of the list: its lanes store
-// the Gaussian indices and issue one bulk copy per record, then lane 0 arms the
-// stage's barrier with the byte count.  The copies may complete before that
-// arrival (the phase cannot complete while the arrival is pending), and the
-// arrival releases the index stores to the warps that wait on the phase.
-__device__ __forceinline__ void stage_batch_warp(int s, int b, int batch, uint32_t start, int n, int view,
+// The calling warp fills ring stage s with batch b of the list (use u of the
+// ring): its lanes store the Gaussian indices and issue one bulk copy per
+// record, then lane 0 records u as the stage's last fill and arms the stage's
+// barrier with the byte count.  The copies may complete before that arrival (the
+// phase cannot complete while the arrival is pending), and the arrival releases
+// the index stores to the warps that wait on the phase.
+__device__ __forceinline__ void stage_batch_warp(int s, int u, int b, int batch, uint32_t start, int n, int view,
                                                  int n_pad, const uint32_t* __restrict__ vals,
                                                  const float4* __restrict__ rec, Rec* buf, uint32_t* s_idx,
-                                                 uint64_t* full) {
+                                                 uint64_t* full, int* fill_use) {
   const int lane = threadIdx.x & 31;
   const int cnt = min(batch, n - b * batch);
   __syncwarp();
@@ -329,7 +347,10 @@ __device__ __forceinline__ void stage_batch_warp(int s, int b, int batch, uint32
     bulk_g2s(&buf[s * batch + q], rec + 3 * ((size_t)view * n_pad + gi), sizeof(Rec), &full[s]);
   }
   __syncwarp();
-  if (lane == 0) mbar_arrive_expect_tx(&full[s], (uint32_t)(cnt * (int)sizeof(Rec)));
+  if (lane == 0) {
+    fill_use[s] = u;
+    mbar_arrive_expect_tx(&full[s], (uint32_t)(cnt * (int)sizeof(Rec)));
+  }
 }
 
 // True if the splat can reach alpha >= 1/255 at some pixel centre of the 8 x 8
@@ -479,6 +500,7 @@ __global__ void GS_BWD_BOUNDS raster_bwd_kernel(
   __shared__ uint32_t s_max;
   __shared__ int s_abort;
   __shared__ float s_loss[8];
+  __shared__ int s_fill_use[kBwdStages];  // ring use of each stage's last fill (-1: none)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   // the tile of this block: the heaviest tiles first when an order is given
   const int blk = order ? (int)min(__ldg(order + blockIdx.x), gridDim.x - 1) : (int)blockIdx.x;
@@ -544,6 +566,7 @@ __global__ void GS_BWD_BOUNDS raster_bwd_kernel(
     for (int k = 0; k < K; ++k) {
       mbar_init(&full[k], 1);
       released[k] = 0;
+      s_fill_use[k] = -1;
     }
     fence_mbar_init();
   }
@@ -568,19 +591,22 @@ __global__ void GS_BWD_BOUNDS raster_bwd_kernel(
   const int nb = (n + batch - 1) / batch;
   // batch b is use u = nb - 1 - b of the ring: stage u % K, its (u / K)-th fill
   for (int u = warp; u < min(K, nb); u += nwarps)
-    stage_batch_warp(u, nb - 1 - u, batch, start, n, view, n_pad, vals, rec, buf, s_idx, full);
+    stage_batch_warp(u, u, nb - 1 - u, batch, start, n, view, n_pad, vals, rec, buf, s_idx, full, s_fill_use);
   bool ok = true;
   for (int u = 0; u < nb; ++u) {
     const int st = u % K, b = nb - 1 - u;
     // every lane waits (bounded) for the stage's phase: each acquires the copies
-    // and indices; after a wait ran out the warp waits no more
-    const bool landed = ok && mbar_wait_bounded(&full[st], (uint32_t)((u / K) & 1), status);
-    ok = __all_sync(0xffffffffu, ok && landed) != 0;
+    // and indices.  A warp whose wait ran out stops at once: it releases no
+    // further stage, so no later round completes and nothing is refilled
+    // behind it; the other warps run into their own bounded waits.
+    const bool landed = mbar_wait_bounded(&full[st], (uint32_t)((u / K) & 1), status);
+    ok = __all_sync(0xffffffffu, landed) != 0;
+    if (!ok) break;
     const int cnt = min(batch, n - b * batch);
     const Rec* bb = buf + st * batch;
     // the warp walks, back to front, only the splats its block can see and
     // that lie before its last contributor: one ballot per 32 splats
-    for (int j0 = ((cnt - 1) & ~31); ok && (uint32_t)(b * batch) < warp_nc && j0 >= 0; j0 -= 32) {
+    for (int j0 = ((cnt - 1) & ~31); (uint32_t)(b * batch) < warp_nc && j0 >= 0; j0 -= 32) {
       const int jl = j0 + lane;
       uint32_t bits =
           __ballot_sync(0xffffffffu, jl < cnt && (uint32_t)(b * batch + jl) < warp_nc && block_sees(bb[jl], wx0, wy0));
@@ -631,9 +657,17 @@ __global__ void GS_BWD_BOUNDS raster_bwd_kernel(
       }
     }
     last = __shfl_sync(0xffffffffu, last, 0);
-    if (last && ok && u + K < nb)
-      stage_batch_warp(st, nb - 1 - (u + K), batch, start, n, view, n_pad, vals, rec, buf, s_idx, full);
+    if (last && u + K < nb)
+      stage_batch_warp(st, u + K, nb - 1 - (u + K), batch, start, n, view, n_pad, vals, rec, buf, s_idx, full,
+                       s_fill_use);
   }
+  // Drain after a failed wait: a stage is refilled only by a warp that saw its
+  // previous fill land, so each stage has at most one fill in flight, its last.
+  // One thread per stage waits (bounded) for that fill, so that no bulk copy is
+  // still writing into this block's shared memory, or completing on its
+  // barrier, when the block exits.  Without a failure every fill has landed.
+  if (__syncthreads_or(!ok) && tid < K && s_fill_use[tid] >= 0)
+    mbar_wait_bounded(&full[tid], (uint32_t)((s_fill_use[tid] / K) & 1), status);
 }
 
 // ------------------------------------------------ projection reverse pass
