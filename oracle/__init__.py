@@ -56,26 +56,26 @@ def lib():
             L.or_bin_sort.restype = i64
             L.or_bin_sort.argtypes = [i32, i64, P, P, P, P, P, P, P, P, i32, i32, i32, i32, P, P, i64, P]
             L.or_render.restype = i64
-            L.or_render.argtypes = [P, i64, i64, i32, P, i32, i32, i32, P, P, P, P, P]
+            L.or_render.argtypes = [P, i64, i64, i32, P, i32, i32, i32, P, P, P, P, P, P, P, P]
             L.or_jvp.argtypes = [P, i64, i64, i32, P, i32, i32, i32, P, P]
             L.or_jacobian.argtypes = [P, i64, i64, i32, P, i32, i32, i32, P]
             L.or_backward_dssim.restype = d
             L.or_backward_dssim.argtypes = [P, i64, i64, i32, P, i32, i32, i32, P, d, d, u64, C.c_int64, i32,
-                                            P, P, P]
+                                            P, P, P, P, P]
             L.or_ssim.argtypes = [P, P, i32, i32, P, P, P, P]
             L.or_ssim_vjp.argtypes = [P, P, i32, i32, P, P]
             L.or_ssim_jvp.argtypes = [P, P, i32, i32, P, P]
             L.or_backward.restype = d
             L.or_backward.argtypes = [P, i64, i64, i32, P, i32, i32, i32, P, i32, d, u64, C.c_int64, i32,
-                                      P, P, P, P]
+                                      P, P, P, P, P, P, P]
             L.or_shd_radius.argtypes = [P, i64, i64, i32, d, P, P]
             L.or_tr_update.argtypes = [P, P, P, P, P, i64, i64, i32, P, C.c_int64, d, P]
             L.or_adam_tr_update.argtypes = [P, P, P, P, i64, i64, i32, P, P, C.c_int64, d, P]
             L.or_project_tangent.argtypes = [P, i64, i64, i32, P, P, P]
             L.or_render_pixels.argtypes = [P, i64, i64, i32, P, i32, i32, i64, P, P, u64, C.c_int64, i32, P, P, P,
-                                           P, P, P]
+                                           P, P, P, P, P, P]
             L.or_backward_sampled.argtypes = [P, i64, i64, i32, P, i32, i32, i32, P, i32, d, u64, C.c_int64, i32,
-                                              i64, P, P, P, P]
+                                              i64, P, P, P, P, d, P, P, P]
             L.or_signature.argtypes = [P, i64, i64, i32, P, i32, i32, i32, P]
             L.or_hellinger.restype = d
             L.or_hellinger.argtypes = [P, P, d, P, P, d]
@@ -223,6 +223,10 @@ def bin_sort(mx, my, radius, depth, width: int, height: int, tw: int = 16, th: i
 
 
 def render(P: np.ndarray, deg: int, cams, tw: int = 16, th: int = 16, with_margin: bool = True):
+    """Image, final T, n_contrib; with_margin adds the decision margin, the bounds
+    ``impact`` / ``t_impact`` on what FP32 flips of the blend's decisions can do to
+    each pixel's colour and final T, ``err`` on the colour's own FP32 rounding,
+    and the n_contrib range they allow."""
     P = _f64(P)
     rows, n = P.shape
     ca = camera_array(cams)
@@ -233,8 +237,13 @@ def render(P: np.ndarray, deg: int, cams, tw: int = 16, th: int = 16, with_margi
     nc = np.zeros((V, H, W), np.int32)
     mg = np.zeros((V, H, W)) if with_margin else None
     rng = np.zeros((V, H, W, 2), np.int32) if with_margin else None
-    pairs = lib().or_render(_p(P), n, n, deg, _p(ca), V, tw, th, _p(img), _p(T), _p(nc), _p(mg), _p(rng))
-    out = dict(image=img, final_T=T, n_contrib=nc, margin=mg, n_pairs=int(pairs))
+    imp = np.zeros((V, H, W)) if with_margin else None
+    timp = np.zeros((V, H, W)) if with_margin else None
+    err = np.zeros((V, H, W)) if with_margin else None
+    pairs = lib().or_render(_p(P), n, n, deg, _p(ca), V, tw, th, _p(img), _p(T), _p(nc), _p(mg), _p(rng),
+                            _p(imp), _p(timp), _p(err))
+    out = dict(image=img, final_T=T, n_contrib=nc, margin=mg, n_pairs=int(pairs), impact=imp, t_impact=timp,
+               err=err)
     if with_margin:
         out["n_contrib_lo"], out["n_contrib_hi"] = rng[..., 0], rng[..., 1]
     return out
@@ -278,9 +287,13 @@ def jacobian(P: np.ndarray, deg: int, cams, tw: int = 16, th: int = 16) -> np.nd
 
 def backward(P: np.ndarray, deg: int, cams, target: np.ndarray, *, loss_kind: int = 0,
              gn_floor: float = 1e-3, seed: int = 42, t: int = 1, nu: int = 0,
-             tw: int = 16, th: int = 16, want_tangents: bool = False, lam: float = 0.2):
+             tw: int = 16, th: int = 16, want_tangents: bool = False, lam: float = 0.2, masses: bool = False):
     """Objective, gradient (rows x n) and, if nu > 0, the Hutchinson diagonal (rows x n).
-    loss_kind 0: L1, 1: L2, 2: (1 - lam) L1 + lam D-SSIM (res_margin not computed)."""
+    loss_kind 0: L1, 1: L2, 2: (1 - lam) L1 + lam D-SSIM (res_margin not computed).
+    masses: also grad_mass / hz_mass, per entry the sum of the absolute values of
+    the terms that form it (the scale its FP32 rounding is measured against),
+    and for the L1 loss hz_sens, the bound on how far each Hutchinson entry moves
+    when each residual moves by its pixel's FP32 rounding bound."""
     P = _f64(P)
     rows, n = P.shape
     ca = camera_array(cams)
@@ -291,14 +304,18 @@ def backward(P: np.ndarray, deg: int, cams, target: np.ndarray, *, loss_kind: in
     hz = np.zeros((rows, n)) if nu > 0 else None
     it = np.zeros((nu, V, 3, H, W)) if (want_tangents and nu > 0) else None
     rm = np.zeros((V, H, W))
+    gm = np.zeros((rows, n)) if masses else None
+    hm = np.zeros((rows, n)) if (masses and nu > 0) else None
+    hs = np.zeros((rows, n)) if (masses and nu > 0 and loss_kind == 0) else None
     if loss_kind == 2:
         f = lib().or_backward_dssim(_p(P), n, n, deg, _p(ca), V, tw, th, _p(tg), lam, gn_floor, seed, t, nu,
-                                    _p(grad), _p(hz), _p(it))
+                                    _p(grad), _p(hz), _p(it), _p(gm), _p(hm))
         rm = None
     else:
         f = lib().or_backward(_p(P), n, n, deg, _p(ca), V, tw, th, _p(tg), loss_kind, gn_floor, seed, t, nu,
-                              _p(grad), _p(hz), _p(it), _p(rm))
-    return dict(loss=float(f), grad=grad, hz=hz, image_tangent=it, res_margin=rm)
+                              _p(grad), _p(hz), _p(it), _p(rm), _p(gm), _p(hm), _p(hs))
+    return dict(loss=float(f), grad=grad, hz=hz, image_tangent=it, res_margin=rm, grad_mass=gm, hz_mass=hm,
+                hz_sens=hs)
 
 
 def ssim(x: np.ndarray, y: np.ndarray):
@@ -384,15 +401,23 @@ def render_pixels(P: np.ndarray, deg: int, cam, xs, ys, *, seed: int = 42, t: in
     mg = np.zeros(k)
     jz = np.zeros((k, max(nu, 1), 3))
     rng = np.zeros((k, 2), np.int32)
+    imp = np.zeros(k)
+    timp = np.zeros(k)
+    kinds = np.zeros(k, np.int32)
     lib().or_render_pixels(_p(P), n, n, deg, _p(camera_array([cam])), tw, th, k, _p(xs), _p(ys), seed, t, nu,
-                           _p(rgb), _p(T), _p(nc), _p(mg), _p(jz), _p(rng))
+                           _p(rgb), _p(T), _p(nc), _p(mg), _p(jz), _p(rng), _p(imp), _p(timp), _p(kinds))
     return dict(rgb=rgb, final_T=T, n_contrib=nc, margin=mg, jz=jz[:, :nu], n_contrib_lo=rng[:, 0],
-                n_contrib_hi=rng[:, 1])
+                n_contrib_hi=rng[:, 1], impact=imp, t_impact=timp, flip_kinds=kinds)
 
 
 def backward_sampled(P: np.ndarray, deg: int, cams, target: np.ndarray, samples, *, loss_kind: int = 0,
-                     gn_floor: float = 1e-3, seed: int = 42, t: int = 1, nu: int = 0, tw: int = 16, th: int = 16):
-    """Gradient and Hutchinson rows of chosen Gaussians over a full frame of views, with comparability flags."""
+                     gn_floor: float = 1e-3, seed: int = 42, t: int = 1, nu: int = 0, tw: int = 16, th: int = 16,
+                     eps_img: float = 1e-5):
+    """Gradient and Hutchinson rows of chosen Gaussians over a full frame of views,
+    with comparability flags, the masses of the entries' sums (grad_mass,
+    hz_mass) and hz_sens, the largest change of each Hutchinson entry when each
+    residual moves by the FP32 rounding bound of its pixel's colour.  eps_img:
+    the residual-sign window of flag 4 (the image tolerance)."""
     P = _f64(P)
     rows, n = P.shape
     tg = _f64(target)
@@ -401,6 +426,9 @@ def backward_sampled(P: np.ndarray, deg: int, cams, target: np.ndarray, samples,
     grad = np.zeros((k, rows))
     hz = np.zeros((k, rows))
     flag = np.zeros(k, np.int32)
+    gm, hm, hs = (np.zeros((k, rows)) for _ in range(3))
     lib().or_backward_sampled(_p(P), n, n, deg, _p(camera_array(cams)), len(cams), tw, th, _p(tg), loss_kind,
-                              gn_floor, seed, t, nu, k, _p(smp), _p(grad), _p(hz if nu > 0 else None), _p(flag))
-    return dict(grad=grad, hz=hz if nu > 0 else None, flag=flag)
+                              gn_floor, seed, t, nu, k, _p(smp), _p(grad), _p(hz if nu > 0 else None), _p(flag),
+                              eps_img, _p(gm), _p(hm if nu > 0 else None), _p(hs if nu > 0 else None))
+    return dict(grad=grad, hz=hz if nu > 0 else None, flag=flag, grad_mass=gm,
+                hz_mass=hm if nu > 0 else None, hz_sens=hs if nu > 0 else None)

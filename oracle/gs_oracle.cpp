@@ -720,6 +720,172 @@ double binning_margin(const View& V, int tx, int ty, double pcx, double pcy, int
   return std::numeric_limits<double>::infinity();
 }
 
+// ------------------------------------------------ FP32 decision uncertainty
+// The CUDA path takes the blend's discrete decisions (Sec. 3.1 thresholds) on
+// FP32 splat records, which differ from the oracle's FP64 ones by rounding.  A
+// decision whose FP64 value lies closer to its threshold than that rounding can
+// move it may come out the other way there.  The model below bounds the
+// rounding: the record's mean carries a few ulps of its pixel coordinates
+// (camera transform, perspective division and principal point, each rounded in
+// FP32), its conic a few ulps relative to its entries, amplified by 1/(1 - rho^2)
+// when the inversion cancels (rho the conic's correlation), and exp and the
+// opacity a few ulps.  Returns the bound on |power_FP32 - power_FP64| at offset
+// (dx, dy) from the mean.
+double power_uncertainty(const Splat<double>& g, double dx, double dy) {
+  const double ulp = std::ldexp(1.0, -24);
+  const double dpos = 4.0 * ulp * (std::fabs(g.mx) + std::fabs(g.my)) + 1e-6;  // pixels
+  const double rho2 = std::min(g.B * g.B / std::max(g.A * g.C, 1e-300), 0.999999);
+  const double dconic = 32.0 * ulp / (1.0 - rho2);                               // relative
+  const double gx = std::fabs(g.A * dx + g.B * dy), gy = std::fabs(g.B * dx + g.C * dy);
+  const double q = 0.5 * (std::fabs(g.A) * dx * dx + std::fabs(g.C) * dy * dy) + std::fabs(g.B * dx * dy);
+  return (gx + gy) * dpos + q * dconic + 1e-6;
+}
+
+// Where FP32 may flip the blend's decisions at one pixel, and what that can do.
+//   impact    bound on |C_FP32 - C_FP64| from decisions that may flip (per
+//             channel, the largest): dropping or adding a splat k moves the
+//             colour by at most a_k T_k (c_k + c_max) (its own term plus the
+//             (1 - a_k) it puts on everything behind it, whose colours sum to at
+//             most T_k c_max); an earlier or later termination at k moves it by
+//             at most T_k c_max; swapping two splats of nearly equal depth by
+//             T a_i a_j c_max.
+//   t_impact  the same bound for the final transmittance.
+//   nc_lo, nc_hi  the n_contrib values those flips allow.
+//   err       bound on the rounding of the colour itself with every decision
+//             as here: sum over blended splats of c_k a_k T_k times the relative
+//             rounding of a_k (from power_uncertainty) and of T_k (accumulated).
+// Decisions whose FP64 value is farther from the threshold than the rounding
+// bound (power_uncertainty, and for the termination test the transmittance's
+// own accumulated rounding plus the changes upstream flips make to it) are
+// firm.  `maybe` lists splats whose membership in the tile's list may differ
+// (see build_view); those in the list may be missing on the GPU, the others
+// may be present there.
+struct Flip {
+  double impact = 0.0, t_impact = 0.0, err = 0.0;
+  int nc_lo = 0, nc_hi = 0;
+  int kinds = 0;  // flips that count: 1 skip, 2 termination, 4 list membership, 8 depth order
+};
+
+Flip blend_flips(const std::vector<int>& list, const std::vector<int>& maybe, const std::vector<Splat<double>>& sp,
+                 double pcx, double pcy, int nc) {
+  Flip f;
+  f.nc_lo = f.nc_hi = nc;
+  // the walk order: the list, with the possibly-present splats merged in by key
+  struct Entry {
+    int i;
+    bool in_list;
+    float depth;
+  };
+  std::vector<Entry> order;
+  order.reserve(list.size() + maybe.size());
+  for (int i : list) order.push_back({i, true, (float)sp[i].depth});
+  for (int i : maybe)
+    if (std::find(list.begin(), list.end(), i) == list.end()) order.push_back({i, false, (float)sp[i].depth});
+  std::stable_sort(order.begin(), order.end(), [](const Entry& a, const Entry& b) {
+    return a.depth < b.depth || (a.depth == b.depth && a.i < b.i);
+  });
+  auto cmax_of = [&](int i) { return std::max({sp[i].rgb[0], sp[i].rgb[1], sp[i].rgb[2], 0.0}); };
+  double cmax = 0.0;
+  for (const Entry& e : order) cmax = std::max(cmax, cmax_of(e.i));
+  auto is_maybe = [&](int i) { return std::find(maybe.begin(), maybe.end(), i) != maybe.end(); };
+  double T = 1.0;
+  double rho = 0.0;  // relative change of T that upstream flips can make
+  double tun = 0.0;  // relative rounding of T accumulated by the FP32 products
+  int pos = 0, firm_last = 0, maybe_before = 0;
+  std::vector<int> extra_at;  // list positions at which possibly-present splats sort
+  double prev_depth = -1.0, prev_a = 0.0;
+  int prev_i = -1;
+  bool prev_blended = false;
+  for (const Entry& e : order) {
+    const Splat<double>& g = sp[e.i];
+    const double dx = g.mx - pcx, dy = g.my - pcy;
+    const double power = -0.5 * (g.A * dx * dx + g.C * dy * dy) - g.B * dx * dy;
+    const double dp = power_uncertainty(g, dx, dy);
+    const double oG = g.o * std::exp(std::min(power, 0.0));
+    const bool capped = oG > kAlphaMax;
+    const double a = capped ? kAlphaMax : oG;
+    const bool blends = power <= 0.0 && a >= kAlphaMin;
+    const bool near = std::fabs(power) <= dp || (!capped && std::fabs(a / kAlphaMin - 1.0) <= dp + 2e-6);
+    const double drop = a * T * (cmax_of(e.i) + cmax);  // colour bound of adding or dropping it
+    if (!e.in_list) {
+      // may be listed on the GPU: an extra splat wherever it would blend
+      if (blends || near) {
+        f.kinds |= 4;
+        f.impact += drop;
+        f.t_impact += a * T;
+        rho += a / (1.0 - a);
+      }
+      extra_at.push_back(pos);
+      continue;
+    }
+    const int k = pos++;
+    if (k < nc && is_maybe(e.i)) ++maybe_before;  // may be missing on the GPU: later positions move up
+    if (!blends) {
+      if (near) {  // skipped here, may blend on the GPU
+        f.kinds |= 1;
+        f.impact += drop;
+        f.t_impact += a * T;
+        rho += a / (1.0 - a);
+        f.nc_hi = std::max(f.nc_hi, k + 1);
+      }
+      continue;
+    }
+    // blended here; the termination test first
+    const double Tn = T * (1.0 - a);
+    const double da = capped ? 0.0 : (dp + 2e-6) * a / (1.0 - a);
+    const bool near_term = std::fabs(Tn / kTMin - 1.0) <= tun + rho + da + 1e-6;
+    if (Tn < kTMin) {
+      if (near_term) {  // the GPU may go on past this point
+        f.kinds |= 2;
+        f.impact += T * cmax;
+        f.t_impact += T;
+        f.nc_hi = (int)list.size();
+      }
+      break;
+    }
+    if (near_term) {  // the GPU may stop here
+      f.kinds |= 2;
+      f.impact += T * cmax;
+      f.t_impact += T;
+      f.nc_lo = std::min(f.nc_lo, firm_last);
+    }
+    const bool amb = is_maybe(e.i);
+    if (near || amb) {
+      f.kinds |= near ? 1 : 4;
+      f.impact += drop;
+      f.t_impact += a * T;
+      rho += a / (1.0 - a);
+    } else {
+      firm_last = k + 1;
+    }
+    // two consecutive blended splats whose FP32 depths (a few ulps apart on the
+    // two sides) may sort the other way: the swap moves the colour by
+    // T a_i a_j (c_i - c_j), T the transmittance in front of the pair
+    if (prev_blended && std::fabs((double)e.depth - prev_depth) <= 4.0 * std::ldexp(std::fabs(prev_depth), -23)) {
+      double dc = 0.0;
+      for (int ch = 0; ch < 3; ++ch) dc = std::max(dc, std::fabs(g.rgb[ch] - sp[prev_i].rgb[ch]));
+      f.kinds |= 8;
+      f.impact += T / (1.0 - prev_a) * prev_a * a * dc;
+    }
+    prev_blended = true;
+    prev_depth = e.depth;
+    prev_a = a;
+    prev_i = e.i;
+    f.err += cmax_of(e.i) * a * T * ((capped ? 0.0 : dp + 2e-6) + tun + 2e-7);
+    tun += (capped ? 0.0 : (dp + 2e-6) * a / (1.0 - a)) + 2e-7;
+    T = Tn;
+  }
+  f.nc_lo = std::min(f.nc_lo, firm_last) - maybe_before;
+  int extra_before = 0;  // possibly-present splats in front of the last possible contributor
+  for (int at : extra_at) extra_before += at < f.nc_hi;
+  f.nc_hi += extra_before;
+  return f;
+}
+
+// The tolerance the CUDA path's images are held to (max-abs): residuals of the
+// two sides differ by at most this where the images are compared.
+const double kImageTol = 1e-5;
+
 // Calls f(tx, ty, x, y) for every pixel of the view, tile by tile.
 template <class F>
 void for_each_pixel(const View& V, F f) {
@@ -898,6 +1064,38 @@ void blend_reverse(const std::vector<Contrib>& tr, const std::vector<Splat<doubl
   }
 }
 
+// The magnitudes of the terms blend_reverse adds, with |w| in place of w: for
+// every splat of the trace and every q, the absolute value of its per-pixel
+// term, where dC/da's two parts (c T and the suffix over 1 - a) count by their
+// absolute values.  Summed over pixels this is the mass that an FP32 sum of the
+// same terms rounds against (the terms' own rounding scales with it too).
+void blend_reverse_abs(const std::vector<Contrib>& tr, const std::vector<Splat<double>>& sp, const double w[3],
+                       double* cot) {
+  std::vector<double> suffix(3 * (tr.size() + 1), 0.0);
+  for (long k = (long)tr.size() - 1; k >= 0; --k)
+    for (int ch = 0; ch < 3; ++ch)
+      suffix[3 * k + ch] = suffix[3 * (k + 1) + ch] + std::fabs(sp[tr[k].i].rgb[ch]) * tr[k].alpha * tr[k].T;
+  for (size_t k = 0; k < tr.size(); ++k) {
+    const Contrib& e = tr[k];
+    const Splat<double>& g = sp[e.i];
+    double ga = 0.0;
+    for (int ch = 0; ch < 3; ++ch)
+      ga += std::fabs(w[ch]) * (std::fabs(g.rgb[ch]) * e.T + suffix[3 * (k + 1) + ch] / (1.0 - e.alpha));
+    double* c = cot + (long)e.i * NQ;
+    c[Q_R] += std::fabs(w[0]) * e.alpha * e.T;
+    c[Q_G] += std::fabs(w[1]) * e.alpha * e.T;
+    c[Q_BL] += std::fabs(w[2]) * e.alpha * e.T;
+    if (e.capped) continue;
+    double gpow = ga * e.alpha;
+    c[Q_O] += ga * e.G;
+    c[Q_A] += 0.5 * e.dx * e.dx * gpow;
+    c[Q_B] += std::fabs(e.dx * e.dy) * gpow;
+    c[Q_C] += 0.5 * e.dy * e.dy * gpow;
+    c[Q_MX] += (std::fabs(g.A * e.dx) + std::fabs(g.B * e.dy)) * gpow;
+    c[Q_MY] += (std::fabs(g.C * e.dy) + std::fabs(g.B * e.dx)) * gpow;
+  }
+}
+
 // Parameter cotangent of splat i: sum_q cot_q d(splat_q)/d(param_r), with the
 // projection Jacobian taken column by column in forward mode.
 void project_reverse(const double* P, long pitch, long i, int deg, const Cam& cam, const double* cot,
@@ -913,6 +1111,24 @@ void project_reverse(const double* P, long pitch, long i, int deg, const Cam& ca
     const double col[NQ] = {s.mx.d, s.my.d, s.A.d, s.B.d, s.C.d, s.o.d, s.rgb[0].d, s.rgb[1].d, s.rgb[2].d};
     double acc = 0.0;
     for (int q = 0; q < NQ; ++q) acc += cot[q] * col[q];
+    gout[r] += acc;
+  }
+}
+
+// sum_q |cot_q| |d(splat_q)/d(param_r)|: the mass of project_reverse's sums.
+void project_reverse_abs(const double* P, long pitch, long i, int deg, const Cam& cam, const double* cot,
+                         std::vector<double>& gout /* rows values, added */) {
+  int rows = n_rows(deg);
+  std::vector<double> tan(rows, 0.0);
+  for (int r = 0; r < rows; ++r) {
+    std::fill(tan.begin(), tan.end(), 0.0);
+    tan[r] = 1.0;
+    G3<Dual> g = load_gaussian<Dual>(P, pitch, i, deg, tan.data());
+    Splat<Dual> s = project(g, cam);
+    if (!s.valid) continue;
+    const double col[NQ] = {s.mx.d, s.my.d, s.A.d, s.B.d, s.C.d, s.o.d, s.rgb[0].d, s.rgb[1].d, s.rgb[2].d};
+    double acc = 0.0;
+    for (int q = 0; q < NQ; ++q) acc += std::fabs(cot[q]) * std::fabs(col[q]);
     gout[r] += acc;
   }
 }
@@ -1203,11 +1419,14 @@ long or_bin_sort(int n_views, long n, const float* mx, const float* my, const fl
 // Render every view.  image: V x 3 x H x W, final_T and margin: V x H x W,
 // n_contrib: V x H x W.  margin is the smallest relative distance of a threshold
 // decision at the pixel, or 0 where binning is within rounding of a boundary.
-// nc_range (V x H x W x 2, may be null): the range of n_contrib that the tile
-// sets within rounding give (see binning_margin).  Returns the total number of
-// (tile, splat) pairs.
+// impact, t_impact, err (V x H x W, may be null): the bounds of blend_flips on
+// what FP32 decision flips can do to the colour and the final T, and on the
+// colour's own rounding; nc_range (V x H x W x 2, may be null): the n_contrib
+// values those flips and the tile sets within rounding allow.  Returns the
+// total number of (tile, splat) pairs.
 long or_render(const double* P, long pitch, long n, int deg, const double* cams, int n_views, int tw, int th,
-               double* image, double* final_T, int32_t* n_contrib, double* margin, int32_t* nc_range) {
+               double* image, double* final_T, int32_t* n_contrib, double* margin, int32_t* nc_range,
+               double* impact, double* t_impact, double* err) {
   long pairs = 0;
   for (int v = 0; v < n_views; ++v) {
     View V = build_view(P, pitch, n, deg, cams + 24 * v, tw, th);
@@ -1225,6 +1444,15 @@ long or_render(const double* P, long pitch, long n, int deg, const double* cams,
       int lo = nc, hi = nc;
       if (margin)
         margin[v * HW + px] = std::min(mg, binning_margin(V, tx, ty, x + 0.5, y + 0.5, nc, &lo, &hi));
+      if (impact || nc_range || err) {
+        const size_t tile = (size_t)ty * V.Tx + tx;
+        const Flip fl = blend_flips(V.lists[tile], V.amb[tile], V.sp, x + 0.5, y + 0.5, nc);
+        if (impact) impact[v * HW + px] = fl.impact;
+        if (t_impact) t_impact[v * HW + px] = fl.t_impact;
+        if (err) err[v * HW + px] = fl.err;
+        lo = fl.nc_lo;
+        hi = fl.nc_hi;
+      }
       if (nc_range) {
         nc_range[2 * (v * HW + px)] = lo;
         nc_range[2 * (v * HW + px) + 1] = hi;
@@ -1300,9 +1528,16 @@ void or_jacobian(const double* P, long pitch, long n, int deg, const double* cam
 //     ((1 - lambda) sign(r) - lambda sum_p dS_p/dC), and the Gauss-Newton
 //     vector of probe k is (1 - lambda)/(4 max(|r|, gn_floor))/m . J z_k plus
 //     the adjoint of S applied to lambda/(4 max(1 - S, gn_floor))/m . dS[J z_k].
+// grad_mass, hz_mass (rows x n, may be null): per entry, the mass of the sum
+// that forms it (blend_reverse_abs over every pixel, then project_reverse_abs),
+// the scale an FP32 evaluation of the same sums rounds against.  hz_sens (rows
+// x n, may be null; L1 only): the bound of or_backward_sampled on how far the
+// Hutchinson entries move when each residual moves by its pixel's FP32 rounding
+// bound or by the image tolerance kImageTol, whichever is smaller.
 double backward_impl(const double* P, long pitch, long n, int deg, const double* cams, int n_views, int tw,
                      int th, const double* target, int loss_kind, double lambda, double gn_floor, uint64_t seed,
-                     int64_t t, int nu, double* grad, double* hz, double* img_tan, double* res_margin) {
+                     int64_t t, int nu, double* grad, double* hz, double* img_tan, double* res_margin,
+                     double* grad_mass, double* hz_mass, double* hz_sens = nullptr) {
   int rows = n_rows(deg);
   double m = 0.0;
   std::vector<View> views;
@@ -1312,6 +1547,11 @@ double backward_impl(const double* P, long pitch, long n, int deg, const double*
   }
   for (long k = 0; k < (long)rows * n; ++k) grad[k] = 0.0;
   if (hz) for (long k = 0; k < (long)rows * n; ++k) hz[k] = 0.0;
+  const bool masses = grad_mass != nullptr;
+  if (grad_mass) for (long k = 0; k < (long)rows * n; ++k) grad_mass[k] = 0.0;
+  if (hz_mass) for (long k = 0; k < (long)rows * n; ++k) hz_mass[k] = 0.0;
+  if (hz_sens) for (long k = 0; k < (long)rows * n; ++k) hz_sens[k] = 0.0;
+  const bool sensing = hz_sens != nullptr && loss_kind == 0 && nu > 0;
 
   // probe directions z_k over the parameter vector (entry i * rows + r)
   std::vector<std::vector<double>> z(nu, std::vector<double>((size_t)rows * pitch, 0.0));
@@ -1330,6 +1570,8 @@ double backward_impl(const double* P, long pitch, long n, int deg, const double*
     const double* tg = target + img_off;
     // streams: 0 = gradient, 1..nu = Gauss-Newton products
     std::vector<std::vector<double>> cot(1 + nu, std::vector<double>((size_t)n * NQ, 0.0));
+    std::vector<std::vector<double>> cot_abs(masses ? 1 + nu : 0, std::vector<double>((size_t)n * NQ, 0.0));
+    std::vector<std::vector<double>> cot_sens(sensing ? nu : 0, std::vector<double>((size_t)n * NQ, 0.0));
     std::vector<std::vector<double>> jz(nu, std::vector<double>(3 * HW, 0.0));
     for (int k = 0; k < nu; ++k) {
       std::vector<Splat<Dual>> sd = project_tangent(V, P, pitch, n, deg, z[k].data());
@@ -1398,11 +1640,28 @@ double backward_impl(const double* P, long pitch, long n, int deg, const double*
       }
       if (res_margin) res_margin[v * HW + px] = rmin;
       blend_reverse(tr, V.sp, w, cot[0].data());
+      if (masses) blend_reverse_abs(tr, V.sp, w, cot_abs[0].data());
+      double sens[3] = {0.0, 0.0, 0.0};
+      if (sensing) {
+        const size_t tile = (size_t)ty * V.Tx + tx;
+        const double e_px =
+            std::min(blend_flips(V.lists[tile], V.amb[tile], V.sp, x + 0.5, y + 0.5, nc).err, kImageTol);
+        for (int ch = 0; ch < 3; ++ch) {
+          const double r = std::fabs(C[ch] - tg[ch * HW + px]);
+          sens[ch] = r + e_px > gn_floor ? e_px / std::max(r, gn_floor) : 0.0;
+        }
+      }
       for (int k = 0; k < nu; ++k) {
         double wk[3];
         for (int ch = 0; ch < 3; ++ch)
           wk[ch] = loss_kind == 2 ? cu[((size_t)k * 3 + ch) * HW + px] : wgn[ch] * jz[k][ch * HW + px];
         blend_reverse(tr, V.sp, wk, cot[1 + k].data());
+        if (masses) blend_reverse_abs(tr, V.sp, wk, cot_abs[1 + k].data());
+        if (sensing) {
+          double ws[3];
+          for (int ch = 0; ch < 3; ++ch) ws[ch] = wk[ch] * sens[ch];
+          blend_reverse_abs(tr, V.sp, ws, cot_sens[k].data());
+        }
       }
     });
     for (long i = 0; i < n; ++i) {
@@ -1418,6 +1677,18 @@ double backward_impl(const double* P, long pitch, long n, int deg, const double*
           if (s == 0) grad[(long)r * n + i] += g_acc[r];
           else hz[(long)r * n + i] += z[s - 1][(size_t)r * pitch + i] * g_acc[r] / nu;
         }
+        if (sensing && s > 0) {
+          std::fill(g_acc.begin(), g_acc.end(), 0.0);
+          project_reverse_abs(P, pitch, i, deg, V.cam, cot_sens[s - 1].data() + i * NQ, g_acc);
+          for (int r = 0; r < rows; ++r) hz_sens[(long)r * n + i] += g_acc[r] / nu;
+        }
+        if (!masses || (s > 0 && !hz_mass)) continue;
+        std::fill(g_acc.begin(), g_acc.end(), 0.0);
+        project_reverse_abs(P, pitch, i, deg, V.cam, cot_abs[s].data() + i * NQ, g_acc);
+        for (int r = 0; r < rows; ++r) {
+          if (s == 0) grad_mass[(long)r * n + i] += g_acc[r];
+          else hz_mass[(long)r * n + i] += g_acc[r] / nu;
+        }
       }
     }
     img_off += 3 * HW;
@@ -1427,16 +1698,17 @@ double backward_impl(const double* P, long pitch, long n, int deg, const double*
 
 double or_backward(const double* P, long pitch, long n, int deg, const double* cams, int n_views, int tw,
                    int th, const double* target, int loss_kind, double gn_floor, uint64_t seed, int64_t t,
-                   int nu, double* grad, double* hz, double* img_tan, double* res_margin) {
+                   int nu, double* grad, double* hz, double* img_tan, double* res_margin, double* grad_mass,
+                   double* hz_mass, double* hz_sens) {
   return backward_impl(P, pitch, n, deg, cams, n_views, tw, th, target, loss_kind, 0.0, gn_floor, seed, t, nu,
-                       grad, hz, img_tan, res_margin);
+                       grad, hz, img_tan, res_margin, grad_mass, hz_mass, hz_sens);
 }
 
 double or_backward_dssim(const double* P, long pitch, long n, int deg, const double* cams, int n_views, int tw,
                          int th, const double* target, double lambda, double gn_floor, uint64_t seed, int64_t t,
-                         int nu, double* grad, double* hz, double* img_tan) {
+                         int nu, double* grad, double* hz, double* img_tan, double* grad_mass, double* hz_mass) {
   return backward_impl(P, pitch, n, deg, cams, n_views, tw, th, target, 2, lambda, gn_floor, seed, t, nu, grad, hz,
-                       img_tan, nullptr);
+                       img_tan, nullptr, grad_mass, hz_mass);
 }
 
 // SSIM map of one channel and its partials (for the pins), and the adjoint and
@@ -1578,7 +1850,8 @@ std::vector<Splat<Dual>> tile_tangents(const View& V, const std::vector<int>& li
 // nu > 0, the image tangents J z_k (npix x nu x 3) for the probes of (seed, t).
 void or_render_pixels(const double* P, long pitch, long n, int deg, const double* cam24, int tw, int th, long npix,
                       const int32_t* xs, const int32_t* ys, uint64_t seed, int64_t t, int nu, double* rgb,
-                      double* T_out, int32_t* nc_out, double* margin, double* jz, int32_t* nc_range) {
+                      double* T_out, int32_t* nc_out, double* margin, double* jz, int32_t* nc_range,
+                      double* impact, double* t_impact, int32_t* flip_kinds) {
   View V = build_view(P, pitch, n, deg, cam24, tw, th);
   std::vector<int> local;
   for (long q = 0; q < npix; ++q) {
@@ -1592,6 +1865,14 @@ void or_render_pixels(const double* P, long pitch, long n, int deg, const double
     nc_out[q] = nc;
     int lo = nc, hi = nc;
     margin[q] = std::min(mg, binning_margin(V, tx, ty, x + 0.5, y + 0.5, nc, &lo, &hi));
+    if (impact) {
+      const Flip fl = blend_flips(list, V.amb[(size_t)ty * V.Tx + tx], V.sp, x + 0.5, y + 0.5, nc);
+      impact[q] = fl.impact;
+      if (t_impact) t_impact[q] = fl.t_impact;
+      if (flip_kinds) flip_kinds[q] = fl.kinds;
+      lo = fl.nc_lo;
+      hi = fl.nc_hi;
+    }
     if (nc_range) {
       nc_range[2 * q] = lo;
       nc_range[2 * q + 1] = hi;
@@ -1615,12 +1896,23 @@ void or_render_pixels(const double* P, long pitch, long n, int deg, const double
 // tiles a Gaussian is listed in involve it.  flag[s] collects the reasons an
 // FP32 evaluation may legitimately take another discrete decision somewhere in
 // the sample's footprint: 1 its own tile set is within rounding of changing; at
-// a pixel where it is visible, 2 its own alpha / cap / power decision, 4 the
-// residual sign, 8 another splat's binning, 16 another splat's threshold decision
-// is within 1e-5 of flipping.
+// a pixel where it is visible, 2 its own alpha / cap / power decision is within
+// the FP32 rounding bound of power_uncertainty, 4 the residual sign is within
+// eps_img (the image tolerance) of flipping, 8 another splat's binning, 16
+// another splat's threshold decision is within 1e-5 of flipping.
+// grad_mass, hz_mass (ns x rows, may be null): the masses of the entries' sums
+// (as or_backward).  hz_sens (ns x rows, may be null): how far the Hutchinson
+// entries move, at most, when every residual moves by e, the FP32 rounding
+// bound of its pixel's colour (Flip::err of blend_flips) or eps_img (the
+// tolerance the images are held to), whichever is smaller: the L1 Gauss-Newton weight
+// 1/(4 max(|r|, gn_floor)) then changes by a factor within e / max(|r|,
+// gn_floor) wherever |r| + e exceeds the floor, and the bound is that relative
+// change carried through the absolute terms (blend_reverse_abs,
+// project_reverse_abs).
 void or_backward_sampled(const double* P, long pitch, long n, int deg, const double* cams, int n_views, int tw,
                          int th, const double* target, int loss_kind, double gn_floor, uint64_t seed, int64_t t,
-                         int nu, long ns, const int64_t* samples, double* grad_out, double* hz_out, int32_t* flag) {
+                         int nu, long ns, const int64_t* samples, double* grad_out, double* hz_out, int32_t* flag,
+                         double eps_img, double* grad_mass, double* hz_mass, double* hz_sens) {
   int rows = n_rows(deg);
   double m = 0.0;
   for (int v = 0; v < n_views; ++v) {
@@ -1630,7 +1922,11 @@ void or_backward_sampled(const double* P, long pitch, long n, int deg, const dou
   for (long k = 0; k < ns * rows; ++k) {
     grad_out[k] = 0.0;
     if (hz_out) hz_out[k] = 0.0;
+    if (grad_mass) grad_mass[k] = 0.0;
+    if (hz_mass) hz_mass[k] = 0.0;
+    if (hz_sens) hz_sens[k] = 0.0;
   }
+  const bool masses = grad_mass || hz_mass || hz_sens;
   for (long sidx = 0; sidx < ns; ++sidx) flag[sidx] = 0;
   long img_off = 0;
   std::vector<double> g_acc(rows);
@@ -1650,6 +1946,8 @@ void or_backward_sampled(const double* P, long pitch, long n, int deg, const dou
         for (int tx = h[0]; tx < h[1]; ++tx) need[(size_t)ty * V.Tx + tx] = 1;
     }
     std::vector<std::vector<double>> cot(1 + nu, std::vector<double>((size_t)n * NQ, 0.0));
+    // masses: 0 the gradient, 1..nu the probes, nu+1..2nu the probes' sensitivity
+    std::vector<std::vector<double>> cab(masses ? 1 + 2 * nu : 0, std::vector<double>((size_t)n * NQ, 0.0));
     std::vector<int> local;
     for (int ty = 0; ty < V.Ty; ++ty)
       for (int tx = 0; tx < V.Tx; ++tx) {
@@ -1666,16 +1964,22 @@ void or_backward_sampled(const double* P, long pitch, long n, int deg, const dou
             std::vector<Contrib> tr;
             blend(list, V.sp, x + 0.5, y + 0.5, C, T, nc, &mg, &tr);
             long px = (long)y * V.cam.W + x;
-            double w[3], wgn[3], rmin = kInf;
+            double w[3], wgn[3], sens[3], rmin = kInf;
+            const double e_px =
+                masses ? std::min(blend_flips(list, V.amb[(size_t)ty * V.Tx + tx], V.sp, x + 0.5, y + 0.5, nc).err,
+                                  eps_img)
+                       : 0.0;
             for (int ch = 0; ch < 3; ++ch) {
               double r = C[ch] - tg[ch * HW + px];
               rmin = std::min(rmin, std::fabs(r));
               if (loss_kind == 0) {
                 w[ch] = (r > 0 ? 1.0 : (r < 0 ? -1.0 : 0.0)) / (2.0 * m);
                 wgn[ch] = 1.0 / (4.0 * std::max(std::fabs(r), gn_floor)) / m;
+                sens[ch] = std::fabs(r) + e_px > gn_floor ? e_px / std::max(std::fabs(r), gn_floor) : 0.0;
               } else {
                 w[ch] = r / m;
                 wgn[ch] = 1.0 / m;
+                sens[ch] = 0.0;
               }
             }
             const double mb = binning_margin(V, tx, ty, x + 0.5, y + 0.5);
@@ -1689,21 +1993,30 @@ void or_backward_sampled(const double* P, long pitch, long n, int deg, const dou
               double power = -0.5 * (g.A * dx * dx + g.C * dy * dy) - g.B * dx * dy;
               double oG = g.o * std::exp(power);
               if (oG < 0.5 * kAlphaMin) continue;
-              double own = std::min({std::fabs(std::min(oG, kAlphaMax) - kAlphaMin) / kAlphaMin,
-                                     std::fabs(oG - kAlphaMax) / kAlphaMax, std::fabs(power) * 1e6});
-              if (own < 1e-5) flag[sidx] |= 2;
-              if (rmin < 1e-5) flag[sidx] |= 4;
+              const double dp = power_uncertainty(g, dx, dy);
+              if (std::fabs(std::min(oG, kAlphaMax) / kAlphaMin - 1.0) <= dp + 2e-6 ||
+                  std::fabs(oG / kAlphaMax - 1.0) <= dp + 2e-6 || std::fabs(power) <= dp)
+                flag[sidx] |= 2;
+              if (rmin < eps_img) flag[sidx] |= 4;
               if (mb < 1e-5) flag[sidx] |= 8;
               if (mg < 1e-5) flag[sidx] |= 16;
             }
             blend_reverse(tr, V.sp, w, cot[0].data());
+            if (masses) blend_reverse_abs(tr, V.sp, w, cab[0].data());
             for (int k = 0; k < nu; ++k) {
               Dual Cd[3], Td;
               int ncd;
               blend(local, sd[k], x + 0.5, y + 0.5, Cd, Td, ncd, nullptr, nullptr);
-              double wk[3];
-              for (int ch = 0; ch < 3; ++ch) wk[ch] = wgn[ch] * Cd[ch].d;
+              double wk[3], ws[3];
+              for (int ch = 0; ch < 3; ++ch) {
+                wk[ch] = wgn[ch] * Cd[ch].d;
+                ws[ch] = wk[ch] * sens[ch];
+              }
               blend_reverse(tr, V.sp, wk, cot[1 + k].data());
+              if (masses) {
+                blend_reverse_abs(tr, V.sp, wk, cab[1 + k].data());
+                blend_reverse_abs(tr, V.sp, ws, cab[1 + nu + k].data());
+              }
             }
           }
       }
@@ -1717,6 +2030,13 @@ void or_backward_sampled(const double* P, long pitch, long n, int deg, const dou
           if (st == 0) grad_out[sidx * rows + r] += g_acc[r];
           else hz_out[sidx * rows + r] += rademacher(seed, t, st - 1, probe_entry(i, r, rows)) * g_acc[r] / nu;
         }
+      }
+      for (int st = 0; masses && st <= 2 * nu; ++st) {
+        std::fill(g_acc.begin(), g_acc.end(), 0.0);
+        project_reverse_abs(P, pitch, i, deg, V.cam, cab[st].data() + i * NQ, g_acc);
+        double* out = st == 0 ? grad_mass : (st <= nu ? hz_mass : hz_sens);
+        if (!out) continue;
+        for (int r = 0; r < rows; ++r) out[sidx * rows + r] += g_acc[r] / (st == 0 ? 1.0 : nu);
       }
     }
     img_off += 3 * HW;

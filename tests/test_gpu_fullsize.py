@@ -2,15 +2,23 @@
 
 1M Gaussians (SH degree 3, 20 clusters), 8 views of 1920x1080, 16x16 tiles,
 nu = 2 probes: one projection / bin-sort / forward / reverse pass through the C
-ABI, compared with the FP64 oracle on outputs it can compute one by one:
-  * sampled pixels of every view: colour (1e-5 max-abs), final T, n_contrib
-    (within the range that tile sets within rounding allow) and the probe
-    tangents J z_k, away from pixels whose decisions are within rounding of a
-    threshold (counted);
-  * sampled Gaussians: their gradient rows (1e-4 relative to the group's largest
-    sampled entry) and Hutchinson rows (1e-3 + 1e-6/delta, see below), unless their own tile set, their
-    own threshold decision or a residual sign in their footprint is within
-    rounding of flipping (flagged and counted).
+ABI, compared with the FP64 oracle on outputs it can compute one by one.
+
+  * 256 sampled pixels of every view: colour (1e-5 max-abs), final T (1e-5),
+    n_contrib (within the range the oracle's flip analysis allows) and the probe
+    tangents J z_k (1e-4 of the largest).  A pixel is left out only where a blend
+    decision that FP32 rounding may flip could move its colour or final T by more
+    than half the tolerance (the oracle's impact bound: a_k T_k (c_k + c_max) for
+    a skip, T_k c_max for a termination, T a_i a_j |c_i - c_j| for a depth swap);
+    the excluded fraction is printed and held below 5 %.
+  * 64 sampled Gaussians: their gradient rows (1e-4 of the group's largest
+    sampled entry, and each entry within 1e-4 of the mass of the sum that forms
+    it) and Hutchinson rows (1e-3 of the group's largest, plus for each entry the
+    oracle's bound on how far it moves when each residual moves by its pixel's
+    FP32 rounding bound: the L1 Gauss-Newton weight 1/(4 max(|r|, delta)) is that
+    sensitive near the floor; the entries that needed it are counted), unless
+    their own tile set, their own threshold decision or a residual sign in their
+    footprint is within rounding of flipping (flagged and counted).
 The targets are seeded images from the generator module, never GPU output.
 """
 import numpy as np
@@ -24,6 +32,8 @@ torch = pytest.importorskip("torch")
 
 GROUPS = {"mean": slice(0, 3), "log_scale": slice(3, 6), "quat": slice(6, 10), "opacity": slice(10, 11),
           "sh": slice(11, None)}
+IMG_TOL, GRAD_TOL, HZ_TOL = 1e-5, 1e-4, 1e-3
+FLIP_MAX = 0.5 * IMG_TOL  # a pixel whose possible flips could move it by more is left out
 
 
 @pytest.fixture(scope="module")
@@ -65,25 +75,24 @@ def test_sampled_pixels_match_oracle(fullsize):
     rng = np.random.default_rng(5)
     excluded = total = 0
     for v in range(f["V"]):
-        xs = rng.integers(0, f["W"], 32)
-        ys = rng.integers(0, f["H"], 32)
+        xs = rng.integers(0, f["W"], 256)
+        ys = rng.integers(0, f["H"], 256)
         with O.footprint_bins():  # the engine's default binning
             ref = O.render_pixels(P, 3, f["cams"][v], xs, ys, seed=42, t=f["t"], nu=f["nu"])
-        ok = ref["margin"] >= 1e-5
+        ok = (ref["impact"] <= FLIP_MAX) & (ref["t_impact"] <= FLIP_MAX)
         total += len(xs)
         excluded += int((~ok).sum())
         img = f["image"][v][:, ys, xs].T
-        assert np.abs(img - ref["rgb"])[ok].max(initial=0.0) <= 1e-5
-        assert np.abs(f["final_T"][v][ys, xs] - ref["final_T"])[ok].max(initial=0.0) <= 1e-5
+        assert np.abs(img - ref["rgb"])[ok].max(initial=0.0) <= IMG_TOL
+        assert np.abs(f["final_T"][v][ys, xs] - ref["final_T"])[ok].max(initial=0.0) <= IMG_TOL
         nc = f["n_contrib"][v][ys, xs]
         assert np.all(((nc >= ref["n_contrib_lo"]) & (nc <= ref["n_contrib_hi"]))[ok])
         for k in range(f["nu"]):
             jz = f["image_tan"][k, v][:, ys, xs].T
             scale = max(np.abs(ref["jz"][:, k, :]).max(), 1e-6)
             assert np.abs(jz - ref["jz"][:, k, :])[ok].max(initial=0.0) <= 1e-4 * scale
-    # dense cluster tiles evaluate thousands of splats per pixel, so a sizeable
-    # share of pixels has some threshold decision within 1e-5 of flipping
-    assert excluded <= 0.25 * total, (excluded, total)
+    print(f"\nfull size: {excluded} of {total} sampled pixels ({excluded / total:.2%}) excluded by the flip bound")
+    assert excluded <= 0.05 * total, (excluded, total)
 
 
 def test_sampled_gaussians_match_oracle(fullsize):
@@ -91,26 +100,29 @@ def test_sampled_gaussians_match_oracle(fullsize):
     P = O.params64(f["sc"])
     visible = np.nonzero((f["radius"] > 0).sum(0) >= 4)[0]
     rng = np.random.default_rng(6)
-    smp = rng.choice(visible, 8, replace=False)
-    ref = O.backward_sampled(P, 3, f["cams"], f["target"].astype(np.float64), smp, seed=42, t=f["t"], nu=f["nu"])
+    smp = rng.choice(visible, 64, replace=False)
+    ref = O.backward_sampled(P, 3, f["cams"], f["target"].astype(np.float64), smp, seed=42, t=f["t"], nu=f["nu"],
+                             eps_img=IMG_TOL)
     # Excluded: samples whose own tile set, own threshold decision or a residual
     # sign under their footprint is within rounding of flipping.  Decisions of
     # other splats (flags 8, 16) move a sum over thousands of pixels far less
     # than the tolerance, so those samples stay in.
     keep = (ref["flag"] & 7) == 0
-    assert keep.sum() >= 4, ref["flag"]
-    g_gpu = f["grad"][:, smp].T[keep]
-    h_gpu = f["hz"][:, smp].T[keep]
-    g_ref = ref["grad"][keep]
-    h_ref = ref["hz"][keep]
-    # The L1 Gauss-Newton weight 1/(4 max(|r|, delta)) changes by |dr|/|r| when
-    # the residual moves by dr; FP32 images carry |dr| ~ 1e-6, so near the floor
-    # delta = 1e-3 the weight itself is uncertain by 1e-6/delta = 1e-3.  The
-    # Hutchinson rows are therefore held to 1e-3 + 1e-6/delta at this size (the
-    # small-scene tests hold them to 1e-3).
-    hz_tol = 1e-3 + 1e-6 / 1e-3
+    print(f"\nfull size: {int(keep.sum())} of {len(smp)} sampled Gaussians compared (flags {np.bincount(ref['flag'] & 7)})")
+    assert keep.sum() >= 48, ref["flag"]
+    g_gpu, h_gpu = f["grad"][:, smp].T[keep], f["hz"][:, smp].T[keep]
+    g_ref, h_ref = ref["grad"][keep], ref["hz"][keep]
+    g_mass, h_sens = ref["grad_mass"][keep], ref["hz_sens"][keep]
+    allowance_used = entries = 0
     for name, sl in GROUPS.items():
         gs = np.abs(g_ref[:, sl]).max()
         hs = np.abs(h_ref[:, sl]).max()
-        assert np.abs(g_gpu[:, sl] - g_ref[:, sl]).max() <= 1e-4 * gs, name
-        assert np.abs(h_gpu[:, sl] - h_ref[:, sl]).max() <= hz_tol * hs, name
+        g_err = np.abs(g_gpu[:, sl] - g_ref[:, sl])
+        assert g_err.max() <= GRAD_TOL * gs, name
+        assert np.all(g_err <= GRAD_TOL * g_mass[:, sl]), name
+        h_err = np.abs(h_gpu[:, sl] - h_ref[:, sl])
+        assert np.all(h_err <= HZ_TOL * hs + h_sens[:, sl]), name
+        allowance_used += int((h_err > HZ_TOL * hs).sum())
+        entries += h_err.size
+    print(f"full size: {allowance_used} of {entries} Hutchinson entries beyond 1e-3 of their group, "
+          f"all within the rounding allowance")

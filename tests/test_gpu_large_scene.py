@@ -6,13 +6,17 @@ The render is `autograd.render`; the L1 objective of Sec. 3.2 is formed in
 PyTorch on its output, and `loss.backward()` runs the reverse pass from the
 image gradient (recomputing each T_i from the final T: nothing per pair is kept
 between the passes).  The Gauss-Newton diagonal comes from `gn_diagonal` with
-the L1 weights 1/(4 max(|r|, delta))/m.  Compared with the FP64 oracle on what
-it computes one by one:
-  * sampled pixels: colour (1e-5), final T and n_contrib, away from pixels with a
-    decision within rounding of a threshold;
-  * sampled Gaussians: gradient rows (1e-4 of the group's largest sampled
-    entry) and Hutchinson rows (1e-3 + 1e-6/delta, as at the benchmark size),
-    unless their own decisions are within rounding of flipping.
+the L1 weights 1/(4 max(|r|, delta))/m, which the library applies to J z_k
+itself.  Compared with the FP64 oracle on what it computes one by one, with the
+readings of the benchmark-size test:
+  * 256 sampled pixels: colour and final T (1e-5), n_contrib in the range the
+    oracle's flip analysis allows, leaving out pixels where a decision FP32 may
+    flip could move the colour or final T by more than half the tolerance;
+  * 64 sampled Gaussians: gradient rows (1e-4 of the group's largest sampled
+    entry, each entry within 1e-4 of its sum's mass) and Hutchinson rows (1e-3
+    of the group's largest, plus the oracle's bound on how far an entry moves
+    when the residuals move by their FP32 rounding), unless their own decisions
+    are within rounding of flipping.
 """
 import numpy as np
 import pytest
@@ -50,7 +54,7 @@ def large():
     loss.backward()
     r = (img.detach() - tg)
     w = 1.0 / (4.0 * torch.clamp(r.abs(), min=1e-3)) / m
-    hz = gn_diagonal(e, t, w)
+    hz = gn_diagonal(params, w, e, t)
     torch.cuda.synchronize()
     peak = torch.cuda.max_memory_allocated()
     assert e.read_status() == 0
@@ -80,12 +84,13 @@ def test_sampled_pixels_match_oracle(large):
     f = large
     P = O.params64(f["sc"])
     rng = np.random.default_rng(8)
-    xs = rng.integers(0, W, 48)
-    ys = rng.integers(0, H, 48)
+    xs = rng.integers(0, W, 256)
+    ys = rng.integers(0, H, 256)
     with O.footprint_bins():  # the engine's default binning
         ref = O.render_pixels(P, DEG, f["cam"], xs, ys)
-    ok = ref["margin"] >= 1e-5
-    assert ok.sum() >= 24
+    ok = (ref["impact"] <= 5e-6) & (ref["t_impact"] <= 5e-6)
+    print(f"\nlarge scene: {int((~ok).sum())} of {len(xs)} sampled pixels excluded by the flip bound")
+    assert ok.mean() >= 0.95
     img = f["img"][:, ys, xs].T
     assert np.abs(img - ref["rgb"])[ok].max() <= 1e-5
     assert np.abs(f["final_T"][ys, xs] - ref["final_T"])[ok].max() <= 1e-5
@@ -98,15 +103,18 @@ def test_sampled_gaussians_match_oracle(large):
     P = O.params64(f["sc"])
     visible = np.nonzero(f["radius"] > 0)[0]
     rng = np.random.default_rng(9)
-    smp = rng.choice(visible, 8, replace=False)
+    smp = rng.choice(visible, 64, replace=False)
     ref = O.backward_sampled(P, DEG, [f["cam"]], f["target"].astype(np.float64), smp, seed=42, t=f["t"], nu=1)
     keep = (ref["flag"] & 7) == 0
-    assert keep.sum() >= 4, ref["flag"]
+    print(f"\nlarge scene: {int(keep.sum())} of {len(smp)} sampled Gaussians compared")
+    assert keep.sum() >= 48, ref["flag"]
     g_gpu, h_gpu = f["grad"][:, smp].T[keep], f["hz"][:, smp].T[keep]
     g_ref, h_ref = ref["grad"][keep], ref["hz"][keep]
-    hz_tol = 1e-3 + 1e-6 / 1e-3
+    g_mass, h_sens = ref["grad_mass"][keep], ref["hz_sens"][keep]
     for name, sl in GROUPS.items():
         gs = np.abs(g_ref[:, sl]).max()
         hs = np.abs(h_ref[:, sl]).max()
-        assert np.abs(g_gpu[:, sl] - g_ref[:, sl]).max() <= 1e-4 * gs, name
-        assert np.abs(h_gpu[:, sl] - h_ref[:, sl]).max() <= hz_tol * hs, name
+        g_err = np.abs(g_gpu[:, sl] - g_ref[:, sl])
+        assert g_err.max() <= 1e-4 * gs, name
+        assert np.all(g_err <= 1e-4 * g_mass[:, sl]), name
+        assert np.all(np.abs(h_gpu[:, sl] - h_ref[:, sl]) <= 1e-3 * hs + h_sens[:, sl]), name
