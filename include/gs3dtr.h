@@ -157,7 +157,7 @@ typedef struct gs_sorted {
   uint32_t* order;
 } gs_sorted;
 
-enum { GS_LOSS_L1 = 0, GS_LOSS_L2 = 1, GS_LOSS_COTANGENT = 2 };
+enum { GS_LOSS_L1 = 0, GS_LOSS_L2 = 1, GS_LOSS_COTANGENT = 2, GS_LOSS_WEIGHTED = 3 };
 
 /* Per-pixel loss of Sec. 3.2 in least-squares form f = 1/(2m) sum F^2 over the
  * m = 3 H W V residual components r = render - target:
@@ -169,7 +169,14 @@ enum { GS_LOSS_L1 = 0, GS_LOSS_L2 = 1, GS_LOSS_COTANGENT = 2 };
  *       u_k whose pull-back J^T u_k is the Gauss-Newton product G z_k (for the
  *       objective of Sec. 3.2, u_k = (1/m) sum_j grad_C F_j (grad_C F_j . J z_k)).
  *       The image is not read, loss_out is left as it is, and the probe count
- *       comes from `probe` alone (image_tangent is not read). */
+ *       comes from `probe` alone (image_tangent is not read).
+ *   GS_LOSS_WEIGHTED: a least-squares objective whose Gauss-Newton weights the
+ *       caller forms per pixel and channel: `target` holds, when the gradient is
+ *       requested, the image dL/dC first, then one weight image w (V x 3 x H x W);
+ *       the reverse pass forms u_k = w . J z_k itself from image_tangent, so that
+ *       G z_k = J^T diag(w) J z_k (Sec. 4.1; for the objective of Sec. 3.2,
+ *       w = 1/(4 max(|r|, delta))/m).  The image is not read and loss_out is left
+ *       as it is. */
 typedef struct gs_loss {
   int32_t kind;
   float gn_floor;

@@ -8,10 +8,14 @@ hands the incoming image gradient to the reverse pass as its cotangent
 T_i from the pixel's final transmittance (nothing per pair is stored), so the
 memory of a render is its records, pairs and images at any scene size.
 
-`gn_diagonal(step, t, weights)` is the Hutchinson estimate of the diagonal of
-the Gauss-Newton matrix J^T diag(weights) J of the last render (Sec. 4.1), for
-a per-pixel weight image (for the L1 objective of Sec. 3.2,
-weights = 1 / (4 max(|r|, delta)) / m).
+`gn_diagonal(params, weights, step, t)` is the Hutchinson estimate of the
+diagonal of the Gauss-Newton matrix J^T diag(weights) J at params (Sec. 4.1),
+for a per-pixel weight image (for the L1 objective of Sec. 3.2,
+weights = 1 / (4 max(|r|, delta)) / m), as a torch.autograd.Function: the
+library renders with the probe tangents J z_k and its reverse pass forms
+weights * J z_k and J^T of it itself (GS_LOSS_WEIGHTED).  The estimate enters
+the optimiser's update as a constant (Algorithm 1 does not differentiate D_t),
+so the Function's output carries no gradient.
 """
 from __future__ import annotations
 
@@ -45,15 +49,28 @@ def render(params: torch.Tensor, step: TRStep) -> torch.Tensor:
     return _Render.apply(params, step)
 
 
-def gn_diagonal(step: TRStep, t: int, weights: torch.Tensor) -> torch.Tensor:
+class _GNDiagonal(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, params: torch.Tensor, weights: torch.Tensor, step: TRStep, t: int) -> torch.Tensor:
+        if params.data_ptr() != step.x.data_ptr():
+            step.x.copy_(params.detach())
+        step.project(t, probes=True)
+        step.bin_sort()
+        step.raster_fwd(t, probes=True)
+        w = weights.detach().to(torch.float32).contiguous().view(-1)
+        step.hvp_weighted(t, w)
+        out = step.hz.clone()
+        ctx.mark_non_differentiable(out)
+        return out
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        return None, None, None, None
+
+
+def gn_diagonal(params: torch.Tensor, weights: torch.Tensor, step: TRStep, t: int) -> torch.Tensor:
     """Hutchinson estimate (step.nu probes of step t) of diag(J^T diag(w) J) at
-    step.x for the weight image w (V x 3 x H x W), from a render with the probe
-    tangents and one reverse pass of the vectors w * J z_k."""
-    step.project(t, probes=True)
-    step.bin_sort()
-    step.raster_fwd(t, probes=True)
-    nu, V, H, W = step.nu, step.V, step.H, step.W
-    jz = step.image_tan.view(nu, V, 3, H, W)
-    cot = (jz * weights.view(1, V, 3, H, W)).contiguous().view(-1)
-    step.raster_bwd_cotangent(cot, t, want_grad=False)
-    return step.hz.clone()
+    params for the weight image w (V x 3 x H x W): one render with the probe
+    tangents and one reverse pass that weights and pulls back J z_k, both in the
+    library.  step's records, pairs, images and hz are overwritten."""
+    return _GNDiagonal.apply(params, weights, step, t)

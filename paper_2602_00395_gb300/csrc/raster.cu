@@ -363,6 +363,13 @@ __device__ __forceinline__ bool block_sees(const Rec& r, float x0, float y0) {
   return r.a.x + hx >= x0 && r.a.x - hx <= x0 + 7.f && r.a.y + hy >= y0 && r.a.y - hy <= y0 + 7.f;
 }
 
+// A splat that at most this many lanes of a warp blend is added by those lanes
+// one by one (each its own row of partial derivatives, as float4 atomics)
+// instead of through the warp-wide reduction (0: always reduce).
+#ifndef GS_BWD_SPARSE_LANES
+#define GS_BWD_SPARSE_LANES 8
+#endif
+constexpr int kBwdSparseLanes = GS_BWD_SPARSE_LANES;
 // Minimum resident CTAs per SM requested from the compiler for the reverse
 // kernel (0: no request).
 #ifndef GS_BWD_MIN_BLOCKS
@@ -540,6 +547,18 @@ __global__ void GS_BWD_BOUNDS raster_bwd_kernel(
         for (int ch = 0; ch < 3; ++ch) p.w[st][ch] = target[(((size_t)st * fr.n_views + view) * 3 + ch) * HW + at0];
       continue;
     }
+    if (loss_kind == GS_LOSS_WEIGHTED) {  // dL/dC (gradient stream), then the weights of w . J z_k
+      const float* wimg = target + (GRAD ? (size_t)fr.n_views * 3 * HW : 0);
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) {
+        if constexpr (GRAD) p.w[0][ch] = target[((size_t)view * 3 + ch) * HW + at0];
+        const float wv = wimg[((size_t)view * 3 + ch) * HW + at0];
+#pragma unroll
+        for (int k = 0; k < NU; ++k)
+          p.w[(GRAD ? 1 : 0) + k][ch] = wv * image_tan[(((size_t)k * fr.n_views + view) * 3 + ch) * HW + at0];
+      }
+      continue;
+    }
 #pragma unroll
     for (int ch = 0; ch < 3; ++ch) {
       const size_t at = ((size_t)view * 3 + ch) * HW + at0;
@@ -629,7 +648,8 @@ __global__ void GS_BWD_BOUNDS raster_bwd_kernel(
           on[q] = pos < pix[q].nc && power <= 0.f && alpha[q] >= kAlphaMin;
           if (!on[q]) G[q] = oG[q] = alpha[q] = 0.f;
         }
-        if (!__any_sync(0xffffffffu, on[0] || on[1])) continue;
+        const uint32_t act = __ballot_sync(0xffffffffu, on[0] || on[1]);  // lanes that blend the splat
+        if (!act) continue;
         float v[32];
         bwd_accumulate<S, true>(pix[0], r, dx[0], dy[0], G[0], oG[0], alpha[0], v);
         bwd_accumulate<S, false>(pix[1], r, dx[1], dy[1], G[1], oG[1], alpha[1], v);
@@ -637,6 +657,16 @@ __global__ void GS_BWD_BOUNDS raster_bwd_kernel(
         for (int q = 9 * S; q < 32; ++q) v[q] = 0.f;
         const uint32_t gi = s_idx[st * batch + j];
         float* dst = cot + ((size_t)view * n_pad + gi) * NVP;
+        if (__popc(act) <= kBwdSparseLanes) {
+          // few lanes blend the splat: each adds its own row instead of the
+          // warp-wide reduction (the other lanes' rows are zero)
+          if (on[0] || on[1]) {
+#pragma unroll
+            for (int q = 0; q < NVP; q += 4)
+              atomicAdd(reinterpret_cast<float4*>(dst + q), make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]));
+          }
+          continue;
+        }
         float qs[4];
         if constexpr (NVP <= 16) warp_reduce_quads16(v, qs);
         else warp_reduce_quads32(v, qs);
@@ -1218,10 +1248,13 @@ gs_status run_bwd(bool want_grad, const gs_params* x, const gs_camera* cams, gs_
   GS_REQUIRE(proj->rec && sorted->vals && sorted->ranges && x->data, "%s: null device buffer", name);
   GS_REQUIRE(frame_ok(frame), "%s: bad frame", name);
   GS_REQUIRE(x->n >= 0 && x->n_pad >= x->n && x->n_pad % 4 == 0, "%s: bad n/n_pad", name);
-  GS_REQUIRE(loss.kind == GS_LOSS_L1 || loss.kind == GS_LOSS_L2 || loss.kind == GS_LOSS_COTANGENT,
+  GS_REQUIRE(loss.kind == GS_LOSS_L1 || loss.kind == GS_LOSS_L2 || loss.kind == GS_LOSS_COTANGENT ||
+                 loss.kind == GS_LOSS_WEIGHTED,
              "%s: bad loss kind %d", name, loss.kind);
   const bool given = loss.kind == GS_LOSS_COTANGENT;
   const int nu = ((image_tangent || given) && probe) ? probe->nu : 0;
+  GS_REQUIRE(loss.kind != GS_LOSS_WEIGHTED || nu == 0 || image_tangent, "%s: weighted loss needs image_tangent",
+             name);
   if (nu < 0 || nu > 2 || x->sh_degree < 0 || x->sh_degree > 3) {
     set_error("%s: unsupported nu=%d sh_degree=%d", name, nu, x->sh_degree);
     return GS_ERR_UNSUPPORTED;

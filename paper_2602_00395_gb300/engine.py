@@ -85,16 +85,18 @@ class TRStep:
             self.g_ema = z(self.rows, self.n_pad)
             self.d_ema = z(self.rows, self.n_pad)
         self.grad = w(self.rows, self.n_pad)
-        self.hz = w(self.rows, self.n_pad)
+        # the curvature buffers exist only for a step with probes (nu > 0); a
+        # gradient-only step (ADAM-TR) holds x, its two moments and the gradient
+        self.hz = w(self.rows, self.n_pad) if nu > 0 else None
         self.cams = (torch.zeros if zero_init else torch.empty)(96 * n_views, dtype=torch.uint8, device=self.device)
         self.rec = w(n_views * self.n_pad * 12)
-        self.tan = w(max(nu, 1) * n_views * self.n_pad * 12)
+        self.tan = w(nu * n_views * self.n_pad * 12 if nu > 0 else 4)
         HW = width * height
         self.image = w(n_views * 3 * HW)
         self.final_T = w(n_views * HW)
         self.n_contrib = (torch.zeros if zero_init else torch.empty)(n_views * HW, dtype=torch.int32,
                                                                     device=self.device)
-        self.image_tan = w(max(nu, 1) * n_views * 3 * HW)
+        self.image_tan = w(nu * n_views * 3 * HW if nu > 0 else 4)
         self.target = w(n_views * 3 * HW)
         self.status = torch.zeros(1, dtype=torch.int32, device=self.device)
         self.loss_val = z(1)
@@ -190,6 +192,16 @@ class TRStep:
             G.gs_hvp_diag(self.P(self.x), self.cams, self.frame, self.proj(), self.sorted(), self.image, cot,
                           self.final_T, self.n_contrib, None, pr, loss, self.P(self.hz), self.bwd_ws, self.status,
                           stream)
+
+    def hvp_weighted(self, t: int, weights, stream=None) -> None:
+        """Hutchinson diagonal of J^T diag(weights) J (GS_LOSS_WEIGHTED): the
+        reverse pass forms weights * J z_k from the image tangents of the last
+        forward pass with the probes of step t; weights is V x 3 x H x W."""
+        pr = self.probe(t)
+        loss = G.gs_loss(G.GS_LOSS_WEIGHTED, self.loss.gn_floor)
+        G.gs_hvp_diag(self.P(self.x), self.cams, self.frame, self.proj(), self.sorted(), self.image, weights,
+                      self.final_T, self.n_contrib, self.image_tan, pr, loss, self.P(self.hz), self.bwd_ws,
+                      self.status, stream)
 
     def hvp_diag(self, t: int, stream=None) -> None:
         pr = self.probe(t)

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libgs3dtr.so")
 
 GS_OK, GS_ERR_INVALID_ARG, GS_ERR_CUDA, GS_ERR_UNSUPPORTED = 0, 1, 2, 3
 GS_FLAG_CAPACITY, GS_FLAG_NONFINITE, GS_FLAG_TIMEOUT = 1, 2, 4
-GS_LOSS_L1, GS_LOSS_L2, GS_LOSS_COTANGENT = 0, 1, 2
+GS_LOSS_L1, GS_LOSS_L2, GS_LOSS_COTANGENT, GS_LOSS_WEIGHTED = 0, 1, 2, 3
 
 EXPORTED = ("gs_last_error", "gs_version", "gs_project", "gs_bin_sort_workspace_size", "gs_bin_sort",
             "gs_bin_sort_noalloc",
