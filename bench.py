@@ -52,6 +52,10 @@ def parse():
     ap.add_argument("--impl", default="cuda", choices=["cuda", "reference"])
     ap.add_argument("--n", type=int, default=N_GAUSS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--oracle-full-step", action="store_true",
+                    help="time one full oracle step of the workload (nothing scaled) and exit")
+    ap.add_argument("--configs", action="store_true",
+                    help="GPU plain-loop steps/s of the smaller configurations and their oracle steps, then exit")
     ap.add_argument("--no-serve", action="store_true", help="skip the served multi-scene measurement")
     ap.add_argument("--profile-steps", type=int, default=0, help="run N untimed steps only (for ncu)")
     ap.add_argument("--profile-views", type=int, default=N_VIEWS,
@@ -188,7 +192,10 @@ def retile_workload(eng, cam_dev, targets, batches, tile, device, batch=0):
 
 
 def timed_steps(eng, cam_dev, targets, K, W0, t0, stream, per_call=False):
-    """K steps on `stream`; returns (ms total from events, per-call ms dict)."""
+    """K steps on `stream`; returns (ms total from events, per-call ms dict).
+    With per_call, each call is bracketed by its own events, and the work units
+    of those very launches are summed on the device between the calls: the dict
+    then also holds "sum_n_contrib" and "pairs", their means per step."""
     import torch
     from paper_2602_00395_gb300.engine import eps_schedule
     calls = ["project", "bin_sort", "raster_fwd", "raster_bwd", "update"]
@@ -196,6 +203,7 @@ def timed_steps(eng, cam_dev, targets, K, W0, t0, stream, per_call=False):
     start = torch.cuda.Event(enable_timing=True)
     stop = torch.cuda.Event(enable_timing=True)
     nb = len(targets)
+    units = torch.zeros(2, dtype=torch.float64, device=eng.device)  # sum n_contrib, pairs
     with torch.cuda.stream(stream):
         start.record(stream)
         for k in range(K):
@@ -218,12 +226,17 @@ def timed_steps(eng, cam_dev, targets, K, W0, t0, stream, per_call=False):
                     fn()
                     z.record(stream)
                     ev[name].append((a, z))
+                    if name == "raster_fwd":  # outside the calls' event brackets
+                        units[0] += eng.n_contrib.sum(dtype=torch.float64)
+                        units[1] += eng.n_pairs.to(torch.float64).sum()
                 else:
                     fn()
         stop.record(stream)
     stop.synchronize()
     total = start.elapsed_time(stop)
     per = {c: (sum(a.elapsed_time(z) for a, z in ev[c]) / len(ev[c]) if ev[c] else None) for c in calls}
+    if per_call:
+        per["sum_n_contrib"], per["pairs"] = (float(u) / K for u in units.cpu())
     return total, per
 
 
@@ -464,6 +477,55 @@ def variant_costs(eng, cam_dev, targets, K, stream):
     return out
 
 
+# ------------------------------------------------------------------ memory
+def memory_footprint(eng, cam_dev, targets, device, stream):
+    """Device memory of one trust-region step against one ADAM-TR step (the
+    paper's comparison of peak GPU memory, Sec. 5, Table 1) on the bench's scene
+    (1M Gaussians, SH 3, 1920x1080): each step is built fresh on the same
+    parameters, cameras and targets, and its peak is torch's max allocated bytes
+    during construction and one step, above what was allocated before.  Two
+    settings: the bench's step (8 views, nu = 2, fused) and the paper's (one view
+    per step, nu = 1).  The ADAM-TR step holds x, m, v and the gradient; the
+    trust-region step adds the curvature estimate hz, the probe tangents of the
+    splat records and images, and the extra cotangent streams of the reverse pass."""
+    import torch
+    from paper_2602_00395_gb300.engine import TRStep
+    rows = 11 + 3 * (SH_DEG + 1) ** 2
+    mat = rows * eng.n_pad * 4
+    HW3 = 3 * W * H
+    out = {}
+    for setting, views, nu in (("bench_8_views_nu2", N_VIEWS, NU), ("one_view_nu1", 1, 1)):
+        res = {}
+        for kind in ("tr", "adam_tr"):
+            torch.cuda.synchronize(device)
+            torch.cuda.empty_cache()
+            base = torch.cuda.memory_allocated(device)
+            torch.cuda.reset_peak_memory_stats(device)
+            e = TRStep(eng.n, SH_DEG, views, W, H, nu=nu if kind == "tr" else 0, tile=eng.tile, cfg=eng.cfg,
+                       device=device, capacity=eng.capacity, batch=eng.frame.batch)
+            e.x.copy_(eng.x)
+            e.cams.copy_(cam_dev[0][:96 * views])
+            e.target.copy_(targets[0][:HW3 * views])
+            with torch.cuda.stream(stream):
+                if kind == "tr":
+                    e.step(1, 1e-6, stream)
+                else:
+                    e.step_adam(1, 1e-6, None, stream)
+            torch.cuda.synchronize(device)
+            assert e.read_status() == 0, e.read_status()
+            res[kind] = (torch.cuda.max_memory_allocated(device) - base) / 1e9
+            del e
+        torch.cuda.empty_cache()
+        out[setting] = {"tr_step_peak_GB": res["tr"], "adam_tr_step_peak_GB": res["adam_tr"],
+                        "overhead_GB": res["tr"] - res["adam_tr"],
+                        "overhead_frac": res["tr"] / res["adam_tr"] - 1.0,
+                        "optimizer_state_GB": {"tr (x, g_ema, d_ema, g, hz)": 5 * mat / 1e9,
+                                               "adam_tr (x, m, v, g)": 4 * mat / 1e9}}
+    out["paper"] = ("A100, whole training process, 3DGS^2-TR vs ADAM peak memory: +0.91 / +0.84 / +0.95 GB "
+                    "(MipNeRF-360 / Deep Blending / T&T), 17 % on average (Sec. 5, Table 1); context only")
+    return out
+
+
 # ------------------------------------------------------------------ serving
 def served_metrics(device, n_requests=200, slots=16, budget_gb=40.0):
     """The served multi-scene workload: 16 resident scenes (50k-2M Gaussians, SH 3,
@@ -543,6 +605,11 @@ def raster_bwd_traffic():
     return RASTER_BWD_TRAFFIC["bytes"]
 
 
+def fp32_peak_tflops(n_sm: int, sm_mhz: float) -> float:
+    """FP32 FMA peak: n_sm SMs x 128 FP32 lanes x 2 FLOP per FMA x the SM clock."""
+    return n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -616,34 +683,159 @@ def oracle_sample(frac: int = 100, parallel: bool = True, pool=None):
 
 
 def run_reference(args):
+    """The FP64 oracle on the host's cores, on bounded samples of the workload:
+    each step is one sample (1/100 of the Gaussians, all 8 views in spawned
+    processes, then the update), timed by the wall clock.  The line reports the
+    samples it ran (steps, ms_per_step = measured time per sample) and the
+    metric scaled from them (value = 1 / (ms_per_step x sample_scale))."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return
     import __graft_entry__  # noqa: F401
     import oracle
     oracle.build()
+    frac = 100
     pool = oracle_pool()
+    nwarm = min(1, max(0, args.warmup))  # one warm-up sample is enough for a CPU program
     try:
-        for _ in range(max(0, args.warmup)):
-            oracle_sample(pool=pool)
-            break  # one warm-up sample is enough for a CPU program
+        for _ in range(nwarm):
+            oracle_sample(frac, pool=pool)
         times = []
         desc, cores = "", 1
         for _ in range(args.steps):
-            dt, scale, desc, cores = oracle_sample(pool=pool)
-            times.append(dt * scale)
+            dt, scale, desc, cores = oracle_sample(frac, pool=pool)
+            times.append(dt)
     finally:
         pool[0].shutdown()
-    step_s = sum(times) / len(times)
-    val = 1.0 / step_s
+    sample_s = sum(times) / len(times)
+    val = 1.0 / (sample_s * scale)
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True,
+        "steps": len(times), "warmup": nwarm, "ms_per_step": sample_s * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "sample_scale": scale,
+        "value_note": (f"each step ran one sample; value = 1 / (ms_per_step x {scale}) in full-workload steps/s "
+                       "(a full oracle step at 1M Gaussians is measured apart: bench.py --oracle-full-step)"),
         "config": {"workload": WORKLOAD, "sample": desc},
         "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
         "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
+
+
+def _oracle_view_full(v):
+    """One view of a full oracle step on the whole bench scene; returns (seconds, grad, hz)."""
+    return _oracle_view((1, v))
+
+
+def oracle_full_step():
+    """One full oracle step of the bench workload, nothing scaled: all 1M
+    Gaussians, the 8 views of one batch in spawned processes (one per view),
+    gradients and Hutchinson diagonals summed, then the update; by the wall clock."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    import numpy as np
+    import oracle as O
+    from paper_2602_00395_gb300 import synth as S
+    O.build()
+    cores = min(N_VIEWS, os.cpu_count() or 1)
+    t0 = time.perf_counter()
+    with cf.ProcessPoolExecutor(max_workers=cores, mp_context=mp.get_context("spawn")) as ex:
+        res = list(ex.map(_oracle_view_full, range(N_VIEWS)))
+    g = sum(r[1] for r in res)
+    hz = sum(r[2] for r in res)
+    P = O.params64(S.make_scene(N_GAUSS, SH_DEG, seed=1000, kind="clusters", extent=10.0))
+    O.tr_update(P, np.zeros_like(P), np.zeros_like(P), g, hz, SH_DEG, t=1, eps=1e-6, cfg=O.tr_config(l=1))
+    dt = time.perf_counter() - t0
+    return {"oracle_full_step_s": dt, "value": 1.0 / dt, "unit": UNIT, "cores": cores,
+            "host_cpus": os.cpu_count(), "per_view_s": [r[0] for r in res],
+            "sample": f"one full step: {N_GAUSS} Gaussians, {N_VIEWS} views at {W}x{H} in {cores} spawned "
+                      f"processes, nu={NU}, update; nothing scaled"}
+
+
+# The smaller configurations: (name, Gaussians, SH degree, scene kind, extent,
+# log-scale shift, image, views per step, nu, oracle steps timed).
+CONFIGS = [
+    ("tiny plain step", 1000, 0, "cube", 1.0, None, (128, 128), 1, 1, 10),
+    ("plain single-view training", 100_000, 3, "cube", 5.0, None, (1297, 840), 1, 1, 5),
+    ("large scene, recomputed transmittance", 6_000_000, 3, "clusters", 10.0, None, (1920, 1080), 1, 1, 0),
+]
+
+
+def _config_oracle_step(job):
+    name, n, deg, kind, ext, shift, (w, h), V, nu, _ = job
+    import numpy as np
+    import oracle as O
+    from paper_2602_00395_gb300 import synth as S
+    sc = S.make_scene(n, deg, seed=1000, kind=kind, extent=ext, log_scale_shift=shift)
+    cams = S.camera_ring(RING, w, h, ext, seed=7)[:V] if n > 1000 else [S.single_camera(w, h)]
+    target = S.noise_target(V, h, w, seed=2000).astype(np.float64)
+    P = O.params64(sc)
+    t0 = time.perf_counter()
+    out = O.backward(P, deg, cams, target, seed=42, t=1, nu=nu)
+    O.tr_update(P, np.zeros_like(P), np.zeros_like(P), out["grad"], out["hz"], deg, t=1, eps=1e-6,
+                cfg=O.tr_config(l=1))
+    return time.perf_counter() - t0
+
+
+def run_configs(device):
+    """GPU plain loop (the six calls per step, no graph) of configurations 1, 2
+    and 4, and the oracle's full steps of configurations 1 and 2 (single
+    thread, nothing scaled)."""
+    import torch
+    import oracle as O
+    from paper_2602_00395_gb300 import gs3dtr as G
+    from paper_2602_00395_gb300 import synth as S
+    from paper_2602_00395_gb300.engine import TRConfig, TRStep, eps_schedule
+    O.build()
+    out = []
+    for job in CONFIGS:
+        name, n, deg, kind, ext, shift, (w, h), V, nu, osteps = job
+        sc = S.make_scene(n, deg, seed=1000, kind=kind, extent=ext, log_scale_shift=shift)
+        cams = S.camera_ring(RING, w, h, ext, seed=7) if n > 1000 else [S.single_camera(w, h)]
+        e = TRStep(n, deg, V, w, h, nu=nu, tile=TILE, cfg=TRConfig(l=1), device=device)
+        e.set_params(sc.params)
+        e.set_cameras(cams[:V])
+        gt = S.make_scene(n, deg, seed=2000, kind=kind, extent=ext, log_scale_shift=shift)
+        e.set_params(gt.params)
+        e.ensure_capacity()
+        e.render()
+        e.target.copy_(e.image)
+        e.set_params(sc.params)
+        need = e.ensure_capacity()
+        if need * 1.2 > e.capacity:
+            e._alloc_pairs(int(need * 1.4))
+        stream = torch.cuda.Stream(device=device)
+        total = 10 if n <= 100_000 else 500
+        dev_cams = [torch.from_numpy(G.camera_bytes([c])).to(device) for c in cams[:8]]
+        with torch.cuda.stream(stream):
+            for t in range(1, 4):
+                e.cams = dev_cams[(t - 1) % len(dev_cams)]
+                e.step(t, eps_schedule(t, total), stream)
+        K = 10 if n <= 1000 else 20
+        a = torch.cuda.Event(enable_timing=True)
+        z = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            a.record(stream)
+            for t in range(4, 4 + K):
+                e.cams = dev_cams[(t - 1) % len(dev_cams)]
+                e.step(t, eps_schedule(t, total), stream)
+            z.record(stream)
+        z.synchronize()
+        ms = a.elapsed_time(z) / K
+        status = e.read_status()
+        del e
+        torch.cuda.empty_cache()
+        row = {"config": name, "gaussians": n, "sh_degree": deg, "image": f"{w}x{h}", "views_per_step": V,
+               "nu": nu, "gpu_plain_ms_per_step": ms, "gpu_plain_steps_per_s": 1e3 / ms, "status_word": status,
+               "pairs": need}
+        if osteps:
+            times = [_config_oracle_step(job) for _ in range(osteps)]
+            row["oracle_steps_timed"] = osteps
+            row["oracle_s_per_step"] = sum(times) / len(times)
+            row["oracle_steps_per_s"] = len(times) / sum(times)
+            row["oracle_cores"] = 1
+        out.append(row)
+    return out
 
 
 # ------------------------------------------------------------------ main
@@ -734,11 +926,16 @@ def run_cuda(args):
     restore()
     # the plain one-view-at-a-time loop on the same workload
     plain_ms = plain_loop_steps(eng, cam_dev, targets, max(3, min(args.steps, 10)), 9000, stream, device)
-    # roofline of the dominant call
+    restore()
+    memory = memory_footprint(eng, cam_dev, targets, device, stream)
+    # roofline of the dominant call: the work units are those of the launches
+    # the per-call times come from (summed between the calls of those steps)
     torch.cuda.synchronize()
-    sum_nc = float(eng.n_contrib.double().sum().item())
+    sum_nc = per_call.pop("sum_n_contrib")
+    pairs_timed = per_call.pop("pairs")
     hbm, sm_mhz, src = peaks()
-    fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    fp32_peak = fp32_peak_tflops(n_sm, sm_mhz)
     # every call against its own bound (HBM for the streaming calls, the FP32
     # pipe for the blends); algorithmic work per unit as documented
     R = N_VIEWS * eng.n_pad
@@ -757,7 +954,7 @@ def run_cuda(args):
         # 28 B written by the count pass (count, key, value, row-table header; the
         # row entries are not counted), 16 B per pass, 12 B count gather, 16 B
         # header read by the emit
-        "bin_sort": ("hbm", need * (12 + 24 * pair_pass + 8) + R * (48 + 28 + 16 * rec_pass + 12 + 16)),
+        "bin_sort": ("hbm", pairs_timed * (12 + 24 * pair_pass + 8) + R * (48 + 28 + 16 * rec_pass + 12 + 16)),
         "raster_fwd": ("alu", raster_fwd_flops_per_unit() * sum_nc),
         "raster_bwd": ("alu", raster_bwd_flops_per_unit() * sum_nc),
         "update": ("hbm", eng.n * rows * 4 * (5 + 3)),
@@ -783,8 +980,10 @@ def run_cuda(args):
     achieved = per_unit * sum_nc / (ms_k * 1e-3) / 1e12
     roof = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
             "frac": achieved / fp32_peak, "traffic": traffic, "launch_ms": ms_k,
-            "peak_source": f"152 SMs x 128 FP32 lanes x 2 FLOP x {sm_mhz:.0f} MHz ({src} max SM clock)",
-            "work": f"{per_unit} FLOP x {sum_nc:.4g} units (sum over pixels of n_contrib, all views)"}
+            "peak_source": (f"{n_sm} SMs (device query) x 128 FP32 lanes x 2 FLOP x {sm_mhz:.0f} MHz "
+                            f"({src} max SM clock)"),
+            "work": (f"{per_unit} FLOP x {sum_nc:.4g} units (sum over pixels of n_contrib, all views, mean of "
+                     f"the steps the call was timed on)")}
     clocks = clk.summary()
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -808,7 +1007,8 @@ def run_cuda(args):
                        "image": f"{W}x{H}", "nu": NU, "tile": f"{eng.tile[0]}x{eng.tile[1]}",
                        "blend_batch": eng.frame.batch or "one per thread",
                        "tile_autotune_ms": {f"{a}x{b}" + (f"/{c}" if c else ""): round(v, 3)
-                                            for (a, b, c), v in tile_ms.items()}, "pairs_per_step": need,
+                                            for (a, b, c), v in tile_ms.items()}, "pairs_per_step": pairs_timed,
+                       "pairs_max_over_view_batches": need,
                        "parallelism": "replicas" if ws > 1 else "single GPU",
                        "l2": "inputs larger than L2 (236 MB parameters, 199 MB targets per step)",
                        "view_steps_per_s": value * N_VIEWS},
@@ -822,7 +1022,7 @@ def run_cuda(args):
                       "what": "the same steps as six C-ABI calls issued from the host per step, no graph"},
             "graph": "one captured CUDA graph per view batch, step index and eps_t on the device",
             "curvature": {**curv, "l1_fused_ms": ms_per_step, "overhead_l1_fused": ms_per_step / curv["gradient_only_ms"] - 1.0},
-            "variants": variants,
+            "variants": variants, "memory": memory,
             "gpu_launches": kernel_launches_per_step(eng) * args.steps,
             "roofline": roof, "roofline_calls": roof_calls, "clocks": clocks, "cpu_baseline": cpu,
             "served": None,
@@ -839,7 +1039,15 @@ def run_cuda(args):
 
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.oracle_full_step:
+        print(json.dumps(oracle_full_step()))
+    elif args.configs:
+        import torch
+        torch.cuda.set_device(0)
+        import __graft_entry__
+        __graft_entry__.build()
+        print(json.dumps({"configs": run_configs("cuda:0")}))
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_cuda(args)

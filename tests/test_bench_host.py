@@ -7,9 +7,13 @@ import bench
 
 
 def test_traffic_is_reported_only_for_the_captured_sources(monkeypatch):
-    assert bench.raster_bwd_traffic() == bench.RASTER_BWD_TRAFFIC["bytes"]
-    changed = dict(bench.RASTER_BWD_TRAFFIC)
-    changed["sources"] = dict(changed["sources"])
+    import hashlib
+    sources = {rel: hashlib.sha256(open(os.path.join(bench.ROOT, rel), "rb").read()).hexdigest()
+               for rel in bench.RASTER_BWD_TRAFFIC["sources"]}
+    same = dict(bench.RASTER_BWD_TRAFFIC, sources=sources)
+    monkeypatch.setattr(bench, "RASTER_BWD_TRAFFIC", same)
+    assert bench.raster_bwd_traffic() == same["bytes"]
+    changed = dict(same, sources=dict(sources))
     first = next(iter(changed["sources"]))
     changed["sources"][first] = "0" * 64
     monkeypatch.setattr(bench, "RASTER_BWD_TRAFFIC", changed)
@@ -60,6 +64,8 @@ def test_reference_arm_prints_one_json_line():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
     assert d["value"] > 0 and d["higher_is_better"] is True and d["steps"] == 1 and d["warmup"] == 0
+    # the line reports the sample it timed and the scale that gives the metric
+    assert abs(d["value"] * d["ms_per_step"] * 1e-3 * d["sample_scale"] - 1.0) < 1e-9
     assert d["config"]["workload"] == bench.WORKLOAD
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["cpu_baseline"]["value"] == d["value"]
