@@ -489,6 +489,10 @@ struct View {
   std::vector<std::vector<int>> amb;
   // per splat: some tile of its own may enter or leave under rounding
   std::vector<char> own_amb;
+  // per tile, for blend_flips: the splats of amb not in the list, in key order,
+  // and the largest colour channel of the list's and those splats
+  std::vector<std::vector<int>> amb_extra;
+  std::vector<double> tile_cmax;
 };
 
 // Tiles whose membership in a splat's per-row spans may differ between the
@@ -620,6 +624,21 @@ View build_view(const double* P, long pitch, long n, int deg, const double* cam2
     tiles.erase(std::unique(tiles.begin(), tiles.end()), tiles.end());
     for (int t : tiles) V.amb[(size_t)t].push_back((int)i);
   }
+  V.amb_extra.assign((size_t)V.Tx * V.Ty, {});
+  V.tile_cmax.assign((size_t)V.Tx * V.Ty, 0.0);
+  auto cmax_of = [&](int i) { return std::max({V.sp[i].rgb[0], V.sp[i].rgb[1], V.sp[i].rgb[2], 0.0}); };
+  for (size_t t = 0; t < V.lists.size(); ++t) {
+    for (int i : V.lists[t]) V.tile_cmax[t] = std::max(V.tile_cmax[t], cmax_of(i));
+    for (int i : V.amb[t])
+      if (std::find(V.lists[t].begin(), V.lists[t].end(), i) == V.lists[t].end()) {
+        V.amb_extra[t].push_back(i);
+        V.tile_cmax[t] = std::max(V.tile_cmax[t], cmax_of(i));
+      }
+    std::sort(V.amb_extra[t].begin(), V.amb_extra[t].end(), [&](int a, int b) {
+      const float da = (float)V.sp[a].depth, db = (float)V.sp[b].depth;
+      return da < db || (da == db && a < b);
+    });
+  }
   return V;
 }
 
@@ -720,6 +739,9 @@ double binning_margin(const View& V, int tx, int ty, double pcx, double pcy, int
   return std::numeric_limits<double>::infinity();
 }
 
+// Cotangents of the 2-D splat quantities, 9 per splat: (mx, my, A, B, C, o, r, g, b).
+enum { Q_MX, Q_MY, Q_A, Q_B, Q_C, Q_O, Q_R, Q_G, Q_BL, NQ };
+
 // ------------------------------------------------ FP32 decision uncertainty
 // The CUDA path takes the blend's discrete decisions (Sec. 3.1 thresholds) on
 // FP32 splat records, which differ from the oracle's FP64 ones by rounding.  A
@@ -757,36 +779,59 @@ double power_uncertainty(const Splat<double>& g, double dx, double dy) {
 // Decisions whose FP64 value is farther from the threshold than the rounding
 // bound (power_uncertainty, and for the termination test the transmittance's
 // own accumulated rounding plus the changes upstream flips make to it) are
-// firm.  `maybe` lists splats whose membership in the tile's list may differ
-// (see build_view); those in the list may be missing on the GPU, the others
-// may be present there.
+// firm.  The tile's amb splats (see build_view) are those whose membership in
+// its list may differ: those in the list may be missing on the GPU, the others
+// (amb_extra) may be present there.
+// A decision of splat i's own at one pixel that FP32 may flip (its 1/255 skip,
+// its cap, its power sign) or its membership in the tile's list: its alpha with
+// the cap lifted, exp(power), offset from the pixel and the transmittance in
+// front of it.
+struct OwnFlip {
+  int i;
+  double a, G, dx, dy, T;
+};
+
+// The terms splat g adds at one pixel for the cotangent w, as absolute values,
+// with its alpha uncapped: a bound on how far its reverse-pass terms there move
+// when a decision of its own flips (added, dropped or uncapped).  cmax bounds
+// the colours behind it (the suffix over 1 - a is at most T cmax / (1 - a)).
+void own_terms(const Splat<double>& g, const OwnFlip& q, double cmax, const double w[3], double* out) {
+  double gab = 0.0;
+  for (int ch = 0; ch < 3; ++ch) gab += std::fabs(w[ch]) * q.T * (std::fabs(g.rgb[ch]) + cmax / (1.0 - q.a));
+  out[Q_R] += std::fabs(w[0]) * q.a * q.T;
+  out[Q_G] += std::fabs(w[1]) * q.a * q.T;
+  out[Q_BL] += std::fabs(w[2]) * q.a * q.T;
+  out[Q_O] += gab * q.G;
+  const double gpow = gab * q.a;
+  out[Q_A] += 0.5 * q.dx * q.dx * gpow;
+  out[Q_B] += std::fabs(q.dx * q.dy) * gpow;
+  out[Q_C] += 0.5 * q.dy * q.dy * gpow;
+  out[Q_MX] += (std::fabs(g.A * q.dx) + std::fabs(g.B * q.dy)) * gpow;
+  out[Q_MY] += (std::fabs(g.C * q.dy) + std::fabs(g.B * q.dx)) * gpow;
+}
+
 struct Flip {
   double impact = 0.0, t_impact = 0.0, err = 0.0;
   int nc_lo = 0, nc_hi = 0;
   int kinds = 0;  // flips that count: 1 skip, 2 termination, 4 list membership, 8 depth order
 };
 
-Flip blend_flips(const std::vector<int>& list, const std::vector<int>& maybe, const std::vector<Splat<double>>& sp,
-                 double pcx, double pcy, int nc) {
+// owns (may be null) receives the splats whose own decision (skip, cap or
+// power sign) or list membership may flip here, in walk order.
+Flip blend_flips(const View& V, size_t tile, double pcx, double pcy, int nc, std::vector<OwnFlip>* owns = nullptr) {
+  const std::vector<int>& list = V.lists[tile];
+  const std::vector<int>& maybe = V.amb[tile];
+  const std::vector<int>& extra = V.amb_extra[tile];
+  const std::vector<Splat<double>>& sp = V.sp;
   Flip f;
   f.nc_lo = f.nc_hi = nc;
-  // the walk order: the list, with the possibly-present splats merged in by key
   struct Entry {
     int i;
     bool in_list;
     float depth;
   };
-  std::vector<Entry> order;
-  order.reserve(list.size() + maybe.size());
-  for (int i : list) order.push_back({i, true, (float)sp[i].depth});
-  for (int i : maybe)
-    if (std::find(list.begin(), list.end(), i) == list.end()) order.push_back({i, false, (float)sp[i].depth});
-  std::stable_sort(order.begin(), order.end(), [](const Entry& a, const Entry& b) {
-    return a.depth < b.depth || (a.depth == b.depth && a.i < b.i);
-  });
   auto cmax_of = [&](int i) { return std::max({sp[i].rgb[0], sp[i].rgb[1], sp[i].rgb[2], 0.0}); };
-  double cmax = 0.0;
-  for (const Entry& e : order) cmax = std::max(cmax, cmax_of(e.i));
+  const double cmax = V.tile_cmax[tile];
   auto is_maybe = [&](int i) { return std::find(maybe.begin(), maybe.end(), i) != maybe.end(); };
   double T = 1.0;
   double rho = 0.0;  // relative change of T that upstream flips can make
@@ -796,7 +841,29 @@ Flip blend_flips(const std::vector<int>& list, const std::vector<int>& maybe, co
   double prev_depth = -1.0, prev_a = 0.0;
   int prev_i = -1;
   bool prev_blended = false;
-  for (const Entry& e : order) {
+  // the walk order: the list, with the possibly-present splats merged in by key
+  size_t li = 0, ei = 0;
+  while (li < list.size() || ei < extra.size()) {
+    Entry e;
+    if (ei < extra.size()) {
+      const int a = extra[ei];
+      const float da = (float)sp[a].depth;
+      bool take = li == list.size();
+      if (!take) {
+        const float dl = (float)sp[list[li]].depth;
+        take = da < dl || (da == dl && a < list[li]);
+      }
+      if (take) {
+        e = {a, false, da};
+        ++ei;
+      } else {
+        e = {list[li], true, (float)sp[list[li]].depth};
+        ++li;
+      }
+    } else {
+      e = {list[li], true, (float)sp[list[li]].depth};
+      ++li;
+    }
     const Splat<double>& g = sp[e.i];
     const double dx = g.mx - pcx, dy = g.my - pcy;
     const double power = -0.5 * (g.A * dx * dx + g.C * dy * dy) - g.B * dx * dy;
@@ -807,6 +874,9 @@ Flip blend_flips(const std::vector<int>& list, const std::vector<int>& maybe, co
     const bool blends = power <= 0.0 && a >= kAlphaMin;
     const bool near = std::fabs(power) <= dp || (!capped && std::fabs(a / kAlphaMin - 1.0) <= dp + 2e-6);
     const double drop = a * T * (cmax_of(e.i) + cmax);  // colour bound of adding or dropping it
+    if (owns && oG >= 0.5 * kAlphaMin &&
+        (near || !e.in_list || is_maybe(e.i) || std::fabs(oG / kAlphaMax - 1.0) <= dp + 2e-6))
+      owns->push_back({e.i, std::min(oG, 1.0 - 1e-6), oG / g.o, dx, dy, T});
     if (!e.in_list) {
       // may be listed on the GPU: an extra splat wherever it would blend
       if (blends || near) {
@@ -1027,8 +1097,7 @@ std::vector<double> ssim_jvp(const double* x, const double* y, int H, int W, con
 }
 
 // ----------------------------------------------------------- reverse pass
-// Cotangents of the 2-D splat quantities, 9 per splat: (mx, my, A, B, C, o, r, g, b).
-enum { Q_MX, Q_MY, Q_A, Q_B, Q_C, Q_O, Q_R, Q_G, Q_BL, NQ };
+// Cotangents of the 2-D splat quantities, 9 per splat (the enum Q_* above).
 
 // Reverse pass of one pixel's blend, written out from
 //   dC/dc_i = a_i T_i,
@@ -1446,7 +1515,7 @@ long or_render(const double* P, long pitch, long n, int deg, const double* cams,
         margin[v * HW + px] = std::min(mg, binning_margin(V, tx, ty, x + 0.5, y + 0.5, nc, &lo, &hi));
       if (impact || nc_range || err) {
         const size_t tile = (size_t)ty * V.Tx + tx;
-        const Flip fl = blend_flips(V.lists[tile], V.amb[tile], V.sp, x + 0.5, y + 0.5, nc);
+        const Flip fl = blend_flips(V, tile, x + 0.5, y + 0.5, nc);
         if (impact) impact[v * HW + px] = fl.impact;
         if (t_impact) t_impact[v * HW + px] = fl.t_impact;
         if (err) err[v * HW + px] = fl.err;
@@ -1537,7 +1606,8 @@ void or_jacobian(const double* P, long pitch, long n, int deg, const double* cam
 double backward_impl(const double* P, long pitch, long n, int deg, const double* cams, int n_views, int tw,
                      int th, const double* target, int loss_kind, double lambda, double gn_floor, uint64_t seed,
                      int64_t t, int nu, double* grad, double* hz, double* img_tan, double* res_margin,
-                     double* grad_mass, double* hz_mass, double* hz_sens = nullptr) {
+                     double* grad_mass, double* hz_mass, double* hz_sens = nullptr, double* grad_allow = nullptr,
+                     double* hz_allow = nullptr) {
   int rows = n_rows(deg);
   double m = 0.0;
   std::vector<View> views;
@@ -1551,7 +1621,10 @@ double backward_impl(const double* P, long pitch, long n, int deg, const double*
   if (grad_mass) for (long k = 0; k < (long)rows * n; ++k) grad_mass[k] = 0.0;
   if (hz_mass) for (long k = 0; k < (long)rows * n; ++k) hz_mass[k] = 0.0;
   if (hz_sens) for (long k = 0; k < (long)rows * n; ++k) hz_sens[k] = 0.0;
+  if (grad_allow) for (long k = 0; k < (long)rows * n; ++k) grad_allow[k] = 0.0;
+  if (hz_allow) for (long k = 0; k < (long)rows * n; ++k) hz_allow[k] = 0.0;
   const bool sensing = hz_sens != nullptr && loss_kind == 0 && nu > 0;
+  const bool allowing = grad_allow != nullptr;
 
   // probe directions z_k over the parameter vector (entry i * rows + r)
   std::vector<std::vector<double>> z(nu, std::vector<double>((size_t)rows * pitch, 0.0));
@@ -1572,6 +1645,8 @@ double backward_impl(const double* P, long pitch, long n, int deg, const double*
     std::vector<std::vector<double>> cot(1 + nu, std::vector<double>((size_t)n * NQ, 0.0));
     std::vector<std::vector<double>> cot_abs(masses ? 1 + nu : 0, std::vector<double>((size_t)n * NQ, 0.0));
     std::vector<std::vector<double>> cot_sens(sensing ? nu : 0, std::vector<double>((size_t)n * NQ, 0.0));
+    std::vector<std::vector<double>> cot_allow(allowing ? 1 + nu : 0, std::vector<double>((size_t)n * NQ, 0.0));
+    std::vector<OwnFlip> ofl;
     std::vector<std::vector<double>> jz(nu, std::vector<double>(3 * HW, 0.0));
     for (int k = 0; k < nu; ++k) {
       std::vector<Splat<Dual>> sd = project_tangent(V, P, pitch, n, deg, z[k].data());
@@ -1642,14 +1717,24 @@ double backward_impl(const double* P, long pitch, long n, int deg, const double*
       blend_reverse(tr, V.sp, w, cot[0].data());
       if (masses) blend_reverse_abs(tr, V.sp, w, cot_abs[0].data());
       double sens[3] = {0.0, 0.0, 0.0};
-      if (sensing) {
-        const size_t tile = (size_t)ty * V.Tx + tx;
-        const double e_px =
-            std::min(blend_flips(V.lists[tile], V.amb[tile], V.sp, x + 0.5, y + 0.5, nc).err, kImageTol);
-        for (int ch = 0; ch < 3; ++ch) {
+      const size_t tile = (size_t)ty * V.Tx + tx;
+      ofl.clear();
+      if (sensing || allowing) {
+        const double e_px = std::min(blend_flips(V, tile, x + 0.5, y + 0.5, nc, allowing ? &ofl : nullptr).err,
+                                     kImageTol);
+        for (int ch = 0; sensing && ch < 3; ++ch) {
           const double r = std::fabs(C[ch] - tg[ch * HW + px]);
           sens[ch] = r + e_px > gn_floor ? e_px / std::max(r, gn_floor) : 0.0;
         }
+      }
+      if (allowing) {
+        // own decisions that may flip here, and (L1) residual signs within the
+        // image tolerance, whose dL/dC then changes by 2 |w|
+        for (const OwnFlip& q : ofl) own_terms(V.sp[q.i], q, V.tile_cmax[tile], w, cot_allow[0].data() + q.i * NQ);
+        double wflip[3];
+        for (int ch = 0; ch < 3; ++ch)
+          wflip[ch] = (loss_kind == 0 && std::fabs(C[ch] - tg[ch * HW + px]) < kImageTol) ? 2.0 * w[ch] : 0.0;
+        blend_reverse_abs(tr, V.sp, wflip, cot_allow[0].data());
       }
       for (int k = 0; k < nu; ++k) {
         double wk[3];
@@ -1662,6 +1747,9 @@ double backward_impl(const double* P, long pitch, long n, int deg, const double*
           for (int ch = 0; ch < 3; ++ch) ws[ch] = wk[ch] * sens[ch];
           blend_reverse_abs(tr, V.sp, ws, cot_sens[k].data());
         }
+        if (allowing)
+          for (const OwnFlip& q : ofl)
+            own_terms(V.sp[q.i], q, V.tile_cmax[tile], wk, cot_allow[1 + k].data() + q.i * NQ);
       }
     });
     for (long i = 0; i < n; ++i) {
@@ -1669,7 +1757,8 @@ double backward_impl(const double* P, long pitch, long n, int deg, const double*
       for (int s = 0; s <= nu; ++s) {
         const double* c = cot[s].data() + i * NQ;
         bool any = false;
-        for (int q = 0; q < NQ; ++q) any = any || c[q] != 0.0;
+        for (int q = 0; q < NQ; ++q)
+          any = any || c[q] != 0.0 || (allowing && cot_allow[s][(size_t)i * NQ + q] != 0.0);
         if (!any) continue;
         std::fill(g_acc.begin(), g_acc.end(), 0.0);
         project_reverse(P, pitch, i, deg, V.cam, c, g_acc);
@@ -1681,6 +1770,11 @@ double backward_impl(const double* P, long pitch, long n, int deg, const double*
           std::fill(g_acc.begin(), g_acc.end(), 0.0);
           project_reverse_abs(P, pitch, i, deg, V.cam, cot_sens[s - 1].data() + i * NQ, g_acc);
           for (int r = 0; r < rows; ++r) hz_sens[(long)r * n + i] += g_acc[r] / nu;
+        }
+        if (allowing && (s == 0 || hz_allow)) {
+          std::fill(g_acc.begin(), g_acc.end(), 0.0);
+          project_reverse_abs(P, pitch, i, deg, V.cam, cot_allow[s].data() + i * NQ, g_acc);
+          for (int r = 0; r < rows; ++r) (s == 0 ? grad_allow : hz_allow)[(long)r * n + i] += g_acc[r] / (s == 0 ? 1 : nu);
         }
         if (!masses || (s > 0 && !hz_mass)) continue;
         std::fill(g_acc.begin(), g_acc.end(), 0.0);
@@ -1699,16 +1793,17 @@ double backward_impl(const double* P, long pitch, long n, int deg, const double*
 double or_backward(const double* P, long pitch, long n, int deg, const double* cams, int n_views, int tw,
                    int th, const double* target, int loss_kind, double gn_floor, uint64_t seed, int64_t t,
                    int nu, double* grad, double* hz, double* img_tan, double* res_margin, double* grad_mass,
-                   double* hz_mass, double* hz_sens) {
+                   double* hz_mass, double* hz_sens, double* grad_allow, double* hz_allow) {
   return backward_impl(P, pitch, n, deg, cams, n_views, tw, th, target, loss_kind, 0.0, gn_floor, seed, t, nu,
-                       grad, hz, img_tan, res_margin, grad_mass, hz_mass, hz_sens);
+                       grad, hz, img_tan, res_margin, grad_mass, hz_mass, hz_sens, grad_allow, hz_allow);
 }
 
 double or_backward_dssim(const double* P, long pitch, long n, int deg, const double* cams, int n_views, int tw,
                          int th, const double* target, double lambda, double gn_floor, uint64_t seed, int64_t t,
-                         int nu, double* grad, double* hz, double* img_tan, double* grad_mass, double* hz_mass) {
+                         int nu, double* grad, double* hz, double* img_tan, double* grad_mass, double* hz_mass,
+                         double* grad_allow, double* hz_allow) {
   return backward_impl(P, pitch, n, deg, cams, n_views, tw, th, target, 2, lambda, gn_floor, seed, t, nu, grad, hz,
-                       img_tan, nullptr, grad_mass, hz_mass);
+                       img_tan, nullptr, grad_mass, hz_mass, nullptr, grad_allow, hz_allow);
 }
 
 // SSIM map of one channel and its partials (for the pins), and the adjoint and
@@ -1866,7 +1961,7 @@ void or_render_pixels(const double* P, long pitch, long n, int deg, const double
     int lo = nc, hi = nc;
     margin[q] = std::min(mg, binning_margin(V, tx, ty, x + 0.5, y + 0.5, nc, &lo, &hi));
     if (impact) {
-      const Flip fl = blend_flips(list, V.amb[(size_t)ty * V.Tx + tx], V.sp, x + 0.5, y + 0.5, nc);
+      const Flip fl = blend_flips(V, (size_t)ty * V.Tx + tx, x + 0.5, y + 0.5, nc);
       impact[q] = fl.impact;
       if (t_impact) t_impact[q] = fl.t_impact;
       if (flip_kinds) flip_kinds[q] = fl.kinds;
@@ -1909,10 +2004,17 @@ void or_render_pixels(const double* P, long pitch, long n, int deg, const double
 // gn_floor) wherever |r| + e exceeds the floor, and the bound is that relative
 // change carried through the absolute terms (blend_reverse_abs,
 // project_reverse_abs).
+// grad_allow, hz_allow (ns x rows, may be null): how far the entries may move
+// when a decision of the sample's own flips in FP32 at a pixel where it is
+// visible (its 1/255 skip, its cap, its power sign, or its membership in the
+// tile's list), or a residual sign flips there (gradient only, 2 |dL/dC|): at
+// each such pixel, the absolute values of the terms the sample adds there with
+// its alpha uncapped, carried through project_reverse_abs.
 void or_backward_sampled(const double* P, long pitch, long n, int deg, const double* cams, int n_views, int tw,
                          int th, const double* target, int loss_kind, double gn_floor, uint64_t seed, int64_t t,
                          int nu, long ns, const int64_t* samples, double* grad_out, double* hz_out, int32_t* flag,
-                         double eps_img, double* grad_mass, double* hz_mass, double* hz_sens) {
+                         double eps_img, double* grad_mass, double* hz_mass, double* hz_sens, double* grad_allow,
+                         double* hz_allow) {
   int rows = n_rows(deg);
   double m = 0.0;
   for (int v = 0; v < n_views; ++v) {
@@ -1925,8 +2027,11 @@ void or_backward_sampled(const double* P, long pitch, long n, int deg, const dou
     if (grad_mass) grad_mass[k] = 0.0;
     if (hz_mass) hz_mass[k] = 0.0;
     if (hz_sens) hz_sens[k] = 0.0;
+    if (grad_allow) grad_allow[k] = 0.0;
+    if (hz_allow) hz_allow[k] = 0.0;
   }
   const bool masses = grad_mass || hz_mass || hz_sens;
+  const bool allow = grad_allow != nullptr;
   for (long sidx = 0; sidx < ns; ++sidx) flag[sidx] = 0;
   long img_off = 0;
   std::vector<double> g_acc(rows);
@@ -1948,11 +2053,25 @@ void or_backward_sampled(const double* P, long pitch, long n, int deg, const dou
     std::vector<std::vector<double>> cot(1 + nu, std::vector<double>((size_t)n * NQ, 0.0));
     // masses: 0 the gradient, 1..nu the probes, nu+1..2nu the probes' sensitivity
     std::vector<std::vector<double>> cab(masses ? 1 + 2 * nu : 0, std::vector<double>((size_t)n * NQ, 0.0));
+    // allowances per sample and stream (0 the gradient, 1..nu the probes), NQ each
+    std::vector<double> al(allow ? (size_t)ns * (1 + nu) * NQ : 0, 0.0);
+    struct Own {
+      long sidx;
+      double a, G, dx, dy, T;
+      bool own;  // its own decision or its tile membership may flip here
+    };
+    std::vector<Own> owns;
+    double own_cmax = 0.0;  // the largest colour channel of the current tile's splats
+    auto own_add = [&](const Own& q, const double wv[3], double* out) {
+      own_terms(V.sp[samples[q.sidx]], OwnFlip{(int)samples[q.sidx], q.a, q.G, q.dx, q.dy, q.T}, own_cmax, wv, out);
+    };
     std::vector<int> local;
     for (int ty = 0; ty < V.Ty; ++ty)
       for (int tx = 0; tx < V.Tx; ++tx) {
         if (!need[(size_t)ty * V.Tx + tx]) continue;
         const std::vector<int>& list = V.lists[(size_t)ty * V.Tx + tx];
+        const std::vector<int>& amb = V.amb[(size_t)ty * V.Tx + tx];
+        own_cmax = V.tile_cmax[(size_t)ty * V.Tx + tx];
         std::vector<std::vector<Splat<Dual>>> sd(nu);
         for (int k = 0; k < nu; ++k) sd[k] = tile_tangents(V, list, P, pitch, deg, seed, t, k, n);
         local.resize(list.size());
@@ -1966,8 +2085,7 @@ void or_backward_sampled(const double* P, long pitch, long n, int deg, const dou
             long px = (long)y * V.cam.W + x;
             double w[3], wgn[3], sens[3], rmin = kInf;
             const double e_px =
-                masses ? std::min(blend_flips(list, V.amb[(size_t)ty * V.Tx + tx], V.sp, x + 0.5, y + 0.5, nc).err,
-                                  eps_img)
+                masses ? std::min(blend_flips(V, (size_t)ty * V.Tx + tx, x + 0.5, y + 0.5, nc).err, eps_img)
                        : 0.0;
             for (int ch = 0; ch < 3; ++ch) {
               double r = C[ch] - tg[ch * HW + px];
@@ -1984,25 +2102,54 @@ void or_backward_sampled(const double* P, long pitch, long n, int deg, const dou
             }
             const double mb = binning_margin(V, tx, ty, x + 0.5, y + 0.5);
             // reasons a sample visible here may see another decision in FP32:
-            // 2 its own alpha / cap / power decision within 1e-5, 4 the residual
-            // sign, 8 another splat's binning, 16 another splat's threshold decision
+            // 2 its own alpha / cap / power decision within the rounding bound, 4
+            // the residual sign, 8 another splat's binning, 16 another splat's
+            // threshold decision within 1e-5
+            owns.clear();
             for (long sidx = 0; sidx < ns; ++sidx) {
-              const Splat<double>& g = V.sp[samples[sidx]];
+              const int si = (int)samples[sidx];
+              const Splat<double>& g = V.sp[si];
               if (!g.valid) continue;
               double dx = g.mx - (x + 0.5), dy = g.my - (y + 0.5);
               double power = -0.5 * (g.A * dx * dx + g.C * dy * dy) - g.B * dx * dy;
-              double oG = g.o * std::exp(power);
+              double oG = g.o * std::exp(std::min(power, 0.0));
               if (oG < 0.5 * kAlphaMin) continue;
               const double dp = power_uncertainty(g, dx, dy);
-              if (std::fabs(std::min(oG, kAlphaMax) / kAlphaMin - 1.0) <= dp + 2e-6 ||
-                  std::fabs(oG / kAlphaMax - 1.0) <= dp + 2e-6 || std::fabs(power) <= dp)
-                flag[sidx] |= 2;
+              const bool own_near = std::fabs(std::min(oG, kAlphaMax) / kAlphaMin - 1.0) <= dp + 2e-6 ||
+                                    std::fabs(oG / kAlphaMax - 1.0) <= dp + 2e-6 || std::fabs(power) <= dp;
+              const bool in_tile = std::find(list.begin(), list.end(), si) != list.end();
+              const bool membership = std::find(amb.begin(), amb.end(), si) != amb.end();
+              if (own_near) flag[sidx] |= 2;
               if (rmin < eps_img) flag[sidx] |= 4;
               if (mb < 1e-5) flag[sidx] |= 8;
               if (mg < 1e-5) flag[sidx] |= 16;
+              if (!allow || (!in_tile && !membership)) continue;
+              // transmittance in front of it: its own trace entry, else that of
+              // the first blended splat behind it, else the final T
+              const float dsi = (float)g.depth;
+              double Ts = T;
+              for (const Contrib& e : tr) {
+                const float de = (float)V.sp[e.i].depth;
+                if (e.i == si || de > dsi || (de == dsi && e.i > si)) {
+                  Ts = e.T;
+                  break;
+                }
+              }
+              owns.push_back({sidx, std::min(oG, 1.0 - 1e-6), oG / g.o, dx, dy, Ts, own_near || membership});
             }
             blend_reverse(tr, V.sp, w, cot[0].data());
             if (masses) blend_reverse_abs(tr, V.sp, w, cab[0].data());
+            if (allow) {
+              // a residual whose sign may flip changes its dL/dC by 2 |w|
+              double wflip[3];
+              for (int ch = 0; ch < 3; ++ch)
+                wflip[ch] = (loss_kind == 0 && std::fabs(C[ch] - tg[ch * HW + px]) < eps_img) ? 2.0 * w[ch] : 0.0;
+              for (const Own& q : owns) {
+                double* out = al.data() + ((size_t)q.sidx * (1 + nu)) * NQ;
+                if (q.own) own_add(q, w, out);
+                own_add(q, wflip, out);
+              }
+            }
             for (int k = 0; k < nu; ++k) {
               Dual Cd[3], Td;
               int ncd;
@@ -2012,6 +2159,9 @@ void or_backward_sampled(const double* P, long pitch, long n, int deg, const dou
                 wk[ch] = wgn[ch] * Cd[ch].d;
                 ws[ch] = wk[ch] * sens[ch];
               }
+              if (allow)
+                for (const Own& q : owns)
+                  if (q.own) own_add(q, wk, al.data() + ((size_t)q.sidx * (1 + nu) + 1 + k) * NQ);
               blend_reverse(tr, V.sp, wk, cot[1 + k].data());
               if (masses) {
                 blend_reverse_abs(tr, V.sp, wk, cab[1 + k].data());
@@ -2035,6 +2185,13 @@ void or_backward_sampled(const double* P, long pitch, long n, int deg, const dou
         std::fill(g_acc.begin(), g_acc.end(), 0.0);
         project_reverse_abs(P, pitch, i, deg, V.cam, cab[st].data() + i * NQ, g_acc);
         double* out = st == 0 ? grad_mass : (st <= nu ? hz_mass : hz_sens);
+        if (!out) continue;
+        for (int r = 0; r < rows; ++r) out[sidx * rows + r] += g_acc[r] / (st == 0 ? 1.0 : nu);
+      }
+      for (int st = 0; allow && st <= nu; ++st) {
+        std::fill(g_acc.begin(), g_acc.end(), 0.0);
+        project_reverse_abs(P, pitch, i, deg, V.cam, al.data() + ((size_t)sidx * (1 + nu) + st) * NQ, g_acc);
+        double* out = st == 0 ? grad_allow : hz_allow;
         if (!out) continue;
         for (int r = 0; r < rows; ++r) out[sidx * rows + r] += g_acc[r] / (st == 0 ? 1.0 : nu);
       }

@@ -11,14 +11,14 @@ ABI, compared with the FP64 oracle on outputs it can compute one by one.
     than half the tolerance (the oracle's impact bound: a_k T_k (c_k + c_max) for
     a skip, T_k c_max for a termination, T a_i a_j |c_i - c_j| for a depth swap);
     the excluded fraction is printed and held below 5 %.
-  * 64 sampled Gaussians: their gradient rows (1e-4 of the group's largest
-    sampled entry, and each entry within 1e-4 of the mass of the sum that forms
-    it) and Hutchinson rows (1e-3 of the group's largest, plus for each entry the
-    oracle's bound on how far it moves when each residual moves by its pixel's
-    FP32 rounding bound: the L1 Gauss-Newton weight 1/(4 max(|r|, delta)) is that
-    sensitive near the floor; the entries that needed it are counted), unless
-    their own tile set, their own threshold decision or a residual sign in their
-    footprint is within rounding of flipping (flagged and counted).
+  * 64 sampled Gaussians, every one compared: their gradient rows (1e-4 of the
+    group's largest sampled entry, and each entry within 1e-4 of the mass of the
+    sum that forms it) and Hutchinson rows (1e-3 of the group's largest), each
+    entry plus the oracle's allowances: how far it moves when each residual
+    moves by its pixel's FP32 rounding bound (the L1 Gauss-Newton weight
+    1/(4 max(|r|, delta)) is that sensitive near the floor), and what the pixels
+    where a decision of the sample's own or a residual sign may flip in FP32 can
+    change.  The entries that needed an allowance are counted.
 The targets are seeded images from the generator module, never GPU output.
 """
 import numpy as np
@@ -103,26 +103,25 @@ def test_sampled_gaussians_match_oracle(fullsize):
     smp = rng.choice(visible, 64, replace=False)
     ref = O.backward_sampled(P, 3, f["cams"], f["target"].astype(np.float64), smp, seed=42, t=f["t"], nu=f["nu"],
                              eps_img=IMG_TOL)
-    # Excluded: samples whose own tile set, own threshold decision or a residual
-    # sign under their footprint is within rounding of flipping.  Decisions of
-    # other splats (flags 8, 16) move a sum over thousands of pixels far less
-    # than the tolerance, so those samples stay in.
-    keep = (ref["flag"] & 7) == 0
-    print(f"\nfull size: {int(keep.sum())} of {len(smp)} sampled Gaussians compared (flags {np.bincount(ref['flag'] & 7)})")
-    assert keep.sum() >= 48, ref["flag"]
-    g_gpu, h_gpu = f["grad"][:, smp].T[keep], f["hz"][:, smp].T[keep]
-    g_ref, h_ref = ref["grad"][keep], ref["hz"][keep]
-    g_mass, h_sens = ref["grad_mass"][keep], ref["hz_sens"][keep]
-    allowance_used = entries = 0
+    # Every sample is compared.  Where a decision of its own (its 1/255 skip, its
+    # cap, its power sign, its tile membership) or a residual sign may flip in
+    # FP32 at a pixel where it is visible, the oracle bounds what that pixel's
+    # terms can change (grad_allow, hz_allow); decisions of other splats move a
+    # sum over hundreds of pixels far less than the tolerance.
+    g_gpu, h_gpu = f["grad"][:, smp].T, f["hz"][:, smp].T
+    g_ref, h_ref = ref["grad"], ref["hz"]
+    g_mass, g_allow = ref["grad_mass"], ref["grad_allow"]
+    h_allow = ref["hz_sens"] + ref["hz_allow"]
+    used = {"grad": 0, "hz": 0}
     for name, sl in GROUPS.items():
         gs = np.abs(g_ref[:, sl]).max()
         hs = np.abs(h_ref[:, sl]).max()
         g_err = np.abs(g_gpu[:, sl] - g_ref[:, sl])
-        assert g_err.max() <= GRAD_TOL * gs, name
-        assert np.all(g_err <= GRAD_TOL * g_mass[:, sl]), name
+        assert np.all(g_err <= GRAD_TOL * gs + g_allow[:, sl]), name
+        assert np.all(g_err <= GRAD_TOL * g_mass[:, sl] + g_allow[:, sl]), name
         h_err = np.abs(h_gpu[:, sl] - h_ref[:, sl])
-        assert np.all(h_err <= HZ_TOL * hs + h_sens[:, sl]), name
-        allowance_used += int((h_err > HZ_TOL * hs).sum())
-        entries += h_err.size
-    print(f"full size: {allowance_used} of {entries} Hutchinson entries beyond 1e-3 of their group, "
-          f"all within the rounding allowance")
+        assert np.all(h_err <= HZ_TOL * hs + h_allow[:, sl]), name
+        used["grad"] += int((g_err > GRAD_TOL * gs).sum())
+        used["hz"] += int((h_err > HZ_TOL * hs).sum())
+    print(f"\nfull size: 64 sampled Gaussians ({int((np.abs(g_ref).max(1) > 0).sum())} with a nonzero gradient); "
+          f"entries beyond the group tolerance, within the oracle's allowances: {used} of {g_ref.size} each")

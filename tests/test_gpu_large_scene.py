@@ -105,16 +105,16 @@ def test_sampled_gaussians_match_oracle(large):
     rng = np.random.default_rng(9)
     smp = rng.choice(visible, 64, replace=False)
     ref = O.backward_sampled(P, DEG, [f["cam"]], f["target"].astype(np.float64), smp, seed=42, t=f["t"], nu=1)
-    keep = (ref["flag"] & 7) == 0
-    print(f"\nlarge scene: {int(keep.sum())} of {len(smp)} sampled Gaussians compared")
-    assert keep.sum() >= 48, ref["flag"]
-    g_gpu, h_gpu = f["grad"][:, smp].T[keep], f["hz"][:, smp].T[keep]
-    g_ref, h_ref = ref["grad"][keep], ref["hz"][keep]
-    g_mass, h_sens = ref["grad_mass"][keep], ref["hz_sens"][keep]
+    # every sample is compared, with the oracle's allowances for flips of its own
+    # decisions and residual signs (see the benchmark-size test)
+    g_gpu, h_gpu = f["grad"][:, smp].T, f["hz"][:, smp].T
+    g_ref, h_ref = ref["grad"], ref["hz"]
+    g_mass, g_allow = ref["grad_mass"], ref["grad_allow"]
+    h_allow = ref["hz_sens"] + ref["hz_allow"]
     for name, sl in GROUPS.items():
         gs = np.abs(g_ref[:, sl]).max()
         hs = np.abs(h_ref[:, sl]).max()
         g_err = np.abs(g_gpu[:, sl] - g_ref[:, sl])
-        assert g_err.max() <= 1e-4 * gs, name
-        assert np.all(g_err <= 1e-4 * g_mass[:, sl]), name
-        assert np.all(np.abs(h_gpu[:, sl] - h_ref[:, sl]) <= 1e-3 * hs + h_sens[:, sl]), name
+        assert np.all(g_err <= 1e-4 * gs + g_allow[:, sl]), name
+        assert np.all(g_err <= 1e-4 * g_mass[:, sl] + g_allow[:, sl]), name
+        assert np.all(np.abs(h_gpu[:, sl] - h_ref[:, sl]) <= 1e-3 * hs + h_allow[:, sl]), name
