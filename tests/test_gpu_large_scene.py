@@ -60,7 +60,7 @@ def large():
     assert e.read_status() == 0
     out = dict(sc=sc, cam=cam, target=target, t=t, img=img.detach()[0].cpu().numpy(),
                final_T=e.final_T.view(H, W).cpu().numpy(), n_contrib=None, grad=params.grad[:, :N].cpu().numpy(),
-               hz=hz[:, :N].cpu().numpy(), radius=e.rec.view(1, e.n_pad, 12)[0, :N, 10].cpu().numpy().view(np.int32),
+               hz=hz[:, :N].cpu().numpy(),
                peak=peak, state_bytes=5 * e.rows * e.n_pad * 4, loss=float(loss.detach()))
     # n_contrib of the plain render (gn_diagonal re-renders with the same lists)
     out["n_contrib"] = e.n_contrib.view(H, W).cpu().numpy()
@@ -101,9 +101,12 @@ def test_sampled_pixels_match_oracle(large):
 def test_sampled_gaussians_match_oracle(large):
     f = large
     P = O.params64(f["sc"])
-    visible = np.nonzero(f["radius"] > 0)[0]
+    # samples chosen by the oracle's projection: visible, among the nearest fifth
+    pr = O.project(P, DEG, f["cam"])
+    cand = np.nonzero(pr["radius"] > 0)[0]
+    cand = cand[np.argsort(pr["depth"][cand])[: max(64, len(cand) // 5)]]
     rng = np.random.default_rng(9)
-    smp = rng.choice(visible, 64, replace=False)
+    smp = rng.choice(cand, 64, replace=False)
     ref = O.backward_sampled(P, DEG, [f["cam"]], f["target"].astype(np.float64), smp, seed=42, t=f["t"], nu=1)
     # every sample is compared, with the oracle's allowances for flips of its own
     # decisions and residual signs (see the benchmark-size test)
