@@ -838,6 +838,147 @@ def run_configs(device):
     return out
 
 
+def rooflines(eng, per_call, sum_nc, pairs_timed, local, full_size):
+    """The dominant call's roofline and every call's, from per-call CUDA-event
+    times and the work units of the same launches."""
+    import torch
+    hbm, sm_mhz, src = peaks()
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    fp32_peak = fp32_peak_tflops(n_sm, sm_mhz)
+    # every call against its own bound (HBM for the streaming calls, the FP32
+    # pipe for the blends); algorithmic work per unit as documented
+    R = N_VIEWS * eng.n_pad
+    rows = 11 + 3 * (SH_DEG + 1) ** 2
+
+    def bits(v):
+        b = 0
+        while (1 << b) < v:
+            b += 1
+        return b
+    rec_pass = 4
+    pair_pass = max(1, (bits(N_VIEWS * eng.Tx * eng.Ty) + 7) // 8)
+    work = {
+        "project": ("hbm", eng.n * rows * 4 + N_VIEWS * eng.n * 48 * (1 + NU)),
+        # per pair: emit 12 B, 24 B per pass, ranges 8 B; per record: 48 B read and
+        # 28 B written by the count pass (count, key, value, row-table header; the
+        # row entries are not counted), 16 B per pass, 12 B count gather, 16 B
+        # header read by the emit
+        "bin_sort": ("hbm", pairs_timed * (12 + 24 * pair_pass + 8) + R * (48 + 28 + 16 * rec_pass + 12 + 16)),
+        "raster_fwd": ("alu", raster_fwd_flops_per_unit() * sum_nc),
+        "raster_bwd": ("alu", raster_bwd_flops_per_unit() * sum_nc),
+        "update": ("hbm", eng.n * rows * 4 * (5 + 3)),
+    }
+    roof_calls = {}
+    for name, (kind, amount) in work.items():
+        ms_c = per_call[name]
+        if kind == "hbm":
+            ach = amount / (ms_c * 1e-3) / 1e9
+            roof_calls[name] = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                                "bytes": amount, "ms": ms_c}
+        else:
+            ach = amount / (ms_c * 1e-3) / 1e12
+            roof_calls[name] = {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
+                                "frac": ach / fp32_peak, "flop": amount, "ms": ms_c}
+    fwd_ms, bwd_ms = per_call["raster_fwd"], per_call["raster_bwd"]
+    if fwd_ms >= bwd_ms:
+        name, ms_k, per_unit = "gs_raster_fwd (blend + fused JVP, nu=2)", fwd_ms, raster_fwd_flops_per_unit()
+        traffic = None
+    else:
+        name, ms_k, per_unit = "gs_raster_bwd (reverse blend, 1+nu streams, + projection reverse)", bwd_ms, raster_bwd_flops_per_unit()
+        traffic = raster_bwd_traffic() if full_size else None
+    achieved = per_unit * sum_nc / (ms_k * 1e-3) / 1e12
+    roof = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+            "frac": achieved / fp32_peak, "traffic": traffic, "launch_ms": ms_k,
+            "peak_source": (f"{n_sm} SMs (device query) x 128 FP32 lanes x 2 FLOP x {sm_mhz:.0f} MHz "
+                            f"({src} max SM clock)"),
+            "work": (f"{per_unit} FLOP x {sum_nc:.4g} units (sum over pixels of n_contrib, all views, mean of "
+                     f"the steps the call was timed on)")}
+    return roof, roof_calls
+
+
+def dp_steps(eng, cam_dev, targets, my_batches, K, t0, stream, exchange, host_targets=None):
+    """K data-parallel steps on this rank: its view batch of each step (step t
+    takes my_batches[(t - 1) % len]), the eager six calls with the all-reduce of
+    g and hz between the reverse pass and the update.  With host_targets each
+    step's targets are copied from pinned host memory and the loss read back
+    inside the steps.  Returns ms from CUDA events on `stream`."""
+    import torch
+    from paper_2602_00395_gb300.engine import eps_schedule
+    loss_host = torch.zeros(max(K, 1), dtype=torch.float32).pin_memory()
+    dev_tg = torch.empty_like(targets[0]) if host_targets is not None else None
+    a = torch.cuda.Event(enable_timing=True)
+    z = torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        a.record(stream)
+        for k in range(K):
+            t = t0 + k
+            b = my_batches[(t - 1) % len(my_batches)]
+            eng.cams = cam_dev[b]
+            if host_targets is not None:
+                dev_tg.copy_(host_targets[b], non_blocking=True)
+                eng.target = dev_tg
+            else:
+                eng.target = targets[b]
+            eng.step(t, eps_schedule(t, 30000), stream, exchange)
+            if host_targets is not None:
+                loss_host[k:k + 1].copy_(eng.loss_val, non_blocking=True)
+        z.record(stream)
+    z.synchronize()
+    return a.elapsed_time(z)
+
+
+def run_data_parallel(args, ws, rank, local, device):
+    """N ranks split the training over views: every rank holds the same scene and
+    trust-region state and renders its own batch of 8 views per step; the
+    gradients and Hutchinson diagonals are summed over ranks (NCCL all-reduce,
+    weighted by each rank's residual count) before the identical update on every
+    rank.  Weak scaling: each rank's work per step is fixed; value = the view
+    batches all ranks processed per second."""
+    import torch
+    import torch.distributed as dist
+    from paper_2602_00395_gb300.exchange import GradExchange
+    eng, cam_dev, targets, batches, need = make_workload(args.n, device, 0)  # one scene on every rank
+    stream = torch.cuda.Stream(device=device)
+    mine = [b for b in range(len(cam_dev)) if b % ws == rank % len(cam_dev)] or [rank % len(cam_dev)]
+    ex = GradExchange()
+    dp_steps(eng, cam_dev, targets, mine, max(args.warmup, 3), 1, stream, ex)
+    _, per_call = timed_steps(eng, cam_dev, targets, max(2, min(args.steps, 5)), 0, 100, stream, per_call=True)
+    eng.status.zero_()
+    dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ms = dp_steps(eng, cam_dev, targets, mine, args.steps, 1000, stream, ex)
+        torch.cuda.synchronize()
+    host_targets = [tg.cpu().pin_memory() for tg in targets]
+    dist.barrier()
+    e2e_ms = dp_steps(eng, cam_dev, targets, mine, args.steps, 5000, stream, ex, host_targets)
+    tt = torch.tensor([ms, e2e_ms], device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    ms, e2e_ms = (float(v) for v in tt.cpu())
+    sum_nc = per_call.pop("sum_n_contrib")
+    pairs_timed = per_call.pop("pairs")
+    roof, roof_calls = rooflines(eng, per_call, sum_nc, pairs_timed, local, args.n == N_GAUSS)
+    status = eng.read_status()
+    if rank == 0:
+        ms_per_step = ms / args.steps
+        print(json.dumps({
+            "metric": METRIC, "value": ws * args.steps / (ms / 1e3), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_gaussians": args.n, "views_per_step": N_VIEWS * ws,
+                       "views_per_rank": N_VIEWS, "image": f"{W}x{H}", "nu": NU,
+                       "parallelism": f"data-parallel over views, {ws} ranks, NCCL all-reduce of g and hz",
+                       "graph": "eager six calls per step (the all-reduce sits between reverse pass and update)",
+                       "l2": "inputs larger than L2 (236 MB parameters, 199 MB targets per rank and step)"},
+            "per_call_ms": per_call, "status_word": status,
+            "e2e": {"value": ws * args.steps / (e2e_ms / 1e3), "unit": UNIT,
+                    "h2d_bytes_per_step": targets[0].numel() * 4, "d2h_bytes_per_step": 4},
+            # the eager step launches no step counter
+            "gpu_launches": (kernel_launches_per_step(eng) - 1) * args.steps,
+            "roofline": roof, "roofline_calls": roof_calls, "clocks": clk.summary(), "cpu_baseline": None,
+        }))
+
+
 # ------------------------------------------------------------------ main
 def run_cuda(args):
     import torch
@@ -853,6 +994,10 @@ def run_cuda(args):
         torch.distributed.barrier()
     from paper_2602_00395_gb300 import gs3dtr as G
     G.load()
+    if ws > 1 and not args.profile_steps:
+        run_data_parallel(args, ws, rank, local, device)
+        torch.distributed.destroy_process_group()
+        return
     if args.profile_steps:
         eng, cam_dev, targets, batches, need = make_workload(args.n, device, rank, args.profile_views, 2)
         stream = torch.cuda.Stream(device=device)
@@ -933,57 +1078,7 @@ def run_cuda(args):
     torch.cuda.synchronize()
     sum_nc = per_call.pop("sum_n_contrib")
     pairs_timed = per_call.pop("pairs")
-    hbm, sm_mhz, src = peaks()
-    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
-    fp32_peak = fp32_peak_tflops(n_sm, sm_mhz)
-    # every call against its own bound (HBM for the streaming calls, the FP32
-    # pipe for the blends); algorithmic work per unit as documented
-    R = N_VIEWS * eng.n_pad
-    rows = 11 + 3 * (SH_DEG + 1) ** 2
-
-    def bits(v):
-        b = 0
-        while (1 << b) < v:
-            b += 1
-        return b
-    rec_pass = 4
-    pair_pass = max(1, (bits(N_VIEWS * eng.Tx * eng.Ty) + 7) // 8)
-    work = {
-        "project": ("hbm", eng.n * rows * 4 + N_VIEWS * eng.n * 48 * (1 + NU)),
-        # per pair: emit 12 B, 24 B per pass, ranges 8 B; per record: 48 B read and
-        # 28 B written by the count pass (count, key, value, row-table header; the
-        # row entries are not counted), 16 B per pass, 12 B count gather, 16 B
-        # header read by the emit
-        "bin_sort": ("hbm", pairs_timed * (12 + 24 * pair_pass + 8) + R * (48 + 28 + 16 * rec_pass + 12 + 16)),
-        "raster_fwd": ("alu", raster_fwd_flops_per_unit() * sum_nc),
-        "raster_bwd": ("alu", raster_bwd_flops_per_unit() * sum_nc),
-        "update": ("hbm", eng.n * rows * 4 * (5 + 3)),
-    }
-    roof_calls = {}
-    for name, (kind, amount) in work.items():
-        ms_c = per_call[name]
-        if kind == "hbm":
-            ach = amount / (ms_c * 1e-3) / 1e9
-            roof_calls[name] = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                                "bytes": amount, "ms": ms_c}
-        else:
-            ach = amount / (ms_c * 1e-3) / 1e12
-            roof_calls[name] = {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
-                                "frac": ach / fp32_peak, "flop": amount, "ms": ms_c}
-    fwd_ms, bwd_ms = per_call["raster_fwd"], per_call["raster_bwd"]
-    if fwd_ms >= bwd_ms:
-        name, ms_k, per_unit = "gs_raster_fwd (blend + fused JVP, nu=2)", fwd_ms, raster_fwd_flops_per_unit()
-        traffic = None
-    else:
-        name, ms_k, per_unit = "gs_raster_bwd (reverse blend, 1+nu streams, + projection reverse)", bwd_ms, raster_bwd_flops_per_unit()
-        traffic = raster_bwd_traffic() if args.n == N_GAUSS else None
-    achieved = per_unit * sum_nc / (ms_k * 1e-3) / 1e12
-    roof = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-            "frac": achieved / fp32_peak, "traffic": traffic, "launch_ms": ms_k,
-            "peak_source": (f"{n_sm} SMs (device query) x 128 FP32 lanes x 2 FLOP x {sm_mhz:.0f} MHz "
-                            f"({src} max SM clock)"),
-            "work": (f"{per_unit} FLOP x {sum_nc:.4g} units (sum over pixels of n_contrib, all views, mean of "
-                     f"the steps the call was timed on)")}
+    roof, roof_calls = rooflines(eng, per_call, sum_nc, pairs_timed, local, args.n == N_GAUSS)
     clocks = clk.summary()
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

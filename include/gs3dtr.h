@@ -345,6 +345,56 @@ gs_status gs_adam_tr_update(gs_params* x, gs_params* m, gs_params* v, const gs_p
  * training loop replayed as a CUDA graph). */
 gs_status gs_step_advance(int64_t* t_device, void* stream);
 
+/* ------------------------------------------------------------ batches
+ * Several independent requests in shared launches (no paper counterpart: the
+ * paper trains one scene at a time, Sec. 5).  A batch holds up to GS_BATCH_MAX
+ * items of one image size; item b is one view of its own scene, with its own
+ * parameters, step index and trust-region state.  The batch's splat records sit
+ * in slot b of one set of buffers (records of item b at [b * n_pad_max, ...)),
+ * so gs_bin_sort and gs_raster_fwd run on it unchanged as a frame of
+ * frame.n_views = n_items views; each item's objective is its own view's
+ * (m = 3 H W).  A training step of a batch is
+ *   gs_project_batch -> gs_bin_sort -> gs_raster_fwd -> gs_raster_bwd_batch
+ *   -> gs_tr_update_batch,
+ * a render the first three.  All items share the SH degree, the tile shape
+ * and the probe seed and count; n_pad_max >= every item's n, a multiple of 4. */
+enum { GS_BATCH_MAX = 16 };
+
+typedef struct gs_batch_item {
+  gs_params x;             /* device: the scene's parameters */
+  gs_params grad, hz;      /* device: its gradient and Hutchinson diagonal (written; hz.data NULL without probes) */
+  gs_params g_ema, d_ema;  /* device: its trust-region state (gs_tr_update_batch updates both in place) */
+  const gs_camera* cam;    /* device: the item's camera */
+  int64_t t;               /* the scene's step index t >= 1: probes and curvature interval */
+  float eps;               /* the radius parameter eps_t of its update */
+  int32_t hvp;             /* 1: its update takes d_ema from hz ((t - 1) % l == 0), 0: keeps d_ema */
+} gs_batch_item;
+
+/* gs_project for a batch: item b's Gaussians projected into its camera, records
+ * (and, with probe, probe->nu tangent records along its probes of step
+ * items[b].t) in slot b; columns n..n_pad_max - 1 of a slot are written culled.
+ * items: host array of n_items (1..GS_BATCH_MAX); frame.n_views = n_items. */
+gs_status gs_project_batch(const gs_batch_item* items, int32_t n_items, int32_t n_pad_max, gs_frame frame,
+                           const gs_probe* probe, gs_projected* out, int32_t* status, void* stream);
+
+/* gs_raster_bwd for a batch (Sec. 4.1 per item): item b's gradient
+ * (1/m) J^T F of its own view's objective (m = 3 H W) into items[b].grad and,
+ * with image_tangent and probe, its Hutchinson diagonal into items[b].hz
+ * (overwritten).  loss_out: NULL or n_items floats, item b's objective added
+ * to loss_out[b].  workspace from gs_raster_bwd_workspace_size(n_pad_max,
+ * frame, nu).  The remaining arguments are those of gs_raster_bwd on the batch's
+ * frame. */
+gs_status gs_raster_bwd_batch(const gs_batch_item* items, int32_t n_items, int32_t n_pad_max, gs_frame frame,
+                              const gs_projected* proj, const gs_sorted* sorted, const float* image,
+                              const float* target, const float* final_T, const uint32_t* n_contrib,
+                              const float* image_tangent, const gs_probe* probe, gs_loss loss, float* loss_out,
+                              void* workspace, size_t workspace_bytes, int32_t* status, void* stream);
+
+/* gs_tr_update for a batch: Algorithm 1 on each item's scene with its own t,
+ * eps and hvp (Sec. 4.2, App. B), one launch for all items. */
+gs_status gs_tr_update_batch(const gs_batch_item* items, int32_t n_items, const gs_tr_config* cfg, int32_t* status,
+                             void* stream);
+
 /* Diagnostics (no paper counterpart): runs, in one warp, the bounded wait that
  * every kernel uses on its asynchronous copies, on an mbarrier that nothing
  * completes, giving up after `limit` tries (1 <= limit <= 2^20).  Raises

@@ -61,13 +61,13 @@ def lib():
             L.or_jacobian.argtypes = [P, i64, i64, i32, P, i32, i32, i32, P]
             L.or_backward_dssim.restype = d
             L.or_backward_dssim.argtypes = [P, i64, i64, i32, P, i32, i32, i32, P, d, d, u64, C.c_int64, i32,
-                                            P, P, P, P, P, P, P]
+                                            P, P, P, P, P, P, P, P, P]
             L.or_ssim.argtypes = [P, P, i32, i32, P, P, P, P]
             L.or_ssim_vjp.argtypes = [P, P, i32, i32, P, P]
             L.or_ssim_jvp.argtypes = [P, P, i32, i32, P, P]
             L.or_backward.restype = d
             L.or_backward.argtypes = [P, i64, i64, i32, P, i32, i32, i32, P, i32, d, u64, C.c_int64, i32,
-                                      P, P, P, P, P, P, P, P, P]
+                                      P, P, P, P, P, P, P, P, P, P, P]
             L.or_shd_radius.argtypes = [P, i64, i64, i32, d, P, P]
             L.or_tr_update.argtypes = [P, P, P, P, P, i64, i64, i32, P, C.c_int64, d, P]
             L.or_adam_tr_update.argtypes = [P, P, P, P, i64, i64, i32, P, P, C.c_int64, d, P]
@@ -75,7 +75,7 @@ def lib():
             L.or_render_pixels.argtypes = [P, i64, i64, i32, P, i32, i32, i64, P, P, u64, C.c_int64, i32, P, P, P,
                                            P, P, P, P, P, P]
             L.or_backward_sampled.argtypes = [P, i64, i64, i32, P, i32, i32, i32, P, i32, d, u64, C.c_int64, i32,
-                                              i64, P, P, P, P, d, P, P, P, P, P]
+                                              i64, P, P, P, P, d, P, P, P, P, P, P, P]
             L.or_signature.argtypes = [P, i64, i64, i32, P, i32, i32, i32, P]
             L.or_hellinger.restype = d
             L.or_hellinger.argtypes = [P, P, d, P, P, d]
@@ -295,7 +295,9 @@ def backward(P: np.ndarray, deg: int, cams, target: np.ndarray, *, loss_kind: in
     for the L1 loss hz_sens, the bound on how far each Hutchinson entry moves
     when each residual moves by its pixel's FP32 rounding bound, and
     grad_allow / hz_allow, how far each entry may move when a decision of its
-    Gaussian's own (or, for the L1 gradient, a residual sign) flips in FP32."""
+    Gaussian's own (or, for the L1 gradient, a residual sign) flips in FP32,
+    and grad_round / hz_round, the rounding its terms carry under the oracle's
+    model of the FP32 records."""
     P = _f64(P)
     rows, n = P.shape
     ca = camera_array(cams)
@@ -311,15 +313,18 @@ def backward(P: np.ndarray, deg: int, cams, target: np.ndarray, *, loss_kind: in
     hs = np.zeros((rows, n)) if (masses and nu > 0 and loss_kind == 0) else None
     ga = np.zeros((rows, n)) if masses else None
     ha = np.zeros((rows, n)) if (masses and nu > 0) else None
+    gr = np.zeros((rows, n)) if masses else None
+    hr = np.zeros((rows, n)) if (masses and nu > 0) else None
     if loss_kind == 2:
         f = lib().or_backward_dssim(_p(P), n, n, deg, _p(ca), V, tw, th, _p(tg), lam, gn_floor, seed, t, nu,
-                                    _p(grad), _p(hz), _p(it), _p(gm), _p(hm), _p(ga), _p(ha))
+                                    _p(grad), _p(hz), _p(it), _p(gm), _p(hm), _p(ga), _p(ha), _p(gr), _p(hr))
         rm = None
     else:
         f = lib().or_backward(_p(P), n, n, deg, _p(ca), V, tw, th, _p(tg), loss_kind, gn_floor, seed, t, nu,
-                              _p(grad), _p(hz), _p(it), _p(rm), _p(gm), _p(hm), _p(hs), _p(ga), _p(ha))
+                              _p(grad), _p(hz), _p(it), _p(rm), _p(gm), _p(hm), _p(hs), _p(ga), _p(ha), _p(gr),
+                              _p(hr))
     return dict(loss=float(f), grad=grad, hz=hz, image_tangent=it, res_margin=rm, grad_mass=gm, hz_mass=hm,
-                hz_sens=hs, grad_allow=ga, hz_allow=ha)
+                hz_sens=hs, grad_allow=ga, hz_allow=ha, grad_round=gr, hz_round=hr)
 
 
 def ssim(x: np.ndarray, y: np.ndarray):
@@ -423,7 +428,9 @@ def backward_sampled(P: np.ndarray, deg: int, cams, target: np.ndarray, samples,
     residual moves by the FP32 rounding bound of its pixel's colour (capped at
     eps_img), and grad_allow / hz_allow, how far each entry may move when a
     decision of the sample's own (or a residual sign, for the gradient) flips in
-    FP32 somewhere in its footprint.  eps_img: the image tolerance."""
+    FP32 somewhere in its footprint, and grad_round / hz_round, the rounding its
+    terms carry under the oracle's model of the FP32 records.  eps_img: the
+    image tolerance."""
     P = _f64(P)
     rows, n = P.shape
     tg = _f64(target)
@@ -432,11 +439,10 @@ def backward_sampled(P: np.ndarray, deg: int, cams, target: np.ndarray, samples,
     grad = np.zeros((k, rows))
     hz = np.zeros((k, rows))
     flag = np.zeros(k, np.int32)
-    gm, hm, hs, ga, ha = (np.zeros((k, rows)) for _ in range(5))
+    gm, hm, hs, ga, ha, gr, hr = (np.zeros((k, rows)) for _ in range(7))
+    h = (lambda a: a) if nu > 0 else (lambda a: None)
     lib().or_backward_sampled(_p(P), n, n, deg, _p(camera_array(cams)), len(cams), tw, th, _p(tg), loss_kind,
-                              gn_floor, seed, t, nu, k, _p(smp), _p(grad), _p(hz if nu > 0 else None), _p(flag),
-                              eps_img, _p(gm), _p(hm if nu > 0 else None), _p(hs if nu > 0 else None), _p(ga),
-                              _p(ha if nu > 0 else None))
-    return dict(grad=grad, hz=hz if nu > 0 else None, flag=flag, grad_mass=gm,
-                hz_mass=hm if nu > 0 else None, hz_sens=hs if nu > 0 else None, grad_allow=ga,
-                hz_allow=ha if nu > 0 else None)
+                              gn_floor, seed, t, nu, k, _p(smp), _p(grad), _p(h(hz)), _p(flag), eps_img, _p(gm),
+                              _p(h(hm)), _p(h(hs)), _p(ga), _p(h(ha)), _p(gr), _p(h(hr)))
+    return dict(grad=grad, hz=h(hz), flag=flag, grad_mass=gm, hz_mass=h(hm), hz_sens=h(hs), grad_allow=ga,
+                hz_allow=h(ha), grad_round=gr, hz_round=h(hr))

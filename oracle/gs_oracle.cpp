@@ -1138,8 +1138,11 @@ void blend_reverse(const std::vector<Contrib>& tr, const std::vector<Splat<doubl
 // term, where dC/da's two parts (c T and the suffix over 1 - a) count by their
 // absolute values.  Summed over pixels this is the mass that an FP32 sum of the
 // same terms rounds against (the terms' own rounding scales with it too).
+struct TraceRounding;
+double tr_rel(const TraceRounding* r, size_t k);
+double tr_dS(const TraceRounding* r, size_t k);
 void blend_reverse_abs(const std::vector<Contrib>& tr, const std::vector<Splat<double>>& sp, const double w[3],
-                       double* cot) {
+                       double* cot, const TraceRounding* rnd = nullptr) {
   std::vector<double> suffix(3 * (tr.size() + 1), 0.0);
   for (long k = (long)tr.size() - 1; k >= 0; --k)
     for (int ch = 0; ch < 3; ++ch)
@@ -1147,16 +1150,21 @@ void blend_reverse_abs(const std::vector<Contrib>& tr, const std::vector<Splat<d
   for (size_t k = 0; k < tr.size(); ++k) {
     const Contrib& e = tr[k];
     const Splat<double>& g = sp[e.i];
-    double ga = 0.0;
-    for (int ch = 0; ch < 3; ++ch)
+    double ga = 0.0, wsum = 0.0;
+    for (int ch = 0; ch < 3; ++ch) {
       ga += std::fabs(w[ch]) * (std::fabs(g.rgb[ch]) * e.T + suffix[3 * (k + 1) + ch] / (1.0 - e.alpha));
+      wsum += std::fabs(w[ch]);
+    }
     double* c = cot + (long)e.i * NQ;
-    c[Q_R] += std::fabs(w[0]) * e.alpha * e.T;
-    c[Q_G] += std::fabs(w[1]) * e.alpha * e.T;
-    c[Q_BL] += std::fabs(w[2]) * e.alpha * e.T;
+    const double f = rnd ? tr_rel(rnd, k) : 1.0;
+    // with a rounding model, the suffix changes of flips behind it come on top
+    if (rnd) ga += wsum * tr_dS(rnd, k) / (1.0 - e.alpha) / f;
+    c[Q_R] += f * std::fabs(w[0]) * e.alpha * e.T;
+    c[Q_G] += f * std::fabs(w[1]) * e.alpha * e.T;
+    c[Q_BL] += f * std::fabs(w[2]) * e.alpha * e.T;
     if (e.capped) continue;
-    double gpow = ga * e.alpha;
-    c[Q_O] += ga * e.G;
+    double gpow = f * ga * e.alpha;
+    c[Q_O] += f * ga * e.G;
     c[Q_A] += 0.5 * e.dx * e.dx * gpow;
     c[Q_B] += std::fabs(e.dx * e.dy) * gpow;
     c[Q_C] += 0.5 * e.dy * e.dy * gpow;
@@ -1164,6 +1172,52 @@ void blend_reverse_abs(const std::vector<Contrib>& tr, const std::vector<Splat<d
     c[Q_MY] += (std::fabs(g.C * e.dy) + std::fabs(g.B * e.dx)) * gpow;
   }
 }
+
+// What the FP32 evaluation of each trace entry's terms may differ by, under the
+// model of power_uncertainty: rel[k], relative, from its alpha's rounding (0
+// when capped), the accumulated rounding of the transmittance in front of it,
+// the relative change a_j / (1 - a_j) of that transmittance for every splat j in
+// front of it whose own decision may flip (flips, in walk order, from
+// blend_flips), and for the suffix of the splats behind it that dC/dalpha uses,
+// the largest of theirs; dS[k], absolute, the change a_j T_j (c_j + c_max) of
+// that suffix from the splats behind it whose decisions may flip.
+struct TraceRounding {
+  std::vector<double> rel, dS;
+};
+TraceRounding trace_rounding(const std::vector<Contrib>& tr, const std::vector<Splat<double>>& sp,
+                             const std::vector<OwnFlip>& flips, double cmax) {
+  TraceRounding r;
+  r.rel.assign(tr.size(), 0.0);
+  r.dS.assign(tr.size(), 0.0);
+  auto key_less = [&](int a, int b) {
+    const float da = (float)sp[a].depth, db = (float)sp[b].depth;
+    return da < db || (da == db && a < b);
+  };
+  double tun = 0.0, front = 0.0;
+  size_t f = 0;
+  for (size_t k = 0; k < tr.size(); ++k) {
+    const Contrib& e = tr[k];
+    for (; f < flips.size() && key_less(flips[f].i, e.i); ++f) front += flips[f].a / (1.0 - flips[f].a);
+    const double da = e.capped ? 0.0 : power_uncertainty(sp[e.i], e.dx, e.dy) + 2e-6;
+    r.rel[k] = da + tun + front + 2e-7;
+    tun += da * e.alpha / (1.0 - e.alpha) + 2e-7;
+  }
+  for (long k = (long)tr.size() - 2; k >= 0; --k) r.rel[k] = std::max(r.rel[k], r.rel[k + 1]);
+  // suffix changes: flips behind entry k, walked back to front
+  double behind = 0.0;
+  long g = (long)flips.size() - 1;
+  for (long k = (long)tr.size() - 1; k >= 0; --k) {
+    for (; g >= 0 && key_less(tr[k].i, flips[g].i); --g) {
+      const OwnFlip& q = flips[g];
+      const double cq = std::max({sp[q.i].rgb[0], sp[q.i].rgb[1], sp[q.i].rgb[2], 0.0});
+      behind += q.a * q.T * (cq + cmax);
+    }
+    r.dS[k] = behind;
+  }
+  return r;
+}
+double tr_rel(const TraceRounding* r, size_t k) { return r->rel[k]; }
+double tr_dS(const TraceRounding* r, size_t k) { return r->dS[k]; }
 
 // Parameter cotangent of splat i: sum_q cot_q d(splat_q)/d(param_r), with the
 // projection Jacobian taken column by column in forward mode.
@@ -1607,7 +1661,7 @@ double backward_impl(const double* P, long pitch, long n, int deg, const double*
                      int th, const double* target, int loss_kind, double lambda, double gn_floor, uint64_t seed,
                      int64_t t, int nu, double* grad, double* hz, double* img_tan, double* res_margin,
                      double* grad_mass, double* hz_mass, double* hz_sens = nullptr, double* grad_allow = nullptr,
-                     double* hz_allow = nullptr) {
+                     double* hz_allow = nullptr, double* grad_round = nullptr, double* hz_round = nullptr) {
   int rows = n_rows(deg);
   double m = 0.0;
   std::vector<View> views;
@@ -1623,6 +1677,8 @@ double backward_impl(const double* P, long pitch, long n, int deg, const double*
   if (hz_sens) for (long k = 0; k < (long)rows * n; ++k) hz_sens[k] = 0.0;
   if (grad_allow) for (long k = 0; k < (long)rows * n; ++k) grad_allow[k] = 0.0;
   if (hz_allow) for (long k = 0; k < (long)rows * n; ++k) hz_allow[k] = 0.0;
+  if (grad_round) for (long k = 0; k < (long)rows * n; ++k) grad_round[k] = 0.0;
+  if (hz_round) for (long k = 0; k < (long)rows * n; ++k) hz_round[k] = 0.0;
   const bool sensing = hz_sens != nullptr && loss_kind == 0 && nu > 0;
   const bool allowing = grad_allow != nullptr;
 
@@ -1646,7 +1702,9 @@ double backward_impl(const double* P, long pitch, long n, int deg, const double*
     std::vector<std::vector<double>> cot_abs(masses ? 1 + nu : 0, std::vector<double>((size_t)n * NQ, 0.0));
     std::vector<std::vector<double>> cot_sens(sensing ? nu : 0, std::vector<double>((size_t)n * NQ, 0.0));
     std::vector<std::vector<double>> cot_allow(allowing ? 1 + nu : 0, std::vector<double>((size_t)n * NQ, 0.0));
+    std::vector<std::vector<double>> cot_round(allowing ? 1 + nu : 0, std::vector<double>((size_t)n * NQ, 0.0));
     std::vector<OwnFlip> ofl;
+    TraceRounding trel;
     std::vector<std::vector<double>> jz(nu, std::vector<double>(3 * HW, 0.0));
     for (int k = 0; k < nu; ++k) {
       std::vector<Splat<Dual>> sd = project_tangent(V, P, pitch, n, deg, z[k].data());
@@ -1735,6 +1793,8 @@ double backward_impl(const double* P, long pitch, long n, int deg, const double*
         for (int ch = 0; ch < 3; ++ch)
           wflip[ch] = (loss_kind == 0 && std::fabs(C[ch] - tg[ch * HW + px]) < kImageTol) ? 2.0 * w[ch] : 0.0;
         blend_reverse_abs(tr, V.sp, wflip, cot_allow[0].data());
+        trel = trace_rounding(tr, V.sp, ofl, V.tile_cmax[tile]);
+        blend_reverse_abs(tr, V.sp, w, cot_round[0].data(), &trel);
       }
       for (int k = 0; k < nu; ++k) {
         double wk[3];
@@ -1747,9 +1807,11 @@ double backward_impl(const double* P, long pitch, long n, int deg, const double*
           for (int ch = 0; ch < 3; ++ch) ws[ch] = wk[ch] * sens[ch];
           blend_reverse_abs(tr, V.sp, ws, cot_sens[k].data());
         }
-        if (allowing)
+        if (allowing) {
           for (const OwnFlip& q : ofl)
             own_terms(V.sp[q.i], q, V.tile_cmax[tile], wk, cot_allow[1 + k].data() + q.i * NQ);
+          blend_reverse_abs(tr, V.sp, wk, cot_round[1 + k].data(), &trel);
+        }
       }
     });
     for (long i = 0; i < n; ++i) {
@@ -1758,7 +1820,8 @@ double backward_impl(const double* P, long pitch, long n, int deg, const double*
         const double* c = cot[s].data() + i * NQ;
         bool any = false;
         for (int q = 0; q < NQ; ++q)
-          any = any || c[q] != 0.0 || (allowing && cot_allow[s][(size_t)i * NQ + q] != 0.0);
+          any = any || c[q] != 0.0 || (allowing && (cot_allow[s][(size_t)i * NQ + q] != 0.0 ||
+                                                    cot_round[s][(size_t)i * NQ + q] != 0.0));
         if (!any) continue;
         std::fill(g_acc.begin(), g_acc.end(), 0.0);
         project_reverse(P, pitch, i, deg, V.cam, c, g_acc);
@@ -1775,6 +1838,12 @@ double backward_impl(const double* P, long pitch, long n, int deg, const double*
           std::fill(g_acc.begin(), g_acc.end(), 0.0);
           project_reverse_abs(P, pitch, i, deg, V.cam, cot_allow[s].data() + i * NQ, g_acc);
           for (int r = 0; r < rows; ++r) (s == 0 ? grad_allow : hz_allow)[(long)r * n + i] += g_acc[r] / (s == 0 ? 1 : nu);
+        }
+        double* rout = s == 0 ? grad_round : hz_round;
+        if (allowing && rout) {
+          std::fill(g_acc.begin(), g_acc.end(), 0.0);
+          project_reverse_abs(P, pitch, i, deg, V.cam, cot_round[s].data() + i * NQ, g_acc);
+          for (int r = 0; r < rows; ++r) rout[(long)r * n + i] += g_acc[r] / (s == 0 ? 1 : nu);
         }
         if (!masses || (s > 0 && !hz_mass)) continue;
         std::fill(g_acc.begin(), g_acc.end(), 0.0);
@@ -1793,17 +1862,19 @@ double backward_impl(const double* P, long pitch, long n, int deg, const double*
 double or_backward(const double* P, long pitch, long n, int deg, const double* cams, int n_views, int tw,
                    int th, const double* target, int loss_kind, double gn_floor, uint64_t seed, int64_t t,
                    int nu, double* grad, double* hz, double* img_tan, double* res_margin, double* grad_mass,
-                   double* hz_mass, double* hz_sens, double* grad_allow, double* hz_allow) {
+                   double* hz_mass, double* hz_sens, double* grad_allow, double* hz_allow, double* grad_round,
+                   double* hz_round) {
   return backward_impl(P, pitch, n, deg, cams, n_views, tw, th, target, loss_kind, 0.0, gn_floor, seed, t, nu,
-                       grad, hz, img_tan, res_margin, grad_mass, hz_mass, hz_sens, grad_allow, hz_allow);
+                       grad, hz, img_tan, res_margin, grad_mass, hz_mass, hz_sens, grad_allow, hz_allow, grad_round,
+                       hz_round);
 }
 
 double or_backward_dssim(const double* P, long pitch, long n, int deg, const double* cams, int n_views, int tw,
                          int th, const double* target, double lambda, double gn_floor, uint64_t seed, int64_t t,
                          int nu, double* grad, double* hz, double* img_tan, double* grad_mass, double* hz_mass,
-                         double* grad_allow, double* hz_allow) {
+                         double* grad_allow, double* hz_allow, double* grad_round, double* hz_round) {
   return backward_impl(P, pitch, n, deg, cams, n_views, tw, th, target, 2, lambda, gn_floor, seed, t, nu, grad, hz,
-                       img_tan, nullptr, grad_mass, hz_mass, nullptr, grad_allow, hz_allow);
+                       img_tan, nullptr, grad_mass, hz_mass, nullptr, grad_allow, hz_allow, grad_round, hz_round);
 }
 
 // SSIM map of one channel and its partials (for the pins), and the adjoint and
@@ -2009,12 +2080,14 @@ void or_render_pixels(const double* P, long pitch, long n, int deg, const double
 // visible (its 1/255 skip, its cap, its power sign, or its membership in the
 // tile's list), or a residual sign flips there (gradient only, 2 |dL/dC|): at
 // each such pixel, the absolute values of the terms the sample adds there with
-// its alpha uncapped, carried through project_reverse_abs.
+// its alpha uncapped, carried through project_reverse_abs.  grad_round,
+// hz_round (may be null): the rounding its terms carry everywhere under the
+// model of trace_rounding, the same way.
 void or_backward_sampled(const double* P, long pitch, long n, int deg, const double* cams, int n_views, int tw,
                          int th, const double* target, int loss_kind, double gn_floor, uint64_t seed, int64_t t,
                          int nu, long ns, const int64_t* samples, double* grad_out, double* hz_out, int32_t* flag,
                          double eps_img, double* grad_mass, double* hz_mass, double* hz_sens, double* grad_allow,
-                         double* hz_allow) {
+                         double* hz_allow, double* grad_round, double* hz_round) {
   int rows = n_rows(deg);
   double m = 0.0;
   for (int v = 0; v < n_views; ++v) {
@@ -2029,6 +2102,8 @@ void or_backward_sampled(const double* P, long pitch, long n, int deg, const dou
     if (hz_sens) hz_sens[k] = 0.0;
     if (grad_allow) grad_allow[k] = 0.0;
     if (hz_allow) hz_allow[k] = 0.0;
+    if (grad_round) grad_round[k] = 0.0;
+    if (hz_round) hz_round[k] = 0.0;
   }
   const bool masses = grad_mass || hz_mass || hz_sens;
   const bool allow = grad_allow != nullptr;
@@ -2055,6 +2130,10 @@ void or_backward_sampled(const double* P, long pitch, long n, int deg, const dou
     std::vector<std::vector<double>> cab(masses ? 1 + 2 * nu : 0, std::vector<double>((size_t)n * NQ, 0.0));
     // allowances per sample and stream (0 the gradient, 1..nu the probes), NQ each
     std::vector<double> al(allow ? (size_t)ns * (1 + nu) * NQ : 0, 0.0);
+    // the rounding of every splat's terms, per stream (n x NQ each)
+    std::vector<std::vector<double>> cround(allow ? 1 + nu : 0, std::vector<double>((size_t)n * NQ, 0.0));
+    TraceRounding trel;
+    std::vector<OwnFlip> pflips;
     struct Own {
       long sidx;
       double a, G, dx, dy, T;
@@ -2084,8 +2163,10 @@ void or_backward_sampled(const double* P, long pitch, long n, int deg, const dou
             blend(list, V.sp, x + 0.5, y + 0.5, C, T, nc, &mg, &tr);
             long px = (long)y * V.cam.W + x;
             double w[3], wgn[3], sens[3], rmin = kInf;
+            pflips.clear();
             const double e_px =
-                masses ? std::min(blend_flips(V, (size_t)ty * V.Tx + tx, x + 0.5, y + 0.5, nc).err, eps_img)
+                masses ? std::min(blend_flips(V, (size_t)ty * V.Tx + tx, x + 0.5, y + 0.5, nc, &pflips).err,
+                                  eps_img)
                        : 0.0;
             for (int ch = 0; ch < 3; ++ch) {
               double r = C[ch] - tg[ch * HW + px];
@@ -2149,6 +2230,8 @@ void or_backward_sampled(const double* P, long pitch, long n, int deg, const dou
                 if (q.own) own_add(q, w, out);
                 own_add(q, wflip, out);
               }
+              trel = trace_rounding(tr, V.sp, pflips, own_cmax);
+              blend_reverse_abs(tr, V.sp, w, cround[0].data(), &trel);
             }
             for (int k = 0; k < nu; ++k) {
               Dual Cd[3], Td;
@@ -2159,9 +2242,11 @@ void or_backward_sampled(const double* P, long pitch, long n, int deg, const dou
                 wk[ch] = wgn[ch] * Cd[ch].d;
                 ws[ch] = wk[ch] * sens[ch];
               }
-              if (allow)
+              if (allow) {
                 for (const Own& q : owns)
                   if (q.own) own_add(q, wk, al.data() + ((size_t)q.sidx * (1 + nu) + 1 + k) * NQ);
+                blend_reverse_abs(tr, V.sp, wk, cround[1 + k].data(), &trel);
+              }
               blend_reverse(tr, V.sp, wk, cot[1 + k].data());
               if (masses) {
                 blend_reverse_abs(tr, V.sp, wk, cab[1 + k].data());
@@ -2192,8 +2277,13 @@ void or_backward_sampled(const double* P, long pitch, long n, int deg, const dou
         std::fill(g_acc.begin(), g_acc.end(), 0.0);
         project_reverse_abs(P, pitch, i, deg, V.cam, al.data() + ((size_t)sidx * (1 + nu) + st) * NQ, g_acc);
         double* out = st == 0 ? grad_allow : hz_allow;
-        if (!out) continue;
-        for (int r = 0; r < rows; ++r) out[sidx * rows + r] += g_acc[r] / (st == 0 ? 1.0 : nu);
+        if (out)
+          for (int r = 0; r < rows; ++r) out[sidx * rows + r] += g_acc[r] / (st == 0 ? 1.0 : nu);
+        std::fill(g_acc.begin(), g_acc.end(), 0.0);
+        project_reverse_abs(P, pitch, i, deg, V.cam, cround[st].data() + (size_t)i * NQ, g_acc);
+        out = st == 0 ? grad_round : hz_round;
+        if (out)
+          for (int r = 0; r < rows; ++r) out[sidx * rows + r] += g_acc[r] / (st == 0 ? 1.0 : nu);
       }
     }
     img_off += 3 * HW;

@@ -64,6 +64,52 @@ inline ProbeArg probe_arg(const gs_probe* p) {
 }
 __device__ __forceinline__ int64_t probe_step(const ProbeArg& a) { return a.t_dev ? *a.t_dev : a.t; }
 
+// The items of a batch (gs_batch_item) as one kernel argument, with the first
+// block of each item's share of a launch (first_block[n_items] = the grid).
+struct BatchArg {
+  int n_items;
+  int first_block[GS_BATCH_MAX + 1];
+  const float* P[GS_BATCH_MAX];
+  int n[GS_BATCH_MAX], n_pad[GS_BATCH_MAX];
+  const gs_camera* cam[GS_BATCH_MAX];
+  int64_t t[GS_BATCH_MAX];
+  float* grad[GS_BATCH_MAX];
+  float* hz[GS_BATCH_MAX];
+  float* ge[GS_BATCH_MAX];
+  float* de[GS_BATCH_MAX];
+  float eps[GS_BATCH_MAX];
+  int hvp[GS_BATCH_MAX];
+};
+// The item whose share of the launch holds block `blk`.
+__device__ __forceinline__ int batch_item(const BatchArg& ba, int blk) {
+  int b = 0;
+  while (b + 1 < ba.n_items && blk >= ba.first_block[b + 1]) ++b;
+  return b;
+}
+// Host: the batch argument of items[0..n_items), blocks_of(item) blocks each.
+template <class F>
+BatchArg batch_arg(const gs_batch_item* items, int n_items, F blocks_of) {
+  BatchArg a{};
+  a.n_items = n_items;
+  a.first_block[0] = 0;
+  for (int b = 0; b < n_items; ++b) {
+    const gs_batch_item& it = items[b];
+    a.P[b] = it.x.data;
+    a.n[b] = it.x.n;
+    a.n_pad[b] = it.x.n_pad;
+    a.cam[b] = it.cam;
+    a.t[b] = it.t;
+    a.grad[b] = it.grad.data;
+    a.hz[b] = it.hz.data;
+    a.ge[b] = it.g_ema.data;
+    a.de[b] = it.d_ema.data;
+    a.eps[b] = it.eps;
+    a.hvp[b] = it.hvp;
+    a.first_block[b + 1] = a.first_block[b] + blocks_of(it);
+  }
+  return a;
+}
+
 // Signs of Rademacher probe k at step t for the rows [0, rows) of Gaussian i:
 // bit r is set where entry j = i * rows + r is -1.  Entry j is bit j mod 64 of
 // the hash of word j / 64 (64 entries per hash), so the rows of one Gaussian

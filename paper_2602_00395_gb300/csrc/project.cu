@@ -37,27 +37,28 @@ __device__ __forceinline__ void store_culled(float4* rec, size_t at) {
 #define GS_PROJ_BOUNDS __launch_bounds__(128)
 #endif
 
+// Column i of the parameter matrix P (n Gaussians, row pitch n_pad) projected
+// into views cams[0..V): record v * pitch + i of rec, tangent records
+// (v * NU + k) * pitch + i of tan; columns n <= i < pitch are written culled.
+// Called by every thread of a 128-thread block (the SH staging is block-wide).
 template <int DEG, int NU>
-__global__ void GS_PROJ_BOUNDS project_kernel(const float* __restrict__ P, int n, int n_pad,
-                                                      const gs_camera* __restrict__ cams, gs_frame fr,
-                                                      ProbeArg pa, float4* __restrict__ rec,
-                                                      float4* __restrict__ tan) {
+__device__ __forceinline__ void project_column(const float* __restrict__ P, int n, int n_pad, int i, int pitch,
+                                               const gs_camera* __restrict__ cams, int V, gs_frame fr, ProbeArg pa,
+                                               float4* __restrict__ rec, float4* __restrict__ tan) {
   using S = typename std::conditional<NU == 0, float, Dn<(NU > 0 ? NU : 1)>>::type;
   constexpr int K = (DEG + 1) * (DEG + 1);
   constexpr int ROWS = kRowSH + 3 * K;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
   // the block's SH coefficients, staged once and read per view from shared
   // memory (volatile: re-read, not held in registers across the view loop)
   __shared__ float s_sh[3 * K][128];
   for (int r = 0; r < 3 * K; ++r) s_sh[r][threadIdx.x] = i < n ? P[(size_t)(kRowSH + r) * n_pad + i] : 0.f;
   __syncthreads();
   const volatile float* vsh = &s_sh[0][0];
-  if (i >= n_pad) return;
-  const int V = fr.n_views;
+  if (i >= pitch) return;
   if (i >= n) {
     for (int v = 0; v < V; ++v) {
-      store_culled(rec, (size_t)v * n_pad + i);
-      for (int k = 0; k < NU; ++k) store_culled(tan, ((size_t)v * NU + k) * n_pad + i);
+      store_culled(rec, (size_t)v * pitch + i);
+      for (int k = 0; k < NU; ++k) store_culled(tan, ((size_t)v * NU + k) * pitch + i);
     }
     return;
   }
@@ -115,7 +116,7 @@ __global__ void GS_PROJ_BOUNDS project_kernel(const float* __restrict__ P, int n
 #pragma unroll 1
   for (int v = 0; v < V; ++v) {
     const gs_camera* c = cams + v;
-    const size_t at = (size_t)v * n_pad + i;
+    const size_t at = (size_t)v * pitch + i;
     float Rc[3][3], tc[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -129,7 +130,7 @@ __global__ void GS_PROJ_BOUNDS project_kernel(const float* __restrict__ P, int n
     S t2 = Rc[2][0] * mu0 + Rc[2][1] * mu1 + Rc[2][2] * mu2 + tc[2];
     if (!(val(t2) > c->near_plane)) {
       store_culled(rec, at);
-      for (int k = 0; k < NU; ++k) store_culled(tan, ((size_t)v * NU + k) * n_pad + i);
+      for (int k = 0; k < NU; ++k) store_culled(tan, ((size_t)v * NU + k) * pitch + i);
       continue;
     }
     // camera-frame covariance Rc Sigma Rc^T
@@ -156,7 +157,7 @@ __global__ void GS_PROJ_BOUNDS project_kernel(const float* __restrict__ P, int n
     const S det = a * cc - b * b;
     if (!(val(det) > 0.f)) {
       store_culled(rec, at);
-      for (int k = 0; k < NU; ++k) store_culled(tan, ((size_t)v * NU + k) * n_pad + i);
+      for (int k = 0; k < NU; ++k) store_culled(tan, ((size_t)v * NU + k) * pitch + i);
       continue;
     }
     const S idet = 1.f / det;
@@ -204,7 +205,7 @@ __global__ void GS_PROJ_BOUNDS project_kernel(const float* __restrict__ P, int n
     if constexpr (NU > 0) {
 #pragma unroll
       for (int k = 0; k < NU; ++k) {
-        const size_t tk = ((size_t)v * NU + k) * n_pad + i;
+        const size_t tk = ((size_t)v * NU + k) * pitch + i;
         tan[3 * tk + 0] = make_float4(mx.d[k], my.d[k], cA.d[k], cB.d[k]);
         tan[3 * tk + 1] = make_float4(cC.d[k], opac.d[k], rgb[0].d[k], rgb[1].d[k]);
         tan[3 * tk + 2] = make_float4(rgb[2].d[k], 0.f, 0.f, 0.f);
@@ -213,6 +214,27 @@ __global__ void GS_PROJ_BOUNDS project_kernel(const float* __restrict__ P, int n
     (void)clx;
     (void)cly;
   }
+}
+
+template <int DEG, int NU>
+__global__ void GS_PROJ_BOUNDS project_kernel(const float* __restrict__ P, int n, int n_pad,
+                                              const gs_camera* __restrict__ cams, gs_frame fr, ProbeArg pa,
+                                              float4* __restrict__ rec, float4* __restrict__ tan) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  project_column<DEG, NU>(P, n, n_pad, i, n_pad, cams, fr.n_views, fr, pa, rec, tan);
+}
+
+// A batch: item b's share of the grid projects its columns into its camera,
+// records in slot b (pitch n_pad_max) with its own probe step.
+template <int DEG, int NU>
+__global__ void GS_PROJ_BOUNDS project_batch_kernel(BatchArg ba, int pitch, gs_frame fr, ProbeArg pa,
+                                                    float4* __restrict__ rec, float4* __restrict__ tan) {
+  const int b = batch_item(ba, (int)blockIdx.x);
+  const int i = ((int)blockIdx.x - ba.first_block[b]) * blockDim.x + threadIdx.x;
+  pa.t = ba.t[b];
+  pa.t_dev = nullptr;
+  project_column<DEG, NU>(ba.P[b], ba.n[b], ba.n_pad[b], i, pitch, ba.cam[b], 1, fr, pa,
+                          rec + 3 * (size_t)b * pitch, tan ? tan + 3 * (size_t)b * NU * pitch : nullptr);
 }
 
 template <int DEG, int NU>
@@ -259,4 +281,56 @@ extern "C" gs_status gs_project(const gs_params* x, const gs_camera* cams, gs_fr
     default: gs::dispatch_nu<3>(nu, x, cams, frame, pa, out, st); break;
   }
   return gs::check_launch("gs_project");
+}
+
+namespace gs {
+namespace {
+template <int DEG>
+void dispatch_batch(int nu, const BatchArg& ba, int pitch, gs_frame fr, ProbeArg pa, gs_projected* out,
+                    cudaStream_t st) {
+  const int blocks = ba.first_block[ba.n_items];
+  float4* rec = reinterpret_cast<float4*>(out->rec);
+  float4* tan = reinterpret_cast<float4*>(out->tangent);
+  if (nu == 0) project_batch_kernel<DEG, 0><<<blocks, 128, 0, st>>>(ba, pitch, fr, pa, rec, nullptr);
+  else if (nu == 1) project_batch_kernel<DEG, 1><<<blocks, 128, 0, st>>>(ba, pitch, fr, pa, rec, tan);
+  else project_batch_kernel<DEG, 2><<<blocks, 128, 0, st>>>(ba, pitch, fr, pa, rec, tan);
+}
+}  // namespace
+}  // namespace gs
+
+extern "C" gs_status gs_project_batch(const gs_batch_item* items, int32_t n_items, int32_t n_pad_max, gs_frame frame,
+                                      const gs_probe* probe, gs_projected* out, int32_t* status, void* stream) {
+  (void)status;
+  GS_REQUIRE(items && out && out->rec, "gs_project_batch: null argument");
+  GS_REQUIRE(n_items >= 1 && n_items <= GS_BATCH_MAX, "gs_project_batch: n_items=%d outside [1, %d]", n_items,
+             GS_BATCH_MAX);
+  GS_REQUIRE(frame.n_views == n_items && frame.width >= 1 && frame.height >= 1,
+             "gs_project_batch: frame.n_views must equal n_items");
+  GS_REQUIRE(n_pad_max >= 4 && n_pad_max % 4 == 0, "gs_project_batch: bad n_pad_max=%d", n_pad_max);
+  const int nu = probe ? probe->nu : 0;
+  const int deg = items[0].x.sh_degree;
+  if (deg < 0 || deg > 3 || nu < 0 || nu > 2) {
+    gs::set_error("gs_project_batch: unsupported sh_degree=%d nu=%d", deg, nu);
+    return GS_ERR_UNSUPPORTED;
+  }
+  GS_REQUIRE(nu == 0 || out->tangent, "gs_project_batch: probes given but out->tangent is NULL");
+  for (int b = 0; b < n_items; ++b) {
+    const gs_batch_item& it = items[b];
+    GS_REQUIRE(it.x.data && it.cam, "gs_project_batch: item %d has a null buffer", b);
+    GS_REQUIRE(it.x.sh_degree == deg, "gs_project_batch: items differ in SH degree");
+    GS_REQUIRE(it.x.n >= 0 && it.x.n <= n_pad_max && it.x.n_pad >= it.x.n && it.x.n_pad % 4 == 0,
+               "gs_project_batch: item %d has n=%d n_pad=%d for n_pad_max=%d", b, it.x.n, it.x.n_pad, n_pad_max);
+    GS_REQUIRE(nu == 0 || it.t >= 1, "gs_project_batch: item %d needs t >= 1 with probes", b);
+  }
+  const int per_item = (n_pad_max + 127) / 128;
+  const gs::BatchArg ba = gs::batch_arg(items, n_items, [&](const gs_batch_item&) { return per_item; });
+  gs::ProbeArg pa = gs::probe_arg(probe);
+  cudaStream_t st = (cudaStream_t)stream;
+  switch (deg) {
+    case 0: gs::dispatch_batch<0>(nu, ba, n_pad_max, frame, pa, out, st); break;
+    case 1: gs::dispatch_batch<1>(nu, ba, n_pad_max, frame, pa, out, st); break;
+    case 2: gs::dispatch_batch<2>(nu, ba, n_pad_max, frame, pa, out, st); break;
+    default: gs::dispatch_batch<3>(nu, ba, n_pad_max, frame, pa, out, st); break;
+  }
+  return gs::check_launch("gs_project_batch");
 }

@@ -493,7 +493,7 @@ __global__ void GS_BWD_BOUNDS raster_bwd_kernel(
     const float* __restrict__ target,
     const float* __restrict__ final_T, const uint32_t* __restrict__ n_contrib, const float* __restrict__ image_tan,
     int loss_kind, float gn_floor, float inv_m, float* __restrict__ cot, float* __restrict__ loss_out,
-    int32_t* status) {
+    int loss_per_view, int32_t* status) {
   constexpr int S = (GRAD ? 1 : 0) + NU;  // cotangent streams
   constexpr int NVP = cot_stride(S);      // padded row stride of their 9 S values
   static_assert(NVP <= 32, "streams");
@@ -604,7 +604,7 @@ __global__ void GS_BWD_BOUNDS raster_bwd_kernel(
   if (loss_out && tid == 0) {
     float tot = 0.f;
     for (int k = 0; k < nwarps; ++k) tot += s_loss[k];
-    atomicAdd(loss_out, tot);
+    atomicAdd(loss_out + (loss_per_view ? view : 0), tot);
   }
   const int n = s_abort ? 0 : (int)min(s_max, list_len);  // n_contrib never exceeds the tile's list
   const int nb = (n + batch - 1) / batch;
@@ -766,16 +766,17 @@ __device__ __forceinline__ void view_direction(const ViewGeom& v, const float mu
   d[2] = d2 / dn;
 }
 
+// Column i (of n Gaussians, parameter pitch n_pad) summed over views cams[0..V),
+// its cotangent row of view v at (v * cot_pitch + i) * NVP of cot.  Called by
+// every thread of a kPbwdThreads block (the SH staging is block-wide).
 template <int DEG, int NU, bool GRAD>
-__global__ void GS_PBWD_BOUNDS project_bwd_kernel(const float* __restrict__ P, int n, int n_pad,
-                                                                   const gs_camera* __restrict__ cams, gs_frame fr,
-                                                                   const float* __restrict__ cot, ProbeArg pa,
-                                                                   float* __restrict__ grad,
-                                                                   float* __restrict__ hz) {
+__device__ __forceinline__ void project_bwd_column(const float* __restrict__ P, int n, int n_pad, int i,
+                                                   const gs_camera* __restrict__ cams, int V, gs_frame fr,
+                                                   const float* __restrict__ cot, int cot_pitch, ProbeArg pa,
+                                                   float* __restrict__ grad, float* __restrict__ hz) {
   constexpr int S = (GRAD ? 1 : 0) + NU;
   constexpr int NVP = cot_stride(S);
   constexpr int K = (DEG + 1) * (DEG + 1);
-  const int i = blockIdx.x * kPbwdThreads + threadIdx.x;
   // the block's SH coefficients, staged once and read per view from shared
   // memory (volatile: re-read, not held in registers across the view loops)
   __shared__ float s_sh[3 * K][kPbwdThreads];
@@ -832,10 +833,10 @@ __global__ void GS_PBWD_BOUNDS project_bwd_kernel(const float* __restrict__ P, i
   }
   uint64_t clamp_bits = 0;  // bit 3 v + c: colour channel c clamped at 0 in view v (v < kClampViews)
 #pragma unroll 1
-  for (int v = 0; v < fr.n_views; ++v) {
+  for (int v = 0; v < V; ++v) {
     float c[NVP];
     bool any = false;
-    const float4* row4 = reinterpret_cast<const float4*>(cot + ((size_t)v * n_pad + i) * NVP);
+    const float4* row4 = reinterpret_cast<const float4*>(cot + ((size_t)v * cot_pitch + i) * NVP);
 #pragma unroll
     for (int q = 0; q < NVP / 4; ++q) {
       const float4 x4 = row4[q];
@@ -1041,7 +1042,7 @@ __global__ void GS_PBWD_BOUNDS project_bwd_kernel(const float* __restrict__ P, i
 #pragma unroll
       for (int ch = 0; ch < 3; ++ch) g[ch] = stash(v, 3 * st + ch);
     } else {
-      const float* cv = cot + ((size_t)v * n_pad + i) * NVP + 9 * st + 6;
+      const float* cv = cot + ((size_t)v * cot_pitch + i) * NVP + 9 * st + 6;
 #pragma unroll
       for (int ch = 0; ch < 3; ++ch) g[ch] = cv[ch];
     }
@@ -1072,7 +1073,7 @@ __global__ void GS_PBWD_BOUNDS project_bwd_kernel(const float* __restrict__ P, i
 #pragma unroll
     for (int k = 0; k < K; ++k) g_sh[k][0] = g_sh[k][1] = g_sh[k][2] = 0.f;
 #pragma unroll 1
-    for (int v = 0; v < fr.n_views; ++v) {
+    for (int v = 0; v < V; ++v) {
       float gcol[3];
       colour_cot(v, st, gcol);
       if (gcol[0] == 0.f && gcol[1] == 0.f && gcol[2] == 0.f) continue;
@@ -1114,7 +1115,7 @@ __global__ void GS_PBWD_BOUNDS project_bwd_kernel(const float* __restrict__ P, i
 #pragma unroll
       for (int ch = 0; ch < 3; ++ch) sp[k][ch] = sm[k][ch] = 0.f;
 #pragma unroll 1
-    for (int v = 0; v < fr.n_views; ++v) {
+    for (int v = 0; v < V; ++v) {
       float g1[3], g2[3];
       colour_cot(v, s1, g1);
       colour_cot(v, s2, g2);
@@ -1148,6 +1149,30 @@ __global__ void GS_PBWD_BOUNDS project_bwd_kernel(const float* __restrict__ P, i
         hz[(size_t)r * n_pad + i] = (n1 ? -val : val) * inv_nu;
       }
   }
+}
+
+template <int DEG, int NU, bool GRAD>
+__global__ void GS_PBWD_BOUNDS project_bwd_kernel(const float* __restrict__ P, int n, int n_pad,
+                                                  const gs_camera* __restrict__ cams, gs_frame fr,
+                                                  const float* __restrict__ cot, ProbeArg pa, float* __restrict__ grad,
+                                                  float* __restrict__ hz) {
+  const int i = blockIdx.x * kPbwdThreads + threadIdx.x;
+  project_bwd_column<DEG, NU, GRAD>(P, n, n_pad, i, cams, fr.n_views, fr, cot, n_pad, pa, grad, hz);
+}
+
+// A batch: item b's share of the grid takes its columns through the reverse of
+// its own projection, from its slot of the cotangents (pitch cot_pitch), with
+// its own probe step, into its own gradient and Hutchinson rows.
+template <int DEG, int NU, bool GRAD>
+__global__ void GS_PBWD_BOUNDS project_bwd_batch_kernel(BatchArg ba, gs_frame fr, const float* __restrict__ cot,
+                                                        int cot_pitch, ProbeArg pa) {
+  constexpr int NVP = cot_stride((GRAD ? 1 : 0) + NU);
+  const int b = batch_item(ba, (int)blockIdx.x);
+  const int i = ((int)blockIdx.x - ba.first_block[b]) * kPbwdThreads + threadIdx.x;
+  pa.t = ba.t[b];
+  pa.t_dev = nullptr;
+  project_bwd_column<DEG, NU, GRAD>(ba.P[b], ba.n[b], ba.n_pad[b], i, ba.cam[b], 1, fr,
+                                    cot + (size_t)b * cot_pitch * NVP, cot_pitch, pa, ba.grad[b], ba.hz[b]);
 }
 
 // ------------------------------------------------------------------ host side
@@ -1209,11 +1234,15 @@ void launch_pbwd(const gs_params* x, const gs_camera* cams, gs_frame fr, const f
                                                           grad, hz);
 }
 
+// The reverse blend over the frame, then the projection's reverse pass: of the
+// one scene x (ba NULL), or of each batch item from its slot (ba given: records
+// and cotangents at pitch n_pad, each view its own objective, m = 3 H W).
 template <int NU, bool GRAD>
-void launch_bwd_kernels(const gs_params* x, const gs_camera* cams, const gs_projected* proj, const gs_sorted* sorted,
-                        gs_frame fr, const float* image, const float* target, const float* final_T,
-                        const uint32_t* n_contrib, const float* image_tan, const gs_probe* probe, gs_loss loss,
-                        float* grad, float* hz, float* loss_out, float* cot, int32_t* status, cudaStream_t st) {
+void launch_bwd_kernels(const gs_params* x, const BatchArg* ba, int n_pad, int deg, const gs_camera* cams,
+                        const gs_projected* proj, const gs_sorted* sorted, gs_frame fr, const float* image,
+                        const float* target, const float* final_T, const uint32_t* n_contrib, const float* image_tan,
+                        const gs_probe* probe, gs_loss loss, float* grad, float* hz, float* loss_out, float* cot,
+                        int32_t* status, cudaStream_t st) {
   const TileGrid g = tile_grid(fr);
   const int nthr = fr.tile_w * fr.tile_h / kPixPerThread, batch = bwd_batch(fr, nthr);
   const size_t smem = bwd_smem_bytes(batch);
@@ -1224,12 +1253,37 @@ void launch_bwd_kernels(const gs_params* x, const gs_camera* cams, const gs_proj
     if (allow_smem(kern, smem) != cudaSuccess) return;  // the caller reports the error
     attr[cb] = smem;
   }
-  const float inv_m = (float)(1.0 / (3.0 * (double)fr.width * fr.height * fr.n_views));
+  const double views_per_objective = ba ? 1.0 : (double)fr.n_views;
+  const float inv_m = (float)(1.0 / (3.0 * (double)fr.width * fr.height * views_per_objective));
   const unsigned blocks = (unsigned)((size_t)fr.n_views * g.T);
   kern<<<blocks, nthr, smem, st>>>(
-      reinterpret_cast<const float4*>(proj->rec), sorted->vals, sorted->ranges, sorted->order, x->n_pad, fr, g.Tx,
+      reinterpret_cast<const float4*>(proj->rec), sorted->vals, sorted->ranges, sorted->order, n_pad, fr, g.Tx,
       g.T, image,
-      target, final_T, n_contrib, image_tan, loss.kind, loss.gn_floor, inv_m, cot, loss_out, status);
+      target, final_T, n_contrib, image_tan, loss.kind, loss.gn_floor, inv_m, cot, loss_out, ba ? 1 : 0, status);
+  if (ba) {
+    if (ba->first_block[ba->n_items] == 0) return;
+    constexpr int S = (GRAD ? 1 : 0) + NU;
+    const size_t sm = pbwd_stash_bytes(1, S);
+    const ProbeArg pa = probe_arg(probe);
+    const dim3 grid(ba->first_block[ba->n_items]), blk(kPbwdThreads);
+#define GS_PBWD_BATCH(D)                                                                           \
+  do {                                                                                             \
+    static size_t battr = 0;                                                                       \
+    if (sm > battr) {                                                                              \
+      if (allow_smem(project_bwd_batch_kernel<D, NU, GRAD>, sm) != cudaSuccess) return;            \
+      battr = sm;                                                                                  \
+    }                                                                                              \
+    project_bwd_batch_kernel<D, NU, GRAD><<<grid, blk, sm, st>>>(*ba, fr, cot, n_pad, pa);         \
+  } while (0)
+    switch (deg) {
+      case 0: GS_PBWD_BATCH(0); break;
+      case 1: GS_PBWD_BATCH(1); break;
+      case 2: GS_PBWD_BATCH(2); break;
+      default: GS_PBWD_BATCH(3); break;
+    }
+#undef GS_PBWD_BATCH
+    return;
+  }
   if (x->n == 0) return;
   switch (x->sh_degree) {
     case 0: launch_pbwd<0, NU, GRAD>(x, cams, fr, cot, probe, grad, hz, st); break;
@@ -1237,6 +1291,26 @@ void launch_bwd_kernels(const gs_params* x, const gs_camera* cams, const gs_proj
     case 2: launch_pbwd<2, NU, GRAD>(x, cams, fr, cot, probe, grad, hz, st); break;
     default: launch_pbwd<3, NU, GRAD>(x, cams, fr, cot, probe, grad, hz, st); break;
   }
+}
+
+// The kernels of one reverse call for the stream counts: the gradient stream
+// (want_grad) and nu probe streams.
+void launch_bwd_streams(bool want_grad, int nu, const gs_params* x, const BatchArg* ba, int n_pad, int deg,
+                        const gs_camera* cams, const gs_projected* proj, const gs_sorted* sorted, gs_frame frame,
+                        const float* image, const float* target, const float* final_T, const uint32_t* n_contrib,
+                        const float* image_tangent, const gs_probe* probe, gs_loss loss, float* gptr, float* hptr,
+                        float* loss_out, float* cot, int32_t* status, cudaStream_t st) {
+#define GS_BWD_ARGS x, ba, n_pad, deg, cams, proj, sorted, frame, image, target, final_T, n_contrib, image_tangent, \
+                    probe, loss, gptr, hptr, loss_out, cot, status, st
+  if (want_grad) {
+    if (nu == 0) launch_bwd_kernels<0, true>(GS_BWD_ARGS);
+    else if (nu == 1) launch_bwd_kernels<1, true>(GS_BWD_ARGS);
+    else launch_bwd_kernels<2, true>(GS_BWD_ARGS);
+  } else {
+    if (nu == 1) launch_bwd_kernels<1, false>(GS_BWD_ARGS);
+    else launch_bwd_kernels<2, false>(GS_BWD_ARGS);
+  }
+#undef GS_BWD_ARGS
 }
 
 gs_status run_bwd(bool want_grad, const gs_params* x, const gs_camera* cams, gs_frame frame, const gs_projected* proj,
@@ -1273,14 +1347,8 @@ gs_status run_bwd(bool want_grad, const gs_params* x, const gs_camera* cams, gs_
   if (cudaMemsetAsync(cot, 0, need, st) != cudaSuccess) return check_launch(name);
   float* gptr = want_grad ? grad->data : nullptr;
   float* hptr = nu ? hz->data : nullptr;
-  if (want_grad) {
-    if (nu == 0) launch_bwd_kernels<0, true>(x, cams, proj, sorted, frame, image, target, final_T, n_contrib, image_tangent, probe, loss, gptr, hptr, loss_out, cot, status, st);
-    else if (nu == 1) launch_bwd_kernels<1, true>(x, cams, proj, sorted, frame, image, target, final_T, n_contrib, image_tangent, probe, loss, gptr, hptr, loss_out, cot, status, st);
-    else launch_bwd_kernels<2, true>(x, cams, proj, sorted, frame, image, target, final_T, n_contrib, image_tangent, probe, loss, gptr, hptr, loss_out, cot, status, st);
-  } else {
-    if (nu == 1) launch_bwd_kernels<1, false>(x, cams, proj, sorted, frame, image, target, final_T, n_contrib, image_tangent, probe, loss, gptr, hptr, loss_out, cot, status, st);
-    else launch_bwd_kernels<2, false>(x, cams, proj, sorted, frame, image, target, final_T, n_contrib, image_tangent, probe, loss, gptr, hptr, loss_out, cot, status, st);
-  }
+  launch_bwd_streams(want_grad, nu, x, nullptr, x->n_pad, x->sh_degree, cams, proj, sorted, frame, image, target,
+                     final_T, n_contrib, image_tangent, probe, loss, gptr, hptr, loss_out, cot, status, st);
   return check_launch(name);
 }
 
@@ -1329,4 +1397,54 @@ extern "C" gs_status gs_hvp_diag(const gs_params* x, const gs_camera* cams, gs_f
                                  void* stream) {
   return gs::run_bwd(false, x, cams, frame, proj, sorted, image, target, final_T, n_contrib, image_tangent, probe, loss,
                      nullptr, hz, nullptr, workspace, workspace_bytes, status, stream, "gs_hvp_diag");
+}
+
+extern "C" gs_status gs_raster_bwd_batch(const gs_batch_item* items, int32_t n_items, int32_t n_pad_max,
+                                         gs_frame frame, const gs_projected* proj, const gs_sorted* sorted,
+                                         const float* image, const float* target, const float* final_T,
+                                         const uint32_t* n_contrib, const float* image_tangent, const gs_probe* probe,
+                                         gs_loss loss, float* loss_out, void* workspace, size_t workspace_bytes,
+                                         int32_t* status, void* stream) {
+  using namespace gs;
+  const char* name = "gs_raster_bwd_batch";
+  GS_REQUIRE(items && proj && sorted && image && target && final_T && n_contrib, "%s: null argument", name);
+  GS_REQUIRE(proj->rec && sorted->vals && sorted->ranges, "%s: null device buffer", name);
+  GS_REQUIRE(n_items >= 1 && n_items <= GS_BATCH_MAX, "%s: n_items=%d outside [1, %d]", name, n_items, GS_BATCH_MAX);
+  GS_REQUIRE(frame_ok(frame) && frame.n_views == n_items, "%s: bad frame (n_views must equal n_items)", name);
+  GS_REQUIRE(n_pad_max >= 4 && n_pad_max % 4 == 0, "%s: bad n_pad_max=%d", name, n_pad_max);
+  GS_REQUIRE(loss.kind == GS_LOSS_L1 || loss.kind == GS_LOSS_L2 || loss.kind == GS_LOSS_COTANGENT ||
+                 loss.kind == GS_LOSS_WEIGHTED,
+             "%s: bad loss kind %d", name, loss.kind);
+  const bool given = loss.kind == GS_LOSS_COTANGENT;
+  const int nu = ((image_tangent || given) && probe) ? probe->nu : 0;
+  const int deg = items[0].x.sh_degree;
+  if (nu < 0 || nu > 2 || deg < 0 || deg > 3) {
+    set_error("%s: unsupported nu=%d sh_degree=%d", name, nu, deg);
+    return GS_ERR_UNSUPPORTED;
+  }
+  GS_REQUIRE(loss.kind != GS_LOSS_WEIGHTED || nu == 0 || image_tangent, "%s: weighted loss needs image_tangent",
+             name);
+  for (int b = 0; b < n_items; ++b) {
+    const gs_batch_item& it = items[b];
+    auto same = [&](const gs_params& p) { return p.n == it.x.n && p.n_pad == it.x.n_pad && p.sh_degree == deg; };
+    GS_REQUIRE(it.x.data && it.cam && it.grad.data && same(it.x) && same(it.grad),
+               "%s: item %d needs x, cam and a gradient of x's layout", name, b);
+    GS_REQUIRE(nu == 0 || (it.hz.data && same(it.hz) && it.t >= 1), "%s: item %d needs hz and t >= 1 with probes",
+               name, b);
+    GS_REQUIRE(it.x.n >= 0 && it.x.n <= n_pad_max && it.x.n_pad % 4 == 0, "%s: item %d: bad n=%d n_pad=%d", name,
+               b, it.x.n, it.x.n_pad);
+  }
+  const size_t need = bwd_cot_floats(n_pad_max, frame, 1 + nu) * sizeof(float);
+  GS_REQUIRE(workspace && workspace_bytes >= need, "%s: workspace needs %zu bytes, got %zu", name, need,
+             workspace_bytes);
+  cudaStream_t st = (cudaStream_t)stream;
+  float* cot = (float*)workspace;
+  if (cudaMemsetAsync(cot, 0, bwd_cot_floats(n_pad_max, frame, 1 + nu) * sizeof(float), st) != cudaSuccess)
+    return check_launch(name);
+  const BatchArg ba = batch_arg(items, n_items, [](const gs_batch_item& it) {
+    return (it.x.n + kPbwdThreads - 1) / kPbwdThreads;
+  });
+  launch_bwd_streams(true, nu, nullptr, &ba, n_pad_max, deg, nullptr, proj, sorted, frame, image, target, final_T,
+                     n_contrib, image_tangent, probe, loss, nullptr, nullptr, loss_out, cot, status, st);
+  return check_launch(name);
 }

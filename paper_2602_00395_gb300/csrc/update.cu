@@ -125,28 +125,18 @@ __device__ __forceinline__ int row_group(int r) {
   return r < 3 ? 0 : r < 6 ? 1 : r < 10 ? 2 : r < 11 ? 3 : r < 14 ? 4 : 5;
 }
 
-template <int DEG, bool HVP, bool ETA, bool ADAM = false>
-__global__ void __launch_bounds__(256) tr_update_kernel(float* __restrict__ x, float* __restrict__ ge,
-                                                        float* __restrict__ de, const float* __restrict__ g,
-                                                        const float* __restrict__ hz, float* __restrict__ eta_out,
-                                                        int n, int n_pad, gs_tr_config cfg, float eps,
-                                                        const int64_t* __restrict__ t_dev, gs_eps_schedule sched,
-                                                        AdamArg adam, int32_t* status) {
+// The columns [c0, c0 + kUpdCols) of one scene (n Gaussians, pitch n_pad):
+// phase 1 and phase 2 above.  hvp_now: this step takes d_ema from hz.
+template <int DEG, bool HVP, bool ETA, bool ADAM>
+__device__ __forceinline__ void tr_update_columns(float* __restrict__ x, float* __restrict__ ge,
+                                                  float* __restrict__ de, const float* __restrict__ g,
+                                                  const float* __restrict__ hz, float* __restrict__ eta_out, int n,
+                                                  int n_pad, const gs_tr_config& cfg, float eps, bool hvp_now,
+                                                  const AdamArg& adam, int c0, int32_t* status) {
   constexpr int K = (DEG + 1) * (DEG + 1);
   constexpr int ROWS = kRowSH + 3 * K;
   constexpr int kLanesPerRow = kUpdCols / 4;  // 64
   __shared__ __align__(16) float s_eta[kEtaRows][kUpdCols];
-  const int c0 = blockIdx.x * kUpdCols;
-  bool hvp_now = HVP;
-  if (t_dev) {
-    const int64_t t = *t_dev;
-    if (t < 1) {
-      if (blockIdx.x == 0 && threadIdx.x == 0 && status) atomicOr(status, GS_FLAG_NONFINITE);
-      return;
-    }
-    eps = eps_of(sched, t);
-    hvp_now = HVP && ((t - 1) % cfg.l) == 0;
-  }
   // phase 1: radii of this block's columns, from x_t
   {
     const int i = c0 + (int)threadIdx.x;
@@ -213,6 +203,39 @@ __global__ void __launch_bounds__(256) tr_update_kernel(float* __restrict__ x, f
     }
   }
   if (bad && status) atomicOr(status, GS_FLAG_NONFINITE);
+}
+
+template <int DEG, bool HVP, bool ETA, bool ADAM = false>
+__global__ void __launch_bounds__(256) tr_update_kernel(float* __restrict__ x, float* __restrict__ ge,
+                                                        float* __restrict__ de, const float* __restrict__ g,
+                                                        const float* __restrict__ hz, float* __restrict__ eta_out,
+                                                        int n, int n_pad, gs_tr_config cfg, float eps,
+                                                        const int64_t* __restrict__ t_dev, gs_eps_schedule sched,
+                                                        AdamArg adam, int32_t* status) {
+  bool hvp_now = HVP;
+  if (t_dev) {
+    const int64_t t = *t_dev;
+    if (t < 1) {
+      if (blockIdx.x == 0 && threadIdx.x == 0 && status) atomicOr(status, GS_FLAG_NONFINITE);
+      return;
+    }
+    eps = eps_of(sched, t);
+    hvp_now = HVP && ((t - 1) % cfg.l) == 0;
+  }
+  tr_update_columns<DEG, HVP, ETA, ADAM>(x, ge, de, g, hz, eta_out, n, n_pad, cfg, eps, hvp_now, adam,
+                                         (int)blockIdx.x * kUpdCols, status);
+}
+
+// A batch: item b's share of the grid updates its scene with its own eps and
+// curvature decision.
+template <int DEG>
+__global__ void __launch_bounds__(256) tr_update_batch_kernel(BatchArg ba, gs_tr_config cfg, int32_t* status) {
+  const int b = batch_item(ba, (int)blockIdx.x);
+  const int c0 = ((int)blockIdx.x - ba.first_block[b]) * kUpdCols;
+  // the item's x was given as a writable gs_params (BatchArg keeps it as const)
+  tr_update_columns<DEG, true, false, false>(const_cast<float*>(ba.P[b]), ba.ge[b], ba.de[b], ba.grad[b], ba.hz[b],
+                                             nullptr, ba.n[b], ba.n_pad[b], cfg, ba.eps[b], ba.hvp[b] != 0,
+                                             AdamArg{}, c0, status);
 }
 
 template <int DEG>
@@ -355,4 +378,41 @@ extern "C" gs_status gs_adam_tr_update(gs_params* x, gs_params* m, gs_params* v,
     default: launch_adam<3>(eta, x, m, v, grad, eta_out, *cfg, eps, a, status, st); break;
   }
   return check_launch("gs_adam_tr_update");
+}
+
+extern "C" gs_status gs_tr_update_batch(const gs_batch_item* items, int32_t n_items, const gs_tr_config* cfg,
+                                        int32_t* status, void* stream) {
+  using namespace gs;
+  const char* name = "gs_tr_update_batch";
+  GS_REQUIRE(items && cfg, "%s: null argument", name);
+  GS_REQUIRE(n_items >= 1 && n_items <= GS_BATCH_MAX, "%s: n_items=%d outside [1, %d]", name, n_items, GS_BATCH_MAX);
+  GS_REQUIRE(cfg->l >= 1, "%s: need l >= 1", name);
+  const int deg = items[0].x.sh_degree;
+  if (deg < 0 || deg > 3) {
+    set_error("%s: unsupported sh_degree=%d", name, deg);
+    return GS_ERR_UNSUPPORTED;
+  }
+  for (int b = 0; b < n_items; ++b) {
+    const gs_batch_item& it = items[b];
+    auto same = [&](const gs_params& p) { return p.n == it.x.n && p.n_pad == it.x.n_pad && p.sh_degree == deg; };
+    GS_REQUIRE(it.x.data && it.g_ema.data && it.d_ema.data && it.grad.data, "%s: item %d has a null buffer", name,
+               b);
+    GS_REQUIRE(same(it.x) && same(it.g_ema) && same(it.d_ema) && same(it.grad), "%s: item %d: buffers differ in layout",
+               name, b);
+    GS_REQUIRE(!it.hvp || (it.hz.data && same(it.hz)), "%s: item %d takes curvature but has no hz", name, b);
+    GS_REQUIRE(it.x.n_pad % 4 == 0 && it.t >= 1 && it.eps > 0.f, "%s: item %d: bad n_pad, t or eps", name, b);
+  }
+  const BatchArg ba = batch_arg(items, n_items, [](const gs_batch_item& it) {
+    return (it.x.n + kUpdCols - 1) / kUpdCols;
+  });
+  const int blocks = ba.first_block[n_items];
+  if (blocks == 0) return GS_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  switch (deg) {
+    case 0: tr_update_batch_kernel<0><<<blocks, 256, 0, st>>>(ba, *cfg, status); break;
+    case 1: tr_update_batch_kernel<1><<<blocks, 256, 0, st>>>(ba, *cfg, status); break;
+    case 2: tr_update_batch_kernel<2><<<blocks, 256, 0, st>>>(ba, *cfg, status); break;
+    default: tr_update_batch_kernel<3><<<blocks, 256, 0, st>>>(ba, *cfg, status); break;
+  }
+  return check_launch(name);
 }

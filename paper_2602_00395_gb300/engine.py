@@ -15,6 +15,7 @@ loop (step counter, eps schedule).  Nothing here synchronises the stream except
 """
 from __future__ import annotations
 
+import contextlib
 import math
 from dataclasses import dataclass, field
 
@@ -299,14 +300,22 @@ class TRStep:
             self.step_device(hvp, schedule, s)
         return g
 
-    def step(self, t: int, eps: float, stream=None) -> None:
-        """One iteration of Algorithm 1 on the frame's views (S1 = S2)."""
+    def step(self, t: int, eps: float, stream=None, exchange=None) -> None:
+        """One iteration of Algorithm 1 on the frame's views (S1 = S2).  With an
+        exchange (exchange.GradExchange) the step's views are this rank's share
+        of a data-parallel step: after the reverse pass the gradient and the
+        Hutchinson diagonal are summed over ranks, each weighted by its share of
+        the residual count (Sec. 4.1 normalises by m over all views), and every
+        rank then applies the same update."""
         hvp = self.nu > 0 and ((t - 1) % self.cfg.l) == 0
         self.loss_val.zero_()
         self.project(t, probes=hvp, stream=stream)
         self.bin_sort(stream)
         self.raster_fwd(t, probes=hvp, stream=stream)
         self.raster_bwd(t, probes=hvp, stream=stream)
+        if exchange is not None:
+            with torch.cuda.stream(stream) if stream is not None else contextlib.nullcontext():
+                exchange(3 * self.W * self.H * self.V, self.grad, self.hz if hvp else None)
         self.update(t, eps, with_hz=hvp, stream=stream)
 
     def ensure_capacity(self, headroom: float = 1.25) -> int:
@@ -364,3 +373,128 @@ def autotune_tile(eng: TRStep, candidates=((16, 16), (32, 8), (8, 32), (16, 8)),
             run(best_tile, batch)
     best = min((k for k in times if (k[0], k[1]) == tuple(best_tile)), key=times.get)
     return best, times
+
+
+@dataclass
+class BatchEntry:
+    """One request of a batch: one view of a resident scene.  x, g_ema, d_ema are
+    the scene's rows x n_pad state (updated in place by a training step), cam its
+    camera (96 bytes on the device), target its 3 x H x W target image (device)."""
+    x: torch.Tensor
+    g_ema: torch.Tensor
+    d_ema: torch.Tensor
+    n: int
+    cam: torch.Tensor
+    target: torch.Tensor | None = None
+    t: int = 1
+    eps: float = 1e-6
+
+
+class BatchStep:
+    """Training steps or renders of several requests of one image size in shared
+    launches (gs_project_batch, gs_bin_sort, gs_raster_fwd, gs_raster_bwd_batch,
+    gs_tr_update_batch): request b is view b of the batch frame, its splat
+    records in slot b of one set of buffers.  Each request keeps its own
+    objective (m = 3 H W), probes (its scene's step t) and update; its image is
+    images()[b].  Buffers are allocated for the batch at construction (on the
+    current stream, from PyTorch's caching allocator)."""
+
+    def __init__(self, entries: list[BatchEntry], width: int, height: int, *, sh_degree: int = 3, nu: int = 1,
+                 tile=(16, 16), capacity: int, train: bool = True, loss_kind: int = G.GS_LOSS_L1,
+                 gn_floor: float = 1e-3, cfg: TRConfig | None = None, probe_seed: int = 42, device: str = "cuda",
+                 footprint_bins: bool = True, batch: int = 0):
+        G.load()
+        assert 1 <= len(entries) <= G.GS_BATCH_MAX
+        self.entries, self.B, self.W, self.H, self.deg = entries, len(entries), width, height, sh_degree
+        self.train, self.nu = train, (nu if train else 0)
+        self.cfg = cfg or TRConfig()
+        self.loss = G.gs_loss(loss_kind, gn_floor)
+        self.probe_seed = probe_seed
+        self.device = torch.device(device)
+        self.rows = synth.n_rows(sh_degree)
+        self.n_pad = max(e.x.shape[1] for e in entries)
+        self.frame = G.frame_struct(self.B, width, height, *tile, footprint_bins=footprint_bins, batch=batch)
+        Tx, Ty = -(-width // tile[0]), -(-height // tile[1])
+        f32 = dict(dtype=torch.float32, device=self.device)
+        i32 = dict(dtype=torch.int32, device=self.device)
+        HW, B = width * height, self.B
+        self.rec = torch.empty(B * self.n_pad * 12, **f32)
+        self.tan = torch.empty(self.nu * B * self.n_pad * 12 if self.nu else 4, **f32)
+        self.image = torch.empty(B * 3 * HW, **f32)
+        self.final_T = torch.empty(B * HW, **f32)
+        self.n_contrib = torch.empty(B * HW, **i32)
+        self.image_tan = torch.empty(self.nu * B * 3 * HW if self.nu else 4, **f32)
+        self.status = torch.zeros(1, **i32)
+        self.ranges = torch.empty(2 * B * Tx * Ty, **i32)
+        self.order = torch.empty(B * Tx * Ty, **i32)
+        self.n_pairs = torch.empty(1, **i32)
+        self.capacity = int(capacity)
+        self.keys = torch.empty(self.capacity, dtype=torch.int64, device=self.device)
+        self.vals = torch.empty(self.capacity, **i32)
+        self.sort_ws = torch.empty(G.gs_bin_sort_workspace_size(self.n_pad, self.frame, self.capacity),
+                                   dtype=torch.uint8, device=self.device)
+        self.cams = torch.cat([e.cam for e in entries])
+        if train:
+            self.target = torch.empty(B * 3 * HW, **f32)
+            self.loss_val = torch.zeros(B, **f32)
+            self.grads = [torch.empty(self.rows, e.x.shape[1], **f32) for e in entries]
+            self.hzs = [torch.empty(self.rows, e.x.shape[1], **f32) for e in entries] if self.nu else None
+            self.bwd_ws = torch.empty(G.gs_raster_bwd_workspace_size(self.n_pad, self.frame, self.nu),
+                                      dtype=torch.uint8, device=self.device)
+
+    @staticmethod
+    def working_bytes(n_pads: list[int], width: int, height: int, *, sh_degree: int = 3, nu: int = 1,
+                      tile=(16, 16), capacity: int, train: bool = True) -> int:
+        """Device bytes the buffers of a batch of scenes with these row pitches take."""
+        B, n_pad, rows, HW = len(n_pads), max(n_pads), synth.n_rows(sh_degree), width * height
+        nu = nu if train else 0
+        frame = G.frame_struct(B, width, height, *tile)
+        Tx, Ty = -(-width // tile[0]), -(-height // tile[1])
+        b = B * n_pad * 48 * (1 + nu) + B * HW * 4 * (3 + 1 + 1 + 3 * nu) + B * Tx * Ty * 12 + capacity * 12
+        b += G.gs_bin_sort_workspace_size(n_pad, frame, capacity) + 96 * B
+        if train:
+            b += B * HW * 12 + G.gs_raster_bwd_workspace_size(n_pad, frame, nu)
+            b += sum(rows * p * 4 * (1 + (1 if nu else 0)) for p in n_pads)
+        return int(b)
+
+    def items(self) -> list:
+        out = []
+        for b, e in enumerate(self.entries):
+            P = lambda t: G.params_struct(t, e.n, self.deg)
+            hvp = 1 if (self.nu and (e.t - 1) % self.cfg.l == 0) else 0
+            if self.train:
+                out.append(G.gs_batch_item(P(e.x), P(self.grads[b]), P(self.hzs[b]) if self.nu else G.gs_params(),
+                                           P(e.g_ema), P(e.d_ema), self.cams.data_ptr() + 96 * b, e.t, e.eps, hvp))
+            else:
+                out.append(G.gs_batch_item(P(e.x), G.gs_params(), G.gs_params(), G.gs_params(), G.gs_params(),
+                                           self.cams.data_ptr() + 96 * b, max(e.t, 1), e.eps, 0))
+        return out
+
+    def run(self, stream=None) -> None:
+        """The batch's calls on `stream`: a training step of every request (or a render)."""
+        items = self.items()
+        pr = G.probe_struct(self.probe_seed, 0, self.nu) if self.nu else None
+        proj = G.gs_projected(self.rec.data_ptr(), self.tan.data_ptr())
+        srt = G.gs_sorted(self.keys.data_ptr(), self.vals.data_ptr(), self.ranges.data_ptr(),
+                          self.n_pairs.data_ptr(), self.capacity, self.order.data_ptr())
+        G.gs_project_batch(items, self.n_pad, self.frame, pr, proj, self.status, stream)
+        G.gs_bin_sort(proj, self.n_pad, self.frame, self.sort_ws, srt, self.status, stream)
+        G.gs_raster_fwd(proj, srt, self.n_pad, self.frame, pr, self.image, self.final_T, self.n_contrib,
+                        self.image_tan if pr else None, self.status, stream)
+        if not self.train:
+            return
+        HW3 = 3 * self.W * self.H
+        with torch.cuda.stream(stream) if stream is not None else contextlib.nullcontext():
+            for b, e in enumerate(self.entries):
+                self.target[HW3 * b: HW3 * (b + 1)].copy_(e.target, non_blocking=True)
+            self.loss_val.zero_()
+        G.gs_raster_bwd_batch(items, self.n_pad, self.frame, proj, srt, self.image, self.target, self.final_T,
+                              self.n_contrib, self.image_tan if pr else None, pr, self.loss, self.loss_val,
+                              self.bwd_ws, self.status, stream)
+        G.gs_tr_update_batch(items, self.cfg.struct(), self.status, stream)
+
+    def images(self) -> torch.Tensor:
+        return self.image.view(self.B, 3, self.H, self.W)
+
+    def read_status(self) -> int:
+        return int(self.status.item())

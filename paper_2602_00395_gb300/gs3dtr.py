@@ -25,7 +25,7 @@ EXPORTED = ("gs_last_error", "gs_version", "gs_project", "gs_bin_sort_workspace_
             "gs_bin_sort_noalloc",
             "gs_raster_fwd", "gs_raster_bwd_workspace_size", "gs_raster_bwd", "gs_hvp_diag", "gs_tr_update",
             "gs_tr_update_dev", "gs_step_advance", "gs_adam_tr_update", "gs_dssim_workspace_size",
-            "gs_dssim_cotangents", "gs_wait_check")
+            "gs_dssim_cotangents", "gs_wait_check", "gs_project_batch", "gs_raster_bwd_batch", "gs_tr_update_batch")
 
 
 class gs_params(C.Structure):
@@ -81,7 +81,16 @@ class gs_tr_config(C.Structure):
                 ("l", C.c_int32), ("mean_exact", C.c_int32)]
 
 
+GS_BATCH_MAX = 16
+
+
+class gs_batch_item(C.Structure):
+    _fields_ = [("x", gs_params), ("grad", gs_params), ("hz", gs_params), ("g_ema", gs_params), ("d_ema", gs_params),
+                ("cam", C.c_void_p), ("t", C.c_int64), ("eps", C.c_float), ("hvp", C.c_int32)]
+
+
 assert C.sizeof(gs_camera) == 96 and C.sizeof(gs_params) == 24 and C.sizeof(gs_sorted) == 48
+assert C.sizeof(gs_batch_item) == 144
 
 
 class GSError(RuntimeError):
@@ -146,6 +155,16 @@ def load():
         L.gs_dssim_cotangents.restype = st
         L.gs_dssim_cotangents.argtypes = [gs_frame, P, P, P, C.c_int32, C.c_float, C.c_float, C.c_int32, P, P, P,
                                           C.c_size_t, P, P]
+        BI = C.POINTER(gs_batch_item)
+        L.gs_project_batch.restype = st
+        L.gs_project_batch.argtypes = [BI, C.c_int32, C.c_int32, gs_frame, C.POINTER(gs_probe),
+                                       C.POINTER(gs_projected), P, P]
+        L.gs_raster_bwd_batch.restype = st
+        L.gs_raster_bwd_batch.argtypes = [BI, C.c_int32, C.c_int32, gs_frame, C.POINTER(gs_projected),
+                                          C.POINTER(gs_sorted), P, P, P, P, P, C.POINTER(gs_probe), gs_loss, P, P,
+                                          C.c_size_t, P, P]
+        L.gs_tr_update_batch.restype = st
+        L.gs_tr_update_batch.argtypes = [BI, C.c_int32, C.POINTER(gs_tr_config), P, P]
         L.gs_adam_tr_update.restype = st
         L.gs_adam_tr_update.argtypes = [C.POINTER(gs_params), C.POINTER(gs_params), C.POINTER(gs_params),
                                         C.POINTER(gs_params), C.POINTER(gs_tr_config), C.POINTER(gs_adam_config),
@@ -310,3 +329,39 @@ def gs_dssim_cotangents(frame: gs_frame, image, target, image_tangent, nu: int, 
                                 int(want_grad), ptr(cot), ptr(loss_out), ptr(workspace),
                                 workspace.numel() * workspace.element_size(), ptr(status), stream_handle(stream)),
           "gs_dssim_cotangents")
+
+
+# ------------------------------------------------------------ batches
+def batch_items(items) -> "C.Array":
+    """A host array of gs_batch_item from a sequence of them."""
+    arr = (gs_batch_item * len(items))()
+    for k, it in enumerate(items):
+        arr[k] = it
+    return arr
+
+
+def gs_project_batch(items, n_pad_max: int, frame: gs_frame, probe: gs_probe | None, out: gs_projected,
+                     status=None, stream=None) -> None:
+    L = load()
+    arr = batch_items(items)
+    check(L.gs_project_batch(arr, len(items), n_pad_max, frame, C.byref(probe) if probe else None, C.byref(out),
+                             ptr(status), stream_handle(stream)), "gs_project_batch")
+
+
+def gs_raster_bwd_batch(items, n_pad_max: int, frame: gs_frame, proj: gs_projected, sorted_: gs_sorted, image,
+                        target, final_T, n_contrib, image_tangent, probe: gs_probe | None, loss: gs_loss, loss_out,
+                        workspace, status=None, stream=None) -> None:
+    L = load()
+    arr = batch_items(items)
+    check(L.gs_raster_bwd_batch(arr, len(items), n_pad_max, frame, C.byref(proj), C.byref(sorted_), ptr(image),
+                                ptr(target), ptr(final_T), ptr(n_contrib), ptr(image_tangent),
+                                C.byref(probe) if probe else None, loss, ptr(loss_out), ptr(workspace),
+                                workspace.numel() * workspace.element_size(), ptr(status), stream_handle(stream)),
+          "gs_raster_bwd_batch")
+
+
+def gs_tr_update_batch(items, cfg: gs_tr_config, status=None, stream=None) -> None:
+    L = load()
+    arr = batch_items(items)
+    check(L.gs_tr_update_batch(arr, len(items), C.byref(cfg), ptr(status), stream_handle(stream)),
+          "gs_tr_update_batch")

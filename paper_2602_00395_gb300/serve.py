@@ -5,23 +5,27 @@ continuous batching on the GPU.
   cameras and its target images resident in HBM, and a host step counter.
 * A request is one training step of Algorithm 1 on one view of a scene
   (projection, binning, forward, reverse pass with the Hutchinson probes,
-  update) or one render (projection, binning, forward).  Its working buffers
-  (records, pairs, images, cotangents, gradient, curvature) are allocated for
-  the request from PyTorch's caching allocator on the request's stream and
-  released when it completes.
+  update) or one render (projection, binning, forward).  The working buffers
+  of a batch of requests (records, pairs, images, cotangents, gradients,
+  curvature) are allocated for it from PyTorch's caching allocator on its
+  stream and released when it completes.
 * Admission: a request that has arrived is started when a slot (a CUDA stream)
   is free, its scene has no request in flight (a training step changes the
-  scene), and its working set fits the HBM budget left by the requests in
-  flight.  Requests are taken in arrival order; one that cannot start does not
+  scene), and its batch's working set fits the HBM budget left by the batches
+  in flight.  Requests are taken in arrival order; one that cannot start does not
   hold back later ones for other scenes, and no later request of its own scene
   overtakes it.
-* Continuous batching: every started request runs on its own stream, so the
-  kernels of requests of different scenes overlap on the device; a request that
-  arrives while others run starts as soon as a slot and memory free up.  Render
-  requests of one scene that wait together (with no training step of that scene
-  between them) start as one multi-view render: one projection over their
-  views, one sort, one blend launch.  Each keeps its own image, equal to the one
-  it gets alone (the forward pass has no cross-view arithmetic).
+* Continuous batching: waiting requests of one kind and one image size start
+  together as one batch in shared launches (gs_project_batch, gs_bin_sort,
+  gs_raster_fwd, gs_raster_bwd_batch, gs_tr_update_batch; engine.BatchStep):
+  each request is one view of the batch frame with its own scene, objective,
+  probes and update, so that many small requests fill one set of launches
+  instead of each paying for a full sequence of small kernels.  A batch of
+  training steps holds at most one request per scene (a step changes its
+  scene); renders of one scene may share a batch.  Every batch runs on its own
+  stream, so batches overlap on the device, and a request that arrives while
+  others run starts as soon as a slot and memory free up.  Each request keeps
+  its own result, equal to the one it gets alone.
 * Latency of a request = completion (its end event observed by the host) minus
   arrival, both on the host clock.
 
@@ -44,7 +48,7 @@ import torch
 
 from . import gs3dtr as G
 from . import synth
-from .engine import TRConfig, TRStep, eps_schedule
+from .engine import BatchEntry, BatchStep, TRConfig, TRStep, eps_schedule
 
 
 @dataclass
@@ -137,14 +141,15 @@ class Scene:
                 e.render(stream)
         return e
 
-    def enqueue_renders(self, reqs: list, stream) -> TRStep:
-        """One multi-view render of the requests' views on `stream`; image j of
-        the returned step belongs to reqs[j]."""
-        with torch.cuda.stream(stream):
-            e = self.make_step(len(reqs))
-            e.cams = torch.cat([self.cams[96 * r.view: 96 * (r.view + 1)] for r in reqs])
-            e.render(stream)
-        return e
+    def entry(self, req: Request) -> BatchEntry:
+        """The batch entry of a request of this scene; a training step takes the
+        scene's next step index."""
+        cam = self.cams[96 * req.view: 96 * (req.view + 1)]
+        if req.kind == "train":
+            self.t += 1
+            return BatchEntry(self.x, self.g_ema, self.d_ema, self.n, cam, self.targets[req.view], self.t,
+                              eps_schedule(self.t, self.total_steps))
+        return BatchEntry(self.x, self.g_ema, self.d_ema, self.n, cam, None, max(self.t, 1))
 
 
 @dataclass
@@ -215,20 +220,38 @@ def plain_loop(scenes: list[Scene], stream_spec, stream=None, keep_results: bool
 class Server:
     """Continuous batching of requests over resident scenes (see the module text)."""
 
-    def __init__(self, scenes: list[Scene], slots: int = 4, budget_bytes: int | None = None):
+    def __init__(self, scenes: list[Scene], slots: int = 4, budget_bytes: int | None = None, max_batch: int = 8):
         self.scenes = _by_sid(scenes)
         self.streams = [torch.cuda.Stream() for _ in range(slots)]
         self.budget = budget_bytes if budget_bytes is not None else 1 << 62
+        self.max_batch = max(1, min(max_batch, G.GS_BATCH_MAX))
         # each slot's status word lands here by an asynchronous copy on the slot's
         # stream, so that reading it never synchronises with requests in flight
         self.status_host = torch.zeros(slots, dtype=torch.int32).pin_memory()
 
-    def run(self, stream_spec, keep_results: bool = False, max_render_batch: int = 8) -> ServeResult:
+    def batch_bytes(self, reqs: list) -> int:
+        scs = [self.scenes[r.scene] for r in reqs]
+        s0 = scs[0]
+        return BatchStep.working_bytes([synth.pad_count(sc.n) for sc in scs], s0.W, s0.H, sh_degree=s0.deg,
+                                       nu=s0.nu, tile=s0.tile, capacity=sum(sc.capacity for sc in scs),
+                                       train=reqs[0].kind == "train")
+
+    def start(self, batch: list, stream) -> BatchStep:
+        scs = [self.scenes[r.scene] for r in batch]
+        s0 = scs[0]
+        with torch.cuda.stream(stream):
+            bs = BatchStep([sc.entry(r) for sc, r in zip(scs, batch)], s0.W, s0.H, sh_degree=s0.deg, nu=s0.nu,
+                           tile=s0.tile, capacity=sum(sc.capacity for sc in scs), train=batch[0].kind == "train",
+                           cfg=s0.cfg, device=str(s0.device))
+            bs.run(stream)
+        return bs
+
+    def run(self, stream_spec, keep_results: bool = False) -> ServeResult:
         reqs = _requests(stream_spec)
         waiting = deque()
         upcoming = deque(reqs)
         free = list(range(len(self.streams)))
-        inflight = {}  # slot -> (requests, step, end event, bytes)
+        inflight = {}  # slot -> (requests, batch step, end event, bytes)
         busy = set()
         used = peak = 0
         statuses = []
@@ -237,22 +260,24 @@ class Server:
             now = time.perf_counter() - t0
             # completions
             for slot in list(inflight):
-                batch, e, ev, nb = inflight[slot]
+                batch, bs, ev, nb = inflight[slot]
                 if ev.query():
                     done = time.perf_counter() - t0
                     statuses.append(int(self.status_host[slot]))
                     for j, r in enumerate(batch):
                         r.done = done
                         if keep_results and r.kind == "render":
-                            r.image = e.image.view(len(batch), -1)[j]
-                    busy.discard(batch[0].scene)
+                            r.image = bs.images()[j]
+                    for r in batch:
+                        busy.discard(r.scene)
                     used -= nb
                     free.append(slot)
                     del inflight[slot]
             while upcoming and upcoming[0].arrival <= now:
                 waiting.append(upcoming.popleft())
-            # admissions, in arrival order; a scene whose request cannot start
-            # admits none of its later ones in this pass
+            # admissions, in arrival order: a request starts with the later ones
+            # of its kind and image size that may join it; a scene whose earliest
+            # waiting request cannot start admits none of its later ones
             started = False
             blocked = set()
             taken = set()
@@ -262,46 +287,48 @@ class Server:
                 if r.rid in taken:
                     continue
                 sc = self.scenes[r.scene]
-                nb = sc.working_bytes(r.kind)
-                if nb > self.budget:  # can never fit: rejected at once
+                if self.batch_bytes([r]) > self.budget:  # can never fit: rejected at once
                     r.rejected = True
                     r.start = r.done = time.perf_counter() - t0
                     waiting.remove(r)
                     continue
-                if r.scene in busy or r.scene in blocked or used + nb > self.budget:
+                if r.scene in busy or r.scene in blocked or used + self.batch_bytes([r]) > self.budget:
                     blocked.add(r.scene)
                     continue
                 batch = [r]
-                if r.kind == "render":
-                    # later renders of this scene up to its next training step
-                    after = False
-                    for q in waiting:
-                        if len(batch) >= max_render_batch:
-                            break
-                        if q is r:
-                            after = True
-                            continue
-                        if not after or q.scene != r.scene:
-                            continue
-                        if q.kind != "render":
-                            break
-                        nb2 = sc.working_bytes("render", len(batch) + 1)
-                        if used + nb2 > self.budget:
-                            break
+                later_blocked = set(blocked)
+                after = False
+                for q in waiting:
+                    if len(batch) >= self.max_batch:
+                        break
+                    if q is r:
+                        after = True
+                        continue
+                    if not after or q.rid in taken:
+                        continue
+                    qs = self.scenes[q.scene]
+                    joins = (q.kind == r.kind and (qs.W, qs.H) == (sc.W, sc.H) and q.scene not in busy
+                             and q.scene not in later_blocked
+                             and (q.kind == "render" or all(b.scene != q.scene for b in batch))
+                             and used + self.batch_bytes(batch + [q]) <= self.budget)
+                    if joins:
                         batch.append(q)
-                        nb = nb2
+                    else:
+                        later_blocked.add(q.scene)  # none of its later requests may overtake q
+                nb = self.batch_bytes(batch)
                 slot = free.pop()
                 st = self.streams[slot]
                 start = time.perf_counter() - t0
                 for q in batch:
                     q.nbytes, q.start, q.batch = nb, start, len(batch)
-                e = sc.enqueue(r, st) if len(batch) == 1 else sc.enqueue_renders(batch, st)
+                bs = self.start(batch, st)
                 with torch.cuda.stream(st):
-                    self.status_host[slot: slot + 1].copy_(e.status, non_blocking=True)
+                    self.status_host[slot: slot + 1].copy_(bs.status, non_blocking=True)
                 ev = torch.cuda.Event()
                 ev.record(st)
-                inflight[slot] = (batch, e, ev, nb)
-                busy.add(r.scene)
+                inflight[slot] = (batch, bs, ev, nb)
+                for q in batch:
+                    busy.add(q.scene)
                 used += nb
                 peak = max(peak, used)
                 for q in batch:

@@ -36,7 +36,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 STRUCTS = ["gs_params", "gs_camera", "gs_frame", "gs_probe", "gs_eps_schedule", "gs_projected", "gs_sorted",
-           "gs_loss", "gs_tr_config", "gs_adam_config"]
+           "gs_loss", "gs_tr_config", "gs_adam_config", "gs_batch_item"]
 
 
 def test_struct_sizes_match_header_layout(tmp_path):

@@ -1,6 +1,7 @@
 """The serving loop: each request's result is the same alone and in a mix whose
-requests overlap on the device, admission keeps the working sets within the HBM
-budget, and the plain loop serves in arrival order.
+requests overlap on the device or share launches with requests of other scenes,
+admission keeps the working sets within the HBM budget, and the plain loop
+serves in arrival order.
 
 Results are compared within the tolerances of the parity tests (the reverse
 pass adds with float atomics, so runs agree to rounding, not bit for bit).
@@ -15,7 +16,7 @@ torch = pytest.importorskip("torch")
 def scenes():
     from paper_2602_00395_gb300.serve import Scene
     return [Scene(0, 20000, 256, 256, n_views=4), Scene(1, 30000, 320, 240, n_views=4),
-            Scene(2, 15000, 256, 192, n_views=4)]
+            Scene(2, 15000, 256, 192, n_views=4), Scene(3, 9000, 256, 256, n_views=4)]
 
 
 def _snapshot(sc):
@@ -61,6 +62,34 @@ def test_results_equal_alone_and_in_the_mix(scenes):
         _restore(sc, sn)
 
 
+def test_requests_of_several_scenes_sharing_launches_equal_each_alone(scenes):
+    """Training steps of scenes 0 and 3 (same image size, 20k and 9k Gaussians)
+    waiting together start as one batch; every scene's state and every render
+    equals what it gets served alone."""
+    from paper_2602_00395_gb300.serve import Server
+    snaps = [_snapshot(sc) for sc in scenes]
+    ref = {}
+    for sid in (0, 3):
+        Server(scenes, slots=2).run([(0.0, "train", sid, 1), (0.0, "train", sid, 2)])
+        ref[sid] = [b.clone() for b in (scenes[sid].x, scenes[sid].g_ema, scenes[sid].d_ema)]
+        img = Server(scenes, slots=2).run([(0.0, "render", sid, 3)], keep_results=True).requests[0].image.clone()
+        ref[sid].append(img)
+    for sc, sn in zip(scenes, snaps):
+        _restore(sc, sn)
+    spec = [(0.0, "train", 0, 1), (0.0, "train", 3, 1), (0.0, "train", 0, 2), (0.0, "train", 3, 2),
+            (0.0, "render", 0, 3), (0.0, "render", 3, 3)]
+    res = Server(scenes, slots=4).run(spec, keep_results=True)
+    assert set(res.summary()["status_words"]) == {0}
+    assert [r.batch for r in res.requests] == [2, 2, 2, 2, 2, 2]
+    for sid in (0, 3):
+        for got, want in zip((scenes[sid].x, scenes[sid].g_ema, scenes[sid].d_ema), ref[sid][:3]):
+            _close(got, want, 1e-4)
+        img = [r for r in res.requests if r.scene == sid and r.kind == "render"][0].image
+        assert float((img - ref[sid][3]).abs().max()) <= 1e-5
+    for sc, sn in zip(scenes, snaps):
+        _restore(sc, sn)
+
+
 def test_waiting_renders_of_a_scene_start_as_one_multi_view_render(scenes):
     """Renders of one scene that wait together start as one launch sequence and
     each image equals the one the plain loop renders alone; a training step of
@@ -90,7 +119,9 @@ def test_waiting_renders_of_a_scene_start_as_one_multi_view_render(scenes):
 def test_admission_keeps_working_sets_within_the_budget(scenes):
     from paper_2602_00395_gb300.serve import Server
     snaps = [_snapshot(sc) for sc in scenes]
-    sizes = sorted(sc.working_bytes("train") for sc in scenes)
+    from paper_2602_00395_gb300.serve import Request
+    probe = Server(scenes, slots=1)
+    sizes = sorted(probe.batch_bytes([Request(0, 0.0, "train", s, 0)]) for s in range(3))
     budget = sizes[-1] + sizes[0] // 2  # the largest fits, never two of the larger ones together
     spec = [(0.0, "train", s, v) for v in range(2) for s in range(3)]
     res = Server(scenes, slots=4, budget_bytes=budget).run(spec)
