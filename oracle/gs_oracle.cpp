@@ -840,6 +840,7 @@ Flip blend_flips(const View& V, size_t tile, double pcx, double pcy, int nc, std
   std::vector<int> extra_at;  // list positions at which possibly-present splats sort
   double prev_depth = -1.0, prev_a = 0.0;
   int prev_i = -1;
+  bool drop_rest = false;  // a termination the GPU may take earlier lies in front
   bool prev_blended = false;
   // the walk order: the list, with the possibly-present splats merged in by key
   size_t li = 0, ei = 0;
@@ -910,15 +911,33 @@ Flip blend_flips(const View& V, size_t tile, double pcx, double pcy, int nc, std
         f.impact += T * cmax;
         f.t_impact += T;
         f.nc_hi = (int)list.size();
+        if (owns) {
+          // the splats it may then blend, from this one on, at most at this T
+          double Tc = T;
+          const size_t from = li - 1;  // this splat's list index
+          for (size_t u = from; u < list.size() && Tc >= 0.5 * kTMin; ++u) {
+            const Splat<double>& h = sp[list[u]];
+            const double hx = h.mx - pcx, hy = h.my - pcy;
+            const double hp = -0.5 * (h.A * hx * hx + h.C * hy * hy) - h.B * hx * hy;
+            const double hoG = h.o * std::exp(std::min(hp, 0.0));
+            if (hoG < 0.5 * kAlphaMin) continue;
+            const double ha = std::min(hoG, 1.0 - 1e-6);
+            owns->push_back({list[u], ha, hoG / h.o, hx, hy, Tc});
+            Tc *= 1.0 - std::min(hoG, kAlphaMax);
+          }
+        }
       }
       break;
     }
-    if (near_term) {  // the GPU may stop here
+    if (near_term) {  // the GPU may stop here: this splat and all behind it may be missing
       f.kinds |= 2;
       f.impact += T * cmax;
       f.t_impact += T;
       f.nc_lo = std::min(f.nc_lo, firm_last);
+      drop_rest = true;
     }
+    if (owns && drop_rest && !(near || !e.in_list || is_maybe(e.i) || std::fabs(oG / kAlphaMax - 1.0) <= dp + 2e-6))
+      owns->push_back({e.i, std::min(oG, 1.0 - 1e-6), oG / g.o, dx, dy, T});
     const bool amb = is_maybe(e.i);
     if (near || amb) {
       f.kinds |= near ? 1 : 4;
@@ -1777,21 +1796,26 @@ double backward_impl(const double* P, long pitch, long n, int deg, const double*
       double sens[3] = {0.0, 0.0, 0.0};
       const size_t tile = (size_t)ty * V.Tx + tx;
       ofl.clear();
+      // how far the GPU's residual here may be from the oracle's: its colour's
+      // rounding (capped at the image tolerance) plus what decision flips do to it
+      double e_res = 0.0;
       if (sensing || allowing) {
-        const double e_px = std::min(blend_flips(V, tile, x + 0.5, y + 0.5, nc, allowing ? &ofl : nullptr).err,
-                                     kImageTol);
+        const Flip fl = blend_flips(V, tile, x + 0.5, y + 0.5, nc, allowing ? &ofl : nullptr);
+        e_res = std::min(fl.err, kImageTol) + fl.impact;
         for (int ch = 0; sensing && ch < 3; ++ch) {
           const double r = std::fabs(C[ch] - tg[ch * HW + px]);
-          sens[ch] = r + e_px > gn_floor ? e_px / std::max(r, gn_floor) : 0.0;
+          sens[ch] = r + e_res > gn_floor ? e_res / std::max(r, gn_floor) : 0.0;
         }
       }
       if (allowing) {
-        // own decisions that may flip here, and (L1) residual signs within the
-        // image tolerance, whose dL/dC then changes by 2 |w|
+        // own decisions that may flip here, and dL/dC's own uncertainty: (L1) a
+        // residual sign within e_res changes it by 2 |w|, (L2) w = r/m moves by e_res/m
         for (const OwnFlip& q : ofl) own_terms(V.sp[q.i], q, V.tile_cmax[tile], w, cot_allow[0].data() + q.i * NQ);
         double wflip[3];
-        for (int ch = 0; ch < 3; ++ch)
-          wflip[ch] = (loss_kind == 0 && std::fabs(C[ch] - tg[ch * HW + px]) < kImageTol) ? 2.0 * w[ch] : 0.0;
+        for (int ch = 0; ch < 3; ++ch) {
+          const double r = std::fabs(C[ch] - tg[ch * HW + px]);
+          wflip[ch] = loss_kind == 0 ? (r < e_res ? 2.0 * w[ch] : 0.0) : (loss_kind == 1 ? e_res / m : 0.0);
+        }
         blend_reverse_abs(tr, V.sp, wflip, cot_allow[0].data());
         trel = trace_rounding(tr, V.sp, ofl, V.tile_cmax[tile]);
         blend_reverse_abs(tr, V.sp, w, cot_round[0].data(), &trel);
@@ -2134,6 +2158,7 @@ void or_backward_sampled(const double* P, long pitch, long n, int deg, const dou
     std::vector<std::vector<double>> cround(allow ? 1 + nu : 0, std::vector<double>((size_t)n * NQ, 0.0));
     TraceRounding trel;
     std::vector<OwnFlip> pflips;
+    std::vector<double> cflipw(allow ? (size_t)n * NQ : 0, 0.0);  // dL/dC uncertainty, every splat
     struct Own {
       long sidx;
       double a, G, dx, dy, T;
@@ -2164,10 +2189,13 @@ void or_backward_sampled(const double* P, long pitch, long n, int deg, const dou
             long px = (long)y * V.cam.W + x;
             double w[3], wgn[3], sens[3], rmin = kInf;
             pflips.clear();
-            const double e_px =
-                masses ? std::min(blend_flips(V, (size_t)ty * V.Tx + tx, x + 0.5, y + 0.5, nc, &pflips).err,
-                                  eps_img)
-                       : 0.0;
+            // the residual's uncertainty: the colour's rounding (capped at the
+            // image tolerance) plus what decision flips do to it
+            double e_px = 0.0;
+            if (masses) {
+              const Flip fl = blend_flips(V, (size_t)ty * V.Tx + tx, x + 0.5, y + 0.5, nc, &pflips);
+              e_px = std::min(fl.err, eps_img) + fl.impact;
+            }
             for (int ch = 0; ch < 3; ++ch) {
               double r = C[ch] - tg[ch * HW + px];
               rmin = std::min(rmin, std::fabs(r));
@@ -2216,20 +2244,27 @@ void or_backward_sampled(const double* P, long pitch, long n, int deg, const dou
                   break;
                 }
               }
-              owns.push_back({sidx, std::min(oG, 1.0 - 1e-6), oG / g.o, dx, dy, Ts, own_near || membership});
+              // a flip the walk records for it (its own decisions, a termination
+              // in front of it that the GPU may take elsewhere)
+              bool listed = false;
+              for (const OwnFlip& pf : pflips) listed = listed || pf.i == si;
+              owns.push_back({sidx, std::min(oG, 1.0 - 1e-6), oG / g.o, dx, dy, Ts, own_near || membership || listed});
             }
             blend_reverse(tr, V.sp, w, cot[0].data());
             if (masses) blend_reverse_abs(tr, V.sp, w, cab[0].data());
             if (allow) {
-              // a residual whose sign may flip changes its dL/dC by 2 |w|
+              // dL/dC's own uncertainty: (L1) a residual whose sign may flip
+              // changes it by 2 |w|, (L2) w = r/m moves by e_px/m
               double wflip[3];
-              for (int ch = 0; ch < 3; ++ch)
-                wflip[ch] = (loss_kind == 0 && std::fabs(C[ch] - tg[ch * HW + px]) < eps_img) ? 2.0 * w[ch] : 0.0;
+              for (int ch = 0; ch < 3; ++ch) {
+                const double r = std::fabs(C[ch] - tg[ch * HW + px]);
+                wflip[ch] = loss_kind == 0 ? (r < e_px ? 2.0 * w[ch] : 0.0) : e_px / m;
+              }
               for (const Own& q : owns) {
                 double* out = al.data() + ((size_t)q.sidx * (1 + nu)) * NQ;
                 if (q.own) own_add(q, w, out);
-                own_add(q, wflip, out);
               }
+              blend_reverse_abs(tr, V.sp, wflip, cflipw.data());
               trel = trace_rounding(tr, V.sp, pflips, own_cmax);
               blend_reverse_abs(tr, V.sp, w, cround[0].data(), &trel);
             }
@@ -2273,6 +2308,7 @@ void or_backward_sampled(const double* P, long pitch, long n, int deg, const dou
         if (!out) continue;
         for (int r = 0; r < rows; ++r) out[sidx * rows + r] += g_acc[r] / (st == 0 ? 1.0 : nu);
       }
+      for (int q = 0; allow && q < NQ; ++q) al[((size_t)sidx * (1 + nu)) * NQ + q] += cflipw[(size_t)i * NQ + q];
       for (int st = 0; allow && st <= nu; ++st) {
         std::fill(g_acc.begin(), g_acc.end(), 0.0);
         project_reverse_abs(P, pitch, i, deg, V.cam, al.data() + ((size_t)sidx * (1 + nu) + st) * NQ, g_acc);

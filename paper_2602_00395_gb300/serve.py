@@ -220,11 +220,16 @@ def plain_loop(scenes: list[Scene], stream_spec, stream=None, keep_results: bool
 class Server:
     """Continuous batching of requests over resident scenes (see the module text)."""
 
-    def __init__(self, scenes: list[Scene], slots: int = 4, budget_bytes: int | None = None, max_batch: int = 8):
+    def __init__(self, scenes: list[Scene], slots: int = 4, budget_bytes: int | None = None, max_batch: int = 8,
+                 max_pad_ratio: float | None = 4.0):
+        """max_pad_ratio: a request joins a batch only if its scene's Gaussian
+        count is within this factor of the batch's first (every slot of a batch
+        is padded to the largest scene); None for any."""
         self.scenes = _by_sid(scenes)
         self.streams = [torch.cuda.Stream() for _ in range(slots)]
         self.budget = budget_bytes if budget_bytes is not None else 1 << 62
         self.max_batch = max(1, min(max_batch, G.GS_BATCH_MAX))
+        self.max_pad_ratio = max_pad_ratio
         # each slot's status word lands here by an asynchronous copy on the slot's
         # stream, so that reading it never synchronises with requests in flight
         self.status_host = torch.zeros(slots, dtype=torch.int32).pin_memory()
@@ -307,7 +312,9 @@ class Server:
                     if not after or q.rid in taken:
                         continue
                     qs = self.scenes[q.scene]
-                    joins = (q.kind == r.kind and (qs.W, qs.H) == (sc.W, sc.H) and q.scene not in busy
+                    near_size = (self.max_pad_ratio is None
+                                 or max(qs.n, sc.n) <= self.max_pad_ratio * max(1, min(qs.n, sc.n)))
+                    joins = (q.kind == r.kind and (qs.W, qs.H) == (sc.W, sc.H) and near_size and q.scene not in busy
                              and q.scene not in later_blocked
                              and (q.kind == "render" or all(b.scene != q.scene for b in batch))
                              and used + self.batch_bytes(batch + [q]) <= self.budget)

@@ -149,3 +149,49 @@ def test_hutchinson_sensitivity_bounds_residual_moves():
         assert np.all(moved <= 1.02 * r0["hz_sens"] + 1e-15 * np.abs(r0["hz"]).max())
     on = r0["hz_sens"] > 0
     assert (moved[on] / r0["hz_sens"][on]).max() > 0.9
+
+
+def _skip_scene():
+    cam = _cam()
+    P = _scene([(0.0, 0.0, 0.5, -2.5, 0.0, (0.9, 0.2, 0.1)),
+                (0.03, -0.02, 0.0, -2.5, 0.0, (0.1, 0.8, 0.3)),
+                (0.0, 0.01, -0.5, -2.0, 1.0, (0.2, 0.3, 0.9))])
+    _, G = _alpha_at(P, 1, cam)
+    P[10, 1] = _logit((1.0 / 255.0) / G)
+    return P, 1
+
+
+def _termination_scene():
+    cam = _cam()
+    P = _scene([(0.0, 0.0, 0.6, -1.5, 0.0, (0.9, 0.1, 0.1)),
+                (0.0, 0.0, 0.3, -1.5, 0.0, (0.1, 0.9, 0.1)),
+                (0.0, 0.0, 0.0, -1.5, 0.0, (0.1, 0.1, 0.9)),
+                (0.0, 0.0, -0.3, -1.5, 0.0, (0.8, 0.8, 0.8))])
+    for i, a in enumerate((0.96, 0.97, None, 0.5)):
+        _, G = _alpha_at(P, i, cam)
+        if a is not None:
+            P[10, i] = _logit(a / G)
+    _, G = _alpha_at(P, 2, cam)
+    P[10, 2] = _logit((1.0 - 1e-4 / ((1 - 0.96) * (1 - 0.97))) / G)
+    return P, 2
+
+
+@pytest.mark.parametrize("make", [_skip_scene, _termination_scene])
+def test_gradient_allowances_bound_the_flips(make):
+    """At a skip or termination decision on its threshold, the gradient on either
+    side of the flip differs by no more than the oracle's allowances (flips of a
+    Gaussian's own decisions, terminations in front of it, and the rounding)."""
+    cam = _cam()
+    P, k = make()
+    target = np.full((1, 3, H, W), 0.25)
+    r0 = O.backward(P, 0, [cam], target, loss_kind=1, masses=True)
+    bound = r0["grad_allow"] + r0["grad_round"]
+    assert bound.max() > 0
+    side = []
+    for d in (-1e-9, 1e-9):
+        Q = P.copy()
+        Q[10, k] += d
+        side.append(O.backward(Q, 0, [cam], target, loss_kind=1)["grad"])
+    moved = np.abs(side[1] - side[0])
+    assert moved.max() > 0
+    assert np.all(moved <= bound + 1e-12 * np.abs(r0["grad"]).max())
