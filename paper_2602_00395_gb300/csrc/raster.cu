@@ -363,6 +363,11 @@ __device__ __forceinline__ bool block_sees(const Rec& r, float x0, float y0) {
   return r.a.x + hx >= x0 && r.a.x - hx <= x0 + 7.f && r.a.y + hy >= y0 && r.a.y - hy <= y0 + 7.f;
 }
 
+// 1: skip the reverse of a lane's first or second pixel when no lane of the
+// warp blends the splat at that pixel.
+#ifndef GS_BWD_SKIP_IDLE_ROW
+#define GS_BWD_SKIP_IDLE_ROW 0
+#endif
 // A splat that at most this many lanes of a warp blend is added by those lanes
 // one by one (each its own row of partial derivatives, as float4 atomics)
 // instead of through the warp-wide reduction (0: always reduce).
@@ -651,8 +656,20 @@ __global__ void GS_BWD_BOUNDS raster_bwd_kernel(
         const uint32_t act = __ballot_sync(0xffffffffu, on[0] || on[1]);  // lanes that blend the splat
         if (!act) continue;
         float v[32];
+#if GS_BWD_SKIP_IDLE_ROW
+        // a pixel row of the block (the lanes' first or second pixels) that no
+        // lane blends the splat at adds exact zeros and keeps its state: skip it
+        const bool any0 = __any_sync(0xffffffffu, on[0]), any1 = __any_sync(0xffffffffu, on[1]);
+        if (any0) {
+          bwd_accumulate<S, true>(pix[0], r, dx[0], dy[0], G[0], oG[0], alpha[0], v);
+          if (any1) bwd_accumulate<S, false>(pix[1], r, dx[1], dy[1], G[1], oG[1], alpha[1], v);
+        } else {
+          bwd_accumulate<S, true>(pix[1], r, dx[1], dy[1], G[1], oG[1], alpha[1], v);
+        }
+#else
         bwd_accumulate<S, true>(pix[0], r, dx[0], dy[0], G[0], oG[0], alpha[0], v);
         bwd_accumulate<S, false>(pix[1], r, dx[1], dy[1], G[1], oG[1], alpha[1], v);
+#endif
 #pragma unroll
         for (int q = 9 * S; q < 32; ++q) v[q] = 0.f;
         const uint32_t gi = s_idx[st * batch + j];
