@@ -583,26 +583,34 @@ def raster_bwd_flops_per_unit() -> int:
     return 50 * (1 + NU)
 
 
-# DRAM bytes of one gs_raster_bwd call on this workload (its two kernels, read
-# plus write; the workspace clear is a memset, not counted) from one ncu capture
-# (its summary is kept under profiles/), valid while the kernel
-# sources are the ones captured (their SHA-256 below); otherwise null.
+# DRAM bytes of one gs_raster_bwd call (its two kernels, read plus write; the
+# workspace clear is a memset, not counted) from one-kernel ncu captures of the
+# 2-view case (summaries under profiles/), with that case's pair count: a full
+# launch's traffic is scaled from it by the pairs (the gathered records and the
+# cotangent rows grow with the pairs and views).  Valid while the kernel sources
+# are the ones captured (their SHA-256 below); otherwise null.
 RASTER_BWD_TRAFFIC = {
-    "bytes": 2279314432 + 389193728 + 1132078848 + 432877056,
+    "bytes": None,
+    "pairs": None,
     "sources": {
-        "paper_2602_00395_gb300/csrc/raster.cu": "8c736d14d0e1081a966c2f9a5bfddffcc802b091da2ed210c8a3c7728ab54b50",
-        "paper_2602_00395_gb300/csrc/common.cuh": "f6b0e9b6b861641997b64475b07485e6e52b5fe48da9e63867facaa5cffb4c58",
+        "paper_2602_00395_gb300/csrc/raster.cu": None,
+        "paper_2602_00395_gb300/csrc/common.cuh": None,
     },
 }
 
 
-def raster_bwd_traffic():
+def raster_bwd_traffic(pairs: float | None = None):
+    """Traffic of one reverse call with `pairs` pairs, scaled from the capture."""
     import hashlib
+    if RASTER_BWD_TRAFFIC["bytes"] is None:
+        return None
     for rel, digest in RASTER_BWD_TRAFFIC["sources"].items():
         with open(os.path.join(ROOT, rel), "rb") as f:
             if hashlib.sha256(f.read()).hexdigest() != digest:
                 return None
-    return RASTER_BWD_TRAFFIC["bytes"]
+    if pairs is None or not RASTER_BWD_TRAFFIC["pairs"]:
+        return RASTER_BWD_TRAFFIC["bytes"]
+    return RASTER_BWD_TRAFFIC["bytes"] * pairs / RASTER_BWD_TRAFFIC["pairs"]
 
 
 def fp32_peak_tflops(n_sm: int, sm_mhz: float) -> float:
@@ -885,7 +893,7 @@ def rooflines(eng, per_call, sum_nc, pairs_timed, local, full_size):
         traffic = None
     else:
         name, ms_k, per_unit = "gs_raster_bwd (reverse blend, 1+nu streams, + projection reverse)", bwd_ms, raster_bwd_flops_per_unit()
-        traffic = raster_bwd_traffic() if full_size else None
+        traffic = raster_bwd_traffic(pairs_timed) if full_size else None
     achieved = per_unit * sum_nc / (ms_k * 1e-3) / 1e12
     roof = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
             "frac": achieved / fp32_peak, "traffic": traffic, "launch_ms": ms_k,

@@ -10,9 +10,10 @@ def test_traffic_is_reported_only_for_the_captured_sources(monkeypatch):
     import hashlib
     sources = {rel: hashlib.sha256(open(os.path.join(bench.ROOT, rel), "rb").read()).hexdigest()
                for rel in bench.RASTER_BWD_TRAFFIC["sources"]}
-    same = dict(bench.RASTER_BWD_TRAFFIC, sources=sources)
+    same = dict(bench.RASTER_BWD_TRAFFIC, sources=sources, bytes=1000, pairs=10)
     monkeypatch.setattr(bench, "RASTER_BWD_TRAFFIC", same)
-    assert bench.raster_bwd_traffic() == same["bytes"]
+    assert bench.raster_bwd_traffic() == 1000
+    assert bench.raster_bwd_traffic(40) == 4000  # scaled by the pairs
     changed = dict(same, sources=dict(sources))
     first = next(iter(changed["sources"]))
     changed["sources"][first] = "0" * 64
