@@ -629,12 +629,12 @@ def peaks():
 # ------------------------------------------------------------------ CPU oracle
 def _oracle_view(job):
     """One view's share of an oracle step (forward, reverse pass with the
-    Hutchinson product) at 1/frac of the Gaussians; returns (seconds, grad, hz)."""
-    frac, v = job
+    Hutchinson product) on the bench scene of n Gaussians; returns (seconds,
+    grad, hz)."""
+    n, v = job
     import numpy as np
     import oracle as O
     from paper_2602_00395_gb300 import synth as S
-    n = N_GAUSS // frac
     sc = S.make_scene(n, SH_DEG, seed=1000, kind="clusters", extent=10.0)
     cam = [S.camera_ring(RING, W, H, 10.0, seed=7)[v * (RING // N_VIEWS)]]
     target = S.noise_target(1, H, W, seed=2000 + v).astype(np.float64)
@@ -650,114 +650,75 @@ def oracle_pool():
     import multiprocessing as mp
     cores = min(N_VIEWS, os.cpu_count() or 1)
     ex = cf.ProcessPoolExecutor(max_workers=cores, mp_context=mp.get_context("spawn"))
-    list(ex.map(_oracle_view, [(N_GAUSS // 1000, v) for v in range(cores)]))  # workers up, oracle loaded
+    list(ex.map(_oracle_view, [(1000, v) for v in range(cores)]))  # workers up, oracle loaded
     return ex, cores
 
 
-def oracle_sample(frac: int = 100, parallel: bool = True, pool=None):
-    """Bounded oracle sample of one full step (forward, reverse pass with the
-    Hutchinson product, update) at 1/frac of the Gaussians, nu = 2, 1080p.
-    parallel: the 8 views in 8 processes (spawned) on the host's cores, then
-    their gradients summed and the update, timed by the wall clock; otherwise
-    one view on one core, scaled by 8.  The result is scaled x frac to the full
-    Gaussian count.  Returns (seconds, scale, description, cores)."""
-    import numpy as np
-    import oracle as O
-    from paper_2602_00395_gb300 import synth as S
-    n = N_GAUSS // frac
-    if parallel:
-        ex, cores = pool if pool is not None else oracle_pool()
-        try:
-            t0 = time.perf_counter()
-            res = list(ex.map(_oracle_view, [(frac, v) for v in range(N_VIEWS)]))
-            g = sum(r[1] for r in res)
-            hz = sum(r[2] for r in res)
-            P = O.params64(S.make_scene(n, SH_DEG, seed=1000, kind="clusters", extent=10.0))
-            O.tr_update(P, np.zeros_like(P), np.zeros_like(P), g, hz, SH_DEG, t=1, eps=1e-6, cfg=O.tr_config(l=1))
-            dt = time.perf_counter() - t0
-        finally:
-            if pool is None:
-                ex.shutdown()
-        return dt, frac, (f"{n} Gaussians (1/{frac}), all {N_VIEWS} views at {W}x{H} in {cores} spawned "
-                          f"processes, nu={NU}, one full step; scaled x{frac}"), cores
-    dt, g, hz = _oracle_view((frac, 0))
-    P = O.params64(S.make_scene(n, SH_DEG, seed=1000, kind="clusters", extent=10.0))
-    t0 = time.perf_counter()
-    O.tr_update(P, np.zeros_like(P), np.zeros_like(P), g, hz, SH_DEG, t=1, eps=1e-6, cfg=O.tr_config(l=1))
-    dt += time.perf_counter() - t0
-    scale = frac * N_VIEWS
-    return dt, scale, (f"{n} Gaussians (1/{frac}), 1 of {N_VIEWS} views at {W}x{H}, nu={NU}, one full step, "
-                       f"single thread; scaled x{scale}"), 1
-
-
 def run_reference(args):
-    """The FP64 oracle on the host's cores, on bounded samples of the workload:
-    each step is one sample (1/100 of the Gaussians, all 8 views in spawned
-    processes, then the update), timed by the wall clock.  The line reports the
-    samples it ran (steps, ms_per_step = measured time per sample) and the
-    metric scaled from them (value = 1 / (ms_per_step x sample_scale))."""
+    """The FP64 oracle on the host's cores, timed on whole steps of the workload
+    (all 1M Gaussians, the 8 views in spawned processes, gradients summed, the
+    update; nothing scaled), by the wall clock.  A step takes tens of seconds, so
+    the arm times as many of the requested steps as fit about three minutes and
+    reports the steps it ran."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return
     import __graft_entry__  # noqa: F401
     import oracle
     oracle.build()
-    frac = 100
     pool = oracle_pool()
-    nwarm = min(1, max(0, args.warmup))  # one warm-up sample is enough for a CPU program
     try:
-        for _ in range(nwarm):
-            oracle_sample(frac, pool=pool)
-        times = []
-        desc, cores = "", 1
-        for _ in range(args.steps):
-            dt, scale, desc, cores = oracle_sample(frac, pool=pool)
-            times.append(dt)
+        times, full = [], None
+        for k in range(max(1, args.steps)):
+            full = oracle_full_step(pool, args.n)
+            times.append(full["oracle_full_step_s"])
+            if sum(times) + times[-1] > 180.0:
+                break
     finally:
         pool[0].shutdown()
-    sample_s = sum(times) / len(times)
-    val = 1.0 / (sample_s * scale)
+    step_s = sum(times) / len(times)
+    val = 1.0 / step_s
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": len(times), "warmup": nwarm, "ms_per_step": sample_s * 1e3, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "sample_scale": scale,
-        "value_note": (f"each step ran one sample; value = 1 / (ms_per_step x {scale}) in full-workload steps/s "
-                       "(a full oracle step at 1M Gaussians is measured apart: bench.py --oracle-full-step)"),
-        "config": {"workload": WORKLOAD, "sample": desc},
-        "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+        "steps": len(times), "steps_requested": args.steps, "warmup": 0, "ms_per_step": step_s * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": full["sample"]},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": full["cores"], "kind": "oracle",
+                         "sample": full["sample"]},
         "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
 
-def _oracle_view_full(v):
-    """One view of a full oracle step on the whole bench scene; returns (seconds, grad, hz)."""
-    return _oracle_view((1, v))
 
 
-def oracle_full_step():
+
+def oracle_full_step(pool=None, n: int = N_GAUSS):
     """One full oracle step of the bench workload, nothing scaled: all 1M
     Gaussians, the 8 views of one batch in spawned processes (one per view),
-    gradients and Hutchinson diagonals summed, then the update; by the wall clock."""
-    import concurrent.futures as cf
-    import multiprocessing as mp
+    gradients and Hutchinson diagonals summed, then the update; by the wall clock
+    (pool: a running oracle_pool(), else one is started and stopped outside the
+    timed region)."""
     import numpy as np
     import oracle as O
     from paper_2602_00395_gb300 import synth as S
     O.build()
-    cores = min(N_VIEWS, os.cpu_count() or 1)
-    t0 = time.perf_counter()
-    with cf.ProcessPoolExecutor(max_workers=cores, mp_context=mp.get_context("spawn")) as ex:
-        res = list(ex.map(_oracle_view_full, range(N_VIEWS)))
+    own = pool is None
+    ex, cores = oracle_pool() if own else pool
+    try:
+        t0 = time.perf_counter()
+        res = list(ex.map(_oracle_view, [(n, v) for v in range(N_VIEWS)]))
+    finally:
+        if own:
+            ex.shutdown()
     g = sum(r[1] for r in res)
     hz = sum(r[2] for r in res)
-    P = O.params64(S.make_scene(N_GAUSS, SH_DEG, seed=1000, kind="clusters", extent=10.0))
+    P = O.params64(S.make_scene(n, SH_DEG, seed=1000, kind="clusters", extent=10.0))
     O.tr_update(P, np.zeros_like(P), np.zeros_like(P), g, hz, SH_DEG, t=1, eps=1e-6, cfg=O.tr_config(l=1))
     dt = time.perf_counter() - t0
     return {"oracle_full_step_s": dt, "value": 1.0 / dt, "unit": UNIT, "cores": cores,
             "host_cpus": os.cpu_count(), "per_view_s": [r[0] for r in res],
-            "sample": f"one full step: {N_GAUSS} Gaussians, {N_VIEWS} views at {W}x{H} in {cores} spawned "
-                      f"processes, nu={NU}, update; nothing scaled"}
+            "sample": f"one full step: {n} Gaussians, {N_VIEWS} views at {W}x{H} in {cores} spawned "
+                      f"processes (each generating its scene), nu={NU}, update; nothing scaled"}
 
 
 # The smaller configurations: (name, Gaussians, SH degree, scene kind, extent,
@@ -1091,14 +1052,10 @@ def run_cuda(args):
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         try:
-            import oracle
-            oracle.build()
-            dt, scale, desc, cores = oracle_sample(25, parallel=True)
-            dt1, scale1, desc1, _ = oracle_sample(25, parallel=False)
-            cpu = {"value": 1.0 / (dt * scale), "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc,
-                   "sample_seconds": dt,
-                   "single_thread": {"value": 1.0 / (dt1 * scale1), "cores": 1, "sample": desc1,
-                                     "sample_seconds": dt1}}
+            full = oracle_full_step(n=args.n)
+            cpu = {"value": full["value"], "unit": UNIT, "cores": full["cores"], "kind": "oracle",
+                   "sample": full["sample"], "sample_seconds": full["oracle_full_step_s"],
+                   "host_cpus": full["host_cpus"], "per_view_s": full["per_view_s"]}
         except Exception as ex:  # pragma: no cover
             cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {ex}"}
     if rank == 0:

@@ -366,7 +366,7 @@ __device__ __forceinline__ bool block_sees(const Rec& r, float x0, float y0) {
 // 1: skip the reverse of a lane's first or second pixel when no lane of the
 // warp blends the splat at that pixel.
 #ifndef GS_BWD_SKIP_IDLE_ROW
-#define GS_BWD_SKIP_IDLE_ROW 0
+#define GS_BWD_SKIP_IDLE_ROW 1
 #endif
 // A splat that at most this many lanes of a warp blend is added by those lanes
 // one by one (each its own row of partial derivatives, as float4 atomics)

@@ -51,22 +51,23 @@ def test_kernel_count_per_step():
 
 
 def test_reference_arm_prints_one_json_line():
-    """`bench.py --impl reference`: the oracle on the host cores, one bounded
-    sample per step, in the same JSON contract as the CUDA arm."""
+    """`bench.py --impl reference`: the oracle on the host cores, whole steps
+    (here of a 20k-Gaussian scene), in the same JSON contract as the CUDA arm."""
     import json
     import subprocess
     import sys
     root = os.path.dirname(os.path.abspath(bench.__file__))
     r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--steps", "1",
-                        "--warmup", "0"], capture_output=True, text=True, timeout=600, cwd=root)
+                        "--warmup", "0", "--n", "20000"], capture_output=True, text=True, timeout=600, cwd=root)
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
     assert len(lines) == 1
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
     assert d["value"] > 0 and d["higher_is_better"] is True and d["steps"] == 1 and d["warmup"] == 0
-    # the line reports the sample it timed and the scale that gives the metric
-    assert abs(d["value"] * d["ms_per_step"] * 1e-3 * d["sample_scale"] - 1.0) < 1e-9
+    # the line reports the whole steps it timed, nothing scaled
+    assert abs(d["value"] * d["ms_per_step"] * 1e-3 - 1.0) < 1e-9
+    assert "nothing scaled" in d["cpu_baseline"]["sample"]
     assert d["config"]["workload"] == bench.WORKLOAD
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["cpu_baseline"]["value"] == d["value"]
