@@ -590,27 +590,48 @@ def raster_bwd_flops_per_unit() -> int:
 # cotangent rows grow with the pairs and views).  Valid while the kernel sources
 # are the ones captured (their SHA-256 below); otherwise null.
 RASTER_BWD_TRAFFIC = {
-    "bytes": None,
-    "pairs": None,
+    # one-kernel captures (dram__bytes_read.sum + dram__bytes_write.sum) of the
+    # reverse call's two kernels on the 2-view case of the bench scene
+    "blend_bytes": 388_141_056 + 54_955_264,        # raster_bwd_kernel
+    "projection_bytes": 460_073_728 + 420_978_688,  # project_bwd_kernel
+    "pairs": 12_223_264,                            # pairs blended in that launch
+    "n": 1_000_000,
+    "views": 2,
     "sources": {
-        "paper_2602_00395_gb300/csrc/raster.cu": None,
-        "paper_2602_00395_gb300/csrc/common.cuh": None,
+        "paper_2602_00395_gb300/csrc/raster.cu": "ee041c8e316bffd4e9e6fa0018e1d515e6998c6e879aba86c5e4a981e0ff6ab4",
+        "paper_2602_00395_gb300/csrc/common.cuh": "b7201d9f818a49a1c40435b69f8e6e4e3d70dc9d7b4428d641c067699f5e6429",
     },
 }
 
 
-def raster_bwd_traffic(pairs: float | None = None):
-    """Traffic of one reverse call with `pairs` pairs, scaled from the capture."""
+def projection_reverse_bytes(n: int, views: int, sh_degree: int = SH_DEG, nu: int = NU) -> int:
+    """Algorithmic bytes of the projection reverse: each Gaussian's parameter
+    column read once, its cotangent row of every view read once (9 floats per
+    stream, padded to a float4), its gradient and z . Gz columns written."""
+    rows = 11 + 3 * (sh_degree + 1) ** 2
+    streams = 1 + nu
+    cot = 4 * (-(-9 * streams // 4))
+    return n * (4 * rows + views * 4 * cot + (2 if nu > 0 else 1) * 4 * rows)
+
+
+def raster_bwd_traffic(pairs: float | None = None, n: int | None = None, views: int | None = None):
+    """DRAM bytes of one reverse call, scaled from the captures: the blend's by
+    the pairs it blends, the projection reverse's by its algorithmic bytes (the
+    cotangent rows it reads grow with the views).  None once a source of the
+    captured build has changed."""
     import hashlib
-    if RASTER_BWD_TRAFFIC["bytes"] is None:
+    c = RASTER_BWD_TRAFFIC
+    if c["blend_bytes"] is None:
         return None
-    for rel, digest in RASTER_BWD_TRAFFIC["sources"].items():
+    for rel, digest in c["sources"].items():
         with open(os.path.join(ROOT, rel), "rb") as f:
             if hashlib.sha256(f.read()).hexdigest() != digest:
                 return None
-    if pairs is None or not RASTER_BWD_TRAFFIC["pairs"]:
-        return RASTER_BWD_TRAFFIC["bytes"]
-    return RASTER_BWD_TRAFFIC["bytes"] * pairs / RASTER_BWD_TRAFFIC["pairs"]
+    blend = c["blend_bytes"] * (pairs / c["pairs"] if pairs is not None else 1.0)
+    proj = c["projection_bytes"]
+    if n is not None and views is not None:
+        proj *= projection_reverse_bytes(n, views) / projection_reverse_bytes(c["n"], c["views"])
+    return int(round(blend + proj))
 
 
 def fp32_peak_tflops(n_sm: int, sm_mhz: float) -> float:
@@ -854,7 +875,7 @@ def rooflines(eng, per_call, sum_nc, pairs_timed, local, full_size):
         traffic = None
     else:
         name, ms_k, per_unit = "gs_raster_bwd (reverse blend, 1+nu streams, + projection reverse)", bwd_ms, raster_bwd_flops_per_unit()
-        traffic = raster_bwd_traffic(pairs_timed) if full_size else None
+        traffic = raster_bwd_traffic(pairs_timed, N_GAUSS, N_VIEWS) if full_size else None
     achieved = per_unit * sum_nc / (ms_k * 1e-3) / 1e12
     roof = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
             "frac": achieved / fp32_peak, "traffic": traffic, "launch_ms": ms_k,

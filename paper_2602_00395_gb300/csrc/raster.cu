@@ -363,12 +363,6 @@ __device__ __forceinline__ bool block_sees(const Rec& r, float x0, float y0) {
   return r.a.x + hx >= x0 && r.a.x - hx <= x0 + 7.f && r.a.y + hy >= y0 && r.a.y - hy <= y0 + 7.f;
 }
 
-// 1: under the L1 loss keep the gradient stream's per-pixel cotangents as sign
-// codes (2 bits per channel) instead of three floats per pixel.
-#ifndef GS_BWD_L1_SIGNS
-#define GS_BWD_L1_SIGNS 0
-#endif
-constexpr bool kBwdL1Signs = GS_BWD_L1_SIGNS != 0;
 // 1: skip the reverse of a lane's first or second pixel when no lane of the
 // warp blends the splat at that pixel.
 #ifndef GS_BWD_SKIP_IDLE_ROW
@@ -453,14 +447,7 @@ struct BwdPixel {
   float T, suf[3];
   float pxc, pyc;
   uint32_t nc;
-  uint32_t sg;  // L1 gradient stream kept as signs: 2 bits per channel (0: 0, 1: +, 2: -)
 };
-
-// The L1 gradient stream's cotangent of channel ch: the sign code times g0 = 1/(2m).
-__device__ __forceinline__ float sign_code(uint32_t sg, int ch, float g0) {
-  const uint32_t c = (sg >> (2 * ch)) & 3u;
-  return c == 0u ? 0.f : (c == 1u ? g0 : -g0);
-}
 
 // The reverse of one splat at one pixel: recover T_i = T_{i+1}/(1 - a),
 // dC/da = c T_i - suffix/(1 - a), and store (FIRST) or add, for every stream,
@@ -470,9 +457,9 @@ __device__ __forceinline__ float sign_code(uint32_t sg, int ch, float g0) {
 // dL/dB = -M3, dL/dC = -M4/2, dL/dmx = -(A M0 + B M1), dL/dmy = -(B M0 + C M1).  A pixel the splat is not blended at passes alpha = G = oG = 0: its state
 // stays as it is and it contributes exact zeros, so the pixels of a thread need
 // no branches.  One reciprocal of 1 - a serves the four quotients.
-template <int S, bool FIRST, bool L1G>
+template <int S, bool FIRST>
 __device__ __forceinline__ void bwd_accumulate(BwdPixel<S>& p, const Rec& r, float dx, float dy, float G, float oG,
-                                               float alpha, float g0, float (&v)[32]) {
+                                               float alpha, float (&v)[32]) {
   const float inv = __frcp_rn(1.f - alpha);
   const float Ti = p.T * inv;
   const float rgb0 = r.b.z, rgb1 = r.b.w, rgb2 = r.c.x;
@@ -490,21 +477,12 @@ __device__ __forceinline__ void bwd_accumulate(BwdPixel<S>& p, const Rec& r, flo
   const float dxx = dx * dx, dxy = dx * dy, dyy = dy * dy;
 #pragma unroll
   for (int s = 0; s < S; ++s) {
-    float w0, w1, w2;
-    if (L1G && s == 0) {
-      w0 = sign_code(p.sg, 0, g0);
-      w1 = sign_code(p.sg, 1, g0);
-      w2 = sign_code(p.sg, 2, g0);
-    } else {
-      w0 = p.w[s][0];
-      w1 = p.w[s][1];
-      w2 = p.w[s][2];
-    }
-    const float ga = w0 * da0 + w1 * da1 + w2 * da2;
+    const float ga = p.w[s][0] * da0 + p.w[s][1] * da1 + p.w[s][2] * da2;
     const float gp = ga * ac;  // dL/d(power)
     // the power's partials are linear in the conic, so the warp sums moments of
     // (dx, dy) and the projection's reverse pass applies the conic
-    const float c[9] = {dx * gp, dy * gp, dxx * gp, dxy * gp, dyy * gp, ga * Gc, w0 * aT, w1 * aT, w2 * aT};
+    const float c[9] = {dx * gp, dy * gp, dxx * gp, dxy * gp, dyy * gp, ga * Gc,
+                        p.w[s][0] * aT, p.w[s][1] * aT, p.w[s][2] * aT};
 #pragma unroll
     for (int q = 0; q < 9; ++q) {
       if constexpr (FIRST) v[9 * s + q] = c[q];
@@ -513,9 +491,7 @@ __device__ __forceinline__ void bwd_accumulate(BwdPixel<S>& p, const Rec& r, flo
   }
 }
 
-// L1G: the loss is GS_LOSS_L1 and the gradient stream's cotangents are kept as
-// sign codes (fewer live registers per pixel).
-template <int NU, bool GRAD, bool CB, bool L1G>
+template <int NU, bool GRAD, bool CB>
 __global__ void GS_BWD_BOUNDS raster_bwd_kernel(
     const float4* __restrict__ rec, const uint32_t* __restrict__ vals, const uint32_t* __restrict__ ranges,
     const uint32_t* __restrict__ order, int n_pad, gs_frame fr, int Tx, int T, const float* __restrict__ image,
@@ -525,8 +501,6 @@ __global__ void GS_BWD_BOUNDS raster_bwd_kernel(
     int loss_per_view, int32_t* status) {
   constexpr int S = (GRAD ? 1 : 0) + NU;  // cotangent streams
   constexpr int NVP = cot_stride(S);      // padded row stride of their 9 S values
-  static_assert(!L1G || GRAD, "sign codes hold the gradient stream");
-  const float g0 = 0.5f * inv_m;          // |dL/dC| of the L1 objective
   static_assert(NVP <= 32, "streams");
   extern __shared__ __align__(16) unsigned char smem[];
   const int nthr = blockDim.x, nwarps = nthr >> 5, batch = CB ? fr.batch : kBatchPerThread * nthr;
@@ -565,7 +539,6 @@ __global__ void GS_BWD_BOUNDS raster_bwd_kernel(
     p.suf[0] = p.suf[1] = p.suf[2] = 0.f;
     p.T = 0.f;
     p.nc = 0;
-    p.sg = 0;
 #pragma unroll
     for (int st = 0; st < S; ++st) p.w[st][0] = p.w[st][1] = p.w[st][2] = 0.f;
     if (!(px < fr.width && py < fr.height)) continue;
@@ -604,8 +577,7 @@ __global__ void GS_BWD_BOUNDS raster_bwd_kernel(
         lossp += 0.5f * inv_m * r * r;
         lam = 1.f;
       }
-      if constexpr (L1G) p.sg |= (r > 0.f ? 1u : (r < 0.f ? 2u : 0u)) << (2 * ch);
-      else if constexpr (GRAD) p.w[0][ch] = (loss_kind == GS_LOSS_L1) ? (0.5f * inv_m) * ((r > 0.f) - (r < 0.f)) : inv_m * r;
+      if constexpr (GRAD) p.w[0][ch] = (loss_kind == GS_LOSS_L1) ? (0.5f * inv_m) * ((r > 0.f) - (r < 0.f)) : inv_m * r;
 #pragma unroll
       for (int k = 0; k < NU; ++k)
         p.w[(GRAD ? 1 : 0) + k][ch] = inv_m * lam * image_tan[(((size_t)k * fr.n_views + view) * 3 + ch) * HW + at0];
@@ -689,14 +661,14 @@ __global__ void GS_BWD_BOUNDS raster_bwd_kernel(
         // lane blends the splat at adds exact zeros and keeps its state: skip it
         const bool any0 = __any_sync(0xffffffffu, on[0]), any1 = __any_sync(0xffffffffu, on[1]);
         if (any0) {
-          bwd_accumulate<S, true, L1G>(pix[0], r, dx[0], dy[0], G[0], oG[0], alpha[0], g0, v);
-          if (any1) bwd_accumulate<S, false, L1G>(pix[1], r, dx[1], dy[1], G[1], oG[1], alpha[1], g0, v);
+          bwd_accumulate<S, true>(pix[0], r, dx[0], dy[0], G[0], oG[0], alpha[0], v);
+          if (any1) bwd_accumulate<S, false>(pix[1], r, dx[1], dy[1], G[1], oG[1], alpha[1], v);
         } else {
-          bwd_accumulate<S, true, L1G>(pix[1], r, dx[1], dy[1], G[1], oG[1], alpha[1], g0, v);
+          bwd_accumulate<S, true>(pix[1], r, dx[1], dy[1], G[1], oG[1], alpha[1], v);
         }
 #else
-        bwd_accumulate<S, true, L1G>(pix[0], r, dx[0], dy[0], G[0], oG[0], alpha[0], g0, v);
-        bwd_accumulate<S, false, L1G>(pix[1], r, dx[1], dy[1], G[1], oG[1], alpha[1], g0, v);
+        bwd_accumulate<S, true>(pix[0], r, dx[0], dy[0], G[0], oG[0], alpha[0], v);
+        bwd_accumulate<S, false>(pix[1], r, dx[1], dy[1], G[1], oG[1], alpha[1], v);
 #endif
 #pragma unroll
         for (int q = 9 * S; q < 32; ++q) v[q] = 0.f;
@@ -1292,15 +1264,11 @@ void launch_bwd_kernels(const gs_params* x, const BatchArg* ba, int n_pad, int d
   const int nthr = fr.tile_w * fr.tile_h / kPixPerThread, batch = bwd_batch(fr, nthr);
   const size_t smem = bwd_smem_bytes(batch);
   const bool cb = fr.batch != 0;
-  const bool l1g = GRAD && kBwdL1Signs && loss.kind == GS_LOSS_L1;
-  constexpr bool G1 = GRAD;  // sign codes only with the gradient stream
-  auto* kern = cb ? (l1g ? raster_bwd_kernel<NU, GRAD, true, G1> : raster_bwd_kernel<NU, GRAD, true, false>)
-                  : (l1g ? raster_bwd_kernel<NU, GRAD, false, G1> : raster_bwd_kernel<NU, GRAD, false, false>);
-  static size_t attr[4] = {0, 0, 0, 0};
-  const int ak = (cb ? 2 : 0) + (l1g ? 1 : 0);
-  if (smem > 48 * 1024 && smem > attr[ak]) {
+  auto* kern = cb ? raster_bwd_kernel<NU, GRAD, true> : raster_bwd_kernel<NU, GRAD, false>;
+  static size_t attr[2] = {0, 0};
+  if (smem > 48 * 1024 && smem > attr[cb]) {
     if (allow_smem(kern, smem) != cudaSuccess) return;  // the caller reports the error
-    attr[ak] = smem;
+    attr[cb] = smem;
   }
   const double views_per_objective = ba ? 1.0 : (double)fr.n_views;
   const float inv_m = (float)(1.0 / (3.0 * (double)fr.width * fr.height * views_per_objective));
