@@ -139,7 +139,8 @@ typedef struct gs_projected {
 } gs_projected;
 
 /* Sorted (tile, splat) pairs (device, caller-owned).
- *   keys:     capacity x uint64, key = (view * tiles + tile) << 32 | bits(depth)
+ *   keys:     capacity x uint32 (16-byte aligned), key = view * tiles + tile; the
+ *             pairs of one key are in (depth, splat index) order
  *   vals:     capacity x uint32, splat index
  *   ranges:   V * tiles x 2 uint32, [start, end) of each tile's pairs
  *   n_pairs:  one uint32, number of pairs the views need (may exceed capacity)
@@ -149,7 +150,7 @@ typedef struct gs_projected {
  *             within a group); the blends then start the heaviest tiles first.
  *             It changes when a tile runs, never its result. */
 typedef struct gs_sorted {
-  uint64_t* keys;
+  uint32_t* keys;
   uint32_t* vals;
   uint32_t* ranges;
   uint32_t* n_pairs;
@@ -204,7 +205,7 @@ gs_status gs_project(const gs_params* x, const gs_camera* cams, gs_frame frame, 
                      gs_projected* out, int32_t* status, void* stream);
 
 /* Sec. 3.1 tile binning and depth order: all (tile, splat) pairs of all views
- * sorted by (key, splat index), and each tile's [start, end).  A splat's tiles
+ * sorted by (view, tile, depth, splat index), and each tile's [start, end).  A splat's tiles
  * are its 3DGS square, decided in FP32 with one rounding per operation:
  *   x0 = clamp(floor((mx - r)/tw), 0, Tx), x1 = clamp(floor((mx + (r + tw - 1))/tw), 0, Tx)
  * (the same for y); with frame.footprint_bins = 1 also

@@ -2,16 +2,17 @@
 // (Sec. 3.1 of arXiv 2602.00395).
 //
 // Every pair of one splat shares its depth, so the order (tile, depth, splat)
-// is built in two stages instead of sorting 64-bit pair keys on all their bits:
+// is built in two stages instead of sorting 64-bit (tile, depth) pair keys:
 //
 //   records  per (view, splat): its tiles (the FP32 rectangle, narrowed row
 //            by row to the footprint ellipse, see row_span_v); the V x n_pad
 //            records are sorted by (view, depth bits) with a stable LSD radix
 //            sort (record index order breaks ties)
 //   scan     emission offsets in that order and the pair count P
-//   emit     key = (view * tiles + tile) << 32 | bits(depth), value = splat,
-//            written in (view, depth, splat) order
-//   sort     stable LSD radix sort of the pairs on the tile bits only
+//   emit     key = view * tiles + tile (32 bits), value = splat, written in
+//            (view, depth, splat) order
+//   sort     stable LSD radix sort of the pairs on those keys: the depth order
+//            within a tile is the emission order, so no depth bits are moved
 //   ranges   [start, end) of every tile
 //
 // Each radix pass is a per-block digit histogram, a device-wide scan of the
@@ -286,7 +287,7 @@ void exclusive_scan(const uint32_t* in, uint32_t* out, size_t n_max, const uint3
 // over that record's row table (see record_keys_kernel).
 __global__ void emit_kernel(const uint4* __restrict__ hdr, const uint2* __restrict__ rows, int n_pad, gs_frame fr,
                             int Tx, int Ty, const uint32_t* __restrict__ order, const uint32_t* __restrict__ offsets,
-                            uint64_t capacity, uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+                            uint64_t capacity, uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
   const size_t G = (size_t)fr.n_views * n_pad;
   const size_t p0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x;  // sorted record position
   const size_t w0 = p0 - (threadIdx.x & 31);
@@ -331,7 +332,7 @@ __global__ void emit_kernel(const uint4* __restrict__ hdr, const uint2* __restri
     if (p < total && at < capacity) {
       const size_t og = og32;
       const int oview = (int)(og / n_pad);
-      uint64_t tile = (uint64_t)oview * tiles;
+      uint32_t tile = (uint32_t)((uint64_t)oview * tiles);
       if (R > 0) {
         const uint32_t q = p - o_start;
         // last row whose pairs above are <= q (empty rows repeat the count before them)
@@ -344,13 +345,13 @@ __global__ void emit_kernel(const uint4* __restrict__ hdr, const uint2* __restri
         // q - e.x < the row's pairs, so txx stays in the row; the clamp only
         // keeps every tile index inside the view if that ever failed
         const uint32_t txx = min(e.y + (q - e.x), (uint32_t)(Tx - 1));
-        tile += (uint64_t)((oyr & 0xffffu) + a) * Tx + txx;
+        tile += ((oyr & 0xffffu) + a) * (uint32_t)Tx + txx;
       }
       // (R == 0 with pairs: the record's row table did not fit, which happens
       // only when the pairs exceed the capacity and GS_FLAG_CAPACITY is raised;
       // its slots still get a valid tile and splat so that every slot below the
       // capacity holds an in-range pair)
-      keys[at] = (tile << 32) | (uint64_t)od;
+      keys[at] = tile;
       vals[at] = (uint32_t)(og - (size_t)oview * n_pad);
     }
   }
@@ -526,26 +527,24 @@ __device__ __forceinline__ uint32_t pairs_in_use(const uint32_t* n_pairs, uint64
   return (uint32_t)(p < capacity ? p : capacity);
 }
 
-// A thread looks at four consecutive keys (two 16-byte loads) and the key after
+// A thread looks at four consecutive keys (one 16-byte load) and the key after
 // them; a tile starts where its key differs from the previous one and ends
 // where it differs from the next.
-__global__ void ranges_kernel(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ n_pairs,
+__global__ void ranges_kernel(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ n_pairs,
                               uint64_t capacity, uint64_t n_tiles, uint32_t* __restrict__ ranges) {
   const uint32_t P = pairs_in_use(n_pairs, capacity);
   const size_t step = (size_t)gridDim.x * blockDim.x * 4;
   for (size_t p0 = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) * 4; p0 < P; p0 += step) {
     uint32_t tl[5];
     if (p0 + 4 <= P) {
-      const ulonglong2 a = __ldg(reinterpret_cast<const ulonglong2*>(keys + p0));
-      const ulonglong2 b = __ldg(reinterpret_cast<const ulonglong2*>(keys + p0) + 1);
-      tl[0] = (uint32_t)(a.x >> 32); tl[1] = (uint32_t)(a.y >> 32);
-      tl[2] = (uint32_t)(b.x >> 32); tl[3] = (uint32_t)(b.y >> 32);
+      const uint4 a = __ldg(reinterpret_cast<const uint4*>(keys + p0));
+      tl[0] = a.x; tl[1] = a.y; tl[2] = a.z; tl[3] = a.w;
     } else {
 #pragma unroll
-      for (int k = 0; k < 4; ++k) tl[k] = p0 + k < P ? (uint32_t)(keys[p0 + k] >> 32) : 0xffffffffu;
+      for (int k = 0; k < 4; ++k) tl[k] = p0 + k < P ? keys[p0 + k] : 0xffffffffu;
     }
-    tl[4] = p0 + 4 < P ? (uint32_t)(keys[p0 + 4] >> 32) : 0xffffffffu;
-    uint32_t prev = p0 > 0 ? (uint32_t)(keys[p0 - 1] >> 32) : 0xffffffffu;
+    tl[4] = p0 + 4 < P ? keys[p0 + 4] : 0xffffffffu;
+    uint32_t prev = p0 > 0 ? keys[p0 - 1] : 0xffffffffu;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const size_t p = p0 + k;
@@ -649,7 +648,7 @@ SortPlan plan_sort(int32_t n_pad, gs_frame fr, uint64_t capacity) {
   p.off_rk1 = o;    o += align256(p.n_items * 4);
   p.off_rv0 = o;    o += align256(p.n_items * 4);
   p.off_rv1 = o;    o += align256(p.n_items * 4);
-  p.off_keys = o;   o += align256(capacity * 8);
+  p.off_keys = o;   o += align256(capacity * 4);
   p.off_vals = o;   o += align256(capacity * 4);
   p.off_hist = o;   o += align256(hist_n * 4);
   p.rows_cap = std::min<uint64_t>(capacity + 2 * (uint64_t)p.n_items, 0xffffffffull);
@@ -699,6 +698,7 @@ extern "C" gs_status gs_bin_sort(const gs_projected* proj, int32_t n_pad, gs_fra
   GS_REQUIRE(out->capacity > 0 && out->capacity < (1ull << 32), "gs_bin_sort: capacity must be in [1, 2^32)");
   const SortPlan p = plan_sort(n_pad, frame, out->capacity);
   GS_REQUIRE(p.Tx < 65536 && p.Ty < 65536, "gs_bin_sort: at most 65535 tiles per row and column");
+  GS_REQUIRE((uint64_t)frame.n_views * p.Tx * p.Ty < 0xffffffffull, "gs_bin_sort: views x tiles must be below 2^32 - 1");
   GS_REQUIRE(workspace && workspace_bytes >= p.total, "gs_bin_sort: workspace needs %zu bytes, got %zu", p.total,
              workspace_bytes);
   cudaStream_t st = (cudaStream_t)stream;
@@ -733,15 +733,15 @@ extern "C" gs_status gs_bin_sort(const gs_projected* proj, int32_t n_pad, gs_fra
   // emission offsets in that order, and the pair count
   gather_counts_kernel<<<eb, 256, 0, st>>>(rv[rcur], counts, scnt, p.n_items);
   exclusive_scan(scnt, scnt, p.n_items, nullptr, 0, sums, out->n_pairs, out->capacity, status, st);
-  // pairs in (view, depth, splat) order, then stable passes on the tile bits;
+  // pairs in (view, depth, splat) order, then stable passes on their tile keys;
   // the last pass must land in the caller's arrays
-  uint64_t* kbuf[2] = {out->keys, (uint64_t*)(ws + p.off_keys)};
+  uint32_t* kbuf[2] = {out->keys, (uint32_t*)(ws + p.off_keys)};
   uint32_t* vbuf[2] = {out->vals, (uint32_t*)(ws + p.off_vals)};
   int cur = (p.pair_pass % 2 == 0) ? 0 : 1;
   emit_kernel<<<eb, 256, 0, st>>>(hdr, rows, n_pad, frame, p.Tx, p.Ty, rv[rcur], scnt, out->capacity, kbuf[cur],
                                   vbuf[cur]);
   const Seg pseg{out->n_pairs, out->capacity, 0, 0};
-  radix_passes<uint64_t>(kbuf, vbuf, cur, p.pair_pass, 32, pseg, 1, p.nb_pairs, hist, sums, st);
+  radix_passes<uint32_t>(kbuf, vbuf, cur, p.pair_pass, 0, pseg, 1, p.nb_pairs, hist, sums, st);
   const int rb = (int)std::min<uint64_t>((out->capacity + 255) / 256, 152 * 16);
   ranges_kernel<<<rb, 256, 0, st>>>(out->keys, out->n_pairs, out->capacity, (uint64_t)frame.n_views * T,
                                     out->ranges);

@@ -41,6 +41,42 @@ __device__ __forceinline__ float splat_power(const Rec& r, float dx, float dy) {
   return __fmaf_rn(-0.5f, q, -__fmul_rn(r.a.w, __fmul_rn(dx, dy)));
 }
 
+// 1: the blends also test a splat's footprint ellipse itself, not only its
+// bounding box, against each 8 x 8 pixel block (0: the box alone).
+#ifndef GS_EXACT_BLOCK_TEST
+#define GS_EXACT_BLOCK_TEST 1
+#endif
+
+// False only if no pixel centre of the 8 x 8 block with first centre (x0, y0)
+// can reach alpha >= 1/255: the minimum over the rectangle [x0, x0 + 7] x
+// [y0, y0 + 7] of q(u) = A ux^2 + 2 B ux uy + C uy^2, u = p - mean (-2 x the
+// power), is above 2 ln(255 o) by more than a slack that covers the FP32
+// rounding of both this test and the blends' own evaluation (1e-4 of the
+// terms' largest magnitude on the rectangle, 1e-3 relative and absolute, each
+// hundreds of times their error bounds).  With the origin outside the rectangle
+// the convex q takes its minimum on an edge, where it is a parabola in one
+// coordinate.  A conic that is not positive definite is never rejected.
+__device__ __forceinline__ bool footprint_meets_block(const Rec& r, float x0, float y0) {
+  const float A = r.a.z, B = r.a.w, C = r.b.x;
+  if (!(A > 0.f && C > 0.f && A * C > B * B)) return true;
+  const float thr = 2.f * __logf(255.f * r.b.y);
+  const float xl = x0 - r.a.x, xh = xl + 7.f, yl = y0 - r.a.y, yh = yl + 7.f;
+  const float X = fmaxf(fabsf(xl), fabsf(xh)), Y = fmaxf(fabsf(yl), fabsf(yh));
+  const float slack = 1e-4f * (A * X * X + 2.f * fabsf(B) * X * Y + C * Y * Y) + 1e-3f * fabsf(thr) + 1e-3f;
+  if (xl <= 0.f && xh >= 0.f && yl <= 0.f && yh >= 0.f) return thr + slack >= 0.f;
+  const float bc = B / C, ba = B / A;
+  auto on_x_edge = [&](float ux) {  // q on ux = const, minimised over uy in [yl, yh]
+    const float uy = fminf(fmaxf(-bc * ux, yl), yh);
+    return A * ux * ux + 2.f * B * ux * uy + C * uy * uy;
+  };
+  auto on_y_edge = [&](float uy) {
+    const float ux = fminf(fmaxf(-ba * uy, xl), xh);
+    return A * ux * ux + 2.f * B * ux * uy + C * uy * uy;
+  };
+  const float qmin = fminf(fminf(on_x_edge(xl), on_x_edge(xh)), fminf(on_y_edge(yl), on_y_edge(yh)));
+  return qmin <= thr + slack;
+}
+
 // Stage batch b of a tile list (records [b * batch, b * batch + batch)) into
 // buffer (b & 1): one bulk copy per record (and per tangent record), issued by
 // the block's threads in turn, all completing on the buffer's mbarrier.
@@ -108,8 +144,10 @@ __device__ __forceinline__ void pixel_of(int tid, int tile_w, int& lx, int& ly) 
 // Bit w is set if the splat can reach alpha >= 1/255 at some pixel centre of
 // warp block w.  The record's last word holds the half-extents of the bounding
 // box of that footprint, widened and rounded up by the projection
-// (footprint_extents), so a cleared bit skips only pairs that every pixel of
-// the block skips anyway: results are unchanged.
+// (footprint_extents); a block inside the box is then tested against the
+// ellipse (footprint_meets_block).  Both tests are conservative, so a cleared
+// bit skips only pairs that every pixel of the block skips anyway: results are
+// unchanged.
 __device__ __forceinline__ uint32_t warp_block_mask(const Rec& r, float tile_x0, float tile_y0, int tile_w,
                                                     int nwarps) {
   const uint32_t e = __float_as_uint(r.c.w);
@@ -120,7 +158,9 @@ __device__ __forceinline__ uint32_t warp_block_mask(const Rec& r, float tile_x0,
   for (int w = 0; w < nwarps; ++w) {
     const float x0 = tile_x0 + (float)((w % bxn) * 8) + 0.5f, x1 = x0 + 7.f;
     const float y0 = tile_y0 + (float)((w / bxn) * 8) + 0.5f, y1 = y0 + 7.f;
-    if (r.a.x + hx >= x0 && r.a.x - hx <= x1 && r.a.y + hy >= y0 && r.a.y - hy <= y1) m |= 1u << w;
+    if (r.a.x + hx >= x0 && r.a.x - hx <= x1 && r.a.y + hy >= y0 && r.a.y - hy <= y1 &&
+        (!GS_EXACT_BLOCK_TEST || footprint_meets_block(r, x0, y0)))
+      m |= 1u << w;
   }
   return m;
 }
@@ -360,7 +400,8 @@ __device__ __forceinline__ bool block_sees(const Rec& r, float x0, float y0) {
   const uint32_t e = __float_as_uint(r.c.w);
   const float hx = __half2float(__ushort_as_half((unsigned short)(e & 0xffffu)));
   const float hy = __half2float(__ushort_as_half((unsigned short)(e >> 16)));
-  return r.a.x + hx >= x0 && r.a.x - hx <= x0 + 7.f && r.a.y + hy >= y0 && r.a.y - hy <= y0 + 7.f;
+  return r.a.x + hx >= x0 && r.a.x - hx <= x0 + 7.f && r.a.y + hy >= y0 && r.a.y - hy <= y0 + 7.f &&
+         (!GS_EXACT_BLOCK_TEST || footprint_meets_block(r, x0, y0));
 }
 
 // 1: skip the reverse of a lane's first or second pixel when no lane of the

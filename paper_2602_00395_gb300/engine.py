@@ -119,7 +119,7 @@ class TRStep:
     # ------------------------------------------------------------ buffers
     def _alloc_pairs(self, capacity: int) -> None:
         self.capacity = int(capacity)
-        self.keys = torch.empty(self.capacity, dtype=torch.int64, device=self.device)
+        self.keys = torch.empty(self.capacity, dtype=torch.int32, device=self.device)
         self.vals = torch.empty(self.capacity, dtype=torch.int32, device=self.device)
         self.sort_ws = torch.empty(G.gs_bin_sort_workspace_size(self.n_pad, self.frame, self.capacity),
                                    dtype=torch.uint8, device=self.device)
@@ -429,7 +429,7 @@ class BatchStep:
         self.order = torch.empty(B * Tx * Ty, **i32)
         self.n_pairs = torch.empty(1, **i32)
         self.capacity = int(capacity)
-        self.keys = torch.empty(self.capacity, dtype=torch.int64, device=self.device)
+        self.keys = torch.empty(self.capacity, dtype=torch.int32, device=self.device)
         self.vals = torch.empty(self.capacity, **i32)
         self.sort_ws = torch.empty(G.gs_bin_sort_workspace_size(self.n_pad, self.frame, self.capacity),
                                    dtype=torch.uint8, device=self.device)
@@ -450,7 +450,7 @@ class BatchStep:
         nu = nu if train else 0
         frame = G.frame_struct(B, width, height, *tile)
         Tx, Ty = -(-width // tile[0]), -(-height // tile[1])
-        b = B * n_pad * 48 * (1 + nu) + B * HW * 4 * (3 + 1 + 1 + 3 * nu) + B * Tx * Ty * 12 + capacity * 12
+        b = B * n_pad * 48 * (1 + nu) + B * HW * 4 * (3 + 1 + 1 + 3 * nu) + B * Tx * Ty * 12 + capacity * 8
         b += G.gs_bin_sort_workspace_size(n_pad, frame, capacity) + 96 * B
         if train:
             b += B * HW * 12 + G.gs_raster_bwd_workspace_size(n_pad, frame, nu)
