@@ -849,11 +849,11 @@ def rooflines(eng, per_call, sum_nc, pairs_timed, local, full_size):
     pair_pass = max(1, (bits(N_VIEWS * eng.Tx * eng.Ty) + 7) // 8)
     work = {
         "project": ("hbm", eng.n * rows * 4 + N_VIEWS * eng.n * 48 * (1 + NU)),
-        # per pair: emit 12 B, 24 B per pass, ranges 8 B; per record: 48 B read and
-        # 28 B written by the count pass (count, key, value, row-table header; the
-        # row entries are not counted), 16 B per pass, 12 B count gather, 16 B
-        # header read by the emit
-        "bin_sort": ("hbm", pairs_timed * (12 + 24 * pair_pass + 8) + R * (48 + 28 + 16 * rec_pass + 12 + 16)),
+        # per pair (32-bit tile key, 32-bit splat index): emit 8 B, 16 B per pass,
+        # ranges 4 B; per record: 48 B read and 28 B written by the count pass
+        # (count, key, value, row-table header; the row entries are not counted),
+        # 16 B per pass, 12 B count gather, 16 B header read by the emit
+        "bin_sort": ("hbm", pairs_timed * (8 + 16 * pair_pass + 4) + R * (48 + 28 + 16 * rec_pass + 12 + 16)),
         "raster_fwd": ("alu", raster_fwd_flops_per_unit() * sum_nc),
         "raster_bwd": ("alu", raster_bwd_flops_per_unit() * sum_nc),
         "update": ("hbm", eng.n * rows * 4 * (5 + 3)),
