@@ -435,12 +435,6 @@ __global__ void __launch_bounds__(kRadixThreads) radix_hist_kernel(const K* __re
   hist[((size_t)g * 256 + threadIdx.x) * bps + t] = s_cnt[threadIdx.x];
 }
 
-// 1: a scatter finds the lanes that share an item's digit from eight ballots
-// (one per digit bit); 0: from one match instruction.
-#ifndef GS_RADIX_BALLOT_RANK
-#define GS_RADIX_BALLOT_RANK 0
-#endif
-
 // Stable scatter of one tile.  Warp w owns the tile's items
 // [w * 32 * kRadixItems, (w + 1) * 32 * kRadixItems), item k of lane L at
 // offset k * 32 + L, so the warps' strips and the items within a strip are in
@@ -485,18 +479,7 @@ __global__ void __launch_bounds__(kRadixThreads, 4) radix_scatter_kernel(const K
     const bool ok = base + (uint32_t)k * 32 < len;
     const uint32_t d = ok ? digit_of(key[k], shift) : 256u;
     dg[k] = d;
-#if GS_RADIX_BALLOT_RANK
-    // the lanes with the same digit, from one vote per digit bit
-    uint32_t peers = __ballot_sync(0xffffffffu, ok);
-#pragma unroll
-    for (int bit = 0; bit < 8; ++bit) {
-      const bool set = (d >> bit) & 1u;
-      const uint32_t vote = __ballot_sync(0xffffffffu, set);
-      peers &= set ? vote : ~vote;
-    }
-#else
     const uint32_t peers = __match_any_sync(0xffffffffu, d);
-#endif
     const uint32_t before = ok ? s_wc[warp][d] : 0u;
     rank[k] = before + (uint32_t)__popc(peers & lt);
     __syncwarp();
