@@ -177,44 +177,56 @@ struct FwdPixel {
   bool done;
 };
 
-// One splat against one pixel (front to back).  `t0` points at the splat's
-// first rewritten tangent record; the records of further probes follow at
-// stride `tstride`.
+// The splat at one pixel: offsets, Gaussian, alpha, and whether it is blended
+// there (a done pixel blends nothing).
 template <int NU>
-__device__ __forceinline__ void fwd_blend(FwdPixel<NU>& p, const Rec& r, const Rec* t0, int tstride, uint32_t pos) {
-  if (p.done) return;
-  const float dx = __fsub_rn(r.a.x, p.pxc), dy = __fsub_rn(r.a.y, p.pyc);
+__device__ __forceinline__ bool fwd_eval(const FwdPixel<NU>& p, const Rec& r, float& dx, float& dy, float& G,
+                                         float& oG, float& alpha) {
+  dx = __fsub_rn(r.a.x, p.pxc);
+  dy = __fsub_rn(r.a.y, p.pyc);
   const float power = splat_power(r, dx, dy);
-  if (power > 0.f) return;
-  const float G = __expf(power);
-  const float oG = __fmul_rn(r.b.y, G);
-  const float alpha = fminf(kAlphaMax, oG);
-  if (alpha < kAlphaMin) return;
+  G = __expf(power);
+  oG = __fmul_rn(r.b.y, G);
+  alpha = fminf(kAlphaMax, oG);
+  return !p.done && power <= 0.f && alpha >= kAlphaMin;
+}
+
+// The splat's front-to-back update of one pixel, with the decisions as
+// selects: a pixel that does not blend the splat (on false, or the splat would
+// take T below kTMin, which ends the pixel instead) adds exact zeros and keeps
+// T, its tangents and its last position.  `t0` points at the splat's first
+// rewritten tangent record; the records of further probes follow at stride
+// `tstride`.  With the power's tangent pd, a blended pixel gets
+// C += c a T, C' += c' a T + c (a' T + a T'), T' <- T' (1 - a) - T a', T <- T (1 - a),
+// a' = o' G + a pd (0 for a capped alpha).
+template <int NU>
+__device__ __forceinline__ void fwd_apply(FwdPixel<NU>& p, const Rec& r, const Rec* t0, int tstride, uint32_t pos,
+                                          bool on, float dx, float dy, float G, float oG, float alpha) {
   const float Tn = p.T * (1.f - alpha);
-  if (Tn < kTMin) {
-    p.done = true;
-    return;
-  }
-  const float w = alpha * p.T;
+  const bool term = on && Tn < kTMin;
+  const bool bl = on && !term;
+  p.done = p.done || term;
+  const float a = bl ? alpha : 0.f;
+  const float w = a * p.T;
   if constexpr (NU > 0) {
-    const bool capped = oG > kAlphaMax;
+    const bool live = bl && !(oG > kAlphaMax);  // a capped alpha has no tangent
 #pragma unroll
     for (int k = 0; k < NU; ++k) {
       const Rec t = t0[k * tstride];
       const float pd = dx * (t.a.x * dx + t.a.y * dy + t.a.w) + dy * (t.a.z * dy + t.b.x);
-      const float ad = capped ? 0.f : (t.b.y * G + alpha * pd);
-      const float sk = ad * p.T + alpha * p.Td[k];
+      const float ad = live ? (t.b.y * G + alpha * pd) : 0.f;
+      const float sk = ad * p.T + a * p.Td[k];
       p.Cd[k][0] += t.b.z * w + r.b.z * sk;
       p.Cd[k][1] += t.b.w * w + r.b.w * sk;
       p.Cd[k][2] += t.c.x * w + r.c.x * sk;
-      p.Td[k] = p.Td[k] * (1.f - alpha) - p.T * ad;
+      p.Td[k] = p.Td[k] * (1.f - a) - p.T * ad;
     }
   }
   p.C[0] += r.b.z * w;
   p.C[1] += r.b.w * w;
   p.C[2] += r.c.x * w;
-  p.T = Tn;
-  p.last = pos + 1;
+  p.T = bl ? Tn : p.T;
+  p.last = bl ? pos + 1 : p.last;
 }
 
 // CB: the frame sets its own batch (else one record per thread, known to the
@@ -313,8 +325,15 @@ __global__ void GS_FWD_BOUNDS raster_fwd_kernel(const float4* __restrict__ rec, 
         const Rec r = bb[j];
         const Rec* t0 = tbuf + (size_t)bi * NU * batch + j;
         const uint32_t pos = (uint32_t)(b * batch + j);
+        float dx[kPixPerThread], dy[kPixPerThread], G[kPixPerThread], oG[kPixPerThread], al[kPixPerThread];
+        bool on[kPixPerThread];
 #pragma unroll
-        for (int q = 0; q < kPixPerThread; ++q) fwd_blend<NU>(pix[q], r, t0, batch, pos);
+        for (int q = 0; q < kPixPerThread; ++q) on[q] = fwd_eval<NU>(pix[q], r, dx[q], dy[q], G[q], oG[q], al[q]);
+        // a pixel row (the lanes' first or second pixels) that no lane blends
+        // the splat at is skipped as a whole
+#pragma unroll
+        for (int q = 0; q < kPixPerThread; ++q)
+          if (__any_sync(0xffffffffu, on[q])) fwd_apply<NU>(pix[q], r, t0, batch, pos, on[q], dx[q], dy[q], G[q], oG[q], al[q]);
       }
     }
     if (__syncthreads_count(pix[0].done && pix[1].done) == nthr) break;
