@@ -592,13 +592,13 @@ def raster_bwd_flops_per_unit() -> int:
 RASTER_BWD_TRAFFIC = {
     # one-kernel captures (dram__bytes_read.sum + dram__bytes_write.sum) of the
     # reverse call's two kernels on the 2-view case of the bench scene
-    "blend_bytes": 386_962_944 + 55_052_288,        # raster_bwd_kernel
-    "projection_bytes": 460_313_344 + 420_973_824,  # project_bwd_kernel
+    "blend_bytes": 387_207_936 + 54_813_696,        # raster_bwd_kernel
+    "projection_bytes": 460_112_640 + 420_741_120,  # project_bwd_kernel
     "pairs": 12_223_264,                            # pairs blended in that launch
     "n": 1_000_000,
     "views": 2,
     "sources": {
-        "paper_2602_00395_gb300/csrc/raster.cu": "7417fba206e2cb0255953dbd2c585b0fb68d56769e2111e150f14bf92e8a365a",
+        "paper_2602_00395_gb300/csrc/raster.cu": "d296c19b9856454a949af5f5646e50be31146d100d97686e36662c71fd4a7733",
         "paper_2602_00395_gb300/csrc/common.cuh": "b7201d9f818a49a1c40435b69f8e6e4e3d70dc9d7b4428d641c067699f5e6429",
     },
 }
