@@ -330,10 +330,22 @@ __global__ void GS_FWD_BOUNDS raster_fwd_kernel(const float4* __restrict__ rec, 
 #pragma unroll
         for (int q = 0; q < kPixPerThread; ++q) on[q] = fwd_eval<NU>(pix[q], r, dx[q], dy[q], G[q], oG[q], al[q]);
         // a pixel row (the lanes' first or second pixels) that no lane blends
-        // the splat at is skipped as a whole
+        // the splat at is skipped as a whole; the splat's probe tangent records
+        // are read once for both rows
+        bool rows[kPixPerThread];
+        bool anyrow = false;
+#pragma unroll
+        for (int q = 0; q < kPixPerThread; ++q) {
+          rows[q] = __any_sync(0xffffffffu, on[q]);
+          anyrow = anyrow || rows[q];
+        }
+        if (!anyrow) continue;
+        Rec tk[NU > 0 ? NU : 1];
+#pragma unroll
+        for (int k = 0; k < NU; ++k) tk[k] = t0[k * batch];
 #pragma unroll
         for (int q = 0; q < kPixPerThread; ++q)
-          if (__any_sync(0xffffffffu, on[q])) fwd_apply<NU>(pix[q], r, t0, batch, pos, on[q], dx[q], dy[q], G[q], oG[q], al[q]);
+          if (rows[q]) fwd_apply<NU>(pix[q], r, tk, 1, pos, on[q], dx[q], dy[q], G[q], oG[q], al[q]);
       }
     }
     if (__syncthreads_count(pix[0].done && pix[1].done) == nthr) break;
