@@ -258,8 +258,14 @@ gs_status gs_raster_fwd(const gs_projected* proj, const gs_sorted* sorted, int32
  * frame's views, written to grad (overwritten).  If image_tangent and probe are
  * given (S2 = S1), the same reverse pass also writes the Hutchinson diagonal
  * hz = (1/nu) sum_k z_k . ((1/m) J^T diag(w) J z_k) (overwritten).  loss_out
- * (one float, may be NULL) gets the objective added.  workspace from
- * gs_raster_bwd_workspace_size. */
+ * (one float, may be NULL) gets the objective added.
+ * workspace: device, 16-byte aligned, at least gs_raster_bwd_workspace_size
+ *   bytes (a 256-byte header, then the 2-D cotangent rows the reverse blend adds
+ *   into).  Any content is accepted on entry.  The call leaves the rows zero
+ *   and records that in the header, so a following call on the same workspace
+ *   (the same or a smaller frame) skips clearing them; otherwise the call
+ *   clears them first.  The same holds for gs_hvp_diag and gs_raster_bwd_batch,
+ *   which share this workspace layout. */
 size_t gs_raster_bwd_workspace_size(int32_t n_pad, gs_frame frame, int32_t nu);
 gs_status gs_raster_bwd(const gs_params* x, const gs_camera* cams, gs_frame frame, const gs_projected* proj,
                         const gs_sorted* sorted, const float* image, const float* target, const float* final_T,

@@ -510,6 +510,44 @@ __device__ __forceinline__ void warp_reduce_quads16(float (&v)[32], float (&q)[4
 // whole float4s so that rows can be added and read as vectors.
 __host__ __device__ constexpr int cot_stride(int streams) { return (9 * streams + 3) & ~3; }
 
+// The reverse pass's workspace: a header, then the cotangent rows the reverse
+// blend adds into.  They must be zero when the blend starts.  The projection
+// reverse, which reads every row, leaves each row it read zero, and its last
+// block records in the header that the first clear_floats floats are zero;
+// the next call then clears nothing.  Any other header (a new or reused
+// buffer, a call that stopped between the blend and the projection reverse)
+// makes the next call clear the rows first; the blend marks the rows dirty
+// when it starts.
+struct CotHeader {
+  uint64_t magic;         // kCotClear while clear_floats is valid
+  uint64_t clear_floats;  // leading floats of the rows known to be zero
+  uint32_t done_blocks;   // projection-reverse blocks finished in this call
+};
+constexpr uint64_t kCotClear = 0x9d2c5680a3b1f4e7ull;
+constexpr size_t kCotHeaderBytes = 256;
+
+// Zero the first 4 n4 floats of the rows unless the header says they are zero;
+// reset the projection reverse's block count.
+__global__ void cot_prepare_kernel(CotHeader* __restrict__ h, float4* __restrict__ cot, size_t n4) {
+  const bool clear = h->magic == kCotClear && h->clear_floats >= 4 * n4;
+  if (blockIdx.x == 0 && threadIdx.x == 0) h->done_blocks = 0;
+  if (clear) return;
+  for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n4; k += (size_t)gridDim.x * blockDim.x)
+    cot[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+// End of a projection-reverse block: after every thread's zeroing stores, the
+// last block to finish records that the first `floats` floats are zero.
+__device__ __forceinline__ void cot_mark_clear(CotHeader* h, uint64_t floats) {
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0 && atomicAdd(&h->done_blocks, 1u) == gridDim.x - 1) {
+    __threadfence();
+    h->clear_floats = floats;
+    h->magic = kCotClear;
+  }
+}
+
 // Reverse-pass state of one pixel: the cotangent dL/dC of each stream, the
 // transmittance being recovered back to front, the colour suffix
 // sum_{j>i} c_j a_j T_j, and the list position after its last blended splat.
@@ -570,7 +608,7 @@ __global__ void GS_BWD_BOUNDS raster_bwd_kernel(
     const float* __restrict__ target,
     const float* __restrict__ final_T, const uint32_t* __restrict__ n_contrib, const float* __restrict__ image_tan,
     int loss_kind, float gn_floor, float inv_m, float* __restrict__ cot, float* __restrict__ loss_out,
-    int loss_per_view, int32_t* status) {
+    int loss_per_view, CotHeader* cot_hdr, int32_t* status) {
   constexpr int S = (GRAD ? 1 : 0) + NU;  // cotangent streams
   constexpr int NVP = cot_stride(S);      // padded row stride of their 9 S values
   static_assert(NVP <= 32, "streams");
@@ -656,6 +694,7 @@ __global__ void GS_BWD_BOUNDS raster_bwd_kernel(
     }
   }
   if (tid == 0) {
+    if (blockIdx.x == 0) cot_hdr->clear_floats = 0;  // the rows are being added into
     s_max = 0;
     // a stage wait that ran out in an earlier block: skip the list walk
     s_abort = status ? (*(volatile int32_t*)status & GS_FLAG_TIMEOUT) : 0;
@@ -861,7 +900,7 @@ __device__ __forceinline__ void view_direction(const ViewGeom& v, const float mu
 template <int DEG, int NU, bool GRAD>
 __device__ __forceinline__ void project_bwd_column(const float* __restrict__ P, int n, int n_pad, int i,
                                                    const gs_camera* __restrict__ cams, int V, gs_frame fr,
-                                                   const float* __restrict__ cot, int cot_pitch, ProbeArg pa,
+                                                   float* __restrict__ cot, int cot_pitch, ProbeArg pa,
                                                    float* __restrict__ grad, float* __restrict__ hz) {
   constexpr int S = (GRAD ? 1 : 0) + NU;
   constexpr int NVP = cot_stride(S);
@@ -921,6 +960,7 @@ __device__ __forceinline__ void project_bwd_column(const float* __restrict__ P, 
     for (int e = 0; e < 6; ++e) g_S[st][e] = 0.f;
   }
   uint64_t clamp_bits = 0;  // bit 3 v + c: colour channel c clamped at 0 in view v (v < kClampViews)
+  uint64_t read_rows = 0;   // bit v: the row of view v held a nonzero value (cleared at the end; v >= 64 always)
 #pragma unroll 1
   for (int v = 0; v < V; ++v) {
     float c[NVP];
@@ -932,6 +972,7 @@ __device__ __forceinline__ void project_bwd_column(const float* __restrict__ P, 
       c[4 * q + 0] = x4.x; c[4 * q + 1] = x4.y; c[4 * q + 2] = x4.z; c[4 * q + 3] = x4.w;
       any = any || x4.x != 0.f || x4.y != 0.f || x4.z != 0.f || x4.w != 0.f;
     }
+    if (v < 64) read_rows |= (uint64_t)any << v;
     if (!any) {
       if (v < kStashViews) {
 #pragma unroll
@@ -1238,23 +1279,32 @@ __device__ __forceinline__ void project_bwd_column(const float* __restrict__ P, 
         hz[(size_t)r * n_pad + i] = (n1 ? -val : val) * inv_nu;
       }
   }
+  // leave the rows read above zero for the next call (CotHeader)
+  for (int v = 0; v < V; ++v) {
+    if (v < 64 && !((read_rows >> v) & 1ull)) continue;
+    float4* row4 = reinterpret_cast<float4*>(cot + ((size_t)v * cot_pitch + i) * NVP);
+#pragma unroll
+    for (int q = 0; q < NVP / 4; ++q) row4[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
 }
 
 template <int DEG, int NU, bool GRAD>
 __global__ void GS_PBWD_BOUNDS project_bwd_kernel(const float* __restrict__ P, int n, int n_pad,
                                                   const gs_camera* __restrict__ cams, gs_frame fr,
-                                                  const float* __restrict__ cot, ProbeArg pa, float* __restrict__ grad,
-                                                  float* __restrict__ hz) {
+                                                  float* __restrict__ cot, ProbeArg pa, float* __restrict__ grad,
+                                                  float* __restrict__ hz, CotHeader* cot_hdr, uint64_t cot_floats) {
   const int i = blockIdx.x * kPbwdThreads + threadIdx.x;
   project_bwd_column<DEG, NU, GRAD>(P, n, n_pad, i, cams, fr.n_views, fr, cot, n_pad, pa, grad, hz);
+  cot_mark_clear(cot_hdr, cot_floats);
 }
 
 // A batch: item b's share of the grid takes its columns through the reverse of
 // its own projection, from its slot of the cotangents (pitch cot_pitch), with
 // its own probe step, into its own gradient and Hutchinson rows.
 template <int DEG, int NU, bool GRAD>
-__global__ void GS_PBWD_BOUNDS project_bwd_batch_kernel(BatchArg ba, gs_frame fr, const float* __restrict__ cot,
-                                                        int cot_pitch, ProbeArg pa) {
+__global__ void GS_PBWD_BOUNDS project_bwd_batch_kernel(BatchArg ba, gs_frame fr, float* __restrict__ cot,
+                                                        int cot_pitch, ProbeArg pa, CotHeader* cot_hdr,
+                                                        uint64_t cot_floats) {
   constexpr int NVP = cot_stride((GRAD ? 1 : 0) + NU);
   const int b = batch_item(ba, (int)blockIdx.x);
   const int i = ((int)blockIdx.x - ba.first_block[b]) * kPbwdThreads + threadIdx.x;
@@ -1262,6 +1312,7 @@ __global__ void GS_PBWD_BOUNDS project_bwd_batch_kernel(BatchArg ba, gs_frame fr
   pa.t_dev = nullptr;
   project_bwd_column<DEG, NU, GRAD>(ba.P[b], ba.n[b], ba.n_pad[b], i, ba.cam[b], 1, fr,
                                     cot + (size_t)b * cot_pitch * NVP, cot_pitch, pa, ba.grad[b], ba.hz[b]);
+  cot_mark_clear(cot_hdr, cot_floats);
 }
 
 // ------------------------------------------------------------------ host side
@@ -1308,8 +1359,28 @@ size_t bwd_cot_floats(int32_t n_pad, gs_frame fr, int streams) {
   return (size_t)fr.n_views * n_pad * cot_stride(streams);
 }
 
+// The reverse call's workspace: its header, the rows, and how many floats of
+// them this call uses.
+struct CotWs {
+  CotHeader* hdr;
+  float* cot;
+  uint64_t floats;
+};
+
+// Point ws at the workspace and have the rows zero before the blend: the
+// prepare kernel clears them unless the header says they already are.
+cudaError_t cot_prepare(void* workspace, uint64_t floats, CotWs& ws, cudaStream_t st) {
+  ws.hdr = reinterpret_cast<CotHeader*>(workspace);
+  ws.cot = reinterpret_cast<float*>(reinterpret_cast<char*>(workspace) + kCotHeaderBytes);
+  ws.floats = floats;
+  const size_t n4 = floats / 4;  // rows are whole float4s
+  const unsigned blocks = (unsigned)std::max<size_t>(1, std::min<size_t>((n4 + 255) / 256, 152 * 8));
+  cot_prepare_kernel<<<blocks, 256, 0, st>>>(ws.hdr, reinterpret_cast<float4*>(ws.cot), n4);
+  return cudaGetLastError();
+}
+
 template <int DEG, int NU, bool GRAD>
-void launch_pbwd(const gs_params* x, const gs_camera* cams, gs_frame fr, const float* cot, const gs_probe* probe,
+void launch_pbwd(const gs_params* x, const gs_camera* cams, gs_frame fr, CotWs ws, const gs_probe* probe,
                  float* grad, float* hz, cudaStream_t st) {
   constexpr int S = (GRAD ? 1 : 0) + NU;
   const size_t smem = pbwd_stash_bytes(fr.n_views, S);
@@ -1319,8 +1390,8 @@ void launch_pbwd(const gs_params* x, const gs_camera* cams, gs_frame fr, const f
     attr = smem;
   }
   const dim3 pg((x->n + kPbwdThreads - 1) / kPbwdThreads), pb(kPbwdThreads);
-  project_bwd_kernel<DEG, NU, GRAD><<<pg, pb, smem, st>>>(x->data, x->n, x->n_pad, cams, fr, cot, probe_arg(probe),
-                                                          grad, hz);
+  project_bwd_kernel<DEG, NU, GRAD><<<pg, pb, smem, st>>>(x->data, x->n, x->n_pad, cams, fr, ws.cot,
+                                                          probe_arg(probe), grad, hz, ws.hdr, ws.floats);
 }
 
 // The reverse blend over the frame, then the projection's reverse pass: of the
@@ -1330,7 +1401,7 @@ template <int NU, bool GRAD>
 void launch_bwd_kernels(const gs_params* x, const BatchArg* ba, int n_pad, int deg, const gs_camera* cams,
                         const gs_projected* proj, const gs_sorted* sorted, gs_frame fr, const float* image,
                         const float* target, const float* final_T, const uint32_t* n_contrib, const float* image_tan,
-                        const gs_probe* probe, gs_loss loss, float* grad, float* hz, float* loss_out, float* cot,
+                        const gs_probe* probe, gs_loss loss, float* grad, float* hz, float* loss_out, CotWs ws,
                         int32_t* status, cudaStream_t st) {
   const TileGrid g = tile_grid(fr);
   const int nthr = fr.tile_w * fr.tile_h / kPixPerThread, batch = bwd_batch(fr, nthr);
@@ -1348,7 +1419,8 @@ void launch_bwd_kernels(const gs_params* x, const BatchArg* ba, int n_pad, int d
   kern<<<blocks, nthr, smem, st>>>(
       reinterpret_cast<const float4*>(proj->rec), sorted->vals, sorted->ranges, sorted->order, n_pad, fr, g.Tx,
       g.T, image,
-      target, final_T, n_contrib, image_tan, loss.kind, loss.gn_floor, inv_m, cot, loss_out, ba ? 1 : 0, status);
+      target, final_T, n_contrib, image_tan, loss.kind, loss.gn_floor, inv_m, ws.cot, loss_out, ba ? 1 : 0, ws.hdr,
+      status);
   if (ba) {
     if (ba->first_block[ba->n_items] == 0) return;
     constexpr int S = (GRAD ? 1 : 0) + NU;
@@ -1362,7 +1434,8 @@ void launch_bwd_kernels(const gs_params* x, const BatchArg* ba, int n_pad, int d
       if (allow_smem(project_bwd_batch_kernel<D, NU, GRAD>, sm) != cudaSuccess) return;            \
       battr = sm;                                                                                  \
     }                                                                                              \
-    project_bwd_batch_kernel<D, NU, GRAD><<<grid, blk, sm, st>>>(*ba, fr, cot, n_pad, pa);         \
+    project_bwd_batch_kernel<D, NU, GRAD><<<grid, blk, sm, st>>>(*ba, fr, ws.cot, n_pad, pa, ws.hdr, \
+                                                                 ws.floats);                       \
   } while (0)
     switch (deg) {
       case 0: GS_PBWD_BATCH(0); break;
@@ -1375,10 +1448,10 @@ void launch_bwd_kernels(const gs_params* x, const BatchArg* ba, int n_pad, int d
   }
   if (x->n == 0) return;
   switch (x->sh_degree) {
-    case 0: launch_pbwd<0, NU, GRAD>(x, cams, fr, cot, probe, grad, hz, st); break;
-    case 1: launch_pbwd<1, NU, GRAD>(x, cams, fr, cot, probe, grad, hz, st); break;
-    case 2: launch_pbwd<2, NU, GRAD>(x, cams, fr, cot, probe, grad, hz, st); break;
-    default: launch_pbwd<3, NU, GRAD>(x, cams, fr, cot, probe, grad, hz, st); break;
+    case 0: launch_pbwd<0, NU, GRAD>(x, cams, fr, ws, probe, grad, hz, st); break;
+    case 1: launch_pbwd<1, NU, GRAD>(x, cams, fr, ws, probe, grad, hz, st); break;
+    case 2: launch_pbwd<2, NU, GRAD>(x, cams, fr, ws, probe, grad, hz, st); break;
+    default: launch_pbwd<3, NU, GRAD>(x, cams, fr, ws, probe, grad, hz, st); break;
   }
 }
 
@@ -1388,9 +1461,9 @@ void launch_bwd_streams(bool want_grad, int nu, const gs_params* x, const BatchA
                         const gs_camera* cams, const gs_projected* proj, const gs_sorted* sorted, gs_frame frame,
                         const float* image, const float* target, const float* final_T, const uint32_t* n_contrib,
                         const float* image_tangent, const gs_probe* probe, gs_loss loss, float* gptr, float* hptr,
-                        float* loss_out, float* cot, int32_t* status, cudaStream_t st) {
+                        float* loss_out, CotWs ws, int32_t* status, cudaStream_t st) {
 #define GS_BWD_ARGS x, ba, n_pad, deg, cams, proj, sorted, frame, image, target, final_T, n_contrib, image_tangent, \
-                    probe, loss, gptr, hptr, loss_out, cot, status, st
+                    probe, loss, gptr, hptr, loss_out, ws, status, st
   if (want_grad) {
     if (nu == 0) launch_bwd_kernels<0, true>(GS_BWD_ARGS);
     else if (nu == 1) launch_bwd_kernels<1, true>(GS_BWD_ARGS);
@@ -1428,16 +1501,18 @@ gs_status run_bwd(bool want_grad, const gs_params* x, const gs_camera* cams, gs_
   auto same = [&](const gs_params* p) { return !p || (p->n == x->n && p->n_pad == x->n_pad && p->sh_degree == x->sh_degree); };
   GS_REQUIRE(same(grad) && same(hz), "%s: grad/hz layout differs from x", name);
   const int streams = (want_grad ? 1 : 0) + nu;
-  const size_t need = bwd_cot_floats(x->n_pad, frame, streams) * sizeof(float);
+  const size_t floats = bwd_cot_floats(x->n_pad, frame, streams);
+  const size_t need = kCotHeaderBytes + floats * sizeof(float);
   GS_REQUIRE(workspace && workspace_bytes >= need, "%s: workspace needs %zu bytes, got %zu", name, need,
              workspace_bytes);
+  GS_REQUIRE(((uintptr_t)workspace & 15) == 0, "%s: workspace must be 16-byte aligned", name);
   cudaStream_t st = (cudaStream_t)stream;
-  float* cot = (float*)workspace;
-  if (cudaMemsetAsync(cot, 0, need, st) != cudaSuccess) return check_launch(name);
+  CotWs ws;
+  if (cot_prepare(workspace, floats, ws, st) != cudaSuccess) return check_launch(name);
   float* gptr = want_grad ? grad->data : nullptr;
   float* hptr = nu ? hz->data : nullptr;
   launch_bwd_streams(want_grad, nu, x, nullptr, x->n_pad, x->sh_degree, cams, proj, sorted, frame, image, target,
-                     final_T, n_contrib, image_tangent, probe, loss, gptr, hptr, loss_out, cot, status, st);
+                     final_T, n_contrib, image_tangent, probe, loss, gptr, hptr, loss_out, ws, status, st);
   return check_launch(name);
 }
 
@@ -1466,7 +1541,7 @@ extern "C" gs_status gs_raster_fwd(const gs_projected* proj, const gs_sorted* so
 
 extern "C" size_t gs_raster_bwd_workspace_size(int32_t n_pad, gs_frame frame, int32_t nu) {
   if (n_pad < 0 || nu < 0 || nu > 2 || !gs::frame_ok(frame)) return 0;
-  return gs::bwd_cot_floats(n_pad, frame, 1 + nu) * sizeof(float);
+  return gs::kCotHeaderBytes + gs::bwd_cot_floats(n_pad, frame, 1 + nu) * sizeof(float);
 }
 
 extern "C" gs_status gs_raster_bwd(const gs_params* x, const gs_camera* cams, gs_frame frame, const gs_projected* proj,
@@ -1523,17 +1598,18 @@ extern "C" gs_status gs_raster_bwd_batch(const gs_batch_item* items, int32_t n_i
     GS_REQUIRE(it.x.n >= 0 && it.x.n <= n_pad_max && it.x.n_pad % 4 == 0, "%s: item %d: bad n=%d n_pad=%d", name,
                b, it.x.n, it.x.n_pad);
   }
-  const size_t need = bwd_cot_floats(n_pad_max, frame, 1 + nu) * sizeof(float);
+  const size_t floats = bwd_cot_floats(n_pad_max, frame, 1 + nu);
+  const size_t need = kCotHeaderBytes + floats * sizeof(float);
   GS_REQUIRE(workspace && workspace_bytes >= need, "%s: workspace needs %zu bytes, got %zu", name, need,
              workspace_bytes);
+  GS_REQUIRE(((uintptr_t)workspace & 15) == 0, "%s: workspace must be 16-byte aligned", name);
   cudaStream_t st = (cudaStream_t)stream;
-  float* cot = (float*)workspace;
-  if (cudaMemsetAsync(cot, 0, bwd_cot_floats(n_pad_max, frame, 1 + nu) * sizeof(float), st) != cudaSuccess)
-    return check_launch(name);
+  CotWs ws;
+  if (cot_prepare(workspace, floats, ws, st) != cudaSuccess) return check_launch(name);
   const BatchArg ba = batch_arg(items, n_items, [](const gs_batch_item& it) {
     return (it.x.n + kPbwdThreads - 1) / kPbwdThreads;
   });
   launch_bwd_streams(true, nu, nullptr, &ba, n_pad_max, deg, nullptr, proj, sorted, frame, image, target, final_T,
-                     n_contrib, image_tangent, probe, loss, nullptr, nullptr, loss_out, cot, status, st);
+                     n_contrib, image_tangent, probe, loss, nullptr, nullptr, loss_out, ws, status, st);
   return check_launch(name);
 }

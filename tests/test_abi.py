@@ -75,7 +75,8 @@ def test_host_argument_checks_reject_without_touching_the_device(lib):
     assert lib.gs_bin_sort_workspace_size(32, G.frame_struct(1, 64, 64, 12, 16), 1000) == 0
     assert lib.gs_bin_sort_workspace_size(32, G.frame_struct(1, 64, 64, 16, 16), 1000) > 0
     assert lib.gs_raster_bwd_workspace_size(32, G.frame_struct(2, 64, 64), 3) == 0
-    assert lib.gs_raster_bwd_workspace_size(32, G.frame_struct(2, 64, 64), 2) == 2 * 32 * 28 * 4
+    # a 256-byte header, then 2 views x 32 columns x 28 floats of cotangent rows
+    assert lib.gs_raster_bwd_workspace_size(32, G.frame_struct(2, 64, 64), 2) == 256 + 2 * 32 * 28 * 4
     cfg = G.gs_tr_config(0.9, 0.999, 1e-12, 1e-2, 0, 0)
     x = G.gs_params(10, 32, 0, 0, 16)
     rc = lib.gs_tr_update(C.byref(x), C.byref(x), C.byref(x), C.byref(x), None, C.byref(cfg), 1, 1e-6, None,

@@ -384,6 +384,35 @@ def test_reverse_pass_from_given_cotangents_matches_oracle(want_grad):
                  rnd=ref["hz_round"])
 
 
+def test_reverse_workspace_is_left_clear_and_reused():
+    """The reverse call leaves its cotangent rows zero and says so in the
+    workspace header, so the next call skips clearing them; a workspace of
+    arbitrary bytes is cleared first.  Either way the results are the first
+    call's (up to the order of the float atomics)."""
+    sc, e, ref = _grad_case("ragged", 2)
+    g1, h1 = e.grad[:, : sc.n].clone(), e.hz[:, : sc.n].clone()
+    ws = e.bwd_ws
+    hdr = ws[:16].cpu().numpy().view(np.uint64)
+    rows = ws[256:].view(torch.float32)
+    assert hdr[0] == 0x9D2C5680A3B1F4E7 and hdr[1] >= rows.numel() and int(torch.count_nonzero(rows)) == 0
+
+    def again():
+        e.loss_val.zero_()
+        e.raster_bwd(4, probes=True)
+        torch.cuda.synchronize()
+        assert e.read_status() == 0
+        for a, b in ((e.grad[:, : sc.n], g1), (e.hz[:, : sc.n], h1)):
+            torch.testing.assert_close(a, b, rtol=1e-5, atol=1e-6 * b.abs().max().item())
+
+    again()                      # rows known clear: nothing cleared
+    ws.fill_(0x7F)               # foreign bytes, header included
+    again()
+    e.hvp_diag(4)                # fewer streams over the same workspace
+    torch.cuda.synchronize()
+    again()
+    assert int(torch.count_nonzero(rows)) == 0
+
+
 def test_hvp_diag_standalone_equals_fused():
     sc, e, ref = _grad_case("cfg1", 1)
     fused = e.hz.clone()
