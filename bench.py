@@ -592,13 +592,13 @@ def raster_bwd_flops_per_unit() -> int:
 RASTER_BWD_TRAFFIC = {
     # one-kernel captures (dram__bytes_read.sum + dram__bytes_write.sum) of the
     # reverse call's two kernels on the 2-view case of the bench scene
-    "blend_bytes": 387_207_936 + 54_813_696,        # raster_bwd_kernel
-    "projection_bytes": 460_112_640 + 420_741_120,  # project_bwd_kernel
+    "blend_bytes": 387_655_168 + 54_814_208,        # raster_bwd_kernel
+    "projection_bytes": 460_195_840 + 448_422_656,  # project_bwd_kernel
     "pairs": 12_223_264,                            # pairs blended in that launch
     "n": 1_000_000,
     "views": 2,
     "sources": {
-        "paper_2602_00395_gb300/csrc/raster.cu": "d296c19b9856454a949af5f5646e50be31146d100d97686e36662c71fd4a7733",
+        "paper_2602_00395_gb300/csrc/raster.cu": "5f1eefa26c2570958b4b37b3ac8409012ebeedf652fe0f4d566cd437099814c0",
         "paper_2602_00395_gb300/csrc/common.cuh": "b7201d9f818a49a1c40435b69f8e6e4e3d70dc9d7b4428d641c067699f5e6429",
     },
 }
@@ -607,11 +607,12 @@ RASTER_BWD_TRAFFIC = {
 def projection_reverse_bytes(n: int, views: int, sh_degree: int = SH_DEG, nu: int = NU) -> int:
     """Algorithmic bytes of the projection reverse: each Gaussian's parameter
     column read once, its cotangent row of every view read once (9 floats per
-    stream, padded to a float4), its gradient and z . Gz columns written."""
+    stream, padded to a float4) and cleared for the next call, its gradient and
+    z . Gz columns written."""
     rows = 11 + 3 * (sh_degree + 1) ** 2
     streams = 1 + nu
     cot = 4 * (-(-9 * streams // 4))
-    return n * (4 * rows + views * 4 * cot + (2 if nu > 0 else 1) * 4 * rows)
+    return n * (4 * rows + 2 * views * 4 * cot + (2 if nu > 0 else 1) * 4 * rows)
 
 
 def raster_bwd_traffic(pairs: float | None = None, n: int | None = None, views: int | None = None):

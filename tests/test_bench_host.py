@@ -15,10 +15,11 @@ def test_traffic_is_reported_only_for_the_captured_sources(monkeypatch):
     monkeypatch.setattr(bench, "RASTER_BWD_TRAFFIC", same)
     assert bench.raster_bwd_traffic() == 1500
     assert bench.raster_bwd_traffic(40) == 4500  # the blend's bytes scaled by the pairs
-    # the projection reverse's by its algorithmic bytes: 2 -> 8 views of 112-byte cotangent rows
-    # next to the 236-byte parameter column and two 236-byte output columns (SH degree 3, two probes)
-    assert bench.projection_reverse_bytes(100, 2) == 100 * (236 + 2 * 112 + 2 * 236)
-    want = 4000 + 500 * (236 + 8 * 112 + 472) / (236 + 2 * 112 + 472)
+    # the projection reverse's by its algorithmic bytes: 2 -> 8 views of 112-byte cotangent rows, each
+    # read and cleared, next to the 236-byte parameter column and two 236-byte output columns (SH degree 3,
+    # two probes)
+    assert bench.projection_reverse_bytes(100, 2) == 100 * (236 + 2 * 2 * 112 + 2 * 236)
+    want = 4000 + 500 * (236 + 2 * 8 * 112 + 472) / (236 + 2 * 2 * 112 + 472)
     assert bench.raster_bwd_traffic(40, 100, 8) == round(want)
     changed = dict(same, sources=dict(sources))
     first = next(iter(changed["sources"]))
