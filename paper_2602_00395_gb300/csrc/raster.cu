@@ -229,6 +229,33 @@ __device__ __forceinline__ void fwd_apply(FwdPixel<NU>& p, const Rec& r, const R
   p.last = bl ? pos + 1 : p.last;
 }
 
+// 1: when a batch holds at most one record per thread, each thread reads the
+// Gaussian index of its record in the batch after next one iteration ahead, so
+// that staging a batch does not wait on that read.
+#ifndef GS_FWD_PREFETCH_VALS
+#define GS_FWD_PREFETCH_VALS 1
+#endif
+
+// stage_batch for a batch of at most blockDim.x records, the calling thread's
+// record (threadIdx.x) being splat gi.
+template <int NT>
+__device__ __forceinline__ void stage_batch_one(int b, int batch, int n, int view, int n_pad, uint32_t gi,
+                                                const float4* __restrict__ rec, const float4* __restrict__ tan,
+                                                Rec* buf, Rec* tbuf, uint64_t* bars) {
+  const int bi = b & 1;
+  const int cnt = min(batch, n - b * batch);
+  if (threadIdx.x == 0) mbar_arrive_expect_tx(&bars[bi], (uint32_t)(cnt * (int)sizeof(Rec) * (1 + NT)));
+  fence_proxy_async();
+  const int q = threadIdx.x;
+  if (q < cnt) {
+    bulk_g2s(&buf[bi * batch + q], rec + 3 * ((size_t)view * n_pad + gi), sizeof(Rec), &bars[bi]);
+#pragma unroll
+    for (int k = 0; k < NT; ++k)
+      bulk_g2s(&tbuf[(bi * NT + k) * batch + q], tan + 3 * (((size_t)view * NT + k) * n_pad + gi), sizeof(Rec),
+               &bars[bi]);
+  }
+}
+
 // CB: the frame sets its own batch (else one record per thread, known to the
 // compiler as the block size).
 template <int NU, bool CB>
@@ -282,13 +309,31 @@ __global__ void GS_FWD_BOUNDS raster_fwd_kernel(const float4* __restrict__ rec, 
 
   const int nb = (n + batch - 1) / batch;
   int issued = 0;  // batches staged so far (block-uniform)
+  // with at most one record per thread and batch, the index of this thread's
+  // record in batch bb (0 past the list), read one batch ahead of its staging
+  const bool one = GS_FWD_PREFETCH_VALS && batch <= nthr;
+  auto index_of = [&](int bb) -> uint32_t {
+    const int q = bb * batch + tid;
+    return (bb < nb && tid < batch && q < n) ? __ldg(vals + start + (uint32_t)q) : 0u;
+  };
+  uint32_t gi_next = 0;
   if (nb > 0) {
-    stage_batch<NU>(0, batch, start, n, view, n_pad, vals, rec, tan, buf, tbuf, nullptr, bars);
+    if (one) {
+      stage_batch_one<NU>(0, batch, n, view, n_pad, index_of(0), rec, tan, buf, tbuf, bars);
+      gi_next = index_of(1);
+    } else {
+      stage_batch<NU>(0, batch, start, n, view, n_pad, vals, rec, tan, buf, tbuf, nullptr, bars);
+    }
     issued = 1;
   }
   for (int b = 0; b < nb; ++b) {
     if (b + 1 < nb) {
-      stage_batch<NU>(b + 1, batch, start, n, view, n_pad, vals, rec, tan, buf, tbuf, nullptr, bars);
+      if (one) {
+        stage_batch_one<NU>(b + 1, batch, n, view, n_pad, gi_next, rec, tan, buf, tbuf, bars);
+        gi_next = index_of(b + 2);
+      } else {
+        stage_batch<NU>(b + 1, batch, start, n, view, n_pad, vals, rec, tan, buf, tbuf, nullptr, bars);
+      }
       issued = b + 2;
     }
     const int bi = b & 1;
@@ -548,6 +593,16 @@ __device__ __forceinline__ void cot_mark_clear(CotHeader* h, uint64_t floats) {
   }
 }
 
+// 1: the reverse recovers T_i with the fast division intrinsic's reciprocal
+// of 1 - alpha (at most 2 ulps off; 1 - alpha lies in [0.01, 1]) instead of
+// the correctly rounded one, whose slower path also costs registers: about
+// 2.5 ulps per recovered step instead of 1, which over the few hundred splats
+// a pixel walks back stays orders of magnitude inside the gradient and
+// curvature tolerances.
+#ifndef GS_BWD_APPROX_RCP
+#define GS_BWD_APPROX_RCP 1
+#endif
+
 // Reverse-pass state of one pixel: the cotangent dL/dC of each stream, the
 // transmittance being recovered back to front, the colour suffix
 // sum_{j>i} c_j a_j T_j, and the list position after its last blended splat.
@@ -570,7 +625,11 @@ struct BwdPixel {
 template <int S, bool FIRST>
 __device__ __forceinline__ void bwd_accumulate(BwdPixel<S>& p, const Rec& r, float dx, float dy, float G, float oG,
                                                float alpha, float (&v)[32]) {
+#if GS_BWD_APPROX_RCP
+  const float inv = __fdividef(1.f, 1.f - alpha);
+#else
   const float inv = __frcp_rn(1.f - alpha);
+#endif
   const float Ti = p.T * inv;
   const float rgb0 = r.b.z, rgb1 = r.b.w, rgb2 = r.c.x;
   const float da0 = rgb0 * Ti - p.suf[0] * inv;
