@@ -131,8 +131,10 @@ typedef struct gs_eps_schedule {
  *            rounded up (-inf: no pixel reaches 1/255; +inf: unbounded).
  *            Binning narrows the splat's tile square to that box, and the
  *            rasteriser skips the splat for an 8 x 8 pixel block outside it.
- *   tangent: NULL or V x nu x n_pad records of 12 floats, the forward-mode
- *            derivative of (mx, my, A, B, C, opacity, r, g, b) along probe k */
+ *   tangent: NULL or V x n_pad x nu records of 12 floats (a splat's probes
+ *            adjacent, so that the rasteriser stages them with one copy), the
+ *            forward-mode derivative of (mx, my, A, B, C, opacity, r, g, b)
+ *            along probe k */
 typedef struct gs_projected {
   float* rec;
   float* tangent;

@@ -39,7 +39,8 @@ __device__ __forceinline__ void store_culled(float4* rec, size_t at) {
 
 // Column i of the parameter matrix P (n Gaussians, row pitch n_pad) projected
 // into views cams[0..V): record v * pitch + i of rec, tangent records
-// (v * NU + k) * pitch + i of tan; columns n <= i < pitch are written culled.
+// (v * pitch + i) * NU + k of tan (a splat's probes adjacent); columns n <= i <
+// pitch are written culled.
 // Called by every thread of a 128-thread block (the SH staging is block-wide).
 template <int DEG, int NU>
 __device__ __forceinline__ void project_column(const float* __restrict__ P, int n, int n_pad, int i, int pitch,
@@ -58,7 +59,7 @@ __device__ __forceinline__ void project_column(const float* __restrict__ P, int 
   if (i >= n) {
     for (int v = 0; v < V; ++v) {
       store_culled(rec, (size_t)v * pitch + i);
-      for (int k = 0; k < NU; ++k) store_culled(tan, ((size_t)v * NU + k) * pitch + i);
+      for (int k = 0; k < NU; ++k) store_culled(tan, ((size_t)v * pitch + i) * NU + k);
     }
     return;
   }
@@ -130,7 +131,7 @@ __device__ __forceinline__ void project_column(const float* __restrict__ P, int 
     S t2 = Rc[2][0] * mu0 + Rc[2][1] * mu1 + Rc[2][2] * mu2 + tc[2];
     if (!(val(t2) > c->near_plane)) {
       store_culled(rec, at);
-      for (int k = 0; k < NU; ++k) store_culled(tan, ((size_t)v * NU + k) * pitch + i);
+      for (int k = 0; k < NU; ++k) store_culled(tan, ((size_t)v * pitch + i) * NU + k);
       continue;
     }
     // camera-frame covariance Rc Sigma Rc^T
@@ -157,7 +158,7 @@ __device__ __forceinline__ void project_column(const float* __restrict__ P, int 
     const S det = a * cc - b * b;
     if (!(val(det) > 0.f)) {
       store_culled(rec, at);
-      for (int k = 0; k < NU; ++k) store_culled(tan, ((size_t)v * NU + k) * pitch + i);
+      for (int k = 0; k < NU; ++k) store_culled(tan, ((size_t)v * pitch + i) * NU + k);
       continue;
     }
     const S idet = 1.f / det;
@@ -205,7 +206,7 @@ __device__ __forceinline__ void project_column(const float* __restrict__ P, int 
     if constexpr (NU > 0) {
 #pragma unroll
       for (int k = 0; k < NU; ++k) {
-        const size_t tk = ((size_t)v * NU + k) * pitch + i;
+        const size_t tk = ((size_t)v * pitch + i) * NU + k;
         tan[3 * tk + 0] = make_float4(mx.d[k], my.d[k], cA.d[k], cB.d[k]);
         tan[3 * tk + 1] = make_float4(cC.d[k], opac.d[k], rgb[0].d[k], rgb[1].d[k]);
         tan[3 * tk + 2] = make_float4(rgb[2].d[k], 0.f, 0.f, 0.f);

@@ -78,8 +78,9 @@ __device__ __forceinline__ bool footprint_meets_block(const Rec& r, float x0, fl
 }
 
 // Stage batch b of a tile list (records [b * batch, b * batch + batch)) into
-// buffer (b & 1): one bulk copy per record (and per tangent record), issued by
-// the block's threads in turn, all completing on the buffer's mbarrier.
+// buffer (b & 1): one bulk copy per record and one for its NT adjacent probe
+// tangent records (staged as [batch][NT]), issued by the block's threads in
+// turn, all completing on the buffer's mbarrier.
 template <int NT>
 __device__ __forceinline__ void stage_batch(int b, int batch, uint32_t start, int n, int view, int n_pad,
                                             const uint32_t* __restrict__ vals, const float4* __restrict__ rec,
@@ -93,10 +94,8 @@ __device__ __forceinline__ void stage_batch(int b, int batch, uint32_t start, in
     const uint32_t gi = vals[start + (uint32_t)(b * batch + q)];
     if (s_idx) s_idx[bi * batch + q] = gi;
     bulk_g2s(&buf[bi * batch + q], rec + 3 * ((size_t)view * n_pad + gi), sizeof(Rec), &bars[bi]);
-#pragma unroll
-    for (int k = 0; k < NT; ++k)
-      bulk_g2s(&tbuf[(bi * NT + k) * batch + q], tan + 3 * (((size_t)view * NT + k) * n_pad + gi), sizeof(Rec),
-               &bars[bi]);
+    if (NT > 0)  // the splat's NT probe tangent records are adjacent: one copy
+      bulk_g2s(&tbuf[(bi * batch + q) * NT], tan + 3 * ((size_t)view * n_pad + gi) * NT, NT * sizeof(Rec), &bars[bi]);
   }
 }
 
@@ -249,10 +248,8 @@ __device__ __forceinline__ void stage_batch_one(int b, int batch, int n, int vie
   const int q = threadIdx.x;
   if (q < cnt) {
     bulk_g2s(&buf[bi * batch + q], rec + 3 * ((size_t)view * n_pad + gi), sizeof(Rec), &bars[bi]);
-#pragma unroll
-    for (int k = 0; k < NT; ++k)
-      bulk_g2s(&tbuf[(bi * NT + k) * batch + q], tan + 3 * (((size_t)view * NT + k) * n_pad + gi), sizeof(Rec),
-               &bars[bi]);
+    if (NT > 0)  // the splat's NT probe tangent records are adjacent: one copy
+      bulk_g2s(&tbuf[(bi * batch + q) * NT], tan + 3 * ((size_t)view * n_pad + gi) * NT, NT * sizeof(Rec), &bars[bi]);
   }
 }
 
@@ -347,7 +344,7 @@ __global__ void GS_FWD_BOUNDS raster_fwd_kernel(const float4* __restrict__ rec, 
       s_mask[q] = ok ? warp_block_mask(r, tile_x0, tile_y0, fr.tile_w, nwarps) : 0u;
 #pragma unroll
       for (int k = 0; k < NU; ++k) {
-        Rec* tp = &tbuf[(bi * NU + k) * batch + q];
+        Rec* tp = &tbuf[(bi * batch + q) * NU + k];
         const float4 ta = tp->a;  // dmx, dmy, dA, dB
         const float dC = tp->b.x;
         tp->a = make_float4(-0.5f * ta.z, -ta.w, -0.5f * dC, -(r.a.z * ta.x + r.a.w * ta.y));
@@ -368,7 +365,7 @@ __global__ void GS_FWD_BOUNDS raster_fwd_kernel(const float4* __restrict__ rec, 
         const int j = j0 + __ffs(bits) - 1;
         bits &= bits - 1;
         const Rec r = bb[j];
-        const Rec* t0 = tbuf + (size_t)bi * NU * batch + j;
+        const Rec* t0 = tbuf + ((size_t)bi * batch + j) * NU;
         const uint32_t pos = (uint32_t)(b * batch + j);
         float dx[kPixPerThread], dy[kPixPerThread], G[kPixPerThread], oG[kPixPerThread], al[kPixPerThread];
         bool on[kPixPerThread];
@@ -387,7 +384,7 @@ __global__ void GS_FWD_BOUNDS raster_fwd_kernel(const float4* __restrict__ rec, 
         if (!anyrow) continue;
         Rec tk[NU > 0 ? NU : 1];
 #pragma unroll
-        for (int k = 0; k < NU; ++k) tk[k] = t0[k * batch];
+        for (int k = 0; k < NU; ++k) tk[k] = t0[k];
 #pragma unroll
         for (int q = 0; q < kPixPerThread; ++q)
           if (rows[q]) fwd_apply<NU>(pix[q], r, tk, 1, pos, on[q], dx[q], dy[q], G[q], oG[q], al[q]);
