@@ -492,7 +492,7 @@ constexpr int kBwdSparseLanes = GS_BWD_SPARSE_LANES;
 // Minimum resident CTAs per SM requested from the compiler for the reverse
 // kernel (0: no request).
 #ifndef GS_BWD_MIN_BLOCKS
-#define GS_BWD_MIN_BLOCKS 8
+#define GS_BWD_MIN_BLOCKS 7
 #endif
 #if GS_BWD_MIN_BLOCKS > 0
 #define GS_BWD_BOUNDS __launch_bounds__(128, GS_BWD_MIN_BLOCKS)
