@@ -428,10 +428,11 @@ __global__ void GS_FWD_BOUNDS raster_fwd_kernel(const float4* __restrict__ rec, 
 // on to the next batch as soon as it has landed and tests only its own block's
 // visibility, so a warp with little work in a batch does not wait for the
 // others.  The last warp to release a buffer refills it with the batch
-// kBwdStages further on.  Two stages measured fastest (deeper rings take
-// shared memory from L1 or from resident CTAs).
+// kBwdStages further on.  At 7 CTAs per SM three stages measured fastest (at
+// 8 CTAs per SM two did: deeper rings took shared memory from L1 or from
+// resident CTAs).
 #ifndef GS_BWD_STAGES
-#define GS_BWD_STAGES 2
+#define GS_BWD_STAGES 3
 #endif
 constexpr int kBwdStages = GS_BWD_STAGES;
 // ring header: one mbarrier and one release counter per stage, 16-byte aligned
