@@ -397,13 +397,18 @@ class BatchStep:
     records in slot b of one set of buffers.  Each request keeps its own
     objective (m = 3 H W), probes (its scene's step t) and update; its image is
     images()[b].  Buffers are allocated for the batch at construction (on the
-    current stream, from PyTorch's caching allocator)."""
+    current stream, from PyTorch's caching allocator), or taken from `pool`, a
+    dict of buffers that a caller keeps per stream and that grow as needed:
+    consecutive batches on one stream then reuse them (and the reverse pass
+    finds its workspace already clear).  A pooled batch's outputs (images())
+    are valid until the next batch with the same pool starts."""
 
     def __init__(self, entries: list[BatchEntry], width: int, height: int, *, sh_degree: int = 3, nu: int = 1,
                  tile=(16, 16), capacity: int, train: bool = True, loss_kind: int = G.GS_LOSS_L1,
                  gn_floor: float = 1e-3, cfg: TRConfig | None = None, probe_seed: int = 42, device: str = "cuda",
-                 footprint_bins: bool = True, batch: int = 0):
+                 footprint_bins: bool = True, batch: int = 0, pool: dict | None = None):
         G.load()
+        self.pool = pool
         assert 1 <= len(entries) <= G.GS_BATCH_MAX
         self.entries, self.B, self.W, self.H, self.deg = entries, len(entries), width, height, sh_degree
         self.train, self.nu = train, (nu if train else 0)
@@ -415,32 +420,43 @@ class BatchStep:
         self.n_pad = max(e.x.shape[1] for e in entries)
         self.frame = G.frame_struct(self.B, width, height, *tile, footprint_bins=footprint_bins, batch=batch)
         Tx, Ty = -(-width // tile[0]), -(-height // tile[1])
-        f32 = dict(dtype=torch.float32, device=self.device)
-        i32 = dict(dtype=torch.int32, device=self.device)
+        f32, i32, u8 = torch.float32, torch.int32, torch.uint8
+        buf = self._buf
         HW, B = width * height, self.B
-        self.rec = torch.empty(B * self.n_pad * 12, **f32)
-        self.tan = torch.empty(self.nu * B * self.n_pad * 12 if self.nu else 4, **f32)
-        self.image = torch.empty(B * 3 * HW, **f32)
-        self.final_T = torch.empty(B * HW, **f32)
-        self.n_contrib = torch.empty(B * HW, **i32)
-        self.image_tan = torch.empty(self.nu * B * 3 * HW if self.nu else 4, **f32)
-        self.status = torch.zeros(1, **i32)
-        self.ranges = torch.empty(2 * B * Tx * Ty, **i32)
-        self.order = torch.empty(B * Tx * Ty, **i32)
-        self.n_pairs = torch.empty(1, **i32)
+        self.rec = buf("rec", B * self.n_pad * 12, f32)
+        self.tan = buf("tan", self.nu * B * self.n_pad * 12 if self.nu else 4, f32)
+        self.image = buf("image", B * 3 * HW, f32)
+        self.final_T = buf("final_T", B * HW, f32)
+        self.n_contrib = buf("n_contrib", B * HW, i32)
+        self.image_tan = buf("image_tan", self.nu * B * 3 * HW if self.nu else 4, f32)
+        self.status = buf("status", 1, i32).zero_()
+        self.ranges = buf("ranges", 2 * B * Tx * Ty, i32)
+        self.order = buf("order", B * Tx * Ty, i32)
+        self.n_pairs = buf("n_pairs", 1, i32)
         self.capacity = int(capacity)
-        self.keys = torch.empty(self.capacity, dtype=torch.int32, device=self.device)
-        self.vals = torch.empty(self.capacity, **i32)
-        self.sort_ws = torch.empty(G.gs_bin_sort_workspace_size(self.n_pad, self.frame, self.capacity),
-                                   dtype=torch.uint8, device=self.device)
+        self.keys = buf("keys", self.capacity, i32)
+        self.vals = buf("vals", self.capacity, i32)
+        self.sort_ws = buf("sort_ws", G.gs_bin_sort_workspace_size(self.n_pad, self.frame, self.capacity), u8)
         self.cams = torch.cat([e.cam for e in entries])
         if train:
-            self.target = torch.empty(B * 3 * HW, **f32)
-            self.loss_val = torch.zeros(B, **f32)
-            self.grads = [torch.empty(self.rows, e.x.shape[1], **f32) for e in entries]
-            self.hzs = [torch.empty(self.rows, e.x.shape[1], **f32) for e in entries] if self.nu else None
-            self.bwd_ws = torch.empty(G.gs_raster_bwd_workspace_size(self.n_pad, self.frame, self.nu),
-                                      dtype=torch.uint8, device=self.device)
+            self.target = buf("target", B * 3 * HW, f32)
+            self.loss_val = buf("loss_val", B, f32).zero_()
+            self.grads = [buf(f"grad{b}", self.rows * e.x.shape[1], f32).view(self.rows, e.x.shape[1])
+                          for b, e in enumerate(entries)]
+            self.hzs = ([buf(f"hz{b}", self.rows * e.x.shape[1], f32).view(self.rows, e.x.shape[1])
+                         for b, e in enumerate(entries)] if self.nu else None)
+            self.bwd_ws = buf("bwd_ws", G.gs_raster_bwd_workspace_size(self.n_pad, self.frame, self.nu), u8)
+
+    def _buf(self, name: str, numel: int, dtype) -> torch.Tensor:
+        """A device buffer of numel elements: a new one, or the front of the pool's
+        buffer of that name (replaced by a larger one when too small)."""
+        if self.pool is None:
+            return torch.empty(numel, dtype=dtype, device=self.device)
+        t = self.pool.get(name)
+        if t is None or t.dtype != dtype or t.numel() < numel:
+            t = torch.empty(max(numel, 1), dtype=dtype, device=self.device)
+            self.pool[name] = t
+        return t[:numel]
 
     @staticmethod
     def working_bytes(n_pads: list[int], width: int, height: int, *, sh_degree: int = 3, nu: int = 1,

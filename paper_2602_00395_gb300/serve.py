@@ -7,8 +7,11 @@ continuous batching on the GPU.
   (projection, binning, forward, reverse pass with the Hutchinson probes,
   update) or one render (projection, binning, forward).  The working buffers
   of a batch of requests (records, pairs, images, cotangents, gradients,
-  curvature) are allocated for it from PyTorch's caching allocator on its
-  stream and released when it completes.
+  curvature) come from its slot's pool: each slot (stream) keeps the buffers
+  of its batches and grows them as needed, so that a batch allocates nothing
+  once the slot has seen a batch as large, and the reverse pass finds its
+  workspace already clear.  The budget bounds the working sets of the
+  batches in flight (the pools keep, per slot, the largest seen).
 * Admission: a request that has arrived is started when a slot (a CUDA stream)
   is free, its scene has no request in flight (a training step changes the
   scene), and its batch's working set fits the HBM budget left by the batches
@@ -227,6 +230,9 @@ class Server:
         is padded to the largest scene); None for any."""
         self.scenes = _by_sid(scenes)
         self.streams = [torch.cuda.Stream() for _ in range(slots)]
+        # each slot's batch buffers, reused by its next batch (a slot runs one
+        # batch at a time, so the reuse follows the previous batch's end)
+        self.pools = [dict() for _ in range(slots)]
         self.budget = budget_bytes if budget_bytes is not None else 1 << 62
         self.max_batch = max(1, min(max_batch, G.GS_BATCH_MAX))
         self.max_pad_ratio = max_pad_ratio
@@ -241,13 +247,13 @@ class Server:
                                        nu=s0.nu, tile=s0.tile, capacity=sum(sc.capacity for sc in scs),
                                        train=reqs[0].kind == "train")
 
-    def start(self, batch: list, stream) -> BatchStep:
+    def start(self, batch: list, stream, pool: dict | None = None) -> BatchStep:
         scs = [self.scenes[r.scene] for r in batch]
         s0 = scs[0]
         with torch.cuda.stream(stream):
             bs = BatchStep([sc.entry(r) for sc, r in zip(scs, batch)], s0.W, s0.H, sh_degree=s0.deg, nu=s0.nu,
                            tile=s0.tile, capacity=sum(sc.capacity for sc in scs), train=batch[0].kind == "train",
-                           cfg=s0.cfg, device=str(s0.device))
+                           cfg=s0.cfg, device=str(s0.device), pool=pool)
             bs.run(stream)
         return bs
 
@@ -272,7 +278,7 @@ class Server:
                     for j, r in enumerate(batch):
                         r.done = done
                         if keep_results and r.kind == "render":
-                            r.image = bs.images()[j]
+                            r.image = bs.images()[j].clone()  # the slot's buffers are reused
                     for r in batch:
                         busy.discard(r.scene)
                     used -= nb
@@ -328,7 +334,7 @@ class Server:
                 start = time.perf_counter() - t0
                 for q in batch:
                     q.nbytes, q.start, q.batch = nb, start, len(batch)
-                bs = self.start(batch, st)
+                bs = self.start(batch, st, self.pools[slot])
                 with torch.cuda.stream(st):
                     self.status_host[slot: slot + 1].copy_(bs.status, non_blocking=True)
                 ev = torch.cuda.Event()
