@@ -131,10 +131,11 @@ typedef struct gs_eps_schedule {
  *            rounded up (-inf: no pixel reaches 1/255; +inf: unbounded).
  *            Binning narrows the splat's tile square to that box, and the
  *            rasteriser skips the splat for an 8 x 8 pixel block outside it.
- *   tangent: NULL or V x n_pad x nu records of 12 floats (a splat's probes
- *            adjacent, so that the rasteriser stages them with one copy), the
- *            forward-mode derivative of (mx, my, A, B, C, opacity, r, g, b)
- *            along probe k */
+ *   tangent: NULL or V x n_pad x (1 + nu) records of 12 floats: for each
+ *            (view, splat) a copy of its record in rec, then its nu probe
+ *            tangent records, the forward-mode derivative of (mx, my, A, B, C,
+ *            opacity, r, g, b) along probe k (adjacent, so that the rasteriser
+ *            stages all of a splat's records with one copy) */
 typedef struct gs_projected {
   float* rec;
   float* tangent;

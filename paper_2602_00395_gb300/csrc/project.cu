@@ -39,8 +39,8 @@ __device__ __forceinline__ void store_culled(float4* rec, size_t at) {
 
 // Column i of the parameter matrix P (n Gaussians, row pitch n_pad) projected
 // into views cams[0..V): record v * pitch + i of rec, tangent records
-// (v * pitch + i) * NU + k of tan (a splat's probes adjacent); columns n <= i <
-// pitch are written culled.
+// (v * pitch + i) * (NU + 1) + 1 + k of tan, after a copy of the record at
+// (v * pitch + i) * (NU + 1); columns n <= i < pitch are written culled.
 // Called by every thread of a 128-thread block (the SH staging is block-wide).
 template <int DEG, int NU>
 __device__ __forceinline__ void project_column(const float* __restrict__ P, int n, int n_pad, int i, int pitch,
@@ -59,7 +59,8 @@ __device__ __forceinline__ void project_column(const float* __restrict__ P, int 
   if (i >= n) {
     for (int v = 0; v < V; ++v) {
       store_culled(rec, (size_t)v * pitch + i);
-      for (int k = 0; k < NU; ++k) store_culled(tan, ((size_t)v * pitch + i) * NU + k);
+      if (NU > 0)  // the record's copy and its tangents; no tangent array without probes
+        for (int k = 0; k <= NU; ++k) store_culled(tan, ((size_t)v * pitch + i) * (NU + 1) + k);
     }
     return;
   }
@@ -131,7 +132,8 @@ __device__ __forceinline__ void project_column(const float* __restrict__ P, int 
     S t2 = Rc[2][0] * mu0 + Rc[2][1] * mu1 + Rc[2][2] * mu2 + tc[2];
     if (!(val(t2) > c->near_plane)) {
       store_culled(rec, at);
-      for (int k = 0; k < NU; ++k) store_culled(tan, ((size_t)v * pitch + i) * NU + k);
+      if (NU > 0)  // the record's copy and its tangents; no tangent array without probes
+        for (int k = 0; k <= NU; ++k) store_culled(tan, ((size_t)v * pitch + i) * (NU + 1) + k);
       continue;
     }
     // camera-frame covariance Rc Sigma Rc^T
@@ -158,7 +160,8 @@ __device__ __forceinline__ void project_column(const float* __restrict__ P, int 
     const S det = a * cc - b * b;
     if (!(val(det) > 0.f)) {
       store_culled(rec, at);
-      for (int k = 0; k < NU; ++k) store_culled(tan, ((size_t)v * pitch + i) * NU + k);
+      if (NU > 0)  // the record's copy and its tangents; no tangent array without probes
+        for (int k = 0; k <= NU; ++k) store_culled(tan, ((size_t)v * pitch + i) * (NU + 1) + k);
       continue;
     }
     const S idet = 1.f / det;
@@ -204,9 +207,15 @@ __device__ __forceinline__ void project_column(const float* __restrict__ P, int 
     rec[3 * at + 2] = make_float4(val(rgb[2]), val(t2), __int_as_float(radius),
                                   __uint_as_float(footprint_extents(val(cA), val(cB), val(cC), val(opac))));
     if constexpr (NU > 0) {
+      // the record again, in front of its tangent records: the forward blend
+      // stages all of a splat's records with one copy
+      const size_t t0 = ((size_t)v * pitch + i) * (NU + 1);
+      tan[3 * t0 + 0] = rec[3 * at + 0];
+      tan[3 * t0 + 1] = rec[3 * at + 1];
+      tan[3 * t0 + 2] = rec[3 * at + 2];
 #pragma unroll
       for (int k = 0; k < NU; ++k) {
-        const size_t tk = ((size_t)v * pitch + i) * NU + k;
+        const size_t tk = ((size_t)v * pitch + i) * (NU + 1) + 1 + k;
         tan[3 * tk + 0] = make_float4(mx.d[k], my.d[k], cA.d[k], cB.d[k]);
         tan[3 * tk + 1] = make_float4(cC.d[k], opac.d[k], rgb[0].d[k], rgb[1].d[k]);
         tan[3 * tk + 2] = make_float4(rgb[2].d[k], 0.f, 0.f, 0.f);
@@ -235,7 +244,7 @@ __global__ void GS_PROJ_BOUNDS project_batch_kernel(BatchArg ba, int pitch, gs_f
   pa.t = ba.t[b];
   pa.t_dev = nullptr;
   project_column<DEG, NU>(ba.P[b], ba.n[b], ba.n_pad[b], i, pitch, ba.cam[b], 1, fr, pa,
-                          rec + 3 * (size_t)b * pitch, tan ? tan + 3 * (size_t)b * NU * pitch : nullptr);
+                          rec + 3 * (size_t)b * pitch, tan ? tan + 3 * (size_t)b * (NU + 1) * pitch : nullptr);
 }
 
 template <int DEG, int NU>

@@ -78,13 +78,14 @@ __device__ __forceinline__ bool footprint_meets_block(const Rec& r, float x0, fl
 }
 
 // Stage batch b of a tile list (records [b * batch, b * batch + batch)) into
-// buffer (b & 1): one bulk copy per record and one for its NT adjacent probe
-// tangent records (staged as [batch][NT]), issued by the block's threads in
-// turn, all completing on the buffer's mbarrier.
+// buffer (b & 1): one bulk copy per splat, of its record alone (NT = 0, from
+// rec) or of its record and NT probe tangent records (from tan, where they are
+// adjacent; staged as [batch][1 + NT]), issued by the block's threads in turn,
+// all completing on the buffer's mbarrier.
 template <int NT>
 __device__ __forceinline__ void stage_batch(int b, int batch, uint32_t start, int n, int view, int n_pad,
                                             const uint32_t* __restrict__ vals, const float4* __restrict__ rec,
-                                            const float4* __restrict__ tan, Rec* buf, Rec* tbuf, uint32_t* s_idx,
+                                            const float4* __restrict__ tan, Rec* buf, uint32_t* s_idx,
                                             uint64_t* bars) {
   const int bi = b & 1;
   const int cnt = min(batch, n - b * batch);
@@ -93,9 +94,11 @@ __device__ __forceinline__ void stage_batch(int b, int batch, uint32_t start, in
   for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
     const uint32_t gi = vals[start + (uint32_t)(b * batch + q)];
     if (s_idx) s_idx[bi * batch + q] = gi;
-    bulk_g2s(&buf[bi * batch + q], rec + 3 * ((size_t)view * n_pad + gi), sizeof(Rec), &bars[bi]);
-    if (NT > 0)  // the splat's NT probe tangent records are adjacent: one copy
-      bulk_g2s(&tbuf[(bi * batch + q) * NT], tan + 3 * ((size_t)view * n_pad + gi) * NT, NT * sizeof(Rec), &bars[bi]);
+    if (NT > 0)  // the record and its NT probe tangent records, adjacent in tan: one copy
+      bulk_g2s(&buf[((size_t)bi * batch + q) * (1 + NT)], tan + 3 * ((size_t)view * n_pad + gi) * (1 + NT),
+               (1 + NT) * sizeof(Rec), &bars[bi]);
+    else
+      bulk_g2s(&buf[bi * batch + q], rec + 3 * ((size_t)view * n_pad + gi), sizeof(Rec), &bars[bi]);
   }
 }
 
@@ -240,16 +243,18 @@ __device__ __forceinline__ void fwd_apply(FwdPixel<NU>& p, const Rec& r, const R
 template <int NT>
 __device__ __forceinline__ void stage_batch_one(int b, int batch, int n, int view, int n_pad, uint32_t gi,
                                                 const float4* __restrict__ rec, const float4* __restrict__ tan,
-                                                Rec* buf, Rec* tbuf, uint64_t* bars) {
+                                                Rec* buf, uint64_t* bars) {
   const int bi = b & 1;
   const int cnt = min(batch, n - b * batch);
   if (threadIdx.x == 0) mbar_arrive_expect_tx(&bars[bi], (uint32_t)(cnt * (int)sizeof(Rec) * (1 + NT)));
   fence_proxy_async();
   const int q = threadIdx.x;
   if (q < cnt) {
-    bulk_g2s(&buf[bi * batch + q], rec + 3 * ((size_t)view * n_pad + gi), sizeof(Rec), &bars[bi]);
-    if (NT > 0)  // the splat's NT probe tangent records are adjacent: one copy
-      bulk_g2s(&tbuf[(bi * batch + q) * NT], tan + 3 * ((size_t)view * n_pad + gi) * NT, NT * sizeof(Rec), &bars[bi]);
+    if (NT > 0)  // the record and its NT probe tangent records, adjacent in tan: one copy
+      bulk_g2s(&buf[((size_t)bi * batch + q) * (1 + NT)], tan + 3 * ((size_t)view * n_pad + gi) * (1 + NT),
+               (1 + NT) * sizeof(Rec), &bars[bi]);
+    else
+      bulk_g2s(&buf[bi * batch + q], rec + 3 * ((size_t)view * n_pad + gi), sizeof(Rec), &bars[bi]);
   }
 }
 
@@ -267,8 +272,7 @@ __global__ void GS_FWD_BOUNDS raster_fwd_kernel(const float4* __restrict__ rec, 
   const int nthr = blockDim.x, nwarps = nthr >> 5, batch = CB ? fr.batch : kBatchPerThread * nthr / kFwdBatchDiv;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
   Rec* buf = reinterpret_cast<Rec*>(smem + 16);
-  Rec* tbuf = buf + 2 * batch;
-  uint32_t* s_mask = reinterpret_cast<uint32_t*>(tbuf + 2 * NU * batch);
+  uint32_t* s_mask = reinterpret_cast<uint32_t*>(buf + 2 * (1 + NU) * batch);  // after both buffers
   const int tid = threadIdx.x, lane = tid & 31;
   const uint32_t wbit = 1u << (tid >> 5);
   // the tile of this block: the heaviest tiles first when an order is given
@@ -316,35 +320,38 @@ __global__ void GS_FWD_BOUNDS raster_fwd_kernel(const float4* __restrict__ rec, 
   uint32_t gi_next = 0;
   if (nb > 0) {
     if (one) {
-      stage_batch_one<NU>(0, batch, n, view, n_pad, index_of(0), rec, tan, buf, tbuf, bars);
+      stage_batch_one<NU>(0, batch, n, view, n_pad, index_of(0), rec, tan, buf, bars);
       gi_next = index_of(1);
     } else {
-      stage_batch<NU>(0, batch, start, n, view, n_pad, vals, rec, tan, buf, tbuf, nullptr, bars);
+      stage_batch<NU>(0, batch, start, n, view, n_pad, vals, rec, tan, buf, nullptr, bars);
     }
     issued = 1;
   }
   for (int b = 0; b < nb; ++b) {
     if (b + 1 < nb) {
       if (one) {
-        stage_batch_one<NU>(b + 1, batch, n, view, n_pad, gi_next, rec, tan, buf, tbuf, bars);
+        stage_batch_one<NU>(b + 1, batch, n, view, n_pad, gi_next, rec, tan, buf, bars);
         gi_next = index_of(b + 2);
       } else {
-        stage_batch<NU>(b + 1, batch, start, n, view, n_pad, vals, rec, tan, buf, tbuf, nullptr, bars);
+        stage_batch<NU>(b + 1, batch, start, n, view, n_pad, vals, rec, tan, buf, nullptr, bars);
       }
       issued = b + 2;
     }
     const int bi = b & 1;
     const bool ok = mbar_wait_bounded(&bars[bi], (uint32_t)((b >> 1) & 1), status);
     const int cnt = min(batch, n - b * batch);
-    Rec* bb = buf + bi * batch;
+    // record q of the batch; its probe tangent records follow it (NU > 0)
+    auto recp = [&](int q) -> Rec* {
+      return NU > 0 ? &buf[((size_t)bi * batch + q) * (1 + NU)] : &buf[bi * batch + q];
+    };
     // per splat: which warps it can reach, and the probe tangents of its power
     // rewritten as the quadratic form pd = dx (a dx + b dy + d) + dy (c dy + e)
     for (int q = tid; q < cnt; q += nthr) {
-      const Rec r = bb[q];
+      const Rec r = *recp(q);
       s_mask[q] = ok ? warp_block_mask(r, tile_x0, tile_y0, fr.tile_w, nwarps) : 0u;
 #pragma unroll
       for (int k = 0; k < NU; ++k) {
-        Rec* tp = &tbuf[(bi * batch + q) * NU + k];
+        Rec* tp = recp(q) + 1 + k;
         const float4 ta = tp->a;  // dmx, dmy, dA, dB
         const float dC = tp->b.x;
         tp->a = make_float4(-0.5f * ta.z, -ta.w, -0.5f * dC, -(r.a.z * ta.x + r.a.w * ta.y));
@@ -364,8 +371,8 @@ __global__ void GS_FWD_BOUNDS raster_fwd_kernel(const float4* __restrict__ rec, 
       while (bits) {
         const int j = j0 + __ffs(bits) - 1;
         bits &= bits - 1;
-        const Rec r = bb[j];
-        const Rec* t0 = tbuf + ((size_t)bi * batch + j) * NU;
+        const Rec r = *recp(j);
+        const Rec* t0 = recp(j) + 1;
         const uint32_t pos = (uint32_t)(b * batch + j);
         float dx[kPixPerThread], dy[kPixPerThread], G[kPixPerThread], oG[kPixPerThread], al[kPixPerThread];
         bool on[kPixPerThread];

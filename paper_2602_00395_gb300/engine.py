@@ -91,7 +91,7 @@ class TRStep:
         self.hz = w(self.rows, self.n_pad) if nu > 0 else None
         self.cams = (torch.zeros if zero_init else torch.empty)(96 * n_views, dtype=torch.uint8, device=self.device)
         self.rec = w(n_views * self.n_pad * 12)
-        self.tan = w(nu * n_views * self.n_pad * 12 if nu > 0 else 4)
+        self.tan = w((1 + nu) * n_views * self.n_pad * 12 if nu > 0 else 4)  # each record again, then its probes
         HW = width * height
         self.image = w(n_views * 3 * HW)
         self.final_T = w(n_views * HW)
@@ -424,7 +424,7 @@ class BatchStep:
         buf = self._buf
         HW, B = width * height, self.B
         self.rec = buf("rec", B * self.n_pad * 12, f32)
-        self.tan = buf("tan", self.nu * B * self.n_pad * 12 if self.nu else 4, f32)
+        self.tan = buf("tan", (1 + self.nu) * B * self.n_pad * 12 if self.nu else 4, f32)
         self.image = buf("image", B * 3 * HW, f32)
         self.final_T = buf("final_T", B * HW, f32)
         self.n_contrib = buf("n_contrib", B * HW, i32)
@@ -466,7 +466,8 @@ class BatchStep:
         nu = nu if train else 0
         frame = G.frame_struct(B, width, height, *tile)
         Tx, Ty = -(-width // tile[0]), -(-height // tile[1])
-        b = B * n_pad * 48 * (1 + nu) + B * HW * 4 * (3 + 1 + 1 + 3 * nu) + B * Tx * Ty * 12 + capacity * 8
+        b = B * n_pad * 48 * (1 + (1 + nu if nu else 0)) + B * HW * 4 * (3 + 1 + 1 + 3 * nu) + B * Tx * Ty * 12
+        b += capacity * 8
         b += G.gs_bin_sort_workspace_size(n_pad, frame, capacity) + 96 * B
         if train:
             b += B * HW * 12 + G.gs_raster_bwd_workspace_size(n_pad, frame, nu)

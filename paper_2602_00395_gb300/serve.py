@@ -118,9 +118,9 @@ class Scene:
         n_pad, rows, HW, V = synth.pad_count(self.n), synth.n_rows(self.deg), self.W * self.H, n_views
         frame = G.frame_struct(V, self.W, self.H, *self.tile)
         cap = self.capacity * V
-        b = V * n_pad * 12 * 4 * (1 + max(self.nu, 1))                   # records + tangents
+        b = V * n_pad * 12 * 4 * (2 + max(self.nu, 1))                   # records, their copies + tangents
         b += V * HW * 4 * (3 + 1 + 1 + 3 * max(self.nu, 1) + 3)          # image, T, n_contrib, tangents, target slot
-        b += cap * 12 + G.gs_bin_sort_workspace_size(n_pad, frame, cap)
+        b += cap * 8 + G.gs_bin_sort_workspace_size(n_pad, frame, cap)
         b += G.gs_raster_bwd_workspace_size(n_pad, frame, self.nu) + 2 * rows * n_pad * 4  # cotangents, grad, hz
         return int(b)
 

@@ -82,7 +82,7 @@ def test_project_matches_oracle(case):
     e.project(t, probes=True)
     torch.cuda.synchronize()
     rec = _records(e)
-    tan = e.tan.view(e.V, e.n_pad, e.nu, 12).cpu().numpy()  # a splat's probes adjacent
+    tan = e.tan.view(e.V, e.n_pad, 1 + e.nu, 12).cpu().numpy()  # the record again, then its probes
     P = O.params64(sc)
     fields = [("mx", 0), ("my", 1), ("A", 2), ("B", 3), ("C", 4), ("o", 5), ("r", 6), ("g", 7), ("b", 8),
               ("depth", 9)]
@@ -98,10 +98,12 @@ def test_project_matches_oracle(case):
             r = ref[name][valid]
             scale = np.abs(r).max()
             np.testing.assert_allclose(g, r, rtol=2e-5, atol=2e-6 * scale, err_msg=name)
+        # slot 0 of every (view, splat) in the tangent array is its record, bit for bit
+        assert np.array_equal(tan[v, :, 0, :].view(np.uint32), rec[v].view(np.uint32))
         for k in range(e.nu):
             z = O.probe_matrix(42, t, k, e.rows, sc.n)
             rt = O.project_tangent(P, sc.sh_degree, cam, z)[valid]
-            gt = tan[v, : sc.n, k, :9][valid]
+            gt = tan[v, : sc.n, 1 + k, :9][valid]
             for q in range(9):
                 scale = np.abs(rt[:, q]).max()
                 assert np.abs(gt[:, q] - rt[:, q]).max() <= 1e-4 * scale + 1e-7, (k, q)
