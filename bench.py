@@ -599,13 +599,13 @@ def raster_bwd_flops_per_unit() -> int:
 RASTER_BWD_TRAFFIC = {
     # one-kernel captures (dram__bytes_read.sum + dram__bytes_write.sum) of the
     # reverse call's two kernels on the 2-view case of the bench scene
-    "blend_bytes": 383_836_928 + 51_809_280,        # raster_bwd_kernel
-    "projection_bytes": 460_286_208 + 448_760_064,  # project_bwd_kernel
+    "blend_bytes": 375_577_600 + 42_197_248,        # raster_bwd_kernel
+    "projection_bytes": 460_133_120 + 448_687_616,  # project_bwd_kernel
     "pairs": 12_223_264,                            # pairs blended in that launch
     "n": 1_000_000,
     "views": 2,
     "sources": {
-        "paper_2602_00395_gb300/csrc/raster.cu": "d608bbe5f2a4d504848ebdeecc62a9481f20c9b01cd1aa5fe1b980d4f58e24bf",
+        "paper_2602_00395_gb300/csrc/raster.cu": "2f05b88b8dc9d3f15d90ea7871e3725300e790b10194276d0659fb239968e024",
         "paper_2602_00395_gb300/csrc/common.cuh": "b7201d9f818a49a1c40435b69f8e6e4e3d70dc9d7b4428d641c067699f5e6429",
     },
 }
