@@ -73,7 +73,7 @@ def lib():
             L.or_adam_tr_update.argtypes = [P, P, P, P, i64, i64, i32, P, P, C.c_int64, d, P]
             L.or_project_tangent.argtypes = [P, i64, i64, i32, P, P, P]
             L.or_render_pixels.argtypes = [P, i64, i64, i32, P, i32, i32, i64, P, P, u64, C.c_int64, i32, P, P, P,
-                                           P, P, P, P, P, P]
+                                           P, P, P, P, P, P, i32, d, P, P, P, P, P, P]
             L.or_backward_sampled.argtypes = [P, i64, i64, i32, P, i32, i32, i32, P, i32, d, u64, C.c_int64, i32,
                                               i64, P, P, P, P, d, P, P, P, P, P, P, P]
             L.or_signature.argtypes = [P, i64, i64, i32, P, i32, i32, i32, P]
@@ -396,9 +396,16 @@ def adam_tr_update(x, m, v, grad, deg: int, t: int, eps: float, cfg=None, adam=N
 
 # ------------------------------------------------------------- sampled outputs
 def render_pixels(P: np.ndarray, deg: int, cam, xs, ys, *, seed: int = 42, t: int = 1, nu: int = 0,
-                  tw: int = 16, th: int = 16):
+                  tw: int = 16, th: int = 16, outcomes: int = 0, branch_min: float = 1e-7):
     """Colour, T, n_contrib (and the range the tile sets within rounding allow),
-    margin and (nu > 0) image tangents at chosen pixels of one view."""
+    margin and (nu > 0) image tangents at chosen pixels of one view.
+
+    outcomes > 0: also every result an FP32 blend may reach when the decisions
+    within rounding of their thresholds go either way (at most `outcomes` per
+    pixel; flips whose bound is at most branch_min are summed instead):
+    n_leaves (-1 where there are more), leaf_rgb (k x outcomes x 3), leaf_T,
+    leaf_jz (k x outcomes x nu x 3), rest / t_rest (the largest summed bounds).
+    The FP64 result is the last leaf of each pixel."""
     P = _f64(P)
     rows, n = P.shape
     xs = np.ascontiguousarray(xs, np.int32)
@@ -413,10 +420,49 @@ def render_pixels(P: np.ndarray, deg: int, cam, xs, ys, *, seed: int = 42, t: in
     imp = np.zeros(k)
     timp = np.zeros(k)
     kinds = np.zeros(k, np.int32)
+    L = max(int(outcomes), 1)
+    nl = np.zeros(k, np.int32)
+    lrgb = np.zeros((k, L, 3))
+    lT = np.zeros((k, L))
+    ljz = np.zeros((k, L, max(nu, 1), 3))
+    rest = np.zeros(k)
+    trest = np.zeros(k)
+    want = outcomes > 0
     lib().or_render_pixels(_p(P), n, n, deg, _p(camera_array([cam])), tw, th, k, _p(xs), _p(ys), seed, t, nu,
-                           _p(rgb), _p(T), _p(nc), _p(mg), _p(jz), _p(rng), _p(imp), _p(timp), _p(kinds))
-    return dict(rgb=rgb, final_T=T, n_contrib=nc, margin=mg, jz=jz[:, :nu], n_contrib_lo=rng[:, 0],
-                n_contrib_hi=rng[:, 1], impact=imp, t_impact=timp, flip_kinds=kinds)
+                           _p(rgb), _p(T), _p(nc), _p(mg), _p(jz), _p(rng), _p(imp), _p(timp), _p(kinds), L,
+                           float(branch_min), _p(nl) if want else None, _p(lrgb), _p(lT), _p(ljz), _p(rest),
+                           _p(trest))
+    out = dict(rgb=rgb, final_T=T, n_contrib=nc, margin=mg, jz=jz[:, :nu], n_contrib_lo=rng[:, 0],
+               n_contrib_hi=rng[:, 1], impact=imp, t_impact=timp, flip_kinds=kinds)
+    if want:
+        out.update(n_leaves=nl, leaf_rgb=lrgb, leaf_T=lT, leaf_jz=ljz[:, :, :nu], rest=rest, t_rest=trest)
+    return out
+
+
+def match_outcomes(ref: dict, rgb, final_T, jz=None, *, img_tol: float = 1e-5, jz_tol=None,
+                   flip_max: float = 5e-6):
+    """Which sampled pixels of an FP32 evaluation equal one of the oracle's
+    outcomes (render_pixels with outcomes > 0).
+
+    rgb (k x 3), final_T (k), jz (k x nu x 3, optional, with jz_tol a bound per
+    probe).  A pixel is resolved when its outcomes are complete and the flips
+    summed instead of enumerated are bounded by flip_max (colour and T); it
+    matches when one outcome is within img_tol in colour and T (and jz_tol in
+    the tangents).  Returns (resolved, matched, leaf): leaf is the index of the
+    first matching outcome, -1 where none; the FP64 result is the last one."""
+    nl = ref["n_leaves"]
+    resolved = (nl > 0) & (ref["rest"] <= flip_max) & (ref["t_rest"] <= flip_max)
+    k, L = ref["leaf_T"].shape
+    valid = np.arange(L)[None, :] < nl[:, None]
+    ok = np.abs(ref["leaf_rgb"] - np.asarray(rgb)[:, None, :]).max(axis=2) <= img_tol
+    ok &= np.abs(ref["leaf_T"] - np.asarray(final_T)[:, None]) <= img_tol
+    if jz is not None:
+        tol = np.broadcast_to(np.asarray(jz_tol, np.float64), (ref["leaf_jz"].shape[2],))
+        ok &= (np.abs(ref["leaf_jz"] - np.asarray(jz)[:, None]) <= tol[None, None, :, None]).all(axis=(2, 3))
+    ok &= valid
+    matched = ok.any(axis=1)
+    leaf = np.where(matched, ok.argmax(axis=1), -1)
+    return resolved, matched, leaf
 
 
 def backward_sampled(P: np.ndarray, deg: int, cams, target: np.ndarray, samples, *, loss_kind: int = 0,

@@ -29,6 +29,7 @@
 #include <cstdint>
 #include <cstring>
 #include <limits>
+#include <map>
 #include <vector>
 
 namespace {
@@ -973,6 +974,190 @@ Flip blend_flips(const View& V, size_t tile, double pcx, double pcy, int nc, std
 
 // The tolerance the CUDA path's images are held to (max-abs): residuals of the
 // two sides differ by at most this where the images are compared.
+// Every result of the blend at one pixel that an FP32 evaluation may reach, as
+// the sequences of splats blended, front to back.  The walk takes the tile's
+// list with the possibly-present splats merged in by key (as blend_flips) and
+// takes every decision as FP64 does, except that each decision blend_flips
+// counts as possibly flipped is taken both ways: a splat that may be skipped or
+// blended (its 1/255 skip or its power sign within the rounding bound of
+// power_uncertainty, or its membership in the tile's list ambiguous), a
+// termination within the transmittance's rounding of 1e-4, and the order of two
+// splats that may blend whose FP32 depths are a few ulps apart.  A flip whose
+// bound on the colour and on T (as in blend_flips) is at most branch_min is not
+// taken both ways: its bound is summed along the path instead, and its relative
+// change of T widens later termination tests.  The FP64 walk's own sequence is
+// the last leaf.  rest / t_rest receive the largest sums over the leaves.
+// Returns false (leaves incomplete) when there would be more than max_leaves.
+struct BlendOutcomes {
+  const View& V;
+  double pcx, pcy, cmax, branch_min;
+  size_t max_leaves;
+  struct Entry {
+    int i;
+    bool in_list, maybe;
+    float depth;
+  };
+  std::vector<Entry> E;
+  std::vector<std::vector<int>> leaves;
+  double rest = 0.0, t_rest = 0.0;
+  bool overflow = false;
+
+  BlendOutcomes(const View& V_, size_t tile, double x, double y, double bmin, size_t maxl)
+      : V(V_), pcx(x), pcy(y), cmax(V_.tile_cmax[tile]), branch_min(bmin), max_leaves(maxl) {
+    const std::vector<int>& list = V.lists[tile];
+    const std::vector<int>& maybe = V.amb[tile];
+    const std::vector<int>& extra = V.amb_extra[tile];
+    size_t li = 0, ei = 0;
+    while (li < list.size() || ei < extra.size()) {
+      bool take_extra = ei < extra.size();
+      if (take_extra && li < list.size()) {
+        const float da = (float)V.sp[extra[ei]].depth, dl = (float)V.sp[list[li]].depth;
+        take_extra = da < dl || (da == dl && extra[ei] < list[li]);
+      }
+      const int i = take_extra ? extra[ei++] : list[li++];
+      const bool amb = !take_extra && std::find(maybe.begin(), maybe.end(), i) != maybe.end();
+      E.push_back({i, !take_extra, amb, (float)V.sp[i].depth});
+    }
+  }
+
+  struct Eval {
+    double a, dp, drop;
+    bool capped, blends, near;
+  };
+  Eval eval(int i, double T) const {
+    const Splat<double>& g = V.sp[i];
+    const double dx = g.mx - pcx, dy = g.my - pcy;
+    const double power = -0.5 * (g.A * dx * dx + g.C * dy * dy) - g.B * dx * dy;
+    Eval r;
+    r.dp = power_uncertainty(g, dx, dy);
+    const double oG = g.o * std::exp(std::min(power, 0.0));
+    r.capped = oG > kAlphaMax;
+    r.a = r.capped ? kAlphaMax : oG;
+    r.blends = power <= 0.0 && r.a >= kAlphaMin;
+    r.near = std::fabs(power) <= r.dp || (!r.capped && std::fabs(r.a / kAlphaMin - 1.0) <= r.dp + 2e-6);
+    const double ci = std::max({g.rgb[0], g.rgb[1], g.rgb[2], 0.0});
+    r.drop = r.a * T * (ci + cmax);
+    return r;
+  }
+  // may the entry blend at this pixel on either side
+  bool may_blend(const Entry& e, const Eval& r) const { return r.blends || r.near; }
+
+  void leaf(const std::vector<int>& seq, double rs, double trs) {
+    if (leaves.size() >= max_leaves) {
+      overflow = true;
+      return;
+    }
+    leaves.push_back(seq);
+    rest = std::max(rest, rs);
+    t_rest = std::max(t_rest, trs);
+  }
+
+  // From entry p on, with transmittance T, its accumulated relative rounding
+  // tun, the relative change rho that unbranched flips may make to it, and the
+  // sums of unbranched bounds rs / trs.  no_swap: entry p is the later splat of a
+  // pair already swapped.
+  void walk(size_t p, std::vector<int> seq, double T, double tun, double rho, double rs, double trs, bool no_swap) {
+    for (; p < E.size() && !overflow; ++p, no_swap = false) {
+      Eval r = eval(E[p].i, T);
+      if (!no_swap && may_blend(E[p], r)) {
+        // the next splat that may blend: if its depth is within a few ulps, the
+        // GPU's keys may put it first
+        size_t q = p + 1;
+        Eval rq{};
+        for (; q < E.size(); ++q) {
+          rq = eval(E[q].i, T);
+          if (may_blend(E[q], rq)) break;
+        }
+        const double d0 = E[p].depth;
+        if (q < E.size() && std::fabs((double)E[q].depth - d0) <= 4.0 * std::ldexp(std::fabs(d0), -23)) {
+          double dc = 0.0;
+          for (int ch = 0; ch < 3; ++ch) dc = std::max(dc, std::fabs(V.sp[E[p].i].rgb[ch] - V.sp[E[q].i].rgb[ch]));
+          const double sw = T * r.a * rq.a * dc;
+          if (sw > branch_min) {
+            std::swap(E[p], E[q]);
+            walk(p, seq, T, tun, rho, rs, trs, true);
+            std::swap(E[p], E[q]);
+            if (overflow) return;
+          } else {
+            rs += sw;
+          }
+        }
+      }
+      const Entry& e = E[p];
+      const bool fp64_blend = e.in_list && r.blends;
+      const bool alt = fp64_blend ? (r.near || e.maybe) : (e.in_list ? r.near : (r.blends || r.near));
+      const bool small = r.drop <= branch_min && r.a * T <= branch_min;
+      if (alt && small) {  // summed, not taken both ways
+        rs += r.drop;
+        trs += r.a * T;
+        rho += r.a / (1.0 - r.a);
+      }
+      const bool try_blend = fp64_blend || (alt && !small);
+      const bool try_skip = !fp64_blend || (alt && !small);
+      if (try_blend) {
+        const double Tn = T * (1.0 - r.a);
+        const double da = r.capped ? 0.0 : (r.dp + 2e-6) * r.a / (1.0 - r.a);
+        const bool near_term = std::fabs(Tn / kTMin - 1.0) <= tun + rho + da + 1e-6;
+        const bool stop64 = Tn < kTMin;
+        const bool term_small = T * cmax <= branch_min && T <= branch_min;
+        if (near_term && term_small) {
+          rs += T * cmax;
+          trs += T;
+        }
+        const bool both = near_term && !term_small;
+        const double tun_n = tun + (r.capped ? 0.0 : (r.dp + 2e-6) * r.a / (1.0 - r.a)) + 2e-7;
+        // the outcomes of blending it: stop in front of it, or blend and go on
+        const bool may_stop = stop64 || both, may_go = !stop64 || both;
+        if (fp64_blend) {
+          // the FP64 outcome is followed in this loop; the others first
+          if (try_skip) walk(p + 1, seq, T, tun, rho, rs, trs, false);
+          if (stop64) {
+            if (may_go) {
+              std::vector<int> s2 = seq;
+              s2.push_back(e.i);
+              walk(p + 1, s2, Tn, tun_n, rho, rs, trs, false);
+            }
+            leaf(seq, rs, trs);
+            return;
+          }
+          if (may_stop) leaf(seq, rs, trs);
+          seq.push_back(e.i);
+          T = Tn;
+          tun = tun_n;
+          continue;
+        }
+        // FP64 skips it: the blended alternatives first
+        if (may_stop) leaf(seq, rs, trs);
+        if (may_go) {
+          std::vector<int> s2 = seq;
+          s2.push_back(e.i);
+          walk(p + 1, s2, Tn, tun_n, rho, rs, trs, false);
+        }
+      }
+      // skipped (FP64's outcome when it does not blend)
+    }
+    if (!overflow) leaf(seq, rs, trs);
+  }
+};
+
+// The blend of one pixel over a given sequence of splats (every one blended, in
+// order): C = sum_k c_k a_k T_k with a_k = min(0.99, o_k G_k) (Sec. 3.1).  get(i)
+// returns splat i.
+template <class S, class Get>
+void blend_sequence(const std::vector<int>& seq, Get get, double pcx, double pcy, S C[3], S& T) {
+  T = S(1.0);
+  C[0] = C[1] = C[2] = S(0.0);
+  for (int i : seq) {
+    const Splat<S>& g = get(i);
+    S dx = g.mx - S(pcx), dy = g.my - S(pcy);
+    S power = -0.5 * (g.A * dx * dx + g.C * dy * dy) - g.B * dx * dy;
+    S oG = g.o * exp(power);
+    S alpha = val(oG) > kAlphaMax ? S(kAlphaMax) : oG;
+    for (int ch = 0; ch < 3; ++ch) C[ch] = C[ch] + g.rgb[ch] * alpha * T;
+    T = T * (1.0 - alpha);
+  }
+}
+
 const double kImageTol = 1e-5;
 
 // Calls f(tx, ty, x, y) for every pixel of the view, tile by tile.
@@ -2038,10 +2223,17 @@ std::vector<Splat<Dual>> tile_tangents(const View& V, const std::vector<int>& li
 // Sampled pixels of one view (coordinates xs, ys): colour (npix x 3), final T,
 // n_contrib, the decision margin and n_contrib range as in or_render, and, if
 // nu > 0, the image tangents J z_k (npix x nu x 3) for the probes of (seed, t).
+// With n_leaves given, also the outcomes of BlendOutcomes (at most max_leaves
+// per pixel, flips with bounds up to branch_min summed instead): their count
+// (-1 when there are more), colour (npix x max_leaves x 3), final T (npix x
+// max_leaves), image tangents (npix x max_leaves x nu x 3, if nu > 0) and the
+// sums rest / t_rest.
 void or_render_pixels(const double* P, long pitch, long n, int deg, const double* cam24, int tw, int th, long npix,
                       const int32_t* xs, const int32_t* ys, uint64_t seed, int64_t t, int nu, double* rgb,
                       double* T_out, int32_t* nc_out, double* margin, double* jz, int32_t* nc_range,
-                      double* impact, double* t_impact, int32_t* flip_kinds) {
+                      double* impact, double* t_impact, int32_t* flip_kinds, int max_leaves, double branch_min,
+                      int32_t* n_leaves, double* leaf_rgb, double* leaf_T, double* leaf_jz, double* rest,
+                      double* t_rest) {
   View V = build_view(P, pitch, n, deg, cam24, tw, th);
   std::vector<int> local;
   for (long q = 0; q < npix; ++q) {
@@ -2066,6 +2258,38 @@ void or_render_pixels(const double* P, long pitch, long n, int deg, const double
     if (nc_range) {
       nc_range[2 * q] = lo;
       nc_range[2 * q + 1] = hi;
+    }
+    if (n_leaves) {
+      BlendOutcomes bo(V, (size_t)ty * V.Tx + tx, x + 0.5, y + 0.5, branch_min, (size_t)max_leaves);
+      bo.walk(0, {}, 1.0, 0.0, 0.0, 0.0, 0.0, false);
+      n_leaves[q] = bo.overflow ? -1 : (int)bo.leaves.size();
+      rest[q] = bo.rest;
+      t_rest[q] = bo.t_rest;
+      if (!bo.overflow) {
+        const int rows = n_rows(deg);
+        for (size_t l = 0; l < bo.leaves.size(); ++l) {
+          double C[3], T;
+          blend_sequence<double>(bo.leaves[l], [&](int i) -> const Splat<double>& { return V.sp[i]; }, x + 0.5,
+                                 y + 0.5, C, T);
+          for (int ch = 0; ch < 3; ++ch) leaf_rgb[((size_t)q * max_leaves + l) * 3 + ch] = C[ch];
+          leaf_T[(size_t)q * max_leaves + l] = T;
+        }
+        std::vector<double> tan(rows);
+        for (int k = 0; k < nu; ++k) {
+          std::map<int, Splat<Dual>> sd;  // the splats of the leaves, forward mode along probe k
+          auto get = [&](int i) -> const Splat<Dual>& {
+            auto it = sd.find(i);
+            if (it != sd.end()) return it->second;
+            for (int r = 0; r < rows; ++r) tan[r] = rademacher(seed, t, k, probe_entry(i, r, rows));
+            return sd.emplace(i, project(load_gaussian<Dual>(P, pitch, i, deg, tan.data()), V.cam)).first->second;
+          };
+          for (size_t l = 0; l < bo.leaves.size(); ++l) {
+            Dual Cd[3], Td;
+            blend_sequence<Dual>(bo.leaves[l], get, x + 0.5, y + 0.5, Cd, Td);
+            for (int ch = 0; ch < 3; ++ch) leaf_jz[(((size_t)q * max_leaves + l) * nu + k) * 3 + ch] = Cd[ch].d;
+          }
+        }
+      }
     }
     if (nu > 0) {
       local.resize(list.size());

@@ -87,13 +87,14 @@ def test_sampled_pixels_match_oracle(large):
     xs = rng.integers(0, W, 256)
     ys = rng.integers(0, H, 256)
     with O.footprint_bins():  # the engine's default binning
-        ref = O.render_pixels(P, DEG, f["cam"], xs, ys)
-    ok = (ref["impact"] <= 5e-6) & (ref["t_impact"] <= 5e-6)
-    print(f"\nlarge scene: {int((~ok).sum())} of {len(xs)} sampled pixels excluded by the flip bound")
-    assert ok.mean() >= 0.95
+        ref = O.render_pixels(P, DEG, f["cam"], xs, ys, outcomes=64)
+    # each pixel equals one of the results the blend reaches when the decisions
+    # FP32 may flip go either way
     img = f["img"][:, ys, xs].T
-    assert np.abs(img - ref["rgb"])[ok].max() <= 1e-5
-    assert np.abs(f["final_T"][ys, xs] - ref["final_T"])[ok].max() <= 1e-5
+    ok, matched, _ = O.match_outcomes(ref, img, f["final_T"][ys, xs], img_tol=1e-5, flip_max=5e-6)
+    print(f"\nlarge scene: {int((~ok).sum())} of {len(xs)} sampled pixels unresolved")
+    assert ok.mean() >= 0.99
+    assert np.all(matched[ok])
     nc = f["n_contrib"][ys, xs]
     assert np.all(((nc >= ref["n_contrib_lo"]) & (nc <= ref["n_contrib_hi"]))[ok])
 

@@ -252,7 +252,24 @@ def _render_compare(sc, cams, tile=(16, 16), box=True, batch=0):
     T = e.final_T.view(V, H, W).cpu().numpy()
     nc = e.n_contrib.view(V, H, W).cpu().numpy()
     ok = (ref["impact"] <= 5e-6) & (ref["t_impact"] <= 5e-6)
-    return e, ref, img, T, nc, ok
+    # a pixel where a decision FP32 may flip could move the value by more than
+    # half the tolerance must equal one of the results the blend reaches when
+    # those decisions go either way; it is left out only where they are not
+    # resolved (more than 64, or small flips summing past half the tolerance)
+    unresolved = np.zeros_like(ok)
+    for v in range(V):
+        ys, xs = np.nonzero(~ok[v])
+        if len(xs) == 0:
+            continue
+        with O.footprint_bins(box):
+            px = O.render_pixels(O.params64(sc), sc.sh_degree, cams[v], xs, ys, tw=tile[0], th=tile[1],
+                                 outcomes=64)
+        res, matched, _ = O.match_outcomes(px, img[v][:, ys, xs].T, T[v][ys, xs], img_tol=1e-5, flip_max=5e-6)
+        assert np.all(matched[res]), [(int(xs[q]), int(ys[q])) for q in np.nonzero(res & ~matched)[0][:8]]
+        in_range = (nc[v][ys, xs] >= px["n_contrib_lo"]) & (nc[v][ys, xs] <= px["n_contrib_hi"])
+        assert np.all(in_range[res])
+        unresolved[v][ys[~res], xs[~res]] = True
+    return e, ref, img, T, nc, ok, unresolved
 
 
 @pytest.mark.parametrize("case,tile,box,batch", [("cfg1", (16, 16), True, 0), ("cfg1", (16, 16), False, 0),
@@ -264,13 +281,13 @@ def test_raster_fwd_matches_oracle(case, tile, box, batch):
     the footprint (box True) or by the whole 3DGS tile square, with the default
     and other per-block record batches."""
     sc, cams = _cfg1() if case == "cfg1" else _ragged()
-    e, ref, img, T, nc, ok = _render_compare(sc, cams, tile, box, batch)
+    e, ref, img, T, nc, ok, unresolved = _render_compare(sc, cams, tile, box, batch)
     assert int(e.n_pairs.item()) == ref["n_pairs"] or (~ok).any()
-    # pixels where a decision FP32 may flip could move the value by more than
-    # half the tolerance (the oracle's flip bound)
-    excluded = 1.0 - ok.mean()
-    print(f"\n{case} {tile} box={box} batch={batch}: {excluded:.3%} of pixels excluded by the flip bound")
-    assert excluded < 0.05, excluded
+    # every pixel is compared: those a flip may move by more than half the
+    # tolerance against the oracle's outcomes (in _render_compare), the rest here
+    print(f"\n{case} {tile} box={box} batch={batch}: {1.0 - ok.mean():.3%} of pixels compared with the "
+          f"flip outcomes, {int(unresolved.sum())} unresolved")
+    assert unresolved.mean() < 1e-4, unresolved.mean()
     err = np.abs(img - ref["image"]).max(axis=1)[ok]
     assert err.max() <= 1e-5, err.max()
     assert np.abs(T - ref["final_T"])[ok].max() <= 1e-5

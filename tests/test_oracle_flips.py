@@ -195,3 +195,68 @@ def test_gradient_allowances_bound_the_flips(make):
     moved = np.abs(side[1] - side[0])
     assert moved.max() > 0
     assert np.all(moved <= bound + 1e-12 * np.abs(r0["grad"]).max())
+
+
+def _one_pixel(P, **kw):
+    return O.render_pixels(P, 0, _cam(), [PX], [PY], seed=3, t=2, nu=2, **kw)
+
+
+def _swap_scene():
+    A = (0.0, 0.0, 0.0, -2.0, 0.5, (0.9, 0.1, 0.1))
+    B = (0.01, 0.0, 0.0, -2.2, 1.0, (0.1, 0.2, 0.9))
+    return _scene([A, B]), _scene([B, A])
+
+
+@pytest.mark.parametrize("make", [_skip_scene, _termination_scene])
+def test_outcomes_hold_both_sides_of_a_flip(make):
+    """A decision on its threshold gives two outcomes; each of them is what the
+    blend gives when a perturbation far below the rounding window pushes the
+    decision to that side (colour, T and the image tangents), and the last one is
+    the FP64 result."""
+    P, k = make()
+    r = _one_pixel(P, outcomes=16)
+    assert r["n_leaves"][0] == 2
+    L = r["n_leaves"][0]
+    np.testing.assert_array_equal(r["leaf_rgb"][0, L - 1], r["rgb"][0])
+    np.testing.assert_array_equal(r["leaf_T"][0, L - 1], r["final_T"][0])
+    np.testing.assert_allclose(r["leaf_jz"][0, L - 1], r["jz"][0], rtol=0, atol=1e-15)
+    hit = set()
+    for d in (-1e-9, 1e-9):
+        Q = P.copy()
+        Q[10, k] += d
+        s = _one_pixel(Q)
+        err = [max(np.abs(r["leaf_rgb"][0, l] - s["rgb"][0]).max(), abs(r["leaf_T"][0, l] - s["final_T"][0]),
+                   np.abs(r["leaf_jz"][0, l] - s["jz"][0]).max()) for l in range(L)]
+        assert min(err) <= 1e-8, err
+        hit.add(int(np.argmin(err)))
+    assert hit == {0, 1}  # the two sides reach different outcomes
+
+
+def test_outcomes_hold_both_orders_of_equal_depths():
+    one, two = _swap_scene()
+    r = _one_pixel(one, outcomes=16)
+    assert r["n_leaves"][0] == 2
+    other = _one_pixel(two)
+    err = [np.abs(r["leaf_rgb"][0, l] - other["rgb"][0]).max() for l in range(2)]
+    assert min(err) <= 1e-12 and max(err) > 1e-4
+    np.testing.assert_array_equal(r["leaf_rgb"][0, 1], r["rgb"][0])
+
+
+def test_outcomes_without_a_near_decision_are_the_fp64_result():
+    """Where no decision is within rounding of its threshold there is one
+    outcome, the blend itself; the leaf cap reports -1 when there are more."""
+    sc = S.make_scene(300, 1, seed=21, extent=1.0)
+    cam = S.single_camera(W, H)
+    P = O.params64(sc)
+    rng = np.random.default_rng(8)
+    xs, ys = rng.integers(0, W, 200), rng.integers(0, H, 200)
+    r = O.render_pixels(P, 1, cam, xs, ys, seed=3, t=2, nu=1, outcomes=8)
+    firm = (r["impact"] == 0) & (r["t_impact"] == 0)
+    assert firm.sum() > 150
+    assert np.all(r["n_leaves"][firm] == 1)
+    np.testing.assert_array_equal(r["leaf_rgb"][firm, 0], r["rgb"][firm])
+    np.testing.assert_array_equal(r["leaf_T"][firm, 0], r["final_T"][firm])
+    np.testing.assert_allclose(r["leaf_jz"][firm, 0], r["jz"][firm], rtol=0, atol=1e-15)
+    assert np.all(r["rest"][firm] == 0)
+    P2, _ = _skip_scene()
+    assert _one_pixel(P2, outcomes=1)["n_leaves"][0] == -1
