@@ -29,9 +29,17 @@ namespace {
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 8;
 constexpr int kScanChunk = kScanThreads * kScanItems;  // 2048
+// Items per thread of a radix tile, and the scatter's resident blocks per SM
+// (its launch bound); overridable at build time for sweeps.
+#ifndef GS_RADIX_ITEMS
+#define GS_RADIX_ITEMS 8
+#endif
+#ifndef GS_RADIX_MIN_BLOCKS
+#define GS_RADIX_MIN_BLOCKS 4
+#endif
 constexpr int kRadixThreads = 256;
-constexpr int kRadixItems = 8;
-constexpr int kRadixTile = kRadixThreads * kRadixItems;  // 2048
+constexpr int kRadixItems = GS_RADIX_ITEMS;
+constexpr int kRadixTile = kRadixThreads * kRadixItems;  // 2048 by default
 constexpr int kRadixWarps = kRadixThreads / 32;
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
@@ -443,7 +451,7 @@ __global__ void __launch_bounds__(kRadixThreads) radix_hist_kernel(const K* __re
 // the tile's digit starts follow from one block scan; the keys are reordered by
 // (digit, rank) in shared memory and each digit's run written contiguously.
 template <typename K>
-__global__ void __launch_bounds__(kRadixThreads, 4) radix_scatter_kernel(const K* __restrict__ kin_all,
+__global__ void __launch_bounds__(kRadixThreads, GS_RADIX_MIN_BLOCKS) radix_scatter_kernel(const K* __restrict__ kin_all,
                                                                       const uint32_t* __restrict__ vin_all,
                                                                       K* __restrict__ kout, uint32_t* __restrict__ vout,
                                                                       Seg sg, int bpg, int shift,
