@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--profile-steps", type=int, default=0, help="run N untimed steps only (for ncu)")
     ap.add_argument("--profile-views", type=int, default=N_VIEWS,
                     help="views per step in a --profile-steps run (a smaller case for ncu captures)")
+    ap.add_argument("--profile-tile", default="16x16",
+                    help="tile shape WxH of a --profile-steps run (the shape the autotuner picked)")
     return ap.parse_args()
 
 
@@ -126,7 +128,7 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ workload
-def make_workload(n, device, rank=0, views=N_VIEWS, n_batches=None):
+def make_workload(n, device, rank=0, views=N_VIEWS, n_batches=None, tile=TILE):
     import numpy as np
     import torch
     from paper_2602_00395_gb300 import synth as S
@@ -138,7 +140,7 @@ def make_workload(n, device, rank=0, views=N_VIEWS, n_batches=None):
     cams = S.camera_ring(RING, W, H, 10.0, seed=7)
     batches = [[cams[b + RING // views * k] for k in range(views)] for b in range(RING // views)]
     batches = batches[:n_batches] if n_batches else batches
-    eng = TRStep(n, SH_DEG, views, W, H, nu=NU, tile=TILE, cfg=TRConfig(l=1), device=device)
+    eng = TRStep(n, SH_DEG, views, W, H, nu=NU, tile=tile, cfg=TRConfig(l=1), device=device)
     # targets: the ground-truth set rendered by the forward pass, one batch of views at a time
     eng.set_params(gt.params)
     cam_dev, targets = [], []
@@ -250,7 +252,8 @@ def plain_loop_steps(eng, cam_dev, targets, K, t0, stream, device):
     step (device time, CUDA events)."""
     import torch
     from paper_2602_00395_gb300.engine import TRConfig, TRStep, eps_schedule
-    one = TRStep(eng.n, SH_DEG, 1, W, H, nu=NU, tile=TILE, cfg=TRConfig(l=1), capacity=eng.capacity, device=device)
+    one = TRStep(eng.n, SH_DEG, 1, W, H, nu=NU, tile=eng.tile, cfg=TRConfig(l=1), capacity=eng.capacity,
+                 device=device)
     one.x.copy_(eng.x)
     g_acc = torch.zeros_like(one.grad)
     h_acc = torch.zeros_like(one.hz)
@@ -997,7 +1000,8 @@ def run_cuda(args):
         torch.distributed.destroy_process_group()
         return
     if args.profile_steps:
-        eng, cam_dev, targets, batches, need = make_workload(args.n, device, rank, args.profile_views, 2)
+        ptile = tuple(int(v) for v in args.profile_tile.lower().split("x"))
+        eng, cam_dev, targets, batches, need = make_workload(args.n, device, rank, args.profile_views, 2, ptile)
         stream = torch.cuda.Stream(device=device)
         timed_steps(eng, cam_dev, targets, args.profile_steps, 0, 1, stream)
         torch.cuda.synchronize()

@@ -87,8 +87,8 @@ typedef struct gs_camera {
 } gs_camera;
 
 /* Views rendered by one call; every camera of the call has this size.
- * tile_w is 8, 16 or 32, tile_h a power of two >= 8, tile_w * tile_h is 64, 128
- * or 256 (two pixels per thread; each warp covers an 8 x 8 pixel block).
+ * tile_w is 8, 16 or 32, tile_h a power of two >= 8, tile_w * tile_h is 64, 128,
+ * 256 or 512 (two pixels per thread; each warp covers an 8 x 8 pixel block).
  * footprint_bins selects the tiles of a splat (see gs_bin_sort): 0 its 3DGS tile
  * square, 1 that square narrowed to its alpha >= 1/255 footprint (its box, then
  * row by row its ellipse).  Both give the same images and derivatives; 1 gives

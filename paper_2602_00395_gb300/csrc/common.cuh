@@ -513,12 +513,12 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 // ---------------------------------------------------------- frames
 // Tile shapes the kernels support: two pixels per thread and warps covering
 // 8 x 8 pixel blocks, so tile_w is 8, 16 or 32, tile_h a power of two >= 8, and
-// tile_w * tile_h is 64, 128 or 256.
+// tile_w * tile_h is 64, 128, 256 or 512 (at most eight warps per tile).
 inline bool frame_ok(gs_frame fr) {
   auto pow2 = [](int v) { return v > 0 && (v & (v - 1)) == 0; };
   const int tt = fr.tile_w * fr.tile_h;
   return fr.n_views >= 1 && fr.width >= 1 && fr.height >= 1 && (fr.tile_w == 8 || fr.tile_w == 16 || fr.tile_w == 32) &&
-         pow2(fr.tile_h) && fr.tile_h >= 8 && (tt == 64 || tt == 128 || tt == 256) &&
+         pow2(fr.tile_h) && fr.tile_h >= 8 && (tt == 64 || tt == 128 || tt == 256 || tt == 512) &&
          (fr.footprint_bins == 0 || fr.footprint_bins == 1) &&
          (fr.batch == 0 || (fr.batch % 32 == 0 && fr.batch >= 32 && fr.batch <= 512));
 }

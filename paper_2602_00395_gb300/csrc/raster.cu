@@ -125,17 +125,22 @@ __host__ __device__ __forceinline__ int fwd_batch(const gs_frame& fr, int nthr) 
 __host__ __device__ __forceinline__ int bwd_batch(const gs_frame& fr, int nthr) {
   return fr.batch ? fr.batch : kBatchPerThread * nthr;
 }
-// Minimum resident CTAs per SM requested for the forward kernel (0: none).
-// Six (80 registers, a few bytes spilled) measured 9 % faster than the five
-// that 93 unbounded registers allow; seven spilled more and gained less.
+// Minimum resident CTAs per SM requested for the forward kernel (0: none), for
+// blocks of 128 threads; blocks of NT threads (tiles of 2 NT pixels) request
+// the same threads per SM.  Six (80 registers, a few bytes spilled) measured
+// 9 % faster than the five that 93 unbounded registers allow; seven spilled
+// more and gained less.
 #ifndef GS_FWD_MIN_BLOCKS
 #define GS_FWD_MIN_BLOCKS 6
 #endif
 #if GS_FWD_MIN_BLOCKS > 0
-#define GS_FWD_BOUNDS __launch_bounds__(128, GS_FWD_MIN_BLOCKS)
+#define GS_FWD_BOUNDS(NT) __launch_bounds__(NT, (GS_FWD_MIN_BLOCKS * 128) / (NT))
 #else
-#define GS_FWD_BOUNDS __launch_bounds__(128)
+#define GS_FWD_BOUNDS(NT) __launch_bounds__(NT)
 #endif
+// Threads per block the blends are built for: tiles of up to 256 pixels run
+// as blocks of at most 128 threads, tiles of 512 pixels as blocks of 256.
+__host__ __device__ constexpr int blend_threads(int nthr) { return nthr <= 128 ? 128 : 256; }
 
 __device__ __forceinline__ void pixel_of(int tid, int tile_w, int& lx, int& ly) {
   const int warp = tid >> 5, lane = tid & 31, bxn = tile_w >> 3;
@@ -260,8 +265,8 @@ __device__ __forceinline__ void stage_batch_one(int b, int batch, int n, int vie
 
 // CB: the frame sets its own batch (else one record per thread, known to the
 // compiler as the block size).
-template <int NU, bool CB>
-__global__ void GS_FWD_BOUNDS raster_fwd_kernel(const float4* __restrict__ rec, const float4* __restrict__ tan,
+template <int NU, bool CB, int NT>
+__global__ void GS_FWD_BOUNDS(NT) raster_fwd_kernel(const float4* __restrict__ rec, const float4* __restrict__ tan,
                                                          const uint32_t* __restrict__ vals,
                                                          const uint32_t* __restrict__ ranges,
                                                          const uint32_t* __restrict__ order, int n_pad, gs_frame fr,
@@ -503,9 +508,9 @@ constexpr int kBwdSparseLanes = GS_BWD_SPARSE_LANES;
 #define GS_BWD_MIN_BLOCKS 7
 #endif
 #if GS_BWD_MIN_BLOCKS > 0
-#define GS_BWD_BOUNDS __launch_bounds__(128, GS_BWD_MIN_BLOCKS)
+#define GS_BWD_BOUNDS(NT) __launch_bounds__(NT, (GS_BWD_MIN_BLOCKS * 128) / (NT))
 #else
-#define GS_BWD_BOUNDS __launch_bounds__(128)
+#define GS_BWD_BOUNDS(NT) __launch_bounds__(NT)
 #endif
 
 // Warp sums of v[0..31] delivered as quads: afterwards every lane L with
@@ -665,8 +670,8 @@ __device__ __forceinline__ void bwd_accumulate(BwdPixel<S>& p, const Rec& r, flo
   }
 }
 
-template <int NU, bool GRAD, bool CB>
-__global__ void GS_BWD_BOUNDS raster_bwd_kernel(
+template <int NU, bool GRAD, bool CB, int NT>
+__global__ void GS_BWD_BOUNDS(NT) raster_bwd_kernel(
     const float4* __restrict__ rec, const uint32_t* __restrict__ vals, const uint32_t* __restrict__ ranges,
     const uint32_t* __restrict__ order, int n_pad, gs_frame fr, int Tx, int T, const float* __restrict__ image,
     const float* __restrict__ target,
@@ -676,6 +681,7 @@ __global__ void GS_BWD_BOUNDS raster_bwd_kernel(
   constexpr int S = (GRAD ? 1 : 0) + NU;  // cotangent streams
   constexpr int NVP = cot_stride(S);      // padded row stride of their 9 S values
   static_assert(NVP <= 32, "streams");
+  static_assert(NT <= 256, "s_loss holds one partial per warp, at most eight");
   extern __shared__ __align__(16) unsigned char smem[];
   const int nthr = blockDim.x, nwarps = nthr >> 5, batch = CB ? fr.batch : kBatchPerThread * nthr;
   constexpr int K = kBwdStages;
@@ -1403,15 +1409,15 @@ gs_status launch_fwd(const gs_projected* proj, const gs_sorted* sorted, int n_pa
   const int nthr = fr.tile_w * fr.tile_h / kPixPerThread, batch = fwd_batch(fr, nthr);
   const size_t smem = 16 + (size_t)batch * (2 * sizeof(Rec) * (1 + NU) + sizeof(uint32_t));
   // the dynamic shared-memory limit, raised as far as a launch needs
-  const bool cb = fr.batch != 0;
-  static size_t attr[2] = {0, 0};
-  if (smem > attr[cb]) {
-    if (allow_smem(cb ? raster_fwd_kernel<NU, true> : raster_fwd_kernel<NU, false>, smem) != cudaSuccess)
-      return check_launch("gs_raster_fwd: smem attribute");
-    attr[cb] = smem;
+  const bool cb = fr.batch != 0, big = blend_threads(nthr) == 256;
+  auto* kern = big ? (cb ? raster_fwd_kernel<NU, true, 256> : raster_fwd_kernel<NU, false, 256>)
+                   : (cb ? raster_fwd_kernel<NU, true, 128> : raster_fwd_kernel<NU, false, 128>);
+  static size_t attr[2][2] = {{0, 0}, {0, 0}};
+  if (smem > attr[big][cb]) {
+    if (allow_smem(kern, smem) != cudaSuccess) return check_launch("gs_raster_fwd: smem attribute");
+    attr[big][cb] = smem;
   }
   const unsigned blocks = (unsigned)((size_t)fr.n_views * g.T);
-  auto* kern = cb ? raster_fwd_kernel<NU, true> : raster_fwd_kernel<NU, false>;
   kern<<<blocks, nthr, smem, st>>>(reinterpret_cast<const float4*>(proj->rec),
                                    reinterpret_cast<const float4*>(proj->tangent), sorted->vals, sorted->ranges,
                                    sorted->order, n_pad,
@@ -1470,12 +1476,13 @@ void launch_bwd_kernels(const gs_params* x, const BatchArg* ba, int n_pad, int d
   const TileGrid g = tile_grid(fr);
   const int nthr = fr.tile_w * fr.tile_h / kPixPerThread, batch = bwd_batch(fr, nthr);
   const size_t smem = bwd_smem_bytes(batch);
-  const bool cb = fr.batch != 0;
-  auto* kern = cb ? raster_bwd_kernel<NU, GRAD, true> : raster_bwd_kernel<NU, GRAD, false>;
-  static size_t attr[2] = {0, 0};
-  if (smem > 48 * 1024 && smem > attr[cb]) {
+  const bool cb = fr.batch != 0, big = blend_threads(nthr) == 256;
+  auto* kern = big ? (cb ? raster_bwd_kernel<NU, GRAD, true, 256> : raster_bwd_kernel<NU, GRAD, false, 256>)
+                   : (cb ? raster_bwd_kernel<NU, GRAD, true, 128> : raster_bwd_kernel<NU, GRAD, false, 128>);
+  static size_t attr[2][2] = {{0, 0}, {0, 0}};
+  if (smem > 48 * 1024 && smem > attr[big][cb]) {
     if (allow_smem(kern, smem) != cudaSuccess) return;  // the caller reports the error
-    attr[cb] = smem;
+    attr[big][cb] = smem;
   }
   const double views_per_objective = ba ? 1.0 : (double)fr.n_views;
   const float inv_m = (float)(1.0 / (3.0 * (double)fr.width * fr.height * views_per_objective));

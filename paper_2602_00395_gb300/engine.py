@@ -333,8 +333,8 @@ class TRStep:
         return int(self.status.item())
 
 
-def autotune_tile(eng: TRStep, candidates=((16, 16), (32, 8), (8, 32), (16, 8)), batches=(0, 64, 256),
-                  steps: int = 3, stream=None) -> tuple[tuple[int, int, int], dict]:
+def autotune_tile(eng: TRStep, candidates=((16, 16), (32, 8), (8, 32), (16, 8), (32, 16), (16, 32)),
+                  batches=(0, 64, 256), steps: int = 3, stream=None) -> tuple[tuple[int, int, int], dict]:
     """Pick the tile shape, then the blends' per-block record batch for it, with
     the shortest step on the caller's own workload: each candidate is a TRStep
     with the same parameters, cameras, targets and probes that runs one untimed

@@ -74,6 +74,8 @@ def test_host_argument_checks_reject_without_touching_the_device(lib):
     # unsupported tile shapes give a zero workspace size
     assert lib.gs_bin_sort_workspace_size(32, G.frame_struct(1, 64, 64, 12, 16), 1000) == 0
     assert lib.gs_bin_sort_workspace_size(32, G.frame_struct(1, 64, 64, 16, 16), 1000) > 0
+    assert lib.gs_bin_sort_workspace_size(32, G.frame_struct(1, 64, 64, 32, 16), 1000) > 0  # eight warps
+    assert lib.gs_bin_sort_workspace_size(32, G.frame_struct(1, 64, 64, 32, 32), 1000) == 0  # sixteen: no
     assert lib.gs_raster_bwd_workspace_size(32, G.frame_struct(2, 64, 64), 3) == 0
     # a 256-byte header, then 2 views x 32 columns x 28 floats of cotangent rows
     assert lib.gs_raster_bwd_workspace_size(32, G.frame_struct(2, 64, 64), 2) == 256 + 2 * 32 * 28 * 4

@@ -153,6 +153,8 @@ def _write_records(e, mx, my, r, d, ext, conic):
     (128, 128, (16, 16), 1, 1000, 40, False),
     (97, 53, (16, 8), 3, 4001, 30, True),
     (61, 45, (8, 8), 2, 777, 60, False),
+    (97, 53, (32, 16), 3, 4001, 30, True),  # 512-pixel tiles: blocks of eight warps
+    (1297, 840, (16, 32), 2, 150000, 80, False),
     (1297, 840, (16, 16), 2, 150000, 80, True),  # ~ millions of pairs, many chunks
     (1297, 840, (16, 16), 2, 150000, 80, False),
     # more tiles per view than the shared counters hold: pairs sorted by radix passes
@@ -275,7 +277,8 @@ def _render_compare(sc, cams, tile=(16, 16), box=True, batch=0):
 @pytest.mark.parametrize("case,tile,box,batch", [("cfg1", (16, 16), True, 0), ("cfg1", (16, 16), False, 0),
                                                 ("ragged", (16, 8), True, 0), ("ragged", (8, 8), True, 0),
                                                 ("ragged", (16, 16), False, 0), ("ragged", (16, 16), True, 32),
-                                                ("cfg1", (16, 16), True, 512)])
+                                                ("cfg1", (16, 16), True, 512), ("ragged", (32, 16), True, 0),
+                                                ("ragged", (16, 32), False, 0), ("cfg1", (32, 16), True, 128)])
 def test_raster_fwd_matches_oracle(case, tile, box, batch):
     """Image, final T, n_contrib and the pair count equal the oracle's, binning by
     the footprint (box True) or by the whole 3DGS tile square, with the default
@@ -299,11 +302,11 @@ def test_raster_fwd_matches_oracle(case, tile, box, batch):
 
 
 # ------------------------------------------------------------------ reverse
-def _grad_case(case, nu, loss_kind=0, batch=0):
+def _grad_case(case, nu, loss_kind=0, batch=0, tile=(16, 16)):
     sc, cams = _cfg1() if case == "cfg1" else _ragged()
     V, H, W = len(cams), cams[0].height, cams[0].width
     target = S.noise_target(V, H, W, seed=2000)
-    e = _engine(sc.n, sc.sh_degree, cams, nu=nu, loss_kind=loss_kind, batch=batch)
+    e = _engine(sc.n, sc.sh_degree, cams, tile=tile, nu=nu, loss_kind=loss_kind, batch=batch)
     e.set_params(sc.params)
     e.set_target(target)
     e.ensure_capacity()
@@ -315,15 +318,18 @@ def _grad_case(case, nu, loss_kind=0, batch=0):
     e.raster_bwd(t, probes=nu > 0)
     torch.cuda.synchronize()
     ref = O.backward(O.params64(sc), sc.sh_degree, cams, target.astype(np.float64), loss_kind=loss_kind,
-                     seed=42, t=t, nu=nu, want_tangents=nu > 0, masses=True)
+                     seed=42, t=t, nu=nu, tw=tile[0], th=tile[1], want_tangents=nu > 0, masses=True)
     return sc, e, ref
 
 
-@pytest.mark.parametrize("case,nu,loss_kind,batch", [("cfg1", 0, 0, 0), ("cfg1", 1, 0, 0), ("ragged", 2, 0, 0),
-                                                     ("ragged", 1, 1, 0), ("ragged", 2, 0, 64),
-                                                     ("cfg1", 1, 0, 512)])
-def test_gradient_and_hutchinson_match_oracle(case, nu, loss_kind, batch):
-    sc, e, ref = _grad_case(case, nu, loss_kind, batch)
+@pytest.mark.parametrize("case,nu,loss_kind,batch,tile", [("cfg1", 0, 0, 0, (16, 16)), ("cfg1", 1, 0, 0, (16, 16)),
+                                                          ("ragged", 2, 0, 0, (16, 16)), ("ragged", 1, 1, 0, (16, 16)),
+                                                          ("ragged", 2, 0, 64, (16, 16)),
+                                                          ("cfg1", 1, 0, 512, (16, 16)),
+                                                          ("ragged", 2, 0, 0, (32, 16)),
+                                                          ("cfg1", 1, 1, 0, (16, 32))])
+def test_gradient_and_hutchinson_match_oracle(case, nu, loss_kind, batch, tile):
+    sc, e, ref = _grad_case(case, nu, loss_kind, batch, tile)
     grad = e.grad[:, : sc.n].cpu().numpy()
     _group_close(grad, ref["grad"], 1e-4, "grad", ref["grad_mass"], ref["grad_allow"], rnd=ref["grad_round"])
     assert abs(float(e.loss_val.item()) - ref["loss"]) <= 1e-5 * ref["loss"]
