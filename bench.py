@@ -602,14 +602,14 @@ def raster_bwd_flops_per_unit() -> int:
 RASTER_BWD_TRAFFIC = {
     # one-kernel captures (dram__bytes_read.sum + dram__bytes_write.sum) of the
     # reverse call's two kernels on the 2-view case of the bench scene
-    "blend_bytes": 375_577_600 + 42_197_248,        # raster_bwd_kernel
-    "projection_bytes": 460_133_120 + 448_687_616,  # project_bwd_kernel
+    "blend_bytes": 375_195_392 + 42_175_744,        # raster_bwd_kernel
+    "projection_bytes": 460_125_952 + 448_824_320,  # project_bwd_kernel
     "pairs": 12_223_264,                            # pairs blended in that launch
     "n": 1_000_000,
     "views": 2,
     "sources": {
-        "paper_2602_00395_gb300/csrc/raster.cu": "2f05b88b8dc9d3f15d90ea7871e3725300e790b10194276d0659fb239968e024",
-        "paper_2602_00395_gb300/csrc/common.cuh": "b7201d9f818a49a1c40435b69f8e6e4e3d70dc9d7b4428d641c067699f5e6429",
+        "paper_2602_00395_gb300/csrc/raster.cu": "3652345efb9441e91ed6d07a44209d2957c99d4f235c695c7b18774750d6f9af",
+        "paper_2602_00395_gb300/csrc/common.cuh": "717ae4cfbf722db44969cb1b4c8974cb88deb3c71b60bd452f4448c33bb37054",
     },
 }
 
