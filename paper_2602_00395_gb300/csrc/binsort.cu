@@ -307,6 +307,10 @@ __global__ void emit_kernel(const uint4* __restrict__ hdr, const uint2* __restri
     g = order[p0];
     h = hdr[g];
   }
+  // this lane's record as (first tile key of its view, splat index): one
+  // division per record instead of one per pair (views x tiles < 2^32)
+  const uint32_t gview = g / (uint32_t)n_pad;
+  const uint32_t gkey0 = gview * (uint32_t)(Tx * Ty), gsplat = g - gview * (uint32_t)n_pad;
   const uint32_t cnt = h.w;
   // inclusive warp scan of the counts
   uint32_t incl = cnt;
@@ -318,7 +322,6 @@ __global__ void emit_kernel(const uint4* __restrict__ hdr, const uint2* __restri
   const uint32_t start = incl - cnt;
   const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
   const uint64_t base = offsets[w0];
-  const uint64_t tiles = (uint64_t)Tx * Ty;
   const uint32_t rounds = (total + 31) / 32;
   for (uint32_t rd = 0; rd < rounds; ++rd) {
     const uint32_t p = rd * 32 + lane;
@@ -331,16 +334,14 @@ __global__ void emit_kernel(const uint4* __restrict__ hdr, const uint2* __restri
       if (cand < 32 && sc <= p) lo = cand;
     }
     const uint32_t o_start = __shfl_sync(0xffffffffu, start, lo);
-    const uint32_t og32 = __shfl_sync(0xffffffffu, g, lo);
-    const uint32_t od = __shfl_sync(0xffffffffu, h.x, lo);
+    const uint32_t okey0 = __shfl_sync(0xffffffffu, gkey0, lo);
+    const uint32_t osplat = __shfl_sync(0xffffffffu, gsplat, lo);
     const uint32_t oyr = __shfl_sync(0xffffffffu, h.y, lo);
     const uint32_t ooff = __shfl_sync(0xffffffffu, h.z, lo);
     const uint32_t R = oyr >> 16;
     const uint64_t at = base + p;
     if (p < total && at < capacity) {
-      const size_t og = og32;
-      const int oview = (int)(og / n_pad);
-      uint32_t tile = (uint32_t)((uint64_t)oview * tiles);
+      uint32_t tile = okey0;
       if (R > 0) {
         const uint32_t q = p - o_start;
         // last row whose pairs above are <= q (empty rows repeat the count before them)
@@ -360,7 +361,7 @@ __global__ void emit_kernel(const uint4* __restrict__ hdr, const uint2* __restri
       // its slots still get a valid tile and splat so that every slot below the
       // capacity holds an in-range pair)
       keys[at] = tile;
-      vals[at] = (uint32_t)(og - (size_t)oview * n_pad);
+      vals[at] = osplat;
     }
   }
 }
