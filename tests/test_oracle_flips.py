@@ -260,3 +260,25 @@ def test_outcomes_without_a_near_decision_are_the_fp64_result():
     assert np.all(r["rest"][firm] == 0)
     P2, _ = _skip_scene()
     assert _one_pixel(P2, outcomes=1)["n_leaves"][0] == -1
+
+
+def test_outcomes_cover_every_pixel_of_a_scene():
+    """On every pixel of a small scene: at least one outcome, the last one the
+    FP64 blend bit for bit, every T in [0, 1], and a single outcome wherever
+    the flip bound is zero."""
+    sc = S.make_scene(400, 1, seed=23, extent=1.0, log_scale_shift=math.log(1.5))
+    cam = S.single_camera(40, 32)
+    P = O.params64(sc)
+    ys, xs = np.mgrid[0:32, 0:40]
+    xs, ys = xs.ravel(), ys.ravel()
+    r = O.render_pixels(P, 1, cam, xs, ys, outcomes=64)
+    nl = r["n_leaves"]
+    assert np.all(nl >= 1)
+    last = nl - 1
+    k = np.arange(len(xs))
+    np.testing.assert_array_equal(r["leaf_rgb"][k, last], r["rgb"])
+    np.testing.assert_array_equal(r["leaf_T"][k, last], r["final_T"])
+    valid = np.arange(r["leaf_T"].shape[1])[None, :] < nl[:, None]
+    assert np.all((r["leaf_T"][valid] >= 0.0) & (r["leaf_T"][valid] <= 1.0))
+    firm = (r["impact"] == 0) & (r["t_impact"] == 0)
+    assert np.all(nl[firm] == 1)
