@@ -1039,8 +1039,8 @@ struct BlendOutcomes {
     r.drop = r.a * T * (ci + cmax);
     return r;
   }
-  // may the entry blend at this pixel on either side
-  bool may_blend(const Entry& e, const Eval& r) const { return r.blends || r.near; }
+  // may the splat blend at this pixel on either side
+  static bool may_blend(const Eval& r) { return r.blends || r.near; }
 
   void leaf(const std::vector<int>& seq, double rs, double trs) {
     if (leaves.size() >= max_leaves) {
@@ -1059,14 +1059,14 @@ struct BlendOutcomes {
   void walk(size_t p, std::vector<int> seq, double T, double tun, double rho, double rs, double trs, bool no_swap) {
     for (; p < E.size() && !overflow; ++p, no_swap = false) {
       Eval r = eval(E[p].i, T);
-      if (!no_swap && may_blend(E[p], r)) {
+      if (!no_swap && may_blend(r)) {
         // the next splat that may blend: if its depth is within a few ulps, the
         // GPU's keys may put it first
         size_t q = p + 1;
         Eval rq{};
         for (; q < E.size(); ++q) {
           rq = eval(E[q].i, T);
-          if (may_blend(E[q], rq)) break;
+          if (may_blend(rq)) break;
         }
         const double d0 = E[p].depth;
         if (q < E.size() && std::fabs((double)E[q].depth - d0) <= 4.0 * std::ldexp(std::fabs(d0), -23)) {
