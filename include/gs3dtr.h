@@ -151,7 +151,16 @@ typedef struct gs_projected {
  *             (view * tiles + tile) from the longest list to the shortest
  *             (lengths grouped in steps of 1/8 of a power of two, any order
  *             within a group); the blends then start the heaviest tiles first.
- *             It changes when a tile runs, never its result. */
+ *             It changes when a tile runs, never its result.
+ *   masks:    NULL, or capacity bytes.  gs_raster_fwd writes, for every pair it
+ *             stages, which 8 x 8 pixel blocks of the pair's tile the splat's
+ *             footprint reaches (bit w: the block of warp w, see gs_frame);
+ *             gs_raster_bwd, gs_hvp_diag and gs_raster_bwd_batch then read those
+ *             bits instead of testing the footprint again.  The bits of a pair
+ *             are valid once gs_raster_fwd has run on these sorted pairs with the
+ *             same frame (the reverse passes read only list positions the
+ *             forward staged); pass NULL to a reverse pass otherwise.  Either
+ *             way the results are the same. */
 typedef struct gs_sorted {
   uint32_t* keys;
   uint32_t* vals;
@@ -159,6 +168,7 @@ typedef struct gs_sorted {
   uint32_t* n_pairs;
   uint64_t capacity;
   uint32_t* order;
+  uint8_t* masks;
 } gs_sorted;
 
 enum { GS_LOSS_L1 = 0, GS_LOSS_L2 = 1, GS_LOSS_COTANGENT = 2, GS_LOSS_WEIGHTED = 3 };

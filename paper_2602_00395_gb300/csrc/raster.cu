@@ -272,7 +272,8 @@ __global__ void GS_FWD_BOUNDS(NT) raster_fwd_kernel(const float4* __restrict__ r
                                                          const uint32_t* __restrict__ order, int n_pad, gs_frame fr,
                                                          int Tx, int T, float* __restrict__ image,
                                                          float* __restrict__ final_T, uint32_t* __restrict__ n_contrib,
-                                                         float* __restrict__ image_tan, int32_t* status) {
+                                                         float* __restrict__ image_tan, uint8_t* __restrict__ masks,
+                                                         int32_t* status) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int nthr = blockDim.x, nwarps = nthr >> 5, batch = CB ? fr.batch : kBatchPerThread * nthr / kFwdBatchDiv;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
@@ -354,6 +355,7 @@ __global__ void GS_FWD_BOUNDS(NT) raster_fwd_kernel(const float4* __restrict__ r
     for (int q = tid; q < cnt; q += nthr) {
       const Rec r = *recp(q);
       s_mask[q] = ok ? warp_block_mask(r, tile_x0, tile_y0, fr.tile_w, nwarps) : 0u;
+      if (masks) masks[start + (uint32_t)(b * batch + q)] = (uint8_t)s_mask[q];  // for the reverse passes
 #pragma unroll
       for (int k = 0; k < NU; ++k) {
         Rec* tp = recp(q) + 1 + k;
@@ -450,19 +452,22 @@ constexpr int kBwdStages = GS_BWD_STAGES;
 // ring header: one mbarrier and one release counter per stage, 16-byte aligned
 constexpr size_t kBwdRingHdr = (kBwdStages * (sizeof(uint64_t) + sizeof(uint32_t)) + 15) / 16 * 16;
 __host__ __device__ constexpr size_t bwd_smem_bytes(int batch) {
-  return kBwdRingHdr + (size_t)kBwdStages * batch * (sizeof(Rec) + sizeof(uint32_t));
+  return kBwdRingHdr + (size_t)kBwdStages * batch * (sizeof(Rec) + sizeof(uint32_t)) +
+         ((size_t)kBwdStages * batch + 15) / 16 * 16;  // and the staged block masks, one byte per record
 }
 
 // The calling warp fills ring stage s with batch b of the list (use u of the
-// ring): its lanes store the Gaussian indices and issue one bulk copy per
-// record, then lane 0 records u as the stage's last fill and arms the stage's
-// barrier with the byte count.  The copies may complete before that arrival (the
+// ring): its lanes store the Gaussian indices (and, given the forward pass's
+// block masks, each record's mask byte) and issue one bulk copy per record,
+// then lane 0 records u as the stage's last fill and arms the stage's barrier
+// with the byte count.  The copies may complete before that arrival (the
 // phase cannot complete while the arrival is pending), and the arrival releases
 // the index stores to the warps that wait on the phase.
 __device__ __forceinline__ void stage_batch_warp(int s, int u, int b, int batch, uint32_t start, int n, int view,
                                                  int n_pad, const uint32_t* __restrict__ vals,
-                                                 const float4* __restrict__ rec, Rec* buf, uint32_t* s_idx,
-                                                 uint64_t* full, int* fill_use) {
+                                                 const float4* __restrict__ rec, const uint8_t* __restrict__ masks,
+                                                 Rec* buf, uint32_t* s_idx, uint8_t* s_bits, uint64_t* full,
+                                                 int* fill_use) {
   const int lane = threadIdx.x & 31;
   const int cnt = min(batch, n - b * batch);
   __syncwarp();
@@ -470,6 +475,7 @@ __device__ __forceinline__ void stage_batch_warp(int s, int u, int b, int batch,
   for (int q = lane; q < cnt; q += 32) {
     const uint32_t gi = __ldg(vals + start + (uint32_t)(b * batch + q));
     s_idx[s * batch + q] = gi;
+    if (masks) s_bits[s * batch + q] = __ldg(masks + start + (uint32_t)(b * batch + q));
     bulk_g2s(&buf[s * batch + q], rec + 3 * ((size_t)view * n_pad + gi), sizeof(Rec), &full[s]);
   }
   __syncwarp();
@@ -677,7 +683,7 @@ __global__ void GS_BWD_BOUNDS(NT) raster_bwd_kernel(
     const float* __restrict__ target,
     const float* __restrict__ final_T, const uint32_t* __restrict__ n_contrib, const float* __restrict__ image_tan,
     int loss_kind, float gn_floor, float inv_m, float* __restrict__ cot, float* __restrict__ loss_out,
-    int loss_per_view, CotHeader* cot_hdr, int32_t* status) {
+    int loss_per_view, CotHeader* cot_hdr, const uint8_t* __restrict__ masks, int32_t* status) {
   constexpr int S = (GRAD ? 1 : 0) + NU;  // cotangent streams
   constexpr int NVP = cot_stride(S);      // padded row stride of their 9 S values
   static_assert(NVP <= 32, "streams");
@@ -689,6 +695,7 @@ __global__ void GS_BWD_BOUNDS(NT) raster_bwd_kernel(
   uint32_t* released = reinterpret_cast<uint32_t*>(smem + K * sizeof(uint64_t));  // K release counters
   Rec* buf = reinterpret_cast<Rec*>(smem + kBwdRingHdr);
   uint32_t* s_idx = reinterpret_cast<uint32_t*>(buf + K * batch);
+  uint8_t* s_bits = reinterpret_cast<uint8_t*>(s_idx + K * batch);  // block masks of the staged records
   __shared__ uint32_t s_max;
   __shared__ int s_abort;
   __shared__ float s_loss[8];
@@ -796,7 +803,8 @@ __global__ void GS_BWD_BOUNDS(NT) raster_bwd_kernel(
   const int nb = (n + batch - 1) / batch;
   // batch b is use u = nb - 1 - b of the ring: stage u % K, its (u / K)-th fill
   for (int u = warp; u < min(K, nb); u += nwarps)
-    stage_batch_warp(u, u, nb - 1 - u, batch, start, n, view, n_pad, vals, rec, buf, s_idx, full, s_fill_use);
+    stage_batch_warp(u, u, nb - 1 - u, batch, start, n, view, n_pad, vals, rec, masks, buf, s_idx, s_bits, full,
+                     s_fill_use);
   bool ok = true;
   for (int u = 0; u < nb; ++u) {
     const int st = u % K, b = nb - 1 - u;
@@ -809,12 +817,15 @@ __global__ void GS_BWD_BOUNDS(NT) raster_bwd_kernel(
     if (!ok) break;
     const int cnt = min(batch, n - b * batch);
     const Rec* bb = buf + st * batch;
-    // the warp walks, back to front, only the splats its block can see and
+    // the warp walks, back to front, only the splats its block can see (the
+    // forward pass's mask bit when given, else the same footprint test) and
     // that lie before its last contributor: one ballot per 32 splats
+    const uint8_t* sb = s_bits + st * batch;
     for (int j0 = ((cnt - 1) & ~31); (uint32_t)(b * batch) < warp_nc && j0 >= 0; j0 -= 32) {
       const int jl = j0 + lane;
-      uint32_t bits =
-          __ballot_sync(0xffffffffu, jl < cnt && (uint32_t)(b * batch + jl) < warp_nc && block_sees(bb[jl], wx0, wy0));
+      uint32_t bits = __ballot_sync(
+          0xffffffffu, jl < cnt && (uint32_t)(b * batch + jl) < warp_nc &&
+                           (masks ? ((sb[jl] >> warp) & 1u) != 0 : block_sees(bb[jl], wx0, wy0)));
       while (bits) {
         const int hb = 31 - __clz(bits);
         bits &= ~(1u << hb);
@@ -886,8 +897,8 @@ __global__ void GS_BWD_BOUNDS(NT) raster_bwd_kernel(
     }
     last = __shfl_sync(0xffffffffu, last, 0);
     if (last && u + K < nb)
-      stage_batch_warp(st, u + K, nb - 1 - (u + K), batch, start, n, view, n_pad, vals, rec, buf, s_idx, full,
-                       s_fill_use);
+      stage_batch_warp(st, u + K, nb - 1 - (u + K), batch, start, n, view, n_pad, vals, rec, masks, buf, s_idx,
+                       s_bits, full, s_fill_use);
   }
   // Drain after a failed wait: a stage is refilled only by a warp that saw its
   // previous fill land, so each stage has at most one fill in flight, its last.
@@ -1421,7 +1432,7 @@ gs_status launch_fwd(const gs_projected* proj, const gs_sorted* sorted, int n_pa
   kern<<<blocks, nthr, smem, st>>>(reinterpret_cast<const float4*>(proj->rec),
                                    reinterpret_cast<const float4*>(proj->tangent), sorted->vals, sorted->ranges,
                                    sorted->order, n_pad,
-                                   fr, g.Tx, g.T, image, final_T, n_contrib, image_tan, status);
+                                   fr, g.Tx, g.T, image, final_T, n_contrib, image_tan, sorted->masks, status);
   return check_launch("gs_raster_fwd");
 }
 
@@ -1491,7 +1502,7 @@ void launch_bwd_kernels(const gs_params* x, const BatchArg* ba, int n_pad, int d
       reinterpret_cast<const float4*>(proj->rec), sorted->vals, sorted->ranges, sorted->order, n_pad, fr, g.Tx,
       g.T, image,
       target, final_T, n_contrib, image_tan, loss.kind, loss.gn_floor, inv_m, ws.cot, loss_out, ba ? 1 : 0, ws.hdr,
-      status);
+      sorted->masks, status);
   if (ba) {
     if (ba->first_block[ba->n_items] == 0) return;
     constexpr int S = (GRAD ? 1 : 0) + NU;

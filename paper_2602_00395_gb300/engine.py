@@ -121,6 +121,9 @@ class TRStep:
         self.capacity = int(capacity)
         self.keys = torch.empty(self.capacity, dtype=torch.int32, device=self.device)
         self.vals = torch.empty(self.capacity, dtype=torch.int32, device=self.device)
+        # the forward pass's block masks of the pairs, read by the reverse passes
+        self.masks = torch.empty(self.capacity, dtype=torch.uint8, device=self.device)
+        self.masks_valid = False  # set by a forward pass, cleared by the next bin-sort
         self.sort_ws = torch.empty(G.gs_bin_sort_workspace_size(self.n_pad, self.frame, self.capacity),
                                    dtype=torch.uint8, device=self.device)
 
@@ -143,9 +146,17 @@ class TRStep:
     def proj(self) -> G.gs_projected:
         return G.gs_projected(self.rec.data_ptr(), self.tan.data_ptr())
 
-    def sorted(self) -> G.gs_sorted:
+    def sorted(self, masks: bool = True) -> G.gs_sorted:
+        """The sorted pairs; with masks, the block-mask buffer (the forward pass
+        writes it, a reverse pass reads it)."""
         return G.gs_sorted(self.keys.data_ptr(), self.vals.data_ptr(), self.ranges.data_ptr(),
-                           self.n_pairs.data_ptr(), self.capacity, self.order.data_ptr())
+                           self.n_pairs.data_ptr(), self.capacity, self.order.data_ptr(),
+                           self.masks.data_ptr() if masks else None)
+
+    def sorted_rev(self) -> G.gs_sorted:
+        """The sorted pairs for a reverse pass: the masks only if a forward pass
+        has written them for the current sort."""
+        return self.sorted(self.masks_valid)
 
     def probe(self, t: int | None, device_t: bool = False) -> G.gs_probe | None:
         if self.nu == 0:
@@ -159,11 +170,13 @@ class TRStep:
 
     def bin_sort(self, stream=None) -> None:
         G.gs_bin_sort(self.proj(), self.n_pad, self.frame, self.sort_ws, self.sorted(), self.status, stream)
+        self.masks_valid = False
 
     def raster_fwd(self, t: int | None = None, probes: bool = True, stream=None) -> None:
         pr = self.probe(t) if (probes and t is not None) else None
         G.gs_raster_fwd(self.proj(), self.sorted(), self.n_pad, self.frame, pr, self.image, self.final_T,
                         self.n_contrib, self.image_tan if pr else None, self.status, stream)
+        self.masks_valid = True
 
     def raster_bwd(self, t: int | None = None, probes: bool = True, stream=None) -> None:
         pr = self.probe(t) if (probes and t is not None) else None
@@ -174,8 +187,8 @@ class TRStep:
                                   self.dssim_ws, self.status, stream)
             self.raster_bwd_cotangent(self.cot_img, t if pr else None, True, stream)
             return
-        G.gs_raster_bwd(self.P(self.x), self.cams, self.frame, self.proj(), self.sorted(), self.image, self.target,
-                        self.final_T, self.n_contrib, self.image_tan if pr else None, pr, self.loss,
+        G.gs_raster_bwd(self.P(self.x), self.cams, self.frame, self.proj(), self.sorted_rev(), self.image,
+                        self.target, self.final_T, self.n_contrib, self.image_tan if pr else None, pr, self.loss,
                         self.P(self.grad), self.P(self.hz) if pr else None, self.loss_val, self.bwd_ws,
                         self.status, stream)
 
@@ -186,11 +199,11 @@ class TRStep:
         pr = self.probe(t) if t is not None else None
         loss = G.gs_loss(G.GS_LOSS_COTANGENT, self.loss.gn_floor)
         if want_grad:
-            G.gs_raster_bwd(self.P(self.x), self.cams, self.frame, self.proj(), self.sorted(), self.image, cot,
+            G.gs_raster_bwd(self.P(self.x), self.cams, self.frame, self.proj(), self.sorted_rev(), self.image, cot,
                             self.final_T, self.n_contrib, None, pr, loss, self.P(self.grad),
                             self.P(self.hz) if pr else None, None, self.bwd_ws, self.status, stream)
         else:
-            G.gs_hvp_diag(self.P(self.x), self.cams, self.frame, self.proj(), self.sorted(), self.image, cot,
+            G.gs_hvp_diag(self.P(self.x), self.cams, self.frame, self.proj(), self.sorted_rev(), self.image, cot,
                           self.final_T, self.n_contrib, None, pr, loss, self.P(self.hz), self.bwd_ws, self.status,
                           stream)
 
@@ -200,7 +213,7 @@ class TRStep:
         forward pass with the probes of step t; weights is V x 3 x H x W."""
         pr = self.probe(t)
         loss = G.gs_loss(G.GS_LOSS_WEIGHTED, self.loss.gn_floor)
-        G.gs_hvp_diag(self.P(self.x), self.cams, self.frame, self.proj(), self.sorted(), self.image, weights,
+        G.gs_hvp_diag(self.P(self.x), self.cams, self.frame, self.proj(), self.sorted_rev(), self.image, weights,
                       self.final_T, self.n_contrib, self.image_tan, pr, loss, self.P(self.hz), self.bwd_ws,
                       self.status, stream)
 
@@ -211,7 +224,7 @@ class TRStep:
                                   self.loss.gn_floor, False, self.cot_img, None, self.dssim_ws, self.status, stream)
             self.raster_bwd_cotangent(self.cot_img, t, False, stream)
             return
-        G.gs_hvp_diag(self.P(self.x), self.cams, self.frame, self.proj(), self.sorted(), self.image, self.target,
+        G.gs_hvp_diag(self.P(self.x), self.cams, self.frame, self.proj(), self.sorted_rev(), self.image, self.target,
                       self.final_T, self.n_contrib, self.image_tan, pr, self.loss, self.P(self.hz), self.bwd_ws,
                       self.status, stream)
 
@@ -281,8 +294,9 @@ class TRStep:
         self.bin_sort(stream)
         G.gs_raster_fwd(self.proj(), self.sorted(), self.n_pad, self.frame, pr, self.image, self.final_T,
                         self.n_contrib, self.image_tan if pr else None, self.status, stream)
-        G.gs_raster_bwd(self.P(self.x), self.cams, self.frame, self.proj(), self.sorted(), self.image, self.target,
-                        self.final_T, self.n_contrib, self.image_tan if pr else None, pr, self.loss,
+        self.masks_valid = True
+        G.gs_raster_bwd(self.P(self.x), self.cams, self.frame, self.proj(), self.sorted_rev(), self.image,
+                        self.target, self.final_T, self.n_contrib, self.image_tan if pr else None, pr, self.loss,
                         self.P(self.grad), self.P(self.hz) if pr else None, self.loss_val, self.bwd_ws,
                         self.status, stream)
         G.gs_tr_update_dev(self.P(self.x), self.P(self.g_ema), self.P(self.d_ema), self.P(self.grad),
@@ -436,6 +450,7 @@ class BatchStep:
         self.capacity = int(capacity)
         self.keys = buf("keys", self.capacity, i32)
         self.vals = buf("vals", self.capacity, i32)
+        self.masks = buf("masks", self.capacity, u8)  # written by the forward pass, read by the reverse
         self.sort_ws = buf("sort_ws", G.gs_bin_sort_workspace_size(self.n_pad, self.frame, self.capacity), u8)
         self.cams = torch.cat([e.cam for e in entries])
         if train:
@@ -467,7 +482,7 @@ class BatchStep:
         frame = G.frame_struct(B, width, height, *tile)
         Tx, Ty = -(-width // tile[0]), -(-height // tile[1])
         b = B * n_pad * 48 * (1 + (1 + nu if nu else 0)) + B * HW * 4 * (3 + 1 + 1 + 3 * nu) + B * Tx * Ty * 12
-        b += capacity * 8
+        b += capacity * 9  # keys, values, block masks
         b += G.gs_bin_sort_workspace_size(n_pad, frame, capacity) + 96 * B
         if train:
             b += B * HW * 12 + G.gs_raster_bwd_workspace_size(n_pad, frame, nu)
@@ -493,7 +508,7 @@ class BatchStep:
         pr = G.probe_struct(self.probe_seed, 0, self.nu) if self.nu else None
         proj = G.gs_projected(self.rec.data_ptr(), self.tan.data_ptr())
         srt = G.gs_sorted(self.keys.data_ptr(), self.vals.data_ptr(), self.ranges.data_ptr(),
-                          self.n_pairs.data_ptr(), self.capacity, self.order.data_ptr())
+                          self.n_pairs.data_ptr(), self.capacity, self.order.data_ptr(), self.masks.data_ptr())
         G.gs_project_batch(items, self.n_pad, self.frame, pr, proj, self.status, stream)
         G.gs_bin_sort(proj, self.n_pad, self.frame, self.sort_ws, srt, self.status, stream)
         G.gs_raster_fwd(proj, srt, self.n_pad, self.frame, pr, self.image, self.final_T, self.n_contrib,

@@ -69,7 +69,7 @@ class gs_projected(C.Structure):
 
 class gs_sorted(C.Structure):
     _fields_ = [("keys", C.c_void_p), ("vals", C.c_void_p), ("ranges", C.c_void_p), ("n_pairs", C.c_void_p),
-                ("capacity", C.c_uint64), ("order", C.c_void_p)]
+                ("capacity", C.c_uint64), ("order", C.c_void_p), ("masks", C.c_void_p)]
 
 
 class gs_loss(C.Structure):
@@ -89,7 +89,7 @@ class gs_batch_item(C.Structure):
                 ("cam", C.c_void_p), ("t", C.c_int64), ("eps", C.c_float), ("hvp", C.c_int32)]
 
 
-assert C.sizeof(gs_camera) == 96 and C.sizeof(gs_params) == 24 and C.sizeof(gs_sorted) == 48
+assert C.sizeof(gs_camera) == 96 and C.sizeof(gs_params) == 24 and C.sizeof(gs_sorted) == 56
 assert C.sizeof(gs_batch_item) == 144
 
 

@@ -120,7 +120,7 @@ class Scene:
         cap = self.capacity * V
         b = V * n_pad * 12 * 4 * (2 + max(self.nu, 1))                   # records, their copies + tangents
         b += V * HW * 4 * (3 + 1 + 1 + 3 * max(self.nu, 1) + 3)          # image, T, n_contrib, tangents, target slot
-        b += cap * 8 + G.gs_bin_sort_workspace_size(n_pad, frame, cap)
+        b += cap * 9 + G.gs_bin_sort_workspace_size(n_pad, frame, cap)  # keys, values, block masks
         b += G.gs_raster_bwd_workspace_size(n_pad, frame, self.nu) + 2 * rows * n_pad * 4  # cotangents, grad, hz
         return int(b)
 

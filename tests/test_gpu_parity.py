@@ -342,6 +342,37 @@ def test_gradient_and_hutchinson_match_oracle(case, nu, loss_kind, batch, tile):
         assert np.abs(it - ref["image_tangent"]).max() <= 1e-4 * scale
 
 
+@pytest.mark.parametrize("tile,box", [((16, 16), True), ((16, 16), False), ((32, 16), True)])
+def test_reverse_pass_with_the_forward_masks_equals_its_own_footprint_test(tile, box):
+    """The reverse pass reads the forward pass's block masks (gs_sorted.masks)
+    or, given none, tests each splat's footprint against its warp's block
+    itself: the same splats are visited, so the gradient and Hutchinson rows
+    agree up to the order of the float atomics that sum them."""
+    sc, cams = _ragged()
+    V, H, W = len(cams), cams[0].height, cams[0].width
+    e = _engine(sc.n, sc.sh_degree, cams, tile=tile, nu=2, footprint_bins=box)
+    e.set_params(sc.params)
+    e.set_target(S.noise_target(V, H, W, seed=2000))
+    e.ensure_capacity()
+    t = 3
+    e.project(t)
+    e.bin_sort()
+    e.raster_fwd(t)
+    assert e.masks_valid
+    out = []
+    for use_masks in (True, False):
+        e.grad.zero_()
+        e.hz.zero_()
+        e.masks_valid = use_masks
+        e.raster_bwd(t)
+        torch.cuda.synchronize()
+        out.append((e.grad[:, : sc.n].cpu().numpy().copy(), e.hz[:, : sc.n].cpu().numpy().copy()))
+    assert e.read_status() == 0
+    for a, b in zip(out[0], out[1]):
+        assert np.abs(a).max() > 0
+        assert np.abs(a - b).max() <= 1e-5 * np.abs(a).max()
+
+
 def test_step_with_separate_curvature_batch_matches_oracle():
     """Algorithm 1 with S2 != S1 (Sec. 4.1): the gradient from S1's view, the
     Hutchinson product from S2's view, then the update; l = 2 so that the next
