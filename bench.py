@@ -602,13 +602,13 @@ def raster_bwd_flops_per_unit() -> int:
 RASTER_BWD_TRAFFIC = {
     # one-kernel captures (dram__bytes_read.sum + dram__bytes_write.sum) of the
     # reverse call's two kernels on the 2-view case of the bench scene
-    "blend_bytes": 375_195_392 + 42_175_744,        # raster_bwd_kernel
-    "projection_bytes": 460_125_952 + 448_824_320,  # project_bwd_kernel
+    "blend_bytes": 376_053_760 + 42_944_512,        # raster_bwd_kernel
+    "projection_bytes": 460_134_656 + 448_670_720,  # project_bwd_kernel
     "pairs": 12_223_264,                            # pairs blended in that launch
     "n": 1_000_000,
     "views": 2,
     "sources": {
-        "paper_2602_00395_gb300/csrc/raster.cu": "3652345efb9441e91ed6d07a44209d2957c99d4f235c695c7b18774750d6f9af",
+        "paper_2602_00395_gb300/csrc/raster.cu": "8b921d07294e5538f909dd67b67d2deb0e81b2b5488131abab5203f770442d7f",
         "paper_2602_00395_gb300/csrc/common.cuh": "717ae4cfbf722db44969cb1b4c8974cb88deb3c71b60bd452f4448c33bb37054",
     },
 }
