@@ -93,7 +93,7 @@ def test_sampled_pixels_match_oracle(large):
     img = f["img"][:, ys, xs].T
     ok, matched, _ = O.match_outcomes(ref, img, f["final_T"][ys, xs], img_tol=1e-5, flip_max=5e-6)
     print(f"\nlarge scene: {int((~ok).sum())} of {len(xs)} sampled pixels unresolved")
-    assert ok.mean() >= 0.99
+    assert (~ok).mean() <= 1e-4, int((~ok).sum())
     assert np.all(matched[ok])
     nc = f["n_contrib"][ys, xs]
     assert np.all(((nc >= ref["n_contrib_lo"]) & (nc <= ref["n_contrib_hi"]))[ok])
