@@ -284,24 +284,29 @@ def test_outcomes_cover_every_pixel_of_a_scene():
     assert np.all(nl[firm] == 1)
 
 
-def test_outcomes_hold_both_sides_of_a_membership_flip():
+@pytest.mark.parametrize("side", ["added", "dropped"])
+def test_outcomes_hold_both_sides_of_a_membership_flip(side):
     """3DGS tile squares (the oracle's default binning): a bright splat of
-    radius 10 px whose square starts exactly on the tile boundary x = 32, so
-    whether tile 1 lists it is within FP32 rounding, while its alpha at the
-    pixel just left of the boundary is above 1/255.  That pixel has two
-    outcomes, with and without the splat; moving the splat by a few FP32 ulps
-    either way reproduces each."""
+    radius 10 px whose square ends exactly on a tile boundary, so whether the
+    tile beyond lists it is within FP32 rounding, while its alpha at the pixel
+    just past the boundary is above 1/255.  "added": the square starts at
+    x = 32 (mx - r = 32), FP64 leaves tile 1 out and FP32 may list the splat
+    there (pixel 31); "dropped": it ends so that (mx + r + 15) / 16 = 4
+    (mx + r = 49), FP64 lists it in tile 3 and FP32 may not (pixel 48).  That
+    pixel has two outcomes, with and without the splat; moving the splat by a
+    few FP32 ulps either way reproduces each."""
     cam = _cam()
 
     def scene(y):
         return _scene([(y, 0.0, 0.0, -1.5, 3.0, (0.9, 0.2, 0.1)),
                        (0.0, 0.0, -0.6, -1.0, 0.0, (0.2, 0.3, 0.8))])
 
-    def edge(y):  # left end of the splat's square, minus the boundary
+    def edge(y):  # the square's end, minus the boundary it is put on
         s = O.project(scene(y), 0, cam)
-        return s["mx"][0] - s["radius"][0] - 32.0
+        mx, r = s["mx"][0], s["radius"][0]
+        return mx - r - 32.0 if side == "added" else mx + r - 49.0
 
-    a, b = 0.5, 1.0  # secant solve of edge(y) = 0
+    a, b = (0.5, 1.0) if side == "added" else (0.3, 0.6)  # secant solve of edge(y) = 0
     fa, fb = edge(a), edge(b)
     for _ in range(60):
         if fb == 0.0 or fa == fb:
@@ -309,12 +314,13 @@ def test_outcomes_hold_both_sides_of_a_membership_flip():
         a, b, fa = b, b - fb * (b - a) / (fb - fa), fb
         fb = edge(b)
     assert abs(fb) < 1e-9 and O.project(scene(b), 0, cam)["radius"][0] == 10
-    r = O.render_pixels(scene(b), 0, cam, [31], [24], outcomes=16)
+    px = 31 if side == "added" else 48
+    r = O.render_pixels(scene(b), 0, cam, [px], [24], outcomes=16)
     assert r["n_leaves"][0] == 2 and r["flip_kinds"][0] & 4
-    np.testing.assert_array_equal(r["leaf_rgb"][0, 1], r["rgb"][0])  # FP64: the square misses tile 1
+    np.testing.assert_array_equal(r["leaf_rgb"][0, 1], r["rgb"][0])  # the last outcome is the FP64 blend
     hit = set()
     for d in (-2e-6, 2e-6):  # about 2.8e-5 px, several FP32 ulps of mx
-        s = O.render_pixels(scene(b + d), 0, cam, [31], [24])
+        s = O.render_pixels(scene(b + d), 0, cam, [px], [24])
         err = [np.abs(r["leaf_rgb"][0, l] - s["rgb"][0]).max() for l in range(2)]
         assert min(err) <= 1e-6, err
         hit.add(int(np.argmin(err)))
